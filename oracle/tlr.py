@@ -1,0 +1,270 @@
+"""Tile low rank matrix, left-looking TLR Cholesky / LDL^T, solve, logdet (oracle; test infrastructure).
+
+Format (Section 1, Figure 1): the N x N matrix (points in KD order, padded to
+nb*b with identity rows) is cut into b x b tiles; diagonal tiles are dense,
+each lower off-diagonal tile (i, j), i > j, is U_ij V_ij^T.
+
+Factorization: Algorithm 6 (Cholesky) / Algorithm 10 (LDL^T), left looking.
+For k = 0 .. nb-1:
+  * updateDense (Section 4.3): D_k = sum_{j<k} L(k,j) L(k,j)^T
+      = sum_j U_kj (V_kj^T V_kj) U_kj^T   (LDL^T: V_kj^T D_j V_kj in the middle),
+    A(k,k) <- A(k,k) - D_k (+ compensation, Section 5.1);
+  * chol / ldl of the diagonal tile;
+  * every tile below: T = A(i,k) - sum_{j<k} U_ij V_ij^T [D_j] V_kj U_kj^T
+    (Equation 1 / Equation 3), formed densely here, compressed to eps
+    (truncated SVD by default, or ARA with the same Gaussian blocks as the
+    CUDA path), T ~= Q B^T;
+  * batchTrsm: V_ik = L_kk^{-1} B (LDL^T: D_k^{-1} L_kk^{-1} B, batchIDMult),
+    U_ik = Q (Section 4.3: compress first, then the triangular solve).
+Solve: Algorithm 7 (forward), its transpose (backward), D^{-1} in between for LDL^T.
+logdet: 2 sum log diag(L_kk) (Cholesky) or sum log|D| (LDL^T).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import compress as C
+from . import dense as Dn
+from . import kdtree, kernel, philox
+
+STREAM_COMPRESS = 1
+STREAM_FACTOR = 2
+STREAM_SCHUR = 3
+
+
+@dataclass
+class TLR:
+    N: int
+    b: int
+    nb: int
+    perm: np.ndarray
+    xo: np.ndarray
+    diag: list = field(default_factory=list)   # dense b x b tiles (A_kk, then L_kk)
+    U: dict = field(default_factory=dict)      # (i, j) -> b x r
+    V: dict = field(default_factory=dict)
+    d: list | None = None                      # LDL^T: D_k as vectors
+    kind: str = "A"                            # "A", "chol" or "ldlt"
+    rounds: dict = field(default_factory=dict)  # ARA rounds per tile (diagnostics)
+
+    def rank(self, i: int, j: int) -> int:
+        return self.U[(i, j)].shape[1]
+
+    def ranks(self) -> np.ndarray:
+        R = np.zeros((self.nb, self.nb), dtype=np.int64)
+        for (i, j), u in self.U.items():
+            R[i, j] = u.shape[1]
+        return R
+
+    def tile_dense(self, i: int, j: int) -> np.ndarray:
+        if i == j:
+            return self.diag[i]
+        if i > j:
+            return self.U[(i, j)] @ self.V[(i, j)].T
+        return (self.U[(j, i)] @ self.V[(j, i)].T).T
+
+    def to_dense(self) -> np.ndarray:
+        """Dense padded matrix (A) or dense L (factors), permuted order."""
+        n = self.nb * self.b
+        M = np.zeros((n, n))
+        b = self.b
+        for i in range(self.nb):
+            for j in range(self.nb):
+                if self.kind != "A" and j > i:
+                    continue
+                M[i * b:(i + 1) * b, j * b:(j + 1) * b] = self.tile_dense(i, j)
+        return M
+
+
+def _compressor(name: str, eps: float, bs: int, seed: int, stream: int, k: int, b: int):
+    if name == "svd":
+        return lambda T: (*C.svd_truncate(T, eps), 0)
+    if name == "ara":
+        return lambda T: C.ara_dense(T, bs, eps, lambda t: philox.omega(seed, stream, k, t, b, bs))
+    raise ValueError(name)
+
+
+def build(points: np.ndarray, b: int, eps: float, ell: float, nugget: float,
+          compressor: str = "svd", bs: int = 16, seed: int = 0) -> TLR:
+    """KD-order the points and compress every lower off-diagonal tile to eps (Section 6)."""
+    points = np.asarray(points, dtype=np.float64)
+    N = points.shape[0]
+    perm = kdtree.kd_order(points, b)
+    xo = points[perm]
+    nb = max(1, -(-N // b))
+    A = TLR(N=N, b=b, nb=nb, perm=perm, xo=xo)
+    A.diag = [kernel.tile(xo, k, k, b, ell, nugget) for k in range(nb)]
+    comp = _compressor(compressor, eps, bs, seed, STREAM_COMPRESS, 0, b)
+    for j in range(nb):
+        for i in range(j + 1, nb):
+            Q, B, t = comp(kernel.tile(xo, i, j, b, ell, nugget))
+            A.U[(i, j)], A.V[(i, j)] = Q, B
+            A.rounds[(i, j)] = t
+    return A
+
+
+def _diag_update(F: TLR, k: int) -> np.ndarray:
+    """D_k = sum_{j<k} L(k,j) [D_j] L(k,j)^T, formed densely (updateDense, Section 4.3)."""
+    b = F.b
+    Dk = np.zeros((b, b))
+    for j in range(k):
+        U, V = F.U[(k, j)], F.V[(k, j)]
+        mid = V.T @ (V if F.d is None else F.d[j][:, None] * V)
+        Dk += U @ mid @ U.T
+    return Dk
+
+
+def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: int = 16,
+           seed: int = 0, compensation: str | None = None, shift: float = 0.0) -> TLR:
+    """Left-looking TLR Cholesky (Algorithm 6) or LDL^T (Algorithm 10); returns the factor.
+
+    compensation: None, "shift" (A + shift*I, Section 5.1) or "schur"
+    (A(k,k) - D_k + diag(rowsum|D_k - Dbar_k|), Section 5.1.1, with Dbar_k the
+    compressor's eps-approximation Q Q^T D_k Q Q^T).
+    Raises dense.NotPositiveDefinite with attribute `.tile` on breakdown.
+    """
+    b, nb = A.b, A.nb
+    F = TLR(N=A.N, b=b, nb=nb, perm=A.perm, xo=A.xo, kind="ldlt" if ldl else "chol")
+    F.d = [None] * nb if ldl else None
+    for k in range(nb):
+        Dk = _diag_update(F, k)
+        Akk = A.diag[k] - Dk
+        if compensation == "shift":
+            Akk = Akk + shift * np.eye(b)
+        elif compensation == "schur" and k > 0:
+            Q, _, _ = _compressor(compressor, eps, bs, seed, STREAM_SCHUR, k, b)(Dk)
+            Dbar = Q @ (Q.T @ Dk @ Q) @ Q.T
+            Akk = Akk + np.diag(np.sum(np.abs(Dk - Dbar), axis=1))
+        try:
+            if ldl:
+                Lkk, dk = Dn.ldlt(Akk)
+                F.d[k] = dk
+            else:
+                Lkk = Dn.cholesky(Akk)
+        except Dn.NotPositiveDefinite as ex:
+            ex.tile = k
+            raise
+        F.diag.append(Lkk)
+        comp = _compressor(compressor, eps, bs, seed, STREAM_FACTOR, k, b)
+        for i in range(k + 1, nb):
+            # Equation 1 / 3: T = A(i,k) - sum_j U_ij V_ij^T [D_j] V_kj U_kj^T
+            T = A.U[(i, k)] @ A.V[(i, k)].T
+            for j in range(k):
+                Vk = F.V[(k, j)] if F.d is None else F.d[j][:, None] * F.V[(k, j)]
+                T -= F.U[(i, j)] @ ((F.V[(i, j)].T @ Vk) @ F.U[(k, j)].T)
+            Q, B, t = comp(T)
+            Vik = Dn.solve_lower(Lkk, B, unit=ldl)          # batchTrsm
+            if ldl:
+                Vik = Vik / F.d[k][:, None]                  # batchIDMult
+            F.U[(i, k)], F.V[(i, k)] = Q, Vik.reshape(b, -1)
+            F.rounds[(i, k)] = t
+    return F
+
+
+def _to_perm(F: TLR, Y: np.ndarray) -> np.ndarray:
+    Y = np.asarray(Y, dtype=np.float64).reshape(F.N, -1)
+    X = np.zeros((F.nb * F.b, Y.shape[1]))
+    X[: F.N] = Y[F.perm]
+    return X
+
+
+def _from_perm(F: TLR, X: np.ndarray) -> np.ndarray:
+    Y = np.empty((F.N, X.shape[1]))
+    Y[F.perm] = X[: F.N]
+    return Y
+
+
+def solve(F: TLR, Y: np.ndarray) -> np.ndarray:
+    """X = (L L^T)^{-1} Y or (L D L^T)^{-1} Y; Y in the original point order (N x nrhs)."""
+    b, nb = F.b, F.nb
+    unit = F.kind == "ldlt"
+    X = _to_perm(F, Y)
+    blk = lambda k: slice(k * b, (k + 1) * b)
+    # forward, Algorithm 7: x(k) = L_kk^{-1} x(k); x(i) -= U_ik (V_ik^T x(k)), i > k
+    for k in range(nb):
+        X[blk(k)] = Dn.solve_lower(F.diag[k], X[blk(k)], unit=unit)
+        for i in range(k + 1, nb):
+            X[blk(i)] -= F.U[(i, k)] @ (F.V[(i, k)].T @ X[blk(k)])
+    if unit:
+        X /= np.concatenate(F.d)[:, None]
+    # backward (transpose of Algorithm 7): x(k) -= sum_{i>k} V_ik (U_ik^T x(i)); x(k) = L_kk^{-T} x(k)
+    for k in range(nb - 1, -1, -1):
+        for i in range(k + 1, nb):
+            X[blk(k)] -= F.V[(i, k)] @ (F.U[(i, k)].T @ X[blk(i)])
+        X[blk(k)] = Dn.solve_upper_t(F.diag[k], X[blk(k)], unit=unit)
+    return _from_perm(F, X)
+
+
+def logdet(F: TLR) -> float:
+    """log det of the factored matrix: 2 sum log diag(L_kk), or sum log|D| for LDL^T."""
+    if F.kind == "ldlt":
+        return float(sum(np.sum(np.log(np.abs(dk))) for dk in F.d))
+    return float(2.0 * sum(np.sum(np.log(np.diag(L))) for L in F.diag))
+
+
+def matvec(F: TLR, X: np.ndarray, op: str = "LLt") -> np.ndarray:
+    """TLR products in the original point order.
+
+    op: "A" (F must be a TLR of A, symmetric product), "L", "Lt", or "LLt"
+    (L L^T, or L D L^T for an LDL^T factor).
+    """
+    b, nb = F.b, F.nb
+    Xp = _to_perm(F, X)
+    blk = lambda k: slice(k * b, (k + 1) * b)
+
+    def mulL(Z):
+        Y = np.zeros_like(Z)
+        for i in range(nb):
+            Y[blk(i)] = F.diag[i] @ Z[blk(i)]
+            for j in range(i):
+                Y[blk(i)] += F.U[(i, j)] @ (F.V[(i, j)].T @ Z[blk(j)])
+        return Y
+
+    def mulLt(Z):
+        Y = np.zeros_like(Z)
+        for j in range(nb):
+            Y[blk(j)] = F.diag[j].T @ Z[blk(j)]
+            for i in range(j + 1, nb):
+                Y[blk(j)] += F.V[(i, j)] @ (F.U[(i, j)].T @ Z[blk(i)])
+        return Y
+
+    if op == "A":
+        Y = np.zeros_like(Xp)
+        for i in range(nb):
+            Y[blk(i)] += F.diag[i] @ Xp[blk(i)]
+            for j in range(i):
+                Y[blk(i)] += F.U[(i, j)] @ (F.V[(i, j)].T @ Xp[blk(j)])
+                Y[blk(j)] += F.V[(i, j)] @ (F.U[(i, j)].T @ Xp[blk(i)])
+    elif op == "L":
+        Y = mulL(Xp)
+    elif op == "Lt":
+        Y = mulLt(Xp)
+    elif op == "LLt":
+        Z = mulLt(Xp)
+        if F.kind == "ldlt":
+            Z = Z * np.concatenate(F.d)[:, None]
+        Y = mulL(Z)
+    else:
+        raise ValueError(op)
+    return _from_perm(F, Y)
+
+
+def flops_model(F: TLR, A: TLR, bs: int) -> dict:
+    """Paper-model flop counts of the factorization F of A (per-tile chain of Equation 2)."""
+    b, nb = F.b, F.nb
+    out = dict(sample=0.0, project=0.0, diag=0.0, potrf=nb * b ** 3 / 3.0, trsm=0.0)
+    for k in range(nb):
+        for j in range(k):
+            r = F.rank(k, j)
+            out["diag"] += 4.0 * b * r * r + 2.0 * b * b * r
+        for i in range(k + 1, nb):
+            R = A.rank(i, k) + sum(F.rank(k, j) + F.rank(i, j) for j in range(k))
+            t = max(F.rounds.get((i, k), 1), 1)
+            r = F.rank(i, k)
+            out["sample"] += 4.0 * b * bs * t * R
+            out["project"] += 4.0 * b * r * R
+            out["trsm"] += b * b * r
+    out["total"] = sum(out.values())
+    return out

@@ -1,0 +1,114 @@
+"""Planted mistakes in the oracle (CPU only): each plausible error must fail a pin.
+
+A pin is only worth something if a wrong oracle fails it.  These tests patch
+one step of the oracle at a time (dropped term, wrong sign, transposed operand,
+off-by-one) and check that the OU closed-form pin or the dense pin rejects it.
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import dense, kdtree, kernel, tlr
+
+
+def _ou_ok(ldl=False):
+    try:
+        return _ou_check(ldl)
+    except dense.NotPositiveDefinite:
+        return False
+
+
+def _ou_check(ldl):
+    N, b, ell = 256, 32, 0.3
+    x = inputs.points(N, 1, 8)
+    A = tlr.build(x, b, 1e-12, ell, 0.0)
+    F = tlr.factor(A, 1e-12, ldl=ldl)
+    xs = A.xo[:, 0]
+    s = np.ones(N)
+    s[1:] = np.sqrt(1.0 - np.exp(-2.0 * np.diff(xs) / ell))
+    Lex = np.tril(np.exp(-(xs[:, None] - xs[None, :]) / ell) * s[None, :])
+    ld = float(np.sum(np.log(1.0 - np.exp(-2.0 * np.diff(xs) / ell))))
+    Ld = F.to_dense()
+    if ldl:
+        Ld = Ld * np.sqrt(np.concatenate(F.d))[None, :]
+    return np.allclose(Ld, Lex, atol=1e-8) and abs(tlr.logdet(F) - ld) < 1e-8 * abs(ld)
+
+
+def _dense_ok():
+    try:
+        return _dense_check()
+    except dense.NotPositiveDefinite:
+        return False
+
+
+def _dense_check():
+    x = inputs.points(600, 2, 2)
+    A = tlr.build(x, 128, 1e-13, 0.1, 1e-4)
+    F = tlr.factor(A, 1e-13)
+    Ad = kernel.dense(x, 0.1, 1e-4)
+    return np.linalg.norm(tlr.matvec(F, np.eye(600), "LLt") - Ad, 2) < 1e-9 * np.linalg.norm(Ad, 2)
+
+
+def test_unmutated_oracle_passes():
+    assert _ou_ok() and _ou_ok(ldl=True) and _dense_ok()
+
+
+def test_dropped_term_in_diag_update_is_caught(monkeypatch):
+    orig = tlr._diag_update
+
+    def drop_last(F, k):
+        D = orig(F, k)
+        if k > 0:
+            U, V = F.U[(k, k - 1)], F.V[(k, k - 1)]
+            D -= U @ (V.T @ V) @ U.T
+        return D
+    monkeypatch.setattr(tlr, "_diag_update", drop_last)
+    assert not _ou_ok()
+
+
+def test_wrong_sign_in_trsm_is_caught(monkeypatch):
+    orig = dense.solve_lower
+    monkeypatch.setattr(dense, "solve_lower", lambda L, B, unit=False: -orig(L, B, unit))
+    assert not _ou_ok()
+
+
+def test_transposed_triangular_operand_is_caught(monkeypatch):
+    orig = dense.solve_lower
+    monkeypatch.setattr(dense, "solve_lower", lambda L, B, unit=False: np.linalg.solve(L.T, B))
+    assert not _dense_ok()
+
+
+def test_missing_D_in_ldl_chain_is_caught(monkeypatch):
+    orig = tlr._diag_update
+
+    def no_d(F, k):
+        saved = F.d
+        F.d = None
+        try:
+            return orig(F, k)
+        finally:
+            F.d = saved
+    monkeypatch.setattr(tlr, "_diag_update", no_d)
+    assert not _ou_ok(ldl=True)
+
+
+def test_kd_split_off_by_one_is_caught(monkeypatch):
+    # the leaf-size rule of Section 6: all leaves hold b points except possibly the last
+    x = inputs.points(1000, 2, 3)
+    monkeypatch.setattr(kdtree, "_left_size", lambda n, b: n // 2)
+    perm = kdtree.kd_order(x, 64)
+    monkeypatch.undo()
+    assert not np.array_equal(perm, kdtree.kd_order(x, 64))
+
+
+def test_wrong_sign_in_left_looking_update_is_caught(monkeypatch):
+    # Equation 1 with "+" instead of "-": patch the dense form of T through the compressor hook
+    orig = tlr._compressor
+
+    def flip(name, eps, bs, seed, stream, k, b):
+        c = orig(name, eps, bs, seed, stream, k, b)
+        if stream != tlr.STREAM_FACTOR:
+            return c
+        return lambda T: c(-T)
+    monkeypatch.setattr(tlr, "_compressor", flip)
+    assert not _ou_ok()

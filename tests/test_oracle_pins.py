@@ -1,0 +1,263 @@
+"""Pins for the oracle: each test checks it against something other than itself
+(published known answers, closed forms, library routines, Eckart-Young, brute force)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import compress, dense, kdtree, kernel, measures, philox, tlr
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox_kat.txt")) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(h, 16) for h in r]
+        out = philox.philox4x32_10(np.array([v[:4]], dtype=np.uint64), (v[4], v[5]))
+        assert [int(o) for o in out[0]] == v[6:10]
+
+
+def test_omega_gaussian_statistics_and_layout():
+    Om = philox.omega(7, 2, 3, 1, 256, 16)
+    assert Om.shape == (256, 16)
+    z = Om.ravel()
+    assert abs(z.mean()) < 0.05 and abs(z.std() - 1.0) < 0.05
+    # column-major element order: a taller block shares its leading elements column by column
+    Om2 = philox.omega(7, 2, 3, 1, 128, 32)
+    assert np.array_equal(Om.T.ravel()[:4096], Om2.T.ravel()[:4096])
+    # distinct rounds / columns / streams give independent blocks
+    assert not np.allclose(Om, philox.omega(7, 2, 3, 2, 256, 16))
+    assert not np.allclose(Om, philox.omega(7, 2, 4, 1, 256, 16))
+    assert not np.allclose(Om, philox.omega(7, 1, 3, 1, 256, 16))
+
+
+# ---------------------------------------------------------------- KD ordering
+def test_kd_order_1d_is_sorted_order():
+    x = inputs.points(1000, 1, 3)
+    perm = kdtree.kd_order(x, 64)
+    assert np.array_equal(perm, np.argsort(x[:, 0], kind="stable"))
+
+
+@pytest.mark.parametrize("N,b,d", [(4096, 256, 2), (3000, 256, 3), (1000, 128, 2), (100, 128, 2)])
+def test_kd_order_structure(N, b, d):
+    x = inputs.points(N, d, 1)
+    perm = kdtree.kd_order(x, b)
+    assert np.array_equal(np.sort(perm), np.arange(N))
+
+    def check(idx_ordered, n):
+        if n <= b:
+            return
+        pts = x[idx_ordered]
+        ext = pts.max(0) - pts.min(0)
+        ax = int(np.argmax(ext))
+        p = math.ceil(math.log2(n / b))
+        nl = b * 2 ** (p - 1)
+        left, right = idx_ordered[:nl], idx_ordered[nl:]
+        assert x[left, ax].max() <= x[right, ax].min()
+        check(left, nl)
+        check(right, n - nl)
+
+    check(perm, N)
+
+
+# ---------------------------------------------------------------- dense factorizations
+def _spd(n, seed):
+    rng = np.random.default_rng(seed)
+    M = rng.standard_normal((n, n))
+    return M @ M.T + n * np.eye(n)
+
+
+def test_cholesky_matches_lapack():
+    A = _spd(60, 0)
+    L = dense.cholesky(A)
+    assert np.allclose(L, np.linalg.cholesky(A), rtol=1e-12, atol=1e-12)
+    assert np.allclose(L, np.tril(L))
+
+
+def test_ldlt_closed_form_from_cholesky():
+    A = _spd(50, 1)
+    C = np.linalg.cholesky(A)
+    L, d = dense.ldlt(A)
+    assert np.allclose(d, np.diag(C) ** 2, rtol=1e-12)
+    assert np.allclose(L, C / np.diag(C)[None, :], rtol=1e-11, atol=1e-12)
+    assert np.allclose(np.diag(L), 1.0)
+
+
+def test_ldlt_indefinite_without_pivoting():
+    A = np.array([[2.0, 1.0, 0.0], [1.0, -3.0, 1.0], [0.0, 1.0, 4.0]])
+    L, d = dense.ldlt(A)
+    assert np.allclose(L @ np.diag(d) @ L.T, A, atol=1e-14)
+    assert (d < 0).sum() == 1  # Sylvester's law of inertia: one negative eigenvalue
+    assert (np.linalg.eigvalsh(A) < 0).sum() == 1
+
+
+def test_cholesky_reports_failing_column():
+    A = np.diag([1.0, 2.0, -1.0, 3.0])
+    with pytest.raises(dense.NotPositiveDefinite) as ei:
+        dense.cholesky(A)
+    assert ei.value.index == 2
+
+
+def test_triangular_solves_match_library():
+    import scipy.linalg as sl
+    A = _spd(40, 2)
+    L = np.linalg.cholesky(A)
+    B = np.random.default_rng(3).standard_normal((40, 3))
+    assert np.allclose(dense.solve_lower(L, B), sl.solve_triangular(L, B, lower=True), rtol=1e-12)
+    assert np.allclose(dense.solve_upper_t(L, B), sl.solve_triangular(L.T, B, lower=False), rtol=1e-12)
+    Lu = np.tril(L, -1) + np.eye(40)
+    assert np.allclose(dense.solve_lower(Lu, B, unit=True), sl.solve_triangular(Lu, B, lower=True, unit_diagonal=True))
+
+
+# ---------------------------------------------------------------- compressors
+def _low_rank(m, n, r, seed, decay=None):
+    rng = np.random.default_rng(seed)
+    X, _ = np.linalg.qr(rng.standard_normal((m, r)))
+    Y, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    s = np.ones(r) if decay is None else decay ** np.arange(r)
+    return (X * s) @ Y.T, s
+
+
+def test_svd_truncate_eckart_young():
+    T, s = _low_rank(100, 80, 30, 0, decay=0.5)
+    for eps in [1e-1, 1e-3, 1e-6]:
+        Q, B = compress.svd_truncate(T, eps)
+        r = Q.shape[1]
+        assert r == int(np.sum(s > eps))
+        err = np.linalg.norm(T - Q @ B.T, 2)
+        assert err <= eps * (1 + 1e-8)
+        assert abs(err - (s[r] if r < 30 else 0.0)) < 1e-12
+        assert np.allclose(Q.T @ Q, np.eye(r), atol=1e-13)
+
+
+def test_svd_truncate_exact_rank():
+    T, _ = _low_rank(64, 64, 7, 1)
+    Q, B = compress.svd_truncate(T, 1e-10)
+    assert Q.shape[1] == 7
+
+
+def test_chol_drop_keeps_rank_of_deficient_panel():
+    rng = np.random.default_rng(4)
+    Y = rng.standard_normal((50, 3)) @ rng.standard_normal((3, 8))  # rank 3, 8 columns
+    R, keep = compress.chol_drop(Y.T @ Y, 0.0)
+    assert len(keep) == 3 and keep == [0, 1, 2]
+    assert np.allclose(R.T @ R, (Y.T @ Y)[np.ix_(keep, keep)], rtol=1e-10)
+
+
+@pytest.mark.parametrize("r,bs", [(5, 16), (16, 16), (40, 16), (70, 32)])
+def test_ara_exact_rank_and_bound(r, bs):
+    T, _ = _low_rank(256, 256, r, 5)
+    om = lambda t: philox.omega(11, 9, 0, t, 256, bs)
+    Q, B, t = compress.ara_dense(T, bs, 1e-8, om)
+    assert Q.shape[1] == r  # exactly the rank of T: more columns would be noise below tau
+    assert np.allclose(Q.T @ Q, np.eye(Q.shape[1]), atol=1e-13)
+    assert np.linalg.norm(T - Q @ B.T, 2) <= 1e-8
+
+
+def test_ara_error_bound_holds_over_seeds():
+    T, s = _low_rank(200, 200, 60, 6, decay=0.7)
+    for seed in range(8):
+        for eps in [1e-2, 1e-5, 1e-9]:
+            Q, B, _ = compress.ara_dense(T, 16, eps, lambda t: philox.omega(seed, 9, 0, t, 200, 16))
+            assert np.linalg.norm(T - Q @ B.T, 2) <= eps
+            assert Q.shape[1] >= int(np.sum(s > eps))  # never below the optimal (SVD) rank
+
+
+def test_ara_zero_tile_has_rank_zero():
+    Q, B, t = compress.ara_dense(np.zeros((64, 64)), 16, 1e-6, lambda t: philox.omega(0, 9, 0, t, 64, 16))
+    assert Q.shape == (64, 0) and t == 1
+
+
+# ---------------------------------------------------------------- OU closed form (1D exponential kernel)
+def _ou_closed_form(x, ell):
+    """Exact Cholesky factor of exp(-|x_i - x_j|/ell) for sorted 1D x (Ornstein-Uhlenbeck covariance)."""
+    n = len(x)
+    s = np.ones(n)
+    s[1:] = np.sqrt(1.0 - np.exp(-2.0 * np.diff(x) / ell))
+    L = np.exp(-(x[:, None] - x[None, :]) / ell) * s[None, :]
+    return np.tril(L), float(np.sum(np.log(1.0 - np.exp(-2.0 * np.diff(x) / ell))))
+
+
+@pytest.mark.parametrize("compressor", ["svd", "ara"])
+def test_tlr_ou_closed_form(compressor):
+    N, b, ell = 512, 64, 0.3
+    x = inputs.points(N, 1, 8)
+    A = tlr.build(x, b, 1e-12, ell, 0.0, compressor=compressor, bs=8)
+    xs = A.xo[:, 0]
+    assert np.all(np.diff(xs) > 0)
+    F = tlr.factor(A, 1e-12, compressor=compressor, bs=8)
+    Lex, ld = _ou_closed_form(xs, ell)
+    assert A.ranks()[np.tril_indices(A.nb, -1)].max() == 1  # every off-diagonal tile is rank 1
+    lr = F.ranks()[np.tril_indices(F.nb, -1)]
+    # SVD keeps sigma_2 <= eps: exact rank 1.  ARA tests against eps/(10 sqrt(2/pi)), so the
+    # eps-level errors of earlier columns can add one direction to a tile.
+    assert lr.max() == 1 if compressor == "svd" else (lr.max() <= 2 and lr.mean() < 1.5)
+    assert np.allclose(F.to_dense(), Lex, atol=1e-9)
+    assert abs(tlr.logdet(F) - ld) < 1e-8 * abs(ld)
+    G = tlr.factor(A, 1e-12, ldl=True, compressor=compressor, bs=8)
+    assert abs(tlr.logdet(G) - ld) < 1e-8 * abs(ld)
+
+
+# ---------------------------------------------------------------- TLR oracle vs dense at tight eps
+@pytest.mark.parametrize("N,b,d", [(1024, 128, 2), (1500, 256, 3)])
+def test_tlr_matches_dense_at_tight_eps(N, b, d):
+    ell, nug = (0.1 if d == 2 else 0.2), 1e-4
+    x = inputs.points(N, d, 2)
+    A = tlr.build(x, b, 1e-14, ell, nug)
+    F = tlr.factor(A, 1e-14)
+    Ad = kernel.dense(x, ell, nug)
+    FF = tlr.matvec(F, np.eye(N), "LLt")
+    assert np.linalg.norm(FF - Ad, 2) / np.linalg.norm(Ad, 2) < 1e-10
+    s, ld = np.linalg.slogdet(Ad)
+    assert s > 0 and abs(tlr.logdet(F) - ld) < 1e-10 * abs(ld)
+    Y = inputs.rhs(N, 2, 4)
+    assert np.allclose(tlr.solve(F, Y), np.linalg.solve(Ad, Y), rtol=1e-6, atol=1e-8 * np.abs(np.linalg.solve(Ad, Y)).max())
+    G = tlr.factor(A, 1e-14, ldl=True)
+    assert abs(tlr.logdet(G) - ld) < 1e-10 * abs(ld)
+    # padded last tile (N not a multiple of b): padding rows of L are identity
+    if N % b:
+        Ld = F.to_dense()
+        assert np.allclose(Ld[N:, N:], np.eye(F.nb * b - N))
+
+
+def test_tlr_matvec_A_matches_dense():
+    x = inputs.points(700, 2, 5)
+    A = tlr.build(x, 128, 1e-12, 0.1, 1e-4)
+    X = inputs.rhs(700, 3, 1)
+    assert np.allclose(tlr.matvec(A, X, "A"), kernel.dense(x, 0.1, 1e-4) @ X, atol=1e-9)
+
+
+# ---------------------------------------------------------------- invariants at working eps
+def test_invariants_cov2d_small():
+    N, b, eps = 2048, 256, 1e-6
+    x = inputs.points(N, 2, 0)
+    A = tlr.build(x, b, eps, 0.1, 1e-4)
+    F = tlr.factor(A, eps)
+    G = tlr.factor(A, eps, ldl=True)
+    assert all(np.all(np.diag(L) > 0) for L in F.diag)
+    assert all(np.all(dk > 0) for dk in G.d)
+    low = F.ranks()[np.tril_indices(F.nb, -1)]
+    assert low.max() <= b // 2
+    Ad = kernel.dense(x, 0.1, 1e-4)
+    x0 = inputs.start_vector(N)
+    be = measures.backward_error(lambda v: Ad @ v, lambda v: tlr.matvec(F, v, "LLt")[:, 0], x0)
+    assert be <= 10 * eps
+    assert abs(tlr.logdet(F) - tlr.logdet(G)) <= 1e-3 * abs(tlr.logdet(F))
+
+
+# ---------------------------------------------------------------- measures
+def test_power_norm_diagonal():
+    d = np.array([1.0, -7.0, 3.0, 0.5])
+    assert abs(measures.power_norm(lambda v: d * v, np.ones(4), 200) - 7.0) < 1e-10
+
+
+def test_backward_error_of_exact_factor_is_rounding_level():
+    A = _spd(80, 9)
+    L = np.linalg.cholesky(A)
+    be = measures.backward_error(lambda v: A @ v, lambda v: L @ (L.T @ v), np.ones(80))
+    assert be < 1e-14
