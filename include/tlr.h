@@ -1,0 +1,221 @@
+/*
+ * tlr.h -- C ABI of the GB300 tile-low-rank (TLR) Cholesky / LDL^T library.
+ *
+ * Method: Boukaram, Zampini, Turkiyyah, Keyes, "H2OPUS-TLR: High Performance
+ * Tile Low Rank Symmetric Factorizations using Adaptive Randomized
+ * Approximation" (arXiv 2108.11932).  Section and algorithm numbers below
+ * refer to that paper.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a tlr_status; no C++ exception crosses the ABI.
+ *   - Work is enqueued on the context's CUDA stream.  Calls that return host
+ *     values (logdet, info, ranks, tile export) synchronize that stream.
+ *   - Inputs are owned by the caller and only read during the call.  Objects
+ *     returned through `tlr_mat**` are owned by the library until tlr_free.
+ *   - Matrices are column-major FP64 unless stated.  "device" pointers must be
+ *     device memory of the context's GPU; "host" pointers are plain host memory.
+ *   - Point order: callers pass points, right-hand sides and vectors in their
+ *     ORIGINAL order; the library keeps the KD-tree permutation internally.
+ *   - A failed factorization leaves the matrix in state FAILED; every later
+ *     call on it except tlr_info/tlr_free returns TLR_ERR_STATE.
+ */
+#ifndef TLR_GB300_H
+#define TLR_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tlr_ctx tlr_ctx; /* device, stream, allocator, workspaces */
+typedef struct tlr_mat tlr_mat; /* a TLR matrix or its factor, device-resident */
+
+typedef enum {
+  TLR_OK = 0,
+  TLR_ERR_ARG = -1,      /* invalid argument (null pointer, bad size, bad option) */
+  TLR_ERR_NOMEM = -2,    /* device or host allocation failed */
+  TLR_ERR_NOT_SPD = -3,  /* a diagonal tile lost definiteness (Section 5.1); see tlr_info.k_fail */
+  TLR_ERR_CUDA = -4,     /* a CUDA runtime call failed */
+  TLR_ERR_TIMEOUT = -5,  /* a bounded device wait expired */
+  TLR_ERR_STATE = -6,    /* object in the wrong state (e.g. solve on an unfactored matrix) */
+  TLR_ERR_LIMIT = -7     /* a size exceeds a compiled-in limit */
+} tlr_status;
+
+/* Kernel of the generated covariance matrix (Section 6):
+ *   A_ij = exp(-||x_i - x_j||_2 / ell) + nugget * delta_ij.                   */
+enum { TLR_KERNEL_EXP = 0 };
+typedef struct {
+  int type;      /* TLR_KERNEL_EXP */
+  double ell;    /* length scale > 0 */
+  double nugget; /* >= 0, added to the diagonal */
+} tlr_kernel;
+
+/* Arithmetic of the ARA sampling / projection products (the chains of
+ * Equation 2 / Equation 3).  Orthogonalization, convergence norms, the dense
+ * diagonal-tile factorization and the triangular solves are FP64 always.     */
+enum {
+  TLR_PREC_FP64 = 0, /* everything FP64 */
+  TLR_PREC_FP32 = 1  /* sampling/projection chains in FP32 with FP32 accumulation */
+};
+
+/* Definiteness safeguards (Section 5.1). */
+enum {
+  TLR_COMP_NONE = 0,
+  TLR_COMP_SHIFT = 1, /* factor A + shift*I (Section 5.1, "diagonal shifting") */
+  TLR_COMP_SCHUR = 2  /* A(k,k) - D_k + diag(rowsum|D_k - Dbar_k|) (Section 5.1.1) */
+};
+
+typedef struct {
+  int bs;           /* ARA sampling block width (Algorithm 1), 1..64; 0 = 16 */
+  int max_slots;    /* dynamic-batch width: tiles sampled concurrently (Algorithm 5
+                       subset ri); 0 = every tile of the column */
+  int precision;    /* TLR_PREC_* */
+  int compensation; /* TLR_COMP_* */
+  double shift;     /* diagonal shift for TLR_COMP_SHIFT (Section 5.1: s <= eps) */
+  uint64_t seed;    /* Philox key of the Gaussian blocks */
+  int ldl;          /* internal: set by tlr_ldlt */
+  int reserved[7];
+} tlr_opts;
+
+/* Fill `o` with defaults: bs 16, all tiles in the batch, FP64, no compensation, seed 0. */
+void tlr_opts_default(tlr_opts* o);
+
+/* Optional device allocator.  If both are NULL the library uses
+ * cudaMallocAsync/cudaFreeAsync on the context stream.  `alloc` returns NULL on
+ * failure (the call then returns TLR_ERR_NOMEM). */
+typedef void* (*tlr_alloc_fn)(size_t bytes, void* user);
+typedef void (*tlr_free_fn)(void* ptr, void* user);
+
+/* Create a context on `device`, enqueuing work on `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream). */
+tlr_status tlr_create(tlr_ctx** ctx, int device, void* cuda_stream, tlr_alloc_fn alloc,
+                      tlr_free_fn free_fn, void* user);
+tlr_status tlr_destroy(tlr_ctx* ctx);
+
+/* TLR construction (Section 1, Figure 1; Section 6 clustering paragraph):
+ * KD-order the N points (host, row-major N x d, d in 1..3), generate the kernel
+ * matrix tile by tile on the device and compress every lower off-diagonal b x b
+ * tile with batched ARA (Algorithm 1) to the absolute 2-norm threshold eps.
+ * Diagonal tiles stay dense.  If b does not divide N the last tile is padded
+ * with identity rows/columns.  *A receives a new matrix in state "A". */
+tlr_status tlr_compress(tlr_ctx* ctx, const double* points_host, int64_t N, int d,
+                        const tlr_kernel* kernel, int b, double eps, const tlr_opts* opts,
+                        tlr_mat** A);
+
+/* Deep copy (device-to-device) of a TLR matrix or factor. */
+tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* src, tlr_mat** dst);
+
+/* Left-looking TLR Cholesky, Algorithm 6 (updateDense, chol, cholARAUpdate
+ * with dynamic batching per Algorithm 5, batchTrsm, updateTiles).  In place:
+ * A := L with A ~= L L^T.  Every updated tile is recompressed to eps.
+ * TLR_ERR_NOT_SPD if a diagonal tile is not positive definite (k_fail in tlr_info). */
+tlr_status tlr_potrf(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts);
+
+/* Pivot-free left-looking TLR LDL^T, Algorithm 10 (five-product sampling
+ * chain of Equation 3, dense unpivoted LDL^T of the diagonal tiles, batchTrsm
+ * followed by batchIDMult).  In place: A := (L, D), L unit lower on the diagonal
+ * tiles.  TLR_ERR_NOT_SPD if a pivot of D is exactly zero or not finite. */
+tlr_status tlr_ldlt(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts);
+
+/* Solve (L L^T) X = B or (L D L^T) X = B with the TLR triangular solve of
+ * Algorithm 7 (forward) and its transpose (backward).  B: device, N x nrhs,
+ * leading dimension ldb >= N, original point order; overwritten with X. */
+tlr_status tlr_solve(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* B, int64_t ldb);
+
+/* log|det| of the factored matrix: 2 sum log diag(L_kk) (Cholesky) or
+ * sum log|D_ii| (LDL^T); *sign = sign of the determinant.  Host outputs. */
+tlr_status tlr_logdet(tlr_ctx* ctx, const tlr_mat* F, double* logdet, int* sign);
+
+/* Matrix products with the TLR data (Section 4.4), original point order:
+ *   op TLR_OP_A   : Y = A X     (F in state "A": symmetric TLR product)
+ *   op TLR_OP_L   : Y = L X     (factor)
+ *   op TLR_OP_LT  : Y = L^T X   (factor)
+ *   op TLR_OP_LLT : Y = L L^T X or L D L^T X (factor)
+ * X, Y: device, N x nrhs, leading dimensions ldx, ldy >= N; X and Y must not overlap. */
+enum { TLR_OP_A = 0, TLR_OP_L = 1, TLR_OP_LT = 2, TLR_OP_LLT = 3 };
+tlr_status tlr_matvec(tlr_ctx* ctx, const tlr_mat* F, int op, int nrhs, const double* X,
+                      int64_t ldx, double* Y, int64_t ldy);
+
+/* Exact kernel-matrix product Y = A X, A generated on the fly from the points
+ * (used to measure backward errors and residuals; Section 6 "all results were
+ * verified ...").  Points host row-major N x d in ORIGINAL order; X, Y device
+ * N x nrhs (ldx, ldy >= N). */
+tlr_status tlr_kernel_matvec(tlr_ctx* ctx, const double* points_host, int64_t N, int d,
+                             const tlr_kernel* kernel, int nrhs, const double* X, int64_t ldx,
+                             double* Y, int64_t ldy);
+
+typedef struct {
+  int64_t N;
+  int b, nb, d;
+  int state;           /* 0 = A, 1 = Cholesky factor, 2 = LDL^T factor, 3 = FAILED */
+  int k_fail;          /* failing tile column for TLR_ERR_NOT_SPD, else -1 */
+  int max_rank;        /* over lower off-diagonal tiles */
+  double mean_rank;
+  int64_t bytes;       /* device bytes of the representation */
+  double flops_exec;   /* flops executed by the last factorization (all phases) */
+  double flops_model;  /* paper-model flops: per-tile chains of Equation 2 */
+  double ara_rounds;   /* total ARA rounds of the last factorization (all columns) */
+  double seconds;      /* host wall time of the last factorization call */
+} tlr_info;
+tlr_status tlr_get_info(const tlr_mat* M, tlr_info* info);
+
+/* Ranks of the lower off-diagonal tiles: host int array nb x nb, row-major,
+ * entry (i, j) for i > j, zero elsewhere. */
+tlr_status tlr_get_ranks(tlr_ctx* ctx, const tlr_mat* M, int* ranks);
+
+/* KD permutation: host int64 array, perm[p] = original index of ordered point p. */
+tlr_status tlr_get_perm(const tlr_mat* M, int64_t* perm);
+
+/* Export tiles to host for inspection (KD order, padded, b rows each):
+ *   diagonal tile k (i == j): b x b into U (V unused); LDL^T D_k (b) into V if V != NULL;
+ *   off-diagonal (i > j): U_ij (b x r) into U and V_ij (b x r) into V, r = rank. */
+tlr_status tlr_get_tile(tlr_ctx* ctx, const tlr_mat* M, int i, int j, double* U, double* V);
+
+tlr_status tlr_free(tlr_ctx* ctx, tlr_mat* M);
+const char* tlr_strerror(tlr_status s);
+
+/* ---------------- building blocks (each one step of the method) ---------------- */
+
+/* KD-tree ordering of Section 6 (host only): recursive split along the axis of
+ * largest bounding-box extent (ties: lowest axis), points sorted by (coordinate,
+ * index), left part b * 2^(ceil(log2(n/b)) - 1) points.  perm[p] = original
+ * index of ordered point p.  points: host row-major N x d. */
+tlr_status tlr_kd_order(const double* points, int64_t N, int d, int b, int64_t* perm);
+
+/* Gaussian block Omega (b x bs, column-major, device) for (seed, stream,
+ * column k, round t): Philox4x32-10 (Salmon et al., SC'11) counters
+ * (pair index, t, k, stream), key (seed lo, seed hi), Box-Muller pairs. */
+tlr_status tlr_omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t,
+                     int b, int bs, double* out);
+
+/* Batched ARA (Algorithm 1) on explicit dense n x n operands: T[s] at
+ * T + s*n*n (device, column-major).  Gaussian blocks (seed, stream, k, t) are
+ * shared by all operands of a round.  Outputs per operand s: Q[s] and B[s]
+ * (device, n x n capacity each, column-major, first rank[s] columns used,
+ * T[s] ~= Q B^T) and rank[s] (device int).  eps: absolute 2-norm threshold. */
+tlr_status tlr_ara_dense(tlr_ctx* ctx, int nops, int n, const double* T, int bs, double eps,
+                         uint64_t seed, uint32_t stream, uint32_t k, double* Q, double* B,
+                         int* rank);
+
+/* Dense FP64 Cholesky (lower, in place) of an n x n device matrix (lda >= n);
+ * *info (host) = -1 on success, else the first failing column. */
+tlr_status tlr_dense_potrf(tlr_ctx* ctx, int n, double* A, int lda, int* info);
+/* Dense unpivoted LDL^T (in place: unit L below the diagonal, D on it). */
+tlr_status tlr_dense_ldlt(tlr_ctx* ctx, int n, double* A, int lda, int* info);
+/* X = L^{-1} B in place (L lower n x n, unit diagonal if unit != 0), B n x nrhs. */
+tlr_status tlr_dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int unit, int nrhs,
+                          double* B, int ldb);
+
+/* Measurement utility (not part of the method): FP64 DFMA throughput of this
+ * GPU in TFLOP/s, from a register-resident FMA loop timed with CUDA events. */
+tlr_status tlr_fp64_peak(tlr_ctx* ctx, double* tflops);
+
+/* Number of kernels this library launched on the context since creation. */
+int64_t tlr_launch_count(const tlr_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TLR_GB300_H */

@@ -1,0 +1,198 @@
+// Internal declarations of the GB300 TLR library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/tlr.h"
+
+namespace tlr {
+
+// Error carried inside the library; converted to a tlr_status at the ABI.
+struct Error : std::runtime_error {
+  tlr_status status;
+  Error(tlr_status s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+#define TLR_CUDA(x)                                                                       \
+  do {                                                                                    \
+    cudaError_t e_ = (x);                                                                 \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::tlr::Error(TLR_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TLR_REQUIRE(c, st, msg) \
+  do {                          \
+    if (!(c)) throw ::tlr::Error((st), (msg)); \
+  } while (0)
+
+// Launch bookkeeping: every kernel launch of the library goes through this.
+#define TLR_LAUNCH_CHECK(ctx) \
+  do {                        \
+    (ctx)->launches++;        \
+    TLR_CUDA(cudaPeekAtLastError()); \
+  } while (0)
+
+// Ω streams: which factorization step a Gaussian block belongs to.
+enum : uint32_t { STREAM_COMPRESS = 1, STREAM_FACTOR = 2, STREAM_SCHUR = 3 };
+
+// Column-major batched GEMM job: C(M x N) = alpha * sum_s op(A_s) op(B_s) + beta * C.
+// op(A_s) is M x K_s, op(B_s) is K_s x N.  Up to two K-segments (the products
+// "[U0 | Urow] W" of the sampling chain have two left operands).
+template <typename T>
+struct GemmJob {
+  const T* A[2];
+  const T* B[2];
+  T* C;
+  T* ws;         // split-K partials: nsplit x M x N (column-major), or null
+  int lda[2], ldb[2], K[2];
+  int ldc, M, N;
+  int tile0;     // first linear CTA of this job
+  int tiles_m, tiles_n, nsplit;
+  int flags;     // GEMM_TRIL: write only C(m, n) with m >= n; skip tiles strictly above
+  double alpha, beta;
+};
+enum { GEMM_TRIL = 1 };
+enum GemmMode { NN = 0, TN = 1, NT = 2 };
+
+constexpr int GEMM_TM = 64, GEMM_TN = 32, GEMM_TK = 16;
+
+}  // namespace tlr
+
+// ----------------------------------------------------------------------------------------
+// Library-owned objects.
+struct tlr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  tlr_alloc_fn alloc = nullptr;
+  tlr_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  int sm_count = 0;
+  int64_t launches = 0;
+  // Job upload ring: pinned host staging mirrored by a device buffer.
+  char* pinned = nullptr;
+  char* djobs = nullptr;
+  size_t ring_cap = 0, ring_pos = 0;
+  // Split-K / small scratch, grown on demand (stream-ordered frees).
+  void* scratch = nullptr;
+  size_t scratch_cap = 0;
+  // Small host-pinned status buffer for per-round device->host reads.
+  void* hstatus = nullptr;
+  size_t hstatus_cap = 0;
+};
+
+struct tlr_mat {
+  int64_t N = 0;
+  int d = 0, b = 0, nb = 0;
+  int state = 0;  // 0 A, 1 chol, 2 ldlt, 3 failed
+  int k_fail = -1;
+  tlr_kernel kern{};
+  double eps = 0;
+  std::vector<int64_t> perm;
+  double* pts = nullptr;   // device, ordered points (N x d row-major)
+  double* diag = nullptr;  // device, nb * b * b
+  double* dvec = nullptr;  // device, nb * b (LDL^T D)
+  std::vector<int> rank;   // nb * nb (i > j)
+  std::vector<int64_t> uoff, voff;  // column offsets of U_ij in Urow[i], V_ij in Vcol[j]
+  std::vector<double*> Urow, Vcol;  // per block row / block column panels (device)
+  std::vector<int64_t> ucap;        // capacity (columns) of Urow[i]
+  std::vector<int64_t> vlen;        // columns of Vcol[j]
+  std::vector<int64_t> ulen;        // used columns of Urow[i]
+  // statistics of the last factorization
+  double flops_exec = 0, flops_model = 0, ara_rounds = 0, seconds = 0;
+};
+
+namespace tlr {
+
+// memory
+void* dalloc(tlr_ctx* ctx, size_t bytes);
+void dfree(tlr_ctx* ctx, void* p);
+void* scratch(tlr_ctx* ctx, size_t bytes);
+void* upload(tlr_ctx* ctx, const void* host, size_t bytes);  // returns device copy (ring)
+void* host_status(tlr_ctx* ctx, size_t bytes);               // pinned host buffer
+
+// GEMM (k_gemm.cu)
+template <typename T>
+void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs);
+template <typename T>
+GemmJob<T> job(GemmMode mode, int M, int N, const T* A, int lda, const T* B, int ldb, int K, T* C,
+               int ldc, double alpha, double beta);
+
+// Kernels (k_misc.cu) -- all enqueue on ctx->stream.
+void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t, int b, int bs,
+           double* out);
+void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget, int b,
+               const int* tile_ij /*device, 2 per tile*/, int ntiles, double* out);
+// per-slot orthogonalization helpers (Cholesky-QR with dropping)
+void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mout, int* status,
+                  double* enorm, double thr, double tau, int first_pass, const int* nk_in);
+// dense diagonal-tile factorization pieces
+void potrf_diag_block(tlr_ctx* ctx, int nbk, double* A, int lda, int ldl, double* dvec, int* info,
+                      int col0);
+void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, double* X, int ldx,
+                      int ldl, const double* dvec);
+void trsm_left_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs, double* X,
+                     int ldx);
+void trsm_left_t_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs,
+                       double* X, int ldx);
+void scale_rows(tlr_ctx* ctx, int m, int n, const double* dvec, int inv, const double* X, int ldx,
+                double* Y, int ldy);
+void add_diag(tlr_ctx* ctx, int n, double* A, int lda, double s);
+void add_rowsum_abs(tlr_ctx* ctx, int n, const double* E, int lde, double* A, int lda);
+void logdet_reduce(tlr_ctx* ctx, int n, const double* diag_tiles, int b, int nb, const double* dvec,
+                   double* out2 /*device: [sum log|.|, count negative]*/);
+void kernel_matvec(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget,
+                   int nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy);
+void permute_rows(tlr_ctx* ctx, int64_t n_out, int nrhs, const int64_t* idx, int gather,
+                  const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n_pad);
+void copy_matrix(tlr_ctx* ctx, int m, int n, const double* X, int ldx, double* Y, int ldy);
+void to_float(tlr_ctx* ctx, int64_t n, const double* x, float* y);
+void to_double(tlr_ctx* ctx, int64_t n, const float* x, double* y);
+
+// blocked chains of the sampling (k_misc.cu): see the definitions for layouts.
+struct BlkTables {
+  const int* rank;   // nb*nb
+  const int* uoff;   // nb*nb
+  const int* voff;   // nb*nb
+  int nb, k;
+};
+struct SlotDesc {
+  int i;       // tile row
+  int r0;      // rank of A(i,k)
+  int x0off;   // row offset of tile i's block in the X0 buffer
+  int Ki;      // columns of Urow_i used (sum_{j<k} r_ij)
+  int64_t woff;  // element offset of this slot's W / Z block
+  int64_t poff;  // element offset of this slot's P block (projection)
+  int q;       // basis width (projection)
+};
+template <typename T>
+void blkdiag_sample(tlr_ctx* ctx, const BlkTables& tb, int nslots, const SlotDesc* slots_dev,
+                    const int64_t* goff_dev, const int* gld_dev, const T* G, const T* X,
+                    int ldx, const T* X0, int ldx0, int bs, T* W);
+template <typename T>
+void blkdiag_project(tlr_ctx* ctx, const BlkTables& tb, int nslots, const SlotDesc* slots_dev,
+                     const int64_t* goff_dev, const int* gld_dev, const T* G, const T* P, T* Z,
+                     int Kk, int qmax);
+
+double fp64_peak(tlr_ctx* ctx);
+
+struct CopyJob {
+  const double* src;
+  double* dst;
+  int64_t n;
+};
+void batched_copy(tlr_ctx* ctx, std::vector<CopyJob>& jobs);
+void scale_cols(tlr_ctx* ctx, int m, int n, const double* dvec, const double* X, int ldx, double* Y,
+                int ldy);
+void tril_mask(tlr_ctx* ctx, int n, double* A, int lda, int unit);
+void set_diag(tlr_ctx* ctx, int n, double* A, int lda, const double* d);
+void axpy_matrix(tlr_ctx* ctx, int m, int n, double alpha, const double* X, int ldx, double* Y, int ldy);
+
+// kdtree.cpp
+void kd_order(const double* pts, int64_t N, int d, int b, int64_t* perm);
+
+}  // namespace tlr

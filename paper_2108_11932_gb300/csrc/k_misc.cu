@@ -1,0 +1,740 @@
+// Small and medium kernels of the TLR factorization (everything except the batched GEMM).
+#include <math.h>
+
+#include "common.h"
+
+namespace tlr {
+
+static inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ------------------------------------------------------------------ Omega (Algorithm 1 randn)
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64
+// multiplications (0xD2511F53, 0xCD9E8D57) with Weyl key increments
+// (0x9E3779B9, 0xBB67AE85).  Counter (pair m, round t, column k, stream),
+// key (seed lo, seed hi); Box-Muller turns the 4 words into 2 Gaussians.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+__global__ void k_omega(uint32_t s0, uint32_t s1, uint32_t stream, uint32_t k, uint32_t t, int n,
+                        double* __restrict__ out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (2 * m >= n) return;
+  uint32_t c[4] = {(uint32_t)m, t, k, stream};
+  philox4x32_10(c, s0, s1);
+  const uint64_t a = ((uint64_t)c[1] << 32) | c[0];
+  const uint64_t w = ((uint64_t)c[3] << 32) | c[2];
+  const double u1 = ((double)(a >> 11) + 0.5) * 0x1p-53;
+  const double u2 = (double)(w >> 11) * 0x1p-53 + 0x1p-54;
+  const double rho = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  out[2 * m] = rho * cs;
+  if (2 * m + 1 < n) out[2 * m + 1] = rho * sn;
+}
+
+void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t, int b, int bs,
+           double* out) {
+  const int n = b * bs;
+  const int pairs = (n + 1) / 2;
+  k_omega<<<cdiv(pairs, 256), 256, 0, ctx->stream>>>((uint32_t)seed, (uint32_t)(seed >> 32), stream,
+                                                      k, t, n, out);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// ------------------------------------------------------------------ kernel tiles (Section 6)
+__global__ void k_gen_tiles(const double* __restrict__ pts, int64_t N, int d, double inv_ell,
+                            double nugget, int b, const int* __restrict__ ij, double* __restrict__ out) {
+  const int t = blockIdx.y;
+  const int i = ij[2 * t], j = ij[2 * t + 1];
+  double* T = out + (size_t)t * b * b;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < b * b; e += gridDim.x * blockDim.x) {
+    const int r = e % b, c = e / b;
+    const int64_t gi = (int64_t)i * b + r, gj = (int64_t)j * b + c;
+    double v;
+    if (gi < N && gj < N) {
+      double s = 0.0;
+      for (int q = 0; q < d; ++q) {
+        const double df = pts[gi * d + q] - pts[gj * d + q];
+        s = fma(df, df, s);
+      }
+      v = exp(-sqrt(s) * inv_ell);
+      if (gi == gj) v += nugget;
+    } else {
+      v = (gi == gj) ? 1.0 : 0.0;  // identity padding of a ragged last tile
+    }
+    T[e] = v;
+  }
+}
+
+void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget, int b,
+               const int* tile_ij, int ntiles, double* out) {
+  if (ntiles <= 0) return;
+  dim3 grid(std::min<unsigned>(cdiv((int64_t)b * b, 256), 64u), (unsigned)ntiles);
+  k_gen_tiles<<<grid, 256, 0, ctx->stream>>>(pts, N, d, 1.0 / ell, nugget, b, tile_ij, out);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// ------------------------------------------------------------------ Cholesky-QR with dropping
+// One warp per slot.  First pass: G = Y1^T Y1 of the projected panel; the
+// convergence quantity e = sqrt(max_c G_cc) = max column norm of (I - QQ^T)Y.
+// If e <= thr the slot converged and M = 0.  Otherwise an unpivoted Cholesky
+// keeps column j when its pivot (squared norm orthogonal to the kept earlier
+// columns) exceeds max(thr^2, tau * G_jj); M = E_keep R^{-1} (bs x bs, kept
+// columns first, zero columns after), so W = Y M has orthonormal-ish columns.
+// Second pass (re-orthogonalization): same on the leading nk x nk block of
+// W^T W with thr = 0.
+constexpr int MAXBS = 64;
+__global__ void __launch_bounds__(32) k_cholqr_small(int bs, const double* __restrict__ Gall,
+                                                     double* __restrict__ Mall, int* __restrict__ status,
+                                                     double* __restrict__ enorm, double thr, double tau,
+                                                     int first_pass, const int* __restrict__ nk_in) {
+  extern __shared__ double dsm[];
+  const int ld = bs + 1;
+  double* Rm = dsm;                 // bs x (bs + 1), row-major R(row, col)
+  double* Rim = dsm + bs * ld;      // inverse of the kept factor
+  int* keep = reinterpret_cast<int*>(dsm + 2 * bs * ld);
+#define R(r, c) Rm[(r) * ld + (c)]
+#define Ri(r, c) Rim[(r) * ld + (c)]
+  const int s = blockIdx.x, lane = threadIdx.x;
+  const double* G = Gall + (size_t)s * bs * bs;
+  double* M = Mall + (size_t)s * bs * bs;
+  for (int e = lane; e < bs * bs; e += 32) M[e] = 0.0;
+  int n = bs;
+  double thr2 = thr * thr;
+  if (first_pass) {
+    double gmax = 0.0;
+    for (int c = lane; c < bs; c += 32) gmax = fmax(gmax, G[c + (size_t)c * bs]);
+    for (int o = 16; o; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    const double e = sqrt(fmax(gmax, 0.0));
+    if (lane == 0) enorm[s] = e;
+    if (!(e > thr)) {  // converged (also catches NaN-free zero panels)
+      if (lane == 0) { status[2 * s] = 1; status[2 * s + 1] = 0; }
+      return;
+    }
+    if (lane == 0) status[2 * s] = 0;
+  } else {
+    n = nk_in[2 * s + 1];
+    thr2 = 0.0;
+    if (n <= 0) {
+      if (lane == 0) status[2 * s + 1] = 0;
+      return;
+    }
+  }
+  int nk = 0;
+  for (int j = 0; j < n; ++j) {
+    // R(keep[p], j) for kept rows, in order
+    for (int p = 0; p < nk; ++p) {
+      const int l = keep[p];
+      double part = 0.0;
+      for (int q = lane; q < p; q += 32) part = fma(R(keep[q], l), R(keep[q], j), part);
+      for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) R(l, j) = (G[l + (size_t)j * bs] - part) / R(l, l);
+      __syncwarp();
+    }
+    double part = 0.0;
+    for (int q = lane; q < nk; q += 32) part = fma(R(keep[q], j), R(keep[q], j), part);
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const double gjj = G[j + (size_t)j * bs];
+    const double dpiv = gjj - part;
+    const bool kept = (dpiv > fmax(thr2, tau * gjj)) && (dpiv > 0.0) && isfinite(dpiv);
+    if (kept) {
+      if (lane == 0) { R(j, j) = sqrt(dpiv); keep[nk] = j; }
+      ++nk;
+    }
+    __syncwarp();
+  }
+  // Rinv = inverse of the kept upper-triangular factor (nk x nk), column per lane.
+  for (int c = lane; c < nk; c += 32) {
+    Ri(c, c) = 1.0 / R(keep[c], keep[c]);
+    for (int p = c - 1; p >= 0; --p) {
+      double acc = 0.0;
+      for (int q = p + 1; q <= c; ++q) acc = fma(R(keep[p], keep[q]), Ri(q, c), acc);
+      Ri(p, c) = -acc / R(keep[p], keep[p]);
+    }
+  }
+  __syncwarp();
+  for (int e = lane; e < nk * nk; e += 32) {
+    const int p = e % nk, c = e / nk;
+    if (p <= c) M[keep[p] + (size_t)c * bs] = Ri(p, c);
+  }
+  if (lane == 0) status[2 * s + 1] = nk;
+#undef R
+#undef Ri
+}
+
+void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mout, int* status,
+                  double* enorm, double thr, double tau, int first_pass, const int* nk_in) {
+  if (nslots <= 0) return;
+  TLR_REQUIRE(bs <= MAXBS, TLR_ERR_LIMIT, "ARA block width above 64");
+  const size_t smem = sizeof(double) * 2 * bs * (bs + 1) + sizeof(int) * bs;
+  static bool attr_set = false;
+  if (!attr_set) {
+    TLR_CUDA(cudaFuncSetAttribute(k_cholqr_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(double) * 2 * MAXBS * (MAXBS + 1) + sizeof(int) * MAXBS)));
+    attr_set = true;
+  }
+  k_cholqr_small<<<(unsigned)nslots, 32, smem, ctx->stream>>>(bs, G, Mout, status, enorm, thr, tau,
+                                                               first_pass, nk_in);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// ------------------------------------------------------------------ dense diagonal-tile factorization
+// Factor the nbk x nbk diagonal block at A (lda) in shared memory, one CTA.
+// Cholesky: right-looking column by column.  LDL^T (unpivoted, Section 5.3):
+// d_j = a_jj, l_ij = a_ij / d_j, a_il -= l_ij d_j l_lj; the unit diagonal is
+// written to A and d to dvec.  *info records the first failing global column
+// (atomicCAS from -1), after which the block stops.
+constexpr int PB = 64;
+__global__ void __launch_bounds__(256) k_potrf_block(int nbk, double* __restrict__ A, int lda, int ldl,
+                                                     double* __restrict__ dvec, int* __restrict__ info,
+                                                     int col0) {
+  __shared__ double S[PB][PB + 1];
+  __shared__ int fail;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < nbk * nbk; e += blockDim.x) {
+    const int r = e % nbk, c = e / nbk;
+    S[r][c] = (r >= c) ? A[r + (size_t)c * lda] : 0.0;
+  }
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < nbk; ++j) {
+    const double piv = S[j][j];
+    const bool bad = ldl ? (piv == 0.0 || !isfinite(piv)) : !(piv > 0.0) || !isfinite(piv);
+    if (bad) {
+      if (tid == 0) { fail = 1; atomicCAS(info, -1, col0 + j); }
+      __syncthreads();
+      break;
+    }
+    const double sj = ldl ? piv : sqrt(piv);
+    __syncthreads();  // everyone has read S[j][j]
+    // column j below the diagonal
+    for (int r = j + 1 + tid; r < nbk; r += blockDim.x) S[r][j] = S[r][j] / sj;
+    if (tid == 0) S[j][j] = ldl ? piv : sj;
+    __syncthreads();
+    // trailing update of the lower triangle
+    const int m = nbk - j - 1;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int r = j + 1 + e % m, c = j + 1 + e / m;
+      if (r >= c) S[r][c] -= S[r][j] * (ldl ? piv : 1.0) * S[c][j];
+    }
+    __syncthreads();
+  }
+  if (fail) return;
+  for (int e = tid; e < nbk * nbk; e += blockDim.x) {
+    const int r = e % nbk, c = e / nbk;
+    if (r > c) A[r + (size_t)c * lda] = S[r][c];
+    else if (r == c) {
+      if (ldl) { dvec[col0 + r] = S[r][r]; A[r + (size_t)c * lda] = 1.0; }
+      else A[r + (size_t)c * lda] = S[r][r];
+    }
+  }
+}
+
+void potrf_diag_block(tlr_ctx* ctx, int nbk, double* A, int lda, int ldl, double* dvec, int* info,
+                      int col0) {
+  TLR_REQUIRE(nbk <= PB, TLR_ERR_LIMIT, "potrf block above 64");
+  k_potrf_block<<<1, 256, 0, ctx->stream>>>(nbk, A, lda, ldl, dvec, info, col0);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// X (m x nbk) <- X L^{-T} (Cholesky) or X L^{-T} D^{-1} (LDL^T, unit L), L the
+// factored nbk x nbk diagonal block.  One thread per row of X; 64 rows per CTA.
+__global__ void __launch_bounds__(64) k_trsm_panel_right(int m, int nbk, const double* __restrict__ L,
+                                                         int lda, double* __restrict__ X, int ldx, int ldl,
+                                                         const double* __restrict__ dvec) {
+  __shared__ double Xs[PB][PB + 1];
+  const int tid = threadIdx.x, r0 = blockIdx.x * PB;
+  // every thread reads the same L entry at the same time: served as an L1 broadcast
+#define Ls(r, c) __ldg(L + (r) + (size_t)(c) * lda)
+  const int rows = min(PB, m - r0);
+  for (int e = tid; e < rows * nbk; e += 64) {
+    const int r = e % rows, c = e / rows;
+    Xs[r][c] = X[(r0 + r) + (size_t)c * ldx];
+  }
+  __syncthreads();
+  if (tid < rows) {
+    // solve x L^T = a  <=>  L x^T = a^T: forward substitution over c
+    for (int c = 0; c < nbk; ++c) {
+      double v = Xs[tid][c];
+      for (int l = 0; l < c; ++l) v = fma(-Ls(c, l), Xs[tid][l], v);
+      Xs[tid][c] = ldl ? v : v / Ls(c, c);
+    }
+    if (ldl)
+      for (int c = 0; c < nbk; ++c) Xs[tid][c] /= dvec[c];
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * nbk; e += 64) {
+    const int r = e % rows, c = e / rows;
+    X[(r0 + r) + (size_t)c * ldx] = Xs[r][c];
+  }
+#undef Ls
+}
+
+void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, double* X, int ldx,
+                      int ldl, const double* dvec) {
+  if (m <= 0) return;
+  k_trsm_panel_right<<<cdiv(m, PB), 64, 0, ctx->stream>>>(m, nbk, L, lda, X, ldx, ldl, dvec);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// X (nbk x nrhs) <- L^{-1} X, L the nbk x nbk lower diagonal block (unit if
+// `unit`).  One thread per right-hand-side column; 64 columns per CTA.
+__global__ void __launch_bounds__(64) k_trsm_left_block(int nbk, const double* __restrict__ L, int lda,
+                                                        int unit, int nrhs, double* __restrict__ X, int ldx,
+                                                        int trans) {
+  __shared__ double Xs[PB][PB + 1];
+  const int tid = threadIdx.x, c0 = blockIdx.x * PB;
+#define Ls(r, c) __ldg(L + (r) + (size_t)(c) * lda)
+  const int cols = min(PB, nrhs - c0);
+  for (int e = tid; e < nbk * cols; e += 64) {
+    const int r = e % nbk, c = e / nbk;
+    Xs[r][c] = X[r + (size_t)(c0 + c) * ldx];
+  }
+  __syncthreads();
+  if (tid < cols) {
+    if (!trans) {
+      for (int r = 0; r < nbk; ++r) {
+        double v = Xs[r][tid];
+        for (int l = 0; l < r; ++l) v = fma(-Ls(r, l), Xs[l][tid], v);
+        Xs[r][tid] = unit ? v : v / Ls(r, r);
+      }
+    } else {  // L^T x = b: backward substitution
+      for (int r = nbk - 1; r >= 0; --r) {
+        double v = Xs[r][tid];
+        for (int l = r + 1; l < nbk; ++l) v = fma(-Ls(l, r), Xs[l][tid], v);
+        Xs[r][tid] = unit ? v : v / Ls(r, r);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < nbk * cols; e += 64) {
+    const int r = e % nbk, c = e / nbk;
+    X[r + (size_t)(c0 + c) * ldx] = Xs[r][c];
+  }
+#undef Ls
+}
+
+void trsm_left_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs, double* X,
+                     int ldx) {
+  if (nrhs <= 0) return;
+  k_trsm_left_block<<<cdiv(nrhs, PB), 64, 0, ctx->stream>>>(nbk, L, lda, unit, nrhs, X, ldx, 0);
+  TLR_LAUNCH_CHECK(ctx);
+}
+void trsm_left_t_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs,
+                       double* X, int ldx) {
+  if (nrhs <= 0) return;
+  k_trsm_left_block<<<cdiv(nrhs, PB), 64, 0, ctx->stream>>>(nbk, L, lda, unit, nrhs, X, ldx, 1);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// ------------------------------------------------------------------ elementwise helpers
+__global__ void k_scale_rows(int m, int n, const double* __restrict__ dv, int inv, const double* X,
+                             int ldx, double* Y, int ldy) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    const double s = inv ? 1.0 / dv[r] : dv[r];
+    Y[r + (size_t)c * ldy] = X[r + (size_t)c * ldx] * s;
+  }
+}
+void scale_rows(tlr_ctx* ctx, int m, int n, const double* dvec, int inv, const double* X, int ldx,
+                double* Y, int ldy) {
+  if ((int64_t)m * n <= 0) return;
+  k_scale_rows<<<std::min<unsigned>(cdiv((int64_t)m * n, 256), 4096u), 256, 0, ctx->stream>>>(
+      m, n, dvec, inv, X, ldx, Y, ldy);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+__global__ void k_add_diag(int n, double* A, int lda, double s) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[i + (size_t)i * lda] += s;
+}
+void add_diag(tlr_ctx* ctx, int n, double* A, int lda, double s) {
+  k_add_diag<<<cdiv(n, 256), 256, 0, ctx->stream>>>(n, A, lda, s);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// A_ii += sum_j |E_ij| (diagonal compensation, Section 5.1.1); one warp per row.
+__global__ void k_add_rowsum_abs(int n, const double* __restrict__ E, int lde, double* A, int lda) {
+  const int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int c = lane; c < n; c += 32) s += fabs(E[row + (size_t)c * lde]);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) A[row + (size_t)row * lda] += s;
+}
+void add_rowsum_abs(tlr_ctx* ctx, int n, const double* E, int lde, double* A, int lda) {
+  k_add_rowsum_abs<<<cdiv(n, 8), 256, 0, ctx->stream>>>(n, E, lde, A, lda);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// Deterministic log|det| reduction over the diagonals (fixed thread-to-entry map).
+__global__ void __launch_bounds__(1024) k_logdet(int n, const double* __restrict__ diag, int b,
+                                                 const double* __restrict__ dvec, double* out) {
+  __shared__ double ssum[32];
+  __shared__ int sneg[32];
+  double s = 0.0;
+  int neg = 0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    double v;
+    if (dvec) v = dvec[g];
+    else {
+      const int k = g / b, r = g % b;
+      v = diag[(size_t)k * b * b + r + (size_t)r * b];
+    }
+    s += log(fabs(v));
+    neg += (v < 0.0);
+  }
+  for (int o = 16; o; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    neg += __shfl_xor_sync(0xffffffffu, neg, o);
+  }
+  if ((threadIdx.x & 31) == 0) { ssum[threadIdx.x / 32] = s; sneg[threadIdx.x / 32] = neg; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    int ng = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) { t += ssum[w]; ng += sneg[w]; }
+    out[0] = dvec ? t : 2.0 * t;
+    out[1] = (double)ng;
+  }
+}
+void logdet_reduce(tlr_ctx* ctx, int n, const double* diag_tiles, int b, int nb, const double* dvec,
+                   double* out2) {
+  (void)nb;
+  k_logdet<<<1, 1024, 0, ctx->stream>>>(n, diag_tiles, b, dvec, out2);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// Exact kernel product Y = A X, A_ij = exp(-|x_i - x_j| / ell) + nugget delta_ij,
+// one thread per row, points of the column block staged in shared memory.
+constexpr int KMV_T = 128, KMV_R = 4;
+__global__ void __launch_bounds__(KMV_T) k_kernel_matvec(const double* __restrict__ pts, int64_t N, int d,
+                                                        double inv_ell, double nugget, int nr,
+                                                        const double* __restrict__ X, int64_t ldx,
+                                                        double* __restrict__ Y, int64_t ldy) {
+  __shared__ double P[KMV_T][3];
+  __shared__ double Xs[KMV_T][KMV_R];
+  const int64_t i = blockIdx.x * (int64_t)KMV_T + threadIdx.x;
+  double xi[3] = {0, 0, 0};
+  if (i < N)
+    for (int q = 0; q < d; ++q) xi[q] = pts[i * d + q];
+  double acc[KMV_R] = {0, 0, 0, 0};
+  for (int64_t j0 = 0; j0 < N; j0 += KMV_T) {
+    const int64_t j = j0 + threadIdx.x;
+    __syncthreads();
+    if (j < N) {
+      for (int q = 0; q < d; ++q) P[threadIdx.x][q] = pts[j * d + q];
+      for (int c = 0; c < nr; ++c) Xs[threadIdx.x][c] = X[j + c * ldx];
+    }
+    __syncthreads();
+    const int cnt = (N - j0 < KMV_T) ? (int)(N - j0) : KMV_T;
+    for (int jj = 0; jj < cnt; ++jj) {
+      double s = 0.0;
+      for (int q = 0; q < d; ++q) {
+        const double df = xi[q] - P[jj][q];
+        s = fma(df, df, s);
+      }
+      const double a = exp(-sqrt(s) * inv_ell);
+      for (int c = 0; c < nr; ++c) acc[c] = fma(a, Xs[jj][c], acc[c]);
+    }
+  }
+  if (i < N)
+    for (int c = 0; c < nr; ++c) Y[i + c * ldy] = acc[c] + nugget * X[i + c * ldx];
+}
+void kernel_matvec(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget,
+                   int nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy) {
+  for (int c0 = 0; c0 < nrhs; c0 += KMV_R) {
+    const int nr = std::min(KMV_R, nrhs - c0);
+    k_kernel_matvec<<<cdiv(N, KMV_T), KMV_T, 0, ctx->stream>>>(pts, N, d, 1.0 / ell, nugget, nr,
+                                                              X + c0 * ldx, ldx, Y + c0 * ldy, ldy);
+    TLR_LAUNCH_CHECK(ctx);
+  }
+}
+
+// Row permutation between the original order and the KD (padded) order.
+// gather: Y[p] = X[idx[p]] for p < n_out (rows n_out..n_pad-1 of Y zeroed);
+// scatter: Y[idx[p]] = X[p] for p < n_out.
+__global__ void k_permute(int64_t n_out, int nrhs, const int64_t* __restrict__ idx, int gather,
+                          const double* __restrict__ X, int64_t ldx, double* __restrict__ Y, int64_t ldy,
+                          int64_t n_pad) {
+  const int64_t tot = (gather ? n_pad : n_out) * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t rows = gather ? n_pad : n_out;
+    const int64_t p = e % rows;
+    const int c = (int)(e / rows);
+    if (gather) Y[p + c * ldy] = (p < n_out) ? X[idx[p] + c * ldx] : 0.0;
+    else Y[idx[p] + c * ldy] = X[p + c * ldx];
+  }
+}
+void permute_rows(tlr_ctx* ctx, int64_t n_out, int nrhs, const int64_t* idx, int gather,
+                  const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n_pad) {
+  const int64_t tot = (gather ? n_pad : n_out) * nrhs;
+  if (tot <= 0) return;
+  k_permute<<<std::min<unsigned>(cdiv(tot, 256), 8192u), 256, 0, ctx->stream>>>(n_out, nrhs, idx, gather,
+                                                                               X, ldx, Y, ldy, n_pad);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+__global__ void k_copy_matrix(int m, int n, const double* __restrict__ X, int ldx, double* __restrict__ Y,
+                              int ldy) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    Y[r + (size_t)c * ldy] = X[r + (size_t)c * ldx];
+  }
+}
+void copy_matrix(tlr_ctx* ctx, int m, int n, const double* X, int ldx, double* Y, int ldy) {
+  if ((int64_t)m * n <= 0) return;
+  k_copy_matrix<<<std::min<unsigned>(cdiv((int64_t)m * n, 256), 8192u), 256, 0, ctx->stream>>>(m, n, X, ldx,
+                                                                                              Y, ldy);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ x, float* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (float)x[e];
+}
+__global__ void k_to_double(int64_t n, const float* __restrict__ x, double* __restrict__ y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = (double)x[e];
+}
+void to_float(tlr_ctx* ctx, int64_t n, const double* x, float* y) {
+  if (n <= 0) return;
+  k_to_float<<<std::min<unsigned>(cdiv(n, 256), 8192u), 256, 0, ctx->stream>>>(n, x, y);
+  TLR_LAUNCH_CHECK(ctx);
+}
+void to_double(tlr_ctx* ctx, int64_t n, const float* x, double* y) {
+  if (n <= 0) return;
+  k_to_double<<<std::min<unsigned>(cdiv(n, 256), 8192u), 256, 0, ctx->stream>>>(n, x, y);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// ------------------------------------------------------------------ block-diagonal Gram products
+// Sampling chain with the Gram factor G_ij = V_ij^T [D_j] V_kj (Equation 2 /
+// Equation 3 regrouped): the sample of tile i is
+//   Y_i = U0_ik (V0_ik^T Omega) - sum_j U_ij (G_ij (U_kj^T Omega))
+//       = [U0_ik | U_i0 ... U_i,k-1] W_i,
+//   W_i = [X0_i ; -G_i0 X_0 ; ... ; -G_i,k-1 X_k-1],  X_j = U_kj^T Omega, X0_i = V0_ik^T Omega.
+// G for block column j is stored as Gcol_j = V(j)[tiles i >= k]^T [D_j] V_kj
+// (rows grouped by i at V's column offsets, leading dimension gld[j]).
+// Grid (slot, j in 0..k): block j < k writes -G_ij X_j, block k copies X0_i.
+template <typename T>
+__global__ void k_blkdiag_sample(BlkTables tb, const SlotDesc* __restrict__ slots,
+                                 const int64_t* __restrict__ goff, const int* __restrict__ gld,
+                                 const T* __restrict__ G, const T* __restrict__ X, int ldx,
+                                 const T* __restrict__ X0, int ldx0, int bs, T* __restrict__ W) {
+  const SlotDesc sd = slots[blockIdx.x];
+  const int j = blockIdx.y, nb = tb.nb, k = tb.k, i = sd.i;
+  const int ldw = sd.r0 + sd.Ki;
+  T* Wi = W + sd.woff;
+  if (j == k) {
+    for (int e = threadIdx.x; e < sd.r0 * bs; e += blockDim.x) {
+      const int a = e % sd.r0, c = e / sd.r0;
+      Wi[a + (size_t)c * ldw] = X0[(sd.x0off + a) + (size_t)c * ldx0];
+    }
+    return;
+  }
+  const int rij = tb.rank[i * nb + j], rkj = tb.rank[k * nb + j];
+  if (rij == 0) return;
+  const T* Gij = G + goff[j] + (tb.voff[i * nb + j] - tb.voff[k * nb + j]);
+  const int ldg = gld[j];
+  const T* Xj = X + tb.uoff[k * nb + j];
+  T* out = Wi + sd.r0 + tb.uoff[i * nb + j];
+  for (int e = threadIdx.x; e < rij * bs; e += blockDim.x) {
+    const int a = e % rij, c = e / rij;
+    T acc = T(0);
+    for (int q = 0; q < rkj; ++q) acc = fma(Gij[a + (size_t)q * ldg], Xj[q + (size_t)c * ldx], acc);
+    out[a + (size_t)c * ldw] = -acc;
+  }
+}
+
+// Projection (sampleLeftT): B_i = T_ik^T Q_i = [V0_ik | U_k0 ... U_k,k-1] Z_i with
+//   P_i = [U0_ik | U_i0 ...]^T Q_i ((r0 + K_i) x q),
+//   Z_i = [P_i^(0) ; -G_i0^T P_i^(0-block of j=0) ; ...]   ((r0 + K_k) x q).
+template <typename T>
+__global__ void k_blkdiag_project(BlkTables tb, const SlotDesc* __restrict__ slots,
+                                  const int64_t* __restrict__ goff, const int* __restrict__ gld,
+                                  const T* __restrict__ G, const T* __restrict__ P, T* __restrict__ Z,
+                                  int Kk) {
+  const SlotDesc sd = slots[blockIdx.x];
+  const int j = blockIdx.y, nb = tb.nb, k = tb.k, i = sd.i, q = sd.q;
+  const int ldp = sd.r0 + sd.Ki, ldz = sd.r0 + Kk;
+  const T* Pi = P + sd.poff;
+  T* Zi = Z + sd.woff;
+  if (j == k) {
+    for (int e = threadIdx.x; e < sd.r0 * q; e += blockDim.x) {
+      const int a = e % sd.r0, c = e / sd.r0;
+      Zi[a + (size_t)c * ldz] = Pi[a + (size_t)c * ldp];
+    }
+    return;
+  }
+  const int rij = tb.rank[i * nb + j], rkj = tb.rank[k * nb + j];
+  if (rkj == 0) return;
+  T* out = Zi + sd.r0 + tb.uoff[k * nb + j];
+  const T* Gij = G + goff[j] + (tb.voff[i * nb + j] - tb.voff[k * nb + j]);
+  const int ldg = gld[j];
+  const T* Pj = Pi + sd.r0 + tb.uoff[i * nb + j];
+  for (int e = threadIdx.x; e < rkj * q; e += blockDim.x) {
+    const int a = e % rkj, c = e / rkj;
+    T acc = T(0);
+    for (int l = 0; l < rij; ++l) acc = fma(Gij[l + (size_t)a * ldg], Pj[l + (size_t)c * ldp], acc);
+    out[a + (size_t)c * ldz] = -acc;
+  }
+}
+
+template <typename T>
+void blkdiag_sample(tlr_ctx* ctx, const BlkTables& tb, int nslots, const SlotDesc* slots_dev,
+                    const int64_t* goff_dev, const int* gld_dev, const T* G, const T* X, int ldx,
+                    const T* X0, int ldx0, int bs, T* W) {
+  if (nslots <= 0) return;
+  dim3 grid((unsigned)nslots, (unsigned)(tb.k + 1));
+  k_blkdiag_sample<T><<<grid, 128, 0, ctx->stream>>>(tb, slots_dev, goff_dev, gld_dev, G, X, ldx, X0,
+                                                    ldx0, bs, W);
+  TLR_LAUNCH_CHECK(ctx);
+}
+template <typename T>
+void blkdiag_project(tlr_ctx* ctx, const BlkTables& tb, int nslots, const SlotDesc* slots_dev,
+                     const int64_t* goff_dev, const int* gld_dev, const T* G, const T* P, T* Z,
+                     int Kk, int qmax) {
+  (void)qmax;
+  if (nslots <= 0) return;
+  dim3 grid((unsigned)nslots, (unsigned)(tb.k + 1));
+  k_blkdiag_project<T><<<grid, 128, 0, ctx->stream>>>(tb, slots_dev, goff_dev, gld_dev, G, P, Z, Kk);
+  TLR_LAUNCH_CHECK(ctx);
+}
+template void blkdiag_sample<double>(tlr_ctx*, const BlkTables&, int, const SlotDesc*, const int64_t*,
+                                     const int*, const double*, const double*, int, const double*, int,
+                                     int, double*);
+template void blkdiag_sample<float>(tlr_ctx*, const BlkTables&, int, const SlotDesc*, const int64_t*,
+                                    const int*, const float*, const float*, int, const float*, int, int,
+                                    float*);
+template void blkdiag_project<double>(tlr_ctx*, const BlkTables&, int, const SlotDesc*, const int64_t*,
+                                      const int*, const double*, const double*, double*, int, int);
+template void blkdiag_project<float>(tlr_ctx*, const BlkTables&, int, const SlotDesc*, const int64_t*,
+                                     const int*, const float*, const float*, float*, int, int);
+
+// ------------------------------------------------------------------ FP64 peak probe
+__global__ void k_dfma_loop(double* out, int iters, double a, double b) {
+  double acc[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) acc[c] = threadIdx.x * 1e-3 + c;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = fma(acc[c], a, b);
+  }
+  double s = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += acc[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+double fp64_peak(tlr_ctx* ctx) {
+  const int blocks = ctx->sm_count * 4, threads = 256, iters = 4096;
+  double* d = static_cast<double*>(dalloc(ctx, sizeof(double) * blocks * threads));
+  cudaEvent_t e0, e1;
+  TLR_CUDA(cudaEventCreate(&e0));
+  TLR_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    TLR_CUDA(cudaEventRecord(e0, ctx->stream));
+    k_dfma_loop<<<blocks, threads, 0, ctx->stream>>>(d, iters, 0.9999, 1e-3);
+    TLR_LAUNCH_CHECK(ctx);
+    TLR_CUDA(cudaEventRecord(e1, ctx->stream));
+    TLR_CUDA(cudaEventSynchronize(e1));
+    float ms;
+    TLR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dfree(ctx, d);
+  return 2.0 * 8 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+}
+
+// ------------------------------------------------------------------ batched copies (updateTiles)
+__global__ void k_batched_copy(const CopyJob* __restrict__ jobs, int njobs) {
+  const CopyJob J = jobs[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < J.n; e += (int64_t)gridDim.x * blockDim.x)
+    J.dst[e] = J.src[e];
+}
+void batched_copy(tlr_ctx* ctx, std::vector<CopyJob>& jobs) {
+  std::vector<CopyJob> nz;
+  int64_t mx = 0;
+  for (auto& j : jobs)
+    if (j.n > 0) { nz.push_back(j); mx = std::max(mx, j.n); }
+  for (size_t o = 0; o < nz.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
+    const CopyJob* dj = static_cast<const CopyJob*>(upload(ctx, nz.data() + o, cnt * sizeof(CopyJob)));
+    dim3 grid(std::min<unsigned>(cdiv(mx, 256), 64u), (unsigned)cnt);
+    k_batched_copy<<<grid, 256, 0, ctx->stream>>>(dj, cnt);
+    TLR_LAUNCH_CHECK(ctx);
+  }
+}
+
+__global__ void k_scale_cols(int m, int n, const double* __restrict__ dv, const double* X, int ldx,
+                             double* Y, int ldy) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    Y[r + (size_t)c * ldy] = X[r + (size_t)c * ldx] * dv[c];
+  }
+}
+void scale_cols(tlr_ctx* ctx, int m, int n, const double* dvec, const double* X, int ldx, double* Y,
+                int ldy) {
+  if ((int64_t)m * n <= 0) return;
+  k_scale_cols<<<std::min<unsigned>(cdiv((int64_t)m * n, 256), 4096u), 256, 0, ctx->stream>>>(m, n, dvec, X,
+                                                                                             ldx, Y, ldy);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// Zero the strict upper triangle (and set a unit diagonal if `unit`).
+__global__ void k_tril_mask(int n, double* A, int lda, int unit) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % n), c = (int)(e / n);
+    if (r < c) A[r + (size_t)c * lda] = 0.0;
+    else if (r == c && unit) A[r + (size_t)c * lda] = 1.0;
+  }
+}
+void tril_mask(tlr_ctx* ctx, int n, double* A, int lda, int unit) {
+  if (n <= 0) return;
+  k_tril_mask<<<std::min<unsigned>(cdiv((int64_t)n * n, 256), 4096u), 256, 0, ctx->stream>>>(n, A, lda, unit);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+__global__ void k_set_diag(int n, double* A, int lda, const double* d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) A[i + (size_t)i * lda] = d[i];
+}
+void set_diag(tlr_ctx* ctx, int n, double* A, int lda, const double* d) {
+  if (n <= 0) return;
+  k_set_diag<<<cdiv(n, 256), 256, 0, ctx->stream>>>(n, A, lda, d);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// Y += alpha X (m x n).
+__global__ void k_axpy_matrix(int m, int n, double alpha, const double* __restrict__ X, int ldx, double* Y, int ldy) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % m), c = (int)(e / m);
+    Y[r + (size_t)c * ldy] += alpha * X[r + (size_t)c * ldx];
+  }
+}
+void axpy_matrix(tlr_ctx* ctx, int m, int n, double alpha, const double* X, int ldx, double* Y, int ldy) {
+  if ((int64_t)m * n <= 0) return;
+  k_axpy_matrix<<<std::min<unsigned>(cdiv((int64_t)m * n, 256), 4096u), 256, 0, ctx->stream>>>(m, n, alpha, X, ldx,
+                                                                                              Y, ldy);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+}  // namespace tlr

@@ -1,0 +1,62 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol declared in include/tlr.h, and its host-side KD ordering matches the
+oracle's bit for bit."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import kdtree
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2108_11932_gb300 as T
+    T.build()
+    return T
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "tlr.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = set(re.findall(r"\b(tlr_[a-z0-9_]+)\s*\(", txt))
+    types = set(re.findall(r"typedef\s+[^;]*?\(\s*\*\s*(tlr_[a-z0-9_]+)\s*\)", txt))
+    return sorted(names - types)
+
+
+def test_header_declares_the_boundary():
+    syms = _declared_symbols()
+    for s in ["tlr_compress", "tlr_potrf", "tlr_ldlt", "tlr_solve", "tlr_logdet", "tlr_matvec", "tlr_create"]:
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.library_path())
+    missing = [s for s in _declared_symbols() if not hasattr(so, s)]
+    assert not missing, missing
+
+
+def test_opts_default_and_strerror(lib):
+    o = lib.default_opts()
+    assert o.bs == 16 and o.precision == 0 and o.compensation == 0 and o.max_slots == 0
+    so = lib._load()
+    assert so.tlr_strerror(-3).decode().startswith("matrix not positive definite")
+
+
+def test_null_arguments_are_rejected_without_gpu(lib):
+    so = lib._load()
+    assert so.tlr_compress(None, None, 0, 2, None, 0, 0.0, None, None) == lib.ERR_ARG
+    assert so.tlr_potrf(None, None, 1e-6, None) == lib.ERR_ARG
+    assert so.tlr_destroy(None) == lib.ERR_ARG
+
+
+@pytest.mark.parametrize("N,d,b,seed", [(4096, 2, 256, 0), (5000, 3, 512, 1), (1000, 1, 64, 3), (777, 2, 100, 4),
+                                        (50, 2, 64, 5), (32768, 3, 512, 1)])
+def test_kd_order_bit_exact_vs_oracle(lib, N, d, b, seed):
+    x = inputs.points(N, d, seed)
+    assert np.array_equal(lib.kd_order(x, b), kdtree.kd_order(x, b))
