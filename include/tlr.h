@@ -215,6 +215,15 @@ tlr_status tlr_fp64_peak(tlr_ctx* ctx, double* tflops);
 /* Number of kernels this library launched on the context since creation. */
 int64_t tlr_launch_count(const tlr_ctx* ctx);
 
+/* Measurement utility (not part of the method): phase profiler in the spirit
+ * of the paper's phase breakdown (Section 6.1, Figure 8a).  Stream time between
+ * consecutive phase boundaries (CUDA events) is charged to the earlier phase.
+ * Copies the accumulated milliseconds and kernel launches of the n first phases
+ * (order: gram, diag-update, potrf, sample, orthog, host-sync, project, trsm,
+ * update-tiles, compress, solve, other) into ms / launches (either may be NULL),
+ * resets them, and turns profiling on (enable != 0) or off. */
+tlr_status tlr_profile(tlr_ctx* ctx, int enable, double* ms, int64_t* launches, int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -96,6 +96,7 @@ def _load():
         "tlr_dense_trsm": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, C.c_int]),
         "tlr_fp64_peak": (C.c_int, [P, D]),
         "tlr_launch_count": (C.c_int64, [P]),
+        "tlr_profile": (C.c_int, [P, C.c_int, D, C.POINTER(C.c_int64), C.c_int]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -127,11 +128,11 @@ def fortran(x):
 
 
 def _ld(t) -> int:
-    if t.dim() == 1:
-        return t.shape[0]
-    if t.stride(0) != 1:
+    if t.dim() == 1 or t.shape[1] == 1:
+        return max(t.shape[0], 1)
+    if t.stride(0) != 1 and t.shape[0] > 1:
         raise ValueError("matrices must be column-major: use fortran(x)")
-    return max(t.stride(1), 1)
+    return max(t.stride(1), t.shape[0], 1)
 
 
 def default_opts(**kw) -> Opts:
@@ -242,6 +243,17 @@ class Context:
     def dense_trsm(self, L, B, unit: bool = False):
         _check(_load().tlr_dense_trsm(self.h, L.shape[0], _ptr(L), _ld(L), int(unit), B.shape[1], _ptr(B), _ld(B)),
                "tlr_dense_trsm")
+
+    PHASES = ["gram", "diag_update", "potrf", "sample", "orthog", "host_sync", "project", "trsm", "update_tiles",
+              "compress", "solve", "other"]
+
+    def profile(self, enable: bool = True) -> dict:
+        """Return (and reset) the phase profile {phase: (ms, launches)}; switch profiling on/off."""
+        n = len(self.PHASES)
+        ms = (C.c_double * n)()
+        ln = (C.c_int64 * n)()
+        _check(_load().tlr_profile(self.h, int(enable), ms, ln, n), "tlr_profile")
+        return {p: (ms[i], ln[i]) for i, p in enumerate(self.PHASES)}
 
     def fp64_peak(self) -> float:
         v = C.c_double(0)

@@ -83,6 +83,15 @@ struct tlr_ctx {
   // Small host-pinned status buffer for per-round device->host reads.
   void* hstatus = nullptr;
   size_t hstatus_cap = 0;
+  // Phase profiler (CUDA events at phase boundaries; off by default).
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_phase;
+  size_t ev_n = 0;
+  double phase_ms[16] = {0};
+  int64_t phase_launch[16] = {0};
+  int cur_phase = -1;
+  int64_t phase_launch0 = 0;
 };
 
 struct tlr_mat {
@@ -107,6 +116,12 @@ struct tlr_mat {
 };
 
 namespace tlr {
+
+// phase profiler: the stream time between two marks is charged to the first mark's phase
+enum Phase { PH_GRAM = 0, PH_DIAG, PH_POTRF, PH_SAMPLE, PH_ORTH, PH_SYNC, PH_PROJECT, PH_TRSM, PH_UPDATE,
+             PH_COMPRESS, PH_SOLVE, PH_OTHER, PH_COUNT };
+void prof_mark(tlr_ctx* ctx, int phase);
+void prof_flush(tlr_ctx* ctx);
 
 // memory
 void* dalloc(tlr_ctx* ctx, size_t bytes);

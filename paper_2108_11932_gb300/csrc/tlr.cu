@@ -79,6 +79,35 @@ void* host_status(tlr_ctx* ctx, size_t bytes) {
   return ctx->hstatus;
 }
 
+void prof_mark(tlr_ctx* ctx, int phase) {
+  if (!ctx->prof) return;
+  if (ctx->cur_phase >= 0) ctx->phase_launch[ctx->cur_phase] += ctx->launches - ctx->phase_launch0;
+  ctx->phase_launch0 = ctx->launches;
+  ctx->cur_phase = phase;
+  if (ctx->ev_n == ctx->ev.size()) {
+    cudaEvent_t e;
+    TLR_CUDA(cudaEventCreate(&e));
+    ctx->ev.push_back(e);
+    ctx->ev_phase.push_back(0);
+  }
+  TLR_CUDA(cudaEventRecord(ctx->ev[ctx->ev_n], ctx->stream));
+  ctx->ev_phase[ctx->ev_n] = phase;
+  ctx->ev_n++;
+}
+
+void prof_flush(tlr_ctx* ctx) {
+  if (!ctx->prof || ctx->ev_n == 0) return;
+  prof_mark(ctx, PH_OTHER);
+  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (size_t e = 0; e + 1 < ctx->ev_n; ++e) {
+    float ms = 0;
+    TLR_CUDA(cudaEventElapsedTime(&ms, ctx->ev[e], ctx->ev[e + 1]));
+    ctx->phase_ms[ctx->ev_phase[e]] += ms;
+  }
+  ctx->ev_n = 0;
+  ctx->cur_phase = -1;
+}
+
 // Grow-only device workspace.
 struct Buf {
   tlr_ctx* ctx = nullptr;
@@ -233,6 +262,7 @@ static void ara_run(tlr_ctx* ctx, Sampler& S, int nops, const AraConfig& cf,
     for (int op : active) rounds_present.push_back(round[op]);
     std::sort(rounds_present.begin(), rounds_present.end());
     rounds_present.erase(std::unique(rounds_present.begin(), rounds_present.end()), rounds_present.end());
+    prof_mark(ctx, PH_SAMPLE);
     for (int t : rounds_present) {
       std::vector<int> ops_t, slot_t;
       for (int s = 0; s < ns; ++s)
@@ -251,6 +281,7 @@ static void ara_run(tlr_ctx* ctx, Sampler& S, int nops, const AraConfig& cf,
       }
     }
     // ---- orthog, iteration 1: Y <- Y - Q (Q^T Y); G = Y^T Y
+    prof_mark(ctx, PH_ORTH);
     {
       std::vector<GemmJob<double>> j1, j2, j3;
       for (int s = 0; s < ns; ++s) {
@@ -301,6 +332,7 @@ static void ara_run(tlr_ctx* ctx, Sampler& S, int nops, const AraConfig& cf,
       }
       gemm<double>(ctx, NN, j4);
     }
+    prof_mark(ctx, PH_SYNC);
     d2h_sync(ctx, hs, status, sizeof(int) * 2 * ns);
     st.batches++;
     std::vector<int> still;
@@ -321,6 +353,7 @@ static void ara_run(tlr_ctx* ctx, Sampler& S, int nops, const AraConfig& cf,
     refill();
     ++t_global;
   }
+  prof_mark(ctx, PH_PROJECT);
   S.project(q);
 }
 
@@ -663,6 +696,7 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
   for (int k = 0; k < nb; ++k) {
     const int Kk = (int)F->ulen[k];
     // ---- Gram factors of column k: Gcol_j = V(j)[i >= k]^T [D_j] V_kj, j < k
+    prof_mark(ctx, PH_GRAM);
     std::vector<int64_t> goff(std::max(k, 1), 0);
     std::vector<int> gld(std::max(k, 1), 1);
     int64_t gtot = 0;
@@ -695,6 +729,7 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     }
     // ---- updateDense: A_kk -= sum_j U_kj G_kj U_kj^T  (G_kj = rows of tile k in Gcol_j)
     double* Akk = F->diag + (size_t)k * b * b;
+    prof_mark(ctx, PH_DIAG);
     if (Kk > 0) {
       double* E = bE.need<double>((size_t)b * Kk);
       std::vector<GemmJob<double>> je;
@@ -743,6 +778,7 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     }
     if (o->compensation == TLR_COMP_SHIFT && o->shift != 0.0) add_diag(ctx, b, Akk, b, o->shift);
     // ---- dense factorization of the diagonal tile
+    prof_mark(ctx, PH_POTRF);
     TLR_CUDA(cudaMemsetAsync(info, 0xff, sizeof(int), ctx->stream));
     dense_factor(ctx, b, Akk, b, ldl, ldl ? F->dvec + (size_t)k * b : nullptr, info, bTmp);
     fl_exec += (double)b * b * b / 3.0;
@@ -807,10 +843,12 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     F->Vcol[k] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(Rk, 1) * b));
     F->vlen[k] = Rk;
     fs.Bcol = F->Vcol[k];
+    prof_mark(ctx, PH_PROJECT);
     fs.project(q);
     fl_exec += fs.flops_exec;
     fl_model += fs.flops_model;
     // ---- batchTrsm: V_ik = L_kk^{-1} B_i (LDL^T: then D_k^{-1}, batchIDMult)
+    prof_mark(ctx, PH_TRSM);
     if (Rk > 0) {
       dense_trsm(ctx, b, Akk, b, ldl, (int)Rk, F->Vcol[k], b, 0);
       if (ldl) scale_rows(ctx, b, (int)Rk, F->dvec + (size_t)k * b, 1, F->Vcol[k], b, F->Vcol[k], b);
@@ -818,6 +856,7 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
       fl_model += (double)b * b * Rk;
     }
     // ---- updateTiles: U_ik = Q_i appended to block row i; V_ik in block column k
+    prof_mark(ctx, PH_UPDATE);
     std::vector<CopyJob> cj;
     for (int op = 0; op < nops; ++op) {
       const int i = ops2i[op];
@@ -830,6 +869,7 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     }
     batched_copy(ctx, cj);
   }
+  prof_flush(ctx);
   TLR_CUDA(cudaStreamSynchronize(ctx->stream));
   // A := F
   mat_free_storage(ctx, A);
@@ -1364,5 +1404,19 @@ tlr_status tlr_fp64_peak(tlr_ctx* ctx, double* tflops) {
 }
 
 int64_t tlr_launch_count(const tlr_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+tlr_status tlr_profile(tlr_ctx* ctx, int enable, double* ms, int64_t* launches, int n) {
+  if (!ctx) return TLR_ERR_ARG;
+  ABI_BEGIN
+  prof_flush(ctx);
+  if (ms)
+    for (int p = 0; p < n && p < PH_COUNT; ++p) ms[p] = ctx->phase_ms[p];
+  if (launches)
+    for (int p = 0; p < n && p < PH_COUNT; ++p) launches[p] = ctx->phase_launch[p];
+  for (int p = 0; p < PH_COUNT; ++p) { ctx->phase_ms[p] = 0; ctx->phase_launch[p] = 0; }
+  ctx->prof = enable != 0;
+  return TLR_OK;
+  ABI_END
+}
 
 }  // extern "C"

@@ -1,0 +1,321 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Two oracles are used:
+  * the oracle running the SAME algorithm (ARA with the same Philox Gaussian
+    blocks, Algorithm 1/5/6/10): ranks are integers decided by the same
+    threshold tests and must match exactly; factors agree to rounding;
+  * the truncated-SVD oracle (the reference compressor): the acceptance rule
+    backward error <= max(2x oracle's, 10 eps), solve residual <= 2x oracle's,
+    |logdet - logdet_oracle| <= 1e-3 |logdet_oracle| at eps <= 1e-6.
+Tolerances: FP64 everywhere; products of b x b operands accumulate O(b u)
+rounding, the left-looking chain compounds it over nb columns, so factor
+tiles are compared at 1e-10 relative to the tile's largest entry and
+logdets at 1e-10 relative (ranks exactly).
+"""
+import numpy as np
+import pytest
+
+import inputs
+from oracle import compress, dense, kernel, measures, philox, tlr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    import paper_2108_11932_gb300 as T
+    T.build()
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return T.Context(0)
+
+
+def _t(T, a):
+    import torch
+    return T.fortran(torch.tensor(np.asarray(a), device="cuda:0", dtype=torch.float64))
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ------------------------------------------------------------------ Omega
+@pytest.mark.parametrize("seed,stream,k,t,b,bs", [(0, 1, 0, 0, 256, 16), (5, 2, 3, 7, 512, 32), (2**40 + 3, 3, 127, 9, 97, 5),
+                                                  (1, 2, 0, 0, 1, 1)])
+def test_omega_matches_oracle(T, ctx, seed, stream, k, t, b, bs):
+    g = ctx.omega(seed, stream, k, t, b, bs).cpu().numpy()
+    o = philox.omega(seed, stream, k, t, b, bs)
+    assert g.shape == o.shape
+    assert np.max(np.abs(g - o)) <= 1e-14 * max(1.0, np.max(np.abs(o)))
+
+
+# ------------------------------------------------------------------ dense diagonal-tile kernels
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 200, 512, 1024])
+def test_dense_potrf_ldlt_match_oracle(T, ctx, n):
+    rng = np.random.default_rng(n)
+    M = rng.standard_normal((n, n))
+    A = M @ M.T + n * np.eye(n)
+    At = _t(T, A)
+    assert ctx.dense_potrf(At) == -1
+    assert rel(np.tril(At.cpu().numpy()), dense.cholesky(A)) < 1e-12
+    At = _t(T, A)
+    assert ctx.dense_potrf(At, ldl=True) == -1
+    Ld = At.cpu().numpy()
+    Lo, do = dense.ldlt(A)
+    assert rel(np.tril(Ld, -1) + np.eye(n), Lo) < 1e-12
+    assert rel(np.diag(Ld), do) < 1e-12
+
+
+def test_dense_potrf_reports_failing_column(T, ctx):
+    n = 150
+    A = np.eye(n) * 2.0
+    A[97, 97] = -1.0
+    At = _t(T, A)
+    assert ctx.dense_potrf(At) == 97
+
+
+def test_dense_ldlt_indefinite_pivot_free(T, ctx):
+    rng = np.random.default_rng(3)
+    n = 130
+    M = rng.standard_normal((n, n))
+    A = M + M.T + 0.1 * np.eye(n)  # indefinite, nonzero leading minors (generic)
+    At = _t(T, A)
+    assert ctx.dense_potrf(At, ldl=True) == -1
+    Lo, do = dense.ldlt(A)
+    Ld = At.cpu().numpy()
+    assert rel(np.diag(Ld), do) < 1e-9
+    assert (do < 0).any()
+
+
+@pytest.mark.parametrize("n,nrhs,unit", [(300, 70, False), (64, 1, True), (1000, 5, False)])
+def test_dense_trsm_matches_oracle(T, ctx, n, nrhs, unit):
+    rng = np.random.default_rng(1)
+    M = rng.standard_normal((n, n))
+    L = np.linalg.cholesky(M @ M.T + n * np.eye(n))
+    if unit:
+        L = np.tril(L / np.diag(L)[None, :], -1) + np.eye(n)
+    B = rng.standard_normal((n, nrhs))
+    Lt, Bt = _t(T, L), _t(T, B)
+    ctx.dense_trsm(Lt, Bt, unit=unit)
+    assert rel(Bt.cpu().numpy(), dense.solve_lower(L, B, unit=unit)) < 1e-12
+
+
+# ------------------------------------------------------------------ ARA on dense operands (Algorithm 1)
+def _lowrank(n, r, seed, decay):
+    rng = np.random.default_rng(seed)
+    X, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    Y, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    return (X * decay ** np.arange(r)) @ Y.T
+
+
+def test_ara_dense_matches_oracle(T, ctx):
+    import torch
+    n, bs, eps = 256, 16, 1e-6
+    xo = inputs.points(2048, 2, 0)
+    xo = xo[np.argsort(xo[:, 0])]
+    ops = [kernel.tile(xo, 1, 0, n, 0.1, 1e-4), kernel.tile(xo, 5, 0, n, 0.1, 1e-4), np.zeros((n, n)),
+           _lowrank(n, 7, 1, 1.0), _lowrank(n, 100, 2, 0.8), np.random.default_rng(5).standard_normal((n, n))]
+    Tt = torch.tensor(np.stack([a.T for a in ops]), device="cuda:0")
+    Q, B, r = ctx.ara_dense(Tt, bs, eps, seed=3, stream=1, k=0)
+    for s, A in enumerate(ops):
+        Qo, Bo, _ = compress.ara_dense(A, bs, eps, lambda t: philox.omega(3, 1, 0, t, n, bs))
+        rg = int(r[s])
+        assert rg == Qo.shape[1], (s, rg, Qo.shape[1])
+        Qg, Bg = Q[s].cpu().numpy().T[:, :rg], B[s].cpu().numpy().T[:, :rg]
+        if rg:
+            assert rel(Qg @ Bg.T, Qo @ Bo.T) < 1e-10
+            assert np.allclose(Qg.T @ Qg, np.eye(rg), atol=1e-12)
+        assert np.linalg.norm(A - Qg @ Bg.T, 2) <= eps
+    assert int(r[2]) == 0 and int(r[3]) == 7 and int(r[5]) == n
+
+
+# ------------------------------------------------------------------ TLR: same algorithm as the oracle
+CASES = {
+    "cov2d_2k": dict(N=2048, d=2, ell=0.1, nugget=1e-4, b=256, bs=16, seed=0, eps=1e-6),
+    "cov3d_ragged": dict(N=1500, d=3, ell=0.2, nugget=1e-4, b=256, bs=32, seed=1, eps=1e-5),
+    "cov2d_b100": dict(N=1000, d=2, ell=0.05, nugget=1e-4, b=100, bs=8, seed=4, eps=1e-7),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request, T, ctx):
+    w = CASES[request.param]
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    o = T.default_opts(bs=w["bs"], seed=7)
+    A = ctx.compress(x, w["b"], w["eps"], w["ell"], w["nugget"], o)
+    Ao = tlr.build(x, w["b"], w["eps"], w["ell"], w["nugget"], compressor="ara", bs=w["bs"], seed=7)
+    return dict(w=w, x=x, o=o, A=A, Ao=Ao)
+
+
+def test_compress_matches_oracle_ara(case):
+    A, Ao, w = case["A"], case["Ao"], case["w"]
+    assert np.array_equal(A.perm(), Ao.perm)
+    assert np.array_equal(A.ranks(), Ao.ranks())
+    for k in range(Ao.nb):
+        assert rel(A.tile(k, k)[0], Ao.diag[k]) < 1e-14
+    for (i, j) in Ao.U:
+        U, V = A.tile(i, j)
+        ref = Ao.U[(i, j)] @ Ao.V[(i, j)].T
+        if ref.size and np.abs(ref).max() > 0:
+            assert rel(U @ V.T, ref) < 1e-10
+        assert np.linalg.norm(U @ V.T - kernel.tile(Ao.xo, i, j, w["b"], w["ell"], w["nugget"]), 2) <= w["eps"]
+
+
+@pytest.mark.parametrize("ldl", [False, True])
+def test_factor_matches_oracle_ara(case, ldl):
+    w = case["w"]
+    F = case["A"].copy()
+    (F.ldlt if ldl else F.potrf)(w["eps"], case["o"])
+    Fo = tlr.factor(case["Ao"], w["eps"], ldl=ldl, compressor="ara", bs=w["bs"], seed=7)
+    assert np.array_equal(F.ranks(), Fo.ranks())
+    b = w["b"]
+    for k in range(Fo.nb):
+        L, d = F.tile(k, k)
+        ref = Fo.diag[k]
+        assert rel(np.tril(L, -1) + (np.eye(b) if ldl else np.diag(np.diag(L))), ref) < 1e-10
+        if ldl:
+            assert rel(d, Fo.d[k]) < 1e-10
+    for (i, j) in Fo.U:
+        U, V = F.tile(i, j)
+        ref = Fo.U[(i, j)] @ Fo.V[(i, j)].T
+        if np.abs(ref).max() > 0:
+            assert rel(U @ V.T, ref) < 1e-9
+    ld, sg = F.logdet()
+    assert sg == 1 and abs(ld - tlr.logdet(Fo)) <= 1e-10 * abs(tlr.logdet(Fo))
+    # solve and products against the oracle's factor
+    Y = inputs.rhs(w["N"], 3, 11)
+    import paper_2108_11932_gb300 as TT
+    Yt = _t(TT, Y)
+    F.solve(Yt)
+    assert rel(Yt.cpu().numpy(), tlr.solve(Fo, Y)) < 1e-9
+    Z = inputs.rhs(w["N"], 2, 12)
+    Zt = _t(TT, Z)
+    for op, name in [(TT.OP_L, "L"), (TT.OP_LT, "Lt"), (TT.OP_LLT, "LLt")]:
+        assert rel(F.matvec(Zt, op).cpu().numpy(), tlr.matvec(Fo, Z, name)) < 1e-10
+
+
+def test_tlr_product_of_A(case):
+    import paper_2108_11932_gb300 as TT
+    w = case["w"]
+    Z = inputs.rhs(w["N"], 2, 13)
+    assert rel(case["A"].matvec(_t(TT, Z), TT.OP_A).cpu().numpy(), tlr.matvec(case["Ao"], Z, "A")) < 1e-12
+
+
+def test_kernel_matvec_matches_oracle(T, ctx):
+    x = inputs.points(3000, 3, 9)
+    Z = inputs.rhs(3000, 5, 3)
+    g = ctx.kernel_matvec(x, 0.2, 1e-4, _t(T, Z)).cpu().numpy()
+    assert rel(g, kernel.matvec(x, 0.2, 1e-4, Z)) < 1e-13
+
+
+# ------------------------------------------------------------------ dynamic batching, determinism
+def test_batch_width_does_not_change_results(T, ctx):
+    w = CASES["cov2d_2k"]
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    A = ctx.compress(x, w["b"], w["eps"], w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=7))
+    outs = []
+    for slots in [0, 1, 3]:
+        F = A.copy()
+        F.potrf(w["eps"], T.default_opts(bs=w["bs"], seed=7, max_slots=slots))
+        outs.append((F.ranks(), F.tile(5, 2), F.tile(7, 7)[0], F.logdet()[0]))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        assert np.array_equal(o[1][0], outs[0][1][0]) and np.array_equal(o[1][1], outs[0][1][1])
+        assert np.array_equal(o[2], outs[0][2]) and o[3] == outs[0][3]
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("N,b", [(100, 128), (129, 128), (256, 128), (1, 16)])
+def test_small_and_ragged_sizes_against_dense(T, ctx, N, b):
+    x = inputs.points(N, 2, 21)
+    A = ctx.compress(x, b, 1e-12, 0.1, 1e-2, T.default_opts(bs=8))
+    F = A.copy().potrf(1e-12, T.default_opts(bs=8))
+    Ad = kernel.dense(x, 0.1, 1e-2)
+    s, ld = np.linalg.slogdet(Ad)
+    assert abs(F.logdet()[0] - ld) <= 1e-9 * max(1.0, abs(ld))
+    Y = inputs.rhs(N, 2, 1)
+    Yt = _t(T, Y)
+    F.solve(Yt)
+    assert rel(Yt.cpu().numpy(), np.linalg.solve(Ad, Y)) < 1e-6
+
+
+def test_not_positive_definite_is_reported(T, ctx):
+    w = CASES["cov2d_2k"]
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    A = ctx.compress(x, w["b"], w["eps"], w["ell"], w["nugget"], T.default_opts(bs=16))
+    F = A.copy()
+    bad = T.default_opts(bs=16, compensation=T.COMP_SHIFT, shift=-5.0)  # A - 5 I is indefinite
+    with pytest.raises(T.TLRError) as ei:
+        F.potrf(w["eps"], bad)
+    assert ei.value.status == T.ERR_NOT_SPD
+    inf = F.info()
+    assert inf["state"] == 3 and inf["k_fail"] == 0
+    with pytest.raises(T.TLRError) as ei:
+        F.logdet()
+    assert ei.value.status == T.ERR_STATE
+    # the pivot-free LDL^T of the same indefinite matrix runs through (Section 5.3)
+    G = A.copy()
+    G.ldlt(w["eps"], bad)
+    ld, sg = G.logdet()
+    Go = tlr.factor(tlr.build(x, w["b"], w["eps"], w["ell"], w["nugget"], compressor="ara", bs=16, seed=0),
+                    w["eps"], ldl=True, compressor="ara", bs=16, seed=0, compensation="shift", shift=-5.0)
+    assert abs(ld - tlr.logdet(Go)) <= 1e-9 * abs(tlr.logdet(Go))
+    assert sg == (-1 if sum(int(np.sum(dk < 0)) for dk in Go.d) % 2 else 1)
+
+
+def test_invalid_arguments(T, ctx):
+    x = inputs.points(100, 2, 0)
+    with pytest.raises(T.TLRError) as ei:
+        ctx.compress(x, 64, -1.0, 0.1, 1e-4)
+    assert ei.value.status == T.ERR_ARG
+    with pytest.raises(T.TLRError):
+        ctx.compress(x, 64, 1e-6, 0.1, 1e-4, T.default_opts(bs=65))
+    A = ctx.compress(x, 64, 1e-6, 0.1, 1e-4)
+    with pytest.raises(T.TLRError) as ei:
+        A.solve(_t(T, np.zeros((100, 1))))
+    assert ei.value.status == T.ERR_STATE
+
+
+# ------------------------------------------------------------------ acceptance vs the SVD oracle
+def _gpu_backward_error(T, ctx, F, x, ell, nug, iters=30):
+    import torch
+    v0 = inputs.start_vector(x.shape[0])
+
+    def EA(v):
+        vt = torch.tensor(v, device="cuda:0")
+        return ctx.kernel_matvec(x, ell, nug, vt).cpu().numpy()
+
+    def EF(v):
+        vt = torch.tensor(v, device="cuda:0")
+        return F.matvec(vt).cpu().numpy()
+    return measures.backward_error(EA, EF, v0, iters)
+
+
+@pytest.mark.parametrize("ldl", [False, True])
+def test_acceptance_cov2d_4k_against_svd_oracle(T, ctx, ldl):
+    w = inputs.WORKLOADS["cov2d_4k"]
+    eps = 1e-6
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=0))
+    F = A.copy()
+    (F.ldlt if ldl else F.potrf)(eps, T.default_opts(bs=w["bs"], seed=0))
+    Ao = tlr.build(x, w["b"], eps, w["ell"], w["nugget"])
+    Fo = tlr.factor(Ao, eps, ldl=ldl)
+    Ad = kernel.dense(x, w["ell"], w["nugget"])
+    v0 = inputs.start_vector(w["N"])
+    be_o = measures.backward_error(lambda v: Ad @ v, lambda v: tlr.matvec(Fo, v, "LLt")[:, 0], v0)
+    be_g = _gpu_backward_error(T, ctx, F, x, w["ell"], w["nugget"])
+    assert be_g <= max(2 * be_o, 10 * eps), (be_g, be_o)
+    Y = inputs.rhs(w["N"], 4, 5)
+    Yt = _t(T, Y)
+    F.solve(Yt)
+    res_g = measures.residual(lambda Z: Ad @ Z, Yt.cpu().numpy(), Y)
+    res_o = measures.residual(lambda Z: Ad @ Z, tlr.solve(Fo, Y), Y)
+    assert res_g <= 2 * res_o, (res_g, res_o)
+    ld_o = tlr.logdet(Fo)
+    assert abs(F.logdet()[0] - ld_o) <= 1e-3 * abs(ld_o)
