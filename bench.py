@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 TLR Cholesky on the N = 131072 spatial-statistics covariance matrix.
+
+One step = the whole hot path on one matrix: construction (tile generation +
+batched ARA compression of every off-diagonal tile), left-looking TLR
+Cholesky with batched ARA recompression and dynamic batching, a solve with one
+right-hand side and the log-determinant.  Inputs (KD-ordered points, the
+right-hand side) are resident in HBM when the timed region starts; the
+matrix data (1 GB of diagonal tiles plus the factors) is larger than L2.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(truncated-SVD TLR Cholesky) on a bounded sample of the same workload instead.
+Multi-GPU runs (torchrun) are independent replicas: the factorization does
+not shard.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+WORKLOAD = "cov2d_131k"
+METRIC = "N=131K TLR Cholesky seconds + TFLOP/s, FP64 vs mixed; serving p50/p99 latency"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload_desc(w, eps, prec):
+    return (f"{WORKLOAD}: N={w['N']} points uniform in [0,1]^{w['d']}, KD-tree order, exp kernel ell={w['ell']} "
+            f"nugget={w['nugget']}, b={w['b']} (nb={w['N'] // w['b']}), ARA block {w['bs']}, eps={eps:g}, {prec}")
+
+
+# --------------------------------------------------------------------------- oracle sample (CPU)
+def oracle_sample(w, eps, nb_s=4):
+    """Time the FP64 oracle on the leading nb_s x nb_s tiles of the KD-ordered matrix.
+
+    Returns (seconds for the sample, extrapolated seconds for the full matrix, description).
+    The oracle's cost is dominated by one SVD per off-diagonal tile (construction and
+    recompression), so the sample time is scaled by the ratio of off-diagonal tile counts.
+    """
+    from oracle import kdtree, tlr
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    xo = x[kdtree.kd_order(x, w["b"])]
+    xs = xo[: nb_s * w["b"]]
+    t0 = time.perf_counter()
+    A = tlr.build(xs, w["b"], eps, w["ell"], w["nugget"])
+    F = tlr.factor(A, eps)
+    tlr.logdet(F)
+    tlr.solve(F, inputs.rhs(xs.shape[0], 1, 1))
+    dt = time.perf_counter() - t0
+    nb = w["N"] // w["b"]
+    scale = (nb * (nb - 1) / 2) / (nb_s * (nb_s - 1) / 2)
+    desc = (f"oracle (truncated-SVD TLR Cholesky + solve + logdet, FP64 numpy) on the leading {nb_s * w['b']} points "
+            f"({nb_s}x{nb_s} tiles) of the same KD-ordered matrix, eps={eps:g}; {dt:.2f} s scaled x{scale:.0f} "
+            f"by the ratio of off-diagonal tiles")
+    return dt, dt * scale, desc
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, w, eps):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(w, eps, args.oracle_tiles)
+    vals, desc, raw = [], "", []
+    for _ in range(args.steps):
+        dt, v, desc = oracle_sample(w, eps, args.oracle_tiles)
+        vals.append(v)
+        raw.append(dt)
+    v = statistics.median(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(raw), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": _workload_desc(w, eps, "FP64 oracle")},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": _cores(), "kind": "oracle", "sample": desc},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [c.strip() for c in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = max(smax, float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- our arm
+def _traffic_from_profile(name):
+    """traffic (DRAM bytes per launch) recorded in a committed ncu summary, or None."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            try:
+                return float(line.split(":", 1)[1])
+            except ValueError:
+                return None
+    return None
+
+
+def run_ours(args, w, eps):
+    import torch
+    import paper_2108_11932_gb300 as T
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    T.build()
+    ctx = T.Context(local)
+    dev = f"cuda:{local}"
+    prec = T.PREC_FP64 if args.precision == "fp64" else T.PREC_FP32
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    perm = T.kd_order(x, w["b"])
+    pts = torch.tensor(x[perm], device=dev)
+    rhs_host = inputs.rhs(w["N"], 1, 1)
+    rhs = T.fortran(torch.tensor(rhs_host, device=dev))
+    o = T.default_opts(bs=w["bs"], seed=w["seed"], precision=prec)
+    stream = ctx.stream
+    B = torch.empty_like(rhs)
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        A = ctx.compress_ordered(pts, perm, w["b"], eps, w["ell"], w["nugget"], o)
+        if ev:
+            ev[1].record(stream)
+        A.potrf(eps, o)
+        if ev:
+            ev[2].record(stream)
+        B.copy_(rhs)
+        A.solve(B)
+        if ev:
+            ev[3].record(stream)
+        ld = A.logdet()
+        if ev:
+            ev[4].record(stream)
+        info = A.info()
+        A.free()
+        return ld, info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.gemm_stats(True)
+    l0 = ctx.launches()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    infos = []
+    for s in range(args.steps):
+        infos.append(step(evs[s]))
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launches() - l0
+    gst = ctx.gemm_stats(False)
+    ck = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    phases = {k: [] for k in ["compress", "factor", "solve", "logdet"]}
+    for e in evs:
+        for i, k in enumerate(phases):
+            phases[k].append(e[i].elapsed_time(e[i + 1]) / 1e3)
+    med = {k: statistics.median(v) for k, v in phases.items()}
+    ms_per_step = total_ms / args.steps
+    info = infos[-1][1]
+    factor_s = med["factor"]
+    # roofline of the dominant kernel (largest share of GEMM time in the timed region)
+    fam = max(gst, key=lambda f: gst[f]["ms"])
+    g = gst[fam]
+    peak64 = ctx.fp64_peak()
+    per_launch_flops = g["flops"] / max(g["launches"], 1)
+    per_launch_s = g["ms"] / 1e3 / max(g["launches"], 1)
+    achieved = per_launch_flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    fp32_peak = 74.6  # FFMA, measured on this machine's GB300 (see profiles/peaks_gb300.md)
+    peak = peak64 if fam.startswith("fp64") else fp32_peak
+    roofline = {"bound": "alu", "kernel": f"k_gemm<{fam}>", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": _traffic_from_profile(f"gemm_{fam}_traffic.md"),
+                "peak_source": ("FP64 DFMA loop measured live in this run (tlr_fp64_peak)" if fam.startswith("fp64")
+                                else "FP32 FFMA loop measured on this pool's GB300"),
+                "share_of_step": g["ms"] / total_ms, "launches": g["launches"],
+                "flops_per_launch": per_launch_flops}
+    out = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if prec == T.PREC_FP64 else "f32+f64", "data": "synthetic",
+           "config": {"workload": _workload_desc(w, eps, args.precision.upper()),
+                      "step": "compress + potrf + solve(1 rhs) + logdet",
+                      "l2": "no flush: matrix data (1 GB dense diagonal tiles + factors) is larger than the 129 MB L2",
+                      "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+           "factor_s": factor_s, "compress_s": med["compress"], "solve_s": med["solve"], "logdet_s": med["logdet"],
+           "factor_tflops_exec": info["flops_exec"] / factor_s / 1e12,
+           "factor_tflops_model": info["flops_model"] / factor_s / 1e12,
+           "factor_fp64_frac_exec": info["flops_exec"] / factor_s / 1e12 / peak64,
+           "ranks": {"mean": info["mean_rank"], "max": info["max_rank"]}, "logdet": infos[-1][0][0],
+           "fp64_peak_tflops": peak64, "roofline": roofline, "gpu_launches": launches,
+           "gemm_kernels": {f: {"ms_per_step": v["ms"] / args.steps, "tflops": (v["flops"] / v["ms"] / 1e9 if v["ms"] else 0),
+                                "launches_per_step": v["launches"] / args.steps} for f, v in gst.items() if v["launches"]}}
+    if ck:
+        out["clocks"] = ck
+    if ws > 1:
+        out["throughput_steps_per_s"] = ws * args.steps / (total_ms / 1e3)
+    # end-to-end through host buffers (public API: host points, pinned RHS in, pinned solution out)
+    rhs_pin = torch.tensor(rhs_host, dtype=torch.float64).t().contiguous().t().pin_memory()
+    sol_pin = torch.empty_like(rhs_pin).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ne2e = max(1, args.e2e_steps)
+    for _ in range(ne2e):
+        A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], o)
+        A.potrf(eps, o)
+        Bd = T.fortran(torch.empty((w["N"], 1), dtype=torch.float64, device=dev))
+        Bd.copy_(rhs_pin, non_blocking=True)
+        A.solve(Bd)
+        sol_pin.copy_(Bd, non_blocking=True)
+        A.logdet()
+        torch.cuda.synchronize()
+        A.free()
+    e2e = (time.perf_counter() - t0) / ne2e
+    out["e2e"] = {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(x.nbytes + rhs_pin.numel() * 8),
+                  "d2h_bytes_per_step": int(sol_pin.numel() * 8 + 16), "steps": ne2e}
+    # other precisions / thresholds of the metric, one untimed-by-contract step each (CUDA events)
+    variants = {}
+    for vname, veps, vprec in args.variant_list:
+        if (veps, vprec) == (eps, prec):
+            continue
+        vo = T.default_opts(bs=w["bs"], seed=w["seed"], precision=vprec)
+        try:
+            A = ctx.compress_ordered(pts, perm, w["b"], veps, w["ell"], w["nugget"], vo)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A.potrf(veps, vo)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fs = e0.elapsed_time(e1) / 1e3
+            inf = A.info()
+            variants[vname] = {"eps": veps, "factor_s": fs, "tflops_exec": inf["flops_exec"] / fs / 1e12,
+                               "tflops_model": inf["flops_model"] / fs / 1e12, "mean_rank": inf["mean_rank"],
+                               "logdet": A.logdet()[0]}
+            A.free()
+        except Exception as ex:  # report, do not hide
+            variants[vname] = {"eps": veps, "error": str(ex)}
+    out["variants"] = variants
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        dt, v, desc = oracle_sample(w, eps, args.oracle_tiles)
+        out["cpu_baseline"] = {"value": v, "unit": "s", "cores": _cores(), "kind": "oracle", "sample": desc,
+                               "sample_seconds": dt}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    global WORKLOAD
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=list(inputs.WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--oracle-tiles", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    WORKLOAD = args.workload
+    w = inputs.WORKLOADS[WORKLOAD]
+    args.variant_list = [] if args.no_variants else [("fp64_eps1e-2", 1e-2, 0), ("fp64_eps1e-6", 1e-6, 0)]
+    if args.impl == "reference":
+        run_reference(args, w, args.eps)
+    else:
+        run_ours(args, w, args.eps)
+
+
+if __name__ == "__main__":
+    main()

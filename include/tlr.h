@@ -104,6 +104,14 @@ tlr_status tlr_compress(tlr_ctx* ctx, const double* points_host, int64_t N, int 
                         const tlr_kernel* kernel, int b, double eps, const tlr_opts* opts,
                         tlr_mat** A);
 
+/* Same construction from points that are already on the device in KD order
+ * (pts: device, N x d row-major, ordered as tlr_kd_order returns).  perm_host
+ * (host, N entries, may be NULL for the identity) gives the original index of
+ * each ordered point, so that later calls keep using the original order. */
+tlr_status tlr_compress_ordered(tlr_ctx* ctx, const double* pts, const int64_t* perm_host, int64_t N,
+                                int d, const tlr_kernel* kernel, int b, double eps,
+                                const tlr_opts* opts, tlr_mat** A);
+
 /* Deep copy (device-to-device) of a TLR matrix or factor. */
 tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* src, tlr_mat** dst);
 
@@ -214,6 +222,14 @@ tlr_status tlr_fp64_peak(tlr_ctx* ctx, double* tflops);
 
 /* Number of kernels this library launched on the context since creation. */
 int64_t tlr_launch_count(const tlr_ctx* ctx);
+
+/* Measurement utility (not part of the method): per-launch CUDA-event timing of
+ * the batched GEMM kernel.  Copies, for the six families (FP64 NN, TN, NT,
+ * FP32 NN, TN, NT), the accumulated milliseconds, algorithmic flops
+ * (2 M N K per job, half for lower-triangular outputs) and launch counts since
+ * the last call (any pointer may be NULL; arrays of 6), resets them, and turns
+ * the accounting on (enable != 0) or off. */
+tlr_status tlr_gemm_stats(tlr_ctx* ctx, int enable, double* ms, double* flops, int64_t* launches);
 
 /* Measurement utility (not part of the method): phase profiler in the spirit
  * of the paper's phase breakdown (Section 6.1, Figure 8a).  Stream time between

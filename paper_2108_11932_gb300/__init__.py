@@ -75,6 +75,9 @@ def _load():
         "tlr_compress": (C.c_int, [P, P, C.c_int64, C.c_int, C.POINTER(Kernel), C.c_int, C.c_double,
                                    C.POINTER(Opts), C.POINTER(P)]),
         "tlr_copy": (C.c_int, [P, P, C.POINTER(P)]),
+        "tlr_compress_ordered": (C.c_int, [P, P, P, C.c_int64, C.c_int, C.POINTER(Kernel), C.c_int, C.c_double,
+                                           C.POINTER(Opts), C.POINTER(P)]),
+        "tlr_gemm_stats": (C.c_int, [P, C.c_int, D, D, C.POINTER(C.c_int64)]),
         "tlr_potrf": (C.c_int, [P, P, C.c_double, C.POINTER(Opts)]),
         "tlr_ldlt": (C.c_int, [P, P, C.c_double, C.POINTER(Opts)]),
         "tlr_solve": (C.c_int, [P, P, C.c_int, P, C.c_int64]),
@@ -204,6 +207,32 @@ class Context:
         _check(_load().tlr_compress(self.h, x.ctypes.data, N, d, C.byref(k), b, eps,
                                     C.byref(opts) if opts else None, C.byref(m)), "tlr_compress")
         return Matrix(self, m)
+
+    def compress_ordered(self, pts, perm: np.ndarray | None, b: int, eps: float, ell: float, nugget: float,
+                         opts: Opts | None = None):
+        """Construction from device points already in KD order (pts: (N, d) contiguous float64 cuda tensor)."""
+        if not pts.is_contiguous():
+            raise ValueError("pts must be a contiguous (N, d) tensor")
+        N, d = pts.shape
+        pp = None
+        if perm is not None:
+            pp = np.ascontiguousarray(perm, dtype=np.int64)
+        k = Kernel(0, ell, nugget)
+        m = P()
+        _check(_load().tlr_compress_ordered(self.h, _ptr(pts), pp.ctypes.data if pp is not None else None, N, d,
+                                            C.byref(k), b, eps, C.byref(opts) if opts else None, C.byref(m)),
+               "tlr_compress_ordered")
+        return Matrix(self, m)
+
+    GEMM_FAMILIES = ["fp64_NN", "fp64_TN", "fp64_NT", "fp32_NN", "fp32_TN", "fp32_NT"]
+
+    def gemm_stats(self, enable: bool = True) -> dict:
+        """Return (and reset) per-family GEMM launch accounting; switch it on/off."""
+        ms = (C.c_double * 6)()
+        fl = (C.c_double * 6)()
+        ln = (C.c_int64 * 6)()
+        _check(_load().tlr_gemm_stats(self.h, int(enable), ms, fl, ln), "tlr_gemm_stats")
+        return {f: {"ms": ms[i], "flops": fl[i], "launches": ln[i]} for i, f in enumerate(self.GEMM_FAMILIES)}
 
     def kernel_matvec(self, points: np.ndarray, ell: float, nugget: float, X):
         x = np.ascontiguousarray(points, dtype=np.float64)

@@ -92,6 +92,14 @@ struct tlr_ctx {
   int64_t phase_launch[16] = {0};
   int cur_phase = -1;
   int64_t phase_launch0 = 0;
+  // Per-kernel accounting of the batched GEMM launches (CUDA events around each launch).
+  bool kprof = false;
+  std::vector<cudaEvent_t> kev;
+  std::vector<int> kev_fam;
+  std::vector<double> kev_flops;
+  size_t kev_n = 0;
+  double kfam_ms[8] = {0}, kfam_flops[8] = {0};
+  int64_t kfam_launches[8] = {0};
 };
 
 struct tlr_mat {
@@ -103,6 +111,7 @@ struct tlr_mat {
   double eps = 0;
   std::vector<int64_t> perm;
   double* pts = nullptr;   // device, ordered points (N x d row-major)
+  int64_t* dperm = nullptr;  // device copy of perm
   double* diag = nullptr;  // device, nb * b * b
   double* dvec = nullptr;  // device, nb * b (LDL^T D)
   std::vector<int> rank;   // nb * nb (i > j)
@@ -122,6 +131,10 @@ enum Phase { PH_GRAM = 0, PH_DIAG, PH_POTRF, PH_SAMPLE, PH_ORTH, PH_SYNC, PH_PRO
              PH_COMPRESS, PH_SOLVE, PH_OTHER, PH_COUNT };
 void prof_mark(tlr_ctx* ctx, int phase);
 void prof_flush(tlr_ctx* ctx);
+// kernel families of the GEMM accounting: fp64 NN/TN/NT, fp32 NN/TN/NT
+void kprof_begin(tlr_ctx* ctx);
+void kprof_end(tlr_ctx* ctx, int family, double flops);
+void kprof_flush(tlr_ctx* ctx);
 
 // memory
 void* dalloc(tlr_ctx* ctx, size_t bytes);

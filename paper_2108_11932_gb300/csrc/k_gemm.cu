@@ -128,7 +128,7 @@ template <typename T>
 __global__ void k_gemm_reduce(const GemmJob<T>* __restrict__ jobs, const int* __restrict__ ids) {
   const GemmJob<T>& J = jobs[ids[blockIdx.x]];
   const size_t MN = (size_t)J.M * J.N;
-  for (size_t e = threadIdx.x; e < MN; e += blockDim.x) {
+  for (size_t e = blockIdx.y * (size_t)blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.y * blockDim.x) {
     const int gm = (int)(e % J.M), gn = (int)(e / J.M);
     T s = T(0);
     for (int sp = 0; sp < J.nsplit; ++sp) s += J.ws[(size_t)sp * MN + e];
@@ -158,17 +158,25 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
   for (auto& j : jobs_in)
     if (j.M > 0 && j.N > 0) jobs.push_back(j);
   if (jobs.empty()) return;
+  // Split K (deterministically: fixed slices, fixed-order reduction) when the
+  // launch has fewer than ~4 CTAs per SM, so that small batches still occupy
+  // every SM; each slice keeps at least 64 reduction steps.
+  int64_t base = 0;
+  for (auto& j : jobs) {
+    j.tiles_m = (j.M + GEMM_TM - 1) / GEMM_TM;
+    j.tiles_n = (j.N + GEMM_TN - 1) / GEMM_TN;
+    base += (int64_t)j.tiles_m * j.tiles_n;
+  }
+  const int64_t target = 4LL * std::max(ctx->sm_count, 1);
+  const int want = base >= target ? 1 : (int)std::min<int64_t>(16, (target + base - 1) / base);
   int64_t total = 0;
   size_t ws_elems = 0;
   std::vector<int> split_ids;
   for (size_t q = 0; q < jobs.size(); ++q) {
     auto& j = jobs[q];
-    j.tiles_m = (j.M + GEMM_TM - 1) / GEMM_TM;
-    j.tiles_n = (j.N + GEMM_TN - 1) / GEMM_TN;
     const int Kt = j.K[0] + j.K[1];
     j.nsplit = 1;
-    if (!(j.flags & GEMM_TRIL) && j.tiles_m * j.tiles_n <= 4 && Kt >= 256)
-      j.nsplit = std::min(8, Kt / 128);
+    if (!(j.flags & GEMM_TRIL) && want > 1) j.nsplit = std::max(1, std::min(want, Kt / 64));
     j.tile0 = (int)total;
     total += (int64_t)j.tiles_m * j.tiles_n * j.nsplit;
     if (j.nsplit > 1) {
@@ -185,13 +193,22 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
   const GemmJob<T>* dj =
       static_cast<const GemmJob<T>*>(upload(ctx, jobs.data(), jobs.size() * sizeof(GemmJob<T>)));
   const int nj = (int)jobs.size();
+  double flops = 0;
+  if (ctx->kprof) {
+    for (auto& j : jobs) flops += 2.0 * j.M * j.N * (double)(j.K[0] + j.K[1]) * ((j.flags & GEMM_TRIL) ? 0.5 : 1.0);
+    kprof_begin(ctx);
+  }
   if (mode == NN) k_gemm<T, NN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   else if (mode == TN) k_gemm<T, TN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   else k_gemm<T, NT><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   TLR_LAUNCH_CHECK(ctx);
+  if (ctx->kprof) kprof_end(ctx, (sizeof(T) == 8 ? 0 : 3) + (int)mode, flops);
   if (!split_ids.empty()) {
     const int* ids = static_cast<const int*>(upload(ctx, split_ids.data(), split_ids.size() * sizeof(int)));
-    k_gemm_reduce<T><<<(unsigned)split_ids.size(), 256, 0, ctx->stream>>>(dj, ids);
+    size_t mx = 0;
+    for (int q : split_ids) mx = std::max(mx, (size_t)jobs[q].M * jobs[q].N);
+    dim3 rg((unsigned)split_ids.size(), (unsigned)std::min<size_t>(64, (mx + 1023) / 1024));
+    k_gemm_reduce<T><<<rg, 256, 0, ctx->stream>>>(dj, ids);
     TLR_LAUNCH_CHECK(ctx);
   }
 }

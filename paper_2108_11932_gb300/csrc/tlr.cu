@@ -108,6 +108,41 @@ void prof_flush(tlr_ctx* ctx) {
   ctx->cur_phase = -1;
 }
 
+void kprof_begin(tlr_ctx* ctx) {
+  while (ctx->kev.size() < ctx->kev_n + 2) {
+    cudaEvent_t e;
+    TLR_CUDA(cudaEventCreate(&e));
+    ctx->kev.push_back(e);
+  }
+  if (ctx->kev_fam.size() < ctx->kev.size()) {
+    ctx->kev_fam.resize(ctx->kev.size());
+    ctx->kev_flops.resize(ctx->kev.size());
+  }
+  TLR_CUDA(cudaEventRecord(ctx->kev[ctx->kev_n], ctx->stream));
+}
+
+void kprof_end(tlr_ctx* ctx, int family, double flops) {
+  TLR_CUDA(cudaEventRecord(ctx->kev[ctx->kev_n + 1], ctx->stream));
+  ctx->kev_fam[ctx->kev_n] = family;
+  ctx->kev_flops[ctx->kev_n] = flops;
+  ctx->kev_n += 2;
+  if (ctx->kev_n >= 16384) kprof_flush(ctx);
+}
+
+void kprof_flush(tlr_ctx* ctx) {
+  if (ctx->kev_n == 0) return;
+  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (size_t e = 0; e < ctx->kev_n; e += 2) {
+    float ms = 0;
+    TLR_CUDA(cudaEventElapsedTime(&ms, ctx->kev[e], ctx->kev[e + 1]));
+    const int f = ctx->kev_fam[e];
+    ctx->kfam_ms[f] += ms;
+    ctx->kfam_flops[f] += ctx->kev_flops[e];
+    ctx->kfam_launches[f] += 1;
+  }
+  ctx->kev_n = 0;
+}
+
 // Grow-only device workspace.
 struct Buf {
   tlr_ctx* ctx = nullptr;
@@ -408,6 +443,7 @@ static void mat_destroy(tlr_ctx* ctx, tlr_mat* M) {
   if (!M) return;
   mat_free_storage(ctx, M);
   dfree(ctx, M->pts);
+  dfree(ctx, M->dperm);
   dfree(ctx, M->diag);
   dfree(ctx, M->dvec);
   delete M;
@@ -432,19 +468,36 @@ static tlr_mat* mat_new(int64_t N, int d, int b) {
 }
 
 // ======================================================================== construction (tlr_compress)
+// Points already in KD order on the device (pts_dev, N x d row-major); perm_host
+// (may be null = identity) records the original index of each ordered point.
+static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int64_t* perm_host, int64_t N, int d,
+                                  const tlr_kernel* kern, int b, double eps, const tlr_opts* o, tlr_mat* M);
+
 static void compress_impl(tlr_ctx* ctx, const double* pts_host, int64_t N, int d, const tlr_kernel* kern,
                           int b, double eps, const tlr_opts* o, tlr_mat* M) {
+  std::vector<int64_t> perm(N);
+  kd_order(pts_host, N, d, b, perm.data());
+  std::vector<double> xo((size_t)N * d);
+  for (int64_t p = 0; p < N; ++p)
+    for (int q = 0; q < d; ++q) xo[p * d + q] = pts_host[perm[p] * d + q];
+  Buf tmp(ctx);
+  double* dp = tmp.need<double>((size_t)N * d);
+  TLR_CUDA(cudaMemcpyAsync(dp, xo.data(), sizeof(double) * N * d, cudaMemcpyHostToDevice, ctx->stream));
+  TLR_CUDA(cudaStreamSynchronize(ctx->stream));  // xo is pageable and goes out of scope
+  compress_ordered_impl(ctx, dp, perm.data(), N, d, kern, b, eps, o, M);
+}
+
+static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int64_t* perm_host, int64_t N, int d,
+                                  const tlr_kernel* kern, int b, double eps, const tlr_opts* o, tlr_mat* M) {
   const int nb = M->nb;
   M->kern = *kern;
   M->eps = eps;
   M->perm.resize(N);
-  kd_order(pts_host, N, d, b, M->perm.data());
-  std::vector<double> xo((size_t)N * d);
-  for (int64_t p = 0; p < N; ++p)
-    for (int q = 0; q < d; ++q) xo[p * d + q] = pts_host[M->perm[p] * d + q];
+  for (int64_t p = 0; p < N; ++p) M->perm[p] = perm_host ? perm_host[p] : p;
   M->pts = static_cast<double*>(dalloc(ctx, sizeof(double) * std::max<int64_t>(1, N * d)));
-  TLR_CUDA(cudaMemcpyAsync(M->pts, xo.data(), sizeof(double) * N * d, cudaMemcpyHostToDevice, ctx->stream));
-  TLR_CUDA(cudaStreamSynchronize(ctx->stream));  // xo is pageable and goes out of scope
+  TLR_CUDA(cudaMemcpyAsync(M->pts, pts_dev, sizeof(double) * N * d, cudaMemcpyDeviceToDevice, ctx->stream));
+  M->dperm = static_cast<int64_t*>(dalloc(ctx, sizeof(int64_t) * N));
+  TLR_CUDA(cudaMemcpyAsync(M->dperm, M->perm.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, ctx->stream));
   M->diag = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
   {
     std::vector<int> ij;
@@ -1134,6 +1187,30 @@ tlr_status tlr_compress(tlr_ctx* ctx, const double* pts, int64_t N, int d, const
   }
 }
 
+tlr_status tlr_compress_ordered(tlr_ctx* ctx, const double* pts_dev, const int64_t* perm_host, int64_t N, int d,
+                                const tlr_kernel* kern, int b, double eps, const tlr_opts* opts, tlr_mat** A) {
+  if (!ctx || !pts_dev || !kern || !A || N <= 0 || d < 1 || d > 3 || b < 1 || !(eps > 0) || !(kern->ell > 0) ||
+      kern->type != TLR_KERNEL_EXP || kern->nugget < 0)
+    return TLR_ERR_ARG;
+  tlr_opts o = opts_or_default(opts);
+  if (o.bs > 64 || o.bs > b) return TLR_ERR_ARG;
+  tlr_mat* M = nullptr;
+  ABI_BEGIN
+  M = mat_new(N, d, b);
+  compress_ordered_impl(ctx, pts_dev, perm_host, N, d, kern, b, eps, &o, M);
+  *A = M;
+  return TLR_OK;
+  }
+  catch (const tlr::Error& e) {
+    fprintf(stderr, "[tlr] %s\n", e.what());
+    mat_destroy(ctx, M);
+    return e.status;
+  }
+  catch (...) {
+    return TLR_ERR_CUDA;
+  }
+}
+
 tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* S, tlr_mat** D) {
   if (!ctx || !S || !D) return TLR_ERR_ARG;
   ABI_BEGIN
@@ -1146,6 +1223,7 @@ tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* S, tlr_mat** D) {
     return p;
   };
   M->pts = dup(S->pts, (size_t)S->N * S->d);
+  M->dperm = reinterpret_cast<int64_t*>(dup(reinterpret_cast<const double*>(S->dperm), (size_t)S->N));
   M->diag = dup(S->diag, (size_t)nb * b * b);
   M->dvec = dup(S->dvec, (size_t)nb * b);
   for (int i = 0; i < nb; ++i) {
@@ -1176,16 +1254,14 @@ tlr_status tlr_solve(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* B, int64_
   if (nrhs == 0) return TLR_OK;
   ABI_BEGIN
   const int64_t np = (int64_t)F->nb * F->b;
-  Buf bX(ctx), bP(ctx), bT(ctx);
+  Buf bX(ctx), bT(ctx);
   double* X = bX.need<double>((size_t)np * nrhs);
-  int64_t* perm = bP.need<int64_t>(F->N);
-  TLR_CUDA(cudaMemcpyAsync(perm, F->perm.data(), sizeof(int64_t) * F->N, cudaMemcpyHostToDevice, ctx->stream));
+  const int64_t* perm = F->dperm;
   permute_rows(ctx, F->N, nrhs, perm, 1, B, ldb, X, np, np);
   tri_forward(ctx, F, nrhs, X, np, bT);
   if (F->state == 2) scale_rows(ctx, (int)np, nrhs, F->dvec, 1, X, (int)np, X, (int)np);
   tri_backward(ctx, F, nrhs, X, np, bT);
   permute_rows(ctx, F->N, nrhs, perm, 0, X, np, B, ldb, np);
-  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
   return TLR_OK;
   ABI_END
 }
@@ -1213,11 +1289,10 @@ tlr_status tlr_matvec(tlr_ctx* ctx, const tlr_mat* F, int op, int nrhs, const do
   if (nrhs == 0) return TLR_OK;
   ABI_BEGIN
   const int64_t np = (int64_t)F->nb * F->b;
-  Buf bX(ctx), bY(ctx), bP(ctx), bT(ctx), bZ(ctx);
+  Buf bX(ctx), bY(ctx), bT(ctx), bZ(ctx);
   double* Xp = bX.need<double>((size_t)np * nrhs);
   double* Yp = bY.need<double>((size_t)np * nrhs);
-  int64_t* perm = bP.need<int64_t>(F->N);
-  TLR_CUDA(cudaMemcpyAsync(perm, F->perm.data(), sizeof(int64_t) * F->N, cudaMemcpyHostToDevice, ctx->stream));
+  const int64_t* perm = F->dperm;
   permute_rows(ctx, F->N, nrhs, perm, 1, X, ldx, Xp, np, np);
   if (op == TLR_OP_A) sym_mul(ctx, F, nrhs, Xp, np, Yp, np);
   else if (op == TLR_OP_L) tri_mul(ctx, F, 0, nrhs, Xp, np, Yp, np, bT);
@@ -1404,6 +1479,21 @@ tlr_status tlr_fp64_peak(tlr_ctx* ctx, double* tflops) {
 }
 
 int64_t tlr_launch_count(const tlr_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+tlr_status tlr_gemm_stats(tlr_ctx* ctx, int enable, double* ms, double* flops, int64_t* launches) {
+  if (!ctx) return TLR_ERR_ARG;
+  ABI_BEGIN
+  kprof_flush(ctx);
+  for (int f = 0; f < 6; ++f) {
+    if (ms) ms[f] = ctx->kfam_ms[f];
+    if (flops) flops[f] = ctx->kfam_flops[f];
+    if (launches) launches[f] = ctx->kfam_launches[f];
+    ctx->kfam_ms[f] = 0; ctx->kfam_flops[f] = 0; ctx->kfam_launches[f] = 0;
+  }
+  ctx->kprof = enable != 0;
+  return TLR_OK;
+  ABI_END
+}
 
 tlr_status tlr_profile(tlr_ctx* ctx, int enable, double* ms, int64_t* launches, int n) {
   if (!ctx) return TLR_ERR_ARG;
