@@ -154,6 +154,30 @@ tlr_status tlr_kernel_matvec(tlr_ctx* ctx, const double* points_host, int64_t N,
                              const tlr_kernel* kernel, int nrhs, const double* X, int64_t ldx,
                              double* Y, int64_t ldy);
 
+/* Allocation-free variant of tlr_kernel_matvec.  The paper has no counterpart:
+ * this is a library service for callers that cannot allocate device memory
+ * (a memory manager owns the whole device heap, cudaMalloc's implicit
+ * synchronization is not acceptable, or no tlr_ctx exists).  It computes the
+ * same Y = A X; instead of library-allocated device memory it stages the
+ * points in a fixed device array compiled into the library (3 MiB, held by
+ * every GPU that loads the library until the process exits), so it needs no
+ * context and calls no allocator.
+ *   cuda_stream: cudaStream_t of the CURRENT device (NULL: legacy default
+ *     stream); the call is enqueued on it and returns without synchronizing.
+ *   points_host: host, row-major N x d, original order; copied during the call
+ *     (if it is page-locked, leave it unchanged until the stream has run the call).
+ *   X, Y: device, N x nrhs, column-major, ldx, ldy >= N (caller-owned).
+ * Limits and errors: N * d <= 393216 (131072 points in 3D), else TLR_ERR_LIMIT;
+ * bad arguments TLR_ERR_ARG; a failing CUDA call TLR_ERR_CUDA.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's points;
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialized by the caller. */
+tlr_status tlr_kernel_matvec_noalloc(void* cuda_stream, const double* points_host, int64_t N, int d,
+                                     const tlr_kernel* kernel, int nrhs, const double* X,
+                                     int64_t ldx, double* Y, int64_t ldy);
+
 typedef struct {
   int64_t N;
   int b, nb, d;
