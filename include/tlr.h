@@ -260,7 +260,8 @@ tlr_status tlr_gemm_stats(tlr_ctx* ctx, int enable, double* ms, double* flops, i
  * consecutive phase boundaries (CUDA events) is charged to the earlier phase.
  * Copies the accumulated milliseconds and kernel launches of the n first phases
  * (order: gram, diag-update, potrf, sample, orthog, host-sync, project, trsm,
- * update-tiles, compress, solve, other) into ms / launches (either may be NULL),
+ * update-tiles, compress, solve, other; with n >= 13, ms[12] = host time blocked
+ * in stream synchronizations) into ms / launches (either may be NULL),
  * resets them, and turns profiling on (enable != 0) or off. */
 tlr_status tlr_profile(tlr_ctx* ctx, int enable, double* ms, int64_t* launches, int n);
 

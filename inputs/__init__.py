@@ -74,4 +74,6 @@ WORKLOADS = {
     "cov2d_4k": dict(N=4096, d=2, ell=0.1, nugget=1e-4, b=256, bs=16, seed=0),
     "cov3d_32k": dict(N=32768, d=3, ell=0.2, nugget=1e-4, b=512, bs=32, seed=1),
     "cov2d_131k": dict(N=131072, d=2, ell=0.1, nugget=1e-4, b=1024, bs=16, seed=2),
+    # smaller case of the same 2D recipe (profiling captures)
+    "cov2d_16k": dict(N=16384, d=2, ell=0.1, nugget=1e-4, b=1024, bs=16, seed=2),
 }

@@ -274,7 +274,7 @@ class Context:
                "tlr_dense_trsm")
 
     PHASES = ["gram", "diag_update", "potrf", "sample", "orthog", "host_sync", "project", "trsm", "update_tiles",
-              "compress", "solve", "other"]
+              "compress", "solve", "other", "host_blocked"]
 
     def profile(self, enable: bool = True) -> dict:
         """Return (and reset) the phase profile {phase: (ms, launches)}; switch profiling on/off."""

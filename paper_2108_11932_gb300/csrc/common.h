@@ -67,7 +67,10 @@ constexpr int GEMM_TM = 64, GEMM_TN = 32, GEMM_TK = 16;
 // Library-owned objects.
 struct tlr_ctx {
   int device = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // stream the next launch goes to (main or side)
+  cudaStream_t main = nullptr;    // caller's stream
+  cudaStream_t side = nullptr;    // library stream for work overlapped with the main stream
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   tlr_alloc_fn alloc = nullptr;
   tlr_free_fn free_fn = nullptr;
   void* user = nullptr;
@@ -80,6 +83,8 @@ struct tlr_ctx {
   // Split-K / small scratch, grown on demand (stream-ordered frees).
   void* scratch = nullptr;
   size_t scratch_cap = 0;
+  void* scratch_side = nullptr;  // the side stream's own split-K scratch
+  size_t scratch_side_cap = 0;
   // Small host-pinned status buffer for per-round device->host reads.
   void* hstatus = nullptr;
   size_t hstatus_cap = 0;
@@ -92,6 +97,7 @@ struct tlr_ctx {
   int64_t phase_launch[16] = {0};
   int cur_phase = -1;
   int64_t phase_launch0 = 0;
+  double host_wait_ms = 0;  // host time blocked in stream synchronizations while profiling
   // Per-kernel accounting of the batched GEMM launches (CUDA events around each launch).
   bool kprof = false;
   std::vector<cudaEvent_t> kev;
@@ -114,6 +120,7 @@ struct tlr_mat {
   int64_t* dperm = nullptr;  // device copy of perm
   double* diag = nullptr;  // device, nb * b * b
   double* dvec = nullptr;  // device, nb * b (LDL^T D)
+  double* dinv = nullptr;  // device, nb * b * b: inverses of the (unit for LDL^T) lower diagonal tiles
   std::vector<int> rank;   // nb * nb (i > j)
   std::vector<int64_t> uoff, voff;  // column offsets of U_ij in Urow[i], V_ij in Vcol[j]
   std::vector<double*> Urow, Vcol;  // per block row / block column panels (device)

@@ -170,9 +170,117 @@ __global__ void __launch_bounds__(32) k_cholqr_small(int bs, const double* __res
 #undef Ri
 }
 
+// Register-resident Cholesky-QR step for bs <= 32 (one warp per slot, lane c holds
+// column c of the Gram matrix).  Same decisions as k_cholqr_small, computed
+// right-looking: when column j is kept, every later column c is reduced by the
+// rank-one term R(j, :)^T R(j, c); a dropped column leaves the others unchanged.
+// The kept factor is embedded in an upper-triangular Rt whose dropped rows and
+// columns are the identity, so Rt^{-1} restricted to the kept indices is the
+// inverse of the kept factor, and every register index is a compile-time constant.
+template <int BS>
+__global__ void __launch_bounds__(32) k_cholqr_reg(const double* __restrict__ Gall, double* __restrict__ Mall,
+                                                   int* __restrict__ status, double* __restrict__ enorm,
+                                                   double thr, double tau, int first_pass,
+                                                   const int* __restrict__ nk_in) {
+  const int s = blockIdx.x, lane = threadIdx.x;
+  const double* G = Gall + (size_t)s * BS * BS;
+  double* M = Mall + (size_t)s * BS * BS;
+  double g[BS];  // column `lane` of G, reduced in place
+#pragma unroll
+  for (int r = 0; r < BS; ++r) g[r] = (lane < BS) ? G[r + (size_t)lane * BS] : 0.0;
+  double gdiag = 0.0;
+#pragma unroll
+  for (int r = 0; r < BS; ++r)
+    if (r == lane) gdiag = g[r];
+  int n = BS;
+  double thr2 = thr * thr;
+  if (first_pass) {
+    double gmax = gdiag;
+    for (int o = 16; o; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    const double e = sqrt(fmax(gmax, 0.0));
+    if (lane == 0) enorm[s] = e;
+    if (!(e > thr)) {
+      if (lane < BS) {
+#pragma unroll
+        for (int r = 0; r < BS; ++r) M[r + (size_t)lane * BS] = 0.0;
+      }
+      if (lane == 0) { status[2 * s] = 1; status[2 * s + 1] = 0; }
+      return;
+    }
+    if (lane == 0) status[2 * s] = 0;
+  } else {
+    n = nk_in[2 * s + 1];
+    thr2 = 0.0;
+  }
+  double rt[BS];      // rt[j] = Rt(j, lane)
+  unsigned mask = 0;  // kept columns
+#pragma unroll
+  for (int j = 0; j < BS; ++j) {
+    rt[j] = (lane == j) ? 1.0 : 0.0;
+    if (j < n) {
+      const double dj = __shfl_sync(0xffffffffu, g[j], j);  // pivot of column j
+      const double gjj = __shfl_sync(0xffffffffu, gdiag, j);
+      const bool kept = (dj > fmax(thr2, tau * gjj)) && (dj > 0.0) && isfinite(dj);
+      if (kept) {
+        const double rjj = sqrt(dj);
+        const double rj = (lane == j) ? rjj : ((lane > j && lane < n) ? g[j] / rjj : 0.0);
+#pragma unroll
+        for (int a = j + 1; a < BS; ++a) {
+          const double rja = __shfl_sync(0xffffffffu, rj, a);
+          if (lane > j && lane < n) g[a] = fma(-rja, rj, g[a]);
+        }
+        rt[j] = rj;
+        mask |= 1u << j;
+      }
+    }
+  }
+  // decouple dropped columns: Rt(j, c) = 0 for kept j and dropped c != j
+  const bool mine = (lane < BS) && ((mask >> lane) & 1u);
+#pragma unroll
+  for (int j = 0; j < BS; ++j)
+    if (!mine && lane != j) rt[j] = 0.0;
+  // column `lane` of Rt^{-1} by back substitution: x[p] = -(sum_{q>p} Rt(p,q) x[q]) / Rt(p,p)
+  double x[BS];
+#pragma unroll
+  for (int p = BS - 1; p >= 0; --p) {
+    double acc = 0.0;
+#pragma unroll
+    for (int q = p + 1; q < BS; ++q) {
+      const double rpq = __shfl_sync(0xffffffffu, rt[p], q);
+      if (q <= lane) acc = fma(rpq, x[q], acc);
+    }
+    const double rpp = __shfl_sync(0xffffffffu, rt[p], p);
+    x[p] = (p == lane) ? 1.0 / rpp : ((p < lane) ? -acc / rpp : 0.0);
+  }
+  // M column pos(lane) = kept part of column `lane` of Rt^{-1}; zero elsewhere
+  const int nk = __popc(mask);
+  if (lane < BS) {
+#pragma unroll
+    for (int r = 0; r < BS; ++r) M[r + (size_t)lane * BS] = 0.0;
+  }
+  __syncwarp();
+  if (mine) {
+    const int pos = __popc(mask & ((1u << lane) - 1u));
+#pragma unroll
+    for (int p = 0; p < BS; ++p)
+      if (p <= lane && ((mask >> p) & 1u)) M[p + (size_t)pos * BS] = x[p];
+  }
+  if (lane == 0) status[2 * s + 1] = nk;
+}
+
 void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mout, int* status,
                   double* enorm, double thr, double tau, int first_pass, const int* nk_in) {
   if (nslots <= 0) return;
+  if (bs == 16 || bs == 32 || bs == 8) {
+    if (bs == 16)
+      k_cholqr_reg<16><<<(unsigned)nslots, 32, 0, ctx->stream>>>(G, Mout, status, enorm, thr, tau, first_pass, nk_in);
+    else if (bs == 32)
+      k_cholqr_reg<32><<<(unsigned)nslots, 32, 0, ctx->stream>>>(G, Mout, status, enorm, thr, tau, first_pass, nk_in);
+    else
+      k_cholqr_reg<8><<<(unsigned)nslots, 32, 0, ctx->stream>>>(G, Mout, status, enorm, thr, tau, first_pass, nk_in);
+    TLR_LAUNCH_CHECK(ctx);
+    return;
+  }
   TLR_REQUIRE(bs <= MAXBS, TLR_ERR_LIMIT, "ARA block width above 64");
   const size_t smem = sizeof(double) * 2 * bs * (bs + 1) + sizeof(int) * bs;
   static bool attr_set = false;
@@ -250,10 +358,17 @@ void potrf_diag_block(tlr_ctx* ctx, int nbk, double* A, int lda, int ldl, double
 __global__ void __launch_bounds__(64) k_trsm_panel_right(int m, int nbk, const double* __restrict__ L,
                                                          int lda, double* __restrict__ X, int ldx, int ldl,
                                                          const double* __restrict__ dvec) {
-  __shared__ double Xs[PB][PB + 1];
+  // The 64 x 64 block is staged in shared memory with one coalesced load: the
+  // substitution reads it by rows, which in the column-major array would touch a
+  // new cache line at every step.
+  extern __shared__ double dsm[];
+  double (*Ls)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm);
+  double (*Xs)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm + PB * (PB + 1));
   const int tid = threadIdx.x, r0 = blockIdx.x * PB;
-  // every thread reads the same L entry at the same time: served as an L1 broadcast
-#define Ls(r, c) __ldg(L + (r) + (size_t)(c) * lda)
+  for (int e = tid; e < nbk * nbk; e += 64) {
+    const int r = e % nbk, c = e / nbk;
+    Ls[r][c] = L[r + (size_t)c * lda];
+  }
   const int rows = min(PB, m - r0);
   for (int e = tid; e < rows * nbk; e += 64) {
     const int r = e % rows, c = e / rows;
@@ -264,8 +379,8 @@ __global__ void __launch_bounds__(64) k_trsm_panel_right(int m, int nbk, const d
     // solve x L^T = a  <=>  L x^T = a^T: forward substitution over c
     for (int c = 0; c < nbk; ++c) {
       double v = Xs[tid][c];
-      for (int l = 0; l < c; ++l) v = fma(-Ls(c, l), Xs[tid][l], v);
-      Xs[tid][c] = ldl ? v : v / Ls(c, c);
+      for (int l = 0; l < c; ++l) v = fma(-Ls[c][l], Xs[tid][l], v);
+      Xs[tid][c] = ldl ? v : v / Ls[c][c];
     }
     if (ldl)
       for (int c = 0; c < nbk; ++c) Xs[tid][c] /= dvec[c];
@@ -275,13 +390,20 @@ __global__ void __launch_bounds__(64) k_trsm_panel_right(int m, int nbk, const d
     const int r = e % rows, c = e / rows;
     X[(r0 + r) + (size_t)c * ldx] = Xs[r][c];
   }
-#undef Ls
 }
+
+static size_t two_block_smem() { return sizeof(double) * 2 * PB * (PB + 1); }
 
 void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, double* X, int ldx,
                       int ldl, const double* dvec) {
   if (m <= 0) return;
-  k_trsm_panel_right<<<cdiv(m, PB), 64, 0, ctx->stream>>>(m, nbk, L, lda, X, ldx, ldl, dvec);
+  static bool attr = false;
+  if (!attr) {
+    TLR_CUDA(cudaFuncSetAttribute(k_trsm_panel_right, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)two_block_smem()));
+    attr = true;
+  }
+  k_trsm_panel_right<<<cdiv(m, PB), 64, two_block_smem(), ctx->stream>>>(m, nbk, L, lda, X, ldx, ldl, dvec);
   TLR_LAUNCH_CHECK(ctx);
 }
 
@@ -290,9 +412,14 @@ void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, do
 __global__ void __launch_bounds__(64) k_trsm_left_block(int nbk, const double* __restrict__ L, int lda,
                                                         int unit, int nrhs, double* __restrict__ X, int ldx,
                                                         int trans) {
-  __shared__ double Xs[PB][PB + 1];
+  extern __shared__ double dsm[];
+  double (*Ls)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm);
+  double (*Xs)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm + PB * (PB + 1));
   const int tid = threadIdx.x, c0 = blockIdx.x * PB;
-#define Ls(r, c) __ldg(L + (r) + (size_t)(c) * lda)
+  for (int e = tid; e < nbk * nbk; e += 64) {
+    const int r = e % nbk, c = e / nbk;
+    Ls[r][c] = L[r + (size_t)c * lda];
+  }
   const int cols = min(PB, nrhs - c0);
   for (int e = tid; e < nbk * cols; e += 64) {
     const int r = e % nbk, c = e / nbk;
@@ -303,14 +430,14 @@ __global__ void __launch_bounds__(64) k_trsm_left_block(int nbk, const double* _
     if (!trans) {
       for (int r = 0; r < nbk; ++r) {
         double v = Xs[r][tid];
-        for (int l = 0; l < r; ++l) v = fma(-Ls(r, l), Xs[l][tid], v);
-        Xs[r][tid] = unit ? v : v / Ls(r, r);
+        for (int l = 0; l < r; ++l) v = fma(-Ls[r][l], Xs[l][tid], v);
+        Xs[r][tid] = unit ? v : v / Ls[r][r];
       }
     } else {  // L^T x = b: backward substitution
       for (int r = nbk - 1; r >= 0; --r) {
         double v = Xs[r][tid];
-        for (int l = r + 1; l < nbk; ++l) v = fma(-Ls(l, r), Xs[l][tid], v);
-        Xs[r][tid] = unit ? v : v / Ls(r, r);
+        for (int l = r + 1; l < nbk; ++l) v = fma(-Ls[l][r], Xs[l][tid], v);
+        Xs[r][tid] = unit ? v : v / Ls[r][r];
       }
     }
   }
@@ -319,19 +446,29 @@ __global__ void __launch_bounds__(64) k_trsm_left_block(int nbk, const double* _
     const int r = e % nbk, c = e / nbk;
     X[r + (size_t)(c0 + c) * ldx] = Xs[r][c];
   }
-#undef Ls
+}
+
+static void left_block_attr() {
+  static bool attr = false;
+  if (!attr) {
+    TLR_CUDA(cudaFuncSetAttribute(k_trsm_left_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)two_block_smem()));
+    attr = true;
+  }
 }
 
 void trsm_left_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs, double* X,
                      int ldx) {
   if (nrhs <= 0) return;
-  k_trsm_left_block<<<cdiv(nrhs, PB), 64, 0, ctx->stream>>>(nbk, L, lda, unit, nrhs, X, ldx, 0);
+  left_block_attr();
+  k_trsm_left_block<<<cdiv(nrhs, PB), 64, two_block_smem(), ctx->stream>>>(nbk, L, lda, unit, nrhs, X, ldx, 0);
   TLR_LAUNCH_CHECK(ctx);
 }
 void trsm_left_t_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs,
                        double* X, int ldx) {
   if (nrhs <= 0) return;
-  k_trsm_left_block<<<cdiv(nrhs, PB), 64, 0, ctx->stream>>>(nbk, L, lda, unit, nrhs, X, ldx, 1);
+  left_block_attr();
+  k_trsm_left_block<<<cdiv(nrhs, PB), 64, two_block_smem(), ctx->stream>>>(nbk, L, lda, unit, nrhs, X, ldx, 1);
   TLR_LAUNCH_CHECK(ctx);
 }
 

@@ -39,16 +39,21 @@ void dfree(tlr_ctx* ctx, void* p) {
   else cudaFreeAsync(p, ctx->stream);
 }
 
+// Split-K scratch; each stream has its own so that overlapped launches never share it.
 void* scratch(tlr_ctx* ctx, size_t bytes) {
-  if (bytes > ctx->scratch_cap) {
-    dfree(ctx, ctx->scratch);
-    ctx->scratch = nullptr;
-    ctx->scratch_cap = 0;
-    size_t cap = std::max(bytes, ctx->scratch_cap * 2);
-    ctx->scratch = dalloc(ctx, cap);
-    ctx->scratch_cap = cap;
+  const bool side = ctx->side && ctx->stream == ctx->side;
+  void*& p = side ? ctx->scratch_side : ctx->scratch;
+  size_t& cap = side ? ctx->scratch_side_cap : ctx->scratch_cap;
+  if (bytes > cap) {
+    if (side) TLR_CUDA(cudaStreamSynchronize(ctx->side));  // the old buffer may still be read
+    dfree(ctx, p);
+    p = nullptr;
+    const size_t ncap = std::max(bytes, cap * 2);
+    cap = 0;
+    p = dalloc(ctx, ncap);
+    cap = ncap;
   }
-  return ctx->scratch;
+  return p;
 }
 
 // Job descriptors travel through a pinned staging ring mirrored on the device.
@@ -58,7 +63,9 @@ void* upload(tlr_ctx* ctx, const void* host, size_t bytes) {
   const size_t need = (bytes + 255) & ~size_t(255);
   TLR_REQUIRE(need <= ctx->ring_cap, TLR_ERR_LIMIT, "job list larger than the upload ring");
   if (ctx->ring_pos + need > ctx->ring_cap) {
-    TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+    // no launch on either stream may still read the region about to be reused
+    TLR_CUDA(cudaStreamSynchronize(ctx->main));
+    if (ctx->side) TLR_CUDA(cudaStreamSynchronize(ctx->side));
     ctx->ring_pos = 0;
   }
   char* h = ctx->pinned + ctx->ring_pos;
@@ -98,7 +105,8 @@ void prof_mark(tlr_ctx* ctx, int phase) {
 void prof_flush(tlr_ctx* ctx) {
   if (!ctx->prof || ctx->ev_n == 0) return;
   prof_mark(ctx, PH_OTHER);
-  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  TLR_CUDA(cudaStreamSynchronize(ctx->main));
+  if (ctx->side) TLR_CUDA(cudaStreamSynchronize(ctx->side));
   for (size_t e = 0; e + 1 < ctx->ev_n; ++e) {
     float ms = 0;
     TLR_CUDA(cudaEventElapsedTime(&ms, ctx->ev[e], ctx->ev[e + 1]));
@@ -131,7 +139,8 @@ void kprof_end(tlr_ctx* ctx, int family, double flops) {
 
 void kprof_flush(tlr_ctx* ctx) {
   if (ctx->kev_n == 0) return;
-  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  TLR_CUDA(cudaStreamSynchronize(ctx->main));  // events may sit on either stream
+  if (ctx->side) TLR_CUDA(cudaStreamSynchronize(ctx->side));
   for (size_t e = 0; e < ctx->kev_n; e += 2) {
     float ms = 0;
     TLR_CUDA(cudaEventElapsedTime(&ms, ctx->kev[e], ctx->kev[e + 1]));
@@ -166,7 +175,13 @@ struct Buf {
 
 static void d2h_sync(tlr_ctx* ctx, void* host, const void* dev, size_t bytes) {
   TLR_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->prof) {
+    const auto t0 = std::chrono::steady_clock::now();
+    TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->host_wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  } else {
+    TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
 }
 
 // ======================================================================== dense diagonal tiles
@@ -225,6 +240,25 @@ static void dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int unit, 
         gemm<double>(ctx, TN, jobs);
       }
       trsm_left_t_block(ctx, pb, L + p + (size_t)p * lda, lda, unit, nrhs, X + p, ldx);
+    }
+  }
+}
+
+// Linv = L^{-1} for an n x n lower-triangular L (unit diagonal if `unit`), Linv
+// lower triangular (ld n).  Blocked substitution on the identity: row block p of
+// Linv only has nonzeros in its first p + pb columns, so each step solves and
+// updates only those (n^3/3 flops instead of n^3).
+static void dense_trinv(tlr_ctx* ctx, int n, const double* L, int lda, int unit, double* Linv) {
+  TLR_CUDA(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)n * n, ctx->stream));
+  add_diag(ctx, n, Linv, n, 1.0);
+  for (int p = 0; p < n; p += NBK) {
+    const int pb = std::min(NBK, n - p);
+    trsm_left_block(ctx, pb, L + p + (size_t)p * lda, lda, unit, p + pb, Linv + p, n);
+    const int m = n - p - pb;
+    if (m > 0) {
+      std::vector<GemmJob<double>> jobs{job<double>(NN, m, p + pb, L + (p + pb) + (size_t)p * lda, lda, Linv + p, n,
+                                                    pb, Linv + p + pb, n, -1.0, 1.0)};
+      gemm<double>(ctx, NN, jobs);
     }
   }
 }
@@ -446,6 +480,7 @@ static void mat_destroy(tlr_ctx* ctx, tlr_mat* M) {
   dfree(ctx, M->dperm);
   dfree(ctx, M->diag);
   dfree(ctx, M->dvec);
+  dfree(ctx, M->dinv);
   delete M;
 }
 
@@ -735,13 +770,14 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
   TLR_CUDA(cudaMemcpyAsync(F->diag, A->diag, sizeof(double) * (size_t)nb * b * b, cudaMemcpyDeviceToDevice,
                            ctx->stream));
   if (ldl) F->dvec = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b));
+  F->dinv = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
   for (int i = 0; i < nb; ++i) ensure_ucap(ctx, F, i, std::max<int64_t>(A->ulen[i], 16));
   Buf bQ(ctx), bX(ctx), bX0(ctx), bG(ctx), bE(ctx), bW(ctx), bP(ctx), bZ(ctx), bTab(ctx), bInfo(ctx),
-      bDV(ctx), bTmp(ctx), bDk(ctx);
+      bDV(ctx), bTmp(ctx), bDk(ctx), bBc(ctx);
   const size_t qstride = (size_t)b * (b + bs);
   double* Q = bQ.need<double>((size_t)std::max(nb - 1, 1) * qstride);
   int* info = bInfo.need<int>(2);
-  int* hinfo = static_cast<int*>(host_status(ctx, 64));
+  bTmp.need<double>((size_t)b * NBK);  // sized once: the side stream never reallocates it
   double fl_exec = 0, fl_model = 0;
   int64_t rounds = 0;
   std::vector<int> rtab((size_t)nb * nb * 3);
@@ -780,9 +816,18 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
       }
       gemm<double>(ctx, TN, jg);
     }
+    // The diagonal tile (updateDense, compensation, chol) is not read by the ARA of
+    // column k, only by its batchTrsm: it runs on the side stream, overlapped with
+    // the sampling rounds below, and is joined before the trsm.
+    // (The Schur compensation runs a nested ARA with its own workspaces: it stays on the main stream.)
+    const bool overlap = o->compensation != TLR_COMP_SCHUR;
+    if (overlap) {
+      TLR_CUDA(cudaEventRecord(ctx->ev_fork, ctx->main));
+      TLR_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+      ctx->stream = ctx->side;
+    }
     // ---- updateDense: A_kk -= sum_j U_kj G_kj U_kj^T  (G_kj = rows of tile k in Gcol_j)
     double* Akk = F->diag + (size_t)k * b * b;
-    prof_mark(ctx, PH_DIAG);
     if (Kk > 0) {
       double* E = bE.need<double>((size_t)b * Kk);
       std::vector<GemmJob<double>> je;
@@ -831,24 +876,35 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     }
     if (o->compensation == TLR_COMP_SHIFT && o->shift != 0.0) add_diag(ctx, b, Akk, b, o->shift);
     // ---- dense factorization of the diagonal tile
-    prof_mark(ctx, PH_POTRF);
     TLR_CUDA(cudaMemsetAsync(info, 0xff, sizeof(int), ctx->stream));
     dense_factor(ctx, b, Akk, b, ldl, ldl ? F->dvec + (size_t)k * b : nullptr, info, bTmp);
     fl_exec += (double)b * b * b / 3.0;
     fl_model += (double)b * b * b / 3.0;
-    d2h_sync(ctx, hinfo, info, sizeof(int));
-    if (hinfo[0] >= 0) {
-      mat_destroy(ctx, F);
-      A->state = 3;
-      A->k_fail = k;
-      return TLR_ERR_NOT_SPD;
-    }
+    // L_kk^{-1}: batchTrsm becomes one product, and so does every later diagonal solve
+    dense_trinv(ctx, b, Akk, b, ldl, F->dinv + (size_t)k * b * b);
+    fl_exec += (double)b * b * b / 3.0;
+    TLR_CUDA(cudaEventRecord(ctx->ev_join, ctx->stream));
+    ctx->stream = ctx->main;
+    auto check_tile = [&]() -> bool {
+      TLR_CUDA(cudaStreamWaitEvent(ctx->main, ctx->ev_join, 0));
+      int* hinfo = static_cast<int*>(host_status(ctx, 64));
+      d2h_sync(ctx, hinfo, info, sizeof(int));
+      return hinfo[0] < 0;
+    };
     for (int j = 0; j < k; ++j) {
       const int r = F->rank[ix(F, k, j)];
       fl_model += 4.0 * b * r * r + 2.0 * b * b * r;
     }
     const int nops = nb - k - 1;
-    if (nops == 0) continue;
+    if (nops == 0) {
+      if (!check_tile()) {
+        mat_destroy(ctx, F);
+        A->state = 3;
+        A->k_fail = k;
+        return TLR_ERR_NOT_SPD;
+      }
+      continue;
+    }
     // ---- cholARAUpdate (Algorithm 5): tiles sorted by their original rank, descending
     std::vector<int> ops2i(nops);
     for (int u = 0; u < nops; ++u) ops2i[u] = k + 1 + u;
@@ -895,7 +951,15 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     for (int v : q) Rk += v;
     F->Vcol[k] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(Rk, 1) * b));
     F->vlen[k] = Rk;
-    fs.Bcol = F->Vcol[k];
+    double* Bcol = bBc.need<double>((size_t)std::max<int64_t>(Rk, 1) * b);
+    fs.Bcol = Bcol;
+    prof_mark(ctx, PH_POTRF);  // waiting for the diagonal tile of this column
+    if (!check_tile()) {
+      mat_destroy(ctx, F);
+      A->state = 3;
+      A->k_fail = k;
+      return TLR_ERR_NOT_SPD;
+    }
     prof_mark(ctx, PH_PROJECT);
     fs.project(q);
     fl_exec += fs.flops_exec;
@@ -903,9 +967,11 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     // ---- batchTrsm: V_ik = L_kk^{-1} B_i (LDL^T: then D_k^{-1}, batchIDMult)
     prof_mark(ctx, PH_TRSM);
     if (Rk > 0) {
-      dense_trsm(ctx, b, Akk, b, ldl, (int)Rk, F->Vcol[k], b, 0);
+      std::vector<GemmJob<double>> jt{job<double>(NN, b, (int)Rk, F->dinv + (size_t)k * b * b, b, Bcol, b, b,
+                                                  F->Vcol[k], b, 1.0, 0.0)};
+      gemm<double>(ctx, NN, jt);
       if (ldl) scale_rows(ctx, b, (int)Rk, F->dvec + (size_t)k * b, 1, F->Vcol[k], b, F->Vcol[k], b);
-      fl_exec += (double)b * b * Rk;
+      fl_exec += 2.0 * b * b * Rk;
       fl_model += (double)b * b * Rk;
     }
     // ---- updateTiles: U_ik = Q_i appended to block row i; V_ik in block column k
@@ -930,6 +996,8 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
   dfree(ctx, A->dvec);
   A->diag = F->diag; F->diag = nullptr;
   A->dvec = F->dvec; F->dvec = nullptr;
+  dfree(ctx, A->dinv);
+  A->dinv = F->dinv; F->dinv = nullptr;
   A->rank = F->rank; A->uoff = F->uoff; A->voff = F->voff;
   A->Urow = F->Urow; A->Vcol = F->Vcol; A->ucap = F->ucap; A->vlen = F->vlen; A->ulen = F->ulen;
   F->Urow.assign(nb, nullptr);
@@ -946,35 +1014,36 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
 }
 
 // ======================================================================== solve / products
-// X (nb*b x nrhs, KD order, padded) <- L^{-1} X
-static void tri_forward(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* X, int64_t ldx, Buf& tmp) {
+// Z = L^{-1} X (Algorithm 7): Z_k = L_kk^{-1} X_k, then X_i -= U_ik (V_ik^T Z_k) for i > k.
+// X (nb*b x nrhs, KD order, padded) is consumed.
+static void tri_forward(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* X, double* Z, int64_t ld, Buf& tmp) {
   const int nb = F->nb, b = F->b;
-  const int unit = F->state == 2;
   for (int k = 0; k < nb; ++k) {
-    double* Xk = X + (size_t)k * b;
-    dense_trsm(ctx, b, F->diag + (size_t)k * b * b, b, unit, nrhs, Xk, (int)ldx, 0);
+    double* Zk = Z + (size_t)k * b;
+    std::vector<GemmJob<double>> j0{job<double>(NN, b, nrhs, F->dinv + (size_t)k * b * b, b, X + (size_t)k * b, (int)ld,
+                                                b, Zk, (int)ld, 1.0, 0.0)};
+    gemm<double>(ctx, NN, j0);
     const int64_t Rk = F->vlen[k];
     if (Rk == 0) continue;
     double* T = tmp.need<double>((size_t)Rk * nrhs);
-    std::vector<GemmJob<double>> j1{job<double>(TN, (int)Rk, nrhs, F->Vcol[k], b, Xk, (int)ldx, b, T, (int)Rk, 1.0, 0.0)};
+    std::vector<GemmJob<double>> j1{job<double>(TN, (int)Rk, nrhs, F->Vcol[k], b, Zk, (int)ld, b, T, (int)Rk, 1.0, 0.0)};
     gemm<double>(ctx, TN, j1);
     std::vector<GemmJob<double>> j2;
     for (int i = k + 1; i < nb; ++i) {
       const int r = F->rank[ix(F, i, k)];
       if (r == 0) continue;
       j2.push_back(job<double>(NN, b, nrhs, Uptr(F, i, k), b, T + F->voff[ix(F, i, k)], (int)Rk, r,
-                               X + (size_t)i * b, (int)ldx, -1.0, 1.0));
+                               X + (size_t)i * b, (int)ld, -1.0, 1.0));
     }
     gemm<double>(ctx, NN, j2);
   }
 }
 
-// X <- L^{-T} X
-static void tri_backward(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* X, int64_t ldx, Buf& tmp) {
+// X = L^{-T} Z (transpose of Algorithm 7): Z_k -= sum_{i>k} V_ik (U_ik^T X_i); X_k = L_kk^{-T} Z_k.
+static void tri_backward(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* Z, double* X, int64_t ld, Buf& tmp) {
   const int nb = F->nb, b = F->b;
-  const int unit = F->state == 2;
   for (int k = nb - 1; k >= 0; --k) {
-    double* Xk = X + (size_t)k * b;
+    double* Zk = Z + (size_t)k * b;
     const int64_t Rk = F->vlen[k];
     if (Rk > 0) {
       double* S = tmp.need<double>((size_t)Rk * nrhs);
@@ -982,14 +1051,16 @@ static void tri_backward(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* X, in
       for (int i = k + 1; i < nb; ++i) {
         const int r = F->rank[ix(F, i, k)];
         if (r == 0) continue;
-        j1.push_back(job<double>(TN, r, nrhs, Uptr(F, i, k), b, X + (size_t)i * b, (int)ldx, b,
+        j1.push_back(job<double>(TN, r, nrhs, Uptr(F, i, k), b, X + (size_t)i * b, (int)ld, b,
                                  S + F->voff[ix(F, i, k)], (int)Rk, 1.0, 0.0));
       }
       gemm<double>(ctx, TN, j1);
-      std::vector<GemmJob<double>> j2{job<double>(NN, b, nrhs, F->Vcol[k], b, S, (int)Rk, (int)Rk, Xk, (int)ldx, -1.0, 1.0)};
+      std::vector<GemmJob<double>> j2{job<double>(NN, b, nrhs, F->Vcol[k], b, S, (int)Rk, (int)Rk, Zk, (int)ld, -1.0, 1.0)};
       gemm<double>(ctx, NN, j2);
     }
-    dense_trsm(ctx, b, F->diag + (size_t)k * b * b, b, unit, nrhs, Xk, (int)ldx, 1);
+    std::vector<GemmJob<double>> j3{job<double>(TN, b, nrhs, F->dinv + (size_t)k * b * b, b, Zk, (int)ld, b,
+                                                X + (size_t)k * b, (int)ld, 1.0, 0.0)};
+    gemm<double>(ctx, TN, j3);
   }
 }
 
@@ -1121,6 +1192,10 @@ tlr_status tlr_create(tlr_ctx** out, int device, void* stream, tlr_alloc_fn allo
   ctx->device = device;
   TLR_CUDA(cudaSetDevice(device));
   ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->main = ctx->stream;
+  TLR_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  TLR_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  TLR_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
   ctx->alloc = alloc;
   ctx->free_fn = free_fn;
   ctx->user = user;
@@ -1146,11 +1221,18 @@ tlr_status tlr_destroy(tlr_ctx* ctx) {
   if (!ctx) return TLR_ERR_ARG;
   ABI_BEGIN
   cudaStreamSynchronize(ctx->stream);
+  cudaStreamSynchronize(ctx->side);
   dfree(ctx, ctx->djobs);
   dfree(ctx, ctx->scratch);
+  dfree(ctx, ctx->scratch_side);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->hstatus) cudaFreeHost(ctx->hstatus);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  for (auto e : ctx->ev) cudaEventDestroy(e);
+  for (auto e : ctx->kev) cudaEventDestroy(e);
   delete ctx;
   return TLR_OK;
   ABI_END
@@ -1226,6 +1308,7 @@ tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* S, tlr_mat** D) {
   M->dperm = reinterpret_cast<int64_t*>(dup(reinterpret_cast<const double*>(S->dperm), (size_t)S->N));
   M->diag = dup(S->diag, (size_t)nb * b * b);
   M->dvec = dup(S->dvec, (size_t)nb * b);
+  M->dinv = dup(S->dinv, (size_t)nb * b * b);
   for (int i = 0; i < nb; ++i) {
     M->Urow[i] = S->Urow[i] ? dup(S->Urow[i], (size_t)std::max<int64_t>(S->ucap[i], 1) * b) : nullptr;
     M->Vcol[i] = S->Vcol[i] ? dup(S->Vcol[i], (size_t)std::max<int64_t>(S->vlen[i], 1) * b) : nullptr;
@@ -1254,13 +1337,14 @@ tlr_status tlr_solve(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* B, int64_
   if (nrhs == 0) return TLR_OK;
   ABI_BEGIN
   const int64_t np = (int64_t)F->nb * F->b;
-  Buf bX(ctx), bT(ctx);
+  Buf bX(ctx), bZ(ctx), bT(ctx);
   double* X = bX.need<double>((size_t)np * nrhs);
+  double* Z = bZ.need<double>((size_t)np * nrhs);
   const int64_t* perm = F->dperm;
   permute_rows(ctx, F->N, nrhs, perm, 1, B, ldb, X, np, np);
-  tri_forward(ctx, F, nrhs, X, np, bT);
-  if (F->state == 2) scale_rows(ctx, (int)np, nrhs, F->dvec, 1, X, (int)np, X, (int)np);
-  tri_backward(ctx, F, nrhs, X, np, bT);
+  tri_forward(ctx, F, nrhs, X, Z, np, bT);
+  if (F->state == 2) scale_rows(ctx, (int)np, nrhs, F->dvec, 1, Z, (int)np, Z, (int)np);
+  tri_backward(ctx, F, nrhs, Z, X, np, bT);
   permute_rows(ctx, F->N, nrhs, perm, 0, X, np, B, ldb, np);
   return TLR_OK;
   ABI_END
@@ -1503,7 +1587,9 @@ tlr_status tlr_profile(tlr_ctx* ctx, int enable, double* ms, int64_t* launches, 
     for (int p = 0; p < n && p < PH_COUNT; ++p) ms[p] = ctx->phase_ms[p];
   if (launches)
     for (int p = 0; p < n && p < PH_COUNT; ++p) launches[p] = ctx->phase_launch[p];
+  if (ms && n > PH_COUNT) ms[PH_COUNT] = ctx->host_wait_ms;
   for (int p = 0; p < PH_COUNT; ++p) { ctx->phase_ms[p] = 0; ctx->phase_launch[p] = 0; }
+  ctx->host_wait_ms = 0;
   ctx->prof = enable != 0;
   return TLR_OK;
   ABI_END
