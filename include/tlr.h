@@ -57,7 +57,10 @@ typedef struct {
  * diagonal-tile factorization and the triangular solves are FP64 always.     */
 enum {
   TLR_PREC_FP64 = 0, /* everything FP64 */
-  TLR_PREC_FP32 = 1  /* sampling/projection chains in FP32 with FP32 accumulation */
+  TLR_PREC_FP32 = 1  /* sampling/projection chains in FP32 with FP32 accumulation for every
+                        tile whose estimated FP32 rounding error u32 sqrt(K) (|A_ik|_F +
+                        sum_j |L_ij|_F |L_kj|_F) is below 1/8 of the ARA threshold, FP64 for
+                        the others; eps < 1e-4 uses FP64 throughout */
 };
 
 /* Definiteness safeguards (Section 5.1). */
@@ -186,10 +189,12 @@ typedef struct {
   int max_rank;        /* over lower off-diagonal tiles */
   double mean_rank;
   int64_t bytes;       /* device bytes of the representation */
-  double flops_exec;   /* flops executed by the last factorization (all phases) */
+  double flops_exec;   /* FP64 flops executed by the last factorization (all phases) */
   double flops_model;  /* paper-model flops: per-tile chains of Equation 2 */
   double ara_rounds;   /* total ARA rounds of the last factorization (all columns) */
   double seconds;      /* host wall time of the last factorization call */
+  double flops_fp32;   /* FP32 flops of the sampling/projection chains (TLR_PREC_FP32) */
+  double tile_rounds_fp32, tile_rounds_fp64; /* ARA tile-rounds sampled in FP32 / FP64 (TLR_PREC_FP32) */
 } tlr_info;
 tlr_status tlr_get_info(const tlr_mat* M, tlr_info* info);
 

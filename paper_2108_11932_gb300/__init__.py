@@ -46,7 +46,8 @@ class Info(C.Structure):
     _fields_ = [("N", C.c_int64), ("b", C.c_int), ("nb", C.c_int), ("d", C.c_int), ("state", C.c_int),
                 ("k_fail", C.c_int), ("max_rank", C.c_int), ("mean_rank", C.c_double), ("bytes", C.c_int64),
                 ("flops_exec", C.c_double), ("flops_model", C.c_double), ("ara_rounds", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("flops_fp32", C.c_double), ("tile_rounds_fp32", C.c_double),
+                ("tile_rounds_fp64", C.c_double)]
 
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

@@ -129,6 +129,8 @@ struct tlr_mat {
   std::vector<int64_t> ulen;        // used columns of Urow[i]
   // statistics of the last factorization
   double flops_exec = 0, flops_model = 0, ara_rounds = 0, seconds = 0;
+  double tiles_fp32 = 0, tiles_fp64 = 0;  // tile-rounds sampled in each precision (mixed mode)
+  double flops_fp32 = 0;                  // FP32 flops of the mixed-precision chains
 };
 
 namespace tlr {
@@ -221,6 +223,13 @@ struct CopyJob {
   int64_t n;
 };
 void batched_copy(tlr_ctx* ctx, std::vector<CopyJob>& jobs);
+struct ConvJob {
+  const double* src;
+  float* dst;
+  int64_t n;
+};
+void batched_to_float(tlr_ctx* ctx, std::vector<ConvJob>& jobs);
+void col_sqnorms(tlr_ctx* ctx, const double* X, int rows, int64_t ncols, double* out);
 void scale_cols(tlr_ctx* ctx, int m, int n, const double* dvec, const double* X, int ldx, double* Y,
                 int ldy);
 void tril_mask(tlr_ctx* ctx, int n, double* A, int lda, int unit);

@@ -874,4 +874,41 @@ void axpy_matrix(tlr_ctx* ctx, int m, int n, double alpha, const double* X, int 
   TLR_LAUNCH_CHECK(ctx);
 }
 
+// Batched FP64 -> FP32 conversion of contiguous ranges (FP32 operands of the sampling chains).
+__global__ void k_batched_to_float(const ConvJob* __restrict__ jobs) {
+  const ConvJob J = jobs[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < J.n; e += (int64_t)gridDim.x * blockDim.x)
+    J.dst[e] = (float)J.src[e];
+}
+void batched_to_float(tlr_ctx* ctx, std::vector<ConvJob>& jobs) {
+  std::vector<ConvJob> nz;
+  int64_t mx = 0;
+  for (auto& j : jobs)
+    if (j.n > 0) { nz.push_back(j); mx = std::max(mx, j.n); }
+  for (size_t o = 0; o < nz.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
+    const ConvJob* dj = static_cast<const ConvJob*>(upload(ctx, nz.data() + o, cnt * sizeof(ConvJob)));
+    dim3 grid(std::min<unsigned>(cdiv(mx, 256), 64u), (unsigned)cnt);
+    k_batched_to_float<<<grid, 256, 0, ctx->stream>>>(dj);
+    TLR_LAUNCH_CHECK(ctx);
+  }
+}
+
+// Squared 2-norms of the columns of a column-major rows x ncols matrix (one warp per column).
+__global__ void k_col_sqnorms(const double* __restrict__ X, int rows, int64_t ncols, double* __restrict__ out) {
+  const int64_t c = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (c >= ncols) return;
+  const double* x = X + (size_t)c * rows;
+  double s = 0.0;
+  for (int r = lane; r < rows; r += 32) s = fma(x[r], x[r], s);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[c] = s;
+}
+void col_sqnorms(tlr_ctx* ctx, const double* X, int rows, int64_t ncols, double* out) {
+  if (ncols <= 0) return;
+  k_col_sqnorms<<<cdiv(ncols, 8), 256, 0, ctx->stream>>>(X, rows, ncols, out);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
 }  // namespace tlr

@@ -615,35 +615,59 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
 // ======================================================================== factorization
 namespace tlr {
 
-// Sampling chain of column k (Equation 2 / 3 regrouped with the Gram factors G_ij).
+// Sampling chain of column k (Equation 2 / 3 regrouped with the Gram factors G_ij),
+// evaluated in arithmetic T (double, or float for the mixed-precision path).  The
+// ARA engine works in FP64: Omega arrives in FP64 and Y leaves in FP64; with
+// T = float the chain's operands are FP32 copies of the panels and the products
+// accumulate in FP32.
+template <typename T>
 struct FactorSampler : Sampler {
   tlr_ctx* ctx;
   const tlr_mat* A;  // input (compressed) matrix
   tlr_mat* F;        // factor under construction (columns < k final)
+  const std::vector<T*>* FU;  // panels in arithmetic T (F->Urow, or FP32 copies)
+  const std::vector<T*>* AU;  // A->Urow in T
+  const std::vector<T*>* AV;  // A->Vcol in T
   int k, b, bs, Kk;
   const std::vector<int>* ops2i;  // operand -> tile row i
   BlkTables tb;
   const int64_t* goff_d;
   const int* gld_d;
-  const double* Gbuf;
-  double* X;         // Kk x bs
-  double* X0;        // R0_k x bs
+  const T* Gbuf;
+  T* X;              // Kk x bs
+  T* X0;             // R0_k x bs
   Buf* wsamp;        // W blocks
   Buf* pbuf;
   Buf* zbuf;
+  Buf* cbuf;         // FP32 staging (Omega, Y, Q, B) when T = float
   const double* Q;
   size_t qstride;
   double* Bcol;      // b x R_k (output of the projection, input of batchTrsm)
   std::vector<int64_t> boff;
+  const std::vector<char>* member = nullptr;  // project only these operands (null: all)
   double flops_exec = 0, flops_model = 0;
+  static constexpr bool F32 = sizeof(T) == 4;
+  bool mine(int op) const { return !member || (*member)[op]; }
 
-  void sample(const std::vector<int>& ops, int, const double* Om, double* Y) override {
+  const T* Uk(int i, int j) const { return (*FU)[i] + (size_t)b * F->uoff[ix(F, i, j)]; }
+  const T* U0(int i) const { return (*AU)[i] + (size_t)b * A->uoff[ix(A, i, k)]; }
+  const T* V0(int i) const { return (*AV)[k] + (size_t)b * A->voff[ix(A, i, k)]; }
+
+  void sample(const std::vector<int>& ops, int, const double* Om64, double* Y64) override {
+    const T* Om = reinterpret_cast<const T*>(Om64);
+    T* Y = reinterpret_cast<T*>(Y64);
+    if (F32) {
+      float* st = cbuf->need<float>((size_t)b * bs * (1 + ops.size()));
+      to_float(ctx, (int64_t)b * bs, Om64, st);
+      Om = reinterpret_cast<const T*>(st);
+      Y = reinterpret_cast<T*>(st + (size_t)b * bs);
+    }
     // shared per round: X = Urow_k^T Omega, X0 = V0col_k^T Omega
-    std::vector<GemmJob<double>> jx;
+    std::vector<GemmJob<T>> jx;
     const int64_t R0k = A->vlen[k];
-    if (Kk > 0) jx.push_back(job<double>(TN, Kk, bs, F->Urow[k], b, Om, b, b, X, Kk, 1.0, 0.0));
-    if (R0k > 0) jx.push_back(job<double>(TN, (int)R0k, bs, A->Vcol[k], b, Om, b, b, X0, (int)R0k, 1.0, 0.0));
-    gemm<double>(ctx, TN, jx);
+    if (Kk > 0) jx.push_back(job<T>(TN, Kk, bs, (*FU)[k], b, Om, b, b, X, Kk, 1.0, 0.0));
+    if (R0k > 0) jx.push_back(job<T>(TN, (int)R0k, bs, (*AV)[k], b, Om, b, b, X0, (int)R0k, 1.0, 0.0));
+    gemm<T>(ctx, TN, jx);
     flops_exec += 2.0 * b * bs * (Kk + R0k);
     std::vector<SlotDesc> sd(ops.size());
     int64_t wtot = 0;
@@ -658,17 +682,17 @@ struct FactorSampler : Sampler {
       sd[s].q = bs;
       wtot += (int64_t)(sd[s].r0 + sd[s].Ki) * bs;
     }
-    double* W = wsamp->need<double>((size_t)wtot);
+    T* W = wsamp->need<T>((size_t)wtot);
     const SlotDesc* sdd = static_cast<const SlotDesc*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDesc)));
-    blkdiag_sample<double>(ctx, tb, (int)ops.size(), sdd, goff_d, gld_d, Gbuf, X, std::max(Kk, 1), X0,
-                           (int)std::max<int64_t>(R0k, 1), bs, W);
-    std::vector<GemmJob<double>> jy;
+    blkdiag_sample<T>(ctx, tb, (int)ops.size(), sdd, goff_d, gld_d, Gbuf, X, std::max(Kk, 1), X0,
+                      (int)std::max<int64_t>(R0k, 1), bs, W);
+    std::vector<GemmJob<T>> jy;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int i = sd[s].i, r0 = sd[s].r0, Ki = sd[s].Ki;
       const int ldw = std::max(r0 + Ki, 1);
-      GemmJob<double> g = job<double>(NN, b, bs, r0 ? Uptr(A, i, k) : nullptr, b, W + sd[s].woff, ldw, r0,
-                                      Y + s * (size_t)b * bs, b, 1.0, 0.0);
-      g.A[1] = F->Urow[i];
+      GemmJob<T> g = job<T>(NN, b, bs, r0 ? U0(i) : nullptr, b, W + sd[s].woff, ldw, r0, Y + s * (size_t)b * bs, b,
+                            1.0, 0.0);
+      g.A[1] = (*FU)[i];
       g.lda[1] = b;
       g.B[1] = W + sd[s].woff + r0;
       g.ldb[1] = ldw;
@@ -680,7 +704,8 @@ struct FactorSampler : Sampler {
       for (int j = 0; j < k; ++j) R += F->rank[ix(F, i, j)] + F->rank[ix(F, k, j)];
       flops_model += 4.0 * b * bs * R;
     }
-    gemm<double>(ctx, NN, jy);
+    gemm<T>(ctx, NN, jy);
+    if (F32) to_double(ctx, (int64_t)b * bs * ops.size(), reinterpret_cast<const float*>(Y), Y64);
   }
 
   void project(const std::vector<int>& q) override {
@@ -702,32 +727,47 @@ struct FactorSampler : Sampler {
       boff[op] = btot;
       btot += q[op];
     }
-    double* P = pbuf->need<double>((size_t)std::max<int64_t>(ptot, 1));
-    double* Z = zbuf->need<double>((size_t)std::max<int64_t>(ztot, 1));
-    std::vector<GemmJob<double>> jp;
+    T* P = pbuf->need<T>((size_t)std::max<int64_t>(ptot, 1));
+    T* Z = zbuf->need<T>((size_t)std::max<int64_t>(ztot, 1));
+    // Q_i (and the output B) in arithmetic T
+    const T* Qt = reinterpret_cast<const T*>(Q);
+    size_t qs = qstride;
+    T* Bt = reinterpret_cast<T*>(Bcol);
+    if (F32) {
+      float* st = cbuf->need<float>((size_t)2 * b * std::max<int64_t>(btot, 1));
+      std::vector<ConvJob> cj;
+      for (int op = 0; op < nops; ++op)
+        if (mine(op)) cj.push_back(ConvJob{Q + op * qstride, st + (size_t)boff[op] * b, (int64_t)q[op] * b});
+      batched_to_float(ctx, cj);
+      Qt = reinterpret_cast<const T*>(st);
+      qs = 0;  // per-op offsets come from boff below
+      Bt = reinterpret_cast<T*>(st + (size_t)b * std::max<int64_t>(btot, 1));
+    }
+    auto Qop = [&](int op) -> const T* {
+      return F32 ? Qt + (size_t)boff[op] * b : Qt + op * qs;
+    };
+    std::vector<GemmJob<T>> jp;
     for (int op = 0; op < nops; ++op) {
-      if (q[op] == 0) continue;
+      if (q[op] == 0 || !mine(op)) continue;
       const int i = sd[op].i, r0 = sd[op].r0, Ki = sd[op].Ki;
       const int ldp = r0 + Ki;
-      const double* Qo = Q + op * qstride;
-      if (r0 > 0) jp.push_back(job<double>(TN, r0, q[op], Uptr(A, i, k), b, Qo, b, b, P + sd[op].poff, ldp, 1.0, 0.0));
-      if (Ki > 0)
-        jp.push_back(job<double>(TN, Ki, q[op], F->Urow[i], b, Qo, b, b, P + sd[op].poff + r0, ldp, 1.0, 0.0));
+      if (r0 > 0) jp.push_back(job<T>(TN, r0, q[op], U0(i), b, Qop(op), b, b, P + sd[op].poff, ldp, 1.0, 0.0));
+      if (Ki > 0) jp.push_back(job<T>(TN, Ki, q[op], (*FU)[i], b, Qop(op), b, b, P + sd[op].poff + r0, ldp, 1.0, 0.0));
       flops_exec += 2.0 * b * q[op] * (r0 + Ki);
     }
-    gemm<double>(ctx, TN, jp);
+    gemm<T>(ctx, TN, jp);
     const SlotDesc* sdd = static_cast<const SlotDesc*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDesc)));
     int qmax = 0;
     for (int v : q) qmax = std::max(qmax, v);
-    blkdiag_project<double>(ctx, tb, nops, sdd, goff_d, gld_d, Gbuf, P, Z, Kk, qmax);
-    std::vector<GemmJob<double>> jb;
+    blkdiag_project<T>(ctx, tb, nops, sdd, goff_d, gld_d, Gbuf, P, Z, Kk, qmax);
+    std::vector<GemmJob<T>> jb;
     for (int op = 0; op < nops; ++op) {
-      if (q[op] == 0) continue;
+      if (q[op] == 0 || !mine(op)) continue;
       const int i = sd[op].i, r0 = sd[op].r0;
       const int ldz = r0 + Kk;
-      GemmJob<double> g = job<double>(NN, b, q[op], r0 ? Vptr(A, i, k) : nullptr, b, Z + sd[op].woff,
-                                      std::max(ldz, 1), r0, Bcol + (size_t)boff[op] * b, b, 1.0, 0.0);
-      g.A[1] = F->Urow[k];
+      GemmJob<T> g = job<T>(NN, b, q[op], r0 ? V0(i) : nullptr, b, Z + sd[op].woff, std::max(ldz, 1), r0,
+                            Bt + (size_t)boff[op] * b, b, 1.0, 0.0);
+      g.A[1] = (*FU)[k];
       g.lda[1] = b;
       g.B[1] = Z + sd[op].woff + r0;
       g.ldb[1] = std::max(ldz, 1);
@@ -738,7 +778,55 @@ struct FactorSampler : Sampler {
       for (int j = 0; j < k; ++j) R += F->rank[ix(F, i, j)] + F->rank[ix(F, k, j)];
       flops_model += 4.0 * b * q[op] * R;
     }
-    gemm<double>(ctx, NN, jb);
+    gemm<T>(ctx, NN, jb);
+    if (F32) {
+      if (!member) {
+        to_double(ctx, (int64_t)b * btot, reinterpret_cast<const float*>(Bt), Bcol);
+      } else {
+        for (int op = 0; op < nops; ++op)
+          if (mine(op) && q[op])
+            to_double(ctx, (int64_t)b * q[op], reinterpret_cast<const float*>(Bt) + (size_t)boff[op] * b,
+                      Bcol + (size_t)boff[op] * b);
+      }
+    }
+  }
+};
+
+// Per-tile precision rule: within one round, tiles whose estimated FP32 rounding
+// error is far below the ARA threshold sample in FP32, the others in FP64.
+struct MixedSampler : Sampler {
+  tlr_ctx* ctx;
+  int b, bs;
+  FactorSampler<double>* f64;
+  FactorSampler<float>* f32;
+  std::vector<char> is32, is64;
+  Buf* tmp;
+  int64_t ops32 = 0, ops64 = 0;
+  void sample(const std::vector<int>& ops, int t, const double* Om, double* Y) override {
+    std::vector<int> o32, o64, s32, s64;
+    for (size_t s = 0; s < ops.size(); ++s) {
+      if (is32[ops[s]]) { o32.push_back(ops[s]); s32.push_back((int)s); }
+      else { o64.push_back(ops[s]); s64.push_back((int)s); }
+    }
+    ops32 += (int64_t)o32.size();
+    ops64 += (int64_t)o64.size();
+    if (o64.empty()) { f32->sample(ops, t, Om, Y); return; }
+    if (o32.empty()) { f64->sample(ops, t, Om, Y); return; }
+    double* T = tmp->need<double>((size_t)b * bs * ops.size());
+    f32->sample(o32, t, Om, T);
+    f64->sample(o64, t, Om, T + (size_t)b * bs * o32.size());
+    std::vector<CopyJob> cj;
+    for (size_t u = 0; u < o32.size(); ++u)
+      cj.push_back(CopyJob{T + u * (size_t)b * bs, Y + (size_t)s32[u] * b * bs, (int64_t)b * bs});
+    for (size_t u = 0; u < o64.size(); ++u)
+      cj.push_back(CopyJob{T + (o32.size() + u) * (size_t)b * bs, Y + (size_t)s64[u] * b * bs, (int64_t)b * bs});
+    batched_copy(ctx, cj);
+  }
+  void project(const std::vector<int>& q) override {
+    f32->member = &is32;
+    f64->member = &is64;
+    f32->project(q);
+    f64->project(q);
   }
 };
 
@@ -778,9 +866,56 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
   double* Q = bQ.need<double>((size_t)std::max(nb - 1, 1) * qstride);
   int* info = bInfo.need<int>(2);
   bTmp.need<double>((size_t)b * NBK);  // sized once: the side stream never reallocates it
-  double fl_exec = 0, fl_model = 0;
+  double fl_exec = 0, fl_model = 0, fl_exec32 = 0;
   int64_t rounds = 0;
   std::vector<int> rtab((size_t)nb * nb * 3);
+  // Mixed precision (precision policy): the sampling / projection chains run in FP32
+  // on FP32 copies of the panels when eps >= 1e-4; everything else stays FP64.
+  const bool mixed = o->precision == TLR_PREC_FP32 && eps >= 1e-4;
+  std::vector<float*> AU32(nb, nullptr), AV32(nb, nullptr), FU32(nb, nullptr), FV32(nb, nullptr);
+  std::vector<int64_t> fu32cap(nb, 0);
+  Buf bG32(ctx), bX32(ctx), bX032(ctx), bDV32(ctx), bC32(ctx);
+  auto f32_alloc = [&](int64_t n) { return static_cast<float*>(dalloc(ctx, sizeof(float) * (size_t)std::max<int64_t>(n, 1))); };
+  if (mixed) {
+    std::vector<ConvJob> cj;
+    for (int i = 0; i < nb; ++i) {
+      AU32[i] = f32_alloc((int64_t)b * A->ulen[i]);
+      AV32[i] = f32_alloc((int64_t)b * A->vlen[i]);
+      cj.push_back(ConvJob{A->Urow[i], AU32[i], (int64_t)b * A->ulen[i]});
+      cj.push_back(ConvJob{A->Vcol[i], AV32[i], (int64_t)b * A->vlen[i]});
+      fu32cap[i] = F->ucap[i];
+      FU32[i] = f32_alloc((int64_t)b * fu32cap[i]);
+    }
+    batched_to_float(ctx, cj);
+  }
+  // Frobenius norms of the tiles (|A_ik|_F = |V0_ik|_F and |L_ij|_F = |V_ij|_F, U orthonormal)
+  std::vector<double> nA((size_t)nb * nb, 0.0), nL((size_t)nb * nb, 0.0);
+  Buf bNrm(ctx), bMix(ctx);
+  int64_t tiles32 = 0, tiles64 = 0;
+  auto panel_tile_norms = [&](const tlr_mat* M, int j, std::vector<double>& out) {
+    const int64_t n = M->vlen[j];
+    if (n == 0) return;
+    double* d = bNrm.need<double>((size_t)n);
+    col_sqnorms(ctx, M->Vcol[j], b, n, d);
+    std::vector<double> h(n);
+    TLR_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int i = j + 1; i < nb; ++i) {
+      double sq = 0;
+      for (int c = 0; c < M->rank[ix(M, i, j)]; ++c) sq += h[M->voff[ix(M, i, j)] + c];
+      out[ix(M, i, j)] = std::sqrt(sq);
+    }
+  };
+  if (mixed)
+    for (int j = 0; j < nb; ++j) panel_tile_norms(A, j, nA);
+  struct F32Guard {  // frees the FP32 copies on every exit path
+    tlr_ctx* c;
+    std::vector<float*>* v[4];
+    ~F32Guard() {
+      for (auto* vv : v)
+        for (float* p : *vv) dfree(c, p);
+    }
+  } f32guard{ctx, {&AU32, &AV32, &FU32, &FV32}};
 
   for (int k = 0; k < nb; ++k) {
     const int Kk = (int)F->ulen[k];
@@ -795,26 +930,40 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
       gtot += (int64_t)gld[j] * F->rank[ix(F, k, j)];
     }
     double* G = bG.need<double>((size_t)std::max<int64_t>(gtot, 1));
+    float* G32 = mixed ? bG32.need<float>((size_t)std::max<int64_t>(gtot, 1)) : nullptr;
     {
       std::vector<GemmJob<double>> jg;
+      std::vector<GemmJob<float>> jg32;
+      std::vector<ConvJob> cdv;
       int64_t dvtot = 0;
       for (int j = 0; j < k; ++j) dvtot += (int64_t)b * F->rank[ix(F, k, j)];
       double* DV = ldl ? bDV.need<double>((size_t)std::max<int64_t>(dvtot, 1)) : nullptr;
+      float* DV32 = (ldl && mixed) ? bDV32.need<float>((size_t)std::max<int64_t>(dvtot, 1)) : nullptr;
       int64_t dvo = 0;
       for (int j = 0; j < k; ++j) {
         const int rkj = F->rank[ix(F, k, j)];
         if (rkj == 0) continue;
         const int S = (int)(F->vlen[j] - F->voff[ix(F, k, j)]);
         const double* Vkj = Vptr(F, k, j);
+        const float* Vkj32 = mixed ? FV32[j] + (size_t)b * F->voff[ix(F, k, j)] : nullptr;
         if (ldl) {  // D_j V_kj (Equation 3: D(j,j) inside the chain)
           scale_rows(ctx, b, rkj, F->dvec + (size_t)j * b, 0, Vkj, b, DV + dvo, b);
           Vkj = DV + dvo;
+          if (mixed) {
+            cdv.push_back(ConvJob{DV + dvo, DV32 + dvo, (int64_t)b * rkj});
+            Vkj32 = DV32 + dvo;
+          }
           dvo += (int64_t)b * rkj;
         }
         jg.push_back(job<double>(TN, S, rkj, Vptr(F, k, j), b, Vkj, b, b, G + goff[j], gld[j], 1.0, 0.0));
         fl_exec += 2.0 * b * S * rkj;
+        if (mixed)  // FP32 Gram for the tiles that sample in FP32
+          jg32.push_back(job<float>(TN, S, rkj, FV32[j] + (size_t)b * F->voff[ix(F, k, j)], b, Vkj32, b, b,
+                                    G32 + goff[j], gld[j], 1.0, 0.0));
       }
+      if (!cdv.empty()) batched_to_float(ctx, cdv);
       gemm<double>(ctx, TN, jg);
+      gemm<float>(ctx, TN, jg32);
     }
     // The diagonal tile (updateDense, compensation, chol) is not read by the ARA of
     // column k, only by its batchTrsm: it runs on the side stream, overlapped with
@@ -926,21 +1075,48 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     TLR_CUDA(cudaMemcpyAsync(dgoff, goff.data(), sizeof(int64_t) * std::max(k, 1), cudaMemcpyHostToDevice, ctx->stream));
     TLR_CUDA(cudaMemcpyAsync(dgld, gld.data(), sizeof(int) * std::max(k, 1), cudaMemcpyHostToDevice, ctx->stream));
     TLR_CUDA(cudaStreamSynchronize(ctx->stream));  // rtab / goff / gld are pageable
-    FactorSampler fs;
-    fs.ctx = ctx; fs.A = A; fs.F = F; fs.k = k; fs.b = b; fs.bs = bs; fs.Kk = Kk; fs.ops2i = &ops2i;
-    fs.tb = BlkTables{dtab, dtab + (size_t)nb * nb, dtab + (size_t)2 * nb * nb, nb, k};
-    fs.goff_d = dgoff; fs.gld_d = dgld; fs.Gbuf = G;
-    fs.X = bX.need<double>((size_t)std::max(Kk, 1) * bs);
-    fs.X0 = bX0.need<double>((size_t)std::max<int64_t>(A->vlen[k], 1) * bs);
-    fs.wsamp = &bW; fs.pbuf = &bP; fs.zbuf = &bZ;
-    fs.Q = Q; fs.qstride = qstride;
+    FactorSampler<double> fs;
+    FactorSampler<float> fs32;
+    auto setup = [&](auto& f, auto* X, auto* X0, const void* Gb, auto* FUv, auto* AUv, auto* AVv) {
+      f.ctx = ctx; f.A = A; f.F = F; f.k = k; f.b = b; f.bs = bs; f.Kk = Kk; f.ops2i = &ops2i;
+      f.tb = BlkTables{dtab, dtab + (size_t)nb * nb, dtab + (size_t)2 * nb * nb, nb, k};
+      f.goff_d = dgoff; f.gld_d = dgld;
+      f.Gbuf = static_cast<decltype(f.Gbuf)>(Gb);
+      f.X = X; f.X0 = X0;
+      f.FU = FUv; f.AU = AUv; f.AV = AVv;
+      f.wsamp = &bW; f.pbuf = &bP; f.zbuf = &bZ; f.cbuf = &bC32;
+      f.Q = Q; f.qstride = qstride;
+    };
+    setup(fs, bX.need<double>((size_t)std::max(Kk, 1) * bs),
+          bX0.need<double>((size_t)std::max<int64_t>(A->vlen[k], 1) * bs), G, &F->Urow, &A->Urow, &A->Vcol);
+    MixedSampler ms;
+    Sampler* smp = &fs;
+    if (mixed) {
+      setup(fs32, bX32.need<float>((size_t)std::max(Kk, 1) * bs),
+            bX032.need<float>((size_t)std::max<int64_t>(A->vlen[k], 1) * bs), G32, &FU32, &AU32, &AV32);
+      // estimated FP32 rounding error of tile i's chain: u32 sqrt(K) (|A_ik|_F + sum_j |L_ij|_F |L_kj|_F)
+      const double thr = eps / HALKO;
+      ms.ctx = ctx; ms.b = b; ms.bs = bs; ms.f64 = &fs; ms.f32 = &fs32; ms.tmp = &bMix;
+      ms.is32.assign(nops, 0);
+      ms.is64.assign(nops, 1);
+      for (int op = 0; op < nops; ++op) {
+        const int i = ops2i[op];
+        double sum = nA[ix(A, i, k)];
+        for (int j = 0; j < k; ++j) sum += nL[ix(F, i, j)] * nL[ix(F, k, j)];
+        const double K = (double)A->rank[ix(A, i, k)] + (double)F->ulen[i] + bs;
+        const bool ok = 6e-8 * std::sqrt(K) * sum <= thr / 8.0;
+        ms.is32[op] = ok;
+        ms.is64[op] = !ok;
+      }
+      smp = &ms;
+    }
     // Bcol is allocated after ARA (R_k known) -> run ARA with a deferred projection
     struct Deferred : Sampler {
-      FactorSampler* f;
+      Sampler* f;
       void sample(const std::vector<int>& ops, int t, const double* Om, double* Y) override { f->sample(ops, t, Om, Y); }
       void project(const std::vector<int>&) override {}
     } dsmp;
-    dsmp.f = &fs;
+    dsmp.f = smp;
     AraConfig cf{b, bs, eps, o->seed, STREAM_FACTOR, (uint32_t)k, o->max_slots};
     std::vector<int> q;
     AraStats as;
@@ -953,6 +1129,7 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     F->vlen[k] = Rk;
     double* Bcol = bBc.need<double>((size_t)std::max<int64_t>(Rk, 1) * b);
     fs.Bcol = Bcol;
+    fs32.Bcol = Bcol;
     prof_mark(ctx, PH_POTRF);  // waiting for the diagonal tile of this column
     if (!check_tile()) {
       mat_destroy(ctx, F);
@@ -961,9 +1138,12 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
       return TLR_ERR_NOT_SPD;
     }
     prof_mark(ctx, PH_PROJECT);
-    fs.project(q);
+    smp->project(q);
+    const std::vector<int64_t>& boff = fs.boff;
     fl_exec += fs.flops_exec;
-    fl_model += fs.flops_model;
+    if (mixed) fl_exec32 += fs32.flops_exec;
+    fl_model += fs.flops_model + (mixed ? fs32.flops_model : 0.0);
+    if (mixed) { tiles32 += ms.ops32; tiles64 += ms.ops64; }
     // ---- batchTrsm: V_ik = L_kk^{-1} B_i (LDL^T: then D_k^{-1}, batchIDMult)
     prof_mark(ctx, PH_TRSM);
     if (Rk > 0) {
@@ -977,16 +1157,36 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
     // ---- updateTiles: U_ik = Q_i appended to block row i; V_ik in block column k
     prof_mark(ctx, PH_UPDATE);
     std::vector<CopyJob> cj;
+    std::vector<ConvJob> c32;
     for (int op = 0; op < nops; ++op) {
       const int i = ops2i[op];
       ensure_ucap(ctx, F, i, q[op]);
       F->rank[ix(F, i, k)] = q[op];
       F->uoff[ix(F, i, k)] = F->ulen[i];
-      F->voff[ix(F, i, k)] = fs.boff[op];
+      F->voff[ix(F, i, k)] = boff[op];
       cj.push_back(CopyJob{Q + op * qstride, F->Urow[i] + (size_t)F->ulen[i] * b, (int64_t)q[op] * b});
+      if (mixed) {
+        if (F->ulen[i] + q[op] > fu32cap[i]) {  // grow the FP32 copy of block row i
+          const int64_t cap = std::max<int64_t>(F->ucap[i], F->ulen[i] + q[op]);
+          float* p = f32_alloc((int64_t)b * cap);
+          if (F->ulen[i] > 0)
+            TLR_CUDA(cudaMemcpyAsync(p, FU32[i], sizeof(float) * (size_t)b * F->ulen[i], cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+          dfree(ctx, FU32[i]);
+          FU32[i] = p;
+          fu32cap[i] = cap;
+        }
+        c32.push_back(ConvJob{Q + op * qstride, FU32[i] + (size_t)F->ulen[i] * b, (int64_t)q[op] * b});
+      }
       F->ulen[i] += q[op];
     }
     batched_copy(ctx, cj);
+    if (mixed) {
+      FV32[k] = f32_alloc((int64_t)b * Rk);
+      c32.push_back(ConvJob{F->Vcol[k], FV32[k], (int64_t)b * Rk});
+      batched_to_float(ctx, c32);
+      panel_tile_norms(F, k, nL);
+    }
   }
   prof_flush(ctx);
   TLR_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -1009,6 +1209,9 @@ static tlr_status factor_impl(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_op
   A->flops_exec = fl_exec;
   A->flops_model = fl_model;
   A->ara_rounds = (double)rounds;
+  A->tiles_fp32 = (double)tiles32;
+  A->flops_fp32 = fl_exec32;
+  A->tiles_fp64 = (double)tiles64;
   A->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   return TLR_OK;
 }
@@ -1322,7 +1525,7 @@ static tlr_status factor_abi(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opt
   if (!ctx || !A || !(eps > 0)) return TLR_ERR_ARG;
   if (A->state != 0) return TLR_ERR_STATE;
   tlr_opts o = opts_or_default(opts);
-  if (o.bs > 64 || o.bs > A->b || o.precision != TLR_PREC_FP64) return TLR_ERR_ARG;
+  if (o.bs > 64 || o.bs > A->b || (o.precision != TLR_PREC_FP64 && o.precision != TLR_PREC_FP32)) return TLR_ERR_ARG;
   ABI_BEGIN
   return factor_impl(ctx, A, eps, &o, ldl);
   ABI_END
@@ -1429,6 +1632,9 @@ tlr_status tlr_get_info(const tlr_mat* M, tlr_info* info) {
   info->flops_model = M->flops_model;
   info->ara_rounds = M->ara_rounds;
   info->seconds = M->seconds;
+  info->flops_fp32 = M->flops_fp32;
+  info->tile_rounds_fp32 = M->tiles_fp32;
+  info->tile_rounds_fp64 = M->tiles_fp64;
   return TLR_OK;
 }
 

@@ -319,3 +319,42 @@ def test_acceptance_cov2d_4k_against_svd_oracle(T, ctx, ldl):
     assert res_g <= 2 * res_o, (res_g, res_o)
     ld_o = tlr.logdet(Fo)
     assert abs(F.logdet()[0] - ld_o) <= 1e-3 * abs(ld_o)
+
+
+# ------------------------------------------------------------------ mixed precision (FP32 sampling chains)
+@pytest.mark.parametrize("eps,ldl", [(1e-2, False), (1e-4, False), (1e-4, True)])
+def test_mixed_precision_meets_acceptance(T, ctx, eps, ldl):
+    """FP32 sampling/projection (FP64 orthogonalization, potrf, trsm) meets the same acceptance rule."""
+    w = inputs.WORKLOADS["cov2d_4k"]
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=0))
+    F32 = A.copy()
+    (F32.ldlt if ldl else F32.potrf)(eps, T.default_opts(bs=w["bs"], seed=0, precision=T.PREC_FP32))
+    F64 = A.copy()
+    (F64.ldlt if ldl else F64.potrf)(eps, T.default_opts(bs=w["bs"], seed=0))
+    Ao = tlr.build(x, w["b"], eps, w["ell"], w["nugget"])
+    Fo = tlr.factor(Ao, eps, ldl=ldl)
+    Ad = kernel.dense(x, w["ell"], w["nugget"])
+    v0 = inputs.start_vector(w["N"])
+    be_o = measures.backward_error(lambda v: Ad @ v, lambda v: tlr.matvec(Fo, v, "LLt")[:, 0], v0)
+    be_32 = _gpu_backward_error(T, ctx, F32, x, w["ell"], w["nugget"])
+    assert be_32 <= max(2 * be_o, 10 * eps), (be_32, be_o)
+    Y = inputs.rhs(w["N"], 2, 5)
+    Yt = _t(T, Y)
+    F32.solve(Yt)
+    res_32 = measures.residual(lambda Z: Ad @ Z, Yt.cpu().numpy(), Y)
+    res_o = measures.residual(lambda Z: Ad @ Z, tlr.solve(Fo, Y), Y)
+    assert res_32 <= 2 * res_o, (res_32, res_o)
+    # error of the mixed path against the FP64 path on the same input (stated, bounded)
+    ld32, ld64 = F32.logdet()[0], F64.logdet()[0]
+    assert abs(ld32 - ld64) <= 1e-3 * abs(ld64)
+
+
+def test_mixed_precision_falls_back_to_fp64_below_1e4(T, ctx):
+    w = CASES["cov2d_2k"]
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    A = ctx.compress(x, w["b"], w["eps"], w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=7))
+    F32 = A.copy().potrf(w["eps"], T.default_opts(bs=w["bs"], seed=7, precision=T.PREC_FP32))
+    F64 = A.copy().potrf(w["eps"], T.default_opts(bs=w["bs"], seed=7))
+    assert np.array_equal(F32.ranks(), F64.ranks())
+    assert F32.logdet()[0] == F64.logdet()[0]
