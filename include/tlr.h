@@ -130,6 +130,18 @@ tlr_status tlr_potrf(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts)
  * tiles.  TLR_ERR_NOT_SPD if a pivot of D is exactly zero or not finite. */
 tlr_status tlr_ldlt(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts);
 
+/* Batched factorization of `count` independent matrices (Cholesky if ldl == 0,
+ * else LDL^T), each in place as with tlr_potrf / tlr_ldlt.  The matrices advance
+ * column by column together and every step of every matrix shares the same
+ * launches (one dynamic ARA batch per column step for all matrices; sizes,
+ * thresholds and options may differ per matrix).  Each matrix draws its own
+ * Gaussian blocks (its opts.seed), so its result does not depend on the batch.
+ * eps[m] and opts[m] (opts may be NULL for defaults) per matrix; status[m]
+ * (host) receives each matrix's outcome (TLR_ERR_NOT_SPD leaves it FAILED).
+ * Returns TLR_OK unless the call itself failed. */
+tlr_status tlr_factor_batch(tlr_ctx* ctx, int count, tlr_mat** A, const double* eps, const tlr_opts* opts,
+                            int ldl, tlr_status* status);
+
 /* Solve (L L^T) X = B or (L D L^T) X = B with the TLR triangular solve of
  * Algorithm 7 (forward) and its transpose (backward).  B: device, N x nrhs,
  * leading dimension ldb >= N, original point order; overwritten with X. */

@@ -79,6 +79,7 @@ def _load():
         "tlr_compress_ordered": (C.c_int, [P, P, P, C.c_int64, C.c_int, C.POINTER(Kernel), C.c_int, C.c_double,
                                            C.POINTER(Opts), C.POINTER(P)]),
         "tlr_gemm_stats": (C.c_int, [P, C.c_int, D, D, C.POINTER(C.c_int64)]),
+        "tlr_factor_batch": (C.c_int, [P, C.c_int, C.POINTER(P), D, C.POINTER(Opts), C.c_int, C.POINTER(C.c_int)]),
         "tlr_potrf": (C.c_int, [P, P, C.c_double, C.POINTER(Opts)]),
         "tlr_ldlt": (C.c_int, [P, P, C.c_double, C.POINTER(Opts)]),
         "tlr_solve": (C.c_int, [P, P, C.c_int, P, C.c_int64]),
@@ -224,6 +225,20 @@ class Context:
                                             C.byref(k), b, eps, C.byref(opts) if opts else None, C.byref(m)),
                "tlr_compress_ordered")
         return Matrix(self, m)
+
+    def factor_batch(self, mats: list, eps, opts=None, ldl: bool = False) -> list:
+        """Factor several matrices together (one dynamic batch per column step); returns statuses."""
+        n = len(mats)
+        hs = (P * n)(*[m.h for m in mats])
+        ev = (C.c_double * n)(*([eps] * n if np.isscalar(eps) else list(eps)))
+        if opts is None:
+            op = None
+        else:
+            ol = [opts] * n if isinstance(opts, Opts) else list(opts)
+            op = (Opts * n)(*ol)
+        st = (C.c_int * n)()
+        _check(_load().tlr_factor_batch(self.h, n, hs, ev, op, int(ldl), st), "tlr_factor_batch")
+        return [st[i] for i in range(n)]
 
     GEMM_FAMILIES = ["fp64_NN", "fp64_TN", "fp64_NT", "fp32_NN", "fp32_TN", "fp32_NT"]
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -165,9 +166,30 @@ void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t,
 void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget, int b,
                const int* tile_ij /*device, 2 per tile*/, int ntiles, double* out);
 // per-slot orthogonalization helpers (Cholesky-QR with dropping)
+// thr: device array, per-slot convergence threshold
 void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mout, int* status,
-                  double* enorm, double thr, double tau, int first_pass, const int* nk_in);
-// dense diagonal-tile factorization pieces
+                  double* enorm, const double* thr, double tau, int first_pass, const int* nk_in);
+// dense diagonal-tile factorization pieces (batched over tiles; the single-tile forms wrap them)
+struct PotrfJob {
+  double* A;
+  double* dvec;  // LDL^T: D of the whole tile (entries col0.. written)
+  int* info;
+  int lda, col0, nbk;
+};
+struct PanelJob {
+  const double* L;
+  double* X;
+  const double* dvec;  // LDL^T: D of this block
+  int lda, ldx, m, nbk;
+};
+struct LeftJob {
+  const double* L;
+  double* X;
+  int lda, ldx, nrhs, nbk;
+};
+void potrf_blocks(tlr_ctx* ctx, std::vector<PotrfJob>& jobs, int ldl);
+void trsm_panels(tlr_ctx* ctx, std::vector<PanelJob>& jobs, int ldl);
+void trsm_lefts(tlr_ctx* ctx, std::vector<LeftJob>& jobs, int unit, int trans);
 void potrf_diag_block(tlr_ctx* ctx, int nbk, double* A, int lda, int ldl, double* dvec, int* info,
                       int col0);
 void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, double* X, int ldx,
@@ -191,29 +213,52 @@ void to_float(tlr_ctx* ctx, int64_t n, const double* x, float* y);
 void to_double(tlr_ctx* ctx, int64_t n, const float* x, double* y);
 
 // blocked chains of the sampling (k_misc.cu): see the definitions for layouts.
-struct BlkTables {
-  const int* rank;   // nb*nb
-  const int* uoff;   // nb*nb
-  const int* voff;   // nb*nb
-  int nb, k;
-};
-struct SlotDesc {
-  int i;       // tile row
-  int r0;      // rank of A(i,k)
-  int x0off;   // row offset of tile i's block in the X0 buffer
-  int Ki;      // columns of Urow_i used (sum_{j<k} r_ij)
-  int64_t woff;  // element offset of this slot's W / Z block
-  int64_t poff;  // element offset of this slot's P block (projection)
-  int q;       // basis width (projection)
+template <typename T>
+struct SlotDescT {
+  const int* rank;   // the slot's matrix: ranks, U / V column offsets (nb x nb, device)
+  const int* uoff;
+  const int* voff;
+  const int64_t* goff;  // Gram blocks of the matrix's current column
+  const int* gld;
+  const T* G;
+  const T* X;        // sample: X = Urow_k^T Omega (Kk x bs), X0 = V0col_k^T Omega
+  const T* X0;
+  T* W;              // sample output block ((r0 + Ki) x bs)
+  T* P;              // project: P block ((r0 + Ki) x q) and output Z ((r0 + Kk) x q)
+  T* Z;
+  int ldx, ldx0, nb, k, i, r0, x0off, Ki, Kk, q, bs;
 };
 template <typename T>
-void blkdiag_sample(tlr_ctx* ctx, const BlkTables& tb, int nslots, const SlotDesc* slots_dev,
-                    const int64_t* goff_dev, const int* gld_dev, const T* G, const T* X,
-                    int ldx, const T* X0, int ldx0, int bs, T* W);
+void blkdiag_sample(tlr_ctx* ctx, int nslots, int kmax, const SlotDescT<T>* slots_dev);
 template <typename T>
-void blkdiag_project(tlr_ctx* ctx, const BlkTables& tb, int nslots, const SlotDesc* slots_dev,
-                     const int64_t* goff_dev, const int* gld_dev, const T* G, const T* P, T* Z,
-                     int Kk, int qmax);
+void blkdiag_project(tlr_ctx* ctx, int nslots, int kmax, const SlotDescT<T>* slots_dev);
+
+struct OmegaJob {
+  double* out;
+  uint64_t seed;
+  uint32_t stream, k, t;
+  int b, bs;
+};
+void omega_batched(tlr_ctx* ctx, std::vector<OmegaJob>& jobs);
+struct ConvBackJob {
+  const float* src;
+  double* dst;
+  int64_t n;
+};
+void batched_to_double(tlr_ctx* ctx, std::vector<ConvBackJob>& jobs);
+struct ScaleJob {
+  const double* d;
+  const double* X;
+  double* Y;
+  int m, n, ldx, ldy, inv;
+};
+void batched_scale_rows(tlr_ctx* ctx, std::vector<ScaleJob>& jobs);
+struct DiagJob {
+  double* A;
+  int n, lda;
+  double s;
+};
+void batched_add_diag(tlr_ctx* ctx, std::vector<DiagJob>& jobs);
 
 double fp64_peak(tlr_ctx* ctx);
 

@@ -1,0 +1,855 @@
+// Left-looking TLR Cholesky (Algorithm 6) and LDL^T (Algorithm 10) over a batch of
+// independent matrices.
+//
+// All matrices advance column by column together.  At column k every phase of
+// every matrix goes into the same launches:
+//   1. Gram factors G_ij = V_ij^T [D_j] V_kj of the column (one batched GEMM),
+//   2. on a side stream, overlapped with 3: updateDense D_k = sum_j U_kj G_kj U_kj^T,
+//      the dense potrf / LDL^T of A_kk and its inverse (batched over the matrices),
+//   3. cholARAUpdate (Algorithm 5): one dynamic ARA batch holding the tiles of every
+//      matrix, each round sampling the chains of Equation 2 / 3 (Gram-regrouped),
+//   4. the projection (sampleLeftT), batchTrsm as a product with L_kk^{-1}, updateTiles.
+// A single matrix is the batch of one.  Each matrix draws its own Gaussian blocks
+// (keyed by its seed), and every reduction has a fixed order, so a matrix's result
+// does not depend on the other matrices of the batch.
+#include <chrono>
+#include <memory>
+#include <numeric>
+
+#include "internal.h"
+
+namespace tlr {
+
+namespace {
+
+constexpr double U32 = 5.96e-8;  // FP32 unit roundoff, 2^-24
+
+struct Mat {
+  explicit Mat(tlr_ctx* c) : G(c), G32(c), E(c), DV(c), DV32(c), Bc(c) {}
+  tlr_mat* A = nullptr;  // input, then (on success) the factor
+  tlr_mat* F = nullptr;  // factor under construction
+  double eps = 0, thr = 0;
+  tlr_opts o{};
+  int ldl = 0;
+  bool mixed = false;
+  tlr_status st = TLR_OK;
+  bool live = true;
+  int nb = 0, b = 0;
+  // column state
+  int Kk = 0;
+  std::vector<int64_t> goff;
+  std::vector<int> gld;
+  int64_t gtot = 0, R0k = 0, Rk = 0;
+  const int* dtab = nullptr;  // device rank/uoff/voff of F (nb x nb each)
+  const int64_t* dgoff = nullptr;
+  const int* dgld = nullptr;
+  int op0 = 0, nops = 0;
+  std::vector<int64_t> boff;
+  Buf G, G32, E, DV, DV32, Bc;
+  std::vector<float*> AU32, AV32, FU32, FV32;
+  std::vector<int64_t> fu32cap;
+  std::vector<double> nA, nL;  // Frobenius norms of the tiles of A and of L (mixed precision rule)
+  double fl_exec = 0, fl_model = 0, fl32 = 0;
+  int64_t rounds = 0, t32 = 0, t64 = 0;
+};
+
+template <typename T>
+struct Panels;
+template <>
+struct Panels<double> {
+  static const double* U(const Mat& m, int i) { return m.F->Urow[i]; }
+  static const double* AU(const Mat& m, int i) { return m.A->Urow[i]; }
+  static const double* AV(const Mat& m, int j) { return m.A->Vcol[j]; }
+  static const double* G(const Mat& m) { return static_cast<const double*>(m.G.p); }
+};
+template <>
+struct Panels<float> {
+  static const float* U(const Mat& m, int i) { return m.FU32[i]; }
+  static const float* AU(const Mat& m, int i) { return m.AU32[i]; }
+  static const float* AV(const Mat& m, int j) { return m.AV32[j]; }
+  static const float* G(const Mat& m) { return static_cast<const float*>(m.G32.p); }
+};
+
+// Sampling chains and projection of column k for the operands (tiles) of all
+// matrices of the batch, in arithmetic T (FP64, or FP32 on FP32 copies of the
+// panels).  The ARA engine sees FP64 samples.
+template <typename T>
+struct BatchSampler : Sampler {
+  tlr_ctx* ctx = nullptr;
+  int bs = 0, k = 0;
+  std::vector<Mat*>* L = nullptr;          // matrices of this column step
+  const std::vector<int>* op_m = nullptr;  // operand -> index into L
+  const std::vector<int>* op_i = nullptr;  // operand -> tile row i
+  const std::vector<char>* member = nullptr;
+  const double* Q = nullptr;
+  const std::vector<int64_t>* qoff = nullptr;
+  Buf *bom = nullptr, *bom32 = nullptr, *bx = nullptr, *bw = nullptr, *by32 = nullptr, *bp = nullptr, *bz = nullptr,
+      *bq32 = nullptr, *bb32 = nullptr;
+  static constexpr bool F32 = sizeof(T) == 4;
+  bool owns_omega() const override { return true; }
+  bool mine(int op) const { return !member || (*member)[op]; }
+
+  void sample(const std::vector<int>& ops, int t, const double*, const std::vector<double*>& Ydst) override {
+    // matrices present in this call
+    std::vector<int> mp;
+    std::vector<int> slot_of_m(L->size(), -1);
+    for (int op : ops) {
+      const int m = (*op_m)[op];
+      if (slot_of_m[m] < 0) { slot_of_m[m] = (int)mp.size(); mp.push_back(m); }
+    }
+    // Omega_{m,k,t} per matrix (its own key) and the shared products X = Urow_k^T Omega, X0 = V0col_k^T Omega
+    std::vector<int64_t> omo(mp.size()), xo(mp.size()), x0o(mp.size());
+    int64_t omt = 0, xt = 0;
+    for (size_t u = 0; u < mp.size(); ++u) {
+      const Mat& M = *(*L)[mp[u]];
+      omo[u] = omt;
+      omt += (int64_t)M.b * bs;
+      xo[u] = xt;
+      xt += (int64_t)std::max(M.Kk, 1) * bs;
+      x0o[u] = xt;
+      xt += (int64_t)std::max<int64_t>(M.R0k, 1) * bs;
+    }
+    double* Om = bom->need<double>((size_t)omt);
+    std::vector<OmegaJob> oj;
+    for (size_t u = 0; u < mp.size(); ++u) {
+      const Mat& M = *(*L)[mp[u]];
+      oj.push_back(OmegaJob{Om + omo[u], M.o.seed, STREAM_FACTOR, (uint32_t)k, (uint32_t)t, M.b, bs});
+    }
+    omega_batched(ctx, oj);
+    const T* OmT = reinterpret_cast<const T*>(Om);
+    if (F32) {
+      float* o32 = bom32->need<float>((size_t)omt);
+      to_float(ctx, omt, Om, o32);
+      OmT = reinterpret_cast<const T*>(o32);
+    }
+    T* X = bx->need<T>((size_t)xt);
+    std::vector<GemmJob<T>> jx;
+    for (size_t u = 0; u < mp.size(); ++u) {
+      Mat& M = *(*L)[mp[u]];
+      if (M.Kk > 0)
+        jx.push_back(job<T>(TN, M.Kk, bs, Panels<T>::U(M, k), M.b, OmT + omo[u], M.b, M.b, X + xo[u], M.Kk, 1.0, 0.0));
+      if (M.R0k > 0)
+        jx.push_back(job<T>(TN, (int)M.R0k, bs, Panels<T>::AV(M, k), M.b, OmT + omo[u], M.b, M.b, X + x0o[u],
+                            (int)M.R0k, 1.0, 0.0));
+      (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * bs * (M.Kk + M.R0k);
+    }
+    gemm<T>(ctx, TN, jx);
+    // W blocks of every operand (block-diagonal Gram products), then Y = [U0 | Urow] W
+    std::vector<SlotDescT<T>> sd(ops.size());
+    int64_t wtot = 0, ytot = 0;
+    for (size_t s = 0; s < ops.size(); ++s) {
+      const int op = ops[s], u = slot_of_m[(*op_m)[op]], i = (*op_i)[op];
+      const Mat& M = *(*L)[(*op_m)[op]];
+      SlotDescT<T>& d = sd[s];
+      d.rank = M.dtab;
+      d.uoff = M.dtab + (size_t)M.nb * M.nb;
+      d.voff = M.dtab + (size_t)2 * M.nb * M.nb;
+      d.goff = M.dgoff;
+      d.gld = M.dgld;
+      d.G = Panels<T>::G(M);
+      d.X = X + xo[u];
+      d.X0 = X + x0o[u];
+      d.ldx = std::max(M.Kk, 1);
+      d.ldx0 = (int)std::max<int64_t>(M.R0k, 1);
+      d.nb = M.nb;
+      d.k = k;
+      d.i = i;
+      d.r0 = M.A->rank[ix(M.A, i, k)];
+      d.x0off = (int)M.A->voff[ix(M.A, i, k)];
+      d.Ki = (int)M.F->ulen[i];
+      d.Kk = M.Kk;
+      d.q = bs;
+      d.bs = bs;
+      d.W = reinterpret_cast<T*>(wtot);  // offset, fixed below
+      d.P = nullptr;
+      d.Z = nullptr;
+      wtot += (int64_t)(d.r0 + d.Ki) * bs;
+      ytot += (int64_t)M.b * bs;
+    }
+    T* W = bw->need<T>((size_t)std::max<int64_t>(wtot, 1));
+    for (auto& d : sd) d.W = W + reinterpret_cast<size_t>(d.W);
+    const SlotDescT<T>* sdd = static_cast<const SlotDescT<T>*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDescT<T>)));
+    blkdiag_sample<T>(ctx, (int)ops.size(), k, sdd);
+    T* Y32 = F32 ? reinterpret_cast<T*>(by32->need<float>((size_t)ytot)) : nullptr;
+    std::vector<GemmJob<T>> jy;
+    std::vector<ConvBackJob> cb;
+    int64_t yo = 0;
+    for (size_t s = 0; s < ops.size(); ++s) {
+      const int op = ops[s], i = (*op_i)[op];
+      Mat& M = *(*L)[(*op_m)[op]];
+      const int r0 = sd[s].r0, Ki = sd[s].Ki, ldw = std::max(r0 + Ki, 1);
+      T* Yo = F32 ? Y32 + yo : reinterpret_cast<T*>(Ydst[s]);
+      const T* U0 = r0 ? Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, k)] : nullptr;
+      GemmJob<T> g = job<T>(NN, M.b, bs, U0, M.b, sd[s].W, ldw, r0, Yo, M.b, 1.0, 0.0);
+      g.A[1] = Panels<T>::U(M, i);
+      g.lda[1] = M.b;
+      g.B[1] = sd[s].W + r0;
+      g.ldb[1] = ldw;
+      g.K[1] = Ki;
+      jy.push_back(g);
+      if (F32) cb.push_back(ConvBackJob{reinterpret_cast<const float*>(Yo), Ydst[s], (int64_t)M.b * bs});
+      yo += (int64_t)M.b * bs;
+      (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * bs * (r0 + Ki);
+      double R = r0;  // paper model: 4 products per (i, j) pair, Equation 2
+      for (int j = 0; j < k; ++j) R += M.F->rank[ix(M.F, i, j)] + M.F->rank[ix(M.F, k, j)];
+      M.fl_model += 4.0 * M.b * bs * R;
+      (F32 ? M.t32 : M.t64) += 1;
+    }
+    gemm<T>(ctx, NN, jy);
+    batched_to_double(ctx, cb);
+  }
+
+  void project(const std::vector<int>& q) override {
+    const int nops = (int)q.size();
+    std::vector<int> ops;
+    for (int op = 0; op < nops; ++op)
+      if (mine(op) && q[op] > 0) ops.push_back(op);
+    if (ops.empty()) return;
+    std::vector<SlotDescT<T>> sd(ops.size());
+    int64_t ptot = 0, ztot = 0, q32tot = 0;
+    std::vector<int64_t> q32o(ops.size());
+    for (size_t s = 0; s < ops.size(); ++s) {
+      const int op = ops[s], i = (*op_i)[op];
+      const Mat& M = *(*L)[(*op_m)[op]];
+      SlotDescT<T>& d = sd[s];
+      d.rank = M.dtab;
+      d.uoff = M.dtab + (size_t)M.nb * M.nb;
+      d.voff = M.dtab + (size_t)2 * M.nb * M.nb;
+      d.goff = M.dgoff;
+      d.gld = M.dgld;
+      d.G = Panels<T>::G(M);
+      d.nb = M.nb;
+      d.k = k;
+      d.i = i;
+      d.r0 = M.A->rank[ix(M.A, i, k)];
+      d.Ki = (int)M.F->ulen[i];
+      d.Kk = M.Kk;
+      d.q = q[op];
+      d.bs = bs;
+      d.P = reinterpret_cast<T*>(ptot);
+      d.Z = reinterpret_cast<T*>(ztot);
+      ptot += (int64_t)(d.r0 + d.Ki) * q[op];
+      ztot += (int64_t)(d.r0 + M.Kk) * q[op];
+      q32o[s] = q32tot;
+      q32tot += (int64_t)M.b * q[op];
+    }
+    T* P = bp->need<T>((size_t)std::max<int64_t>(ptot, 1));
+    T* Z = bz->need<T>((size_t)std::max<int64_t>(ztot, 1));
+    for (auto& d : sd) {
+      d.P = P + reinterpret_cast<size_t>(d.P);
+      d.Z = Z + reinterpret_cast<size_t>(d.Z);
+    }
+    // Q_i and the output B_i in arithmetic T
+    float* Q32 = nullptr;
+    float* B32 = nullptr;
+    if (F32) {
+      Q32 = bq32->need<float>((size_t)std::max<int64_t>(q32tot, 1));
+      B32 = bb32->need<float>((size_t)std::max<int64_t>(q32tot, 1));
+      std::vector<ConvJob> cj;
+      for (size_t s = 0; s < ops.size(); ++s) {
+        const int op = ops[s];
+        const Mat& M = *(*L)[(*op_m)[op]];
+        cj.push_back(ConvJob{Q + (*qoff)[op], Q32 + q32o[s], (int64_t)M.b * q[op]});
+      }
+      batched_to_float(ctx, cj);
+    }
+    auto Qop = [&](size_t s) -> const T* {
+      return F32 ? reinterpret_cast<const T*>(Q32 + q32o[s]) : reinterpret_cast<const T*>(Q + (*qoff)[ops[s]]);
+    };
+    std::vector<GemmJob<T>> jp;
+    for (size_t s = 0; s < ops.size(); ++s) {
+      const int op = ops[s], i = (*op_i)[op];
+      Mat& M = *(*L)[(*op_m)[op]];
+      const int r0 = sd[s].r0, Ki = sd[s].Ki, ldp = r0 + Ki;
+      if (r0 > 0)
+        jp.push_back(job<T>(TN, r0, q[op], Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, k)], M.b, Qop(s),
+                            M.b, M.b, sd[s].P, ldp, 1.0, 0.0));
+      if (Ki > 0)
+        jp.push_back(job<T>(TN, Ki, q[op], Panels<T>::U(M, i), M.b, Qop(s), M.b, M.b, sd[s].P + r0, ldp, 1.0, 0.0));
+      (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * q[op] * (r0 + Ki);
+    }
+    gemm<T>(ctx, TN, jp);
+    const SlotDescT<T>* sdd = static_cast<const SlotDescT<T>*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDescT<T>)));
+    blkdiag_project<T>(ctx, (int)ops.size(), k, sdd);
+    std::vector<GemmJob<T>> jb;
+    std::vector<ConvBackJob> cb;
+    for (size_t s = 0; s < ops.size(); ++s) {
+      const int op = ops[s], i = (*op_i)[op];
+      Mat& M = *(*L)[(*op_m)[op]];
+      const int r0 = sd[s].r0, ldz = std::max(r0 + M.Kk, 1);
+      double* Bdst = static_cast<double*>(M.Bc.p) + (size_t)M.boff[op - M.op0] * M.b;
+      T* Bo = F32 ? reinterpret_cast<T*>(B32 + q32o[s]) : reinterpret_cast<T*>(Bdst);
+      const T* V0 = r0 ? Panels<T>::AV(M, k) + (size_t)M.b * M.A->voff[ix(M.A, i, k)] : nullptr;
+      GemmJob<T> g = job<T>(NN, M.b, q[op], V0, M.b, sd[s].Z, ldz, r0, Bo, M.b, 1.0, 0.0);
+      g.A[1] = Panels<T>::U(M, k);
+      g.lda[1] = M.b;
+      g.B[1] = sd[s].Z + r0;
+      g.ldb[1] = ldz;
+      g.K[1] = M.Kk;
+      jb.push_back(g);
+      if (F32) cb.push_back(ConvBackJob{reinterpret_cast<const float*>(Bo), Bdst, (int64_t)M.b * q[op]});
+      (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * q[op] * (r0 + M.Kk);
+      double R = r0;
+      for (int j = 0; j < k; ++j) R += M.F->rank[ix(M.F, i, j)] + M.F->rank[ix(M.F, k, j)];
+      M.fl_model += 4.0 * M.b * q[op] * R;
+    }
+    gemm<T>(ctx, NN, jb);
+    batched_to_double(ctx, cb);
+  }
+};
+
+// Operands split by the per-tile precision rule; both precisions share the slot layout.
+struct SplitSampler : Sampler {
+  BatchSampler<double>* f64;
+  BatchSampler<float>* f32;
+  const std::vector<char>* is32;
+  bool owns_omega() const override { return true; }
+  void sample(const std::vector<int>& ops, int t, const double* Om, const std::vector<double*>& Y) override {
+    std::vector<int> o32, o64;
+    std::vector<double*> y32, y64;
+    for (size_t s = 0; s < ops.size(); ++s) {
+      if ((*is32)[ops[s]]) { o32.push_back(ops[s]); y32.push_back(Y[s]); }
+      else { o64.push_back(ops[s]); y64.push_back(Y[s]); }
+    }
+    if (!o32.empty()) f32->sample(o32, t, Om, y32);
+    if (!o64.empty()) f64->sample(o64, t, Om, y64);
+  }
+  void project(const std::vector<int>& q) override {
+    f32->project(q);
+    f64->project(q);
+  }
+};
+
+float* f32_alloc(tlr_ctx* ctx, int64_t n) {
+  return static_cast<float*>(dalloc(ctx, sizeof(float) * (size_t)std::max<int64_t>(n, 1)));
+}
+
+// Frobenius norms of the tiles of block column j (|V_ij|_F = |U_ij V_ij^T|_F, U orthonormal).
+void panel_tile_norms(tlr_ctx* ctx, const tlr_mat* M, int j, std::vector<double>& out, Buf& tmp) {
+  const int64_t n = M->vlen[j];
+  if (n == 0) return;
+  double* d = tmp.need<double>((size_t)n);
+  col_sqnorms(ctx, M->Vcol[j], M->b, n, d);
+  std::vector<double> h(n);
+  TLR_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int i = j + 1; i < M->nb; ++i) {
+    double sq = 0;
+    for (int c = 0; c < M->rank[ix(M, i, j)]; ++c) sq += h[M->voff[ix(M, i, j)] + c];
+    out[ix(M, i, j)] = std::sqrt(sq);
+  }
+}
+
+void free_f32(tlr_ctx* ctx, Mat& M) {
+  for (auto* v : {&M.AU32, &M.AV32, &M.FU32, &M.FV32})
+    for (float*& p : *v) {
+      dfree(ctx, p);
+      p = nullptr;
+    }
+}
+
+}  // namespace
+
+void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std::vector<double>& eps_in,
+                  const std::vector<tlr_opts>& opts, int ldl, std::vector<tlr_status>& status) {
+  const auto t_start = std::chrono::steady_clock::now();
+  const int nm = (int)mats_in.size();
+  status.assign(nm, TLR_OK);
+  if (nm == 0) return;
+  const int bs = opts[0].bs;
+  for (auto& o : opts) TLR_REQUIRE(o.bs == bs, TLR_ERR_ARG, "all matrices of a batch use one ARA block width");
+  std::vector<std::unique_ptr<Mat>> mats;
+  Buf bnrm(ctx);
+  int kmax = 0;
+  for (int m = 0; m < nm; ++m) {
+    mats.emplace_back(new Mat(ctx));
+    Mat& M = *mats.back();
+    M.A = mats_in[m];
+    M.eps = eps_in[m];
+    M.thr = eps_in[m] / HALKO;
+    M.o = opts[m];
+    M.ldl = ldl;
+    M.nb = M.A->nb;
+    M.b = M.A->b;
+    M.mixed = M.o.precision == TLR_PREC_FP32 && M.eps >= 1e-4;
+    kmax = std::max(kmax, M.nb);
+    const int nb = M.nb, b = M.b;
+    tlr_mat* F = mat_new(M.A->N, M.A->d, b);
+    M.F = F;
+    F->kern = M.A->kern;
+    F->eps = M.eps;
+    F->diag = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
+    TLR_CUDA(cudaMemcpyAsync(F->diag, M.A->diag, sizeof(double) * (size_t)nb * b * b, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    if (ldl) F->dvec = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b));
+    F->dinv = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
+    for (int i = 0; i < nb; ++i) ensure_ucap(ctx, F, i, std::max<int64_t>(M.A->ulen[i], 16));
+    if (M.mixed) {  // FP32 copies of A's panels; tile norms for the precision rule
+      M.AU32.assign(nb, nullptr);
+      M.AV32.assign(nb, nullptr);
+      M.FU32.assign(nb, nullptr);
+      M.FV32.assign(nb, nullptr);
+      M.fu32cap.assign(nb, 0);
+      std::vector<ConvJob> cj;
+      for (int i = 0; i < nb; ++i) {
+        M.AU32[i] = f32_alloc(ctx, (int64_t)b * M.A->ulen[i]);
+        M.AV32[i] = f32_alloc(ctx, (int64_t)b * M.A->vlen[i]);
+        cj.push_back(ConvJob{M.A->Urow[i], M.AU32[i], (int64_t)b * M.A->ulen[i]});
+        cj.push_back(ConvJob{M.A->Vcol[i], M.AV32[i], (int64_t)b * M.A->vlen[i]});
+        M.fu32cap[i] = F->ucap[i];
+        M.FU32[i] = f32_alloc(ctx, (int64_t)b * M.fu32cap[i]);
+      }
+      batched_to_float(ctx, cj);
+      M.nA.assign((size_t)nb * nb, 0.0);
+      M.nL.assign((size_t)nb * nb, 0.0);
+      for (int j = 0; j < nb; ++j) panel_tile_norms(ctx, M.A, j, M.nA, bnrm);
+    }
+  }
+  struct Cleanup {  // FP32 copies and unfinished factors are released on every exit path
+    tlr_ctx* ctx;
+    std::vector<std::unique_ptr<Mat>>* mats;
+    ~Cleanup() {
+      cudaStreamSynchronize(ctx->side);
+      for (auto& M : *mats) {
+        free_f32(ctx, *M);
+        if (M->F) mat_destroy(ctx, M->F);
+      }
+    }
+  } cleanup{ctx, &mats};
+
+  Buf bQ(ctx), bTab(ctx), bInfo(ctx), bTmp(ctx), bOm(ctx), bOm32(ctx), bX(ctx), bW(ctx), bY32(ctx), bP(ctx), bZ(ctx),
+      bQ32(ctx), bB32(ctx);
+  int* info = bInfo.need<int>((size_t)nm);
+  int64_t tmp_need = 0;
+  for (auto& M : mats) tmp_need += (int64_t)M->b * NBK;
+  bTmp.need<double>((size_t)tmp_need);  // sized once: the side stream never reallocates it
+  AraStats total;
+
+  for (int k = 0; k < kmax; ++k) {
+    std::vector<Mat*> L;
+    for (auto& M : mats)
+      if (M->live && k < M->nb) L.push_back(M.get());
+    if (L.empty()) break;
+    // ---------------------------------------------------------------- Gram factors
+    prof_mark(ctx, PH_GRAM);
+    {
+      std::vector<GemmJob<double>> jg;
+      std::vector<GemmJob<float>> jg32;
+      std::vector<ScaleJob> sj;
+      std::vector<ConvJob> cdv;
+      for (Mat* Mp : L) {
+        Mat& M = *Mp;
+        tlr_mat* F = M.F;
+        const int b = M.b;
+        M.Kk = (int)F->ulen[k];
+        M.R0k = M.A->vlen[k];
+        M.goff.assign(std::max(k, 1), 0);
+        M.gld.assign(std::max(k, 1), 1);
+        M.gtot = 0;
+        int64_t dvtot = 0;
+        for (int j = 0; j < k; ++j) {
+          M.goff[j] = M.gtot;
+          M.gld[j] = (int)std::max<int64_t>(1, F->vlen[j] - F->voff[ix(F, k, j)]);
+          M.gtot += (int64_t)M.gld[j] * F->rank[ix(F, k, j)];
+          dvtot += (int64_t)b * F->rank[ix(F, k, j)];
+        }
+        double* G = M.G.need<double>((size_t)std::max<int64_t>(M.gtot, 1));
+        float* G32 = M.mixed ? M.G32.need<float>((size_t)std::max<int64_t>(M.gtot, 1)) : nullptr;
+        double* DV = ldl ? M.DV.need<double>((size_t)std::max<int64_t>(dvtot, 1)) : nullptr;
+        float* DV32 = (ldl && M.mixed) ? M.DV32.need<float>((size_t)std::max<int64_t>(dvtot, 1)) : nullptr;
+        int64_t dvo = 0;
+        for (int j = 0; j < k; ++j) {
+          const int rkj = F->rank[ix(F, k, j)];
+          if (rkj == 0) continue;
+          const int S = (int)(F->vlen[j] - F->voff[ix(F, k, j)]);
+          const double* Vkj = Vptr(F, k, j);
+          const float* Vkj32 = M.mixed ? M.FV32[j] + (size_t)b * F->voff[ix(F, k, j)] : nullptr;
+          if (ldl) {  // D_j V_kj (Equation 3: D(j,j) inside the chain)
+            sj.push_back(ScaleJob{F->dvec + (size_t)j * b, Vkj, DV + dvo, b, rkj, b, b, 0});
+            Vkj = DV + dvo;
+            if (M.mixed) {
+              cdv.push_back(ConvJob{DV + dvo, DV32 + dvo, (int64_t)b * rkj});
+              Vkj32 = DV32 + dvo;
+            }
+            dvo += (int64_t)b * rkj;
+          }
+          jg.push_back(job<double>(TN, S, rkj, Vptr(F, k, j), b, Vkj, b, b, G + M.goff[j], M.gld[j], 1.0, 0.0));
+          M.fl_exec += 2.0 * b * S * rkj;
+          if (M.mixed)  // FP32 Gram for the tiles that sample in FP32
+            jg32.push_back(job<float>(TN, S, rkj, M.FV32[j] + (size_t)b * F->voff[ix(F, k, j)], b, Vkj32, b, b,
+                                      G32 + M.goff[j], M.gld[j], 1.0, 0.0));
+        }
+      }
+      batched_scale_rows(ctx, sj);
+      batched_to_float(ctx, cdv);
+      gemm<double>(ctx, TN, jg);
+      gemm<float>(ctx, TN, jg32);
+    }
+    // ---------------------------------------------------------------- diagonal tiles (side stream)
+    // The diagonal tile is read by the column's batchTrsm only, not by its ARA: its
+    // updateDense, chol / LDL^T and inverse run on the side stream, overlapped with the
+    // sampling rounds, and join before the trsm.  (Schur compensation runs a nested ARA
+    // with its own workspaces and stays on the main stream.)
+    TLR_CUDA(cudaMemsetAsync(info, 0xff, sizeof(int) * nm, ctx->main));
+    TLR_CUDA(cudaEventRecord(ctx->ev_fork, ctx->main));
+    TLR_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    for (int pass = 0; pass < 2; ++pass) {
+      // pass 0: matrices without Schur compensation, on the side stream; pass 1: the others, main stream
+      std::vector<Mat*> S;
+      for (Mat* Mp : L)
+        if ((Mp->o.compensation == TLR_COMP_SCHUR) == (pass == 1)) S.push_back(Mp);
+      if (S.empty()) continue;
+      ctx->stream = pass == 0 ? ctx->side : ctx->main;
+      std::vector<GemmJob<double>> je, jd;
+      std::vector<DiagJob> shifts;
+      std::vector<DenseTile> tiles;
+      for (Mat* Mp : S) {
+        Mat& M = *Mp;
+        tlr_mat* F = M.F;
+        const int b = M.b;
+        double* Akk = F->diag + (size_t)k * b * b;
+        const double* G = static_cast<const double*>(M.G.p);
+        if (M.Kk > 0) {
+          double* E = M.E.need<double>((size_t)b * M.Kk);
+          for (int j = 0; j < k; ++j) {
+            const int rkj = F->rank[ix(F, k, j)];
+            if (rkj == 0) continue;
+            je.push_back(job<double>(NN, b, rkj, Uptr(F, k, j), b, G + M.goff[j], M.gld[j], rkj,
+                                     E + (size_t)b * F->uoff[ix(F, k, j)], b, 1.0, 0.0));
+            M.fl_exec += 2.0 * b * rkj * rkj;
+          }
+          GemmJob<double> g = job<double>(NT, b, b, E, b, F->Urow[k], b, M.Kk, Akk, b, -1.0, 1.0);
+          if (pass == 0) g.flags = GEMM_TRIL;
+          M.fl_exec += (pass == 0 ? 1.0 : 2.0) * b * b * M.Kk;
+          if (pass == 1) {  // full D_k into a scratch tile for the compensation
+            g.C = static_cast<double*>(M.DV.need<double>((size_t)b * b));  // reuse: D_k
+            g.alpha = 1.0;
+            g.beta = 0.0;
+          }
+          jd.push_back(g);
+        }
+        if (M.o.compensation == TLR_COMP_SHIFT && M.o.shift != 0.0) shifts.push_back(DiagJob{Akk, b, b, M.o.shift});
+        int mi = 0;
+        for (; mi < nm; ++mi)
+          if (mats[mi].get() == Mp) break;
+        tiles.push_back(DenseTile{Akk, ldl ? F->dvec + (size_t)k * b : nullptr, info + mi,
+                                  F->dinv + (size_t)k * b * b, b, b});
+        M.fl_exec += 2.0 * (double)b * b * b / 3.0;
+        M.fl_model += (double)b * b * b / 3.0;
+        for (int j = 0; j < k; ++j) {
+          const int r = F->rank[ix(F, k, j)];
+          M.fl_model += 4.0 * b * r * r + 2.0 * b * b * r;
+        }
+      }
+      gemm<double>(ctx, NN, je);
+      gemm<double>(ctx, NT, jd);
+      if (pass == 1) {
+        // Section 5.1.1: A_kk - D_k + diag(rowsum |D_k - Dbar_k|), Dbar_k = Q Q^T D_k Q Q^T,
+        // Q the eps-basis of D_k from ARA.
+        for (Mat* Mp : S) {
+          Mat& M = *Mp;
+          if (M.Kk == 0) continue;
+          const int b = M.b;
+          double* Akk = M.F->diag + (size_t)k * b * b;
+          double* Dk = static_cast<double*>(M.DV.p);
+          axpy_matrix(ctx, b, b, -1.0, Dk, b, Akk, b);
+          Buf bq(ctx), bb(ctx), bc(ctx);
+          double* Qd = bq.need<double>((size_t)b * (b + bs));
+          double* Bd = bb.need<double>((size_t)b * b);
+          double* C1 = bc.need<double>((size_t)2 * b * b);
+          double* C2 = C1 + (size_t)b * b;
+          std::vector<int> qd;
+          AraStats as;
+          ara_dense_run(ctx, 1, b, Dk, bs, M.eps, M.o.seed, STREAM_SCHUR, (uint32_t)k, Qd, Bd, qd, as);
+          const int r = qd[0];
+          if (r > 0) {  // Bd = D Q (D symmetric): C1 = Q^T Bd, C2 = Q C1, E = D - C2 Q^T
+            std::vector<GemmJob<double>> a1{job<double>(TN, r, r, Qd, b, Bd, b, b, C1, r, 1.0, 0.0)};
+            gemm<double>(ctx, TN, a1);
+            std::vector<GemmJob<double>> a2{job<double>(NN, b, r, Qd, b, C1, r, r, C2, b, 1.0, 0.0)};
+            gemm<double>(ctx, NN, a2);
+            std::vector<GemmJob<double>> a3{job<double>(NT, b, b, C2, b, Qd, b, r, Dk, b, -1.0, 1.0)};
+            gemm<double>(ctx, NT, a3);
+          }
+          add_rowsum_abs(ctx, b, Dk, b, Akk, b);
+        }
+      }
+      batched_add_diag(ctx, shifts);
+      dense_factor_batch(ctx, tiles, ldl, bTmp);
+      dense_trinv_batch(ctx, tiles, ldl);
+    }
+    TLR_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
+    ctx->stream = ctx->main;
+    // ---------------------------------------------------------------- cholARAUpdate (Algorithm 5)
+    std::vector<int> op_m, op_i, nrow, order;
+    std::vector<double> thr;
+    std::vector<int64_t> qoff;
+    int64_t qtot = 0;
+    for (size_t u = 0; u < L.size(); ++u) {
+      Mat& M = *L[u];
+      M.op0 = (int)op_m.size();
+      M.nops = M.nb - k - 1;
+      std::vector<int> ord(M.nops);
+      std::iota(ord.begin(), ord.end(), 0);
+      // tiles enter the batch by their original rank, descending (Algorithm 5 sortRanks)
+      std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) {
+        return M.A->rank[ix(M.A, k + 1 + a, k)] > M.A->rank[ix(M.A, k + 1 + c, k)];
+      });
+      for (int v : ord) order.push_back(M.op0 + v);
+      for (int v = 0; v < M.nops; ++v) {
+        op_m.push_back((int)u);
+        op_i.push_back(k + 1 + v);
+        nrow.push_back(M.b);
+        thr.push_back(M.thr);
+        qoff.push_back(qtot);
+        qtot += (int64_t)M.b * (M.b + bs);
+      }
+    }
+    const int nops = (int)op_m.size();
+    std::vector<int> q(nops, 0);
+    double* Q = bQ.need<double>((size_t)std::max<int64_t>(qtot, 1));
+    if (nops > 0) {
+      // device tables of every matrix (ranks and offsets of F, Gram offsets of this column)
+      std::vector<int64_t> toff(L.size());
+      int64_t tint = 0;
+      for (size_t u = 0; u < L.size(); ++u) {
+        toff[u] = tint;
+        tint += (int64_t)3 * L[u]->nb * L[u]->nb + 2 * std::max(k, 1) + 2 * std::max(k, 1);
+      }
+      std::vector<int> htab((size_t)tint, 0);
+      for (size_t u = 0; u < L.size(); ++u) {
+        Mat& M = *L[u];
+        tlr_mat* F = M.F;
+        const int nb2 = M.nb * M.nb;
+        int* t = htab.data() + toff[u];
+        for (int e = 0; e < nb2; ++e) {
+          t[e] = F->rank[e];
+          t[nb2 + e] = (int)F->uoff[e];
+          t[2 * nb2 + e] = (int)F->voff[e];
+        }
+        int64_t* go = reinterpret_cast<int64_t*>(t + 3 * nb2);
+        for (int j = 0; j < std::max(k, 1); ++j) go[j] = M.goff[j];
+        int* gl = t + 3 * nb2 + 2 * std::max(k, 1);
+        for (int j = 0; j < std::max(k, 1); ++j) gl[j] = M.gld[j];
+      }
+      int* dtab = bTab.need<int>((size_t)tint + 2);
+      TLR_CUDA(cudaMemcpyAsync(dtab, htab.data(), sizeof(int) * tint, cudaMemcpyHostToDevice, ctx->stream));
+      TLR_CUDA(cudaStreamSynchronize(ctx->stream));  // htab is pageable
+      for (size_t u = 0; u < L.size(); ++u) {
+        Mat& M = *L[u];
+        const int nb2 = M.nb * M.nb;
+        M.dtab = dtab + toff[u];
+        M.dgoff = reinterpret_cast<const int64_t*>(dtab + toff[u] + 3 * nb2);
+        M.dgld = dtab + toff[u] + 3 * nb2 + 2 * std::max(k, 1);
+      }
+      // per-tile precision rule (mixed precision): FP32 when u32 sqrt(K)(|A_ik|_F + sum_j
+      // |L_ij|_F |L_kj|_F) <= thr / 8, else FP64
+      std::vector<char> is32(nops, 0), is64(nops, 1);
+      bool any32 = false;
+      for (int op = 0; op < nops; ++op) {
+        Mat& M = *L[op_m[op]];
+        if (!M.mixed) continue;
+        const int i = op_i[op];
+        double sum = M.nA[ix(M.A, i, k)];
+        for (int j = 0; j < k; ++j) sum += M.nL[ix(M.F, i, j)] * M.nL[ix(M.F, k, j)];
+        const double K = (double)M.A->rank[ix(M.A, i, k)] + (double)M.F->ulen[i] + bs;
+        if (U32 * std::sqrt(K) * sum <= M.thr / 8.0) {
+          is32[op] = 1;
+          is64[op] = 0;
+          any32 = true;
+        }
+      }
+      BatchSampler<double> s64;
+      BatchSampler<float> s32;
+      auto setup = [&](auto& S, const std::vector<char>* mem) {
+        S.ctx = ctx; S.bs = bs; S.k = k; S.L = &L; S.op_m = &op_m; S.op_i = &op_i; S.member = mem;
+        S.Q = Q; S.qoff = &qoff;
+        S.bom = &bOm; S.bom32 = &bOm32; S.bx = &bX; S.bw = &bW; S.by32 = &bY32; S.bp = &bP; S.bz = &bZ;
+        S.bq32 = &bQ32; S.bb32 = &bB32;
+      };
+      setup(s64, any32 ? &is64 : nullptr);
+      setup(s32, &is32);
+      SplitSampler split;
+      split.f64 = &s64;
+      split.f32 = &s32;
+      split.is32 = &is32;
+      Sampler* smp = any32 ? static_cast<Sampler*>(&split) : static_cast<Sampler*>(&s64);
+      // the projection runs after the join (Bc is allocated once the ranks are known)
+      struct Deferred : Sampler {
+        Sampler* f;
+        bool owns_omega() const override { return true; }
+        void sample(const std::vector<int>& ops, int t, const double* Om, const std::vector<double*>& Y) override {
+          f->sample(ops, t, Om, Y);
+        }
+        void project(const std::vector<int>&) override {}
+      } dsmp;
+      dsmp.f = smp;
+      int max_slots = 0;
+      for (Mat* Mp : L) max_slots += Mp->o.max_slots > 0 ? Mp->o.max_slots : Mp->nb;
+      AraConfig cf{bs, 0, STREAM_FACTOR, (uint32_t)k, max_slots};
+      AraStats as;
+      ara_run(ctx, dsmp, nrow, thr, cf, order, Q, qoff, q, as);
+      total.rounds += as.rounds;
+      total.flops += as.flops;
+      // orthogonalization flops, attributed per matrix by its share of the operands
+      for (size_t u = 0; u < L.size(); ++u)
+        if (nops) L[u]->fl_exec += as.flops * (double)L[u]->nops / nops;
+      // ---------------------------------------------------------------- join, failures
+      prof_mark(ctx, PH_POTRF);  // waiting for the diagonal tiles
+      TLR_CUDA(cudaStreamWaitEvent(ctx->main, ctx->ev_join, 0));
+      std::vector<int> hinfo(nm);
+      TLR_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->main));
+      TLR_CUDA(cudaStreamSynchronize(ctx->main));
+      for (int mi = 0; mi < nm; ++mi) {
+        Mat& M = *mats[mi];
+        if (M.live && k < M.nb && hinfo[mi] >= 0) {
+          M.live = false;
+          M.st = TLR_ERR_NOT_SPD;
+          M.A->state = 3;
+          M.A->k_fail = k;
+        }
+      }
+      // ---------------------------------------------------------------- projection (sampleLeftT)
+      prof_mark(ctx, PH_PROJECT);
+      for (Mat* Mp : L) {
+        Mat& M = *Mp;
+        M.boff.assign(M.nops, 0);
+        M.Rk = 0;
+        for (int v = 0; v < M.nops; ++v) {
+          M.boff[v] = M.Rk;
+          M.Rk += M.live ? q[M.op0 + v] : 0;
+        }
+        M.Bc.need<double>((size_t)std::max<int64_t>(M.Rk, 1) * M.b);
+      }
+      // failed matrices are not projected
+      std::vector<char> keep(nops, 1);
+      for (int op = 0; op < nops; ++op) keep[op] = L[op_m[op]]->live;
+      std::vector<char> k64(nops), k32(nops);
+      for (int op = 0; op < nops; ++op) {
+        k64[op] = keep[op] && is64[op];
+        k32[op] = keep[op] && is32[op];
+      }
+      s64.member = &k64;
+      s32.member = &k32;
+      s64.project(q);
+      if (any32) s32.project(q);
+    } else {
+      prof_mark(ctx, PH_POTRF);
+      TLR_CUDA(cudaStreamWaitEvent(ctx->main, ctx->ev_join, 0));
+      std::vector<int> hinfo(nm);
+      TLR_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->main));
+      TLR_CUDA(cudaStreamSynchronize(ctx->main));
+      for (int mi = 0; mi < nm; ++mi) {
+        Mat& M = *mats[mi];
+        if (M.live && k < M.nb && hinfo[mi] >= 0) {
+          M.live = false;
+          M.st = TLR_ERR_NOT_SPD;
+          M.A->state = 3;
+          M.A->k_fail = k;
+        }
+      }
+    }
+    // ---------------------------------------------------------------- batchTrsm, updateTiles
+    prof_mark(ctx, PH_TRSM);
+    std::vector<GemmJob<double>> jt;
+    std::vector<ScaleJob> sj;
+    for (Mat* Mp : L) {
+      Mat& M = *Mp;
+      if (!M.live || M.nops == 0) continue;
+      tlr_mat* F = M.F;
+      const int b = M.b;
+      F->Vcol[k] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(M.Rk, 1) * b));
+      F->vlen[k] = M.Rk;
+      if (M.Rk > 0) {
+        // V_ik = L_kk^{-1} B_i (LDL^T: then D_k^{-1}, batchIDMult)
+        jt.push_back(job<double>(NN, b, (int)M.Rk, F->dinv + (size_t)k * b * b, b, static_cast<double*>(M.Bc.p), b, b,
+                                 F->Vcol[k], b, 1.0, 0.0));
+        if (ldl) sj.push_back(ScaleJob{F->dvec + (size_t)k * b, F->Vcol[k], F->Vcol[k], b, (int)M.Rk, b, b, 1});
+        M.fl_exec += 2.0 * b * b * M.Rk;
+        M.fl_model += (double)b * b * M.Rk;
+      }
+    }
+    gemm<double>(ctx, NN, jt);
+    batched_scale_rows(ctx, sj);
+    prof_mark(ctx, PH_UPDATE);
+    std::vector<CopyJob> cj;
+    std::vector<ConvJob> c32;
+    for (Mat* Mp : L) {
+      Mat& M = *Mp;
+      if (!M.live || M.nops == 0) continue;
+      tlr_mat* F = M.F;
+      const int b = M.b;
+      for (int v = 0; v < M.nops; ++v) {
+        const int op = M.op0 + v, i = k + 1 + v, r = q[op];
+        ensure_ucap(ctx, F, i, r);
+        F->rank[ix(F, i, k)] = r;
+        F->uoff[ix(F, i, k)] = F->ulen[i];
+        F->voff[ix(F, i, k)] = M.boff[v];
+        cj.push_back(CopyJob{Q + qoff[op], F->Urow[i] + (size_t)F->ulen[i] * b, (int64_t)r * b});
+        if (M.mixed) {
+          if (F->ulen[i] + r > M.fu32cap[i]) {  // grow the FP32 copy of block row i
+            const int64_t cap = std::max<int64_t>(F->ucap[i], F->ulen[i] + r);
+            float* p = f32_alloc(ctx, (int64_t)b * cap);
+            if (F->ulen[i] > 0)
+              TLR_CUDA(cudaMemcpyAsync(p, M.FU32[i], sizeof(float) * (size_t)b * F->ulen[i],
+                                       cudaMemcpyDeviceToDevice, ctx->stream));
+            dfree(ctx, M.FU32[i]);
+            M.FU32[i] = p;
+            M.fu32cap[i] = cap;
+          }
+          c32.push_back(ConvJob{Q + qoff[op], M.FU32[i] + (size_t)F->ulen[i] * b, (int64_t)r * b});
+        }
+        F->ulen[i] += r;
+      }
+      if (M.mixed) {
+        M.FV32[k] = f32_alloc(ctx, (int64_t)b * M.Rk);
+        c32.push_back(ConvJob{F->Vcol[k], M.FV32[k], (int64_t)b * M.Rk});
+      }
+    }
+    batched_copy(ctx, cj);
+    batched_to_float(ctx, c32);
+    for (Mat* Mp : L)
+      if (Mp->live && Mp->mixed && Mp->nops > 0) panel_tile_norms(ctx, Mp->F, k, Mp->nL, bnrm);
+  }
+  prof_flush(ctx);
+  TLR_CUDA(cudaStreamSynchronize(ctx->main));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  for (int mi = 0; mi < nm; ++mi) {
+    Mat& M = *mats[mi];
+    status[mi] = M.st;
+    free_f32(ctx, M);
+    if (!M.live) {
+      mat_destroy(ctx, M.F);
+      M.F = nullptr;
+      continue;
+    }
+    tlr_mat* A = M.A;
+    tlr_mat* F = M.F;
+    const int nb = M.nb;
+    // A := F
+    mat_free_storage(ctx, A);
+    dfree(ctx, A->diag);
+    dfree(ctx, A->dvec);
+    dfree(ctx, A->dinv);
+    A->diag = F->diag; F->diag = nullptr;
+    A->dvec = F->dvec; F->dvec = nullptr;
+    A->dinv = F->dinv; F->dinv = nullptr;
+    A->rank = F->rank; A->uoff = F->uoff; A->voff = F->voff;
+    A->Urow = F->Urow; A->Vcol = F->Vcol; A->ucap = F->ucap; A->vlen = F->vlen; A->ulen = F->ulen;
+    F->Urow.assign(nb, nullptr);
+    F->Vcol.assign(nb, nullptr);
+    mat_destroy(ctx, F);
+    M.F = nullptr;
+    A->state = ldl ? 2 : 1;
+    A->k_fail = -1;
+    A->eps = M.eps;
+    A->flops_exec = M.fl_exec;
+    A->flops_model = M.fl_model;
+    A->flops_fp32 = M.fl32;
+    A->ara_rounds = (double)(M.t32 + M.t64);
+    A->tiles_fp32 = M.mixed ? (double)M.t32 : 0.0;
+    A->tiles_fp64 = M.mixed ? (double)M.t64 : 0.0;
+    A->seconds = secs;
+  }
+}
+
+}  // namespace tlr

@@ -1,0 +1,99 @@
+// Declarations shared by the host-side translation units of the TLR library.
+#pragma once
+
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.h"
+
+namespace tlr {
+
+// Grow-only device workspace.
+struct Buf {
+  tlr_ctx* ctx = nullptr;
+  void* p = nullptr;
+  size_t cap = 0;
+  explicit Buf(tlr_ctx* c) : ctx(c) {}
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  ~Buf() { dfree(ctx, p); }
+  template <typename T>
+  T* need(size_t elems) {
+    const size_t bytes = std::max<size_t>(elems * sizeof(T), 256);
+    if (bytes > cap) {
+      dfree(ctx, p);
+      p = nullptr;
+      cap = 0;
+      p = dalloc(ctx, bytes + bytes / 4);
+      cap = bytes + bytes / 4;
+    }
+    return static_cast<T*>(p);
+  }
+};
+
+void d2h_sync(tlr_ctx* ctx, void* host, const void* dev, size_t bytes);
+
+// dense diagonal tiles (blocked, 64-wide blocks)
+constexpr int NBK = 64;
+struct DenseTile {
+  double* A;     // n x n lower, lda
+  double* dvec;  // LDL^T: D (n), else null
+  int* info;     // device int, -1 on entry
+  double* Linv;  // output of the inverse (n x n, ld n), or null
+  int n, lda;
+};
+void dense_factor_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int ldl, Buf& tmp);
+void dense_trinv_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int unit);
+void dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int unit, int nrhs, double* X, int ldx, int trans);
+
+// ARA engine (Algorithm 1 batched, dynamic batching of Algorithm 5)
+struct Sampler {
+  virtual ~Sampler() {}
+  // true: the sampler draws its own Gaussian blocks (one per matrix of the batch)
+  virtual bool owns_omega() const { return false; }
+  // Y[s] = T_{ops[s]} Omega_t, written to Ydst[s] (n_op x bs, leading dimension n_op).
+  virtual void sample(const std::vector<int>& ops, int t, const double* Om, const std::vector<double*>& Ydst) = 0;
+  // B_op = T_op^T Q_op for every operand, given the final widths q.
+  virtual void project(const std::vector<int>& q) = 0;
+};
+struct AraConfig {
+  int bs;
+  uint64_t seed;      // Gaussian blocks drawn by the engine (when the sampler does not own them)
+  uint32_t stream, k;
+  int max_slots;
+};
+struct AraStats {
+  int64_t rounds = 0;   // sum over operands of their rounds
+  int64_t batches = 0;  // number of batched rounds
+  double flops = 0;     // orthogonalization flops (FP64)
+};
+extern const double HALKO;
+extern const double TAU_DROP;
+// nrow[op] = rows of operand op; thr[op] = its convergence threshold (eps / HALKO);
+// Q_op at Q + qoff[op] with room for nrow[op] x (nrow[op] + bs).
+void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::vector<double>& thr,
+             const AraConfig& cf, const std::vector<int>& order, double* Q, const std::vector<int64_t>& qoff,
+             std::vector<int>& q, AraStats& st);
+
+// Uniform dense ARA: nops operands T + op*n*n (n x n); Q (nops x n x (n+bs)), B (nops x n x n).
+void ara_dense_run(tlr_ctx* ctx, int nops, int n, const double* T, int bs, double eps, uint64_t seed, uint32_t stream,
+                   uint32_t k, double* Q, double* B, std::vector<int>& q, AraStats& st);
+
+// TLR matrix helpers
+inline int64_t ix(const tlr_mat* M, int i, int j) { return (int64_t)i * M->nb + j; }
+inline double* Uptr(const tlr_mat* M, int i, int j) { return M->Urow[i] + (size_t)M->b * M->uoff[ix(M, i, j)]; }
+inline double* Vptr(const tlr_mat* M, int i, int j) { return M->Vcol[j] + (size_t)M->b * M->voff[ix(M, i, j)]; }
+void mat_free_storage(tlr_ctx* ctx, tlr_mat* M);
+void mat_destroy(tlr_ctx* ctx, tlr_mat* M);
+tlr_mat* mat_new(int64_t N, int d, int b);
+void ensure_ucap(tlr_ctx* ctx, tlr_mat* F, int i, int64_t extra);
+
+// Batched left-looking TLR Cholesky / LDL^T over several matrices (factor.cu).
+// On return status[m] is TLR_OK (mats[m] now holds its factor) or an error
+// (TLR_ERR_NOT_SPD: mats[m] in state FAILED with k_fail set).
+void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats, const std::vector<double>& eps,
+                  const std::vector<tlr_opts>& opts, int ldl, std::vector<tlr_status>& status);
+
+}  // namespace tlr

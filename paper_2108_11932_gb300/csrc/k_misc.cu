@@ -94,8 +94,8 @@ void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, do
 constexpr int MAXBS = 64;
 __global__ void __launch_bounds__(32) k_cholqr_small(int bs, const double* __restrict__ Gall,
                                                      double* __restrict__ Mall, int* __restrict__ status,
-                                                     double* __restrict__ enorm, double thr, double tau,
-                                                     int first_pass, const int* __restrict__ nk_in) {
+                                                     double* __restrict__ enorm, const double* __restrict__ thrv,
+                                                     double tau, int first_pass, const int* __restrict__ nk_in) {
   extern __shared__ double dsm[];
   const int ld = bs + 1;
   double* Rm = dsm;                 // bs x (bs + 1), row-major R(row, col)
@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(32) k_cholqr_small(int bs, const double* __res
   double* M = Mall + (size_t)s * bs * bs;
   for (int e = lane; e < bs * bs; e += 32) M[e] = 0.0;
   int n = bs;
+  const double thr = thrv[s];
   double thr2 = thr * thr;
   if (first_pass) {
     double gmax = 0.0;
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(32) k_cholqr_small(int bs, const double* __res
 template <int BS>
 __global__ void __launch_bounds__(32) k_cholqr_reg(const double* __restrict__ Gall, double* __restrict__ Mall,
                                                    int* __restrict__ status, double* __restrict__ enorm,
-                                                   double thr, double tau, int first_pass,
+                                                   const double* __restrict__ thrv, double tau, int first_pass,
                                                    const int* __restrict__ nk_in) {
   const int s = blockIdx.x, lane = threadIdx.x;
   const double* G = Gall + (size_t)s * BS * BS;
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(32) k_cholqr_reg(const double* __restrict__ Ga
   for (int r = 0; r < BS; ++r)
     if (r == lane) gdiag = g[r];
   int n = BS;
+  const double thr = thrv[s];
   double thr2 = thr * thr;
   if (first_pass) {
     double gmax = gdiag;
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(32) k_cholqr_reg(const double* __restrict__ Ga
 }
 
 void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mout, int* status,
-                  double* enorm, double thr, double tau, int first_pass, const int* nk_in) {
+                  double* enorm, const double* thr, double tau, int first_pass, const int* nk_in) {
   if (nslots <= 0) return;
   if (bs == 16 || bs == 32 || bs == 8) {
     if (bs == 16)
@@ -295,15 +297,19 @@ void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mou
 }
 
 // ------------------------------------------------------------------ dense diagonal-tile factorization
-// Factor the nbk x nbk diagonal block at A (lda) in shared memory, one CTA.
-// Cholesky: right-looking column by column.  LDL^T (unpivoted, Section 5.3):
-// d_j = a_jj, l_ij = a_ij / d_j, a_il -= l_ij d_j l_lj; the unit diagonal is
-// written to A and d to dvec.  *info records the first failing global column
-// (atomicCAS from -1), after which the block stops.
+// All three kernels take an array of per-tile descriptors (grid.y = tile), so the
+// diagonal tiles of many matrices factor in the same launches.
+//
+// k_potrf_block: factor the nbk x nbk diagonal block at A (lda) in shared memory,
+// one CTA.  Cholesky: right-looking column by column.  LDL^T (unpivoted, Section
+// 5.3): d_j = a_jj, l_ij = a_ij / d_j, a_il -= l_ij d_j l_lj; the unit diagonal is
+// written to A and d to dvec.  *info records the first failing column (atomicCAS
+// from -1), after which the block stops.
 constexpr int PB = 64;
-__global__ void __launch_bounds__(256) k_potrf_block(int nbk, double* __restrict__ A, int lda, int ldl,
-                                                     double* __restrict__ dvec, int* __restrict__ info,
-                                                     int col0) {
+__global__ void __launch_bounds__(256) k_potrf_block(const PotrfJob* __restrict__ jobs, int ldl) {
+  const PotrfJob J = jobs[blockIdx.y];
+  const int nbk = J.nbk, lda = J.lda;
+  double* A = J.A;
   __shared__ double S[PB][PB + 1];
   __shared__ int fail;
   const int tid = threadIdx.x;
@@ -317,21 +323,21 @@ __global__ void __launch_bounds__(256) k_potrf_block(int nbk, double* __restrict
     const double piv = S[j][j];
     const bool bad = ldl ? (piv == 0.0 || !isfinite(piv)) : !(piv > 0.0) || !isfinite(piv);
     if (bad) {
-      if (tid == 0) { fail = 1; atomicCAS(info, -1, col0 + j); }
+      if (tid == 0) { fail = 1; atomicCAS(J.info, -1, J.col0 + j); }
       __syncthreads();
       break;
     }
     const double sj = ldl ? piv : sqrt(piv);
     __syncthreads();  // everyone has read S[j][j]
-    // column j below the diagonal
     for (int r = j + 1 + tid; r < nbk; r += blockDim.x) S[r][j] = S[r][j] / sj;
     if (tid == 0) S[j][j] = ldl ? piv : sj;
     __syncthreads();
-    // trailing update of the lower triangle
-    const int m = nbk - j - 1;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int r = j + 1 + e % m, c = j + 1 + e / m;
-      if (r >= c) S[r][c] -= S[r][j] * (ldl ? piv : 1.0) * S[c][j];
+    // trailing update of the lower triangle: thread owns column c = tid % 64, rows tid / 64 + 4 i
+    const int c = tid & (PB - 1);
+    if (c > j && c < nbk) {
+      const double lcj = S[c][j] * (ldl ? piv : 1.0);
+      for (int r = (tid >> 6); r < nbk; r += 4)
+        if (r >= c) S[r][c] -= S[r][j] * lcj;
     }
     __syncthreads();
   }
@@ -340,90 +346,71 @@ __global__ void __launch_bounds__(256) k_potrf_block(int nbk, double* __restrict
     const int r = e % nbk, c = e / nbk;
     if (r > c) A[r + (size_t)c * lda] = S[r][c];
     else if (r == c) {
-      if (ldl) { dvec[col0 + r] = S[r][r]; A[r + (size_t)c * lda] = 1.0; }
+      if (ldl) { J.dvec[J.col0 + r] = S[r][r]; A[r + (size_t)c * lda] = 1.0; }
       else A[r + (size_t)c * lda] = S[r][r];
     }
   }
 }
 
-void potrf_diag_block(tlr_ctx* ctx, int nbk, double* A, int lda, int ldl, double* dvec, int* info,
-                      int col0) {
-  TLR_REQUIRE(nbk <= PB, TLR_ERR_LIMIT, "potrf block above 64");
-  k_potrf_block<<<1, 256, 0, ctx->stream>>>(nbk, A, lda, ldl, dvec, info, col0);
-  TLR_LAUNCH_CHECK(ctx);
-}
-
 // X (m x nbk) <- X L^{-T} (Cholesky) or X L^{-T} D^{-1} (LDL^T, unit L), L the
-// factored nbk x nbk diagonal block.  One thread per row of X; 64 rows per CTA.
-__global__ void __launch_bounds__(64) k_trsm_panel_right(int m, int nbk, const double* __restrict__ L,
-                                                         int lda, double* __restrict__ X, int ldx, int ldl,
-                                                         const double* __restrict__ dvec) {
-  // The 64 x 64 block is staged in shared memory with one coalesced load: the
-  // substitution reads it by rows, which in the column-major array would touch a
-  // new cache line at every step.
+// factored nbk x nbk diagonal block.  One thread per row of X; 64 rows per CTA.  The
+// block is staged in shared memory with one coalesced load: the substitution reads
+// it by rows, which in the column-major array would touch a new cache line per step.
+__global__ void __launch_bounds__(64) k_trsm_panel_right(const PanelJob* __restrict__ jobs, int ldl) {
+  const PanelJob J = jobs[blockIdx.y];
+  const int nbk = J.nbk, m = J.m;
+  const int tid = threadIdx.x, r0 = blockIdx.x * PB;
+  if (r0 >= m) return;
   extern __shared__ double dsm[];
   double (*Ls)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm);
   double (*Xs)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm + PB * (PB + 1));
-  const int tid = threadIdx.x, r0 = blockIdx.x * PB;
   for (int e = tid; e < nbk * nbk; e += 64) {
     const int r = e % nbk, c = e / nbk;
-    Ls[r][c] = L[r + (size_t)c * lda];
+    Ls[r][c] = J.L[r + (size_t)c * J.lda];
   }
   const int rows = min(PB, m - r0);
   for (int e = tid; e < rows * nbk; e += 64) {
     const int r = e % rows, c = e / rows;
-    Xs[r][c] = X[(r0 + r) + (size_t)c * ldx];
+    Xs[r][c] = J.X[(r0 + r) + (size_t)c * J.ldx];
   }
   __syncthreads();
   if (tid < rows) {
-    // solve x L^T = a  <=>  L x^T = a^T: forward substitution over c
     for (int c = 0; c < nbk; ++c) {
       double v = Xs[tid][c];
       for (int l = 0; l < c; ++l) v = fma(-Ls[c][l], Xs[tid][l], v);
       Xs[tid][c] = ldl ? v : v / Ls[c][c];
     }
     if (ldl)
-      for (int c = 0; c < nbk; ++c) Xs[tid][c] /= dvec[c];
+      for (int c = 0; c < nbk; ++c) Xs[tid][c] /= J.dvec[c];
   }
   __syncthreads();
   for (int e = tid; e < rows * nbk; e += 64) {
     const int r = e % rows, c = e / rows;
-    X[(r0 + r) + (size_t)c * ldx] = Xs[r][c];
+    J.X[(r0 + r) + (size_t)c * J.ldx] = Xs[r][c];
   }
 }
 
 static size_t two_block_smem() { return sizeof(double) * 2 * PB * (PB + 1); }
 
-void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, double* X, int ldx,
-                      int ldl, const double* dvec) {
-  if (m <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    TLR_CUDA(cudaFuncSetAttribute(k_trsm_panel_right, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)two_block_smem()));
-    attr = true;
-  }
-  k_trsm_panel_right<<<cdiv(m, PB), 64, two_block_smem(), ctx->stream>>>(m, nbk, L, lda, X, ldx, ldl, dvec);
-  TLR_LAUNCH_CHECK(ctx);
-}
-
-// X (nbk x nrhs) <- L^{-1} X, L the nbk x nbk lower diagonal block (unit if
-// `unit`).  One thread per right-hand-side column; 64 columns per CTA.
-__global__ void __launch_bounds__(64) k_trsm_left_block(int nbk, const double* __restrict__ L, int lda,
-                                                        int unit, int nrhs, double* __restrict__ X, int ldx,
-                                                        int trans) {
+// X (nbk x nrhs) <- L^{-1} X (or L^{-T} X if trans), L the nbk x nbk lower
+// diagonal block (unit if `unit`).  One thread per right-hand-side column; 64
+// columns per CTA.
+__global__ void __launch_bounds__(64) k_trsm_left_block(const LeftJob* __restrict__ jobs, int unit, int trans) {
+  const LeftJob J = jobs[blockIdx.y];
+  const int nbk = J.nbk, nrhs = J.nrhs;
+  const int tid = threadIdx.x, c0 = blockIdx.x * PB;
+  if (c0 >= nrhs) return;
   extern __shared__ double dsm[];
   double (*Ls)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm);
   double (*Xs)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm + PB * (PB + 1));
-  const int tid = threadIdx.x, c0 = blockIdx.x * PB;
   for (int e = tid; e < nbk * nbk; e += 64) {
     const int r = e % nbk, c = e / nbk;
-    Ls[r][c] = L[r + (size_t)c * lda];
+    Ls[r][c] = J.L[r + (size_t)c * J.lda];
   }
   const int cols = min(PB, nrhs - c0);
   for (int e = tid; e < nbk * cols; e += 64) {
     const int r = e % nbk, c = e / nbk;
-    Xs[r][c] = X[r + (size_t)(c0 + c) * ldx];
+    Xs[r][c] = J.X[r + (size_t)(c0 + c) * J.ldx];
   }
   __syncthreads();
   if (tid < cols) {
@@ -444,32 +431,71 @@ __global__ void __launch_bounds__(64) k_trsm_left_block(int nbk, const double* _
   __syncthreads();
   for (int e = tid; e < nbk * cols; e += 64) {
     const int r = e % nbk, c = e / nbk;
-    X[r + (size_t)(c0 + c) * ldx] = Xs[r][c];
+    J.X[r + (size_t)(c0 + c) * J.ldx] = Xs[r][c];
   }
 }
 
-static void left_block_attr() {
-  static bool attr = false;
-  if (!attr) {
-    TLR_CUDA(cudaFuncSetAttribute(k_trsm_left_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)two_block_smem()));
-    attr = true;
+static void smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  TLR_CUDA(cudaFuncSetAttribute(k_trsm_panel_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_block_smem()));
+  TLR_CUDA(cudaFuncSetAttribute(k_trsm_left_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_block_smem()));
+  done = true;
+}
+
+void potrf_blocks(tlr_ctx* ctx, std::vector<PotrfJob>& jobs, int ldl) {
+  for (size_t o = 0; o < jobs.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, jobs.size() - o);
+    TLR_REQUIRE(std::all_of(jobs.begin() + o, jobs.begin() + o + cnt, [](const PotrfJob& j) { return j.nbk <= PB; }),
+                TLR_ERR_LIMIT, "potrf block above 64");
+    const PotrfJob* dj = static_cast<const PotrfJob*>(upload(ctx, jobs.data() + o, cnt * sizeof(PotrfJob)));
+    k_potrf_block<<<dim3(1, (unsigned)cnt), 256, 0, ctx->stream>>>(dj, ldl);
+    TLR_LAUNCH_CHECK(ctx);
+  }
+}
+void trsm_panels(tlr_ctx* ctx, std::vector<PanelJob>& jobs, int ldl) {
+  smem_attrs();
+  int mx = 0;
+  std::vector<PanelJob> nz;
+  for (auto& j : jobs)
+    if (j.m > 0) { nz.push_back(j); mx = std::max(mx, j.m); }
+  for (size_t o = 0; o < nz.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
+    const PanelJob* dj = static_cast<const PanelJob*>(upload(ctx, nz.data() + o, cnt * sizeof(PanelJob)));
+    k_trsm_panel_right<<<dim3(cdiv(mx, PB), (unsigned)cnt), 64, two_block_smem(), ctx->stream>>>(dj, ldl);
+    TLR_LAUNCH_CHECK(ctx);
+  }
+}
+void trsm_lefts(tlr_ctx* ctx, std::vector<LeftJob>& jobs, int unit, int trans) {
+  smem_attrs();
+  int mx = 0;
+  std::vector<LeftJob> nz;
+  for (auto& j : jobs)
+    if (j.nrhs > 0) { nz.push_back(j); mx = std::max(mx, j.nrhs); }
+  for (size_t o = 0; o < nz.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
+    const LeftJob* dj = static_cast<const LeftJob*>(upload(ctx, nz.data() + o, cnt * sizeof(LeftJob)));
+    k_trsm_left_block<<<dim3(cdiv(mx, PB), (unsigned)cnt), 64, two_block_smem(), ctx->stream>>>(dj, unit, trans);
+    TLR_LAUNCH_CHECK(ctx);
   }
 }
 
-void trsm_left_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs, double* X,
-                     int ldx) {
-  if (nrhs <= 0) return;
-  left_block_attr();
-  k_trsm_left_block<<<cdiv(nrhs, PB), 64, two_block_smem(), ctx->stream>>>(nbk, L, lda, unit, nrhs, X, ldx, 0);
-  TLR_LAUNCH_CHECK(ctx);
+void potrf_diag_block(tlr_ctx* ctx, int nbk, double* A, int lda, int ldl, double* dvec, int* info, int col0) {
+  std::vector<PotrfJob> j{PotrfJob{A, dvec, info, lda, col0, nbk}};
+  potrf_blocks(ctx, j, ldl);
 }
-void trsm_left_t_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs,
-                       double* X, int ldx) {
-  if (nrhs <= 0) return;
-  left_block_attr();
-  k_trsm_left_block<<<cdiv(nrhs, PB), 64, two_block_smem(), ctx->stream>>>(nbk, L, lda, unit, nrhs, X, ldx, 1);
-  TLR_LAUNCH_CHECK(ctx);
+void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, double* X, int ldx, int ldl,
+                      const double* dvec) {
+  std::vector<PanelJob> j{PanelJob{L, X, dvec, lda, ldx, m, nbk}};
+  trsm_panels(ctx, j, ldl);
+}
+void trsm_left_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs, double* X, int ldx) {
+  std::vector<LeftJob> j{LeftJob{L, X, lda, ldx, nrhs, nbk}};
+  trsm_lefts(ctx, j, unit, 0);
+}
+void trsm_left_t_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs, double* X, int ldx) {
+  std::vector<LeftJob> j{LeftJob{L, X, lda, ldx, nrhs, nbk}};
+  trsm_lefts(ctx, j, unit, 1);
 }
 
 // ------------------------------------------------------------------ elementwise helpers
@@ -664,63 +690,57 @@ void to_double(tlr_ctx* ctx, int64_t n, const float* x, double* y) {
 //   W_i = [X0_i ; -G_i0 X_0 ; ... ; -G_i,k-1 X_k-1],  X_j = U_kj^T Omega, X0_i = V0_ik^T Omega.
 // G for block column j is stored as Gcol_j = V(j)[tiles i >= k]^T [D_j] V_kj
 // (rows grouped by i at V's column offsets, leading dimension gld[j]).
-// Grid (slot, j in 0..k): block j < k writes -G_ij X_j, block k copies X0_i.
+// Every slot carries its own matrix's tables, so slots of different matrices share
+// one launch.  Grid (slot, j in 0..kmax): block j < k writes -G_ij X_j, block k copies X0_i.
 template <typename T>
-__global__ void k_blkdiag_sample(BlkTables tb, const SlotDesc* __restrict__ slots,
-                                 const int64_t* __restrict__ goff, const int* __restrict__ gld,
-                                 const T* __restrict__ G, const T* __restrict__ X, int ldx,
-                                 const T* __restrict__ X0, int ldx0, int bs, T* __restrict__ W) {
-  const SlotDesc sd = slots[blockIdx.x];
-  const int j = blockIdx.y, nb = tb.nb, k = tb.k, i = sd.i;
+__global__ void k_blkdiag_sample(const SlotDescT<T>* __restrict__ slots) {
+  const SlotDescT<T> sd = slots[blockIdx.x];
+  const int j = blockIdx.y, nb = sd.nb, k = sd.k, i = sd.i, bs = sd.bs;
+  if (j > k) return;
   const int ldw = sd.r0 + sd.Ki;
-  T* Wi = W + sd.woff;
   if (j == k) {
     for (int e = threadIdx.x; e < sd.r0 * bs; e += blockDim.x) {
       const int a = e % sd.r0, c = e / sd.r0;
-      Wi[a + (size_t)c * ldw] = X0[(sd.x0off + a) + (size_t)c * ldx0];
+      sd.W[a + (size_t)c * ldw] = sd.X0[(sd.x0off + a) + (size_t)c * sd.ldx0];
     }
     return;
   }
-  const int rij = tb.rank[i * nb + j], rkj = tb.rank[k * nb + j];
+  const int rij = sd.rank[i * nb + j], rkj = sd.rank[k * nb + j];
   if (rij == 0) return;
-  const T* Gij = G + goff[j] + (tb.voff[i * nb + j] - tb.voff[k * nb + j]);
-  const int ldg = gld[j];
-  const T* Xj = X + tb.uoff[k * nb + j];
-  T* out = Wi + sd.r0 + tb.uoff[i * nb + j];
+  const T* Gij = sd.G + sd.goff[j] + (sd.voff[i * nb + j] - sd.voff[k * nb + j]);
+  const int ldg = sd.gld[j];
+  const T* Xj = sd.X + sd.uoff[k * nb + j];
+  T* out = sd.W + sd.r0 + sd.uoff[i * nb + j];
   for (int e = threadIdx.x; e < rij * bs; e += blockDim.x) {
     const int a = e % rij, c = e / rij;
     T acc = T(0);
-    for (int q = 0; q < rkj; ++q) acc = fma(Gij[a + (size_t)q * ldg], Xj[q + (size_t)c * ldx], acc);
+    for (int q = 0; q < rkj; ++q) acc = fma(Gij[a + (size_t)q * ldg], Xj[q + (size_t)c * sd.ldx], acc);
     out[a + (size_t)c * ldw] = -acc;
   }
 }
 
 // Projection (sampleLeftT): B_i = T_ik^T Q_i = [V0_ik | U_k0 ... U_k,k-1] Z_i with
 //   P_i = [U0_ik | U_i0 ...]^T Q_i ((r0 + K_i) x q),
-//   Z_i = [P_i^(0) ; -G_i0^T P_i^(0-block of j=0) ; ...]   ((r0 + K_k) x q).
+//   Z_i = [P_i^(0) ; -G_i0^T P_i^(j=0 block) ; ...]   ((r0 + K_k) x q).
 template <typename T>
-__global__ void k_blkdiag_project(BlkTables tb, const SlotDesc* __restrict__ slots,
-                                  const int64_t* __restrict__ goff, const int* __restrict__ gld,
-                                  const T* __restrict__ G, const T* __restrict__ P, T* __restrict__ Z,
-                                  int Kk) {
-  const SlotDesc sd = slots[blockIdx.x];
-  const int j = blockIdx.y, nb = tb.nb, k = tb.k, i = sd.i, q = sd.q;
-  const int ldp = sd.r0 + sd.Ki, ldz = sd.r0 + Kk;
-  const T* Pi = P + sd.poff;
-  T* Zi = Z + sd.woff;
+__global__ void k_blkdiag_project(const SlotDescT<T>* __restrict__ slots) {
+  const SlotDescT<T> sd = slots[blockIdx.x];
+  const int j = blockIdx.y, nb = sd.nb, k = sd.k, i = sd.i, q = sd.q;
+  if (j > k) return;
+  const int ldp = sd.r0 + sd.Ki, ldz = sd.r0 + sd.Kk;
   if (j == k) {
     for (int e = threadIdx.x; e < sd.r0 * q; e += blockDim.x) {
       const int a = e % sd.r0, c = e / sd.r0;
-      Zi[a + (size_t)c * ldz] = Pi[a + (size_t)c * ldp];
+      sd.Z[a + (size_t)c * ldz] = sd.P[a + (size_t)c * ldp];
     }
     return;
   }
-  const int rij = tb.rank[i * nb + j], rkj = tb.rank[k * nb + j];
+  const int rij = sd.rank[i * nb + j], rkj = sd.rank[k * nb + j];
   if (rkj == 0) return;
-  T* out = Zi + sd.r0 + tb.uoff[k * nb + j];
-  const T* Gij = G + goff[j] + (tb.voff[i * nb + j] - tb.voff[k * nb + j]);
-  const int ldg = gld[j];
-  const T* Pj = Pi + sd.r0 + tb.uoff[i * nb + j];
+  T* out = sd.Z + sd.r0 + sd.uoff[k * nb + j];
+  const T* Gij = sd.G + sd.goff[j] + (sd.voff[i * nb + j] - sd.voff[k * nb + j]);
+  const int ldg = sd.gld[j];
+  const T* Pj = sd.P + sd.r0 + sd.uoff[i * nb + j];
   for (int e = threadIdx.x; e < rkj * q; e += blockDim.x) {
     const int a = e % rkj, c = e / rkj;
     T acc = T(0);
@@ -730,35 +750,114 @@ __global__ void k_blkdiag_project(BlkTables tb, const SlotDesc* __restrict__ slo
 }
 
 template <typename T>
-void blkdiag_sample(tlr_ctx* ctx, const BlkTables& tb, int nslots, const SlotDesc* slots_dev,
-                    const int64_t* goff_dev, const int* gld_dev, const T* G, const T* X, int ldx,
-                    const T* X0, int ldx0, int bs, T* W) {
+void blkdiag_sample(tlr_ctx* ctx, int nslots, int kmax, const SlotDescT<T>* slots_dev) {
   if (nslots <= 0) return;
-  dim3 grid((unsigned)nslots, (unsigned)(tb.k + 1));
-  k_blkdiag_sample<T><<<grid, 128, 0, ctx->stream>>>(tb, slots_dev, goff_dev, gld_dev, G, X, ldx, X0,
-                                                    ldx0, bs, W);
+  dim3 grid((unsigned)nslots, (unsigned)(kmax + 1));
+  k_blkdiag_sample<T><<<grid, 128, 0, ctx->stream>>>(slots_dev);
   TLR_LAUNCH_CHECK(ctx);
 }
 template <typename T>
-void blkdiag_project(tlr_ctx* ctx, const BlkTables& tb, int nslots, const SlotDesc* slots_dev,
-                     const int64_t* goff_dev, const int* gld_dev, const T* G, const T* P, T* Z,
-                     int Kk, int qmax) {
-  (void)qmax;
+void blkdiag_project(tlr_ctx* ctx, int nslots, int kmax, const SlotDescT<T>* slots_dev) {
   if (nslots <= 0) return;
-  dim3 grid((unsigned)nslots, (unsigned)(tb.k + 1));
-  k_blkdiag_project<T><<<grid, 128, 0, ctx->stream>>>(tb, slots_dev, goff_dev, gld_dev, G, P, Z, Kk);
+  dim3 grid((unsigned)nslots, (unsigned)(kmax + 1));
+  k_blkdiag_project<T><<<grid, 128, 0, ctx->stream>>>(slots_dev);
   TLR_LAUNCH_CHECK(ctx);
 }
-template void blkdiag_sample<double>(tlr_ctx*, const BlkTables&, int, const SlotDesc*, const int64_t*,
-                                     const int*, const double*, const double*, int, const double*, int,
-                                     int, double*);
-template void blkdiag_sample<float>(tlr_ctx*, const BlkTables&, int, const SlotDesc*, const int64_t*,
-                                    const int*, const float*, const float*, int, const float*, int, int,
-                                    float*);
-template void blkdiag_project<double>(tlr_ctx*, const BlkTables&, int, const SlotDesc*, const int64_t*,
-                                      const int*, const double*, const double*, double*, int, int);
-template void blkdiag_project<float>(tlr_ctx*, const BlkTables&, int, const SlotDesc*, const int64_t*,
-                                     const int*, const float*, const float*, float*, int, int);
+template void blkdiag_sample<double>(tlr_ctx*, int, int, const SlotDescT<double>*);
+template void blkdiag_sample<float>(tlr_ctx*, int, int, const SlotDescT<float>*);
+template void blkdiag_project<double>(tlr_ctx*, int, int, const SlotDescT<double>*);
+template void blkdiag_project<float>(tlr_ctx*, int, int, const SlotDescT<float>*);
+
+// Batched Philox blocks: block g is Omega(seed_g, stream_g, k_g, t_g), b_g x bs, at out_g.
+__global__ void k_omega_batched(const OmegaJob* __restrict__ jobs) {
+  const OmegaJob J = jobs[blockIdx.y];
+  const int n = J.b * J.bs;
+  for (int m = blockIdx.x * blockDim.x + threadIdx.x; 2 * m < n; m += gridDim.x * blockDim.x) {
+    uint32_t c[4] = {(uint32_t)m, J.t, J.k, J.stream};
+    philox4x32_10(c, (uint32_t)J.seed, (uint32_t)(J.seed >> 32));
+    const uint64_t a = ((uint64_t)c[1] << 32) | c[0];
+    const uint64_t w = ((uint64_t)c[3] << 32) | c[2];
+    const double u1 = ((double)(a >> 11) + 0.5) * 0x1p-53;
+    const double u2 = (double)(w >> 11) * 0x1p-53 + 0x1p-54;
+    const double rho = sqrt(-2.0 * log(u1));
+    double sn, cs;
+    sincospi(2.0 * u2, &sn, &cs);
+    J.out[2 * m] = rho * cs;
+    if (2 * m + 1 < n) J.out[2 * m + 1] = rho * sn;
+  }
+}
+void omega_batched(tlr_ctx* ctx, std::vector<OmegaJob>& jobs) {
+  if (jobs.empty()) return;
+  int mx = 0;
+  for (auto& j : jobs) mx = std::max(mx, j.b * j.bs);
+  const OmegaJob* dj = static_cast<const OmegaJob*>(upload(ctx, jobs.data(), jobs.size() * sizeof(OmegaJob)));
+  dim3 grid(std::min<unsigned>(cdiv((mx + 1) / 2, 256), 64u), (unsigned)jobs.size());
+  k_omega_batched<<<grid, 256, 0, ctx->stream>>>(dj);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// Batched FP32 -> FP64 conversion.
+__global__ void k_batched_to_double(const ConvBackJob* __restrict__ jobs) {
+  const ConvBackJob J = jobs[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < J.n; e += (int64_t)gridDim.x * blockDim.x)
+    J.dst[e] = (double)J.src[e];
+}
+void batched_to_double(tlr_ctx* ctx, std::vector<ConvBackJob>& jobs) {
+  std::vector<ConvBackJob> nz;
+  int64_t mx = 0;
+  for (auto& j : jobs)
+    if (j.n > 0) { nz.push_back(j); mx = std::max(mx, j.n); }
+  for (size_t o = 0; o < nz.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
+    const ConvBackJob* dj = static_cast<const ConvBackJob*>(upload(ctx, nz.data() + o, cnt * sizeof(ConvBackJob)));
+    dim3 grid(std::min<unsigned>(cdiv(mx, 256), 64u), (unsigned)cnt);
+    k_batched_to_double<<<grid, 256, 0, ctx->stream>>>(dj);
+    TLR_LAUNCH_CHECK(ctx);
+  }
+}
+
+// Batched row scaling Y = diag(d)^{+-1} X (LDL^T: D_j V_kj, and V = D^{-1} L^{-1} B).
+__global__ void k_batched_scale_rows(const ScaleJob* __restrict__ jobs) {
+  const ScaleJob J = jobs[blockIdx.y];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)J.m * J.n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % J.m), c = (int)(e / J.m);
+    const double s = J.inv ? 1.0 / J.d[r] : J.d[r];
+    J.Y[r + (size_t)c * J.ldy] = J.X[r + (size_t)c * J.ldx] * s;
+  }
+}
+void batched_scale_rows(tlr_ctx* ctx, std::vector<ScaleJob>& jobs) {
+  std::vector<ScaleJob> nz;
+  int64_t mx = 0;
+  for (auto& j : jobs)
+    if ((int64_t)j.m * j.n > 0) { nz.push_back(j); mx = std::max(mx, (int64_t)j.m * j.n); }
+  for (size_t o = 0; o < nz.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
+    const ScaleJob* dj = static_cast<const ScaleJob*>(upload(ctx, nz.data() + o, cnt * sizeof(ScaleJob)));
+    dim3 grid(std::min<unsigned>(cdiv(mx, 256), 128u), (unsigned)cnt);
+    k_batched_scale_rows<<<grid, 256, 0, ctx->stream>>>(dj);
+    TLR_LAUNCH_CHECK(ctx);
+  }
+}
+
+// Batched diagonal shift A_ii += s.
+__global__ void k_batched_add_diag(const DiagJob* __restrict__ jobs) {
+  const DiagJob J = jobs[blockIdx.y];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.n; i += gridDim.x * blockDim.x)
+    J.A[i + (size_t)i * J.lda] += J.s;
+}
+void batched_add_diag(tlr_ctx* ctx, std::vector<DiagJob>& jobs) {
+  if (jobs.empty()) return;
+  int mx = 0;
+  for (auto& j : jobs) mx = std::max(mx, j.n);
+  for (size_t o = 0; o < jobs.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, jobs.size() - o);
+    const DiagJob* dj = static_cast<const DiagJob*>(upload(ctx, jobs.data() + o, cnt * sizeof(DiagJob)));
+    dim3 grid(std::min<unsigned>(cdiv(mx, 256), 16u), (unsigned)cnt);
+    k_batched_add_diag<<<grid, 256, 0, ctx->stream>>>(dj);
+    TLR_LAUNCH_CHECK(ctx);
+  }
+}
 
 // ------------------------------------------------------------------ FP64 peak probe
 __global__ void k_dfma_loop(double* out, int iters, double a, double b) {

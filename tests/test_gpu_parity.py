@@ -358,3 +358,78 @@ def test_mixed_precision_falls_back_to_fp64_below_1e4(T, ctx):
     F64 = A.copy().potrf(w["eps"], T.default_opts(bs=w["bs"], seed=7))
     assert np.array_equal(F32.ranks(), F64.ranks())
     assert F32.logdet()[0] == F64.logdet()[0]
+
+
+# ------------------------------------------------------------------ batched factorization of many matrices
+BATCH = [dict(N=1500, d=2, ell=0.1, b=256, eps=1e-6, seed=31), dict(N=2048, d=3, ell=0.2, b=256, eps=1e-4, seed=32),
+         dict(N=700, d=2, ell=0.05, b=128, eps=1e-7, seed=33), dict(N=1024, d=3, ell=0.3, b=128, eps=1e-5, seed=34)]
+
+
+def _batch_inputs(T, ctx, specs, prec=0):
+    mats, eps, opts = [], [], []
+    for sp in specs:
+        x = inputs.points(sp["N"], sp["d"], sp["seed"])
+        o = T.default_opts(bs=16, seed=sp["seed"], precision=prec)
+        mats.append(ctx.compress(x, sp["b"], sp["eps"], sp["ell"], 1e-4, o))
+        eps.append(sp["eps"])
+        opts.append(o)
+    return mats, eps, opts
+
+
+@pytest.mark.parametrize("ldl", [False, True])
+def test_batch_equals_individual_bitwise(T, ctx, ldl):
+    """A matrix factored inside a batch gives bit-identical factors to the same matrix alone."""
+    mats, eps, opts = _batch_inputs(T, ctx, BATCH)
+    alone = []
+    for A, e, o in zip(mats, eps, opts):
+        F = A.copy()
+        (F.ldlt if ldl else F.potrf)(e, o)
+        alone.append(F)
+    batch = [A.copy() for A in mats]
+    st = ctx.factor_batch(batch, eps, opts, ldl=ldl)
+    assert st == [0] * len(batch)
+    for F, G in zip(alone, batch):
+        assert np.array_equal(F.ranks(), G.ranks())
+        assert F.logdet() == G.logdet()
+        nb = F.info()["nb"]
+        for (i, j) in [(nb - 1, 0), (nb - 1, nb - 2), (1, 0)]:
+            if i > j:
+                a, g = F.tile(i, j), G.tile(i, j)
+                assert np.array_equal(a[0], g[0]) and np.array_equal(a[1], g[1])
+        assert np.array_equal(F.tile(nb - 1, nb - 1)[0], G.tile(nb - 1, nb - 1)[0])
+
+
+def test_batch_matches_oracle(T, ctx):
+    mats, eps, opts = _batch_inputs(T, ctx, BATCH)
+    st = ctx.factor_batch(mats, eps, opts)
+    assert st == [0] * len(mats)
+    for sp, F in zip(BATCH, mats):
+        x = inputs.points(sp["N"], sp["d"], sp["seed"])
+        Ao = tlr.build(x, sp["b"], sp["eps"], sp["ell"], 1e-4, compressor="ara", bs=16, seed=sp["seed"])
+        Fo = tlr.factor(Ao, sp["eps"], compressor="ara", bs=16, seed=sp["seed"])
+        assert np.array_equal(F.ranks(), Fo.ranks())
+        assert abs(F.logdet()[0] - tlr.logdet(Fo)) <= 1e-10 * abs(tlr.logdet(Fo))
+
+
+def test_batch_isolates_a_failing_matrix(T, ctx):
+    mats, eps, opts = _batch_inputs(T, ctx, BATCH)
+    ref = []
+    for A, e, o in zip(mats, eps, opts):
+        ref.append(A.copy().potrf(e, o).logdet()[0])
+    bad = T.default_opts(bs=16, seed=BATCH[1]["seed"], compensation=T.COMP_SHIFT, shift=-5.0)
+    opts2 = list(opts)
+    opts2[1] = bad
+    st = ctx.factor_batch(mats, eps, opts2)
+    assert st[1] == T.ERR_NOT_SPD and mats[1].info()["state"] == 3
+    for m in (0, 2, 3):
+        assert st[m] == 0 and mats[m].logdet()[0] == ref[m]
+
+
+def test_batch_mixed_precision(T, ctx):
+    specs = [dict(s, eps=1e-2) for s in BATCH]
+    mats, eps, opts = _batch_inputs(T, ctx, specs, prec=1)
+    alone = [A.copy().potrf(e, o) for A, e, o in zip(mats, eps, opts)]
+    st = ctx.factor_batch(mats, eps, opts)
+    assert st == [0] * len(mats)
+    for F, G in zip(alone, mats):
+        assert np.array_equal(F.ranks(), G.ranks()) and F.logdet() == G.logdet()
