@@ -142,6 +142,24 @@ tlr_status tlr_ldlt(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts);
 tlr_status tlr_factor_batch(tlr_ctx* ctx, int count, tlr_mat** A, const double* eps, const tlr_opts* opts,
                             int ldl, tlr_status* status);
 
+/* Continuous batching of factorizations (no counterpart in the paper: the
+ * serving loop of a many-request deployment).  A session holds factorizations in
+ * flight; tlr_session_step advances every unfinished one by one column, all of
+ * them in the same launches (each matrix at its own column index), and matrices
+ * may be added between steps.  A matrix added to a session is factored in place
+ * (Cholesky if ldl == 0, else LDL^T) exactly as tlr_potrf / tlr_ldlt would: same
+ * result bit for bit.  All matrices of a session use one ARA block width. */
+typedef struct tlr_session tlr_session;
+tlr_status tlr_session_create(tlr_ctx* ctx, tlr_session** s);
+tlr_status tlr_session_destroy(tlr_session* s);
+/* Queue A (state "A") for factorization; *ticket identifies it in this session. */
+tlr_status tlr_session_add(tlr_session* s, tlr_mat* A, double eps, const tlr_opts* opts, int ldl, int* ticket);
+/* One column step of every unfinished factorization; *unfinished (may be NULL)
+ * receives how many remain. */
+tlr_status tlr_session_step(tlr_session* s, int* unfinished);
+/* *finished = 1 once the ticket's factorization ended; *result its status. */
+tlr_status tlr_session_poll(tlr_session* s, int ticket, int* finished, tlr_status* result);
+
 /* Solve (L L^T) X = B or (L D L^T) X = B with the TLR triangular solve of
  * Algorithm 7 (forward) and its transpose (backward).  B: device, N x nrhs,
  * leading dimension ldb >= N, original point order; overwritten with X. */

@@ -80,6 +80,11 @@ def _load():
                                            C.POINTER(Opts), C.POINTER(P)]),
         "tlr_gemm_stats": (C.c_int, [P, C.c_int, D, D, C.POINTER(C.c_int64)]),
         "tlr_factor_batch": (C.c_int, [P, C.c_int, C.POINTER(P), D, C.POINTER(Opts), C.c_int, C.POINTER(C.c_int)]),
+        "tlr_session_create": (C.c_int, [P, C.POINTER(P)]),
+        "tlr_session_destroy": (C.c_int, [P]),
+        "tlr_session_add": (C.c_int, [P, P, C.c_double, C.POINTER(Opts), C.c_int, C.POINTER(C.c_int)]),
+        "tlr_session_step": (C.c_int, [P, C.POINTER(C.c_int)]),
+        "tlr_session_poll": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "tlr_potrf": (C.c_int, [P, P, C.c_double, C.POINTER(Opts)]),
         "tlr_ldlt": (C.c_int, [P, P, C.c_double, C.POINTER(Opts)]),
         "tlr_solve": (C.c_int, [P, P, C.c_int, P, C.c_int64]),
@@ -304,6 +309,45 @@ class Context:
         v = C.c_double(0)
         _check(_load().tlr_fp64_peak(self.h, C.byref(v)), "tlr_fp64_peak")
         return v.value
+
+
+class Session:
+    """Factorizations in flight (continuous batching): add() between step() calls."""
+
+    def __init__(self, ctx: "Context"):
+        self.ctx = ctx
+        h = P()
+        _check(_load().tlr_session_create(ctx.h, C.byref(h)), "tlr_session_create")
+        self.h = h
+        self.mats = {}
+
+    def add(self, A: "Matrix", eps: float, opts: Opts | None = None, ldl: bool = False) -> int:
+        t = C.c_int(0)
+        _check(_load().tlr_session_add(self.h, A.h, eps, C.byref(opts) if opts else None, int(ldl), C.byref(t)),
+               "tlr_session_add")
+        self.mats[t.value] = A
+        return t.value
+
+    def step(self) -> int:
+        n = C.c_int(0)
+        _check(_load().tlr_session_step(self.h, C.byref(n)), "tlr_session_step")
+        return n.value
+
+    def poll(self, ticket: int) -> tuple[bool, int]:
+        f, st = C.c_int(0), C.c_int(0)
+        _check(_load().tlr_session_poll(self.h, ticket, C.byref(f), C.byref(st)), "tlr_session_poll")
+        return bool(f.value), st.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _load().tlr_session_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Matrix:

@@ -13,6 +13,7 @@
 // (keyed by its seed), and every reduction has a fixed order, so a matrix's result
 // does not depend on the other matrices of the batch.
 #include <chrono>
+#include <cstdio>
 #include <memory>
 #include <numeric>
 
@@ -35,7 +36,10 @@ struct Mat {
   tlr_status st = TLR_OK;
   bool live = true;
   int nb = 0, b = 0;
-  // column state
+  // column state: this matrix is at column k (matrices of one step may be at different columns)
+  int k = 0;
+  bool done = false, stepped = false;
+  std::chrono::steady_clock::time_point t0;
   int Kk = 0;
   std::vector<int64_t> goff;
   std::vector<int> gld;
@@ -76,7 +80,7 @@ struct Panels<float> {
 template <typename T>
 struct BatchSampler : Sampler {
   tlr_ctx* ctx = nullptr;
-  int bs = 0, k = 0;
+  int bs = 0;
   std::vector<Mat*>* L = nullptr;          // matrices of this column step
   const std::vector<int>* op_m = nullptr;  // operand -> index into L
   const std::vector<int>* op_i = nullptr;  // operand -> tile row i
@@ -113,7 +117,7 @@ struct BatchSampler : Sampler {
     std::vector<OmegaJob> oj;
     for (size_t u = 0; u < mp.size(); ++u) {
       const Mat& M = *(*L)[mp[u]];
-      oj.push_back(OmegaJob{Om + omo[u], M.o.seed, STREAM_FACTOR, (uint32_t)k, (uint32_t)t, M.b, bs});
+      oj.push_back(OmegaJob{Om + omo[u], M.o.seed, STREAM_FACTOR, (uint32_t)M.k, (uint32_t)t, M.b, bs});
     }
     omega_batched(ctx, oj);
     const T* OmT = reinterpret_cast<const T*>(Om);
@@ -127,9 +131,9 @@ struct BatchSampler : Sampler {
     for (size_t u = 0; u < mp.size(); ++u) {
       Mat& M = *(*L)[mp[u]];
       if (M.Kk > 0)
-        jx.push_back(job<T>(TN, M.Kk, bs, Panels<T>::U(M, k), M.b, OmT + omo[u], M.b, M.b, X + xo[u], M.Kk, 1.0, 0.0));
+        jx.push_back(job<T>(TN, M.Kk, bs, Panels<T>::U(M, M.k), M.b, OmT + omo[u], M.b, M.b, X + xo[u], M.Kk, 1.0, 0.0));
       if (M.R0k > 0)
-        jx.push_back(job<T>(TN, (int)M.R0k, bs, Panels<T>::AV(M, k), M.b, OmT + omo[u], M.b, M.b, X + x0o[u],
+        jx.push_back(job<T>(TN, (int)M.R0k, bs, Panels<T>::AV(M, M.k), M.b, OmT + omo[u], M.b, M.b, X + x0o[u],
                             (int)M.R0k, 1.0, 0.0));
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * bs * (M.Kk + M.R0k);
     }
@@ -137,6 +141,7 @@ struct BatchSampler : Sampler {
     // W blocks of every operand (block-diagonal Gram products), then Y = [U0 | Urow] W
     std::vector<SlotDescT<T>> sd(ops.size());
     int64_t wtot = 0, ytot = 0;
+    int kmx = 0;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], u = slot_of_m[(*op_m)[op]], i = (*op_i)[op];
       const Mat& M = *(*L)[(*op_m)[op]];
@@ -152,10 +157,11 @@ struct BatchSampler : Sampler {
       d.ldx = std::max(M.Kk, 1);
       d.ldx0 = (int)std::max<int64_t>(M.R0k, 1);
       d.nb = M.nb;
-      d.k = k;
+      d.k = M.k;
+      kmx = std::max(kmx, M.k);
       d.i = i;
-      d.r0 = M.A->rank[ix(M.A, i, k)];
-      d.x0off = (int)M.A->voff[ix(M.A, i, k)];
+      d.r0 = M.A->rank[ix(M.A, i, M.k)];
+      d.x0off = (int)M.A->voff[ix(M.A, i, M.k)];
       d.Ki = (int)M.F->ulen[i];
       d.Kk = M.Kk;
       d.q = bs;
@@ -169,7 +175,7 @@ struct BatchSampler : Sampler {
     T* W = bw->need<T>((size_t)std::max<int64_t>(wtot, 1));
     for (auto& d : sd) d.W = W + reinterpret_cast<size_t>(d.W);
     const SlotDescT<T>* sdd = static_cast<const SlotDescT<T>*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDescT<T>)));
-    blkdiag_sample<T>(ctx, (int)ops.size(), k, sdd);
+    blkdiag_sample<T>(ctx, (int)ops.size(), kmx, sdd);
     T* Y32 = F32 ? reinterpret_cast<T*>(by32->need<float>((size_t)ytot)) : nullptr;
     std::vector<GemmJob<T>> jy;
     std::vector<ConvBackJob> cb;
@@ -179,7 +185,7 @@ struct BatchSampler : Sampler {
       Mat& M = *(*L)[(*op_m)[op]];
       const int r0 = sd[s].r0, Ki = sd[s].Ki, ldw = std::max(r0 + Ki, 1);
       T* Yo = F32 ? Y32 + yo : reinterpret_cast<T*>(Ydst[s]);
-      const T* U0 = r0 ? Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, k)] : nullptr;
+      const T* U0 = r0 ? Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)] : nullptr;
       GemmJob<T> g = job<T>(NN, M.b, bs, U0, M.b, sd[s].W, ldw, r0, Yo, M.b, 1.0, 0.0);
       g.A[1] = Panels<T>::U(M, i);
       g.lda[1] = M.b;
@@ -191,7 +197,7 @@ struct BatchSampler : Sampler {
       yo += (int64_t)M.b * bs;
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * bs * (r0 + Ki);
       double R = r0;  // paper model: 4 products per (i, j) pair, Equation 2
-      for (int j = 0; j < k; ++j) R += M.F->rank[ix(M.F, i, j)] + M.F->rank[ix(M.F, k, j)];
+      for (int j = 0; j < M.k; ++j) R += M.F->rank[ix(M.F, i, j)] + M.F->rank[ix(M.F, M.k, j)];
       M.fl_model += 4.0 * M.b * bs * R;
       (F32 ? M.t32 : M.t64) += 1;
     }
@@ -207,6 +213,7 @@ struct BatchSampler : Sampler {
     if (ops.empty()) return;
     std::vector<SlotDescT<T>> sd(ops.size());
     int64_t ptot = 0, ztot = 0, q32tot = 0;
+    int kmx = 0;
     std::vector<int64_t> q32o(ops.size());
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
@@ -219,9 +226,10 @@ struct BatchSampler : Sampler {
       d.gld = M.dgld;
       d.G = Panels<T>::G(M);
       d.nb = M.nb;
-      d.k = k;
+      d.k = M.k;
+      kmx = std::max(kmx, M.k);
       d.i = i;
-      d.r0 = M.A->rank[ix(M.A, i, k)];
+      d.r0 = M.A->rank[ix(M.A, i, M.k)];
       d.Ki = (int)M.F->ulen[i];
       d.Kk = M.Kk;
       d.q = q[op];
@@ -262,7 +270,7 @@ struct BatchSampler : Sampler {
       Mat& M = *(*L)[(*op_m)[op]];
       const int r0 = sd[s].r0, Ki = sd[s].Ki, ldp = r0 + Ki;
       if (r0 > 0)
-        jp.push_back(job<T>(TN, r0, q[op], Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, k)], M.b, Qop(s),
+        jp.push_back(job<T>(TN, r0, q[op], Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)], M.b, Qop(s),
                             M.b, M.b, sd[s].P, ldp, 1.0, 0.0));
       if (Ki > 0)
         jp.push_back(job<T>(TN, Ki, q[op], Panels<T>::U(M, i), M.b, Qop(s), M.b, M.b, sd[s].P + r0, ldp, 1.0, 0.0));
@@ -270,7 +278,7 @@ struct BatchSampler : Sampler {
     }
     gemm<T>(ctx, TN, jp);
     const SlotDescT<T>* sdd = static_cast<const SlotDescT<T>*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDescT<T>)));
-    blkdiag_project<T>(ctx, (int)ops.size(), k, sdd);
+    blkdiag_project<T>(ctx, (int)ops.size(), kmx, sdd);
     std::vector<GemmJob<T>> jb;
     std::vector<ConvBackJob> cb;
     for (size_t s = 0; s < ops.size(); ++s) {
@@ -279,9 +287,9 @@ struct BatchSampler : Sampler {
       const int r0 = sd[s].r0, ldz = std::max(r0 + M.Kk, 1);
       double* Bdst = static_cast<double*>(M.Bc.p) + (size_t)M.boff[op - M.op0] * M.b;
       T* Bo = F32 ? reinterpret_cast<T*>(B32 + q32o[s]) : reinterpret_cast<T*>(Bdst);
-      const T* V0 = r0 ? Panels<T>::AV(M, k) + (size_t)M.b * M.A->voff[ix(M.A, i, k)] : nullptr;
+      const T* V0 = r0 ? Panels<T>::AV(M, M.k) + (size_t)M.b * M.A->voff[ix(M.A, i, M.k)] : nullptr;
       GemmJob<T> g = job<T>(NN, M.b, q[op], V0, M.b, sd[s].Z, ldz, r0, Bo, M.b, 1.0, 0.0);
-      g.A[1] = Panels<T>::U(M, k);
+      g.A[1] = Panels<T>::U(M, M.k);
       g.lda[1] = M.b;
       g.B[1] = sd[s].Z + r0;
       g.ldb[1] = ldz;
@@ -290,7 +298,7 @@ struct BatchSampler : Sampler {
       if (F32) cb.push_back(ConvBackJob{reinterpret_cast<const float*>(Bo), Bdst, (int64_t)M.b * q[op]});
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * q[op] * (r0 + M.Kk);
       double R = r0;
-      for (int j = 0; j < k; ++j) R += M.F->rank[ix(M.F, i, j)] + M.F->rank[ix(M.F, k, j)];
+      for (int j = 0; j < M.k; ++j) R += M.F->rank[ix(M.F, i, j)] + M.F->rank[ix(M.F, M.k, j)];
       M.fl_model += 4.0 * M.b * q[op] * R;
     }
     gemm<T>(ctx, NN, jb);
@@ -350,40 +358,59 @@ void free_f32(tlr_ctx* ctx, Mat& M) {
 
 }  // namespace
 
-void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std::vector<double>& eps_in,
-                  const std::vector<tlr_opts>& opts, int ldl, std::vector<tlr_status>& status) {
-  const auto t_start = std::chrono::steady_clock::now();
-  const int nm = (int)mats_in.size();
-  status.assign(nm, TLR_OK);
-  if (nm == 0) return;
-  const int bs = opts[0].bs;
-  for (auto& o : opts) TLR_REQUIRE(o.bs == bs, TLR_ERR_ARG, "all matrices of a batch use one ARA block width");
+// A set of factorizations in flight: matrices join with add(), every step() advances
+// each unfinished matrix by one column (each at its own column index), finished
+// matrices leave.  factor_batch is add() of all matrices then step() until done;
+// the serving loop adds requests between steps (continuous batching).
+struct Session {
+  tlr_ctx* ctx;
+  int bs = -1;
   std::vector<std::unique_ptr<Mat>> mats;
-  Buf bnrm(ctx);
-  int kmax = 0;
-  for (int m = 0; m < nm; ++m) {
+  Buf bnrm, bQ, bTab, bInfo, bTmp, bOm, bOm32, bX, bW, bY32, bP, bZ, bQ32, bB32;
+  AraStats total;
+  explicit Session(tlr_ctx* c)
+      : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bOm(c), bOm32(c), bX(c), bW(c), bY32(c), bP(c), bZ(c),
+        bQ32(c), bB32(c) {}
+  ~Session() {
+    cudaStreamSynchronize(ctx->side);
+    cudaStreamSynchronize(ctx->main);
+    for (auto& M : mats) {
+      free_f32(ctx, *M);
+      if (M->F) mat_destroy(ctx, M->F);
+    }
+  }
+  bool busy() const {
+    for (auto& M : mats)
+      if (M->live && !M->done) return true;
+    return false;
+  }
+
+  int add(tlr_mat* A, double eps, const tlr_opts& o, int ldl) {
+    if (bs < 0) bs = o.bs;
+    TLR_REQUIRE(o.bs == bs, TLR_ERR_ARG, "all matrices of a batch use one ARA block width");
     mats.emplace_back(new Mat(ctx));
     Mat& M = *mats.back();
-    M.A = mats_in[m];
-    M.eps = eps_in[m];
-    M.thr = eps_in[m] / HALKO;
-    M.o = opts[m];
+    M.t0 = std::chrono::steady_clock::now();
+    M.A = A;
+    M.eps = eps;
+    M.thr = eps / HALKO;
+    M.o = o;
     M.ldl = ldl;
-    M.nb = M.A->nb;
-    M.b = M.A->b;
-    M.mixed = M.o.precision == TLR_PREC_FP32 && M.eps >= 1e-4;
-    kmax = std::max(kmax, M.nb);
+    M.nb = A->nb;
+    M.b = A->b;
+    M.k = 0;
+    M.mixed = o.precision == TLR_PREC_FP32 && eps >= 1e-4;
     const int nb = M.nb, b = M.b;
-    tlr_mat* F = mat_new(M.A->N, M.A->d, b);
+    tlr_mat* F = mat_new(A->N, A->d, b);
     M.F = F;
-    F->kern = M.A->kern;
-    F->eps = M.eps;
+    F->kern = A->kern;
+    F->eps = eps;
     F->diag = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
-    TLR_CUDA(cudaMemcpyAsync(F->diag, M.A->diag, sizeof(double) * (size_t)nb * b * b, cudaMemcpyDeviceToDevice,
+    TLR_CUDA(cudaMemcpyAsync(F->diag, A->diag, sizeof(double) * (size_t)nb * b * b, cudaMemcpyDeviceToDevice,
                              ctx->stream));
     if (ldl) F->dvec = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b));
     F->dinv = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
-    for (int i = 0; i < nb; ++i) ensure_ucap(ctx, F, i, std::max<int64_t>(M.A->ulen[i], 16));
+    for (int i = 0; i < nb; ++i) ensure_ucap(ctx, F, i, std::max<int64_t>(A->ulen[i], 16));
     if (M.mixed) {  // FP32 copies of A's panels; tile norms for the precision rule
       M.AU32.assign(nb, nullptr);
       M.AV32.assign(nb, nullptr);
@@ -392,44 +419,81 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       M.fu32cap.assign(nb, 0);
       std::vector<ConvJob> cj;
       for (int i = 0; i < nb; ++i) {
-        M.AU32[i] = f32_alloc(ctx, (int64_t)b * M.A->ulen[i]);
-        M.AV32[i] = f32_alloc(ctx, (int64_t)b * M.A->vlen[i]);
-        cj.push_back(ConvJob{M.A->Urow[i], M.AU32[i], (int64_t)b * M.A->ulen[i]});
-        cj.push_back(ConvJob{M.A->Vcol[i], M.AV32[i], (int64_t)b * M.A->vlen[i]});
+        M.AU32[i] = f32_alloc(ctx, (int64_t)b * A->ulen[i]);
+        M.AV32[i] = f32_alloc(ctx, (int64_t)b * A->vlen[i]);
+        cj.push_back(ConvJob{A->Urow[i], M.AU32[i], (int64_t)b * A->ulen[i]});
+        cj.push_back(ConvJob{A->Vcol[i], M.AV32[i], (int64_t)b * A->vlen[i]});
         M.fu32cap[i] = F->ucap[i];
         M.FU32[i] = f32_alloc(ctx, (int64_t)b * M.fu32cap[i]);
       }
       batched_to_float(ctx, cj);
       M.nA.assign((size_t)nb * nb, 0.0);
       M.nL.assign((size_t)nb * nb, 0.0);
-      for (int j = 0; j < nb; ++j) panel_tile_norms(ctx, M.A, j, M.nA, bnrm);
+      for (int j = 0; j < nb; ++j) panel_tile_norms(ctx, A, j, M.nA, bnrm);
     }
+    return (int)mats.size() - 1;
   }
-  struct Cleanup {  // FP32 copies and unfinished factors are released on every exit path
-    tlr_ctx* ctx;
-    std::vector<std::unique_ptr<Mat>>* mats;
-    ~Cleanup() {
-      cudaStreamSynchronize(ctx->side);
-      for (auto& M : *mats) {
-        free_f32(ctx, *M);
-        if (M->F) mat_destroy(ctx, M->F);
+
+  tlr_status status(int idx) const { return mats[idx]->st; }
+  bool finished(int idx) const { return mats[idx]->done || !mats[idx]->live; }
+
+  // A := its factor (the matrix finished its last column).
+  void finalize(Mat& M) {
+    TLR_CUDA(cudaStreamSynchronize(ctx->main));
+    free_f32(ctx, M);
+    tlr_mat* A = M.A;
+    tlr_mat* F = M.F;
+    const int nb = M.nb;
+    mat_free_storage(ctx, A);
+    dfree(ctx, A->diag);
+    dfree(ctx, A->dvec);
+    dfree(ctx, A->dinv);
+    A->diag = F->diag; F->diag = nullptr;
+    A->dvec = F->dvec; F->dvec = nullptr;
+    A->dinv = F->dinv; F->dinv = nullptr;
+    A->rank = F->rank; A->uoff = F->uoff; A->voff = F->voff;
+    A->Urow = F->Urow; A->Vcol = F->Vcol; A->ucap = F->ucap; A->vlen = F->vlen; A->ulen = F->ulen;
+    F->Urow.assign(nb, nullptr);
+    F->Vcol.assign(nb, nullptr);
+    mat_destroy(ctx, F);
+    M.F = nullptr;
+    A->state = M.ldl ? 2 : 1;
+    A->k_fail = -1;
+    A->eps = M.eps;
+    A->flops_exec = M.fl_exec;
+    A->flops_model = M.fl_model;
+    A->flops_fp32 = M.fl32;
+    A->ara_rounds = (double)(M.t32 + M.t64);
+    A->tiles_fp32 = M.mixed ? (double)M.t32 : 0.0;
+    A->tiles_fp64 = M.mixed ? (double)M.t64 : 0.0;
+    A->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - M.t0).count();
+    M.done = true;
+  }
+
+  void step() {
+    step_columns();
+    for (auto& Mp : mats) {
+      Mat& M = *Mp;
+      if (!M.live) {
+        if (M.F) {
+          free_f32(ctx, M);
+          mat_destroy(ctx, M.F);
+          M.F = nullptr;
+        }
+        continue;
       }
+      if (M.done || !M.stepped) continue;
+      M.stepped = false;
+      if (++M.k == M.nb) finalize(M);
     }
-  } cleanup{ctx, &mats};
+    prof_flush(ctx);
+  }
 
-  Buf bQ(ctx), bTab(ctx), bInfo(ctx), bTmp(ctx), bOm(ctx), bOm32(ctx), bX(ctx), bW(ctx), bY32(ctx), bP(ctx), bZ(ctx),
-      bQ32(ctx), bB32(ctx);
-  int* info = bInfo.need<int>((size_t)nm);
-  int64_t tmp_need = 0;
-  for (auto& M : mats) tmp_need += (int64_t)M->b * NBK;
-  bTmp.need<double>((size_t)tmp_need);  // sized once: the side stream never reallocates it
-  AraStats total;
-
-  for (int k = 0; k < kmax; ++k) {
+  void step_columns() {
     std::vector<Mat*> L;
     for (auto& M : mats)
-      if (M->live && k < M->nb) L.push_back(M.get());
-    if (L.empty()) break;
+      if (M->live && !M->done) L.push_back(M.get());
+    if (L.empty()) return;
     // ---------------------------------------------------------------- Gram factors
     prof_mark(ctx, PH_GRAM);
     {
@@ -441,30 +505,30 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
         Mat& M = *Mp;
         tlr_mat* F = M.F;
         const int b = M.b;
-        M.Kk = (int)F->ulen[k];
-        M.R0k = M.A->vlen[k];
-        M.goff.assign(std::max(k, 1), 0);
-        M.gld.assign(std::max(k, 1), 1);
+        M.Kk = (int)F->ulen[M.k];
+        M.R0k = M.A->vlen[M.k];
+        M.goff.assign(std::max(M.k, 1), 0);
+        M.gld.assign(std::max(M.k, 1), 1);
         M.gtot = 0;
         int64_t dvtot = 0;
-        for (int j = 0; j < k; ++j) {
+        for (int j = 0; j < M.k; ++j) {
           M.goff[j] = M.gtot;
-          M.gld[j] = (int)std::max<int64_t>(1, F->vlen[j] - F->voff[ix(F, k, j)]);
-          M.gtot += (int64_t)M.gld[j] * F->rank[ix(F, k, j)];
-          dvtot += (int64_t)b * F->rank[ix(F, k, j)];
+          M.gld[j] = (int)std::max<int64_t>(1, F->vlen[j] - F->voff[ix(F, M.k, j)]);
+          M.gtot += (int64_t)M.gld[j] * F->rank[ix(F, M.k, j)];
+          dvtot += (int64_t)b * F->rank[ix(F, M.k, j)];
         }
         double* G = M.G.need<double>((size_t)std::max<int64_t>(M.gtot, 1));
         float* G32 = M.mixed ? M.G32.need<float>((size_t)std::max<int64_t>(M.gtot, 1)) : nullptr;
-        double* DV = ldl ? M.DV.need<double>((size_t)std::max<int64_t>(dvtot, 1)) : nullptr;
-        float* DV32 = (ldl && M.mixed) ? M.DV32.need<float>((size_t)std::max<int64_t>(dvtot, 1)) : nullptr;
+        double* DV = M.ldl ? M.DV.need<double>((size_t)std::max<int64_t>(dvtot, 1)) : nullptr;
+        float* DV32 = (M.ldl && M.mixed) ? M.DV32.need<float>((size_t)std::max<int64_t>(dvtot, 1)) : nullptr;
         int64_t dvo = 0;
-        for (int j = 0; j < k; ++j) {
-          const int rkj = F->rank[ix(F, k, j)];
+        for (int j = 0; j < M.k; ++j) {
+          const int rkj = F->rank[ix(F, M.k, j)];
           if (rkj == 0) continue;
-          const int S = (int)(F->vlen[j] - F->voff[ix(F, k, j)]);
-          const double* Vkj = Vptr(F, k, j);
-          const float* Vkj32 = M.mixed ? M.FV32[j] + (size_t)b * F->voff[ix(F, k, j)] : nullptr;
-          if (ldl) {  // D_j V_kj (Equation 3: D(j,j) inside the chain)
+          const int S = (int)(F->vlen[j] - F->voff[ix(F, M.k, j)]);
+          const double* Vkj = Vptr(F, M.k, j);
+          const float* Vkj32 = M.mixed ? M.FV32[j] + (size_t)b * F->voff[ix(F, M.k, j)] : nullptr;
+          if (M.ldl) {  // D_j V_kj (Equation 3: D(j,j) inside the chain)
             sj.push_back(ScaleJob{F->dvec + (size_t)j * b, Vkj, DV + dvo, b, rkj, b, b, 0});
             Vkj = DV + dvo;
             if (M.mixed) {
@@ -473,10 +537,10 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
             }
             dvo += (int64_t)b * rkj;
           }
-          jg.push_back(job<double>(TN, S, rkj, Vptr(F, k, j), b, Vkj, b, b, G + M.goff[j], M.gld[j], 1.0, 0.0));
+          jg.push_back(job<double>(TN, S, rkj, Vptr(F, M.k, j), b, Vkj, b, b, G + M.goff[j], M.gld[j], 1.0, 0.0));
           M.fl_exec += 2.0 * b * S * rkj;
           if (M.mixed)  // FP32 Gram for the tiles that sample in FP32
-            jg32.push_back(job<float>(TN, S, rkj, M.FV32[j] + (size_t)b * F->voff[ix(F, k, j)], b, Vkj32, b, b,
+            jg32.push_back(job<float>(TN, S, rkj, M.FV32[j] + (size_t)b * F->voff[ix(F, M.k, j)], b, Vkj32, b, b,
                                       G32 + M.goff[j], M.gld[j], 1.0, 0.0));
         }
       }
@@ -490,6 +554,14 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
     // updateDense, chol / LDL^T and inverse run on the side stream, overlapped with the
     // sampling rounds, and join before the trsm.  (Schur compensation runs a nested ARA
     // with its own workspaces and stays on the main stream.)
+    const int nm = (int)mats.size();
+    int* info = bInfo.need<int>((size_t)nm);
+    {  // the side stream must not reallocate its workspace: size it here
+      int64_t tn = 0;
+      for (Mat* Mp : L)
+        if (Mp->ldl) tn += (int64_t)Mp->b * NBK;
+      bTmp.need<double>((size_t)std::max<int64_t>(tn, 1));
+    }
     TLR_CUDA(cudaMemsetAsync(info, 0xff, sizeof(int) * nm, ctx->main));
     TLR_CUDA(cudaEventRecord(ctx->ev_fork, ctx->main));
     TLR_CUDA(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
@@ -502,23 +574,23 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       ctx->stream = pass == 0 ? ctx->side : ctx->main;
       std::vector<GemmJob<double>> je, jd;
       std::vector<DiagJob> shifts;
-      std::vector<DenseTile> tiles;
+      std::vector<DenseTile> tiles[2];  // by factorization kind (Cholesky, LDL^T)
       for (Mat* Mp : S) {
         Mat& M = *Mp;
         tlr_mat* F = M.F;
         const int b = M.b;
-        double* Akk = F->diag + (size_t)k * b * b;
+        double* Akk = F->diag + (size_t)M.k * b * b;
         const double* G = static_cast<const double*>(M.G.p);
         if (M.Kk > 0) {
           double* E = M.E.need<double>((size_t)b * M.Kk);
-          for (int j = 0; j < k; ++j) {
-            const int rkj = F->rank[ix(F, k, j)];
+          for (int j = 0; j < M.k; ++j) {
+            const int rkj = F->rank[ix(F, M.k, j)];
             if (rkj == 0) continue;
-            je.push_back(job<double>(NN, b, rkj, Uptr(F, k, j), b, G + M.goff[j], M.gld[j], rkj,
-                                     E + (size_t)b * F->uoff[ix(F, k, j)], b, 1.0, 0.0));
+            je.push_back(job<double>(NN, b, rkj, Uptr(F, M.k, j), b, G + M.goff[j], M.gld[j], rkj,
+                                     E + (size_t)b * F->uoff[ix(F, M.k, j)], b, 1.0, 0.0));
             M.fl_exec += 2.0 * b * rkj * rkj;
           }
-          GemmJob<double> g = job<double>(NT, b, b, E, b, F->Urow[k], b, M.Kk, Akk, b, -1.0, 1.0);
+          GemmJob<double> g = job<double>(NT, b, b, E, b, F->Urow[M.k], b, M.Kk, Akk, b, -1.0, 1.0);
           if (pass == 0) g.flags = GEMM_TRIL;
           M.fl_exec += (pass == 0 ? 1.0 : 2.0) * b * b * M.Kk;
           if (pass == 1) {  // full D_k into a scratch tile for the compensation
@@ -532,12 +604,12 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
         int mi = 0;
         for (; mi < nm; ++mi)
           if (mats[mi].get() == Mp) break;
-        tiles.push_back(DenseTile{Akk, ldl ? F->dvec + (size_t)k * b : nullptr, info + mi,
-                                  F->dinv + (size_t)k * b * b, b, b});
+        tiles[M.ldl].push_back(DenseTile{Akk, M.ldl ? F->dvec + (size_t)M.k * b : nullptr, info + mi,
+                                  F->dinv + (size_t)M.k * b * b, b, b});
         M.fl_exec += 2.0 * (double)b * b * b / 3.0;
         M.fl_model += (double)b * b * b / 3.0;
-        for (int j = 0; j < k; ++j) {
-          const int r = F->rank[ix(F, k, j)];
+        for (int j = 0; j < M.k; ++j) {
+          const int r = F->rank[ix(F, M.k, j)];
           M.fl_model += 4.0 * b * r * r + 2.0 * b * b * r;
         }
       }
@@ -550,7 +622,7 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
           Mat& M = *Mp;
           if (M.Kk == 0) continue;
           const int b = M.b;
-          double* Akk = M.F->diag + (size_t)k * b * b;
+          double* Akk = M.F->diag + (size_t)M.k * b * b;
           double* Dk = static_cast<double*>(M.DV.p);
           axpy_matrix(ctx, b, b, -1.0, Dk, b, Akk, b);
           Buf bq(ctx), bb(ctx), bc(ctx);
@@ -560,7 +632,7 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
           double* C2 = C1 + (size_t)b * b;
           std::vector<int> qd;
           AraStats as;
-          ara_dense_run(ctx, 1, b, Dk, bs, M.eps, M.o.seed, STREAM_SCHUR, (uint32_t)k, Qd, Bd, qd, as);
+          ara_dense_run(ctx, 1, b, Dk, bs, M.eps, M.o.seed, STREAM_SCHUR, (uint32_t)M.k, Qd, Bd, qd, as);
           const int r = qd[0];
           if (r > 0) {  // Bd = D Q (D symmetric): C1 = Q^T Bd, C2 = Q C1, E = D - C2 Q^T
             std::vector<GemmJob<double>> a1{job<double>(TN, r, r, Qd, b, Bd, b, b, C1, r, 1.0, 0.0)};
@@ -574,8 +646,10 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
         }
       }
       batched_add_diag(ctx, shifts);
-      dense_factor_batch(ctx, tiles, ldl, bTmp);
-      dense_trinv_batch(ctx, tiles, ldl);
+      for (int l = 0; l < 2; ++l) {
+        dense_factor_batch(ctx, tiles[l], l, bTmp);
+        dense_trinv_batch(ctx, tiles[l], l);
+      }
     }
     TLR_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));
     ctx->stream = ctx->main;
@@ -587,17 +661,17 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
     for (size_t u = 0; u < L.size(); ++u) {
       Mat& M = *L[u];
       M.op0 = (int)op_m.size();
-      M.nops = M.nb - k - 1;
+      M.nops = M.nb - M.k - 1;
       std::vector<int> ord(M.nops);
       std::iota(ord.begin(), ord.end(), 0);
       // tiles enter the batch by their original rank, descending (Algorithm 5 sortRanks)
       std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) {
-        return M.A->rank[ix(M.A, k + 1 + a, k)] > M.A->rank[ix(M.A, k + 1 + c, k)];
+        return M.A->rank[ix(M.A, M.k + 1 + a, M.k)] > M.A->rank[ix(M.A, M.k + 1 + c, M.k)];
       });
       for (int v : ord) order.push_back(M.op0 + v);
       for (int v = 0; v < M.nops; ++v) {
         op_m.push_back((int)u);
-        op_i.push_back(k + 1 + v);
+        op_i.push_back(M.k + 1 + v);
         nrow.push_back(M.b);
         thr.push_back(M.thr);
         qoff.push_back(qtot);
@@ -613,7 +687,7 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       int64_t tint = 0;
       for (size_t u = 0; u < L.size(); ++u) {
         toff[u] = tint;
-        tint += (int64_t)3 * L[u]->nb * L[u]->nb + 2 * std::max(k, 1) + 2 * std::max(k, 1);
+        tint += (int64_t)3 * L[u]->nb * L[u]->nb + 4 * std::max(L[u]->k, 1);
       }
       std::vector<int> htab((size_t)tint, 0);
       for (size_t u = 0; u < L.size(); ++u) {
@@ -627,9 +701,9 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
           t[2 * nb2 + e] = (int)F->voff[e];
         }
         int64_t* go = reinterpret_cast<int64_t*>(t + 3 * nb2);
-        for (int j = 0; j < std::max(k, 1); ++j) go[j] = M.goff[j];
-        int* gl = t + 3 * nb2 + 2 * std::max(k, 1);
-        for (int j = 0; j < std::max(k, 1); ++j) gl[j] = M.gld[j];
+        for (int j = 0; j < std::max(M.k, 1); ++j) go[j] = M.goff[j];
+        int* gl = t + 3 * nb2 + 2 * std::max(M.k, 1);
+        for (int j = 0; j < std::max(M.k, 1); ++j) gl[j] = M.gld[j];
       }
       int* dtab = bTab.need<int>((size_t)tint + 2);
       TLR_CUDA(cudaMemcpyAsync(dtab, htab.data(), sizeof(int) * tint, cudaMemcpyHostToDevice, ctx->stream));
@@ -639,7 +713,7 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
         const int nb2 = M.nb * M.nb;
         M.dtab = dtab + toff[u];
         M.dgoff = reinterpret_cast<const int64_t*>(dtab + toff[u] + 3 * nb2);
-        M.dgld = dtab + toff[u] + 3 * nb2 + 2 * std::max(k, 1);
+        M.dgld = dtab + toff[u] + 3 * nb2 + 2 * std::max(M.k, 1);
       }
       // per-tile precision rule (mixed precision): FP32 when u32 sqrt(K)(|A_ik|_F + sum_j
       // |L_ij|_F |L_kj|_F) <= thr / 8, else FP64
@@ -649,9 +723,9 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
         Mat& M = *L[op_m[op]];
         if (!M.mixed) continue;
         const int i = op_i[op];
-        double sum = M.nA[ix(M.A, i, k)];
-        for (int j = 0; j < k; ++j) sum += M.nL[ix(M.F, i, j)] * M.nL[ix(M.F, k, j)];
-        const double K = (double)M.A->rank[ix(M.A, i, k)] + (double)M.F->ulen[i] + bs;
+        double sum = M.nA[ix(M.A, i, M.k)];
+        for (int j = 0; j < M.k; ++j) sum += M.nL[ix(M.F, i, j)] * M.nL[ix(M.F, M.k, j)];
+        const double K = (double)M.A->rank[ix(M.A, i, M.k)] + (double)M.F->ulen[i] + bs;
         if (U32 * std::sqrt(K) * sum <= M.thr / 8.0) {
           is32[op] = 1;
           is64[op] = 0;
@@ -661,7 +735,7 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       BatchSampler<double> s64;
       BatchSampler<float> s32;
       auto setup = [&](auto& S, const std::vector<char>* mem) {
-        S.ctx = ctx; S.bs = bs; S.k = k; S.L = &L; S.op_m = &op_m; S.op_i = &op_i; S.member = mem;
+        S.ctx = ctx; S.bs = bs; S.L = &L; S.op_m = &op_m; S.op_i = &op_i; S.member = mem;
         S.Q = Q; S.qoff = &qoff;
         S.bom = &bOm; S.bom32 = &bOm32; S.bx = &bX; S.bw = &bW; S.by32 = &bY32; S.bp = &bP; S.bz = &bZ;
         S.bq32 = &bQ32; S.bb32 = &bB32;
@@ -685,7 +759,7 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       dsmp.f = smp;
       int max_slots = 0;
       for (Mat* Mp : L) max_slots += Mp->o.max_slots > 0 ? Mp->o.max_slots : Mp->nb;
-      AraConfig cf{bs, 0, STREAM_FACTOR, (uint32_t)k, max_slots};
+      AraConfig cf{bs, 0, STREAM_FACTOR, 0, max_slots};
       AraStats as;
       ara_run(ctx, dsmp, nrow, thr, cf, order, Q, qoff, q, as);
       total.rounds += as.rounds;
@@ -701,11 +775,11 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       TLR_CUDA(cudaStreamSynchronize(ctx->main));
       for (int mi = 0; mi < nm; ++mi) {
         Mat& M = *mats[mi];
-        if (M.live && k < M.nb && hinfo[mi] >= 0) {
+        if (M.live && !M.done && hinfo[mi] >= 0) {
           M.live = false;
           M.st = TLR_ERR_NOT_SPD;
           M.A->state = 3;
-          M.A->k_fail = k;
+          M.A->k_fail = M.k;
         }
       }
       // ---------------------------------------------------------------- projection (sampleLeftT)
@@ -740,11 +814,11 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       TLR_CUDA(cudaStreamSynchronize(ctx->main));
       for (int mi = 0; mi < nm; ++mi) {
         Mat& M = *mats[mi];
-        if (M.live && k < M.nb && hinfo[mi] >= 0) {
+        if (M.live && !M.done && hinfo[mi] >= 0) {
           M.live = false;
           M.st = TLR_ERR_NOT_SPD;
           M.A->state = 3;
-          M.A->k_fail = k;
+          M.A->k_fail = M.k;
         }
       }
     }
@@ -757,13 +831,13 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       if (!M.live || M.nops == 0) continue;
       tlr_mat* F = M.F;
       const int b = M.b;
-      F->Vcol[k] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(M.Rk, 1) * b));
-      F->vlen[k] = M.Rk;
+      F->Vcol[M.k] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(M.Rk, 1) * b));
+      F->vlen[M.k] = M.Rk;
       if (M.Rk > 0) {
         // V_ik = L_kk^{-1} B_i (LDL^T: then D_k^{-1}, batchIDMult)
-        jt.push_back(job<double>(NN, b, (int)M.Rk, F->dinv + (size_t)k * b * b, b, static_cast<double*>(M.Bc.p), b, b,
-                                 F->Vcol[k], b, 1.0, 0.0));
-        if (ldl) sj.push_back(ScaleJob{F->dvec + (size_t)k * b, F->Vcol[k], F->Vcol[k], b, (int)M.Rk, b, b, 1});
+        jt.push_back(job<double>(NN, b, (int)M.Rk, F->dinv + (size_t)M.k * b * b, b, static_cast<double*>(M.Bc.p), b, b,
+                                 F->Vcol[M.k], b, 1.0, 0.0));
+        if (M.ldl) sj.push_back(ScaleJob{F->dvec + (size_t)M.k * b, F->Vcol[M.k], F->Vcol[M.k], b, (int)M.Rk, b, b, 1});
         M.fl_exec += 2.0 * b * b * M.Rk;
         M.fl_model += (double)b * b * M.Rk;
       }
@@ -779,11 +853,11 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
       tlr_mat* F = M.F;
       const int b = M.b;
       for (int v = 0; v < M.nops; ++v) {
-        const int op = M.op0 + v, i = k + 1 + v, r = q[op];
+        const int op = M.op0 + v, i = M.k + 1 + v, r = q[op];
         ensure_ucap(ctx, F, i, r);
-        F->rank[ix(F, i, k)] = r;
-        F->uoff[ix(F, i, k)] = F->ulen[i];
-        F->voff[ix(F, i, k)] = M.boff[v];
+        F->rank[ix(F, i, M.k)] = r;
+        F->uoff[ix(F, i, M.k)] = F->ulen[i];
+        F->voff[ix(F, i, M.k)] = M.boff[v];
         cj.push_back(CopyJob{Q + qoff[op], F->Urow[i] + (size_t)F->ulen[i] * b, (int64_t)r * b});
         if (M.mixed) {
           if (F->ulen[i] + r > M.fu32cap[i]) {  // grow the FP32 copy of block row i
@@ -801,55 +875,101 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
         F->ulen[i] += r;
       }
       if (M.mixed) {
-        M.FV32[k] = f32_alloc(ctx, (int64_t)b * M.Rk);
-        c32.push_back(ConvJob{F->Vcol[k], M.FV32[k], (int64_t)b * M.Rk});
+        M.FV32[M.k] = f32_alloc(ctx, (int64_t)b * M.Rk);
+        c32.push_back(ConvJob{F->Vcol[M.k], M.FV32[M.k], (int64_t)b * M.Rk});
       }
     }
     batched_copy(ctx, cj);
     batched_to_float(ctx, c32);
     for (Mat* Mp : L)
-      if (Mp->live && Mp->mixed && Mp->nops > 0) panel_tile_norms(ctx, Mp->F, k, Mp->nL, bnrm);
+      if (Mp->live && Mp->mixed && Mp->nops > 0) panel_tile_norms(ctx, Mp->F, Mp->k, Mp->nL, bnrm);
+  
+    for (Mat* Mp : L) Mp->stepped = true;
   }
-  prof_flush(ctx);
-  TLR_CUDA(cudaStreamSynchronize(ctx->main));
-  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-  for (int mi = 0; mi < nm; ++mi) {
-    Mat& M = *mats[mi];
-    status[mi] = M.st;
-    free_f32(ctx, M);
-    if (!M.live) {
-      mat_destroy(ctx, M.F);
-      M.F = nullptr;
-      continue;
-    }
-    tlr_mat* A = M.A;
-    tlr_mat* F = M.F;
-    const int nb = M.nb;
-    // A := F
-    mat_free_storage(ctx, A);
-    dfree(ctx, A->diag);
-    dfree(ctx, A->dvec);
-    dfree(ctx, A->dinv);
-    A->diag = F->diag; F->diag = nullptr;
-    A->dvec = F->dvec; F->dvec = nullptr;
-    A->dinv = F->dinv; F->dinv = nullptr;
-    A->rank = F->rank; A->uoff = F->uoff; A->voff = F->voff;
-    A->Urow = F->Urow; A->Vcol = F->Vcol; A->ucap = F->ucap; A->vlen = F->vlen; A->ulen = F->ulen;
-    F->Urow.assign(nb, nullptr);
-    F->Vcol.assign(nb, nullptr);
-    mat_destroy(ctx, F);
-    M.F = nullptr;
-    A->state = ldl ? 2 : 1;
-    A->k_fail = -1;
-    A->eps = M.eps;
-    A->flops_exec = M.fl_exec;
-    A->flops_model = M.fl_model;
-    A->flops_fp32 = M.fl32;
-    A->ara_rounds = (double)(M.t32 + M.t64);
-    A->tiles_fp32 = M.mixed ? (double)M.t32 : 0.0;
-    A->tiles_fp64 = M.mixed ? (double)M.t64 : 0.0;
-    A->seconds = secs;
-  }
+};
+
+void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std::vector<double>& eps_in,
+                  const std::vector<tlr_opts>& opts, int ldl, std::vector<tlr_status>& status) {
+  const int nm = (int)mats_in.size();
+  status.assign(nm, TLR_OK);
+  if (nm == 0) return;
+  Session S(ctx);
+  for (int m = 0; m < nm; ++m) S.add(mats_in[m], eps_in[m], opts[m], ldl);
+  while (S.busy()) S.step();
+  for (int m = 0; m < nm; ++m) status[m] = S.status(m);
 }
 
 }  // namespace tlr
+
+// ======================================================================== session C ABI
+struct tlr_session {
+  tlr::Session S;
+  std::vector<int> tickets;
+  explicit tlr_session(tlr_ctx* c) : S(c) {}
+};
+
+#define SESSION_TRY try {
+#define SESSION_CATCH                               \
+  }                                                 \
+  catch (const tlr::Error& e) {                     \
+    fprintf(stderr, "[tlr] %s\n", e.what());        \
+    return e.status;                                \
+  }                                                 \
+  catch (...) {                                     \
+    return TLR_ERR_CUDA;                            \
+  }
+
+extern "C" {
+
+tlr_status tlr_session_create(tlr_ctx* ctx, tlr_session** out) {
+  if (!ctx || !out) return TLR_ERR_ARG;
+  SESSION_TRY
+  *out = new tlr_session(ctx);
+  return TLR_OK;
+  SESSION_CATCH
+}
+
+tlr_status tlr_session_destroy(tlr_session* s) {
+  if (!s) return TLR_ERR_ARG;
+  SESSION_TRY
+  delete s;
+  return TLR_OK;
+  SESSION_CATCH
+}
+
+tlr_status tlr_session_add(tlr_session* s, tlr_mat* A, double eps, const tlr_opts* opts, int ldl, int* ticket) {
+  if (!s || !A || !ticket || !(eps > 0)) return TLR_ERR_ARG;
+  if (A->state != 0) return TLR_ERR_STATE;
+  tlr_opts o;
+  if (opts) o = *opts; else tlr_opts_default(&o);
+  if (o.bs <= 0) o.bs = 16;
+  if (o.bs > 64 || o.bs > A->b || (o.precision != TLR_PREC_FP64 && o.precision != TLR_PREC_FP32) ||
+      (s->S.bs >= 0 && o.bs != s->S.bs))
+    return TLR_ERR_ARG;
+  SESSION_TRY
+  *ticket = s->S.add(A, eps, o, ldl);
+  return TLR_OK;
+  SESSION_CATCH
+}
+
+tlr_status tlr_session_step(tlr_session* s, int* unfinished) {
+  if (!s) return TLR_ERR_ARG;
+  SESSION_TRY
+  s->S.step();
+  if (unfinished) {
+    int n = 0;
+    for (auto& M : s->S.mats) n += (M->live && !M->done) ? 1 : 0;
+    *unfinished = n;
+  }
+  return TLR_OK;
+  SESSION_CATCH
+}
+
+tlr_status tlr_session_poll(tlr_session* s, int ticket, int* finished, tlr_status* result) {
+  if (!s || ticket < 0 || ticket >= (int)s->S.mats.size() || !finished) return TLR_ERR_ARG;
+  *finished = s->S.finished(ticket) ? 1 : 0;
+  if (result) *result = s->S.status(ticket);
+  return TLR_OK;
+}
+
+}  // extern "C"

@@ -433,3 +433,28 @@ def test_batch_mixed_precision(T, ctx):
     assert st == [0] * len(mats)
     for F, G in zip(alone, mats):
         assert np.array_equal(F.ranks(), G.ranks()) and F.logdet() == G.logdet()
+
+
+# ------------------------------------------------------------------ continuous batching (session)
+def test_session_join_mid_flight_is_bitwise_identical(T, ctx):
+    mats, eps, opts = _batch_inputs(T, ctx, BATCH)
+    alone = [A.copy().potrf(e, o) for A, e, o in zip(mats, eps, opts)]
+    S = T.Session(ctx)
+    tickets = {0: S.add(mats[0], eps[0], opts[0])}
+    S.step()
+    S.step()
+    tickets[1] = S.add(mats[1], eps[1], opts[1])   # joins while matrix 0 is at column 2
+    S.step()
+    tickets[2] = S.add(mats[2], eps[2], opts[2])
+    tickets[3] = S.add(mats[3], eps[3], opts[3])
+    while S.step():
+        pass
+    for m, t in tickets.items():
+        done, st = S.poll(t)
+        assert done and st == 0
+        assert np.array_equal(alone[m].ranks(), mats[m].ranks())
+        assert alone[m].logdet() == mats[m].logdet()
+        nb = mats[m].info()["nb"]
+        a, g = alone[m].tile(nb - 1, 0), mats[m].tile(nb - 1, 0)
+        assert np.array_equal(a[0], g[0]) and np.array_equal(a[1], g[1])
+    S.close()
