@@ -279,6 +279,9 @@ def run_ours(args, w, eps):
     # end-to-end through host buffers (public API: host points, pinned RHS in, pinned solution out)
     run_e2e(args, ctx, T, torch, w, eps, o, x, rhs_host, dev, out)
     run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out)
+    if rank == 0 and not args.no_serving:
+        # the metric's serving part: a bounded run of the serving workload (p50/p99 latency)
+        out["serving"] = run_serve(args, ctx=ctx, n=args.serve_default_requests, quiet=True)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         dt, v, desc = oracle_sample(w, eps, args.oracle_tiles)
         out["cpu_baseline"] = {"value": v, "unit": "s", "cores": _cores(), "kind": "oracle", "sample": desc,
@@ -338,6 +341,90 @@ def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
         out["variants"] = variants
 
 
+# --------------------------------------------------------------------------- batched and serving workloads
+def batch_specs(count, seed=3):
+    """512 independent matrices: N = 256 * U{8..64}, d in {2,3} by coin flip, ell ~ U[0.05, 0.3], eps 1e-6."""
+    u = inputs.uniform(seed, 5, 3 * count).reshape(count, 3)
+    out = []
+    for m in range(count):
+        N = 256 * (8 + min(int(u[m, 0] * 57), 56))
+        d = 2 if u[m, 1] < 0.5 else 3
+        out.append(dict(N=N, d=d, ell=0.05 + 0.25 * u[m, 2], eps=1e-6, seed=(3 << 20) + m))
+    return out
+
+
+def run_batch(args):
+    """Batched small factorizations: all matrices factored in one session (shared launches per column)."""
+    import torch
+    import paper_2108_11932_gb300 as T
+    from paper_2108_11932_gb300 import autotune
+    T.build()
+    ctx = T.Context(0)
+    t0 = time.perf_counter()
+    tuned = autotune.tune(ctx)
+    t_tune = time.perf_counter() - t0
+    specs = batch_specs(args.batch_count)
+
+    def build(specs):
+        mats, eps, opts = [], [], []
+        for sp in specs:
+            b = autotune.choose(tuned["table"], sp["N"], sp["d"])
+            o = T.default_opts(bs=16, seed=sp["seed"])
+            mats.append(ctx.compress(inputs.points(sp["N"], sp["d"], sp["seed"]), b, sp["eps"], sp["ell"], 1e-4, o))
+            eps.append(sp["eps"])
+            opts.append(o)
+        return mats, eps, opts
+    warm = build(specs[: min(16, len(specs))])
+    ctx.factor_batch(*warm)
+    for m in warm[0]:
+        m.free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mats, eps, opts = build(specs)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t0
+    l0 = ctx.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    st = ctx.factor_batch(mats, eps, opts)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    fl = sum(m.info()["flops_exec"] for m, s_ in zip(mats, st) if s_ == 0)
+    bs_used = {}
+    for m in mats:
+        bs_used[m.info()["b"]] = bs_used.get(m.info()["b"], 0) + 1
+    out = {"workload": f"batch{len(specs)}: {len(specs)} independent covariance matrices, N=256*U{{8..64}}, d in {{2,3}}, "
+                       "ell~U[0.05,0.3], nugget 1e-4, eps 1e-6, FP64; tile size from the autotuner",
+           "matrices": len(specs), "ok": sum(1 for s_ in st if s_ == 0), "factor_s": secs,
+           "matrices_per_s": len(specs) / secs, "tflops_exec": fl / secs / 1e12, "launches": ctx.launches() - l0,
+           "construction_s": t_build, "autotune_s": t_tune, "tile_sizes": bs_used,
+           "autotune_table": {f"d{k[0]}_N2^{k[1]}": v for k, v in tuned["table"].items()}}
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args, ctx=None, n=None, quiet=False):
+    """Serving: Poisson arrivals, continuous batching; latency arrival -> result."""
+    import paper_2108_11932_gb300 as T
+    from paper_2108_11932_gb300 import serve
+    if ctx is None:
+        T.build()
+        ctx = T.Context(0)
+    n = n or args.requests
+    res = {}
+    for name, prec in (("fp64", 0), ("mixed", 1)):
+        reqs = serve.make_requests(n, args.rate, seed=4, n_max=args.serve_nmax)
+        srv = serve.Server(ctx, budget_bytes=150e9, precision=prec)
+        res[name] = srv.run(reqs)
+    out = {"workload": f"serve: {n} requests, Poisson arrivals at {args.rate}/s, N log-uniform in [4096, {args.serve_nmax}] "
+                       "(multiple of 256), d in {2,3}, ell~U[0.05,0.3], eps in {1e-2,1e-4,1e-6}, nrhs~U{1..32}; "
+                       "factor + solve + logdet per request; 150 GB admission budget; FP64 vs mixed",
+           **res}
+    if not quiet:
+        print(json.dumps(out), flush=True)
+    return out
+
+
 def main():
     global WORKLOAD
     ap = argparse.ArgumentParser()
@@ -352,12 +439,23 @@ def main():
     ap.add_argument("--oracle-tiles", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--serve-nmax", type=int, default=65536)
+    ap.add_argument("--serve-default-requests", type=int, default=40)
     args = ap.parse_args()
     WORKLOAD = args.workload
     w = inputs.WORKLOADS[WORKLOAD]
     args.variant_list = [] if args.no_variants else [("fp64_eps1e-2", 1e-2, 0), ("fp64_eps1e-6", 1e-6, 0)]
     if args.impl == "reference":
         run_reference(args, w, args.eps)
+    elif args.mode == "batch":
+        run_batch(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_ours(args, w, args.eps)
 

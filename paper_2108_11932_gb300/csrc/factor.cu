@@ -683,37 +683,44 @@ struct Session {
     double* Q = bQ.need<double>((size_t)std::max<int64_t>(qtot, 1));
     if (nops > 0) {
       // device tables of every matrix (ranks and offsets of F, Gram offsets of this column)
-      std::vector<int64_t> toff(L.size());
+      // Each matrix's region: rank/uoff/voff (3 nb^2 ints), then the int64 Gram offsets at
+      // an even int offset (8-byte aligned), then the Gram leading dimensions; every
+      // region starts at an even offset as well.
+      auto even = [](int64_t v) { return (v + 1) & ~int64_t(1); };
+      std::vector<int64_t> toff(L.size()), g0(L.size());
       int64_t tint = 0;
       for (size_t u = 0; u < L.size(); ++u) {
+        const int64_t kk = std::max(L[u]->k, 1);
         toff[u] = tint;
-        tint += (int64_t)3 * L[u]->nb * L[u]->nb + 4 * std::max(L[u]->k, 1);
+        g0[u] = even((int64_t)3 * L[u]->nb * L[u]->nb);
+        tint += even(g0[u] + 3 * kk);
       }
       std::vector<int> htab((size_t)tint, 0);
       for (size_t u = 0; u < L.size(); ++u) {
         Mat& M = *L[u];
         tlr_mat* F = M.F;
         const int nb2 = M.nb * M.nb;
+        const int kk = std::max(M.k, 1);
         int* t = htab.data() + toff[u];
         for (int e = 0; e < nb2; ++e) {
           t[e] = F->rank[e];
           t[nb2 + e] = (int)F->uoff[e];
           t[2 * nb2 + e] = (int)F->voff[e];
         }
-        int64_t* go = reinterpret_cast<int64_t*>(t + 3 * nb2);
-        for (int j = 0; j < std::max(M.k, 1); ++j) go[j] = M.goff[j];
-        int* gl = t + 3 * nb2 + 2 * std::max(M.k, 1);
-        for (int j = 0; j < std::max(M.k, 1); ++j) gl[j] = M.gld[j];
+        int64_t* go = reinterpret_cast<int64_t*>(t + g0[u]);
+        for (int j = 0; j < kk; ++j) go[j] = M.goff[j];
+        int* gl = t + g0[u] + 2 * kk;
+        for (int j = 0; j < kk; ++j) gl[j] = M.gld[j];
       }
       int* dtab = bTab.need<int>((size_t)tint + 2);
       TLR_CUDA(cudaMemcpyAsync(dtab, htab.data(), sizeof(int) * tint, cudaMemcpyHostToDevice, ctx->stream));
       TLR_CUDA(cudaStreamSynchronize(ctx->stream));  // htab is pageable
       for (size_t u = 0; u < L.size(); ++u) {
         Mat& M = *L[u];
-        const int nb2 = M.nb * M.nb;
+        const int kk = std::max(M.k, 1);
         M.dtab = dtab + toff[u];
-        M.dgoff = reinterpret_cast<const int64_t*>(dtab + toff[u] + 3 * nb2);
-        M.dgld = dtab + toff[u] + 3 * nb2 + 2 * std::max(M.k, 1);
+        M.dgoff = reinterpret_cast<const int64_t*>(dtab + toff[u] + g0[u]);
+        M.dgld = dtab + toff[u] + g0[u] + 2 * kk;
       }
       // per-tile precision rule (mixed precision): FP32 when u32 sqrt(K)(|A_ik|_F + sum_j
       // |L_ij|_F |L_kj|_F) <= thr / 8, else FP64

@@ -137,7 +137,7 @@ def test_ara_dense_matches_oracle(T, ctx):
 # ------------------------------------------------------------------ TLR: same algorithm as the oracle
 CASES = {
     "cov2d_2k": dict(N=2048, d=2, ell=0.1, nugget=1e-4, b=256, bs=16, seed=0, eps=1e-6),
-    "cov3d_ragged": dict(N=1500, d=3, ell=0.2, nugget=1e-4, b=256, bs=32, seed=1, eps=1e-5),
+    "cov3d_ragged": dict(N=1700, d=3, ell=0.2, nugget=1e-4, b=256, bs=32, seed=1, eps=1e-5),  # nb = 7 (odd)
     "cov2d_b100": dict(N=1000, d=2, ell=0.05, nugget=1e-4, b=100, bs=8, seed=4, eps=1e-7),
 }
 
@@ -362,7 +362,8 @@ def test_mixed_precision_falls_back_to_fp64_below_1e4(T, ctx):
 
 # ------------------------------------------------------------------ batched factorization of many matrices
 BATCH = [dict(N=1500, d=2, ell=0.1, b=256, eps=1e-6, seed=31), dict(N=2048, d=3, ell=0.2, b=256, eps=1e-4, seed=32),
-         dict(N=700, d=2, ell=0.05, b=128, eps=1e-7, seed=33), dict(N=1024, d=3, ell=0.3, b=128, eps=1e-5, seed=34)]
+         dict(N=700, d=2, ell=0.05, b=128, eps=1e-7, seed=33), dict(N=1024, d=3, ell=0.3, b=128, eps=1e-5, seed=34),
+         dict(N=1350, d=2, ell=0.15, b=256, eps=1e-6, seed=35)]  # nb = 6, 8, 6, 8, 6 (7 tiles when padded: 1350/256)
 
 
 def _batch_inputs(T, ctx, specs, prec=0):
