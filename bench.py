@@ -425,6 +425,61 @@ def run_serve(args, ctx=None, n=None, quiet=False):
     return out
 
 
+def run_peaks(args):
+    """Peak rates of this GPU: FP64 DFMA loop (library), and torch.matmul GEMMs (8192^3) per dtype."""
+    import torch
+    import paper_2108_11932_gb300 as T
+    T.build()
+    ctx = T.Context(0)
+    out = {"fp64_dfma_tflops": ctx.fp64_peak()}
+
+    def mm(dtype, tf32=False, n=8192, reps=5):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b_ = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(2):
+            a @ b_
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            a @ b_
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return 2 * n ** 3 / best / 1e9
+    out["fp64_dgemm_tflops"] = mm(torch.float64, reps=3)
+    out["fp32_sgemm_tflops"] = mm(torch.float32)
+    out["tf32_gemm_tflops"] = mm(torch.float32, tf32=True)
+    out["bf16_gemm_tflops"] = mm(torch.bfloat16)
+    print(json.dumps(out), flush=True)
+
+
+def run_phases(args, w, eps):
+    """Phase profile of one factorization (CUDA events at phase boundaries, tlr_profile)."""
+    import torch
+    import paper_2108_11932_gb300 as T
+    T.build()
+    ctx = T.Context(0)
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    prec = T.PREC_FP64 if args.precision == "fp64" else T.PREC_FP32
+    o = T.default_opts(bs=w["bs"], seed=w["seed"], precision=prec)
+    A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], o)
+    ctx.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    A.potrf(eps, o)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    prof = ctx.profile(False)
+    inf = A.info()
+    out = {"workload": _workload_desc(w, eps, args.precision.upper()), "factor_s": wall,
+           "flops_exec": inf["flops_exec"], "flops_fp32": inf["flops_fp32"], "mean_rank": inf["mean_rank"],
+           "phases_ms": {k: v[0] for k, v in prof.items()}, "phase_launches": {k: v[1] for k, v in prof.items()}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     global WORKLOAD
     ap = argparse.ArgumentParser()
@@ -440,7 +495,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve"])
+    ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve", "peaks", "phases"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=20.0)
@@ -456,6 +511,10 @@ def main():
         run_batch(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "peaks":
+        run_peaks(args)
+    elif args.mode == "phases":
+        run_phases(args, w, args.eps)
     else:
         run_ours(args, w, args.eps)
 
