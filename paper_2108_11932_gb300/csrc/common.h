@@ -60,7 +60,7 @@ struct GemmJob {
 enum { GEMM_TRIL = 1 };
 enum GemmMode { NN = 0, TN = 1, NT = 2 };
 
-constexpr int GEMM_TM = 64, GEMM_TN = 32, GEMM_TK = 16;
+constexpr int GEMM_TK = 16;
 
 }  // namespace tlr
 

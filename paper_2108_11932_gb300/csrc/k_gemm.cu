@@ -4,24 +4,44 @@
 // projections (sampleLeftT), orthogonalization and dense updates as
 // non-uniform batched GEMMs (Section 4.1, "marshaling" + vbatched GEMM).  Here
 // one launch takes an array of jobs of different shapes; each CTA computes one
-// 64 x 32 tile of one job over its whole K range (or over one slice of it:
-// deterministic split-K with a fixed-order reduction, used when a job has few
-// output tiles and a long reduction, e.g. Q^T Y with K = b).
+// output tile of one job over its whole K range or over one slice of it
+// (deterministic split-K: fixed slices, fixed-order reduction).
 //
-// FP64 on GB300 issues ~2 DFMA per SM per clock (1.2 TFLOP/s for 152 SMs), so
-// the FP64 instantiation is bound by the DFMA rate as soon as every SM holds a
-// CTA: operands are staged through shared memory (coalesced 128-byte rows of
-// the column-major operands) and each thread keeps a 4 x 4 register tile.
+// Tile shapes follow the arithmetic units.  GB300 issues ~0.5 FP64 FMA lanes per
+// SM sub-partition (SMSP) per clock, so one warp-wide DFMA occupies its SMSP's
+// FP64 pipe for ~64 clocks and a single warp already saturates it: shared-memory
+// bandwidth and register blocking do not matter, the number of warps with work
+// does.  The FP64 instantiation therefore uses small 32 x 16 tiles (2 x 2
+// outputs per thread; a 16-column right-hand side fills every warp) and splits
+// long reductions so that even a single small product spreads over the 4 x 152
+// SMSPs.
+// FP32 FMA is 64x faster per SMSP, so the FP32 instantiation keeps 64 x 32 tiles
+// with 4 x 4 outputs per thread for operand reuse.  Both stage operands through
+// shared memory in 16-deep K chunks, loading chunk c + 1 into registers while
+// chunk c is multiplied.
 #include "common.h"
 
 namespace tlr {
 
-template <typename T, int MODE>
+template <typename T>
+struct GemmTile;
+template <>
+struct GemmTile<double> { static constexpr int RM = 2, RN = 2; };
+template <>
+struct GemmTile<float> { static constexpr int RM = 4, RN = 4; };
+
+// 128 threads as 16 (rows) x 8 (columns); thread (tr, tc) owns rows tr*RM + i and
+// columns tc*RN + j of the TM x TN tile; warp w owns columns [2w RN, 2w RN + 2 RN).
+template <typename T, int MODE, int RM, int RN>
 __global__ void __launch_bounds__(128) k_gemm(const GemmJob<T>* __restrict__ jobs, int njobs) {
-  constexpr int TM = GEMM_TM, TN_ = GEMM_TN, TK = GEMM_TK;
+  constexpr int TM = 16 * RM, TN_ = 8 * RN, TK = GEMM_TK;
+  constexpr int EA = TK * TM / 128, EB = TK * TN_ / 128;
+  // Rows padded by one where the chunk is stored across rows (consecutive threads
+  // take consecutive k), which would otherwise put 16 threads on one bank.
+  constexpr int PADA = (MODE == TN) ? 1 : 0, PADB = (MODE == NT) ? 0 : 1;
   __shared__ GemmJob<T> J;
-  __shared__ T As[TK][TM];
-  __shared__ T Bs[TK][TN_];
+  __shared__ T As[TK][TM + PADA];
+  __shared__ T Bs[TK][TN_ + PADB];
   const int tid = threadIdx.x;
   if (tid == 0) {
     int bid = blockIdx.x, lo = 0, hi = njobs - 1;
@@ -40,75 +60,87 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmJob<T>* __restrict__ job
   if ((J.flags & GEMM_TRIL) && m0 + TM <= n0) return;  // tile strictly above the diagonal
   const int M = J.M, N = J.N;
   const int tr = tid & 15, tc = tid >> 4;
-  const bool active = (n0 + (tid >> 5) * 8) < N;  // warp-uniform: this warp's 8 columns exist
-  T acc[4][4];
+  const bool active = (n0 + (tid >> 5) * 2 * RN) < N;  // warp-uniform: this warp's columns exist
+  T acc[RM][RN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < RN; ++j) acc[i][j] = T(0);
 
-  for (int seg = 0; seg < 2; ++seg) {
-    const int K = J.K[seg];
-    if (K <= 0) continue;
+  // The K chunks of both segments form one sequence; this CTA takes slice [c0, c1).
+  const int nch0 = (J.K[0] + TK - 1) / TK, nch1 = J.K[1] > 0 ? (J.K[1] + TK - 1) / TK : 0;
+  const int nch = nch0 + nch1;
+  const int c0 = (int)((int64_t)nch * split / J.nsplit);
+  const int c1 = (int)((int64_t)nch * (split + 1) / J.nsplit);
+  T ra[EA], rb[EB];
+  auto load = [&](int c) {
+    const int seg = c < nch0 ? 0 : 1;
+    const int k0 = (seg ? c - nch0 : c) * TK, K = J.K[seg];
     const T* __restrict__ A = J.A[seg];
     const T* __restrict__ B = J.B[seg];
     const int lda = J.lda[seg], ldb = J.ldb[seg];
-    const int nch = (K + TK - 1) / TK;
-    const int c0 = (int)((int64_t)nch * split / J.nsplit);
-    const int c1 = (int)((int64_t)nch * (split + 1) / J.nsplit);
-    for (int c = c0; c < c1; ++c) {
-      const int k0 = c * TK;
 #pragma unroll
-      for (int e = 0; e < (TK * TM) / 128; ++e) {
-        const int idx = tid + e * 128;
-        int m, kk;
-        if (MODE == TN) { kk = idx % TK; m = idx / TK; }
-        else { m = idx % TM; kk = idx / TM; }
-        const int gm = m0 + m, gk = k0 + kk;
-        T v = T(0);
-        if (gm < M && gk < K)
-          v = (MODE == TN) ? A[(size_t)gk + (size_t)gm * lda] : A[(size_t)gm + (size_t)gk * lda];
-        As[kk][m] = v;
-      }
-#pragma unroll
-      for (int e = 0; e < (TK * TN_) / 128; ++e) {
-        const int idx = tid + e * 128;
-        int n, kk;
-        if (MODE == NT) { n = idx % TN_; kk = idx / TN_; }
-        else { kk = idx % TK; n = idx / TK; }
-        const int gn = n0 + n, gk = k0 + kk;
-        T v = T(0);
-        if (gn < N && gk < K)
-          v = (MODE == NT) ? B[(size_t)gn + (size_t)gk * ldb] : B[(size_t)gk + (size_t)gn * ldb];
-        Bs[kk][n] = v;
-      }
-      __syncthreads();
-      if (active) {
-#pragma unroll
-        for (int kk = 0; kk < TK; ++kk) {
-          T a[4], bb[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = As[kk][tr * 4 + i];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tc * 4 + j];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
-        }
-      }
-      __syncthreads();
+    for (int e = 0; e < EA; ++e) {
+      const int idx = tid + e * 128;
+      int m, kk;
+      if (MODE == TN) { kk = idx % TK; m = idx / TK; }
+      else { m = idx % TM; kk = idx / TM; }
+      const int gm = m0 + m, gk = k0 + kk;
+      ra[e] = (gm < M && gk < K) ? ((MODE == TN) ? A[(size_t)gk + (size_t)gm * lda] : A[(size_t)gm + (size_t)gk * lda])
+                                 : T(0);
     }
+#pragma unroll
+    for (int e = 0; e < EB; ++e) {
+      const int idx = tid + e * 128;
+      int n, kk;
+      if (MODE == NT) { n = idx % TN_; kk = idx / TN_; }
+      else { kk = idx % TK; n = idx / TK; }
+      const int gn = n0 + n, gk = k0 + kk;
+      rb[e] = (gn < N && gk < K) ? ((MODE == NT) ? B[(size_t)gn + (size_t)gk * ldb] : B[(size_t)gk + (size_t)gn * ldb])
+                                 : T(0);
+    }
+  };
+  if (c0 < c1) load(c0);
+  for (int c = c0; c < c1; ++c) {
+#pragma unroll
+    for (int e = 0; e < EA; ++e) {
+      const int idx = tid + e * 128;
+      if (MODE == TN) As[idx % TK][idx / TK] = ra[e];
+      else As[idx / TM][idx % TM] = ra[e];
+    }
+#pragma unroll
+    for (int e = 0; e < EB; ++e) {
+      const int idx = tid + e * 128;
+      if (MODE == NT) Bs[idx / TN_][idx % TN_] = rb[e];
+      else Bs[idx % TK][idx / TK] = rb[e];
+    }
+    __syncthreads();
+    if (c + 1 < c1) load(c + 1);  // in flight while this chunk is multiplied
+    if (active) {
+#pragma unroll
+      for (int kk = 0; kk < TK; ++kk) {
+        T a[RM], bb[RN];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) a[i] = As[kk][tr * RM + i];
+#pragma unroll
+        for (int j = 0; j < RN; ++j) bb[j] = Bs[kk][tc * RN + j];
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+          for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+      }
+    }
+    __syncthreads();
   }
   if (!active) return;
   const T alpha = (T)J.alpha, beta = (T)J.beta;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + tr * 4 + i;
+  for (int i = 0; i < RM; ++i) {
+    const int gm = m0 + tr * RM + i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tc * 4 + j;
+    for (int j = 0; j < RN; ++j) {
+      const int gn = n0 + tc * RN + j;
       if (gn >= N) continue;
       if (J.nsplit > 1) {
         J.ws[(size_t)split * M * N + gm + (size_t)gn * M] = acc[i][j];
@@ -124,15 +156,17 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmJob<T>* __restrict__ job
 }
 
 // Fixed-order reduction of split-K partials: C = alpha * sum_s ws[s] + beta * C.
+// Partials of tiles that were skipped (strictly above the diagonal of a GEMM_TRIL
+// job) are never read: every entry of such a tile has m < n.
 template <typename T>
 __global__ void k_gemm_reduce(const GemmJob<T>* __restrict__ jobs, const int* __restrict__ ids) {
   const GemmJob<T>& J = jobs[ids[blockIdx.x]];
   const size_t MN = (size_t)J.M * J.N;
   for (size_t e = blockIdx.y * (size_t)blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.y * blockDim.x) {
     const int gm = (int)(e % J.M), gn = (int)(e / J.M);
+    if ((J.flags & GEMM_TRIL) && gm < gn) continue;
     T s = T(0);
     for (int sp = 0; sp < J.nsplit; ++sp) s += J.ws[(size_t)sp * MN + e];
-    if ((J.flags & GEMM_TRIL) && gm < gn) continue;
     T* c = J.C + gm + (size_t)gn * J.ldc;
     T v = (T)J.alpha * s;
     if (J.beta != 0.0) v += (T)J.beta * *c;
@@ -153,30 +187,33 @@ GemmJob<T> job(GemmMode, int M, int N, const T* A, int lda, const T* B, int ldb,
 
 template <typename T>
 void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
+  constexpr int RM = GemmTile<T>::RM, RN = GemmTile<T>::RN, TM = 16 * RM, TN_ = 8 * RN;
   std::vector<GemmJob<T>> jobs;
   jobs.reserve(jobs_in.size());
   for (auto& j : jobs_in)
     if (j.M > 0 && j.N > 0) jobs.push_back(j);
   if (jobs.empty()) return;
-  // Split K (deterministically: fixed slices, fixed-order reduction) when the
-  // launch has fewer than ~4 CTAs per SM, so that small batches still occupy
-  // every SM; each slice keeps at least 64 reduction steps.
-  int64_t base = 0;
-  for (auto& j : jobs) {
-    j.tiles_m = (j.M + GEMM_TM - 1) / GEMM_TM;
-    j.tiles_n = (j.N + GEMM_TN - 1) / GEMM_TN;
-    base += (int64_t)j.tiles_m * j.tiles_n;
-  }
-  const int64_t target = 4LL * std::max(ctx->sm_count, 1);
-  const int want = base >= target ? 1 : (int)std::min<int64_t>(16, (target + base - 1) / base);
+  // Split-K.  Work is counted in warp-chunks (one warp's share of a tile over one
+  // 16-deep K chunk): a job has tiles_m x (warps with columns) x chunks of them.
+  // Each job picks its slice length S (in chunks, at least 4) so that the job
+  // alone would hold about two warps per SMSP (8 per SM), and is cut into
+  // ceil(chunks / S) slices, at most 32.  The choice depends on the job's own
+  // shape only, never on the other jobs of the launch: a product is summed in the
+  // same order whether its matrix is factored alone or in a batch, which keeps
+  // batched results bitwise equal to single ones.
+  const int64_t slots = 8LL * std::max(ctx->sm_count, 1);
   int64_t total = 0;
   size_t ws_elems = 0;
   std::vector<int> split_ids;
   for (size_t q = 0; q < jobs.size(); ++q) {
     auto& j = jobs[q];
-    const int Kt = j.K[0] + j.K[1];
-    j.nsplit = 1;
-    if (!(j.flags & GEMM_TRIL) && want > 1) j.nsplit = std::max(1, std::min(want, Kt / 64));
+    j.tiles_m = (j.M + TM - 1) / TM;
+    j.tiles_n = (j.N + TN_ - 1) / TN_;
+    const int full = j.N / TN_, rem = j.N % TN_;
+    const int64_t wpr = (int64_t)full * 4 + (rem + 2 * RN - 1) / (2 * RN);  // warps with columns, per tile row
+    const int chunks = (j.K[0] + GEMM_TK - 1) / GEMM_TK + (j.K[1] > 0 ? (j.K[1] + GEMM_TK - 1) / GEMM_TK : 0);
+    const int64_t S = std::max<int64_t>(4, ((int64_t)j.tiles_m * wpr * chunks + slots - 1) / slots);
+    j.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(32, chunks / S));
     j.tile0 = (int)total;
     total += (int64_t)j.tiles_m * j.tiles_n * j.nsplit;
     if (j.nsplit > 1) {
@@ -198,16 +235,16 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
     for (auto& j : jobs) flops += 2.0 * j.M * j.N * (double)(j.K[0] + j.K[1]) * ((j.flags & GEMM_TRIL) ? 0.5 : 1.0);
     kprof_begin(ctx);
   }
-  if (mode == NN) k_gemm<T, NN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
-  else if (mode == TN) k_gemm<T, TN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
-  else k_gemm<T, NT><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
+  if (mode == NN) k_gemm<T, NN, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
+  else if (mode == TN) k_gemm<T, TN, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
+  else k_gemm<T, NT, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   TLR_LAUNCH_CHECK(ctx);
   if (ctx->kprof) kprof_end(ctx, (sizeof(T) == 8 ? 0 : 3) + (int)mode, flops);
   if (!split_ids.empty()) {
     const int* ids = static_cast<const int*>(upload(ctx, split_ids.data(), split_ids.size() * sizeof(int)));
     size_t mx = 0;
     for (int q : split_ids) mx = std::max(mx, (size_t)jobs[q].M * jobs[q].N);
-    dim3 rg((unsigned)split_ids.size(), (unsigned)std::min<size_t>(64, (mx + 1023) / 1024));
+    dim3 rg((unsigned)split_ids.size(), (unsigned)std::min<size_t>(64, (mx + 255) / 256));
     k_gemm_reduce<T><<<rg, 256, 0, ctx->stream>>>(dj, ids);
     TLR_LAUNCH_CHECK(ctx);
   }
