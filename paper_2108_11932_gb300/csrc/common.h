@@ -174,26 +174,24 @@ struct PotrfJob {
   double* A;
   double* dvec;  // LDL^T: D of the whole tile (entries col0.. written)
   int* info;
-  int lda, col0, nbk;
+  double* Binv;  // receives the inverse of the factored block (lower; zeros above), ld ldb
+  int lda, col0, nbk, ldb;
 };
 struct PanelJob {
-  const double* L;
-  double* X;
+  const double* Binv;  // inverse of the factored diagonal block (lower), ld ldb
+  double* X;           // panel below the block, m x nbk, updated in place
   const double* dvec;  // LDL^T: D of this block
-  int lda, ldx, m, nbk;
+  double* W;           // LDL^T: receives X L^{-T} before the D^{-1} scaling (m x nbk, ld m)
+  int ldb, ldx, m, nbk;
 };
 struct LeftJob {
   const double* L;
   double* X;
   int lda, ldx, nrhs, nbk;
 };
-void potrf_blocks(tlr_ctx* ctx, std::vector<PotrfJob>& jobs, int ldl);
-void trsm_panels(tlr_ctx* ctx, std::vector<PanelJob>& jobs, int ldl);
+void potrf_inv_blocks(tlr_ctx* ctx, std::vector<PotrfJob>& jobs, int ldl);
+void panel_apply(tlr_ctx* ctx, std::vector<PanelJob>& jobs, int ldl);
 void trsm_lefts(tlr_ctx* ctx, std::vector<LeftJob>& jobs, int unit, int trans);
-void potrf_diag_block(tlr_ctx* ctx, int nbk, double* A, int lda, int ldl, double* dvec, int* info,
-                      int col0);
-void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, double* X, int ldx,
-                      int ldl, const double* dvec);
 void trsm_left_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs, double* X,
                      int ldx);
 void trsm_left_t_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs,

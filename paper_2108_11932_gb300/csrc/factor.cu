@@ -366,10 +366,10 @@ struct Session {
   tlr_ctx* ctx;
   int bs = -1;
   std::vector<std::unique_ptr<Mat>> mats;
-  Buf bnrm, bQ, bTab, bInfo, bTmp, bOm, bOm32, bX, bW, bY32, bP, bZ, bQ32, bB32;
+  Buf bnrm, bQ, bTab, bInfo, bTmp, bTmpMain, bOm, bOm32, bX, bW, bY32, bP, bZ, bQ32, bB32;
   AraStats total;
   explicit Session(tlr_ctx* c)
-      : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bOm(c), bOm32(c), bX(c), bW(c), bY32(c), bP(c), bZ(c),
+      : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bX(c), bW(c), bY32(c), bP(c), bZ(c),
         bQ32(c), bB32(c) {}
   ~Session() {
     cudaStreamSynchronize(ctx->side);
@@ -557,10 +557,11 @@ struct Session {
     const int nm = (int)mats.size();
     int* info = bInfo.need<int>((size_t)nm);
     {  // the side stream must not reallocate its workspace: size it here
-      int64_t tn = 0;
+      std::vector<DenseTile> probe[2];
       for (Mat* Mp : L)
-        if (Mp->ldl) tn += (int64_t)Mp->b * NBK;
-      bTmp.need<double>((size_t)std::max<int64_t>(tn, 1));
+        if (Mp->o.compensation != TLR_COMP_SCHUR)
+          probe[Mp->ldl].push_back(DenseTile{nullptr, nullptr, nullptr, Mp->F->dinv, Mp->b, Mp->b});
+      bTmp.need<double>(std::max(dense_tmp_doubles(probe[0], 0), dense_tmp_doubles(probe[1], 1)));
     }
     TLR_CUDA(cudaMemsetAsync(info, 0xff, sizeof(int) * nm, ctx->main));
     TLR_CUDA(cudaEventRecord(ctx->ev_fork, ctx->main));
@@ -646,9 +647,11 @@ struct Session {
         }
       }
       batched_add_diag(ctx, shifts);
+      // pass 1 runs on the main stream while pass 0 may still be running: own workspace
+      Buf& tmp = pass == 0 ? bTmp : bTmpMain;
       for (int l = 0; l < 2; ++l) {
-        dense_factor_batch(ctx, tiles[l], l, bTmp);
-        dense_trinv_batch(ctx, tiles[l], l);
+        dense_factor_batch(ctx, tiles[l], l, tmp);
+        dense_trinv_batch(ctx, tiles[l], l, tmp);
       }
     }
     TLR_CUDA(cudaEventRecord(ctx->ev_join, ctx->side));

@@ -44,8 +44,10 @@ struct DenseTile {
   double* Linv;  // output of the inverse (n x n, ld n), or null
   int n, lda;
 };
+// workspace (doubles) that dense_factor_batch and dense_trinv_batch take from tmp
+size_t dense_tmp_doubles(const std::vector<DenseTile>& tiles, int ldl);
 void dense_factor_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int ldl, Buf& tmp);
-void dense_trinv_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int unit);
+void dense_trinv_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int unit, Buf& tmp);
 void dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int unit, int nrhs, double* X, int ldx, int trans);
 
 // ARA engine (Algorithm 1 batched, dynamic batching of Algorithm 5)

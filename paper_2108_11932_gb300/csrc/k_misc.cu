@@ -297,96 +297,157 @@ void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mou
 }
 
 // ------------------------------------------------------------------ dense diagonal-tile factorization
-// All three kernels take an array of per-tile descriptors (grid.y = tile), so the
+// All kernels take an array of per-tile descriptors (grid.y = tile), so the
 // diagonal tiles of many matrices factor in the same launches.
 //
-// k_potrf_block: factor the nbk x nbk diagonal block at A (lda) in shared memory,
-// one CTA.  Cholesky: right-looking column by column.  LDL^T (unpivoted, Section
-// 5.3): d_j = a_jj, l_ij = a_ij / d_j, a_il -= l_ij d_j l_lj; the unit diagonal is
-// written to A and d to dvec.  *info records the first failing column (atomicCAS
-// from -1), after which the block stops.
+// GB300 retires about one warp-wide FP64 FMA per SMSP every 64 clocks, so these
+// kernels are built around two rules: keep the sequential pivot chain short (one
+// barrier and one reciprocal per column) and spread the FMAs of each step evenly
+// over all threads of the CTA.
+//
+// k_potrf_inv_block: factor the nbk x nbk diagonal block at A (lda) in shared
+// memory and write the inverse of its factor to Binv (lower, zeros above the
+// diagonal), one CTA of 256 threads per block.
+//   Factorization: right-looking elimination on the unscaled columns,
+//   a_rc -= a_rj a_cj / a_jj for j < c <= r, which is the Schur-complement step of
+//   both Cholesky and unpivoted LDL^T (Section 5.3); afterwards Cholesky takes
+//   l_jj = sqrt(a_jj), l_rj = a_rj / l_jj and LDL^T takes d_j = a_jj, l_rj = a_rj / d_j
+//   with a unit diagonal.  The trailing triangle of column j is enumerated through
+//   a table of (r, c) pairs ordered by descending column, so that it is a prefix of
+//   the table and 256 threads share it evenly; thread 0 updates the next pivot
+//   first and takes its reciprocal while the others finish the step.
+//   Inverse: X = L^{-1} by row elimination; step r subtracts l_r'r X[r, :] from
+//   every later row r' and the last update of a row applies its 1 / l_rr.
+// A pivot that is not positive (Cholesky) or is zero / not finite (LDL^T) records
+// the first failing column in *info (atomicCAS from -1) and stops the block.
 constexpr int PB = 64;
-__global__ void __launch_bounds__(256) k_potrf_block(const PotrfJob* __restrict__ jobs, int ldl) {
+static size_t potrf_inv_smem() { return sizeof(double) * 2 * PB * (PB + 1); }
+
+__global__ void __launch_bounds__(256) k_potrf_inv_block(const PotrfJob* __restrict__ jobs, int ldl) {
   const PotrfJob J = jobs[blockIdx.y];
   const int nbk = J.nbk, lda = J.lda;
   double* A = J.A;
-  __shared__ double S[PB][PB + 1];
+  extern __shared__ double dsm[];
+  double (*S)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm);
+  double (*X)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm + PB * (PB + 1));
+  __shared__ double ip[PB];   // 1 / a_jj
+  __shared__ double idg[PB];  // 1 / l_jj (1 for LDL^T)
+  __shared__ unsigned short tab[PB * (PB + 1) / 2];
   __shared__ int fail;
   const int tid = threadIdx.x;
   for (int e = tid; e < nbk * nbk; e += blockDim.x) {
     const int r = e % nbk, c = e / nbk;
     S[r][c] = (r >= c) ? A[r + (size_t)c * lda] : 0.0;
   }
+  if (tid < nbk) {  // column c = nbk-1-t occupies entries [t(t+1)/2, t(t+1)/2 + t]
+    const int c = nbk - 1 - tid, s0 = tid * (tid + 1) / 2;
+    for (int r = c; r < nbk; ++r) tab[s0 + r - c] = (unsigned short)(r | (c << 8));
+  }
   if (tid == 0) fail = 0;
   __syncthreads();
-  for (int j = 0; j < nbk; ++j) {
-    const double piv = S[j][j];
-    const bool bad = ldl ? (piv == 0.0 || !isfinite(piv)) : !(piv > 0.0) || !isfinite(piv);
-    if (bad) {
-      if (tid == 0) { fail = 1; atomicCAS(J.info, -1, J.col0 + j); }
-      __syncthreads();
-      break;
+  auto bad = [&](double v) { return ldl ? (v == 0.0 || !isfinite(v)) : (!(v > 0.0) || !isfinite(v)); };
+  if (tid == 0) {
+    const double v = S[0][0];
+    if (bad(v)) { fail = 1; atomicCAS(J.info, -1, J.col0); }
+    else ip[0] = 1.0 / v;
+  }
+  __syncthreads();
+  for (int j = 0; j + 1 < nbk; ++j) {
+    if (fail) break;
+    const int m = nbk - 1 - j, Tj = m * (m + 1) / 2, skip = Tj - m;  // skip: entry of (j+1, j+1)
+    const double ipj = ip[j];
+    if (tid == 0) {
+      const double v = fma(-S[j + 1][j], S[j + 1][j] * ipj, S[j + 1][j + 1]);
+      S[j + 1][j + 1] = v;
+      if (bad(v)) { fail = 1; atomicCAS(J.info, -1, J.col0 + j + 1); }
+      else ip[j + 1] = 1.0 / v;
     }
-    const double sj = ldl ? piv : sqrt(piv);
-    __syncthreads();  // everyone has read S[j][j]
-    for (int r = j + 1 + tid; r < nbk; r += blockDim.x) S[r][j] = S[r][j] / sj;
-    if (tid == 0) S[j][j] = ldl ? piv : sj;
-    __syncthreads();
-    // trailing update of the lower triangle: thread owns column c = tid % 64, rows tid / 64 + 4 i
-    const int c = tid & (PB - 1);
-    if (c > j && c < nbk) {
-      const double lcj = S[c][j] * (ldl ? piv : 1.0);
-      for (int r = (tid >> 6); r < nbk; r += 4)
-        if (r >= c) S[r][c] -= S[r][j] * lcj;
+    for (int e = tid; e < Tj; e += blockDim.x) {
+      if (e == skip) continue;
+      const int rc = tab[e], r = rc & 255, c = rc >> 8;
+      S[r][c] = fma(-S[r][j], S[c][j] * ipj, S[r][c]);
     }
     __syncthreads();
   }
   if (fail) return;
+  // scale the columns: L in S, 1 / l_jj in idg
+  if (tid < nbk) idg[tid] = ldl ? 1.0 : 1.0 / sqrt(S[tid][tid]);
+  __syncthreads();
   for (int e = tid; e < nbk * nbk; e += blockDim.x) {
     const int r = e % nbk, c = e / nbk;
-    if (r > c) A[r + (size_t)c * lda] = S[r][c];
-    else if (r == c) {
-      if (ldl) { J.dvec[J.col0 + r] = S[r][r]; A[r + (size_t)c * lda] = 1.0; }
-      else A[r + (size_t)c * lda] = S[r][r];
+    double x = 0.0;
+    if (r > c) S[r][c] = S[r][c] * (ldl ? ip[c] : idg[c]);
+    if (r == c) x = idg[r];
+    X[r][c] = x;
+  }
+  __syncthreads();
+  if (tid < nbk) {
+    if (ldl) { J.dvec[J.col0 + tid] = S[tid][tid]; S[tid][tid] = 1.0; }
+    else S[tid][tid] = sqrt(S[tid][tid]);
+  }
+  __syncthreads();
+  // X = L^{-1}: step r reads the finished row r and updates rows r' > r, columns c <= r
+  for (int r = 0; r + 1 < nbk; ++r) {
+    const int w = r + 1, cnt = (nbk - 1 - r) * w;
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      const int rr = r + 1 + e / w, c = e % w;
+      double v = fma(-S[rr][r], X[r][c], X[rr][c]);
+      if (rr == r + 1) v *= idg[rr];
+      X[rr][c] = v;
     }
+    __syncthreads();
+  }
+  for (int e = tid; e < nbk * nbk; e += blockDim.x) {
+    const int r = e % nbk, c = e / nbk;
+    if (r >= c) A[r + (size_t)c * lda] = S[r][c];
+    J.Binv[r + (size_t)c * J.ldb] = (r >= c) ? X[r][c] : 0.0;
   }
 }
 
-// X (m x nbk) <- X L^{-T} (Cholesky) or X L^{-T} D^{-1} (LDL^T, unit L), L the
-// factored nbk x nbk diagonal block.  One thread per row of X; 64 rows per CTA.  The
-// block is staged in shared memory with one coalesced load: the substitution reads
-// it by rows, which in the column-major array would touch a new cache line per step.
-__global__ void __launch_bounds__(64) k_trsm_panel_right(const PanelJob* __restrict__ jobs, int ldl) {
+// Panel below a factored block, in place: X (m x nbk) <- X Binv^T (Cholesky:
+// X L^{-T}), or for LDL^T W <- X Binv^T and X <- W D^{-1}.  Each CTA owns 8 whole
+// rows, so it reads them completely before writing them back; thread (r, g) forms
+// columns g, g + 16, g + 32, g + 48 of row r, which balances the triangular
+// reductions across warps.
+__global__ void __launch_bounds__(128) k_panel_apply(const PanelJob* __restrict__ jobs, int ldl) {
   const PanelJob J = jobs[blockIdx.y];
   const int nbk = J.nbk, m = J.m;
-  const int tid = threadIdx.x, r0 = blockIdx.x * PB;
+  const int tid = threadIdx.x, r0 = blockIdx.x * 8;
   if (r0 >= m) return;
-  extern __shared__ double dsm[];
-  double (*Ls)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm);
-  double (*Xs)[PB + 1] = reinterpret_cast<double (*)[PB + 1]>(dsm + PB * (PB + 1));
-  for (int e = tid; e < nbk * nbk; e += 64) {
+  __shared__ double Bs[PB][PB + 1];
+  __shared__ double Xs[8][PB + 1];
+  for (int e = tid; e < nbk * nbk; e += 128) {
     const int r = e % nbk, c = e / nbk;
-    Ls[r][c] = J.L[r + (size_t)c * J.lda];
+    Bs[r][c] = J.Binv[r + (size_t)c * J.ldb];
   }
-  const int rows = min(PB, m - r0);
-  for (int e = tid; e < rows * nbk; e += 64) {
-    const int r = e % rows, c = e / rows;
-    Xs[r][c] = J.X[(r0 + r) + (size_t)c * J.ldx];
+  const int rows = min(8, m - r0);
+  for (int e = tid; e < 8 * nbk; e += 128) {
+    const int r = e % 8, c = e / 8;
+    Xs[r][c] = r < rows ? J.X[(r0 + r) + (size_t)c * J.ldx] : 0.0;
   }
   __syncthreads();
-  if (tid < rows) {
-    for (int c = 0; c < nbk; ++c) {
-      double v = Xs[tid][c];
-      for (int l = 0; l < c; ++l) v = fma(-Ls[c][l], Xs[tid][l], v);
-      Xs[tid][c] = ldl ? v : v / Ls[c][c];
+  const int r = tid & 7, g = tid >> 3;
+  double out[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = g + 16 * q;
+    double v = 0.0;
+    if (c < nbk)
+      for (int l = 0; l <= c; ++l) v = fma(Xs[r][l], Bs[c][l], v);
+    out[q] = v;
+  }
+  if (r >= rows) return;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int c = g + 16 * q;
+    if (c >= nbk) continue;
+    const size_t gi = (r0 + r) + (size_t)c * J.ldx;
+    if (ldl) {
+      J.W[(r0 + r) + (size_t)c * m] = out[q];
+      J.X[gi] = out[q] / J.dvec[c];
+    } else {
+      J.X[gi] = out[q];
     }
-    if (ldl)
-      for (int c = 0; c < nbk; ++c) Xs[tid][c] /= J.dvec[c];
-  }
-  __syncthreads();
-  for (int e = tid; e < rows * nbk; e += 64) {
-    const int r = e % rows, c = e / rows;
-    J.X[(r0 + r) + (size_t)c * J.ldx] = Xs[r][c];
   }
 }
 
@@ -438,23 +499,23 @@ __global__ void __launch_bounds__(64) k_trsm_left_block(const LeftJob* __restric
 static void smem_attrs() {
   static bool done = false;
   if (done) return;
-  TLR_CUDA(cudaFuncSetAttribute(k_trsm_panel_right, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_block_smem()));
+  TLR_CUDA(cudaFuncSetAttribute(k_potrf_inv_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_inv_smem()));
   TLR_CUDA(cudaFuncSetAttribute(k_trsm_left_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)two_block_smem()));
   done = true;
 }
 
-void potrf_blocks(tlr_ctx* ctx, std::vector<PotrfJob>& jobs, int ldl) {
+void potrf_inv_blocks(tlr_ctx* ctx, std::vector<PotrfJob>& jobs, int ldl) {
+  smem_attrs();
   for (size_t o = 0; o < jobs.size(); o += 65535) {
     const int cnt = (int)std::min<size_t>(65535, jobs.size() - o);
     TLR_REQUIRE(std::all_of(jobs.begin() + o, jobs.begin() + o + cnt, [](const PotrfJob& j) { return j.nbk <= PB; }),
                 TLR_ERR_LIMIT, "potrf block above 64");
     const PotrfJob* dj = static_cast<const PotrfJob*>(upload(ctx, jobs.data() + o, cnt * sizeof(PotrfJob)));
-    k_potrf_block<<<dim3(1, (unsigned)cnt), 256, 0, ctx->stream>>>(dj, ldl);
+    k_potrf_inv_block<<<dim3(1, (unsigned)cnt), 256, potrf_inv_smem(), ctx->stream>>>(dj, ldl);
     TLR_LAUNCH_CHECK(ctx);
   }
 }
-void trsm_panels(tlr_ctx* ctx, std::vector<PanelJob>& jobs, int ldl) {
-  smem_attrs();
+void panel_apply(tlr_ctx* ctx, std::vector<PanelJob>& jobs, int ldl) {
   int mx = 0;
   std::vector<PanelJob> nz;
   for (auto& j : jobs)
@@ -462,7 +523,7 @@ void trsm_panels(tlr_ctx* ctx, std::vector<PanelJob>& jobs, int ldl) {
   for (size_t o = 0; o < nz.size(); o += 65535) {
     const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
     const PanelJob* dj = static_cast<const PanelJob*>(upload(ctx, nz.data() + o, cnt * sizeof(PanelJob)));
-    k_trsm_panel_right<<<dim3(cdiv(mx, PB), (unsigned)cnt), 64, two_block_smem(), ctx->stream>>>(dj, ldl);
+    k_panel_apply<<<dim3(cdiv(mx, 8), (unsigned)cnt), 128, 0, ctx->stream>>>(dj, ldl);
     TLR_LAUNCH_CHECK(ctx);
   }
 }
@@ -480,15 +541,6 @@ void trsm_lefts(tlr_ctx* ctx, std::vector<LeftJob>& jobs, int unit, int trans) {
   }
 }
 
-void potrf_diag_block(tlr_ctx* ctx, int nbk, double* A, int lda, int ldl, double* dvec, int* info, int col0) {
-  std::vector<PotrfJob> j{PotrfJob{A, dvec, info, lda, col0, nbk}};
-  potrf_blocks(ctx, j, ldl);
-}
-void trsm_panel_right(tlr_ctx* ctx, int m, int nbk, const double* L, int lda, double* X, int ldx, int ldl,
-                      const double* dvec) {
-  std::vector<PanelJob> j{PanelJob{L, X, dvec, lda, ldx, m, nbk}};
-  trsm_panels(ctx, j, ldl);
-}
 void trsm_left_block(tlr_ctx* ctx, int nbk, const double* L, int lda, int unit, int nrhs, double* X, int ldx) {
   std::vector<LeftJob> j{LeftJob{L, X, lda, ldx, nrhs, nbk}};
   trsm_lefts(ctx, j, unit, 0);

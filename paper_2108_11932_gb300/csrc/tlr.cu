@@ -165,50 +165,66 @@ void d2h_sync(tlr_ctx* ctx, void* host, const void* dev, size_t bytes) {
 
 // ======================================================================== dense diagonal tiles
 // Blocked right-looking Cholesky / unpivoted LDL^T of lower n x n tiles, all tiles
-// of the batch advancing block by block in the same launches.  info (device int)
-// must hold -1 on entry and receives the first failing column of its tile.
+// of the batch advancing block by block in the same launches.  Each 64-column step:
+// factor the diagonal block and invert its factor (one CTA per tile), apply the
+// inverse to the panel below it (in place), and update the trailing lower triangle
+// with one batched GEMM.  info (device int) must hold -1 on entry and receives the
+// first failing column of its tile.  When a tile has Linv, the block inverses go to
+// its diagonal blocks (dense_trinv_batch completes the inverse from them) and the
+// rest of Linv is zeroed here; otherwise they go to tmp.
+size_t dense_tmp_doubles(const std::vector<DenseTile>& tiles, int ldl) {
+  size_t f = 0, t = 0;
+  for (auto& x : tiles) {
+    f += (ldl ? (size_t)x.n * NBK : 0) + (x.Linv ? 0 : (size_t)NBK * NBK);
+    t += (size_t)x.n * x.n / 4 + NBK;
+  }
+  return std::max<size_t>(std::max(f, t), 1);
+}
+
 void dense_factor_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int ldl, Buf& tmp) {
   int nmax = 0;
-  for (auto& t : tiles) nmax = std::max(nmax, t.n);
+  size_t wtot = 0;
+  for (auto& t : tiles) {
+    nmax = std::max(nmax, t.n);
+    wtot += (ldl ? (size_t)t.n * NBK : 0) + (t.Linv ? 0 : (size_t)NBK * NBK);
+    if (t.Linv) TLR_CUDA(cudaMemsetAsync(t.Linv, 0, sizeof(double) * (size_t)t.n * t.n, ctx->stream));
+  }
+  double* base = tmp.need<double>(std::max<size_t>(wtot, 1));
+  std::vector<double*> Wt(tiles.size()), Bt(tiles.size());
+  {
+    size_t o = 0;
+    for (size_t i = 0; i < tiles.size(); ++i) {
+      Wt[i] = ldl ? base + o : nullptr;
+      o += ldl ? (size_t)tiles[i].n * NBK : 0;
+      Bt[i] = tiles[i].Linv ? nullptr : base + o;
+      o += tiles[i].Linv ? 0 : (size_t)NBK * NBK;
+    }
+  }
   for (int p = 0; p < nmax; p += NBK) {
     std::vector<PotrfJob> pj;
     std::vector<PanelJob> qj;
-    std::vector<ScaleJob> sj;
     std::vector<GemmJob<double>> gj;
-    int64_t wtot = 0;
-    for (auto& t : tiles)
-      if (ldl && p < t.n) wtot += (int64_t)std::max(0, t.n - p - NBK) * std::min(NBK, t.n - p);
-    double* W = ldl ? tmp.need<double>((size_t)std::max<int64_t>(wtot, 1)) : nullptr;
-    int64_t wo = 0;
-    for (auto& t : tiles) {
+    for (size_t i = 0; i < tiles.size(); ++i) {
+      auto& t = tiles[i];
       if (p >= t.n) continue;
       const int pb = std::min(NBK, t.n - p), lda = t.lda;
       double* App = t.A + p + (size_t)p * lda;
-      pj.push_back(PotrfJob{App, t.dvec, t.info, lda, p, pb});
+      double* Binv = t.Linv ? t.Linv + p + (size_t)p * t.n : Bt[i];
+      const int ldb = t.Linv ? t.n : NBK;
+      pj.push_back(PotrfJob{App, t.dvec, t.info, Binv, lda, p, pb, ldb});
       const int m = t.n - p - pb;
       if (m <= 0) continue;
       double* P = t.A + (p + pb) + (size_t)p * lda;
-      qj.push_back(PanelJob{App, P, ldl ? t.dvec + p : nullptr, lda, lda, m, pb});
-      const double* Pl = P;
-      int ldpl = lda;
-      if (ldl) {
-        // W = P D_p (the trailing update of LDL^T is P D_p P^T): column c of P, seen as a
-        // 1 x m row, scaled by the single entry d_{p+c}
-        for (int c = 0; c < pb; ++c)
-          sj.push_back(ScaleJob{t.dvec + p + c, P + (size_t)c * lda, W + wo + (size_t)c * m, 1, m, 1, 1, 0});
-        Pl = W + wo;
-        ldpl = m;
-        wo += (int64_t)m * pb;
-      }
-      GemmJob<double> g = job<double>(NT, m, m, Pl, ldpl, P, lda, pb, t.A + (p + pb) + (size_t)(p + pb) * lda, lda,
-                                      -1.0, 1.0);
+      qj.push_back(PanelJob{Binv, P, ldl ? t.dvec + p : nullptr, Wt[i], ldb, lda, m, pb});
+      // trailing update: Cholesky P P^T; LDL^T W P^T with W = P D (written by the panel step)
+      GemmJob<double> g = job<double>(NT, m, m, ldl ? Wt[i] : P, ldl ? m : lda, P, lda, pb,
+                                      t.A + (p + pb) + (size_t)(p + pb) * lda, lda, -1.0, 1.0);
       g.flags = GEMM_TRIL;
       gj.push_back(g);
     }
     if (pj.empty()) break;
-    potrf_blocks(ctx, pj, ldl);
-    trsm_panels(ctx, qj, ldl);
-    batched_scale_rows(ctx, sj);  // after the pivots and the panel are known
+    potrf_inv_blocks(ctx, pj, ldl);
+    panel_apply(ctx, qj, ldl);
     gemm<double>(ctx, NT, gj);
   }
 }
@@ -242,33 +258,41 @@ void dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int unit, int nrh
   }
 }
 
-// Linv = L^{-1} for lower-triangular tiles (unit diagonal if `unit`), Linv lower
-// triangular (ld n).  Blocked substitution on the identity: row block p of Linv
-// only has nonzeros in its first p + pb columns, so each step solves and updates
-// only those (n^3/3 flops instead of n^3).
-void dense_trinv_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int unit) {
+// Linv = L^{-1} for the tiles factored by dense_factor_batch (which left the
+// inverses of the 64 x 64 diagonal blocks in Linv and zeros elsewhere).  Recursive
+// doubling on the block lower-triangular structure: with Linv known on two
+// consecutive diagonal blocks of width s, [A 0; B C]^{-1} = [A^-1 0; -C^-1 B A^-1 C^-1],
+// so each level fills the off-diagonal blocks of all pairs with two batched GEMMs
+// (T = B A^-1, then -C^-1 T).  log2(n / 64) levels; every level's products are
+// large enough to occupy the whole GPU.
+void dense_trinv_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int, Buf& tmp) {
   int nmax = 0;
-  std::vector<DiagJob> dj;
+  size_t ttot = 0;
   for (auto& t : tiles) {
     nmax = std::max(nmax, t.n);
-    TLR_CUDA(cudaMemsetAsync(t.Linv, 0, sizeof(double) * (size_t)t.n * t.n, ctx->stream));
-    dj.push_back(DiagJob{t.Linv, t.n, t.n, 1.0});
+    ttot += (size_t)t.n * t.n / 4 + NBK;
   }
-  batched_add_diag(ctx, dj);
-  for (int p = 0; p < nmax; p += NBK) {
-    std::vector<LeftJob> lj;
-    std::vector<GemmJob<double>> gj;
+  double* T = tmp.need<double>(std::max<size_t>(ttot, 1));
+  for (int s = NBK; s < nmax; s *= 2) {
+    std::vector<GemmJob<double>> j1, j2;
+    size_t off = 0;
     for (auto& t : tiles) {
-      if (p >= t.n) continue;
-      const int pb = std::min(NBK, t.n - p);
-      lj.push_back(LeftJob{t.A + p + (size_t)p * t.lda, t.Linv + p, t.lda, t.n, p + pb, pb});
-      const int m = t.n - p - pb;
-      if (m > 0)
-        gj.push_back(job<double>(NN, m, p + pb, t.A + (p + pb) + (size_t)p * t.lda, t.lda, t.Linv + p, t.n, pb,
-                                 t.Linv + p + pb, t.n, -1.0, 1.0));
+      const size_t tile_off = off;
+      off += (size_t)t.n * t.n / 4 + NBK;
+      size_t o2 = tile_off;
+      for (int o = 0; o + s < t.n; o += 2 * s) {
+        const int h = std::min(s, t.n - o - s);
+        const double* B = t.A + (o + s) + (size_t)o * t.lda;
+        const double* Ai = t.Linv + o + (size_t)o * t.n;
+        const double* Ci = t.Linv + (o + s) + (size_t)(o + s) * t.n;
+        double* Tp = T + o2;
+        o2 += (size_t)h * s;
+        j1.push_back(job<double>(NN, h, s, B, t.lda, Ai, t.n, s, Tp, h, 1.0, 0.0));
+        j2.push_back(job<double>(NN, h, s, Ci, t.n, Tp, h, h, t.Linv + (o + s) + (size_t)o * t.n, t.n, -1.0, 0.0));
+      }
     }
-    trsm_lefts(ctx, lj, unit, 0);
-    gemm<double>(ctx, NN, gj);
+    gemm<double>(ctx, NN, j1);
+    gemm<double>(ctx, NN, j2);
   }
 }
 
