@@ -55,9 +55,10 @@ struct GemmJob {
   int tile0;     // first linear CTA of this job
   int tiles_m, tiles_n, nsplit;
   int flags;     // GEMM_TRIL: write only C(m, n) with m >= n; skip tiles strictly above
+                 // GEMM_ALOWER: op(A_0) is lower triangular (NN only): row m reads k <= m
   double alpha, beta;
 };
-enum { GEMM_TRIL = 1 };
+enum { GEMM_TRIL = 1, GEMM_ALOWER = 2 };
 enum GemmMode { NN = 0, TN = 1, NT = 2 };
 
 constexpr int GEMM_TK = 16;

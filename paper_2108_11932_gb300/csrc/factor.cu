@@ -845,10 +845,12 @@ struct Session {
       F->vlen[M.k] = M.Rk;
       if (M.Rk > 0) {
         // V_ik = L_kk^{-1} B_i (LDL^T: then D_k^{-1}, batchIDMult)
-        jt.push_back(job<double>(NN, b, (int)M.Rk, F->dinv + (size_t)M.k * b * b, b, static_cast<double*>(M.Bc.p), b, b,
-                                 F->Vcol[M.k], b, 1.0, 0.0));
+        GemmJob<double> g = job<double>(NN, b, (int)M.Rk, F->dinv + (size_t)M.k * b * b, b,
+                                        static_cast<double*>(M.Bc.p), b, b, F->Vcol[M.k], b, 1.0, 0.0);
+        g.flags = GEMM_ALOWER;  // L_kk^{-1} is lower triangular
+        jt.push_back(g);
         if (M.ldl) sj.push_back(ScaleJob{F->dvec + (size_t)M.k * b, F->Vcol[M.k], F->Vcol[M.k], b, (int)M.Rk, b, b, 1});
-        M.fl_exec += 2.0 * b * b * M.Rk;
+        M.fl_exec += (double)b * (b + 1) * M.Rk;
         M.fl_model += (double)b * b * M.Rk;
       }
     }

@@ -68,7 +68,9 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmJob<T>* __restrict__ job
     for (int j = 0; j < RN; ++j) acc[i][j] = T(0);
 
   // The K chunks of both segments form one sequence; this CTA takes slice [c0, c1).
-  const int nch0 = (J.K[0] + TK - 1) / TK, nch1 = J.K[1] > 0 ? (J.K[1] + TK - 1) / TK : 0;
+  // A lower-triangular first operand contributes nothing beyond k = m0 + TM - 1.
+  const int K0 = (MODE == NN && (J.flags & GEMM_ALOWER)) ? min(J.K[0], m0 + TM) : J.K[0];
+  const int nch0 = (K0 + TK - 1) / TK, nch1 = J.K[1] > 0 ? (J.K[1] + TK - 1) / TK : 0;
   const int nch = nch0 + nch1;
   const int c0 = (int)((int64_t)nch * split / J.nsplit);
   const int c1 = (int)((int64_t)nch * (split + 1) / J.nsplit);
@@ -232,7 +234,11 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
   const int nj = (int)jobs.size();
   double flops = 0;
   if (ctx->kprof) {
-    for (auto& j : jobs) flops += 2.0 * j.M * j.N * (double)(j.K[0] + j.K[1]) * ((j.flags & GEMM_TRIL) ? 0.5 : 1.0);
+    for (auto& j : jobs) {
+      // algorithmic flops: a triangular C or a triangular A halves the product
+      const double k0 = (mode == NN && (j.flags & GEMM_ALOWER)) ? 0.5 * (j.K[0] + 1) : (double)j.K[0];
+      flops += 2.0 * j.M * j.N * (k0 + j.K[1]) * ((j.flags & GEMM_TRIL) ? 0.5 : 1.0);
+    }
     kprof_begin(ctx);
   }
   if (mode == NN) k_gemm<T, NN, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
