@@ -465,8 +465,15 @@ def run_phases(args, w, eps):
     x = inputs.points(w["N"], w["d"], w["seed"])
     prec = T.PREC_FP64 if args.precision == "fp64" else T.PREC_FP32
     o = T.default_opts(bs=w["bs"], seed=w["seed"], precision=prec)
+    if args.profile_compress:
+        ctx.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], o)
-    ctx.profile(True)
+    torch.cuda.synchronize()
+    compress_s = time.perf_counter() - t0
+    if not args.profile_compress:
+        ctx.profile(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     A.potrf(eps, o)
@@ -474,9 +481,12 @@ def run_phases(args, w, eps):
     wall = time.perf_counter() - t0
     prof = ctx.profile(False)
     inf = A.info()
-    out = {"workload": _workload_desc(w, eps, args.precision.upper()), "factor_s": wall,
+    out = {"workload": _workload_desc(w, eps, args.precision.upper()), "compress_s": compress_s, "factor_s": wall,
+           "profiled": "compress + factor" if args.profile_compress else "factor",
            "flops_exec": inf["flops_exec"], "flops_fp32": inf["flops_fp32"], "mean_rank": inf["mean_rank"],
            "phases_ms": {k: v[0] for k, v in prof.items()}, "phase_launches": {k: v[1] for k, v in prof.items()}}
+    A.free()
+    ctx.close()  # writes the per-call-site table when TLR_SITE_PROFILE is set
     print(json.dumps(out), flush=True)
 
 
@@ -495,6 +505,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--profile-compress", action="store_true",
+                    help="phases mode: profile the compression as well as the factorization")
     ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve", "peaks", "phases"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--requests", type=int, default=200)

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <stdexcept>
+#include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -36,6 +38,7 @@ struct Error : std::runtime_error {
   do {                        \
     (ctx)->launches++;        \
     TLR_CUDA(cudaPeekAtLastError()); \
+    if ((ctx)->site_out && (ctx)->prof) ::tlr::site_tick((ctx), __FILE__, __LINE__); \
   } while (0)
 
 // Ω streams: which factorization step a Gaussian block belongs to.
@@ -50,6 +53,7 @@ struct GemmJob {
   const T* B[2];
   T* C;
   T* ws;         // split-K partials: nsplit x M x N (column-major), or null
+  int* ctr;      // split-K: arrival counter per output tile (tiles_m x tiles_n)
   int lda[2], ldb[2], K[2];
   int ldc, M, N;
   int tile0;     // first linear CTA of this job
@@ -87,6 +91,10 @@ struct tlr_ctx {
   size_t scratch_cap = 0;
   void* scratch_side = nullptr;  // the side stream's own split-K scratch
   size_t scratch_side_cap = 0;
+  // split-K arrival counters (zero between launches; the reducing CTA resets its
+  // own), one array per stream
+  int* split_ctr[2] = {nullptr, nullptr};
+  size_t split_ctr_cap[2] = {0, 0};
   // Small host-pinned status buffer for per-round device->host reads.
   void* hstatus = nullptr;
   size_t hstatus_cap = 0;
@@ -108,6 +116,19 @@ struct tlr_ctx {
   size_t kev_n = 0;
   double kfam_ms[8] = {0}, kfam_flops[8] = {0};
   int64_t kfam_launches[8] = {0};
+  // Per-call-site launch profile (diagnostics): while tlr_profile is enabled and the
+  // TLR_SITE_PROFILE environment variable names a file, which receives the table at
+  // tlr_destroy.  An
+  // event follows every launch; a launch is charged the time between the previous
+  // event of its stream and its own, i.e. its device time while the stream is busy.
+  FILE* site_out = nullptr;
+  std::vector<cudaEvent_t> sev[2];
+  std::vector<int> sev_site[2];
+  size_t sev_n[2] = {0, 0};
+  std::map<std::pair<const char*, int>, int> site_id;
+  std::vector<std::string> site_name;
+  std::vector<double> site_ms;
+  std::vector<int64_t> site_count;
 };
 
 struct tlr_mat {
@@ -146,11 +167,29 @@ void prof_flush(tlr_ctx* ctx);
 void kprof_begin(tlr_ctx* ctx);
 void kprof_end(tlr_ctx* ctx, int family, double flops);
 void kprof_flush(tlr_ctx* ctx);
+void site_tick(tlr_ctx* ctx, const char* file, int line);
+// an event just before a launch: the time since the stream's previous event is
+// charged to "gaps" (copies, waits, host delays), so that the launch's own site
+// receives its device time only
+#define TLR_SITE_PRE(ctx) \
+  do {                    \
+    if ((ctx)->site_out && (ctx)->prof) ::tlr::site_tick_on((ctx), (ctx)->stream, nullptr, 0); \
+  } while (0)
+// marks the end of a wait (event wait, host synchronization) on a stream
+void site_tick_on(tlr_ctx* ctx, cudaStream_t stream, const char* file, int line);
+#define TLR_SITE_MARK(ctx, stream) \
+  do {                                \
+    if ((ctx)->site_out && (ctx)->prof) ::tlr::site_tick_on((ctx), (stream), __FILE__, __LINE__); \
+  } while (0)
+void site_flush(tlr_ctx* ctx);
+void site_report(tlr_ctx* ctx);
 
 // memory
 void* dalloc(tlr_ctx* ctx, size_t bytes);
 void dfree(tlr_ctx* ctx, void* p);
 void* scratch(tlr_ctx* ctx, size_t bytes);
+// zeroed split-K arrival counters for the current stream (at least n)
+int* split_counters(tlr_ctx* ctx, size_t n);
 void* upload(tlr_ctx* ctx, const void* host, size_t bytes);  // returns device copy (ring)
 void* host_status(tlr_ctx* ctx, size_t bytes);               // pinned host buffer
 
@@ -227,10 +266,17 @@ struct SlotDescT {
   T* Z;
   int ldx, ldx0, nb, k, i, r0, x0off, Ki, Kk, q, bs;
 };
+// one 16 x 16 output tile of a block-diagonal Gram product: slot, block column j
+// (j = k: the tile's own factor part), row chunk, column chunk
+struct BlkItem {
+  uint32_t slot;
+  uint16_t j;
+  uint8_t rc, cc;  // ranks and widths are at most 1024: 64 chunks
+};
 template <typename T>
-void blkdiag_sample(tlr_ctx* ctx, int nslots, int kmax, const SlotDescT<T>* slots_dev);
+void blkdiag_sample(tlr_ctx* ctx, const std::vector<BlkItem>& items, const SlotDescT<T>* slots_dev);
 template <typename T>
-void blkdiag_project(tlr_ctx* ctx, int nslots, int kmax, const SlotDescT<T>* slots_dev);
+void blkdiag_project(tlr_ctx* ctx, const std::vector<BlkItem>& items, const SlotDescT<T>* slots_dev);
 
 struct OmegaJob {
   double* out;

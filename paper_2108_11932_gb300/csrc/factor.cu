@@ -175,7 +175,18 @@ struct BatchSampler : Sampler {
     T* W = bw->need<T>((size_t)std::max<int64_t>(wtot, 1));
     for (auto& d : sd) d.W = W + reinterpret_cast<size_t>(d.W);
     const SlotDescT<T>* sdd = static_cast<const SlotDescT<T>*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDescT<T>)));
-    blkdiag_sample<T>(ctx, (int)ops.size(), kmx, sdd);
+    std::vector<BlkItem> items;
+    for (size_t s = 0; s < ops.size(); ++s) {  // -G_ij X_j: r_ij x bs tiles; the X0 copy: r0 x bs
+      const Mat& M = *(*L)[(*op_m)[ops[s]]];
+      const int i = sd[s].i;
+      for (int j = 0; j <= M.k; ++j) {
+        const int R = j < M.k ? M.F->rank[ix(M.F, i, j)] : sd[s].r0;
+        for (int rc = 0; 16 * rc < R; ++rc)
+          for (int cc = 0; 16 * cc < bs; ++cc)
+            items.push_back(BlkItem{(uint32_t)s, (uint16_t)j, (uint8_t)rc, (uint8_t)cc});
+      }
+    }
+    blkdiag_sample<T>(ctx, items, sdd);
     T* Y32 = F32 ? reinterpret_cast<T*>(by32->need<float>((size_t)ytot)) : nullptr;
     std::vector<GemmJob<T>> jy;
     std::vector<ConvBackJob> cb;
@@ -278,7 +289,17 @@ struct BatchSampler : Sampler {
     }
     gemm<T>(ctx, TN, jp);
     const SlotDescT<T>* sdd = static_cast<const SlotDescT<T>*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDescT<T>)));
-    blkdiag_project<T>(ctx, (int)ops.size(), kmx, sdd);
+    std::vector<BlkItem> items;
+    for (size_t s = 0; s < ops.size(); ++s) {  // -G_ij^T P_j: r_kj x q tiles; the P0 copy: r0 x q
+      const Mat& M = *(*L)[(*op_m)[ops[s]]];
+      for (int j = 0; j <= M.k; ++j) {
+        const int R = j < M.k ? M.F->rank[ix(M.F, M.k, j)] : sd[s].r0;
+        for (int rc = 0; 16 * rc < R; ++rc)
+          for (int cc = 0; 16 * cc < sd[s].q; ++cc)
+            items.push_back(BlkItem{(uint32_t)s, (uint16_t)j, (uint8_t)rc, (uint8_t)cc});
+      }
+    }
+    blkdiag_project<T>(ctx, items, sdd);
     std::vector<GemmJob<T>> jb;
     std::vector<ConvBackJob> cb;
     for (size_t s = 0; s < ops.size(); ++s) {

@@ -134,46 +134,63 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmJob<T>* __restrict__ job
     }
     __syncthreads();
   }
-  if (!active) return;
   const T alpha = (T)J.alpha, beta = (T)J.beta;
+  if (J.nsplit == 1) {
+    if (!active) return;
 #pragma unroll
-  for (int i = 0; i < RM; ++i) {
-    const int gm = m0 + tr * RM + i;
-    if (gm >= M) continue;
+    for (int i = 0; i < RM; ++i) {
+      const int gm = m0 + tr * RM + i;
+      if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < RN; ++j) {
-      const int gn = n0 + tc * RN + j;
-      if (gn >= N) continue;
-      if (J.nsplit > 1) {
-        J.ws[(size_t)split * M * N + gm + (size_t)gn * M] = acc[i][j];
-      } else {
-        if ((J.flags & GEMM_TRIL) && gm < gn) continue;
+      for (int j = 0; j < RN; ++j) {
+        const int gn = n0 + tc * RN + j;
+        if (gn >= N || ((J.flags & GEMM_TRIL) && gm < gn)) continue;
         T* c = J.C + gm + (size_t)gn * J.ldc;
         T v = alpha * acc[i][j];
         if (J.beta != 0.0) v += beta * *c;
         *c = v;
       }
     }
+    return;
   }
-}
-
-// Fixed-order reduction of split-K partials: C = alpha * sum_s ws[s] + beta * C.
-// Partials of tiles that were skipped (strictly above the diagonal of a GEMM_TRIL
-// job) are never read: every entry of such a tile has m < n.
-template <typename T>
-__global__ void k_gemm_reduce(const GemmJob<T>* __restrict__ jobs, const int* __restrict__ ids) {
-  const GemmJob<T>& J = jobs[ids[blockIdx.x]];
-  const size_t MN = (size_t)J.M * J.N;
-  for (size_t e = blockIdx.y * (size_t)blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.y * blockDim.x) {
-    const int gm = (int)(e % J.M), gn = (int)(e / J.M);
-    if ((J.flags & GEMM_TRIL) && gm < gn) continue;
-    T s = T(0);
-    for (int sp = 0; sp < J.nsplit; ++sp) s += J.ws[(size_t)sp * MN + e];
+  // Split K: store the partial; the CTA that completes the tile's set of slices
+  // (arrival counter) sums all partials in slice order and writes C, then resets
+  // the counter.  No CTA waits for another.  A tile strictly above the diagonal
+  // of a GEMM_TRIL job returned before its first chunk in every slice, so its
+  // counter is never touched.
+  const size_t MN = (size_t)M * N;
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < RM; ++i) {
+      const int gm = m0 + tr * RM + i;
+      if (gm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < RN; ++j) {
+        const int gn = n0 + tc * RN + j;
+        if (gn < N) J.ws[(size_t)split * MN + gm + (size_t)gn * M] = acc[i][j];
+      }
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  __shared__ int last;
+  int* ctr = J.ctr + (m0 / TM) * J.tiles_n + (n0 / TN_);
+  if (tid == 0) last = (atomicAdd(ctr, 1) == J.nsplit - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = tid; e < TM * TN_; e += 128) {
+    const int gm = m0 + e % TM, gn = n0 + e / TM;
+    if (gm >= M || gn >= N || ((J.flags & GEMM_TRIL) && gm < gn)) continue;
+    const size_t o = gm + (size_t)gn * M;
+    T v = T(0);
+    for (int sp = 0; sp < J.nsplit; ++sp) v += __ldcg(J.ws + (size_t)sp * MN + o);
     T* c = J.C + gm + (size_t)gn * J.ldc;
-    T v = (T)J.alpha * s;
-    if (J.beta != 0.0) v += (T)J.beta * *c;
+    v = alpha * v;
+    if (J.beta != 0.0) v += beta * *c;
     *c = v;
   }
+  if (tid == 0) *ctr = 0;
 }
 
 template <typename T>
@@ -183,7 +200,7 @@ GemmJob<T> job(GemmMode, int M, int N, const T* A, int lda, const T* B, int ldb,
   j.A[0] = A; j.B[0] = B; j.lda[0] = lda; j.ldb[0] = ldb; j.K[0] = K;
   j.A[1] = nullptr; j.B[1] = nullptr; j.lda[1] = 1; j.ldb[1] = 1; j.K[1] = 0;
   j.C = C; j.ldc = ldc; j.M = M; j.N = N; j.alpha = alpha; j.beta = beta;
-  j.flags = 0; j.ws = nullptr;
+  j.flags = 0; j.ws = nullptr; j.ctr = nullptr;
   return j;
 }
 
@@ -227,7 +244,14 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
   TLR_REQUIRE(total < (1LL << 31), TLR_ERR_LIMIT, "gemm: too many tiles in one launch");
   if (ws_elems) {
     T* ws = static_cast<T*>(scratch(ctx, ws_elems * sizeof(T)));
-    for (int q : split_ids) jobs[q].ws = ws + reinterpret_cast<size_t>(jobs[q].ws);
+    size_t nctr = 0;
+    for (int q : split_ids) nctr += (size_t)jobs[q].tiles_m * jobs[q].tiles_n;
+    int* ctr = split_counters(ctx, nctr);
+    for (int q : split_ids) {
+      jobs[q].ws = ws + reinterpret_cast<size_t>(jobs[q].ws);
+      jobs[q].ctr = ctr;
+      ctr += (size_t)jobs[q].tiles_m * jobs[q].tiles_n;
+    }
   }
   const GemmJob<T>* dj =
       static_cast<const GemmJob<T>*>(upload(ctx, jobs.data(), jobs.size() * sizeof(GemmJob<T>)));
@@ -241,19 +265,12 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
     }
     kprof_begin(ctx);
   }
+  TLR_SITE_PRE(ctx);
   if (mode == NN) k_gemm<T, NN, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   else if (mode == TN) k_gemm<T, TN, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   else k_gemm<T, NT, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   TLR_LAUNCH_CHECK(ctx);
   if (ctx->kprof) kprof_end(ctx, (sizeof(T) == 8 ? 0 : 3) + (int)mode, flops);
-  if (!split_ids.empty()) {
-    const int* ids = static_cast<const int*>(upload(ctx, split_ids.data(), split_ids.size() * sizeof(int)));
-    size_t mx = 0;
-    for (int q : split_ids) mx = std::max(mx, (size_t)jobs[q].M * jobs[q].N);
-    dim3 rg((unsigned)split_ids.size(), (unsigned)std::min<size_t>(64, (mx + 255) / 256));
-    k_gemm_reduce<T><<<rg, 256, 0, ctx->stream>>>(dj, ids);
-    TLR_LAUNCH_CHECK(ctx);
-  }
 }
 
 template void gemm<double>(tlr_ctx*, GemmMode, std::vector<GemmJob<double>>&);

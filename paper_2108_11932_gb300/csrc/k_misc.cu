@@ -44,6 +44,7 @@ void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t,
            double* out) {
   const int n = b * bs;
   const int pairs = (n + 1) / 2;
+  TLR_SITE_PRE(ctx);
   k_omega<<<cdiv(pairs, 256), 256, 0, ctx->stream>>>((uint32_t)seed, (uint32_t)(seed >> 32), stream,
                                                       k, t, n, out);
   TLR_LAUNCH_CHECK(ctx);
@@ -78,6 +79,7 @@ void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, do
                const int* tile_ij, int ntiles, double* out) {
   if (ntiles <= 0) return;
   dim3 grid(std::min<unsigned>(cdiv((int64_t)b * b, 256), 64u), (unsigned)ntiles);
+  TLR_SITE_PRE(ctx);
   k_gen_tiles<<<grid, 256, 0, ctx->stream>>>(pts, N, d, 1.0 / ell, nugget, b, tile_ij, out);
   TLR_LAUNCH_CHECK(ctx);
 }
@@ -274,6 +276,7 @@ void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mou
                   double* enorm, const double* thr, double tau, int first_pass, const int* nk_in) {
   if (nslots <= 0) return;
   if (bs == 16 || bs == 32 || bs == 8) {
+    TLR_SITE_PRE(ctx);
     if (bs == 16)
       k_cholqr_reg<16><<<(unsigned)nslots, 32, 0, ctx->stream>>>(G, Mout, status, enorm, thr, tau, first_pass, nk_in);
     else if (bs == 32)
@@ -291,6 +294,7 @@ void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mou
                                   (int)(sizeof(double) * 2 * MAXBS * (MAXBS + 1) + sizeof(int) * MAXBS)));
     attr_set = true;
   }
+  TLR_SITE_PRE(ctx);
   k_cholqr_small<<<(unsigned)nslots, 32, smem, ctx->stream>>>(bs, G, Mout, status, enorm, thr, tau,
                                                                first_pass, nk_in);
   TLR_LAUNCH_CHECK(ctx);
@@ -511,6 +515,7 @@ void potrf_inv_blocks(tlr_ctx* ctx, std::vector<PotrfJob>& jobs, int ldl) {
     TLR_REQUIRE(std::all_of(jobs.begin() + o, jobs.begin() + o + cnt, [](const PotrfJob& j) { return j.nbk <= PB; }),
                 TLR_ERR_LIMIT, "potrf block above 64");
     const PotrfJob* dj = static_cast<const PotrfJob*>(upload(ctx, jobs.data() + o, cnt * sizeof(PotrfJob)));
+    TLR_SITE_PRE(ctx);
     k_potrf_inv_block<<<dim3(1, (unsigned)cnt), 256, potrf_inv_smem(), ctx->stream>>>(dj, ldl);
     TLR_LAUNCH_CHECK(ctx);
   }
@@ -523,6 +528,7 @@ void panel_apply(tlr_ctx* ctx, std::vector<PanelJob>& jobs, int ldl) {
   for (size_t o = 0; o < nz.size(); o += 65535) {
     const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
     const PanelJob* dj = static_cast<const PanelJob*>(upload(ctx, nz.data() + o, cnt * sizeof(PanelJob)));
+    TLR_SITE_PRE(ctx);
     k_panel_apply<<<dim3(cdiv(mx, 8), (unsigned)cnt), 128, 0, ctx->stream>>>(dj, ldl);
     TLR_LAUNCH_CHECK(ctx);
   }
@@ -536,6 +542,7 @@ void trsm_lefts(tlr_ctx* ctx, std::vector<LeftJob>& jobs, int unit, int trans) {
   for (size_t o = 0; o < nz.size(); o += 65535) {
     const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
     const LeftJob* dj = static_cast<const LeftJob*>(upload(ctx, nz.data() + o, cnt * sizeof(LeftJob)));
+    TLR_SITE_PRE(ctx);
     k_trsm_left_block<<<dim3(cdiv(mx, PB), (unsigned)cnt), 64, two_block_smem(), ctx->stream>>>(dj, unit, trans);
     TLR_LAUNCH_CHECK(ctx);
   }
@@ -563,6 +570,7 @@ __global__ void k_scale_rows(int m, int n, const double* __restrict__ dv, int in
 void scale_rows(tlr_ctx* ctx, int m, int n, const double* dvec, int inv, const double* X, int ldx,
                 double* Y, int ldy) {
   if ((int64_t)m * n <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_scale_rows<<<std::min<unsigned>(cdiv((int64_t)m * n, 256), 4096u), 256, 0, ctx->stream>>>(
       m, n, dvec, inv, X, ldx, Y, ldy);
   TLR_LAUNCH_CHECK(ctx);
@@ -573,6 +581,7 @@ __global__ void k_add_diag(int n, double* A, int lda, double s) {
   if (i < n) A[i + (size_t)i * lda] += s;
 }
 void add_diag(tlr_ctx* ctx, int n, double* A, int lda, double s) {
+  TLR_SITE_PRE(ctx);
   k_add_diag<<<cdiv(n, 256), 256, 0, ctx->stream>>>(n, A, lda, s);
   TLR_LAUNCH_CHECK(ctx);
 }
@@ -587,6 +596,7 @@ __global__ void k_add_rowsum_abs(int n, const double* __restrict__ E, int lde, d
   if (lane == 0) A[row + (size_t)row * lda] += s;
 }
 void add_rowsum_abs(tlr_ctx* ctx, int n, const double* E, int lde, double* A, int lda) {
+  TLR_SITE_PRE(ctx);
   k_add_rowsum_abs<<<cdiv(n, 8), 256, 0, ctx->stream>>>(n, E, lde, A, lda);
   TLR_LAUNCH_CHECK(ctx);
 }
@@ -625,6 +635,7 @@ __global__ void __launch_bounds__(1024) k_logdet(int n, const double* __restrict
 void logdet_reduce(tlr_ctx* ctx, int n, const double* diag_tiles, int b, int nb, const double* dvec,
                    double* out2) {
   (void)nb;
+  TLR_SITE_PRE(ctx);
   k_logdet<<<1, 1024, 0, ctx->stream>>>(n, diag_tiles, b, dvec, out2);
   TLR_LAUNCH_CHECK(ctx);
 }
@@ -669,6 +680,7 @@ void kernel_matvec(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell
                    int nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy) {
   for (int c0 = 0; c0 < nrhs; c0 += KMV_R) {
     const int nr = std::min(KMV_R, nrhs - c0);
+    TLR_SITE_PRE(ctx);
     k_kernel_matvec<<<cdiv(N, KMV_T), KMV_T, 0, ctx->stream>>>(pts, N, d, 1.0 / ell, nugget, nr,
                                                               X + c0 * ldx, ldx, Y + c0 * ldy, ldy);
     TLR_LAUNCH_CHECK(ctx);
@@ -695,6 +707,7 @@ void permute_rows(tlr_ctx* ctx, int64_t n_out, int nrhs, const int64_t* idx, int
                   const double* X, int64_t ldx, double* Y, int64_t ldy, int64_t n_pad) {
   const int64_t tot = (gather ? n_pad : n_out) * nrhs;
   if (tot <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_permute<<<std::min<unsigned>(cdiv(tot, 256), 8192u), 256, 0, ctx->stream>>>(n_out, nrhs, idx, gather,
                                                                                X, ldx, Y, ldy, n_pad);
   TLR_LAUNCH_CHECK(ctx);
@@ -710,6 +723,7 @@ __global__ void k_copy_matrix(int m, int n, const double* __restrict__ X, int ld
 }
 void copy_matrix(tlr_ctx* ctx, int m, int n, const double* X, int ldx, double* Y, int ldy) {
   if ((int64_t)m * n <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_copy_matrix<<<std::min<unsigned>(cdiv((int64_t)m * n, 256), 8192u), 256, 0, ctx->stream>>>(m, n, X, ldx,
                                                                                               Y, ldy);
   TLR_LAUNCH_CHECK(ctx);
@@ -725,11 +739,13 @@ __global__ void k_to_double(int64_t n, const float* __restrict__ x, double* __re
 }
 void to_float(tlr_ctx* ctx, int64_t n, const double* x, float* y) {
   if (n <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_to_float<<<std::min<unsigned>(cdiv(n, 256), 8192u), 256, 0, ctx->stream>>>(n, x, y);
   TLR_LAUNCH_CHECK(ctx);
 }
 void to_double(tlr_ctx* ctx, int64_t n, const float* x, double* y) {
   if (n <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_to_double<<<std::min<unsigned>(cdiv(n, 256), 8192u), 256, 0, ctx->stream>>>(n, x, y);
   TLR_LAUNCH_CHECK(ctx);
 }
@@ -744,81 +760,98 @@ void to_double(tlr_ctx* ctx, int64_t n, const float* x, double* y) {
 // (rows grouped by i at V's column offsets, leading dimension gld[j]).
 // Every slot carries its own matrix's tables, so slots of different matrices share
 // one launch.  Grid (slot, j in 0..kmax): block j < k writes -G_ij X_j, block k copies X0_i.
-template <typename T>
-__global__ void k_blkdiag_sample(const SlotDescT<T>* __restrict__ slots) {
-  const SlotDescT<T> sd = slots[blockIdx.x];
-  const int j = blockIdx.y, nb = sd.nb, k = sd.k, i = sd.i, bs = sd.bs;
-  if (j > k) return;
-  const int ldw = sd.r0 + sd.Ki;
-  if (j == k) {
-    for (int e = threadIdx.x; e < sd.r0 * bs; e += blockDim.x) {
-      const int a = e % sd.r0, c = e / sd.r0;
-      sd.W[a + (size_t)c * ldw] = sd.X0[(sd.x0off + a) + (size_t)c * sd.ldx0];
-    }
-    return;
-  }
-  const int rij = sd.rank[i * nb + j], rkj = sd.rank[k * nb + j];
-  if (rij == 0) return;
-  const T* Gij = sd.G + sd.goff[j] + (sd.voff[i * nb + j] - sd.voff[k * nb + j]);
-  const int ldg = sd.gld[j];
-  const T* Xj = sd.X + sd.uoff[k * nb + j];
-  T* out = sd.W + sd.r0 + sd.uoff[i * nb + j];
-  for (int e = threadIdx.x; e < rij * bs; e += blockDim.x) {
-    const int a = e % rij, c = e / rij;
-    T acc = T(0);
-    for (int q = 0; q < rkj; ++q) acc = fma(Gij[a + (size_t)q * ldg], Xj[q + (size_t)c * sd.ldx], acc);
-    out[a + (size_t)c * ldw] = -acc;
-  }
-}
-
-// Projection (sampleLeftT): B_i = T_ik^T Q_i = [V0_ik | U_k0 ... U_k,k-1] Z_i with
+//
+// The projection (sampleLeftT) uses the same blocks transposed:
+//   B_i = T_ik^T Q_i = [V0_ik | U_k0 ... U_k,k-1] Z_i with
 //   P_i = [U0_ik | U_i0 ...]^T Q_i ((r0 + K_i) x q),
 //   Z_i = [P_i^(0) ; -G_i0^T P_i^(j=0 block) ; ...]   ((r0 + K_k) x q).
-template <typename T>
-__global__ void k_blkdiag_project(const SlotDescT<T>* __restrict__ slots) {
-  const SlotDescT<T> sd = slots[blockIdx.x];
-  const int j = blockIdx.y, nb = sd.nb, k = sd.k, i = sd.i, q = sd.q;
-  if (j > k) return;
-  const int ldp = sd.r0 + sd.Ki, ldz = sd.r0 + sd.Kk;
-  if (j == k) {
-    for (int e = threadIdx.x; e < sd.r0 * q; e += blockDim.x) {
-      const int a = e % sd.r0, c = e / sd.r0;
-      sd.Z[a + (size_t)c * ldz] = sd.P[a + (size_t)c * ldp];
+//
+// Work is split into 16 x 16 output tiles: item (slot, j, row chunk, column chunk)
+// computes out = -op(G_ij) In on its tile over the whole inner dimension K, with
+// 16-deep chunks of both operands staged in shared memory and two accumulators per
+// thread.  Large blocks (ranks near the diagonal reach 10x the mean) are spread
+// over many CTAs instead of serializing on one SM's FP64 pipe; the host lists
+// only non-empty tiles.  Items with j = k copy the tile's own factor part.
+template <typename T, bool PROJ>
+__global__ void __launch_bounds__(128) k_blkdiag(const SlotDescT<T>* __restrict__ slots,
+                                                 const BlkItem* __restrict__ items) {
+  const BlkItem it = items[blockIdx.x];
+  const SlotDescT<T> sd = slots[it.slot];
+  const int j = it.j, a0 = 16 * it.rc, c0 = 16 * it.cc;
+  const int nb = sd.nb, k = sd.k, i = sd.i;
+  const int tid = threadIdx.x;
+  const int C = PROJ ? sd.q : sd.bs;
+  const int ldin = PROJ ? sd.r0 + sd.Ki : sd.ldx;          // P (project) or X (sample)
+  const int ldout = PROJ ? sd.r0 + sd.Kk : sd.r0 + sd.Ki;  // Z (project) or W (sample)
+  T* const outbase = PROJ ? sd.Z : sd.W;
+  if (j == k) {  // leading block: the tile's own factor part
+    const T* src = PROJ ? sd.P : sd.X0 + sd.x0off;
+    const int lds = PROJ ? ldin : sd.ldx0;
+    for (int e = tid; e < 256; e += blockDim.x) {
+      const int a = a0 + (e & 15), c = c0 + (e >> 4);
+      if (a < sd.r0 && c < C) outbase[a + (size_t)c * ldout] = src[a + (size_t)c * lds];
     }
     return;
   }
   const int rij = sd.rank[i * nb + j], rkj = sd.rank[k * nb + j];
-  if (rkj == 0) return;
-  T* out = sd.Z + sd.r0 + sd.uoff[k * nb + j];
+  const int R = PROJ ? rkj : rij, K = PROJ ? rij : rkj;
   const T* Gij = sd.G + sd.goff[j] + (sd.voff[i * nb + j] - sd.voff[k * nb + j]);
   const int ldg = sd.gld[j];
-  const T* Pj = sd.P + sd.r0 + sd.uoff[i * nb + j];
-  for (int e = threadIdx.x; e < rkj * q; e += blockDim.x) {
-    const int a = e % rkj, c = e / rkj;
-    T acc = T(0);
-    for (int l = 0; l < rij; ++l) acc = fma(Gij[l + (size_t)a * ldg], Pj[l + (size_t)c * ldp], acc);
-    out[a + (size_t)c * ldz] = -acc;
+  // sample: In = X_j (the r_kj rows of X at U_kj's offset); project: In = P_j (r_ij rows)
+  const T* In = PROJ ? sd.P + sd.r0 + sd.uoff[i * nb + j] : sd.X + sd.uoff[k * nb + j];
+  T* out = outbase + sd.r0 + (PROJ ? sd.uoff[k * nb + j] : sd.uoff[i * nb + j]);
+  __shared__ T As[16][17];  // op(G) chunk [row][kk]
+  __shared__ T Bs[16][17];  // In chunk [kk][col]
+  const int row = tid & 15, cp = tid >> 4;  // columns 2 cp, 2 cp + 1 of the tile
+  T acc0 = T(0), acc1 = T(0);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int idx = tid + e * 128;
+      int a, kk;
+      if (PROJ) { kk = idx & 15; a = idx >> 4; }  // G_ij^T: consecutive threads walk a column of G
+      else { a = idx & 15; kk = idx >> 4; }
+      const int ga = a0 + a, gk = k0 + kk;
+      As[a][kk] = (ga < R && gk < K) ? (PROJ ? Gij[gk + (size_t)ga * ldg] : Gij[ga + (size_t)gk * ldg]) : T(0);
+      const int bk = idx & 15, bc = idx >> 4;
+      Bs[bk][bc] = (k0 + bk < K && c0 + bc < C) ? In[(k0 + bk) + (size_t)(c0 + bc) * ldin] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const T av = As[row][kk];
+      acc0 = fma(av, Bs[kk][2 * cp], acc0);
+      acc1 = fma(av, Bs[kk][2 * cp + 1], acc1);
+    }
+    __syncthreads();
+  }
+  const int ga = a0 + row, gc = c0 + 2 * cp;
+  if (ga < R) {
+    if (gc < C) out[ga + (size_t)gc * ldout] = -acc0;
+    if (gc + 1 < C) out[ga + (size_t)(gc + 1) * ldout] = -acc1;
   }
 }
 
 template <typename T>
-void blkdiag_sample(tlr_ctx* ctx, int nslots, int kmax, const SlotDescT<T>* slots_dev) {
-  if (nslots <= 0) return;
-  dim3 grid((unsigned)nslots, (unsigned)(kmax + 1));
-  k_blkdiag_sample<T><<<grid, 128, 0, ctx->stream>>>(slots_dev);
+void blkdiag_sample(tlr_ctx* ctx, const std::vector<BlkItem>& items, const SlotDescT<T>* slots_dev) {
+  if (items.empty()) return;
+  const BlkItem* it = static_cast<const BlkItem*>(upload(ctx, items.data(), items.size() * sizeof(BlkItem)));
+  TLR_SITE_PRE(ctx);
+  k_blkdiag<T, false><<<(unsigned)items.size(), 128, 0, ctx->stream>>>(slots_dev, it);
   TLR_LAUNCH_CHECK(ctx);
 }
 template <typename T>
-void blkdiag_project(tlr_ctx* ctx, int nslots, int kmax, const SlotDescT<T>* slots_dev) {
-  if (nslots <= 0) return;
-  dim3 grid((unsigned)nslots, (unsigned)(kmax + 1));
-  k_blkdiag_project<T><<<grid, 128, 0, ctx->stream>>>(slots_dev);
+void blkdiag_project(tlr_ctx* ctx, const std::vector<BlkItem>& items, const SlotDescT<T>* slots_dev) {
+  if (items.empty()) return;
+  const BlkItem* it = static_cast<const BlkItem*>(upload(ctx, items.data(), items.size() * sizeof(BlkItem)));
+  TLR_SITE_PRE(ctx);
+  k_blkdiag<T, true><<<(unsigned)items.size(), 128, 0, ctx->stream>>>(slots_dev, it);
   TLR_LAUNCH_CHECK(ctx);
 }
-template void blkdiag_sample<double>(tlr_ctx*, int, int, const SlotDescT<double>*);
-template void blkdiag_sample<float>(tlr_ctx*, int, int, const SlotDescT<float>*);
-template void blkdiag_project<double>(tlr_ctx*, int, int, const SlotDescT<double>*);
-template void blkdiag_project<float>(tlr_ctx*, int, int, const SlotDescT<float>*);
+template void blkdiag_sample<double>(tlr_ctx*, const std::vector<BlkItem>&, const SlotDescT<double>*);
+template void blkdiag_sample<float>(tlr_ctx*, const std::vector<BlkItem>&, const SlotDescT<float>*);
+template void blkdiag_project<double>(tlr_ctx*, const std::vector<BlkItem>&, const SlotDescT<double>*);
+template void blkdiag_project<float>(tlr_ctx*, const std::vector<BlkItem>&, const SlotDescT<float>*);
 
 // Batched Philox blocks: block g is Omega(seed_g, stream_g, k_g, t_g), b_g x bs, at out_g.
 __global__ void k_omega_batched(const OmegaJob* __restrict__ jobs) {
@@ -844,6 +877,7 @@ void omega_batched(tlr_ctx* ctx, std::vector<OmegaJob>& jobs) {
   for (auto& j : jobs) mx = std::max(mx, j.b * j.bs);
   const OmegaJob* dj = static_cast<const OmegaJob*>(upload(ctx, jobs.data(), jobs.size() * sizeof(OmegaJob)));
   dim3 grid(std::min<unsigned>(cdiv((mx + 1) / 2, 256), 64u), (unsigned)jobs.size());
+  TLR_SITE_PRE(ctx);
   k_omega_batched<<<grid, 256, 0, ctx->stream>>>(dj);
   TLR_LAUNCH_CHECK(ctx);
 }
@@ -863,6 +897,7 @@ void batched_to_double(tlr_ctx* ctx, std::vector<ConvBackJob>& jobs) {
     const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
     const ConvBackJob* dj = static_cast<const ConvBackJob*>(upload(ctx, nz.data() + o, cnt * sizeof(ConvBackJob)));
     dim3 grid(std::min<unsigned>(cdiv(mx, 256), 64u), (unsigned)cnt);
+    TLR_SITE_PRE(ctx);
     k_batched_to_double<<<grid, 256, 0, ctx->stream>>>(dj);
     TLR_LAUNCH_CHECK(ctx);
   }
@@ -887,6 +922,7 @@ void batched_scale_rows(tlr_ctx* ctx, std::vector<ScaleJob>& jobs) {
     const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
     const ScaleJob* dj = static_cast<const ScaleJob*>(upload(ctx, nz.data() + o, cnt * sizeof(ScaleJob)));
     dim3 grid(std::min<unsigned>(cdiv(mx, 256), 128u), (unsigned)cnt);
+    TLR_SITE_PRE(ctx);
     k_batched_scale_rows<<<grid, 256, 0, ctx->stream>>>(dj);
     TLR_LAUNCH_CHECK(ctx);
   }
@@ -906,6 +942,7 @@ void batched_add_diag(tlr_ctx* ctx, std::vector<DiagJob>& jobs) {
     const int cnt = (int)std::min<size_t>(65535, jobs.size() - o);
     const DiagJob* dj = static_cast<const DiagJob*>(upload(ctx, jobs.data() + o, cnt * sizeof(DiagJob)));
     dim3 grid(std::min<unsigned>(cdiv(mx, 256), 16u), (unsigned)cnt);
+    TLR_SITE_PRE(ctx);
     k_batched_add_diag<<<grid, 256, 0, ctx->stream>>>(dj);
     TLR_LAUNCH_CHECK(ctx);
   }
@@ -935,6 +972,7 @@ double fp64_peak(tlr_ctx* ctx) {
   float best = 1e30f;
   for (int rep = 0; rep < 3; ++rep) {
     TLR_CUDA(cudaEventRecord(e0, ctx->stream));
+    TLR_SITE_PRE(ctx);
     k_dfma_loop<<<blocks, threads, 0, ctx->stream>>>(d, iters, 0.9999, 1e-3);
     TLR_LAUNCH_CHECK(ctx);
     TLR_CUDA(cudaEventRecord(e1, ctx->stream));
@@ -964,6 +1002,7 @@ void batched_copy(tlr_ctx* ctx, std::vector<CopyJob>& jobs) {
     const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
     const CopyJob* dj = static_cast<const CopyJob*>(upload(ctx, nz.data() + o, cnt * sizeof(CopyJob)));
     dim3 grid(std::min<unsigned>(cdiv(mx, 256), 64u), (unsigned)cnt);
+    TLR_SITE_PRE(ctx);
     k_batched_copy<<<grid, 256, 0, ctx->stream>>>(dj, cnt);
     TLR_LAUNCH_CHECK(ctx);
   }
@@ -980,6 +1019,7 @@ __global__ void k_scale_cols(int m, int n, const double* __restrict__ dv, const 
 void scale_cols(tlr_ctx* ctx, int m, int n, const double* dvec, const double* X, int ldx, double* Y,
                 int ldy) {
   if ((int64_t)m * n <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_scale_cols<<<std::min<unsigned>(cdiv((int64_t)m * n, 256), 4096u), 256, 0, ctx->stream>>>(m, n, dvec, X,
                                                                                              ldx, Y, ldy);
   TLR_LAUNCH_CHECK(ctx);
@@ -996,6 +1036,7 @@ __global__ void k_tril_mask(int n, double* A, int lda, int unit) {
 }
 void tril_mask(tlr_ctx* ctx, int n, double* A, int lda, int unit) {
   if (n <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_tril_mask<<<std::min<unsigned>(cdiv((int64_t)n * n, 256), 4096u), 256, 0, ctx->stream>>>(n, A, lda, unit);
   TLR_LAUNCH_CHECK(ctx);
 }
@@ -1006,6 +1047,7 @@ __global__ void k_set_diag(int n, double* A, int lda, const double* d) {
 }
 void set_diag(tlr_ctx* ctx, int n, double* A, int lda, const double* d) {
   if (n <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_set_diag<<<cdiv(n, 256), 256, 0, ctx->stream>>>(n, A, lda, d);
   TLR_LAUNCH_CHECK(ctx);
 }
@@ -1020,6 +1062,7 @@ __global__ void k_axpy_matrix(int m, int n, double alpha, const double* __restri
 }
 void axpy_matrix(tlr_ctx* ctx, int m, int n, double alpha, const double* X, int ldx, double* Y, int ldy) {
   if ((int64_t)m * n <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_axpy_matrix<<<std::min<unsigned>(cdiv((int64_t)m * n, 256), 4096u), 256, 0, ctx->stream>>>(m, n, alpha, X, ldx,
                                                                                               Y, ldy);
   TLR_LAUNCH_CHECK(ctx);
@@ -1040,6 +1083,7 @@ void batched_to_float(tlr_ctx* ctx, std::vector<ConvJob>& jobs) {
     const int cnt = (int)std::min<size_t>(65535, nz.size() - o);
     const ConvJob* dj = static_cast<const ConvJob*>(upload(ctx, nz.data() + o, cnt * sizeof(ConvJob)));
     dim3 grid(std::min<unsigned>(cdiv(mx, 256), 64u), (unsigned)cnt);
+    TLR_SITE_PRE(ctx);
     k_batched_to_float<<<grid, 256, 0, ctx->stream>>>(dj);
     TLR_LAUNCH_CHECK(ctx);
   }
@@ -1058,6 +1102,7 @@ __global__ void k_col_sqnorms(const double* __restrict__ X, int rows, int64_t nc
 }
 void col_sqnorms(tlr_ctx* ctx, const double* X, int rows, int64_t ncols, double* out) {
   if (ncols <= 0) return;
+  TLR_SITE_PRE(ctx);
   k_col_sqnorms<<<cdiv(ncols, 8), 256, 0, ctx->stream>>>(X, rows, ncols, out);
   TLR_LAUNCH_CHECK(ctx);
 }

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <cstdio>
 #include <numeric>
 
@@ -59,6 +60,22 @@ void* scratch(tlr_ctx* ctx, size_t bytes) {
 // Job descriptors travel through a pinned staging ring mirrored on the device.
 // Before the ring wraps the stream is synchronized, so no launch still reads
 // the region being overwritten.
+int* split_counters(tlr_ctx* ctx, size_t n) {
+  const int lane = (ctx->side && ctx->stream == ctx->side) ? 1 : 0;
+  if (n > ctx->split_ctr_cap[lane]) {
+    // earlier launches of this stream may still use the old array
+    TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, ctx->split_ctr[lane]);
+    ctx->split_ctr[lane] = nullptr;
+    ctx->split_ctr_cap[lane] = 0;
+    const size_t cap = std::max<size_t>(n, 1 << 16);
+    ctx->split_ctr[lane] = static_cast<int*>(dalloc(ctx, cap * sizeof(int)));
+    TLR_CUDA(cudaMemsetAsync(ctx->split_ctr[lane], 0, cap * sizeof(int), ctx->stream));
+    ctx->split_ctr_cap[lane] = cap;
+  }
+  return ctx->split_ctr[lane];
+}
+
 void* upload(tlr_ctx* ctx, const void* host, size_t bytes) {
   const size_t need = (bytes + 255) & ~size_t(255);
   TLR_REQUIRE(need <= ctx->ring_cap, TLR_ERR_LIMIT, "job list larger than the upload ring");
@@ -150,6 +167,78 @@ void kprof_flush(tlr_ctx* ctx) {
     ctx->kfam_launches[f] += 1;
   }
   ctx->kev_n = 0;
+}
+
+void site_tick(tlr_ctx* ctx, const char* file, int line) { site_tick_on(ctx, ctx->stream, file, line); }
+
+void site_tick_on(tlr_ctx* ctx, cudaStream_t stream, const char* file, int line) {
+  const int lane = (ctx->side && stream == ctx->side) ? 1 : 0;
+  if (!file) file = "gaps";
+  const int phase = ctx->cur_phase < 0 ? 15 : ctx->cur_phase;  // phases < 16
+  auto key = std::make_pair(file, (line * 2 + lane) * 16 + phase);
+  auto it = ctx->site_id.find(key);
+  int id;
+  if (it == ctx->site_id.end()) {
+    id = (int)ctx->site_name.size();
+    const char* base = strrchr(file, '/');
+    static const char* const pname[16] = {"gram", "diag_update", "potrf", "sample", "orthog", "host_sync",
+                                          "project", "trsm", "update_tiles", "compress", "solve", "other",
+                                          "p12", "p13", "p14", "-"};
+    ctx->site_name.push_back(std::string(base ? base + 1 : file) + (line ? ":" + std::to_string(line) : std::string()) +
+                             (lane ? "@side" : "@main") + "[" + pname[phase] + "]");
+    ctx->site_ms.push_back(0.0);
+    ctx->site_count.push_back(0);
+    ctx->site_id.emplace(key, id);
+  } else {
+    id = it->second;
+  }
+  auto& ev = ctx->sev[lane];
+  size_t& n = ctx->sev_n[lane];
+  if (n == ev.size()) {
+    cudaEvent_t e;
+    TLR_CUDA(cudaEventCreate(&e));
+    ev.push_back(e);
+    ctx->sev_site[lane].push_back(0);
+  }
+  TLR_CUDA(cudaEventRecord(ev[n], stream));
+  ctx->sev_site[lane][n] = id;
+  ++n;
+  if (n >= 8192) site_flush(ctx);
+}
+
+void site_flush(tlr_ctx* ctx) {
+  TLR_CUDA(cudaStreamSynchronize(ctx->main));
+  if (ctx->side) TLR_CUDA(cudaStreamSynchronize(ctx->side));
+  for (int lane = 0; lane < 2; ++lane) {
+    size_t& n = ctx->sev_n[lane];
+    for (size_t e = 1; e < n; ++e) {
+      float ms = 0;
+      TLR_CUDA(cudaEventElapsedTime(&ms, ctx->sev[lane][e - 1], ctx->sev[lane][e]));
+      ctx->site_ms[ctx->sev_site[lane][e]] += ms;
+      ctx->site_count[ctx->sev_site[lane][e]] += 1;
+    }
+    if (n > 0) {  // the last event opens the next batch
+      std::swap(ctx->sev[lane][0], ctx->sev[lane][n - 1]);
+      ctx->sev_site[lane][0] = ctx->sev_site[lane][n - 1];
+      n = 1;
+    }
+  }
+}
+
+void site_report(tlr_ctx* ctx) {
+  if (!ctx->site_out) return;
+  site_flush(ctx);
+  std::vector<int> idx(ctx->site_name.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return ctx->site_ms[a] > ctx->site_ms[b]; });
+  double tot = 0;
+  for (double v : ctx->site_ms) tot += v;
+  fprintf(ctx->site_out, "site\tlaunches\tms\tshare\n");
+  for (int i : idx)
+    if (ctx->site_count[i] > 0)
+      fprintf(ctx->site_out, "%s\t%lld\t%.3f\t%.4f\n", ctx->site_name[i].c_str(), (long long)ctx->site_count[i],
+              ctx->site_ms[i], tot > 0 ? ctx->site_ms[i] / tot : 0.0);
+  fflush(ctx->site_out);
 }
 
 void d2h_sync(tlr_ctx* ctx, void* host, const void* dev, size_t bytes) {
@@ -835,6 +924,7 @@ tlr_status tlr_create(tlr_ctx** out, int device, void* stream, tlr_alloc_fn allo
   ctx->ring_cap = 64ull << 20;
   TLR_CUDA(cudaMallocHost(&ctx->pinned, ctx->ring_cap));
   ctx->djobs = static_cast<char*>(dalloc(ctx, ctx->ring_cap));
+  if (const char* path = getenv("TLR_SITE_PROFILE")) ctx->site_out = fopen(path, "a");
   *out = ctx;
   return TLR_OK;
   }
@@ -854,9 +944,17 @@ tlr_status tlr_destroy(tlr_ctx* ctx) {
   ABI_BEGIN
   cudaStreamSynchronize(ctx->stream);
   cudaStreamSynchronize(ctx->side);
+  if (ctx->site_out) {
+    site_report(ctx);
+    fclose(ctx->site_out);
+    for (auto& v : ctx->sev)
+      for (auto e : v) cudaEventDestroy(e);
+  }
   dfree(ctx, ctx->djobs);
   dfree(ctx, ctx->scratch);
   dfree(ctx, ctx->scratch_side);
+  dfree(ctx, ctx->split_ctr[0]);
+  dfree(ctx, ctx->split_ctr[1]);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->hstatus) cudaFreeHost(ctx->hstatus);
