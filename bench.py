@@ -41,6 +41,16 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(value, device):
+    """The largest of every rank's value (replicas: the job ends with its slowest rank), then a barrier."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def _workload_desc(w, eps, prec):
     return (f"{WORKLOAD}: N={w['N']} points uniform in [0,1]^{w['d']}, KD-tree order, exp kernel ell={w['ell']} "
             f"nugget={w['nugget']}, b={w['b']} (nb={w['N'] // w['b']}), ARA block {w['bs']}, eps={eps:g}, {prec}")
@@ -150,13 +160,18 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------- our arm
-def _traffic_from_profile(name):
-    """traffic (DRAM bytes per launch) recorded in a committed ncu summary, or None."""
+def _traffic_per_flop(name="gemm_fp64.md"):
+    """DRAM bytes per algorithmic flop of a k_gemm launch, from the committed ncu summary, or None.
+
+    The summary records one captured launch of the current kernel (a smaller workload, same code
+    path); operand traffic of these products grows with their flops at a fixed sample width, so the
+    bench scales it by its live flops per launch.
+    """
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     for line in open(p):
-        if line.startswith("traffic_bytes_per_launch:"):
+        if line.startswith("traffic_bytes_per_flop:"):
             try:
                 return float(line.split(":", 1)[1])
             except ValueError:
@@ -230,10 +245,7 @@ def run_ours(args, w, eps):
     ck = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
     if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        torch.distributed.barrier()
+        total_ms = max_over_ranks(total_ms, dev)
     phases = {k: [] for k in ["compress", "factor", "solve", "logdet"]}
     for e in evs:
         for i, k in enumerate(phases):
@@ -252,7 +264,11 @@ def run_ours(args, w, eps):
     fp32_peak = 74.6  # FFMA, measured on this machine's GB300 (see profiles/peaks_gb300.md)
     peak = peak64 if fam.startswith("fp64") else fp32_peak
     roofline = {"bound": "alu", "kernel": f"k_gemm<{fam}>", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": _traffic_from_profile(f"gemm_{fam}_traffic.md"),
+                "frac": achieved / peak if peak else None,
+                "traffic": (_traffic_per_flop() * per_launch_flops
+                            if fam.startswith("fp64") and _traffic_per_flop() is not None else None),
+                "traffic_source": "profiles/gemm_fp64.md: ncu DRAM bytes per flop of a captured k_gemm launch "
+                                  "(cov2d_16k) x live flops per launch",
                 "peak_source": ("FP64 DFMA loop measured live in this run (tlr_fp64_peak)" if fam.startswith("fp64")
                                 else "FP32 FFMA loop measured on this pool's GB300"),
                 "share_of_step": g["ms"] / total_ms, "launches": g["launches"],
