@@ -33,7 +33,7 @@ struct GemmTile<float> { static constexpr int RM = 4, RN = 4; };
 // 128 threads as 16 (rows) x 8 (columns); thread (tr, tc) owns rows tr*RM + i and
 // columns tc*RN + j of the TM x TN tile; warp w owns columns [2w RN, 2w RN + 2 RN).
 template <typename T, int MODE, int RM, int RN>
-__global__ void __launch_bounds__(128) k_gemm(const GemmJob<T>* __restrict__ jobs, int njobs) {
+__device__ __forceinline__ void gemm_body(const GemmJob<T>* __restrict__ jobs, int njobs) {
   constexpr int TM = 16 * RM, TN_ = 8 * RN, TK = GEMM_TK;
   constexpr int EA = TK * TM / 128, EB = TK * TN_ / 128;
   // Rows padded by one where the chunk is stored across rows (consecutive threads
@@ -193,6 +193,34 @@ __global__ void __launch_bounds__(128) k_gemm(const GemmJob<T>* __restrict__ job
   if (tid == 0) *ctr = 0;
 }
 
+// Job table in global memory (uploaded), for launches with many jobs.
+template <typename T, int MODE, int RM, int RN>
+__global__ void __launch_bounds__(128) k_gemm(const GemmJob<T>* __restrict__ jobs, int njobs) {
+  gemm_body<T, MODE, RM, RN>(jobs, njobs);
+}
+
+// Job table passed as a kernel parameter (up to MAXJ jobs): no host-to-device copy ahead of the
+// launch, which is most of the fixed cost of the short per-round products.
+template <typename T, int MAXJ>
+struct GemmParams {
+  int njobs;
+  GemmJob<T> jobs[MAXJ];
+};
+template <typename T, int MODE, int RM, int RN, int MAXJ>
+__global__ void __launch_bounds__(128) k_gemm_p(const __grid_constant__ GemmParams<T, MAXJ> P) {
+  gemm_body<T, MODE, RM, RN>(P.jobs, P.njobs);
+}
+
+template <typename T, int RM, int RN, int MAXJ>
+static void launch_params(tlr_ctx* ctx, GemmMode mode, int64_t total, const std::vector<GemmJob<T>>& jobs) {
+  GemmParams<T, MAXJ> P;
+  P.njobs = (int)jobs.size();
+  std::copy(jobs.begin(), jobs.end(), P.jobs);
+  if (mode == NN) k_gemm_p<T, NN, RM, RN, MAXJ><<<(unsigned)total, 128, 0, ctx->stream>>>(P);
+  else if (mode == TN) k_gemm_p<T, TN, RM, RN, MAXJ><<<(unsigned)total, 128, 0, ctx->stream>>>(P);
+  else k_gemm_p<T, NT, RM, RN, MAXJ><<<(unsigned)total, 128, 0, ctx->stream>>>(P);
+}
+
 template <typename T>
 GemmJob<T> job(GemmMode, int M, int N, const T* A, int lda, const T* B, int ldb, int K, T* C,
                int ldc, double alpha, double beta) {
@@ -253,9 +281,9 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
       ctr += (size_t)jobs[q].tiles_m * jobs[q].tiles_n;
     }
   }
-  const GemmJob<T>* dj =
-      static_cast<const GemmJob<T>*>(upload(ctx, jobs.data(), jobs.size() * sizeof(GemmJob<T>)));
   const int nj = (int)jobs.size();
+  const GemmJob<T>* dj =
+      nj > 64 ? static_cast<const GemmJob<T>*>(upload(ctx, jobs.data(), jobs.size() * sizeof(GemmJob<T>))) : nullptr;
   double flops = 0;
   if (ctx->kprof) {
     for (auto& j : jobs) {
@@ -266,7 +294,9 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
     kprof_begin(ctx);
   }
   TLR_SITE_PRE(ctx);
-  if (mode == NN) k_gemm<T, NN, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
+  if (nj <= 8) launch_params<T, RM, RN, 8>(ctx, mode, total, jobs);
+  else if (nj <= 64) launch_params<T, RM, RN, 64>(ctx, mode, total, jobs);
+  else if (mode == NN) k_gemm<T, NN, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   else if (mode == TN) k_gemm<T, TN, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   else k_gemm<T, NT, RM, RN><<<(unsigned)total, 128, 0, ctx->stream>>>(dj, nj);
   TLR_LAUNCH_CHECK(ctx);

@@ -217,17 +217,22 @@ __global__ void __launch_bounds__(32) k_cholqr_reg(const double* __restrict__ Ga
     thr2 = 0.0;
   }
   double rt[BS];      // rt[j] = Rt(j, lane)
+  double inv[BS];     // 1 / Rt(j, j), the same in every lane
   unsigned mask = 0;  // kept columns
 #pragma unroll
   for (int j = 0; j < BS; ++j) {
     rt[j] = (lane == j) ? 1.0 : 0.0;
+    inv[j] = 1.0;
     if (j < n) {
       const double dj = __shfl_sync(0xffffffffu, g[j], j);  // pivot of column j
       const double gjj = __shfl_sync(0xffffffffu, gdiag, j);
       const bool kept = (dj > fmax(thr2, tau * gjj)) && (dj > 0.0) && isfinite(dj);
       if (kept) {
+        // one reciprocal per pivot: every later use multiplies (a warp-wide FP64 divide costs
+        // as much as ten FMAs on this part, and the factor and its inverse need 3 BS of them)
         const double rjj = sqrt(dj);
-        const double rj = (lane == j) ? rjj : ((lane > j && lane < n) ? g[j] / rjj : 0.0);
+        inv[j] = 1.0 / rjj;
+        const double rj = (lane == j) ? rjj : ((lane > j && lane < n) ? g[j] * inv[j] : 0.0);
 #pragma unroll
         for (int a = j + 1; a < BS; ++a) {
           const double rja = __shfl_sync(0xffffffffu, rj, a);
@@ -253,8 +258,7 @@ __global__ void __launch_bounds__(32) k_cholqr_reg(const double* __restrict__ Ga
       const double rpq = __shfl_sync(0xffffffffu, rt[p], q);
       if (q <= lane) acc = fma(rpq, x[q], acc);
     }
-    const double rpp = __shfl_sync(0xffffffffu, rt[p], p);
-    x[p] = (p == lane) ? 1.0 / rpp : ((p < lane) ? -acc / rpp : 0.0);
+    x[p] = (p == lane) ? inv[p] : ((p < lane) ? -acc * inv[p] : 0.0);
   }
   // M column pos(lane) = kept part of column `lane` of Rt^{-1}; zero elsewhere
   const int nk = __popc(mask);
