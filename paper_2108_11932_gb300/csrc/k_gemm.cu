@@ -59,8 +59,15 @@ __device__ __forceinline__ void gemm_body(const GemmJob<T>* __restrict__ jobs, i
   const int n0 = (local % J.tiles_n) * TN_;
   if ((J.flags & GEMM_TRIL) && m0 + TM <= n0) return;  // tile strictly above the diagonal
   const int M = J.M, N = J.N;
-  const int tr = tid & 15, tc = tid >> 4;
-  const bool active = (n0 + (tid >> 5) * 2 * RN) < N;  // warp-uniform: this warp's columns exist
+  // Warps skip products outside the job (warp-uniform): by default warp w owns columns
+  // 2w RN .. 2w RN + 2 RN - 1 of the tile (narrow N: a projection onto a few basis vectors); an
+  // FP64 tile that is cut short in M (Q^T Y and Y^T Y have M = q or bs) gives warp w rows
+  // 8w .. 8w+7 instead.  Either way each output is summed by one thread in k order, so the
+  // mapping does not change any result.
+  const bool rowwarps = (RM == 2) && (M - m0 < TM);
+  const int tr = rowwarps ? ((tid >> 5) * 4 + ((tid & 31) >> 3)) : (tid & 15);
+  const int tc = rowwarps ? (tid & 7) : (tid >> 4);
+  const bool active = rowwarps ? (m0 + (tid >> 5) * 8 < M) : (n0 + (tid >> 5) * 2 * RN < N);
   T acc[RM][RN];
 #pragma unroll
   for (int i = 0; i < RM; ++i)
@@ -256,8 +263,14 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
     auto& j = jobs[q];
     j.tiles_m = (j.M + TM - 1) / TM;
     j.tiles_n = (j.N + TN_ - 1) / TN_;
-    const int full = j.N / TN_, rem = j.N % TN_;
-    const int64_t wpr = (int64_t)full * 4 + (rem + 2 * RN - 1) / (2 * RN);  // warps with columns, per tile row
+    // warps with work per tile row (columns per warp; FP64 tiles short in M: rows per warp)
+    int64_t wpr;
+    if (RM == 2 && j.M < TM) {
+      wpr = (int64_t)((j.M + 7) / 8) * j.tiles_n;
+    } else {
+      const int full = j.N / TN_, rem = j.N % TN_;
+      wpr = (int64_t)full * 4 + (rem + 2 * RN - 1) / (2 * RN);
+    }
     const int chunks = (j.K[0] + GEMM_TK - 1) / GEMM_TK + (j.K[1] > 0 ? (j.K[1] + GEMM_TK - 1) / GEMM_TK : 0);
     const int64_t S = std::max<int64_t>(4, ((int64_t)j.tiles_m * wpr * chunks + slots - 1) / slots);
     j.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(32, chunks / S));

@@ -806,7 +806,11 @@ __global__ void __launch_bounds__(128) k_blkdiag(const SlotDescT<T>* __restrict_
   T* out = outbase + sd.r0 + (PROJ ? sd.uoff[k * nb + j] : sd.uoff[i * nb + j]);
   __shared__ T As[16][17];  // op(G) chunk [row][kk]
   __shared__ T Bs[16][17];  // In chunk [kk][col]
-  const int row = tid & 15, cp = tid >> 4;  // columns 2 cp, 2 cp + 1 of the tile
+  // Thread (row, column pair): warp w owns rows 4w .. 4w+3, so warps whose rows lie beyond R
+  // skip the products, and the chunk loop stops at K: ranks are mostly well below 16, and
+  // padded rows or depth would otherwise multiply the FP64 work.
+  const int row = tid >> 3, cp = tid & 7;  // columns 2 cp, 2 cp + 1 of the tile
+  const bool rows_live = a0 + 4 * (tid >> 5) < R;  // warp-uniform
   T acc0 = T(0), acc1 = T(0);
   for (int k0 = 0; k0 < K; k0 += 16) {
 #pragma unroll
@@ -821,11 +825,13 @@ __global__ void __launch_bounds__(128) k_blkdiag(const SlotDescT<T>* __restrict_
       Bs[bk][bc] = (k0 + bk < K && c0 + bc < C) ? In[(k0 + bk) + (size_t)(c0 + bc) * ldin] : T(0);
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      const T av = As[row][kk];
-      acc0 = fma(av, Bs[kk][2 * cp], acc0);
-      acc1 = fma(av, Bs[kk][2 * cp + 1], acc1);
+    if (rows_live) {
+      const int kmax = min(16, K - k0);
+      for (int kk = 0; kk < kmax; ++kk) {
+        const T av = As[row][kk];
+        acc0 = fma(av, Bs[kk][2 * cp], acc0);
+        acc1 = fma(av, Bs[kk][2 * cp + 1], acc1);
+      }
     }
     __syncthreads();
   }
