@@ -186,16 +186,33 @@ __device__ __forceinline__ void gemm_body(const GemmJob<T>* __restrict__ jobs, i
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int e = tid; e < TM * TN_; e += 128) {
+  // Each thread sums TM*TN/128 entries side by side, so their partial loads are in flight together.
+  constexpr int PER = TM * TN_ / 128;
+  bool ok[PER];
+  size_t o[PER];
+  T v[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = tid + q * 128;
     const int gm = m0 + e % TM, gn = n0 + e / TM;
-    if (gm >= M || gn >= N || ((J.flags & GEMM_TRIL) && gm < gn)) continue;
-    const size_t o = gm + (size_t)gn * M;
-    T v = T(0);
-    for (int sp = 0; sp < J.nsplit; ++sp) v += __ldcg(J.ws + (size_t)sp * MN + o);
-    T* c = J.C + gm + (size_t)gn * J.ldc;
-    v = alpha * v;
-    if (J.beta != 0.0) v += beta * *c;
-    *c = v;
+    ok[q] = gm < M && gn < N && !((J.flags & GEMM_TRIL) && gm < gn);
+    o[q] = ok[q] ? gm + (size_t)gn * M : 0;
+    v[q] = T(0);
+  }
+  for (int sp = 0; sp < J.nsplit; ++sp) {
+    const T* w = J.ws + (size_t)sp * MN;
+#pragma unroll
+    for (int q = 0; q < PER; ++q)
+      if (ok[q]) v[q] += __ldcg(w + o[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    if (!ok[q]) continue;
+    const int e = tid + q * 128;
+    T* c = J.C + (m0 + e % TM) + (size_t)(n0 + e / TM) * J.ldc;
+    T r = alpha * v[q];
+    if (J.beta != 0.0) r += beta * *c;
+    *c = r;
   }
   if (tid == 0) *ctr = 0;
 }
@@ -249,9 +266,9 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
   if (jobs.empty()) return;
   // Split-K.  Work is counted in warp-chunks (one warp's share of a tile over one
   // 16-deep K chunk): a job has tiles_m x (warps with columns) x chunks of them.
-  // Each job picks its slice length S (in chunks, at least 4) so that the job
+  // Each job picks its slice length S (in chunks, at least 2) so that the job
   // alone would hold about two warps per SMSP (8 per SM), and is cut into
-  // ceil(chunks / S) slices, at most 32.  The choice depends on the job's own
+  // chunks / S slices, at most 64.  The choice depends on the job's own
   // shape only, never on the other jobs of the launch: a product is summed in the
   // same order whether its matrix is factored alone or in a batch, which keeps
   // batched results bitwise equal to single ones.
@@ -272,8 +289,8 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
       wpr = (int64_t)full * 4 + (rem + 2 * RN - 1) / (2 * RN);
     }
     const int chunks = (j.K[0] + GEMM_TK - 1) / GEMM_TK + (j.K[1] > 0 ? (j.K[1] + GEMM_TK - 1) / GEMM_TK : 0);
-    const int64_t S = std::max<int64_t>(4, ((int64_t)j.tiles_m * wpr * chunks + slots - 1) / slots);
-    j.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(32, chunks / S));
+    const int64_t S = std::max<int64_t>(2, ((int64_t)j.tiles_m * wpr * chunks + slots - 1) / slots);
+    j.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(64, chunks / S));
     j.tile0 = (int)total;
     total += (int64_t)j.tiles_m * j.tiles_n * j.nsplit;
     if (j.nsplit > 1) {
