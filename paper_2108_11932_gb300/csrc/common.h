@@ -129,6 +129,9 @@ struct tlr_ctx {
   std::vector<std::string> site_name;
   std::vector<double> site_ms;
   std::vector<int64_t> site_count;
+  std::vector<double> site_flops;   // algorithmic flops of the site's launches (GEMMs)
+  std::vector<double> sev_flops[2];
+  double site_next_flops = 0;       // set by a launcher just before its launch is ticked
 };
 
 struct tlr_mat {

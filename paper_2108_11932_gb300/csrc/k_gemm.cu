@@ -315,14 +315,15 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
   const GemmJob<T>* dj =
       nj > 64 ? static_cast<const GemmJob<T>*>(upload(ctx, jobs.data(), jobs.size() * sizeof(GemmJob<T>))) : nullptr;
   double flops = 0;
-  if (ctx->kprof) {
+  if (ctx->kprof || ctx->site_out) {
     for (auto& j : jobs) {
       // algorithmic flops: a triangular C or a triangular A halves the product
       const double k0 = (mode == NN && (j.flags & GEMM_ALOWER)) ? 0.5 * (j.K[0] + 1) : (double)j.K[0];
       flops += 2.0 * j.M * j.N * (k0 + j.K[1]) * ((j.flags & GEMM_TRIL) ? 0.5 : 1.0);
     }
-    kprof_begin(ctx);
+    if (ctx->kprof) kprof_begin(ctx);
   }
+  ctx->site_next_flops = flops;
   TLR_SITE_PRE(ctx);
   if (nj <= 8) launch_params<T, RM, RN, 8>(ctx, mode, total, jobs);
   else if (nj <= 64) launch_params<T, RM, RN, 64>(ctx, mode, total, jobs);

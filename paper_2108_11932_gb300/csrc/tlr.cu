@@ -188,6 +188,7 @@ void site_tick_on(tlr_ctx* ctx, cudaStream_t stream, const char* file, int line)
                              (lane ? "@side" : "@main") + "[" + pname[phase] + "]");
     ctx->site_ms.push_back(0.0);
     ctx->site_count.push_back(0);
+    ctx->site_flops.push_back(0.0);
     ctx->site_id.emplace(key, id);
   } else {
     id = it->second;
@@ -199,9 +200,12 @@ void site_tick_on(tlr_ctx* ctx, cudaStream_t stream, const char* file, int line)
     TLR_CUDA(cudaEventCreate(&e));
     ev.push_back(e);
     ctx->sev_site[lane].push_back(0);
+    ctx->sev_flops[lane].push_back(0.0);
   }
   TLR_CUDA(cudaEventRecord(ev[n], stream));
   ctx->sev_site[lane][n] = id;
+  ctx->sev_flops[lane][n] = file == std::string("gaps") ? 0.0 : ctx->site_next_flops;
+  if (file != std::string("gaps")) ctx->site_next_flops = 0;
   ++n;
   if (n >= 8192) site_flush(ctx);
 }
@@ -216,10 +220,12 @@ void site_flush(tlr_ctx* ctx) {
       TLR_CUDA(cudaEventElapsedTime(&ms, ctx->sev[lane][e - 1], ctx->sev[lane][e]));
       ctx->site_ms[ctx->sev_site[lane][e]] += ms;
       ctx->site_count[ctx->sev_site[lane][e]] += 1;
+      ctx->site_flops[ctx->sev_site[lane][e]] += ctx->sev_flops[lane][e];
     }
     if (n > 0) {  // the last event opens the next batch
       std::swap(ctx->sev[lane][0], ctx->sev[lane][n - 1]);
       ctx->sev_site[lane][0] = ctx->sev_site[lane][n - 1];
+      ctx->sev_flops[lane][0] = ctx->sev_flops[lane][n - 1];
       n = 1;
     }
   }
@@ -233,11 +239,12 @@ void site_report(tlr_ctx* ctx) {
   std::sort(idx.begin(), idx.end(), [&](int a, int b) { return ctx->site_ms[a] > ctx->site_ms[b]; });
   double tot = 0;
   for (double v : ctx->site_ms) tot += v;
-  fprintf(ctx->site_out, "site\tlaunches\tms\tshare\n");
+  fprintf(ctx->site_out, "site\tlaunches\tms\tshare\tgflop\ttflops\n");
   for (int i : idx)
     if (ctx->site_count[i] > 0)
-      fprintf(ctx->site_out, "%s\t%lld\t%.3f\t%.4f\n", ctx->site_name[i].c_str(), (long long)ctx->site_count[i],
-              ctx->site_ms[i], tot > 0 ? ctx->site_ms[i] / tot : 0.0);
+      fprintf(ctx->site_out, "%s\t%lld\t%.3f\t%.4f\t%.3f\t%.4f\n", ctx->site_name[i].c_str(),
+              (long long)ctx->site_count[i], ctx->site_ms[i], tot > 0 ? ctx->site_ms[i] / tot : 0.0,
+              ctx->site_flops[i] / 1e9, ctx->site_ms[i] > 0 ? ctx->site_flops[i] / ctx->site_ms[i] / 1e9 : 0.0);
   fflush(ctx->site_out);
 }
 
