@@ -275,6 +275,16 @@ tlr_status tlr_dense_ldlt(tlr_ctx* ctx, int n, double* A, int lda, int* info);
 tlr_status tlr_dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int unit, int nrhs,
                           double* B, int ldb);
 
+/* C = T X (trans = 0) or C = T^T X (trans = 1) for one dense n x n FP64 tile T (column-major,
+ * leading dimension n) and X n x ncols (leading dimension ldx), C n x ncols (ldc): the
+ * construction's ARA products (Algorithm 1 samples and projections of Section 6's tiles),
+ * computed on BF16 tensor cores by exact splitting into 7-bit slices (Ozaki et al., 2012)
+ * with an error of the order of an FP64 product.  n must be a positive multiple of 8
+ * (TLR_ERR_LIMIT otherwise); all pointers are device memory owned by the caller; the call
+ * returns after the product is complete. */
+tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const double* T, const double* X,
+                             int ldx, double* C, int ldc);
+
 /* Measurement utility (not part of the method): FP64 DFMA throughput of this
  * GPU in TFLOP/s, from a register-resident FMA loop timed with CUDA events. */
 tlr_status tlr_fp64_peak(tlr_ctx* ctx, double* tflops);

@@ -104,6 +104,7 @@ def _load():
         "tlr_dense_potrf": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int)]),
         "tlr_dense_ldlt": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int)]),
         "tlr_dense_trsm": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, C.c_int]),
+        "tlr_split_product": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, C.c_int, P, C.c_int]),
         "tlr_fp64_peak": (C.c_int, [P, D]),
         "tlr_launch_count": (C.c_int64, [P]),
         "tlr_profile": (C.c_int, [P, C.c_int, D, C.POINTER(C.c_int64), C.c_int]),
@@ -293,6 +294,15 @@ class Context:
     def dense_trsm(self, L, B, unit: bool = False):
         _check(_load().tlr_dense_trsm(self.h, L.shape[0], _ptr(L), _ld(L), int(unit), B.shape[1], _ptr(B), _ld(B)),
                "tlr_dense_trsm")
+
+    def split_product(self, T, X, trans: bool = False, out=None):
+        """C = T X (or T^T X) for a dense n x n tile on BF16 tensor cores by exact splitting."""
+        n, ncols = T.shape[0], X.shape[1]
+        C_ = out if out is not None else fortran(self.torch.empty((n, ncols), dtype=self.torch.float64,
+                                                                   device=T.device))
+        _check(_load().tlr_split_product(self.h, int(trans), n, ncols, _ptr(T), _ptr(X), _ld(X), _ptr(C_), _ld(C_)),
+               "tlr_split_product")
+        return C_
 
     PHASES = ["gram", "diag_update", "potrf", "sample", "orthog", "host_sync", "project", "trsm", "update_tiles",
               "compress", "solve", "other", "host_blocked"]

@@ -207,7 +207,8 @@ GemmJob<T> job(GemmMode mode, int M, int N, const T* A, int lda, const T* B, int
 void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t, int b, int bs,
            double* out);
 void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget, int b,
-               const int* tile_ij /*device, 2 per tile*/, int ntiles, double* out);
+               const int* tile_ij /*device, 2 per tile*/, int ntiles, double* out,
+               unsigned long long* tmax = nullptr /*device, per tile, zeroed*/);
 // per-slot orthogonalization helpers (Cholesky-QR with dropping)
 // thr: device array, per-slot convergence threshold
 void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mout, int* status,
@@ -269,6 +270,28 @@ struct SlotDescT {
   T* Z;
   int ldx, ldx0, nb, k, i, r0, x0off, Ki, Kk, q, bs;
 };
+// FP64 products on BF16 tensor cores by exact splitting (k_ozaki.cu)
+struct OzColJob {        // columns to split: X (K x ncols, ld) -> Xs (8 slices, K x ncols each), e (ncols)
+  const double* X;
+  uint16_t* Xs;
+  int* e;
+  int ld, ncols, col0;
+};
+struct OzJob {           // C (M x N, ldc) = A B with A(m, k) = A_q[k + m * lda], B(k, n) = B_q[k + n * K]
+  const uint16_t* A;     // 8 slices, stride sA
+  const uint16_t* B;     // 8 slices, stride sB
+  const int* eA;         // block exponent of A (device)
+  const int* eB;         // column exponents of B (device, N)
+  double* C;
+  size_t sA, sB;
+  int lda, ldc, M, N, K;
+};
+void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, uint16_t* Sc,
+                    uint16_t* Sr, int* eT);
+void oz_split_cols(tlr_ctx* ctx, int K, std::vector<OzColJob>& jobs);
+void oz_absmax(tlr_ctx* ctx, int nblocks, int64_t n2, const double* T, unsigned long long* tmax);
+void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs);
+
 // one 16 x 16 output tile of a block-diagonal Gram product: slot, block column j
 // (j = k: the tile's own factor part), row chunk, column chunk
 struct BlkItem {

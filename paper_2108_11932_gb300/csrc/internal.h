@@ -80,8 +80,16 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
              std::vector<int>& q, AraStats& st);
 
 // Uniform dense ARA: nops operands T + op*n*n (n x n); Q (nops x n x (n+bs)), B (nops x n x n).
+// BF16 slices of a batch of dense tiles for the split products (k_ozaki.cu)
+struct OzTiles {
+  uint16_t* Sc;  // slices in the tiles' layout (columns of T contiguous)
+  uint16_t* Sr;  // transposed slices (rows of T contiguous)
+  int* e;        // per-tile exponent (device)
+  Buf* bx;       // workspace for the right operand's slices
+  Buf* be;       // workspace for its column exponents
+};
 void ara_dense_run(tlr_ctx* ctx, int nops, int n, const double* T, int bs, double eps, uint64_t seed, uint32_t stream,
-                   uint32_t k, double* Q, double* B, std::vector<int>& q, AraStats& st);
+                   uint32_t k, double* Q, double* B, std::vector<int>& q, AraStats& st, const OzTiles* oz = nullptr);
 
 // TLR matrix helpers
 inline int64_t ix(const tlr_mat* M, int i, int j) { return (int64_t)i * M->nb + j; }

@@ -51,11 +51,14 @@ void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t,
 }
 
 // ------------------------------------------------------------------ kernel tiles (Section 6)
+// With tmax, also records each tile's largest |entry| (as FP64 bits, atomically; zeroed by the caller).
 __global__ void k_gen_tiles(const double* __restrict__ pts, int64_t N, int d, double inv_ell,
-                            double nugget, int b, const int* __restrict__ ij, double* __restrict__ out) {
+                            double nugget, int b, const int* __restrict__ ij, double* __restrict__ out,
+                            unsigned long long* __restrict__ tmax) {
   const int t = blockIdx.y;
   const int i = ij[2 * t], j = ij[2 * t + 1];
   double* T = out + (size_t)t * b * b;
+  double vmax = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < b * b; e += gridDim.x * blockDim.x) {
     const int r = e % b, c = e / b;
     const int64_t gi = (int64_t)i * b + r, gj = (int64_t)j * b + c;
@@ -72,15 +75,20 @@ __global__ void k_gen_tiles(const double* __restrict__ pts, int64_t N, int d, do
       v = (gi == gj) ? 1.0 : 0.0;  // identity padding of a ragged last tile
     }
     T[e] = v;
+    vmax = fmax(vmax, fabs(v));
+  }
+  if (tmax) {
+    for (int o = 16; o; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(tmax + t, (unsigned long long)__double_as_longlong(vmax));
   }
 }
 
 void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget, int b,
-               const int* tile_ij, int ntiles, double* out) {
+               const int* tile_ij, int ntiles, double* out, unsigned long long* tmax) {
   if (ntiles <= 0) return;
   dim3 grid(std::min<unsigned>(cdiv((int64_t)b * b, 256), 64u), (unsigned)ntiles);
   TLR_SITE_PRE(ctx);
-  k_gen_tiles<<<grid, 256, 0, ctx->stream>>>(pts, N, d, 1.0 / ell, nugget, b, tile_ij, out);
+  k_gen_tiles<<<grid, 256, 0, ctx->stream>>>(pts, N, d, 1.0 / ell, nugget, b, tile_ij, out, tmax);
   TLR_LAUNCH_CHECK(ctx);
 }
 

@@ -392,9 +392,6 @@ void dense_trinv_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int, Buf& tm
   }
 }
 
-void ara_dense_run(tlr_ctx* ctx, int nops, int n, const double* T, int bs, double eps, uint64_t seed, uint32_t stream,
-                   uint32_t k, double* Q, double* B, std::vector<int>& q, AraStats& st);
-
 // ======================================================================== ARA engine
 // Batched ARA (Algorithm 1) over operands T_op (nrow[op] x nrow[op]), with the
 // dynamic batching of Algorithm 5: operands enter the batch in `order`, at most
@@ -535,6 +532,8 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
 }
 
 // ---------------------------------------------------------------- dense operands
+// With slices (construction tiles: `oz`), both products run on BF16 tensor cores by exact
+// splitting (k_ozaki.cu): T Omega reads the row-oriented slices, T^T Q the column-oriented ones.
 struct DenseSampler : Sampler {
   tlr_ctx* ctx;
   int n, bs;
@@ -542,36 +541,69 @@ struct DenseSampler : Sampler {
   const double* Q;
   const std::vector<int64_t>* qoff;
   double* B;        // nops x n x n (first q columns used)
+  const OzTiles* oz = nullptr;
   double flops = 0;
   void sample(const std::vector<int>& ops, int, const double* Om, const std::vector<double*>& Ydst) override {
+    flops += 2.0 * n * n * bs * ops.size();
+    if (oz) {
+      uint16_t* Xs = static_cast<uint16_t*>(oz->bx->need<uint16_t>((size_t)8 * n * bs));
+      int* ex = oz->be->need<int>((size_t)bs);
+      std::vector<OzColJob> cj{OzColJob{Om, Xs, ex, n, bs, 0}};
+      oz_split_cols(ctx, n, cj);
+      std::vector<OzJob> jobs;
+      for (size_t s = 0; s < ops.size(); ++s)
+        jobs.push_back(OzJob{oz->Sr + (size_t)ops[s] * 8 * n * n, Xs, oz->e + ops[s], ex, Ydst[s], (size_t)n * n,
+                             (size_t)n * bs, n, n, n, bs, n});
+      oz_gemm(ctx, jobs);
+      return;
+    }
     std::vector<GemmJob<double>> jobs;
     for (size_t s = 0; s < ops.size(); ++s)
       jobs.push_back(job<double>(NN, n, bs, T + (size_t)ops[s] * n * n, n, Om, n, n, Ydst[s], n, 1.0, 0.0));
-    flops += 2.0 * n * n * bs * ops.size();
     gemm<double>(ctx, NN, jobs);
   }
   void project(const std::vector<int>& q) override {
+    for (size_t op = 0; op < q.size(); ++op) flops += 2.0 * n * n * q[op];
+    if (oz) {
+      int64_t cols = 0;
+      for (int v : q) cols += v;
+      if (cols == 0) return;
+      uint16_t* Xs = oz->bx->need<uint16_t>((size_t)8 * n * cols);
+      int* ex = oz->be->need<int>((size_t)cols);
+      std::vector<OzColJob> cj;
+      std::vector<OzJob> jobs;
+      int64_t c0 = 0;
+      for (size_t op = 0; op < q.size(); ++op) {
+        if (q[op] == 0) continue;
+        uint16_t* xo = Xs + (size_t)8 * n * c0;
+        cj.push_back(OzColJob{Q + (*qoff)[op], xo, ex + c0, n, q[op], 0});
+        jobs.push_back(OzJob{oz->Sc + op * (size_t)8 * n * n, xo, oz->e + op, ex + c0, B + op * (size_t)n * n,
+                             (size_t)n * n, (size_t)n * q[op], n, n, n, q[op], n});
+        c0 += q[op];
+      }
+      oz_split_cols(ctx, n, cj);
+      oz_gemm(ctx, jobs);
+      return;
+    }
     std::vector<GemmJob<double>> jobs;
     for (size_t op = 0; op < q.size(); ++op)
-      if (q[op] > 0) {
+      if (q[op] > 0)
         jobs.push_back(job<double>(TN, n, q[op], T + op * (size_t)n * n, n, Q + (*qoff)[op], n, n,
                                    B + op * (size_t)n * n, n, 1.0, 0.0));
-        flops += 2.0 * n * n * q[op];
-      }
     gemm<double>(ctx, TN, jobs);
   }
 };
 
 // Uniform dense ARA (construction tiles, tlr_ara_dense, Schur compensation).
 void ara_dense_run(tlr_ctx* ctx, int nops, int n, const double* T, int bs, double eps, uint64_t seed, uint32_t stream,
-                   uint32_t k, double* Q, double* B, std::vector<int>& q, AraStats& st) {
+                   uint32_t k, double* Q, double* B, std::vector<int>& q, AraStats& st, const OzTiles* oz) {
   std::vector<int> nrow(nops, n), order(nops);
   std::vector<double> thr(nops, eps / HALKO);
   std::vector<int64_t> qoff(nops);
   for (int op = 0; op < nops; ++op) qoff[op] = (int64_t)op * n * (n + bs);
   std::iota(order.begin(), order.end(), 0);
   DenseSampler ds;
-  ds.ctx = ctx; ds.n = n; ds.bs = bs; ds.T = T; ds.Q = Q; ds.qoff = &qoff; ds.B = B;
+  ds.ctx = ctx; ds.n = n; ds.bs = bs; ds.T = T; ds.Q = Q; ds.qoff = &qoff; ds.B = B; ds.oz = oz;
   AraConfig cf{bs, seed, stream, k, 0};
   ara_run(ctx, ds, nrow, thr, cf, order, Q, qoff, q, st);
 }
@@ -668,7 +700,7 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
   const int bs = o->bs;
   const size_t tile_bytes = sizeof(double) * (size_t)b * b;
   const int batch = (int)std::max<size_t>(1, std::min<size_t>(tiles.size(), (size_t)(3ull << 30) / (3 * tile_bytes)));
-  Buf bT(ctx), bQ(ctx), bB(ctx);
+  Buf bT(ctx), bQ(ctx), bB(ctx), bMax(ctx), bSc(ctx), bSr(ctx), bEt(ctx), bXs(ctx), bEx(ctx);
   struct Stored { double* U; double* V; int r; };
   std::vector<Stored> st(tiles.size());
   std::vector<void*> chunks;
@@ -680,10 +712,24 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
     std::vector<int> ij;
     for (int u = 0; u < nt; ++u) { ij.push_back(tiles[t0 + u].first); ij.push_back(tiles[t0 + u].second); }
     const int* dij = static_cast<const int*>(upload(ctx, ij.data(), ij.size() * sizeof(int)));
-    gen_tiles(ctx, M->pts, N, d, kern->ell, kern->nugget, b, dij, nt, T);
     std::vector<int> q;
     AraStats as;
-    ara_dense_run(ctx, nt, b, T, bs, eps, o->seed, STREAM_COMPRESS, 0, Q, B, q, as);
+    if (b % 8 == 0) {  // the tensor-core split products read 16-byte rows
+      unsigned long long* tmax = bMax.need<unsigned long long>((size_t)nt);
+      TLR_CUDA(cudaMemsetAsync(tmax, 0, sizeof(unsigned long long) * nt, ctx->stream));
+      gen_tiles(ctx, M->pts, N, d, kern->ell, kern->nugget, b, dij, nt, T, tmax);
+      OzTiles oz;
+      oz.Sc = bSc.need<uint16_t>((size_t)nt * 8 * b * b);
+      oz.Sr = bSr.need<uint16_t>((size_t)nt * 8 * b * b);
+      oz.e = bEt.need<int>((size_t)nt);
+      oz.bx = &bXs;
+      oz.be = &bEx;
+      oz_split_tiles(ctx, nt, b, T, tmax, oz.Sc, oz.Sr, oz.e);
+      ara_dense_run(ctx, nt, b, T, bs, eps, o->seed, STREAM_COMPRESS, 0, Q, B, q, as, &oz);
+    } else {
+      gen_tiles(ctx, M->pts, N, d, kern->ell, kern->nugget, b, dij, nt, T);
+      ara_dense_run(ctx, nt, b, T, bs, eps, o->seed, STREAM_COMPRESS, 0, Q, B, q, as);
+    }
     int64_t tot = 0;
     for (int u = 0; u < nt; ++u) tot += q[u];
     double* chunk = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(1, 2 * tot * b)));
@@ -1327,6 +1373,30 @@ tlr_status tlr_dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int uni
   if (!ctx || !L || !B || n < 0 || lda < n || ldb < n || nrhs < 0) return TLR_ERR_ARG;
   ABI_BEGIN
   dense_trsm(ctx, n, L, lda, unit, nrhs, B, ldb, 0);
+  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  return TLR_OK;
+  ABI_END
+}
+
+tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const double* T, const double* X, int ldx,
+                             double* C, int ldc) {
+  if (!ctx || !T || !X || !C || n <= 0 || ncols < 0 || ldx < n || ldc < n) return TLR_ERR_ARG;
+  if (n % 8 != 0) return TLR_ERR_LIMIT;
+  if (ncols == 0) return TLR_OK;
+  ABI_BEGIN
+  Buf bm(ctx), bS(ctx), be(ctx), bx(ctx), bex(ctx);
+  unsigned long long* tmax = bm.need<unsigned long long>(1);
+  oz_absmax(ctx, 1, (int64_t)n * n, T, tmax);
+  uint16_t* Sc = bS.need<uint16_t>((size_t)16 * n * n);
+  uint16_t* Sr = Sc + (size_t)8 * n * n;
+  int* eT = be.need<int>(1);
+  oz_split_tiles(ctx, 1, n, T, tmax, Sc, Sr, eT);
+  uint16_t* Xs = bx.need<uint16_t>((size_t)8 * n * ncols);
+  int* ex = bex.need<int>((size_t)ncols);
+  std::vector<OzColJob> cj{OzColJob{X, Xs, ex, ldx, ncols, 0}};
+  oz_split_cols(ctx, n, cj);
+  std::vector<OzJob> jobs{OzJob{trans ? Sc : Sr, Xs, eT, ex, C, (size_t)n * n, (size_t)n * ncols, n, ldc, n, ncols, n}};
+  oz_gemm(ctx, jobs);
   TLR_CUDA(cudaStreamSynchronize(ctx->stream));
   return TLR_OK;
   ABI_END

@@ -113,6 +113,37 @@ def _lowrank(n, r, seed, decay):
     return (X * decay ** np.arange(r)) @ Y.T
 
 
+# ------------------------------------------------------------------ split products (construction)
+@pytest.mark.parametrize("n,ncols,trans,off", [(256, 16, False, 1), (256, 37, True, 3), (1024, 16, False, 1),
+                                               (512, 70, True, 2), (64, 1, False, 0)])
+def test_split_product_matches_fp64(T, ctx, n, ncols, trans, off):
+    """T X and T^T X on BF16 tensor cores by exact 7-bit splitting: error of an FP64 product.
+
+    T is an exponential-kernel tile between two point clusters (entries over several orders of
+    magnitude, off = 0: the diagonal tile with its nugget); X is Gaussian with one scaled column.
+    The reference is numpy's FP64 product; the bound is a few units of 2^-53 of the block bounds
+    times the sum of |X| over the inner dimension.
+    """
+    xo = inputs.points(n * (off + 1), 2, 11)
+    Tn = kernel.tile(xo, off, 0, n, 0.1, 1e-4)
+    X = inputs.gaussian(13, 2, n * ncols).reshape(ncols, n).T.copy()
+    X[:, 0] *= 1e-9
+    ref = (Tn.T if trans else Tn) @ X
+    C = ctx.split_product(_t(T, Tn), _t(T, X), trans=trans).cpu().numpy()
+    scale = np.abs(Tn).max() * np.abs(X).sum(axis=0)
+    err = np.abs(C - ref) / scale[None, :]
+    assert err.max() <= 8 * 2.0 ** -53, err.max()
+    # the scaled column keeps its own accuracy (per-column bounds of X)
+    assert np.abs(C[:, 0] - ref[:, 0]).max() <= 8 * 2.0 ** -53 * scale[0]
+
+
+def test_split_product_rejects_unaligned_size(T, ctx):
+    Tn = np.eye(100)
+    with pytest.raises(T.TLRError) as ei:
+        ctx.split_product(_t(T, Tn), _t(T, np.ones((100, 2))))
+    assert ei.value.status == T.ERR_LIMIT
+
+
 def test_ara_dense_matches_oracle(T, ctx):
     import torch
     n, bs, eps = 256, 16, 1e-6
