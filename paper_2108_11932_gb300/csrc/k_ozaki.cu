@@ -14,9 +14,10 @@
 //  * Each chunk is exact in BF16 (8 significant bits).  A product of chunks is an integer
 //    below 2^14, and the sum of the chunk products of one pair (i, j) over 128 consecutive k,
 //    even added over the (i+j-1) pairs with the same i+j, stays below 2^24: the FP32
-//    accumulation of mma.sync is exact.  Every 128 k the eight group sums (i+j = 2..9) are
-//    added into FP64 accumulators with weight 2^(-7(i+j)); pairs with i+j > 9 are below
-//    2^-63 of the block bounds and are dropped.
+//    accumulation of mma.sync is exact.  Every 128 k the eight group sums (i+j = 2..9) move
+//    to 32-bit integer totals (exact for K <= 16384), which are combined in FP64 with weights
+//    2^(-7(i+j)) once at the end; pairs with i+j > 9 are below 2^-63 of the block bounds and
+//    are dropped.
 //
 // The error of a result entry is below ~2^-55 sum_k 2^eA 2^eB (plus FP64 rounding of the
 // recombination), the same order as an FP64 dot product of the same length.
@@ -62,6 +63,22 @@ __device__ __forceinline__ void oz_split(double x, int e, uint16_t out[OZ_S]) {
     out[i] = (uint16_t)(__float_as_uint(f) >> 16);  // exact: at most 7 significant bits
   }
 }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const uint16_t* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+// 16-byte asynchronous global-to-shared copy; src_bytes = 0 writes zeros (the source is not read).
+__device__ __forceinline__ void cp16(uint16_t* dst, const uint16_t* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
@@ -161,75 +178,85 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
   const int m0 = blockIdx.x * OZ_TM, n0 = blockIdx.y * OZ_TN;
   if (m0 >= J.M || n0 >= J.N) return;
   extern __shared__ __align__(16) uint16_t oz_sm[];
-  uint16_t* As = oz_sm;                          // [slice][row 64][k 32 (+8)]
-  uint16_t* Bs = oz_sm + OZ_S * OZ_TM * OZ_LDS;  // [slice][col 16][k 32 (+8)]
+  constexpr int STAGE = OZ_S * (OZ_TM + OZ_TN) * OZ_LDS;  // elements per buffer
+  // two buffers, each [slice][row 64][k 32 (+8)] (A) then [slice][col 16][k 32 (+8)] (B)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int gq = lane >> 2, tq = lane & 3;
   const int M = J.M, N = J.N, K = J.K;
-  float acc[OZ_S][2][4];
-  double out[2][4];
-#pragma unroll
-  for (int j = 0; j < 2; ++j)
-#pragma unroll
-    for (int r = 0; r < 4; ++r) out[j][r] = 0.0;
+  float acc[OZ_S][2][4];  // exact group sums of the current 128-k window (integers < 2^24)
+  int tot[OZ_S][2][4];    // exact group sums over all k so far (integers < 2^31 for K <= 16384)
 #pragma unroll
   for (int g = 0; g < OZ_S; ++g)
 #pragma unroll
     for (int j = 0; j < 2; ++j)
 #pragma unroll
-      for (int r = 0; r < 4; ++r) acc[g][j][r] = 0.f;
-
-  for (int k0 = 0; k0 < K; k0 += OZ_KC) {
-    // stage the chunk in 16-byte pieces (8 consecutive k): A 8 x 64 x 4, B 8 x 16 x 4 pieces
+      for (int r = 0; r < 4; ++r) {
+        acc[g][j][r] = 0.f;
+        tot[g][j][r] = 0;
+      }
+  // ldmatrix row addresses: A matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15); B matrices
+  // (columns 0-7 | 8-15) x (k 0-7 | 8-15) of the CTA's 16 columns
+  const int mi = lane >> 3, ri = lane & 7;
+  const int a_off = (warp * 16 + ri + (mi & 1) * 8) * OZ_LDS + (mi >> 1) * 8;
+  const int b_off = OZ_S * OZ_TM * OZ_LDS + (ri + (mi >> 1) * 8) * OZ_LDS + (mi & 1) * 8;
+  // copy chunk k0 (16-byte pieces of 8 consecutive k) into buffer `buf`, zero-filled outside
+  auto stage = [&](int k0, int buf) {
+    uint16_t* As = oz_sm + buf * STAGE;
+    uint16_t* Bs = As + OZ_S * OZ_TM * OZ_LDS;
     for (int e = tid; e < OZ_S * OZ_TM * 4; e += 128) {
       const int p = e & 3, r = (e >> 2) % OZ_TM, q = e / (4 * OZ_TM);
       const int gm = m0 + r, gk = k0 + 8 * p;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (gm < M && gk < K) v = *reinterpret_cast<const uint4*>(J.A + (size_t)q * J.sA + gk + (size_t)gm * J.lda);
-      *reinterpret_cast<uint4*>(As + (q * OZ_TM + r) * OZ_LDS + 8 * p) = v;
+      const bool in = gm < M && gk < K;
+      cp16(As + (q * OZ_TM + r) * OZ_LDS + 8 * p, in ? J.A + (size_t)q * J.sA + gk + (size_t)gm * J.lda : J.A,
+           in ? 16 : 0);
     }
     for (int e = tid; e < OZ_S * OZ_TN * 4; e += 128) {
       const int p = e & 3, c = (e >> 2) % OZ_TN, q = e / (4 * OZ_TN);
       const int gn = n0 + c, gk = k0 + 8 * p;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (gn < N && gk < K) v = *reinterpret_cast<const uint4*>(J.B + (size_t)q * J.sB + gk + (size_t)gn * K);
-      *reinterpret_cast<uint4*>(Bs + (q * OZ_TN + c) * OZ_LDS + 8 * p) = v;
+      const bool in = gn < N && gk < K;
+      cp16(Bs + (q * OZ_TN + c) * OZ_LDS + 8 * p, in ? J.B + (size_t)q * J.sB + gk + (size_t)gn * K : J.B,
+           in ? 16 : 0);
+    }
+    cp_commit();
+  };
+  stage(0, 0);
+  int buf = 0;
+  for (int k0 = 0; k0 < K; k0 += OZ_KC, buf ^= 1) {
+    if (k0 + OZ_KC < K) {
+      stage(k0 + OZ_KC, buf ^ 1);  // next chunk in flight while this one is multiplied
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
     }
     __syncthreads();
+    const uint16_t* base = oz_sm + buf * STAGE;
 #pragma unroll
     for (int ks = 0; ks < OZ_KC; ks += 16) {
+      uint32_t b[OZ_S][4];  // per slice j: b0, b1 of columns 0-7, then of columns 8-15
+#pragma unroll
+      for (int j = 0; j < OZ_S; ++j) ldsm_x4(b[j], base + b_off + j * OZ_TN * OZ_LDS + ks);
 #pragma unroll
       for (int i = 0; i < OZ_S; ++i) {
-        const uint16_t* a = As + (i * OZ_TM + warp * 16) * OZ_LDS + ks + 2 * tq;
-        const uint32_t a0 = *reinterpret_cast<const uint32_t*>(a + gq * OZ_LDS);
-        const uint32_t a1 = *reinterpret_cast<const uint32_t*>(a + (gq + 8) * OZ_LDS);
-        const uint32_t a2 = *reinterpret_cast<const uint32_t*>(a + gq * OZ_LDS + 8);
-        const uint32_t a3 = *reinterpret_cast<const uint32_t*>(a + (gq + 8) * OZ_LDS + 8);
+        uint32_t a[4];
+        ldsm_x4(a, base + a_off + i * OZ_TM * OZ_LDS + ks);
 #pragma unroll
         for (int j = 0; j + i < OZ_S; ++j) {
-#pragma unroll
-          for (int nb = 0; nb < 2; ++nb) {
-            const uint16_t* b = Bs + (j * OZ_TN + nb * 8 + gq) * OZ_LDS + ks + 2 * tq;
-            const uint32_t b0 = *reinterpret_cast<const uint32_t*>(b);
-            const uint32_t b1 = *reinterpret_cast<const uint32_t*>(b + 8);
-            mma_bf16(acc[i + j][nb], a0, a1, a2, a3, b0, b1);
-          }
+          mma_bf16(acc[i + j][0], a[0], a[1], a[2], a[3], b[j][0], b[j][1]);
+          mma_bf16(acc[i + j][1], a[0], a[1], a[2], a[3], b[j][2], b[j][3]);
         }
       }
     }
     __syncthreads();
-    if (((k0 + OZ_KC) % OZ_KF) == 0 || k0 + OZ_KC >= K) {  // fold the exact group sums into FP64
+    if (((k0 + OZ_KC) % OZ_KF) == 0 || k0 + OZ_KC >= K) {  // move the exact window sums to integers
 #pragma unroll
-      for (int g = 0; g < OZ_S; ++g) {
-        const double w = ldexp(1.0, -7 * (g + 2));
+      for (int g = 0; g < OZ_S; ++g)
 #pragma unroll
         for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
           for (int r = 0; r < 4; ++r) {
-            out[nb][r] = fma((double)acc[g][nb][r], w, out[nb][r]);
+            tot[g][nb][r] += __float2int_rn(acc[g][nb][r]);
             acc[g][nb][r] = 0.f;
           }
-      }
     }
   }
   const int eA = *J.eA;
@@ -239,7 +266,12 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
     for (int r = 0; r < 4; ++r) {
       const int gm = m0 + warp * 16 + gq + ((r & 2) ? 8 : 0);
       const int gn = n0 + nb * 8 + 2 * tq + (r & 1);
-      if (gm < M && gn < N) J.C[gm + (size_t)gn * J.ldc] = ldexp(out[nb][r], eA + J.eB[gn]);
+      if (gm < M && gn < N) {
+        double v = 0.0;  // smallest weights first
+#pragma unroll
+        for (int g = OZ_S - 1; g >= 0; --g) v = fma((double)tot[g][nb][r], ldexp(1.0, -7 * (g + 2)), v);
+        J.C[gm + (size_t)gn * J.ldc] = ldexp(v, eA + J.eB[gn]);
+      }
     }
 }
 
@@ -262,7 +294,7 @@ void oz_absmax(tlr_ctx* ctx, int nblocks, int64_t n2, const double* T, unsigned 
   TLR_LAUNCH_CHECK(ctx);
 }
 
-static size_t oz_gemm_smem() { return sizeof(uint16_t) * OZ_S * (OZ_TM + OZ_TN) * OZ_LDS; }
+static size_t oz_gemm_smem() { return 2 * sizeof(uint16_t) * OZ_S * (OZ_TM + OZ_TN) * OZ_LDS; }
 
 void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, uint16_t* Sc,
                     uint16_t* Sr, int* eT) {
@@ -295,7 +327,8 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
     attr = true;
   }
   for (auto& j : jobs)
-    TLR_REQUIRE(j.K % 8 == 0 && j.lda % 8 == 0, TLR_ERR_LIMIT, "split product needs K and lda multiples of 8");
+    TLR_REQUIRE(j.K % 8 == 0 && j.lda % 8 == 0 && j.K <= 16384, TLR_ERR_LIMIT,
+                "split product needs K, lda multiples of 8 and K <= 16384");
   int mx = 0, nx = 0;
   double flops = 0;
   for (auto& j : jobs) {
