@@ -275,7 +275,7 @@ struct OzColJob {        // columns to split: X (K x ncols, ld) -> Xs (8 slices,
   const double* X;
   uint16_t* Xs;
   int* e;
-  int ld, ncols, col0;
+  int ld, ncols, col0, K;
 };
 struct OzJob {           // C (M x N, ldc) = A B with A(m, k) = A_q[k + m * lda], B(k, n) = B_q[k + n * K]
   const uint16_t* A;     // 8 slices, stride sA
@@ -286,9 +286,10 @@ struct OzJob {           // C (M x N, ldc) = A B with A(m, k) = A_q[k + m * lda]
   size_t sA, sB;
   int lda, ldc, M, N, K;
 };
+// Sc may be null (only the transposed slices are written)
 void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, uint16_t* Sc,
                     uint16_t* Sr, int* eT);
-void oz_split_cols(tlr_ctx* ctx, int K, std::vector<OzColJob>& jobs);
+void oz_split_cols(tlr_ctx* ctx, std::vector<OzColJob>& jobs);
 void oz_absmax(tlr_ctx* ctx, int nblocks, int64_t n2, const double* T, unsigned long long* tmax);
 void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs);
 

@@ -388,10 +388,11 @@ struct Session {
   int bs = -1;
   std::vector<std::unique_ptr<Mat>> mats;
   Buf bnrm, bQ, bTab, bInfo, bTmp, bTmpMain, bOm, bOm32, bX, bW, bY32, bP, bZ, bQ32, bB32;
+  Buf bOzMax, bOzS, bOzE, bOzX, bOzEx;  // split trsm products
   AraStats total;
   explicit Session(tlr_ctx* c)
       : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bX(c), bW(c), bY32(c), bP(c), bZ(c),
-        bQ32(c), bB32(c) {}
+        bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c) {}
   ~Session() {
     cudaStreamSynchronize(ctx->side);
     cudaStreamSynchronize(ctx->main);
@@ -857,6 +858,11 @@ struct Session {
     prof_mark(ctx, PH_TRSM);
     std::vector<GemmJob<double>> jt;
     std::vector<ScaleJob> sj;
+    // V_ik = L_kk^{-1} B_i (LDL^T: then D_k^{-1}, batchIDMult).  L_kk^{-1} is a dense tile and
+    // B the column's stacked projections: for tiles of a multiple of 8 the product runs on the
+    // tensor cores by exact splitting (k_ozaki.cu), like the construction's products.
+    std::vector<Mat*> split;
+    int64_t scols = 0;
     for (Mat* Mp : L) {
       Mat& M = *Mp;
       if (!M.live || M.nops == 0) continue;
@@ -865,17 +871,51 @@ struct Session {
       F->Vcol[M.k] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(M.Rk, 1) * b));
       F->vlen[M.k] = M.Rk;
       if (M.Rk > 0) {
-        // V_ik = L_kk^{-1} B_i (LDL^T: then D_k^{-1}, batchIDMult)
-        GemmJob<double> g = job<double>(NN, b, (int)M.Rk, F->dinv + (size_t)M.k * b * b, b,
-                                        static_cast<double*>(M.Bc.p), b, b, F->Vcol[M.k], b, 1.0, 0.0);
-        g.flags = GEMM_ALOWER;  // L_kk^{-1} is lower triangular
-        jt.push_back(g);
+        if (b % 8 == 0) {
+          split.push_back(Mp);
+          scols += M.Rk;
+        } else {
+          GemmJob<double> g = job<double>(NN, b, (int)M.Rk, F->dinv + (size_t)M.k * b * b, b,
+                                          static_cast<double*>(M.Bc.p), b, b, F->Vcol[M.k], b, 1.0, 0.0);
+          g.flags = GEMM_ALOWER;  // L_kk^{-1} is lower triangular
+          jt.push_back(g);
+        }
         if (M.ldl) sj.push_back(ScaleJob{F->dvec + (size_t)M.k * b, F->Vcol[M.k], F->Vcol[M.k], b, (int)M.Rk, b, b, 1});
         M.fl_exec += (double)b * (b + 1) * M.Rk;
         M.fl_model += (double)b * b * M.Rk;
       }
     }
     gemm<double>(ctx, NN, jt);
+    if (!split.empty()) {
+      const int ns = (int)split.size();
+      int64_t tel = 0;
+      for (Mat* Mp : split) tel += (int64_t)Mp->b * Mp->b;
+      unsigned long long* tmax = bOzMax.need<unsigned long long>((size_t)ns);
+      uint16_t* Sr = bOzS.need<uint16_t>((size_t)8 * tel);
+      int* eT = bOzE.need<int>((size_t)ns);
+      int64_t xel = 0;
+      for (Mat* Mp : split) xel += (int64_t)8 * Mp->b * Mp->Rk;
+      uint16_t* Xs = bOzX.need<uint16_t>((size_t)std::max<int64_t>(xel, 1));
+      int* ex = bOzEx.need<int>((size_t)scols);
+      std::vector<OzColJob> cj;
+      std::vector<OzJob> oj;
+      int64_t to = 0, co = 0, xo = 0;
+      for (int u = 0; u < ns; ++u) {
+        Mat& M = *split[u];
+        const int b = M.b;
+        const double* Li = M.F->dinv + (size_t)M.k * b * b;
+        oz_absmax(ctx, 1, (int64_t)b * b, Li, tmax + u);
+        oz_split_tiles(ctx, 1, b, Li, tmax + u, nullptr, Sr + 8 * to, eT + u);
+        cj.push_back(OzColJob{static_cast<double*>(M.Bc.p), Xs + xo, ex + co, b, (int)M.Rk, 0, b});
+        oj.push_back(OzJob{Sr + 8 * to, Xs + xo, eT + u, ex + co, M.F->Vcol[M.k], (size_t)b * b,
+                           (size_t)b * M.Rk, b, b, b, (int)M.Rk, b});
+        to += (int64_t)b * b;
+        co += M.Rk;
+        xo += (int64_t)8 * b * M.Rk;
+      }
+      oz_split_cols(ctx, cj);
+      oz_gemm(ctx, oj);
+    }
     batched_scale_rows(ctx, sj);
     prof_mark(ctx, PH_UPDATE);
     std::vector<CopyJob> cj;

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_oz_split_tiles(const double* __restrict
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) eT[t] = e;
   const size_t n2 = (size_t)n * n;
   const double* x = T + (size_t)t * n2;
-  uint16_t* oc = Sc + (size_t)t * OZ_S * n2;
+  uint16_t* oc = Sc ? Sc + (size_t)t * OZ_S * n2 : nullptr;
   uint16_t* orow = Sr + (size_t)t * OZ_S * n2;
   __shared__ uint16_t tr[OZ_S][32][33];
   const int m0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) k_oz_split_tiles(const double* __restrict
       for (int q = 0; q < OZ_S; ++q) sl[q] = 0;
 #pragma unroll
     for (int q = 0; q < OZ_S; ++q) {
-      if (m < n && k < n) oc[(size_t)q * n2 + m + (size_t)k * n] = sl[q];
+      if (oc && m < n && k < n) oc[(size_t)q * n2 + m + (size_t)k * n] = sl[q];
       tr[q][kk][tx] = sl[q];
     }
   }
@@ -135,10 +135,11 @@ __global__ void __launch_bounds__(256) k_oz_split_tiles(const double* __restrict
 // Slices of column blocks X_j (K x ncols_j, leading dimension ld_j) relative to each
 // column's bound; slice q of column c of block j lands at Xs_j + (q * ncols_j + c) * K.
 // One CTA per column.
-__global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restrict__ jobs, const int* __restrict__ col_job,
-                                                       int K) {
+__global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restrict__ jobs,
+                                                       const int* __restrict__ col_job) {
   const int g = blockIdx.x;
   const OzColJob J = jobs[col_job[g]];
+  const int K = J.K;
   const int c = g - J.col0;
   const double* x = J.X + (size_t)c * J.ld;
   __shared__ unsigned long long red[8];
@@ -305,7 +306,7 @@ void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsi
   TLR_LAUNCH_CHECK(ctx);
 }
 
-void oz_split_cols(tlr_ctx* ctx, int K, std::vector<OzColJob>& jobs) {
+void oz_split_cols(tlr_ctx* ctx, std::vector<OzColJob>& jobs) {
   std::vector<int> col_job;
   for (size_t j = 0; j < jobs.size(); ++j) {
     jobs[j].col0 = (int)col_job.size();
@@ -315,7 +316,7 @@ void oz_split_cols(tlr_ctx* ctx, int K, std::vector<OzColJob>& jobs) {
   const OzColJob* dj = static_cast<const OzColJob*>(upload(ctx, jobs.data(), jobs.size() * sizeof(OzColJob)));
   const int* dc = static_cast<const int*>(upload(ctx, col_job.data(), col_job.size() * sizeof(int)));
   TLR_SITE_PRE(ctx);
-  k_oz_split_cols<<<(unsigned)col_job.size(), 256, 0, ctx->stream>>>(dj, dc, K);
+  k_oz_split_cols<<<(unsigned)col_job.size(), 256, 0, ctx->stream>>>(dj, dc);
   TLR_LAUNCH_CHECK(ctx);
 }
 

@@ -548,8 +548,8 @@ struct DenseSampler : Sampler {
     if (oz) {
       uint16_t* Xs = static_cast<uint16_t*>(oz->bx->need<uint16_t>((size_t)8 * n * bs));
       int* ex = oz->be->need<int>((size_t)bs);
-      std::vector<OzColJob> cj{OzColJob{Om, Xs, ex, n, bs, 0}};
-      oz_split_cols(ctx, n, cj);
+      std::vector<OzColJob> cj{OzColJob{Om, Xs, ex, n, bs, 0, n}};
+      oz_split_cols(ctx, cj);
       std::vector<OzJob> jobs;
       for (size_t s = 0; s < ops.size(); ++s)
         jobs.push_back(OzJob{oz->Sr + (size_t)ops[s] * 8 * n * n, Xs, oz->e + ops[s], ex, Ydst[s], (size_t)n * n,
@@ -576,12 +576,12 @@ struct DenseSampler : Sampler {
       for (size_t op = 0; op < q.size(); ++op) {
         if (q[op] == 0) continue;
         uint16_t* xo = Xs + (size_t)8 * n * c0;
-        cj.push_back(OzColJob{Q + (*qoff)[op], xo, ex + c0, n, q[op], 0});
+        cj.push_back(OzColJob{Q + (*qoff)[op], xo, ex + c0, n, q[op], 0, n});
         jobs.push_back(OzJob{oz->Sc + op * (size_t)8 * n * n, xo, oz->e + op, ex + c0, B + op * (size_t)n * n,
                              (size_t)n * n, (size_t)n * q[op], n, n, n, q[op], n});
         c0 += q[op];
       }
-      oz_split_cols(ctx, n, cj);
+      oz_split_cols(ctx, cj);
       oz_gemm(ctx, jobs);
       return;
     }
@@ -1393,8 +1393,8 @@ tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const do
   oz_split_tiles(ctx, 1, n, T, tmax, Sc, Sr, eT);
   uint16_t* Xs = bx.need<uint16_t>((size_t)8 * n * ncols);
   int* ex = bex.need<int>((size_t)ncols);
-  std::vector<OzColJob> cj{OzColJob{X, Xs, ex, ldx, ncols, 0}};
-  oz_split_cols(ctx, n, cj);
+  std::vector<OzColJob> cj{OzColJob{X, Xs, ex, ldx, ncols, 0, n}};
+  oz_split_cols(ctx, cj);
   std::vector<OzJob> jobs{OzJob{trans ? Sc : Sr, Xs, eT, ex, C, (size_t)n * n, (size_t)n * ncols, n, ldc, n, ncols, n}};
   oz_gemm(ctx, jobs);
   TLR_CUDA(cudaStreamSynchronize(ctx->stream));
