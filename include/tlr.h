@@ -275,7 +275,8 @@ tlr_status tlr_dense_ldlt(tlr_ctx* ctx, int n, double* A, int lda, int* info);
 tlr_status tlr_dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int unit, int nrhs,
                           double* B, int ldb);
 
-/* C = T X (trans = 0) or C = T^T X (trans = 1) for one dense n x n FP64 tile T (column-major,
+/* C = T X (trans = 0; trans = 2: the same product through the kernel that reads T by columns,
+ * as the factorization reads its panels) or C = T^T X (trans = 1) for one dense n x n FP64 tile T (column-major,
  * leading dimension n) and X n x ncols (leading dimension ldx), C n x ncols (ldc): the
  * construction's ARA products (Algorithm 1 samples and projections of Section 6's tiles),
  * computed on BF16 tensor cores by exact splitting into 7-bit slices (Ozaki et al., 2012)

@@ -295,8 +295,9 @@ class Context:
         _check(_load().tlr_dense_trsm(self.h, L.shape[0], _ptr(L), _ld(L), int(unit), B.shape[1], _ptr(B), _ld(B)),
                "tlr_dense_trsm")
 
-    def split_product(self, T, X, trans: bool = False, out=None):
-        """C = T X (or T^T X) for a dense n x n tile on BF16 tensor cores by exact splitting."""
+    def split_product(self, T, X, trans=False, out=None):
+        """C = T X (trans False/0, or 2: read T by columns) or T^T X (True/1) on BF16 tensor cores by exact
+        splitting."""
         n, ncols = T.shape[0], X.shape[1]
         C_ = out if out is not None else fortran(self.torch.empty((n, ncols), dtype=self.torch.float64,
                                                                    device=T.device))

@@ -271,13 +271,21 @@ struct SlotDescT {
   int ldx, ldx0, nb, k, i, r0, x0off, Ki, Kk, q, bs;
 };
 // FP64 products on BF16 tensor cores by exact splitting (k_ozaki.cu)
-struct OzColJob {        // columns to split: X (K x ncols, ld) -> Xs (8 slices, K x ncols each), e (ncols)
+// columns to split: X (K x ncols, ld) -> slice q of column c at Xs + q * plane + c * ldo (rows
+// K .. ldo-1 zero), relative to 2^e[c] (e[c] computed), or to 2^efix for every column
+constexpr int OZ_EFIX_NONE = -100000;
+struct OzColJob {
   const double* X;
   uint16_t* Xs;
   int* e;
   int ld, ncols, col0, K;
+  size_t plane = 0;  // 0: ncols * ldo
+  int ldo = 0;       // 0: K
+  int efix = OZ_EFIX_NONE;
 };
-struct OzJob {           // C (M x N, ldc) = A B with A(m, k) = A_q[k + m * lda], B(k, n) = B_q[k + n * K]
+// C (M x N, ldc) = A B (or C += A B), A(m, k) = A_q[k + m * lda] (rows along k) or, with acol,
+// A_q[m + k * lda] (columns along m, M a multiple of 8); B(k, n) = B_q[k + n * ldb]
+struct OzJob {
   const uint16_t* A;     // 8 slices, stride sA
   const uint16_t* B;     // 8 slices, stride sB
   const int* eA;         // block exponent of A (device)
@@ -285,6 +293,9 @@ struct OzJob {           // C (M x N, ldc) = A B with A(m, k) = A_q[k + m * lda]
   double* C;
   size_t sA, sB;
   int lda, ldc, M, N, K;
+  int ldb = 0;           // 0: K
+  int acol = 0;
+  int accumulate = 0;
 };
 // Sc may be null (only the transposed slices are written)
 void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, uint16_t* Sc,

@@ -52,6 +52,11 @@ struct Mat {
   Buf G, G32, E, DV, DV32, Bc;
   std::vector<float*> AU32, AV32, FU32, FV32;
   std::vector<int64_t> fu32cap;
+  // BF16 7-bit slices of F's U panels relative to 2 (their columns are orthonormal basis vectors,
+  // |u| <= 1): 8 planes of b x fuscap[i] each, for the tensor-core split products (b % 8 == 0)
+  bool oz = false;
+  std::vector<uint16_t*> FUs;
+  std::vector<int64_t> fuscap;
   std::vector<double> nA, nL;  // Frobenius norms of the tiles of A and of L (mixed precision rule)
   double fl_exec = 0, fl_model = 0, fl32 = 0;
   int64_t rounds = 0, t32 = 0, t64 = 0;
@@ -89,6 +94,9 @@ struct BatchSampler : Sampler {
   const std::vector<int64_t>* qoff = nullptr;
   Buf *bom = nullptr, *bom32 = nullptr, *bx = nullptr, *bw = nullptr, *by32 = nullptr, *bp = nullptr, *bz = nullptr,
       *bq32 = nullptr, *bb32 = nullptr;
+  // tensor-core split products with F's U panels (FP64 arithmetic, matrices with M.oz)
+  const int* d_one = nullptr;  // device int 1: the exponent of the U-panel slices
+  Buf *bos = nullptr, *boe = nullptr, *bws = nullptr, *bwe = nullptr;  // Omega / W (or Q) slices
   static constexpr bool F32 = sizeof(T) == 4;
   bool owns_omega() const override { return true; }
   bool mine(int op) const { return !member || (*member)[op]; }
@@ -128,9 +136,30 @@ struct BatchSampler : Sampler {
     }
     T* X = bx->need<T>((size_t)xt);
     std::vector<GemmJob<T>> jx;
+    std::vector<OzColJob> ocj;
+    std::vector<OzJob> oxj;
+    if (!F32) {  // slices of Omega for the matrices whose U panel products run split
+      int64_t ne = 0, nx = 0;
+      for (size_t u = 0; u < mp.size(); ++u) {
+        const Mat& M = *(*L)[mp[u]];
+        if (M.oz && M.Kk > 0) { ne += bs; nx += (int64_t)8 * M.b * bs; }
+      }
+      uint16_t* os = bos->need<uint16_t>((size_t)std::max<int64_t>(nx, 1));
+      int* oe = boe->need<int>((size_t)std::max<int64_t>(ne, 1));
+      for (size_t u = 0; u < mp.size(); ++u) {
+        Mat& M = *(*L)[mp[u]];
+        if (!(M.oz && M.Kk > 0)) continue;
+        ocj.push_back(OzColJob{Om + omo[u], os, oe, M.b, bs, 0, M.b});
+        // X = Urow_k^T Omega: rows of A^T are the panel's columns (k along the b rows)
+        oxj.push_back(OzJob{M.FUs[M.k], os, d_one, oe, reinterpret_cast<double*>(X + xo[u]),
+                            (size_t)M.b * M.fuscap[M.k], (size_t)M.b * bs, M.b, M.Kk, M.Kk, bs, M.b});
+        os += (size_t)8 * M.b * bs;
+        oe += bs;
+      }
+    }
     for (size_t u = 0; u < mp.size(); ++u) {
       Mat& M = *(*L)[mp[u]];
-      if (M.Kk > 0)
+      if (M.Kk > 0 && !(!F32 && M.oz))
         jx.push_back(job<T>(TN, M.Kk, bs, Panels<T>::U(M, M.k), M.b, OmT + omo[u], M.b, M.b, X + xo[u], M.Kk, 1.0, 0.0));
       if (M.R0k > 0)
         jx.push_back(job<T>(TN, (int)M.R0k, bs, Panels<T>::AV(M, M.k), M.b, OmT + omo[u], M.b, M.b, X + x0o[u],
@@ -138,6 +167,8 @@ struct BatchSampler : Sampler {
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * bs * (M.Kk + M.R0k);
     }
     gemm<T>(ctx, TN, jx);
+    oz_split_cols(ctx, ocj);
+    oz_gemm(ctx, oxj);
     // W blocks of every operand (block-diagonal Gram products), then Y = [U0 | Urow] W
     std::vector<SlotDescT<T>> sd(ops.size());
     int64_t wtot = 0, ytot = 0;
@@ -190,7 +221,17 @@ struct BatchSampler : Sampler {
     T* Y32 = F32 ? reinterpret_cast<T*>(by32->need<float>((size_t)ytot)) : nullptr;
     std::vector<GemmJob<T>> jy;
     std::vector<ConvBackJob> cb;
+    std::vector<OzColJob> wcj;
+    std::vector<OzJob> wyj;
     int64_t yo = 0;
+    int64_t wsl = 0, wex = 0;  // slices of the W_i rows that multiply Urow_i (split path)
+    if (!F32)
+      for (size_t s = 0; s < ops.size(); ++s) {
+        const Mat& M = *(*L)[(*op_m)[ops[s]]];
+        if (M.oz && sd[s].Ki > 0 && sd[s].Ki <= 16384) { wsl += (int64_t)8 * ((sd[s].Ki + 7) / 8 * 8) * bs; wex += bs; }
+      }
+    uint16_t* ws_ = wsl ? bws->need<uint16_t>((size_t)wsl) : nullptr;
+    int* we_ = wex ? bwe->need<int>((size_t)wex) : nullptr;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
       Mat& M = *(*L)[(*op_m)[op]];
@@ -198,11 +239,27 @@ struct BatchSampler : Sampler {
       T* Yo = F32 ? Y32 + yo : reinterpret_cast<T*>(Ydst[s]);
       const T* U0 = r0 ? Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)] : nullptr;
       GemmJob<T> g = job<T>(NN, M.b, bs, U0, M.b, sd[s].W, ldw, r0, Yo, M.b, 1.0, 0.0);
-      g.A[1] = Panels<T>::U(M, i);
-      g.lda[1] = M.b;
-      g.B[1] = sd[s].W + r0;
-      g.ldb[1] = ldw;
-      g.K[1] = Ki;
+      const bool split = !F32 && M.oz && Ki > 0 && Ki <= 16384;  // exact integer totals need K <= 16384
+      if (split) {  // Y = U0 W[0:r0] here, then + Urow_i W[r0:] on the tensor cores
+        const int ldo = (Ki + 7) / 8 * 8;
+        OzColJob c{reinterpret_cast<const double*>(sd[s].W + r0), ws_, we_, ldw, bs, 0, Ki};
+        c.ldo = ldo;
+        wcj.push_back(c);
+        OzJob y{M.FUs[i], ws_, d_one, we_, reinterpret_cast<double*>(Yo), (size_t)M.b * M.fuscap[i],
+                (size_t)ldo * bs, M.b, M.b, M.b, bs, Ki};
+        y.ldb = ldo;
+        y.acol = 1;
+        y.accumulate = 1;
+        wyj.push_back(y);
+        ws_ += (size_t)8 * ldo * bs;
+        we_ += bs;
+      } else {
+        g.A[1] = Panels<T>::U(M, i);
+        g.lda[1] = M.b;
+        g.B[1] = sd[s].W + r0;
+        g.ldb[1] = ldw;
+        g.K[1] = Ki;
+      }
       jy.push_back(g);
       if (F32) cb.push_back(ConvBackJob{reinterpret_cast<const float*>(Yo), Ydst[s], (int64_t)M.b * bs});
       yo += (int64_t)M.b * bs;
@@ -213,6 +270,8 @@ struct BatchSampler : Sampler {
       (F32 ? M.t32 : M.t64) += 1;
     }
     gemm<T>(ctx, NN, jy);
+    oz_split_cols(ctx, wcj);
+    oz_gemm(ctx, wyj);
     batched_to_double(ctx, cb);
   }
 
@@ -276,6 +335,16 @@ struct BatchSampler : Sampler {
       return F32 ? reinterpret_cast<const T*>(Q32 + q32o[s]) : reinterpret_cast<const T*>(Q + (*qoff)[ops[s]]);
     };
     std::vector<GemmJob<T>> jp;
+    std::vector<OzColJob> qcj;
+    std::vector<OzJob> pqj;
+    int64_t qsl = 0, qex = 0;  // slices of Q_i for the split products with Urow_i
+    if (!F32)
+      for (size_t s = 0; s < ops.size(); ++s) {
+        const Mat& M = *(*L)[(*op_m)[ops[s]]];
+        if (M.oz && sd[s].Ki > 0) { qsl += (int64_t)8 * M.b * q[ops[s]]; qex += q[ops[s]]; }
+      }
+    uint16_t* qs_ = qsl ? bws->need<uint16_t>((size_t)qsl) : nullptr;
+    int* qe_ = qex ? bwe->need<int>((size_t)qex) : nullptr;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
       Mat& M = *(*L)[(*op_m)[op]];
@@ -283,11 +352,22 @@ struct BatchSampler : Sampler {
       if (r0 > 0)
         jp.push_back(job<T>(TN, r0, q[op], Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)], M.b, Qop(s),
                             M.b, M.b, sd[s].P, ldp, 1.0, 0.0));
-      if (Ki > 0)
-        jp.push_back(job<T>(TN, Ki, q[op], Panels<T>::U(M, i), M.b, Qop(s), M.b, M.b, sd[s].P + r0, ldp, 1.0, 0.0));
+      if (Ki > 0) {
+        if (!F32 && M.oz) {  // P[r0:] = Urow_i^T Q_i on the tensor cores
+          qcj.push_back(OzColJob{reinterpret_cast<const double*>(Qop(s)), qs_, qe_, M.b, q[op], 0, M.b});
+          pqj.push_back(OzJob{M.FUs[i], qs_, d_one, qe_, reinterpret_cast<double*>(sd[s].P + r0),
+                              (size_t)M.b * M.fuscap[i], (size_t)M.b * q[op], M.b, ldp, Ki, q[op], M.b});
+          qs_ += (size_t)8 * M.b * q[op];
+          qe_ += q[op];
+        } else {
+          jp.push_back(job<T>(TN, Ki, q[op], Panels<T>::U(M, i), M.b, Qop(s), M.b, M.b, sd[s].P + r0, ldp, 1.0, 0.0));
+        }
+      }
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * q[op] * (r0 + Ki);
     }
     gemm<T>(ctx, TN, jp);
+    oz_split_cols(ctx, qcj);
+    oz_gemm(ctx, pqj);
     const SlotDescT<T>* sdd = static_cast<const SlotDescT<T>*>(upload(ctx, sd.data(), sd.size() * sizeof(SlotDescT<T>)));
     std::vector<BlkItem> items;
     for (size_t s = 0; s < ops.size(); ++s) {  // -G_ij^T P_j: r_kj x q tiles; the P0 copy: r0 x q
@@ -375,6 +455,10 @@ void free_f32(tlr_ctx* ctx, Mat& M) {
       dfree(ctx, p);
       p = nullptr;
     }
+  for (uint16_t*& p : M.FUs) {
+    dfree(ctx, p);
+    p = nullptr;
+  }
 }
 
 }  // namespace
@@ -389,10 +473,18 @@ struct Session {
   std::vector<std::unique_ptr<Mat>> mats;
   Buf bnrm, bQ, bTab, bInfo, bTmp, bTmpMain, bOm, bOm32, bX, bW, bY32, bP, bZ, bQ32, bB32;
   Buf bOzMax, bOzS, bOzE, bOzX, bOzEx;  // split trsm products
+  Buf bOzOs, bOzOe, bOzWs, bOzWe, bOne;  // split sampling / projection products
+  int* d_one = nullptr;
   AraStats total;
   explicit Session(tlr_ctx* c)
       : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bX(c), bW(c), bY32(c), bP(c), bZ(c),
-        bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c) {}
+        bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c), bOzOs(c), bOzOe(c), bOzWs(c), bOzWe(c),
+        bOne(c) {
+    static const int one = 1;
+    d_one = bOne.need<int>(1);
+    TLR_CUDA(cudaMemcpyAsync(d_one, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
   ~Session() {
     cudaStreamSynchronize(ctx->side);
     cudaStreamSynchronize(ctx->main);
@@ -433,6 +525,15 @@ struct Session {
     if (ldl) F->dvec = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b));
     F->dinv = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
     for (int i = 0; i < nb; ++i) ensure_ucap(ctx, F, i, std::max<int64_t>(A->ulen[i], 16));
+    M.oz = b % 8 == 0;
+    if (M.oz) {
+      M.FUs.assign(nb, nullptr);
+      M.fuscap.assign(nb, 0);
+      for (int i = 0; i < nb; ++i) {
+        M.fuscap[i] = F->ucap[i];
+        M.FUs[i] = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * M.fuscap[i]));
+      }
+    }
     if (M.mixed) {  // FP32 copies of A's panels; tile norms for the precision rule
       M.AU32.assign(nb, nullptr);
       M.AV32.assign(nb, nullptr);
@@ -771,6 +872,7 @@ struct Session {
         S.Q = Q; S.qoff = &qoff;
         S.bom = &bOm; S.bom32 = &bOm32; S.bx = &bX; S.bw = &bW; S.by32 = &bY32; S.bp = &bP; S.bz = &bZ;
         S.bq32 = &bQ32; S.bb32 = &bB32;
+        S.d_one = d_one; S.bos = &bOzOs; S.boe = &bOzOe; S.bws = &bOzWs; S.bwe = &bOzWe;
       };
       setup(s64, any32 ? &is64 : nullptr);
       setup(s32, &is32);
@@ -920,6 +1022,7 @@ struct Session {
     prof_mark(ctx, PH_UPDATE);
     std::vector<CopyJob> cj;
     std::vector<ConvJob> c32;
+    std::vector<OzColJob> usl;  // slices of the appended U blocks
     for (Mat* Mp : L) {
       Mat& M = *Mp;
       if (!M.live || M.nops == 0) continue;
@@ -945,6 +1048,24 @@ struct Session {
           }
           c32.push_back(ConvJob{Q + qoff[op], M.FU32[i] + (size_t)F->ulen[i] * b, (int64_t)r * b});
         }
+        if (M.oz && r > 0) {
+          if (F->ulen[i] + r > M.fuscap[i]) {  // grow the slices of block row i (8 planes)
+            const int64_t cap = std::max<int64_t>(F->ucap[i], F->ulen[i] + r);
+            uint16_t* p = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * cap));
+            if (F->ulen[i] > 0)
+              TLR_CUDA(cudaMemcpy2DAsync(p, sizeof(uint16_t) * (size_t)b * cap, M.FUs[i],
+                                         sizeof(uint16_t) * (size_t)b * M.fuscap[i],
+                                         sizeof(uint16_t) * (size_t)b * F->ulen[i], 8, cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
+            dfree(ctx, M.FUs[i]);
+            M.FUs[i] = p;
+            M.fuscap[i] = cap;
+          }
+          OzColJob sjb{Q + qoff[op], M.FUs[i] + (size_t)F->ulen[i] * b, nullptr, b, r, 0, b};
+          sjb.plane = (size_t)b * M.fuscap[i];
+          sjb.efix = 1;
+          usl.push_back(sjb);
+        }
         F->ulen[i] += r;
       }
       if (M.mixed) {
@@ -954,6 +1075,7 @@ struct Session {
     }
     batched_copy(ctx, cj);
     batched_to_float(ctx, c32);
+    oz_split_cols(ctx, usl);
     for (Mat* Mp : L)
       if (Mp->live && Mp->mixed && Mp->nops > 0) panel_tile_norms(ctx, Mp->F, Mp->k, Mp->nL, bnrm);
   

@@ -35,6 +35,7 @@ constexpr int OZ_TN = 16;    // output columns per CTA (2 n8 blocks)
 constexpr int OZ_KC = 32;    // k per shared-memory stage
 constexpr int OZ_KF = 128;   // k per exact FP32 group sum
 constexpr int OZ_LDS = 40;   // shared row stride in BF16 elements (32 + 8: conflict-free fragment loads)
+constexpr int OZ_LDSM = 72;  // shared row stride of a column-oriented A chunk (64 + 8)
 
 inline int64_t oz_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -67,6 +68,12 @@ __device__ __forceinline__ void oz_split(double x, int e, uint16_t out[OZ_S]) {
 __device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const uint16_t* p) {
   const unsigned a = (unsigned)__cvta_generic_to_shared(p);
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const uint16_t* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(a));
 }
@@ -142,6 +149,18 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restric
   const int K = J.K;
   const int c = g - J.col0;
   const double* x = J.X + (size_t)c * J.ld;
+  const int ldo = J.ldo > 0 ? J.ldo : K;
+  const size_t plane = J.plane > 0 ? J.plane : (size_t)J.ncols * ldo;
+  uint16_t* xs = J.Xs + (size_t)c * ldo;
+  if (J.efix != OZ_EFIX_NONE) {
+    for (int k = threadIdx.x; k < ldo; k += blockDim.x) {
+      uint16_t s[OZ_S];
+      if (k < K) oz_split(x[k], J.efix, s);
+#pragma unroll
+      for (int q = 0; q < OZ_S; ++q) xs[(size_t)q * plane + k] = k < K ? s[q] : (uint16_t)0;
+    }
+    return;
+  }
   __shared__ unsigned long long red[8];
   unsigned long long m = 0;
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
@@ -161,11 +180,11 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restric
   __syncthreads();
   const int e = oz_exponent(red[0]);
   if (threadIdx.x == 0) J.e[c] = e;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+  for (int k = threadIdx.x; k < ldo; k += blockDim.x) {
     uint16_t s[OZ_S];
-    oz_split(x[k], e, s);
+    if (k < K) oz_split(x[k], e, s);
 #pragma unroll
-    for (int q = 0; q < OZ_S; ++q) J.Xs[((size_t)q * J.ncols + c) * K + k] = s[q];
+    for (int q = 0; q < OZ_S; ++q) xs[(size_t)q * plane + k] = k < K ? s[q] : (uint16_t)0;
   }
 }
 
@@ -174,6 +193,7 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restric
 // A(m, k) = A_i[k + m * lda] (rows of A contiguous along k), B(k, n) = B_j[k + n * K].
 // K and lda are multiples of 8 (16-byte rows).  Grid (M / 64, N / 16, jobs); warp w owns
 // rows 16w .. 16w+15 of the CTA's 64 x 16 block.
+template <bool ACOL>
 __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs) {
   const OzJob J = jobs[blockIdx.z];
   const int m0 = blockIdx.x * OZ_TM, n0 = blockIdx.y * OZ_TN;
@@ -198,24 +218,40 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
   // ldmatrix row addresses: A matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15); B matrices
   // (columns 0-7 | 8-15) x (k 0-7 | 8-15) of the CTA's 16 columns
   const int mi = lane >> 3, ri = lane & 7;
-  const int a_off = (warp * 16 + ri + (mi & 1) * 8) * OZ_LDS + (mi >> 1) * 8;
+  // row-oriented A chunk [slice][row][k]: matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15);
+  // column-oriented [slice][k][row]: the same four matrices read transposed
+  const int a_off = ACOL ? ((mi >> 1) * 8 + ri) * OZ_LDSM + warp * 16 + (mi & 1) * 8
+                         : (warp * 16 + ri + (mi & 1) * 8) * OZ_LDS + (mi >> 1) * 8;
+  const int a_slice = ACOL ? OZ_KC * OZ_LDSM : OZ_TM * OZ_LDS;  // elements per slice of a chunk
+  const int a_ks = ACOL ? OZ_LDSM : 1;                          // step of k within a chunk
+  const int ldb = J.ldb > 0 ? J.ldb : K;
   const int b_off = OZ_S * OZ_TM * OZ_LDS + (ri + (mi >> 1) * 8) * OZ_LDS + (mi & 1) * 8;
   // copy chunk k0 (16-byte pieces of 8 consecutive k) into buffer `buf`, zero-filled outside
   auto stage = [&](int k0, int buf) {
     uint16_t* As = oz_sm + buf * STAGE;
     uint16_t* Bs = As + OZ_S * OZ_TM * OZ_LDS;
-    for (int e = tid; e < OZ_S * OZ_TM * 4; e += 128) {
-      const int p = e & 3, r = (e >> 2) % OZ_TM, q = e / (4 * OZ_TM);
-      const int gm = m0 + r, gk = k0 + 8 * p;
-      const bool in = gm < M && gk < K;
-      cp16(As + (q * OZ_TM + r) * OZ_LDS + 8 * p, in ? J.A + (size_t)q * J.sA + gk + (size_t)gm * J.lda : J.A,
-           in ? 16 : 0);
+    if (ACOL) {  // pieces of 8 consecutive rows at one k
+      for (int e = tid; e < OZ_S * OZ_KC * 8; e += 128) {
+        const int p = e & 7, kk = (e >> 3) & (OZ_KC - 1), q = e / (8 * OZ_KC);
+        const int gm = m0 + 8 * p, gk = k0 + kk;
+        const bool in = gm < M && gk < K;
+        cp16(As + (q * OZ_KC + kk) * OZ_LDSM + 8 * p, in ? J.A + (size_t)q * J.sA + gm + (size_t)gk * J.lda : J.A,
+             in ? 16 : 0);
+      }
+    } else {  // pieces of 8 consecutive k in one row
+      for (int e = tid; e < OZ_S * OZ_TM * 4; e += 128) {
+        const int p = e & 3, r = (e >> 2) % OZ_TM, q = e / (4 * OZ_TM);
+        const int gm = m0 + r, gk = k0 + 8 * p;
+        const bool in = gm < M && gk < K;
+        cp16(As + (q * OZ_TM + r) * OZ_LDS + 8 * p, in ? J.A + (size_t)q * J.sA + gk + (size_t)gm * J.lda : J.A,
+             in ? 16 : 0);
+      }
     }
     for (int e = tid; e < OZ_S * OZ_TN * 4; e += 128) {
       const int p = e & 3, c = (e >> 2) % OZ_TN, q = e / (4 * OZ_TN);
       const int gn = n0 + c, gk = k0 + 8 * p;
       const bool in = gn < N && gk < K;
-      cp16(Bs + (q * OZ_TN + c) * OZ_LDS + 8 * p, in ? J.B + (size_t)q * J.sB + gk + (size_t)gn * K : J.B,
+      cp16(Bs + (q * OZ_TN + c) * OZ_LDS + 8 * p, in ? J.B + (size_t)q * J.sB + gk + (size_t)gn * ldb : J.B,
            in ? 16 : 0);
     }
     cp_commit();
@@ -239,7 +275,8 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
 #pragma unroll
       for (int i = 0; i < OZ_S; ++i) {
         uint32_t a[4];
-        ldsm_x4(a, base + a_off + i * OZ_TM * OZ_LDS + ks);
+        if (ACOL) ldsm_x4_t(a, base + a_off + i * a_slice + ks * a_ks);
+        else ldsm_x4(a, base + a_off + i * a_slice + ks * a_ks);
 #pragma unroll
         for (int j = 0; j + i < OZ_S; ++j) {
           mma_bf16(acc[i + j][0], a[0], a[1], a[2], a[3], b[j][0], b[j][1]);
@@ -271,7 +308,9 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
         double v = 0.0;  // smallest weights first
 #pragma unroll
         for (int g = OZ_S - 1; g >= 0; --g) v = fma((double)tot[g][nb][r], ldexp(1.0, -7 * (g + 2)), v);
-        J.C[gm + (size_t)gn * J.ldc] = ldexp(v, eA + J.eB[gn]);
+        double* c = J.C + gm + (size_t)gn * J.ldc;
+        v = ldexp(v, eA + J.eB[gn]);
+        *c = J.accumulate ? *c + v : v;
       }
     }
 }
@@ -324,12 +363,18 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
   if (jobs.empty()) return;
   static bool attr = false;
   if (!attr) {
-    TLR_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_gemm_smem()));
+    TLR_CUDA(cudaFuncSetAttribute(k_oz_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_gemm_smem()));
+    TLR_CUDA(cudaFuncSetAttribute(k_oz_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_gemm_smem()));
     attr = true;
   }
-  for (auto& j : jobs)
-    TLR_REQUIRE(j.K % 8 == 0 && j.lda % 8 == 0 && j.K <= 16384, TLR_ERR_LIMIT,
-                "split product needs K, lda multiples of 8 and K <= 16384");
+  const bool acol = jobs[0].acol != 0;
+  for (auto& j : jobs) {
+    const int ldb = j.ldb > 0 ? j.ldb : j.K;
+    // 16-byte pieces: rows of A (or its columns), columns of B, all on 8-element boundaries
+    TLR_REQUIRE((j.acol != 0) == acol && j.lda % 8 == 0 && ldb % 8 == 0 && j.K <= 16384 &&
+                    (acol ? j.M % 8 == 0 : j.K % 8 == 0),
+                TLR_ERR_LIMIT, "split product: unsupported shape");
+  }
   int mx = 0, nx = 0;
   double flops = 0;
   for (auto& j : jobs) {
@@ -343,7 +388,8 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
     dim3 grid((unsigned)oz_cdiv(mx, OZ_TM), (unsigned)oz_cdiv(nx, OZ_TN), (unsigned)cnt);
     ctx->site_next_flops = flops * cnt / jobs.size();
     TLR_SITE_PRE(ctx);
-    k_oz_gemm<<<grid, 128, oz_gemm_smem(), ctx->stream>>>(dj);
+    if (acol) k_oz_gemm<true><<<grid, 128, oz_gemm_smem(), ctx->stream>>>(dj);
+    else k_oz_gemm<false><<<grid, 128, oz_gemm_smem(), ctx->stream>>>(dj);
     TLR_LAUNCH_CHECK(ctx);
   }
 }

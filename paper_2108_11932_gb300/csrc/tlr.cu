@@ -1380,7 +1380,7 @@ tlr_status tlr_dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int uni
 
 tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const double* T, const double* X, int ldx,
                              double* C, int ldc) {
-  if (!ctx || !T || !X || !C || n <= 0 || ncols < 0 || ldx < n || ldc < n) return TLR_ERR_ARG;
+  if (!ctx || !T || !X || !C || n <= 0 || ncols < 0 || ldx < n || ldc < n || trans < 0 || trans > 2) return TLR_ERR_ARG;
   if (n % 8 != 0) return TLR_ERR_LIMIT;
   if (ncols == 0) return TLR_OK;
   ABI_BEGIN
@@ -1395,7 +1395,11 @@ tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const do
   int* ex = bex.need<int>((size_t)ncols);
   std::vector<OzColJob> cj{OzColJob{X, Xs, ex, ldx, ncols, 0, n}};
   oz_split_cols(ctx, cj);
-  std::vector<OzJob> jobs{OzJob{trans ? Sc : Sr, Xs, eT, ex, C, (size_t)n * n, (size_t)n * ncols, n, ldc, n, ncols, n}};
+  std::vector<OzJob> jobs{OzJob{trans == 1 ? Sc : Sr, Xs, eT, ex, C, (size_t)n * n, (size_t)n * ncols, n, ldc, n, ncols, n}};
+  if (trans == 2) {  // T X with T read by columns: A(m, k) = Sc[m + k n]
+    jobs[0].A = Sc;
+    jobs[0].acol = 1;
+  }
   oz_gemm(ctx, jobs);
   TLR_CUDA(cudaStreamSynchronize(ctx->stream));
   return TLR_OK;

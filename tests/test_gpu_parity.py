@@ -114,8 +114,8 @@ def _lowrank(n, r, seed, decay):
 
 
 # ------------------------------------------------------------------ split products (construction)
-@pytest.mark.parametrize("n,ncols,trans,off", [(256, 16, False, 1), (256, 37, True, 3), (1024, 16, False, 1),
-                                               (512, 70, True, 2), (64, 1, False, 0)])
+@pytest.mark.parametrize("n,ncols,trans,off", [(256, 16, 0, 1), (256, 37, 1, 3), (1024, 16, 0, 1),
+                                               (512, 70, 1, 2), (64, 1, 0, 0), (256, 37, 2, 3), (1024, 16, 2, 1)])
 def test_split_product_matches_fp64(T, ctx, n, ncols, trans, off):
     """T X and T^T X on BF16 tensor cores by exact 7-bit splitting: error of an FP64 product.
 
@@ -128,7 +128,7 @@ def test_split_product_matches_fp64(T, ctx, n, ncols, trans, off):
     Tn = kernel.tile(xo, off, 0, n, 0.1, 1e-4)
     X = inputs.gaussian(13, 2, n * ncols).reshape(ncols, n).T.copy()
     X[:, 0] *= 1e-9
-    ref = (Tn.T if trans else Tn) @ X
+    ref = (Tn.T if trans == 1 else Tn) @ X
     C = ctx.split_product(_t(T, Tn), _t(T, X), trans=trans).cpu().numpy()
     scale = np.abs(Tn).max() * np.abs(X).sum(axis=0)
     err = np.abs(C - ref) / scale[None, :]
