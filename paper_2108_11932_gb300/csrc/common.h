@@ -296,6 +296,12 @@ struct OzJob {
   int ldb = 0;           // 0: K
   int acol = 0;
   int accumulate = 0;
+  // split K: slices of whole 32-deep chunks, FP64 partials in ws, summed in slice order by the
+  // last CTA of each output block (arrival counters).  nsplit = 0 lets oz_gemm choose from the
+  // job's shape; the caller may fix it (1: no split).
+  int nsplit = 0, tiles_n = 1;
+  double* ws = nullptr;
+  int* ctr = nullptr;
 };
 // Sc may be null (only the transposed slices are written)
 void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, uint16_t* Sc,

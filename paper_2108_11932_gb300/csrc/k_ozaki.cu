@@ -196,7 +196,9 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restric
 template <bool ACOL>
 __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs) {
   const OzJob J = jobs[blockIdx.z];
-  const int m0 = blockIdx.x * OZ_TM, n0 = blockIdx.y * OZ_TN;
+  if ((int)blockIdx.y >= J.tiles_n * J.nsplit) return;
+  const int nt = blockIdx.y % J.tiles_n, split = blockIdx.y / J.tiles_n;
+  const int m0 = blockIdx.x * OZ_TM, n0 = nt * OZ_TN;
   if (m0 >= J.M || n0 >= J.N) return;
   extern __shared__ __align__(16) uint16_t oz_sm[];
   constexpr int STAGE = OZ_S * (OZ_TM + OZ_TN) * OZ_LDS;  // elements per buffer
@@ -256,10 +258,13 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
     }
     cp_commit();
   };
-  stage(0, 0);
+  const int nch = (K + OZ_KC - 1) / OZ_KC;
+  const int kb = (int)((int64_t)nch * split / J.nsplit) * OZ_KC;
+  const int ke = min(K, (int)((int64_t)nch * (split + 1) / J.nsplit) * OZ_KC);
+  if (kb < ke) stage(kb, 0);
   int buf = 0;
-  for (int k0 = 0; k0 < K; k0 += OZ_KC, buf ^= 1) {
-    if (k0 + OZ_KC < K) {
+  for (int k0 = kb; k0 < ke; k0 += OZ_KC, buf ^= 1) {
+    if (k0 + OZ_KC < ke) {
       stage(k0 + OZ_KC, buf ^ 1);  // next chunk in flight while this one is multiplied
       cp_wait<1>();
     } else {
@@ -285,7 +290,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
       }
     }
     __syncthreads();
-    if (((k0 + OZ_KC) % OZ_KF) == 0 || k0 + OZ_KC >= K) {  // move the exact window sums to integers
+    if (((k0 + OZ_KC - kb) % OZ_KF) == 0 || k0 + OZ_KC >= ke) {  // move the exact window sums to integers
 #pragma unroll
       for (int g = 0; g < OZ_S; ++g)
 #pragma unroll
@@ -298,6 +303,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
     }
   }
   const int eA = *J.eA;
+  const size_t MN = (size_t)M * N;
 #pragma unroll
   for (int nb = 0; nb < 2; ++nb)
 #pragma unroll
@@ -308,11 +314,35 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
         double v = 0.0;  // smallest weights first
 #pragma unroll
         for (int g = OZ_S - 1; g >= 0; --g) v = fma((double)tot[g][nb][r], ldexp(1.0, -7 * (g + 2)), v);
-        double* c = J.C + gm + (size_t)gn * J.ldc;
         v = ldexp(v, eA + J.eB[gn]);
-        *c = J.accumulate ? *c + v : v;
+        if (J.nsplit > 1) {
+          J.ws[(size_t)split * MN + gm + (size_t)gn * M] = v;
+        } else {
+          double* c = J.C + gm + (size_t)gn * J.ldc;
+          *c = J.accumulate ? *c + v : v;
+        }
       }
     }
+  if (J.nsplit == 1) return;
+  // the last slice to finish this output block sums the partials in slice order
+  __threadfence();
+  __syncthreads();
+  __shared__ int last;
+  int* ctr = J.ctr + (m0 / OZ_TM) * J.tiles_n + nt;
+  if (tid == 0) last = (atomicAdd(ctr, 1) == J.nsplit - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = tid; e < OZ_TM * OZ_TN; e += 128) {
+    const int gm = m0 + e % OZ_TM, gn = n0 + e / OZ_TM;
+    if (gm >= M || gn >= N) continue;
+    const size_t o = gm + (size_t)gn * M;
+    double v = 0.0;
+    for (int sp = 0; sp < J.nsplit; ++sp) v += __ldcg(J.ws + (size_t)sp * MN + o);
+    double* c = J.C + gm + (size_t)gn * J.ldc;
+    *c = J.accumulate ? *c + v : v;
+  }
+  if (tid == 0) *ctr = 0;
 }
 
 // Largest |entry| of each of a batch of n2-element blocks, as FP64 bits (atomic max; zeroed first).
@@ -375,17 +405,40 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
                     (acol ? j.M % 8 == 0 : j.K % 8 == 0),
                 TLR_ERR_LIMIT, "split product: unsupported shape");
   }
-  int mx = 0, nx = 0;
+  // Split K per job (its shape only, so a product sums in the same order alone or in a batch):
+  // enough slices of at least eight 32-deep chunks for the job alone to give ~1 CTA per SM.
+  int mx = 0, ny = 0;
   double flops = 0;
+  size_t ws_elems = 0, nctr = 0;
   for (auto& j : jobs) {
+    const int tm = (j.M + OZ_TM - 1) / OZ_TM;
+    j.tiles_n = (j.N + OZ_TN - 1) / OZ_TN;
+    const int nch = (j.K + OZ_KC - 1) / OZ_KC;
+    const int64_t want = ((int64_t)std::max(ctx->sm_count, 1) + (int64_t)tm * j.tiles_n - 1) / ((int64_t)tm * j.tiles_n);
+    if (j.nsplit <= 0) j.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, nch / 8, 64}));
     mx = std::max(mx, j.M);
-    nx = std::max(nx, j.N);
+    ny = std::max(ny, j.tiles_n * j.nsplit);
     flops += 2.0 * j.M * j.N * (double)j.K;
+    if (j.nsplit > 1) {
+      ws_elems += (size_t)j.nsplit * j.M * j.N;
+      nctr += (size_t)tm * j.tiles_n;
+    }
+  }
+  if (ws_elems) {
+    double* ws = static_cast<double*>(scratch(ctx, ws_elems * sizeof(double)));
+    int* ctr = split_counters(ctx, nctr);
+    for (auto& j : jobs)
+      if (j.nsplit > 1) {
+        j.ws = ws;
+        j.ctr = ctr;
+        ws += (size_t)j.nsplit * j.M * j.N;
+        ctr += (size_t)((j.M + OZ_TM - 1) / OZ_TM) * j.tiles_n;
+      }
   }
   for (size_t o = 0; o < jobs.size(); o += 65535) {
     const int cnt = (int)std::min<size_t>(65535, jobs.size() - o);
     const OzJob* dj = static_cast<const OzJob*>(upload(ctx, jobs.data() + o, cnt * sizeof(OzJob)));
-    dim3 grid((unsigned)oz_cdiv(mx, OZ_TM), (unsigned)oz_cdiv(nx, OZ_TN), (unsigned)cnt);
+    dim3 grid((unsigned)oz_cdiv(mx, OZ_TM), (unsigned)ny, (unsigned)cnt);
     ctx->site_next_flops = flops * cnt / jobs.size();
     TLR_SITE_PRE(ctx);
     if (acol) k_oz_gemm<true><<<grid, 128, oz_gemm_smem(), ctx->stream>>>(dj);

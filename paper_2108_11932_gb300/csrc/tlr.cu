@@ -551,9 +551,11 @@ struct DenseSampler : Sampler {
       std::vector<OzColJob> cj{OzColJob{Om, Xs, ex, n, bs, 0, n}};
       oz_split_cols(ctx, cj);
       std::vector<OzJob> jobs;
-      for (size_t s = 0; s < ops.size(); ++s)
+      for (size_t s = 0; s < ops.size(); ++s) {
         jobs.push_back(OzJob{oz->Sr + (size_t)ops[s] * 8 * n * n, Xs, oz->e + ops[s], ex, Ydst[s], (size_t)n * n,
                              (size_t)n * bs, n, n, n, bs, n});
+        jobs.back().nsplit = 1;  // a batch of tiles fills the GPU without splitting K
+      }
       oz_gemm(ctx, jobs);
       return;
     }
@@ -579,6 +581,7 @@ struct DenseSampler : Sampler {
         cj.push_back(OzColJob{Q + (*qoff)[op], xo, ex + c0, n, q[op], 0, n});
         jobs.push_back(OzJob{oz->Sc + op * (size_t)8 * n * n, xo, oz->e + op, ex + c0, B + op * (size_t)n * n,
                              (size_t)n * n, (size_t)n * q[op], n, n, n, q[op], n});
+        jobs.back().nsplit = 1;
         c0 += q[op];
       }
       oz_split_cols(ctx, cj);
