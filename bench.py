@@ -160,23 +160,31 @@ class Clocks:
 
 
 # --------------------------------------------------------------------------- our arm
-def _traffic_per_flop(name="gemm_fp64.md"):
-    """DRAM bytes per algorithmic flop of a k_gemm launch, from the committed ncu summary, or None.
-
-    The summary records one captured launch of the current kernel (a smaller workload, same code
-    path); operand traffic of these products grows with their flops at a fixed sample width, so the
-    bench scales it by its live flops per launch.
-    """
+def _profile_value(name, key):
+    """A `key: value` line of a committed ncu summary under profiles/, or None."""
     p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     for line in open(p):
-        if line.startswith("traffic_bytes_per_flop:"):
+        if line.startswith(key + ":"):
             try:
                 return float(line.split(":", 1)[1])
             except ValueError:
                 return None
     return None
+
+
+def _measured_hbm_gbs():
+    """HBM copy bandwidth of this machine's GB300 (MEASURED_PEAKS.json), else the recipe's fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        for k in ("hbm_gbs", "hbm_copy_gbs"):
+            if k in d:
+                return float(d[k])
+    except (OSError, ValueError, TypeError):
+        pass
+    return 6800.0
 
 
 def run_ours(args, w, eps):
@@ -258,26 +266,46 @@ def run_ours(args, w, eps):
     ms_per_step = total_ms / args.steps
     info = infos[-1][1]
     factor_s = med["factor"]
-    # roofline of the dominant kernel (largest share of GEMM time in the timed region)
-    fam = max(gst, key=lambda f: gst[f]["ms"])
-    g = gst[fam]
+    # Roofline of the dominant kernel: the FP64 batched GEMM k_gemm (all modes; DFMA-bound) or the
+    # tensor-core split product k_oz_gemm (HBM-bound), whichever takes more time in the step.
     peak64 = ctx.fp64_peak()
-    per_launch_flops = g["flops"] / max(g["launches"], 1)
-    per_launch_s = g["ms"] / 1e3 / max(g["launches"], 1)
-    achieved = per_launch_flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
-    fp32_peak = 74.6  # FFMA, measured on this machine's GB300 (see profiles/peaks_gb300.md)
-    peak = peak64 if fam.startswith("fp64") else fp32_peak
-    roofline = {"bound": "alu", "kernel": f"k_gemm<{fam}>", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None,
-                "traffic": (_traffic_per_flop() * per_launch_flops
-                            if fam.startswith("fp64") and _traffic_per_flop() is not None else None),
-                "traffic_source": "profiles/gemm_fp64.md: ncu DRAM bytes per flop of a captured k_gemm launch "
-                                  "(cov2d_16k) x live flops per launch",
-                "peak_source": ("FP64 DFMA loop measured live in this run (tlr_fp64_peak)" if fam.startswith("fp64")
-                                else "FP32 FFMA loop measured on this pool's GB300"),
-                "share_of_step": g["ms"] / ms_per_step, "launches": g["launches"],
-                "measured_on": "one extra step after the timed steps, CUDA events around each launch",
-                "flops_per_launch": per_launch_flops}
+    hbm_peak = _measured_hbm_gbs()
+    g64 = {"ms": sum(gst[f]["ms"] for f in ("fp64_NN", "fp64_TN", "fp64_NT")),
+           "flops": sum(gst[f]["flops"] for f in ("fp64_NN", "fp64_TN", "fp64_NT")),
+           "launches": sum(gst[f]["launches"] for f in ("fp64_NN", "fp64_TN", "fp64_NT"))}
+    gsp = gst.get("split_bf16", {"ms": 0.0, "flops": 0.0, "bytes": 0.0, "launches": 0})
+
+    def roof_gemm():
+        fl = g64["flops"] / max(g64["launches"], 1)
+        sec = g64["ms"] / 1e3 / max(g64["launches"], 1)
+        ach = fl / sec / 1e12 if sec > 0 else 0.0
+        tpf = _profile_value("gemm_fp64.md", "traffic_bytes_per_flop")
+        return {"bound": "alu", "kernel": "k_gemm (FP64, NN/TN/NT)", "achieved": ach, "peak": peak64,
+                "unit": "TFLOP/s", "frac": ach / peak64 if peak64 else None,
+                "traffic": tpf * fl if tpf is not None else None,
+                "traffic_source": "profiles/gemm_fp64.md: ncu DRAM bytes per algorithmic flop of the kernel "
+                                  "(cov2d_16k launch window) x live flops per launch",
+                "peak_source": "FP64 DFMA loop measured live in this run (tlr_fp64_peak)",
+                "share_of_step": g64["ms"] / ms_per_step, "launches": g64["launches"], "flops_per_launch": fl,
+                "measured_on": "one extra step after the timed steps, CUDA events around each launch"}
+
+    def roof_split():
+        by = gsp["bytes"] / max(gsp["launches"], 1)
+        sec = gsp["ms"] / 1e3 / max(gsp["launches"], 1)
+        ach = by / sec / 1e9 if sec > 0 else 0.0
+        tpb = _profile_value("split_product_bf16.md", "traffic_per_algorithmic_byte")
+        return {"bound": "hbm", "kernel": "k_oz_gemm (FP64 products on BF16 tensor cores, exact splitting)",
+                "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak if hbm_peak else None,
+                "traffic": tpb * by if tpb is not None else None,
+                "traffic_source": "profiles/split_product_bf16.md: ncu DRAM bytes per algorithmic byte x live "
+                                  "algorithmic bytes per launch",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "fp64_equivalent_tflops": gsp["flops"] / gsp["ms"] / 1e9 if gsp["ms"] else 0.0,
+                "share_of_step": gsp["ms"] / ms_per_step, "launches": gsp["launches"], "bytes_per_launch": by,
+                "measured_on": "one extra step after the timed steps, CUDA events around each launch"}
+
+    roofline = roof_gemm() if g64["ms"] >= gsp["ms"] else roof_split()
+    roofline_other = roof_split() if g64["ms"] >= gsp["ms"] else roof_gemm()
     out = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if prec == T.PREC_FP64 else "f32+f64", "data": "synthetic",
@@ -290,7 +318,8 @@ def run_ours(args, w, eps):
            "factor_tflops_model": info["flops_model"] / factor_s / 1e12,
            "factor_fp64_frac_exec": info["flops_exec"] / factor_s / 1e12 / peak64,
            "ranks": {"mean": info["mean_rank"], "max": info["max_rank"]}, "logdet": infos[-1][0][0],
-           "fp64_peak_tflops": peak64, "roofline": roofline, "gpu_launches": launches,
+           "fp64_peak_tflops": peak64, "roofline": roofline, "roofline_second_kernel": roofline_other,
+           "gpu_launches": launches,
            "gemm_kernels": {f: {"ms_per_step": v["ms"], "tflops": (v["flops"] / v["ms"] / 1e9 if v["ms"] else 0),
                                 "launches_per_step": v["launches"]} for f, v in gst.items() if v["launches"]}}
     if ck:

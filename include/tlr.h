@@ -293,13 +293,15 @@ tlr_status tlr_fp64_peak(tlr_ctx* ctx, double* tflops);
 /* Number of kernels this library launched on the context since creation. */
 int64_t tlr_launch_count(const tlr_ctx* ctx);
 
-/* Measurement utility (not part of the method): per-launch CUDA-event timing of
- * the batched GEMM kernel.  Copies, for the six families (FP64 NN, TN, NT,
- * FP32 NN, TN, NT), the accumulated milliseconds, algorithmic flops
- * (2 M N K per job, half for lower-triangular outputs) and launch counts since
- * the last call (any pointer may be NULL; arrays of 6), resets them, and turns
- * the accounting on (enable != 0) or off. */
-tlr_status tlr_gemm_stats(tlr_ctx* ctx, int enable, double* ms, double* flops, int64_t* launches);
+/* Measurement utility (not part of the method): per-launch CUDA-event accounting of the
+ * batched products, by family: 0-2 FP64 k_gemm NN / TN / NT, 3-5 FP32 k_gemm NN / TN / NT,
+ * 6 the BF16 tensor-core split products (FP64-equivalent flops).  Copies the accumulated
+ * milliseconds, algorithmic flops (2 M N K per job, half for a triangular operand), algorithmic
+ * bytes (split products only: slices read once, C written) and launch counts since the last call
+ * (any pointer may be NULL; arrays of TLR_GEMM_FAMILIES), resets them, and turns the
+ * accounting on (enable != 0) or off. */
+#define TLR_GEMM_FAMILIES 7
+tlr_status tlr_gemm_stats(tlr_ctx* ctx, int enable, double* ms, double* flops, double* bytes, int64_t* launches);
 
 /* Measurement utility (not part of the method): phase profiler in the spirit
  * of the paper's phase breakdown (Section 6.1, Figure 8a).  Stream time between

@@ -78,7 +78,7 @@ def _load():
         "tlr_copy": (C.c_int, [P, P, C.POINTER(P)]),
         "tlr_compress_ordered": (C.c_int, [P, P, P, C.c_int64, C.c_int, C.POINTER(Kernel), C.c_int, C.c_double,
                                            C.POINTER(Opts), C.POINTER(P)]),
-        "tlr_gemm_stats": (C.c_int, [P, C.c_int, D, D, C.POINTER(C.c_int64)]),
+        "tlr_gemm_stats": (C.c_int, [P, C.c_int, D, D, D, C.POINTER(C.c_int64)]),
         "tlr_factor_batch": (C.c_int, [P, C.c_int, C.POINTER(P), D, C.POINTER(Opts), C.c_int, C.POINTER(C.c_int)]),
         "tlr_session_create": (C.c_int, [P, C.POINTER(P)]),
         "tlr_session_destroy": (C.c_int, [P]),
@@ -246,15 +246,18 @@ class Context:
         _check(_load().tlr_factor_batch(self.h, n, hs, ev, op, int(ldl), st), "tlr_factor_batch")
         return [st[i] for i in range(n)]
 
-    GEMM_FAMILIES = ["fp64_NN", "fp64_TN", "fp64_NT", "fp32_NN", "fp32_TN", "fp32_NT"]
+    GEMM_FAMILIES = ["fp64_NN", "fp64_TN", "fp64_NT", "fp32_NN", "fp32_TN", "fp32_NT", "split_bf16"]
 
     def gemm_stats(self, enable: bool = True) -> dict:
         """Return (and reset) per-family GEMM launch accounting; switch it on/off."""
-        ms = (C.c_double * 6)()
-        fl = (C.c_double * 6)()
-        ln = (C.c_int64 * 6)()
-        _check(_load().tlr_gemm_stats(self.h, int(enable), ms, fl, ln), "tlr_gemm_stats")
-        return {f: {"ms": ms[i], "flops": fl[i], "launches": ln[i]} for i, f in enumerate(self.GEMM_FAMILIES)}
+        nf = len(self.GEMM_FAMILIES)
+        ms = (C.c_double * nf)()
+        fl = (C.c_double * nf)()
+        by = (C.c_double * nf)()
+        ln = (C.c_int64 * nf)()
+        _check(_load().tlr_gemm_stats(self.h, int(enable), ms, fl, by, ln), "tlr_gemm_stats")
+        return {f: {"ms": ms[i], "flops": fl[i], "bytes": by[i], "launches": ln[i]}
+                for i, f in enumerate(self.GEMM_FAMILIES)}
 
     def kernel_matvec(self, points: np.ndarray, ell: float, nugget: float, X):
         x = np.ascontiguousarray(points, dtype=np.float64)

@@ -112,9 +112,9 @@ struct tlr_ctx {
   bool kprof = false;
   std::vector<cudaEvent_t> kev;
   std::vector<int> kev_fam;
-  std::vector<double> kev_flops;
+  std::vector<double> kev_flops, kev_bytes;
   size_t kev_n = 0;
-  double kfam_ms[8] = {0}, kfam_flops[8] = {0};
+  double kfam_ms[8] = {0}, kfam_flops[8] = {0}, kfam_bytes[8] = {0};
   int64_t kfam_launches[8] = {0};
   // Per-call-site launch profile (diagnostics): while tlr_profile is enabled and the
   // TLR_SITE_PROFILE environment variable names a file, which receives the table at
@@ -168,7 +168,8 @@ void prof_mark(tlr_ctx* ctx, int phase);
 void prof_flush(tlr_ctx* ctx);
 // kernel families of the GEMM accounting: fp64 NN/TN/NT, fp32 NN/TN/NT
 void kprof_begin(tlr_ctx* ctx);
-void kprof_end(tlr_ctx* ctx, int family, double flops);
+// families: 0-2 FP64 k_gemm NN/TN/NT, 3-5 FP32 k_gemm, 6 split products (k_oz_gemm)
+void kprof_end(tlr_ctx* ctx, int family, double flops, double bytes = 0);
 void kprof_flush(tlr_ctx* ctx);
 void site_tick(tlr_ctx* ctx, const char* file, int line);
 // an event just before a launch: the time since the stream's previous event is

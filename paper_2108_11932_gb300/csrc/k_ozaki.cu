@@ -435,15 +435,20 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
         ctr += (size_t)((j.M + OZ_TM - 1) / OZ_TM) * j.tiles_n;
       }
   }
+  double bytes = 0;  // algorithmic: every slice read once, C written (and read when accumulating)
+  for (auto& j : jobs)
+    bytes += 16.0 * j.M * j.K + 16.0 * j.K * j.N + 8.0 * j.M * j.N * (j.accumulate ? 2 : 1);
   for (size_t o = 0; o < jobs.size(); o += 65535) {
     const int cnt = (int)std::min<size_t>(65535, jobs.size() - o);
     const OzJob* dj = static_cast<const OzJob*>(upload(ctx, jobs.data() + o, cnt * sizeof(OzJob)));
+    if (ctx->kprof) kprof_begin(ctx);
     dim3 grid((unsigned)oz_cdiv(mx, OZ_TM), (unsigned)ny, (unsigned)cnt);
     ctx->site_next_flops = flops * cnt / jobs.size();
     TLR_SITE_PRE(ctx);
     if (acol) k_oz_gemm<true><<<grid, 128, oz_gemm_smem(), ctx->stream>>>(dj);
     else k_oz_gemm<false><<<grid, 128, oz_gemm_smem(), ctx->stream>>>(dj);
     TLR_LAUNCH_CHECK(ctx);
+    if (ctx->kprof) kprof_end(ctx, 6, flops * cnt / jobs.size(), bytes * cnt / jobs.size());
   }
 }
 

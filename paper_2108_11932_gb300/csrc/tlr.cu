@@ -142,14 +142,16 @@ void kprof_begin(tlr_ctx* ctx) {
   if (ctx->kev_fam.size() < ctx->kev.size()) {
     ctx->kev_fam.resize(ctx->kev.size());
     ctx->kev_flops.resize(ctx->kev.size());
+    ctx->kev_bytes.resize(ctx->kev.size());
   }
   TLR_CUDA(cudaEventRecord(ctx->kev[ctx->kev_n], ctx->stream));
 }
 
-void kprof_end(tlr_ctx* ctx, int family, double flops) {
+void kprof_end(tlr_ctx* ctx, int family, double flops, double bytes) {
   TLR_CUDA(cudaEventRecord(ctx->kev[ctx->kev_n + 1], ctx->stream));
   ctx->kev_fam[ctx->kev_n] = family;
   ctx->kev_flops[ctx->kev_n] = flops;
+  ctx->kev_bytes[ctx->kev_n] = bytes;
   ctx->kev_n += 2;
   if (ctx->kev_n >= 16384) kprof_flush(ctx);
 }
@@ -164,6 +166,7 @@ void kprof_flush(tlr_ctx* ctx) {
     const int f = ctx->kev_fam[e];
     ctx->kfam_ms[f] += ms;
     ctx->kfam_flops[f] += ctx->kev_flops[e];
+    ctx->kfam_bytes[f] += ctx->kev_bytes[e];
     ctx->kfam_launches[f] += 1;
   }
   ctx->kev_n = 0;
@@ -1419,15 +1422,16 @@ tlr_status tlr_fp64_peak(tlr_ctx* ctx, double* tflops) {
 
 int64_t tlr_launch_count(const tlr_ctx* ctx) { return ctx ? ctx->launches : -1; }
 
-tlr_status tlr_gemm_stats(tlr_ctx* ctx, int enable, double* ms, double* flops, int64_t* launches) {
+tlr_status tlr_gemm_stats(tlr_ctx* ctx, int enable, double* ms, double* flops, double* bytes, int64_t* launches) {
   if (!ctx) return TLR_ERR_ARG;
   ABI_BEGIN
   kprof_flush(ctx);
-  for (int f = 0; f < 6; ++f) {
+  for (int f = 0; f < TLR_GEMM_FAMILIES; ++f) {
     if (ms) ms[f] = ctx->kfam_ms[f];
     if (flops) flops[f] = ctx->kfam_flops[f];
+    if (bytes) bytes[f] = ctx->kfam_bytes[f];
     if (launches) launches[f] = ctx->kfam_launches[f];
-    ctx->kfam_ms[f] = 0; ctx->kfam_flops[f] = 0; ctx->kfam_launches[f] = 0;
+    ctx->kfam_ms[f] = 0; ctx->kfam_flops[f] = 0; ctx->kfam_bytes[f] = 0; ctx->kfam_launches[f] = 0;
   }
   ctx->kprof = enable != 0;
   return TLR_OK;
