@@ -382,6 +382,16 @@ struct BatchSampler : Sampler {
     blkdiag_project<T>(ctx, items, sdd);
     std::vector<GemmJob<T>> jb;
     std::vector<ConvBackJob> cb;
+    std::vector<OzColJob> zcj;
+    std::vector<OzJob> zbj;
+    int64_t zsl = 0, zex = 0;  // slices of the Z_i rows that multiply Urow_k (split path)
+    if (!F32)
+      for (size_t s = 0; s < ops.size(); ++s) {
+        const Mat& M = *(*L)[(*op_m)[ops[s]]];
+        if (M.oz && M.Kk > 0 && M.Kk <= 16384) { zsl += (int64_t)8 * ((M.Kk + 7) / 8 * 8) * q[ops[s]]; zex += q[ops[s]]; }
+      }
+    uint16_t* zs_ = zsl ? bws->need<uint16_t>((size_t)zsl) : nullptr;
+    int* ze_ = zex ? bwe->need<int>((size_t)zex) : nullptr;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
       Mat& M = *(*L)[(*op_m)[op]];
@@ -390,11 +400,26 @@ struct BatchSampler : Sampler {
       T* Bo = F32 ? reinterpret_cast<T*>(B32 + q32o[s]) : reinterpret_cast<T*>(Bdst);
       const T* V0 = r0 ? Panels<T>::AV(M, M.k) + (size_t)M.b * M.A->voff[ix(M.A, i, M.k)] : nullptr;
       GemmJob<T> g = job<T>(NN, M.b, q[op], V0, M.b, sd[s].Z, ldz, r0, Bo, M.b, 1.0, 0.0);
-      g.A[1] = Panels<T>::U(M, M.k);
-      g.lda[1] = M.b;
-      g.B[1] = sd[s].Z + r0;
-      g.ldb[1] = ldz;
-      g.K[1] = M.Kk;
+      if (!F32 && M.oz && M.Kk > 0 && M.Kk <= 16384) {  // B = V0 Z[0:r0] here, + Urow_k Z[r0:] split
+        const int ldo = (M.Kk + 7) / 8 * 8;
+        OzColJob c{reinterpret_cast<const double*>(sd[s].Z + r0), zs_, ze_, ldz, q[op], 0, M.Kk};
+        c.ldo = ldo;
+        zcj.push_back(c);
+        OzJob bj{M.FUs[M.k], zs_, d_one, ze_, reinterpret_cast<double*>(Bo), (size_t)M.b * M.fuscap[M.k],
+                 (size_t)ldo * q[op], M.b, M.b, M.b, q[op], M.Kk};
+        bj.ldb = ldo;
+        bj.acol = 1;
+        bj.accumulate = 1;
+        zbj.push_back(bj);
+        zs_ += (size_t)8 * ldo * q[op];
+        ze_ += q[op];
+      } else {
+        g.A[1] = Panels<T>::U(M, M.k);
+        g.lda[1] = M.b;
+        g.B[1] = sd[s].Z + r0;
+        g.ldb[1] = ldz;
+        g.K[1] = M.Kk;
+      }
       jb.push_back(g);
       if (F32) cb.push_back(ConvBackJob{reinterpret_cast<const float*>(Bo), Bdst, (int64_t)M.b * q[op]});
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * q[op] * (r0 + M.Kk);
@@ -403,6 +428,8 @@ struct BatchSampler : Sampler {
       M.fl_model += 4.0 * M.b * q[op] * R;
     }
     gemm<T>(ctx, NN, jb);
+    oz_split_cols(ctx, zcj);
+    oz_gemm(ctx, zbj);
     batched_to_double(ctx, cb);
   }
 };
