@@ -283,6 +283,9 @@ struct OzColJob {
   size_t plane = 0;  // 0: ncols * ldo
   int ldo = 0;       // 0: K
   int efix = OZ_EFIX_NONE;
+  // with emax (device: the block's largest |x| as FP64 bits) every column uses that block bound,
+  // written to e[0]
+  const unsigned long long* emax = nullptr;
 };
 // C (M x N, ldc) = A B (or C += A B), A(m, k) = A_q[k + m * lda] (rows along k) or, with acol,
 // A_q[m + k * lda] (columns along m, M a multiple of 8); B(k, n) = B_q[k + n * ldb]
@@ -297,6 +300,7 @@ struct OzJob {
   int ldb = 0;           // 0: K
   int acol = 0;
   int accumulate = 0;
+  int eB_stride = 1;     // 0: one exponent for all columns of B
   // split K: slices of whole 32-deep chunks, FP64 partials in ws, summed in slice order by the
   // last CTA of each output block (arrival counters).  nsplit = 0 lets oz_gemm choose from the
   // job's shape; the caller may fix it (1: no split).

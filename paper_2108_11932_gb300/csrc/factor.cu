@@ -57,6 +57,10 @@ struct Mat {
   bool oz = false;
   std::vector<uint16_t*> FUs;
   std::vector<int64_t> fuscap;
+  // slices of F's V panels (written once, at column j) relative to each panel's bound
+  std::vector<uint16_t*> FVs;
+  int* dFVe = nullptr;                 // per panel exponent (device, nb)
+  unsigned long long* dFVmax = nullptr;  // per panel largest |v| (device, nb)
   std::vector<double> nA, nL;  // Frobenius norms of the tiles of A and of L (mixed precision rule)
   double fl_exec = 0, fl_model = 0, fl32 = 0;
   int64_t rounds = 0, t32 = 0, t64 = 0;
@@ -482,10 +486,15 @@ void free_f32(tlr_ctx* ctx, Mat& M) {
       dfree(ctx, p);
       p = nullptr;
     }
-  for (uint16_t*& p : M.FUs) {
-    dfree(ctx, p);
-    p = nullptr;
-  }
+  for (auto* v : {&M.FUs, &M.FVs})
+    for (uint16_t*& p : *v) {
+      dfree(ctx, p);
+      p = nullptr;
+    }
+  dfree(ctx, M.dFVe);
+  dfree(ctx, M.dFVmax);
+  M.dFVe = nullptr;
+  M.dFVmax = nullptr;
 }
 
 }  // namespace
@@ -560,6 +569,9 @@ struct Session {
         M.fuscap[i] = F->ucap[i];
         M.FUs[i] = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * M.fuscap[i]));
       }
+      M.FVs.assign(nb, nullptr);
+      M.dFVe = static_cast<int*>(dalloc(ctx, sizeof(int) * nb));
+      M.dFVmax = static_cast<unsigned long long*>(dalloc(ctx, sizeof(unsigned long long) * nb));
     }
     if (M.mixed) {  // FP32 copies of A's panels; tile norms for the precision rule
       M.AU32.assign(nb, nullptr);
@@ -651,6 +663,24 @@ struct Session {
       std::vector<GemmJob<float>> jg32;
       std::vector<ScaleJob> sj;
       std::vector<ConvJob> cdv;
+      std::vector<OzJob> ogj;      // split Gram products
+      std::vector<OzColJob> dvcj;  // LDL^T: slices of D_j V_kj
+      uint16_t* dvs_ = nullptr;
+      int* dve_ = nullptr;
+      {
+        int64_t el = 0, ex = 0;
+        for (Mat* Mp : L)
+          if (Mp->ldl && Mp->oz)
+            for (int j = 0; j < Mp->k; ++j) {
+              const int r = Mp->F->rank[ix(Mp->F, Mp->k, j)];
+              el += (int64_t)8 * Mp->b * r;
+              ex += r;
+            }
+        if (el) {
+          dvs_ = bOzOs.need<uint16_t>((size_t)el);
+          dve_ = bOzOe.need<int>((size_t)ex);
+        }
+      }
       for (Mat* Mp : L) {
         Mat& M = *Mp;
         tlr_mat* F = M.F;
@@ -687,7 +717,25 @@ struct Session {
             }
             dvo += (int64_t)b * rkj;
           }
-          jg.push_back(job<double>(TN, S, rkj, Vptr(F, M.k, j), b, Vkj, b, b, G + M.goff[j], M.gld[j], 1.0, 0.0));
+          if (M.oz && M.FVs[j]) {  // G = Vcol_j[i >= k]^T [D_j] V_kj on the tensor cores
+            const size_t vo = (size_t)b * F->voff[ix(F, M.k, j)], pl = (size_t)b * F->vlen[j];
+            OzJob gj{M.FVs[j] + vo, M.FVs[j] + vo, M.dFVe + j, M.dFVe + j, G + M.goff[j], pl, pl, b, M.gld[j],
+                     S, rkj, b};
+            gj.ldb = b;
+            gj.eB_stride = 0;
+            if (M.ldl) {  // B = D_j V_kj: its own slices, per column
+              gj.B = dvs_ + 0;
+              gj.sB = (size_t)b * rkj;
+              gj.eB = dve_;
+              gj.eB_stride = 1;
+              dvcj.push_back(OzColJob{Vkj, dvs_, dve_, b, rkj, 0, b});
+              dvs_ += (size_t)8 * b * rkj;
+              dve_ += rkj;
+            }
+            ogj.push_back(gj);
+          } else {
+            jg.push_back(job<double>(TN, S, rkj, Vptr(F, M.k, j), b, Vkj, b, b, G + M.goff[j], M.gld[j], 1.0, 0.0));
+          }
           M.fl_exec += 2.0 * b * S * rkj;
           if (M.mixed)  // FP32 Gram for the tiles that sample in FP32
             jg32.push_back(job<float>(TN, S, rkj, M.FV32[j] + (size_t)b * F->voff[ix(F, M.k, j)], b, Vkj32, b, b,
@@ -698,6 +746,8 @@ struct Session {
       batched_to_float(ctx, cdv);
       gemm<double>(ctx, TN, jg);
       gemm<float>(ctx, TN, jg32);
+      oz_split_cols(ctx, dvcj);
+      oz_gemm(ctx, ogj);
     }
     // ---------------------------------------------------------------- diagonal tiles (side stream)
     // The diagonal tile is read by the column's batchTrsm only, not by its ARA: its
@@ -1046,6 +1096,20 @@ struct Session {
       oz_gemm(ctx, oj);
     }
     batched_scale_rows(ctx, sj);
+    {  // slices of the new V panels for the Gram products of the later columns
+      std::vector<OzColJob> vcj;
+      for (Mat* Mp : L) {
+        Mat& M = *Mp;
+        if (!M.live || M.nops == 0 || !M.oz || M.Rk == 0) continue;
+        const int b = M.b;
+        M.FVs[M.k] = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * M.Rk));
+        oz_absmax(ctx, 1, (int64_t)b * M.Rk, M.F->Vcol[M.k], M.dFVmax + M.k);
+        OzColJob c{M.F->Vcol[M.k], M.FVs[M.k], M.dFVe + M.k, b, (int)M.Rk, 0, b};
+        c.emax = M.dFVmax + M.k;
+        vcj.push_back(c);
+      }
+      oz_split_cols(ctx, vcj);
+    }
     prof_mark(ctx, PH_UPDATE);
     std::vector<CopyJob> cj;
     std::vector<ConvJob> c32;

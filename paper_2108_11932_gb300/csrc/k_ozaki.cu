@@ -152,10 +152,12 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restric
   const int ldo = J.ldo > 0 ? J.ldo : K;
   const size_t plane = J.plane > 0 ? J.plane : (size_t)J.ncols * ldo;
   uint16_t* xs = J.Xs + (size_t)c * ldo;
-  if (J.efix != OZ_EFIX_NONE) {
+  if (J.efix != OZ_EFIX_NONE || J.emax) {
+    const int e = J.emax ? oz_exponent(*J.emax) : J.efix;
+    if (J.emax && J.e && c == 0 && threadIdx.x == 0) J.e[0] = e;
     for (int k = threadIdx.x; k < ldo; k += blockDim.x) {
       uint16_t s[OZ_S];
-      if (k < K) oz_split(x[k], J.efix, s);
+      if (k < K) oz_split(x[k], e, s);
 #pragma unroll
       for (int q = 0; q < OZ_S; ++q) xs[(size_t)q * plane + k] = k < K ? s[q] : (uint16_t)0;
     }
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs)
         double v = 0.0;  // smallest weights first
 #pragma unroll
         for (int g = OZ_S - 1; g >= 0; --g) v = fma((double)tot[g][nb][r], ldexp(1.0, -7 * (g + 2)), v);
-        v = ldexp(v, eA + J.eB[gn]);
+        v = ldexp(v, eA + J.eB[gn * J.eB_stride]);
         if (J.nsplit > 1) {
           J.ws[(size_t)split * MN + gm + (size_t)gn * M] = v;
         } else {
