@@ -61,6 +61,10 @@ struct Mat {
   std::vector<uint16_t*> FVs;
   int* dFVe = nullptr;                 // per panel exponent (device, nb)
   unsigned long long* dFVmax = nullptr;  // per panel largest |v| (device, nb)
+  // slices of the compressed input's V panels (static), relative to each panel's bound
+  std::vector<uint16_t*> AVs;
+  int* dAVe = nullptr;
+  unsigned long long* dAVmax = nullptr;
   std::vector<double> nA, nL;  // Frobenius norms of the tiles of A and of L (mixed precision rule)
   double fl_exec = 0, fl_model = 0, fl32 = 0;
   int64_t rounds = 0, t32 = 0, t64 = 0;
@@ -146,17 +150,22 @@ struct BatchSampler : Sampler {
       int64_t ne = 0, nx = 0;
       for (size_t u = 0; u < mp.size(); ++u) {
         const Mat& M = *(*L)[mp[u]];
-        if (M.oz && M.Kk > 0) { ne += bs; nx += (int64_t)8 * M.b * bs; }
+        if (M.oz && (M.Kk > 0 || M.R0k > 0)) { ne += bs; nx += (int64_t)8 * M.b * bs; }
       }
       uint16_t* os = bos->need<uint16_t>((size_t)std::max<int64_t>(nx, 1));
       int* oe = boe->need<int>((size_t)std::max<int64_t>(ne, 1));
       for (size_t u = 0; u < mp.size(); ++u) {
         Mat& M = *(*L)[mp[u]];
-        if (!(M.oz && M.Kk > 0)) continue;
+        if (!(M.oz && (M.Kk > 0 || M.R0k > 0))) continue;
         ocj.push_back(OzColJob{Om + omo[u], os, oe, M.b, bs, 0, M.b});
         // X = Urow_k^T Omega: rows of A^T are the panel's columns (k along the b rows)
-        oxj.push_back(OzJob{M.FUs[M.k], os, d_one, oe, reinterpret_cast<double*>(X + xo[u]),
-                            (size_t)M.b * M.fuscap[M.k], (size_t)M.b * bs, M.b, M.Kk, M.Kk, bs, M.b});
+        if (M.Kk > 0)
+          oxj.push_back(OzJob{M.FUs[M.k], os, d_one, oe, reinterpret_cast<double*>(X + xo[u]),
+                              (size_t)M.b * M.fuscap[M.k], (size_t)M.b * bs, M.b, M.Kk, M.Kk, bs, M.b});
+        // X0 = V0col_k^T Omega with the slices of the compressed input's V panel
+        if (M.R0k > 0)
+          oxj.push_back(OzJob{M.AVs[M.k], os, M.dAVe + M.k, oe, reinterpret_cast<double*>(X + x0o[u]),
+                              (size_t)M.b * M.R0k, (size_t)M.b * bs, M.b, (int)M.R0k, (int)M.R0k, bs, M.b});
         os += (size_t)8 * M.b * bs;
         oe += bs;
       }
@@ -165,7 +174,7 @@ struct BatchSampler : Sampler {
       Mat& M = *(*L)[mp[u]];
       if (M.Kk > 0 && !(!F32 && M.oz))
         jx.push_back(job<T>(TN, M.Kk, bs, Panels<T>::U(M, M.k), M.b, OmT + omo[u], M.b, M.b, X + xo[u], M.Kk, 1.0, 0.0));
-      if (M.R0k > 0)
+      if (M.R0k > 0 && !(!F32 && M.oz))
         jx.push_back(job<T>(TN, (int)M.R0k, bs, Panels<T>::AV(M, M.k), M.b, OmT + omo[u], M.b, M.b, X + x0o[u],
                             (int)M.R0k, 1.0, 0.0));
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * bs * (M.Kk + M.R0k);
@@ -486,15 +495,19 @@ void free_f32(tlr_ctx* ctx, Mat& M) {
       dfree(ctx, p);
       p = nullptr;
     }
-  for (auto* v : {&M.FUs, &M.FVs})
+  for (auto* v : {&M.FUs, &M.FVs, &M.AVs})
     for (uint16_t*& p : *v) {
       dfree(ctx, p);
       p = nullptr;
     }
-  dfree(ctx, M.dFVe);
-  dfree(ctx, M.dFVmax);
-  M.dFVe = nullptr;
-  M.dFVmax = nullptr;
+  for (int** p : {&M.dFVe, &M.dAVe}) {
+    dfree(ctx, *p);
+    *p = nullptr;
+  }
+  for (unsigned long long** p : {&M.dFVmax, &M.dAVmax}) {
+    dfree(ctx, *p);
+    *p = nullptr;
+  }
 }
 
 }  // namespace
@@ -572,6 +585,19 @@ struct Session {
       M.FVs.assign(nb, nullptr);
       M.dFVe = static_cast<int*>(dalloc(ctx, sizeof(int) * nb));
       M.dFVmax = static_cast<unsigned long long*>(dalloc(ctx, sizeof(unsigned long long) * nb));
+      M.AVs.assign(nb, nullptr);
+      M.dAVe = static_cast<int*>(dalloc(ctx, sizeof(int) * nb));
+      M.dAVmax = static_cast<unsigned long long*>(dalloc(ctx, sizeof(unsigned long long) * nb));
+      std::vector<OzColJob> vcj;
+      for (int j = 0; j < nb; ++j) {
+        if (A->vlen[j] == 0) continue;
+        M.AVs[j] = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * A->vlen[j]));
+        oz_absmax(ctx, 1, (int64_t)b * A->vlen[j], A->Vcol[j], M.dAVmax + j);
+        OzColJob c{A->Vcol[j], M.AVs[j], M.dAVe + j, b, (int)A->vlen[j], 0, b};
+        c.emax = M.dAVmax + j;
+        vcj.push_back(c);
+      }
+      oz_split_cols(ctx, vcj);
     }
     if (M.mixed) {  // FP32 copies of A's panels; tile norms for the precision rule
       M.AU32.assign(nb, nullptr);
