@@ -51,10 +51,37 @@ void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t,
 }
 
 // ------------------------------------------------------------------ kernel tiles (Section 6)
+// exp(x) for x <= 0 by the table-driven method of Tang (ACM TOMS 15(2), 1989): x = (64 m + j) ln2/64 + r
+// with |r| <= ln2/128, exp(x) = 2^m 2^(j/64) (1 + p(r)), p the degree-5 Taylor polynomial of
+// e^r - 1 (truncation below 4e-17 on that interval).  tab[j] = 2^(j/64).  Ten FP64 operations:
+// GB300 retires FP64 at 1/64 of FP32, and the kernel tiles are bound by these operations.
+__device__ __forceinline__ double exp_nonpos(double x, const double* __restrict__ tab) {
+  if (x < -708.0) return 0.0;
+  const double inv_l = 92.332482616893656;          // 64 / ln 2
+  const double l1 = 0.010830424696249145;          // ln 2 / 64, high part
+  const double l2 = 3.6235106466348432e-19;        // ln 2 / 64 - l1
+  const double shifter = 6755399441055744.0;       // 1.5 * 2^52: rounds to an integer in the low word
+  const double s = fma(x, inv_l, shifter);
+  const int n = __double2loint(s);
+  const double fn = s - shifter;
+  double r = fma(-fn, l1, x);
+  r = fma(-fn, l2, r);
+  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+  q = fma(r, q, 1.0 / 6.0);
+  q = fma(r, q, 0.5);
+  const double p = fma(r * r, q, r);
+  const double t = tab[n & 63];
+  const double v = fma(t, p, t);                   // in [2^-1/128, 2): normal
+  return __longlong_as_double(__double_as_longlong(v) + ((long long)(n >> 6) << 52));
+}
+
 // With tmax, also records each tile's largest |entry| (as FP64 bits, atomically; zeroed by the caller).
 __global__ void k_gen_tiles(const double* __restrict__ pts, int64_t N, int d, double inv_ell,
                             double nugget, int b, const int* __restrict__ ij, double* __restrict__ out,
                             unsigned long long* __restrict__ tmax) {
+  __shared__ double tab[64];
+  if (threadIdx.x < 64) tab[threadIdx.x] = exp2((double)threadIdx.x / 64.0);
+  __syncthreads();
   const int t = blockIdx.y;
   const int i = ij[2 * t], j = ij[2 * t + 1];
   double* T = out + (size_t)t * b * b;
@@ -69,7 +96,7 @@ __global__ void k_gen_tiles(const double* __restrict__ pts, int64_t N, int d, do
         const double df = pts[gi * d + q] - pts[gj * d + q];
         s = fma(df, df, s);
       }
-      v = exp(-sqrt(s) * inv_ell);
+      v = exp_nonpos(-sqrt(s) * inv_ell, tab);
       if (gi == gj) v += nugget;
     } else {
       v = (gi == gj) ? 1.0 : 0.0;  // identity padding of a ragged last tile

@@ -137,6 +137,25 @@ def test_split_product_matches_fp64(T, ctx, n, ncols, trans, off):
     assert np.abs(C[:, 0] - ref[:, 0]).max() <= 8 * 2.0 ** -53 * scale[0]
 
 
+@pytest.mark.parametrize("d,ell", [(2, 0.1), (3, 0.2)])
+def test_generated_tiles_match_oracle_entrywise(T, ctx, d, ell):
+    """Diagonal tiles as generated (exp-kernel entries, nugget): a few units in the last place.
+
+    exp(-r/ell) carries the rounding of its argument, relative error |r/ell| 2^-53 for either side,
+    hence the bound grows with |log entry|.
+    """
+    from oracle import kdtree
+    N, b = 1024, 256
+    x = inputs.points(N, d, 21)
+    A = ctx.compress(x, b, 1e-6, ell, 1e-4, T.default_opts(bs=16, seed=3))
+    xo = x[kdtree.kd_order(x, b)]
+    for k in range(N // b):
+        got = A.tile(k, k)[0]
+        ref = kernel.tile(xo, k, k, b, ell, 1e-4)
+        bound = 4 * 2.0 ** -52 * (1.0 + np.abs(np.log(ref)))
+        assert np.all(np.abs(got - ref) / np.abs(ref) <= bound)
+
+
 def test_split_product_rejects_unaligned_size(T, ctx):
     Tn = np.eye(100)
     with pytest.raises(T.TLRError) as ei:
