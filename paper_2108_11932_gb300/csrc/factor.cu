@@ -185,7 +185,6 @@ struct BatchSampler : Sampler {
     // W blocks of every operand (block-diagonal Gram products), then Y = [U0 | Urow] W
     std::vector<SlotDescT<T>> sd(ops.size());
     int64_t wtot = 0, ytot = 0;
-    int kmx = 0;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], u = slot_of_m[(*op_m)[op]], i = (*op_i)[op];
       const Mat& M = *(*L)[(*op_m)[op]];
@@ -202,7 +201,6 @@ struct BatchSampler : Sampler {
       d.ldx0 = (int)std::max<int64_t>(M.R0k, 1);
       d.nb = M.nb;
       d.k = M.k;
-      kmx = std::max(kmx, M.k);
       d.i = i;
       d.r0 = M.A->rank[ix(M.A, i, M.k)];
       d.x0off = (int)M.A->voff[ix(M.A, i, M.k)];
@@ -296,7 +294,6 @@ struct BatchSampler : Sampler {
     if (ops.empty()) return;
     std::vector<SlotDescT<T>> sd(ops.size());
     int64_t ptot = 0, ztot = 0, q32tot = 0;
-    int kmx = 0;
     std::vector<int64_t> q32o(ops.size());
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
@@ -310,7 +307,6 @@ struct BatchSampler : Sampler {
       d.G = Panels<T>::G(M);
       d.nb = M.nb;
       d.k = M.k;
-      kmx = std::max(kmx, M.k);
       d.i = i;
       d.r0 = M.A->rank[ix(M.A, i, M.k)];
       d.Ki = (int)M.F->ulen[i];
