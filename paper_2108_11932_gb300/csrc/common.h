@@ -207,8 +207,15 @@ GemmJob<T> job(GemmMode mode, int M, int N, const T* A, int lda, const T* B, int
 // Kernels (k_misc.cu) -- all enqueue on ctx->stream.
 void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t, int b, int bs,
            double* out);
-void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget, int b,
-               const int* tile_ij /*device, 2 per tile*/, int ntiles, double* out,
+// Points on a 64-bit grid for the kernel tiles: X (device, N x d) = round(x 2^q) - round(o 2^q).
+struct GridInfo {
+  int q;
+  int pad;
+  double o[3];
+};
+void grid_points(tlr_ctx* ctx, const double* pts, int64_t N, int d, GridInfo* gi /*device*/, long long* X);
+void gen_tiles(tlr_ctx* ctx, const long long* X, const GridInfo* gi, int64_t N, int d, double ell, double nugget,
+               int b, const int* tile_ij /*device, 2 per tile*/, int ntiles, double* out,
                unsigned long long* tmax = nullptr /*device, per tile, zeroed*/);
 // per-slot orthogonalization helpers (Cholesky-QR with dropping)
 // thr: device array, per-slot convergence threshold

@@ -51,71 +51,261 @@ void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t,
 }
 
 // ------------------------------------------------------------------ kernel tiles (Section 6)
-// exp(x) for x <= 0 by the table-driven method of Tang (ACM TOMS 15(2), 1989): x = (64 m + j) ln2/64 + r
-// with |r| <= ln2/128, exp(x) = 2^m 2^(j/64) (1 + p(r)), p the degree-5 Taylor polynomial of
-// e^r - 1 (truncation below 4e-17 on that interval).  tab[j] = 2^(j/64).  Ten FP64 operations:
-// GB300 retires FP64 at 1/64 of FP32, and the kernel tiles are bound by these operations.
-__device__ __forceinline__ double exp_nonpos(double x, const double* __restrict__ tab) {
-  if (x < -708.0) return 0.0;
-  const double inv_l = 92.332482616893656;          // 64 / ln 2
-  const double l1 = 0.010830424696249145;          // ln 2 / 64, high part
-  const double l2 = 3.6235106466348432e-19;        // ln 2 / 64 - l1
-  const double shifter = 6755399441055744.0;       // 1.5 * 2^52: rounds to an integer in the low word
-  const double s = fma(x, inv_l, shifter);
-  const int n = __double2loint(s);
-  const double fn = s - shifter;
-  double r = fma(-fn, l1, x);
-  r = fma(-fn, l2, r);
-  double q = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  q = fma(r, q, 1.0 / 6.0);
-  q = fma(r, q, 0.5);
-  const double p = fma(r * r, q, r);
-  const double t = tab[n & 63];
-  const double v = fma(t, p, t);                   // in [2^-1/128, 2): normal
-  return __longlong_as_double(__double_as_longlong(v) + ((long long)(n >> 6) << 52));
+// A_ij = exp(-|x_i - x_j| / ell) (+ nugget on the diagonal), evaluated on the integer pipe.  GB300
+// retires FP64 at 1/64 of its FP32 rate, so a tile entry computed in FP64 (distance, square root,
+// exponential: about 25 FP64 instructions) costs as much as ~800 integer instructions; here an entry
+// takes no FP64 instruction at all:
+//
+//  1. Points on a 64-bit grid (k_grid_points, once per matrix): X = round(x 2^q) - round(o 2^q), o the
+//     per-dimension minimum, 2^q the largest power of two with (max - min) 2^q < 2^62.  Differences of
+//     grid coordinates are exact, and they equal the FP64 differences whenever the coordinates are
+//     multiples of 2^-q (every |x| >= range 2^-9); otherwise they are off by at most 2^-q.
+//  2. S = sum_k (X_ik - X_jk)^2 exactly, as a 128-bit integer.
+//  3. sqrt(S): normalised to F = S 2^-e in [1, 4), a single-precision rsqrt seed y0 (relative error
+//     ~2^-21), then one third-order Newton correction sqrt(F) = F y0 (1 + h/2 + 3h^2/8 + O(h^3)),
+//     h = 1 - F y0^2, in 64-bit fixed point (~2^-58 relative).
+//  4. z = c sqrt(S) 2^-q with c = 1/ell, then exp(-z) by the table-driven method of Tang (ACM TOMS
+//     15(2), 1989) in fixed point: z 64/ln2 = n + f (128-bit product, |f| <= 1/2), rho = f ln2/64,
+//     exp(-z) = 2^(-n/64) exp(-rho), exp(-rho) - 1 by its degree-6 Taylor polynomial (truncation
+//     below 2^-60 for |rho| <= ln2/128), 2^(-j/64) from a 64-entry Q63 table, then rounded to 53 bits.
+//
+// Error: under 0.3 x 2^-52 (1 + z) relative (the (1 + z) is the conditioning of exp in its argument,
+// which the FP64 formula has as well).  Entries below 2^-1020 (z > 707) are returned as 0.
+namespace fx {
+// round(64/ln2 2^56), round(ln2/64 2^69), Fk = round(2^62 / k!), TAB[j] = round(2^(63 - j/64))
+constexpr uint64_t KQ = 0x5c551d94ae0bf85eull;
+constexpr long long L69 = 0x58b90bfbe8e7bcd6ll;
+constexpr long long F1 = 0x4000000000000000ll, F2 = 0x2000000000000000ll, F3 = 0x0aaaaaaaaaaaaaabll,
+                    F4 = 0x02aaaaaaaaaaaaabll, F5 = 0x0088888888888889ll, F6 = 0x0016c16c16c16c17ll;
+__device__ const uint64_t TAB[64] = {
+    0x8000000000000000ull, 0x7e9f06067a4360baull, 0x7d41d96db915019dull, 0x7be86fb985689ddcull,
+    0x7a92be8a92436616ull, 0x7940bb9e2cffd89dull, 0x77f25ccdee6d7ae6ull, 0x76a7980f6cca15c2ull,
+    0x75606373ee921c97ull, 0x741cb5281e25ee34ull, 0x72dc8373be41a454ull, 0x719fc4b95f452d29ull,
+    0x70666f76154a7089ull, 0x6f307a412f074892ull, 0x6dfddbcbed791babull, 0x6cce8ae13c57ebdbull,
+    0x6ba27e656b4eb57aull, 0x6a79ad55e7f6fd10ull, 0x69540ec8f895722dull, 0x683199ed779592caull,
+    0x6712460a8fc24072ull, 0x65f60a7f79393e2eull, 0x64dcdec3371793d1ull, 0x63c6ba6455dcd8aeull,
+    0x62b39508aa836d6full, 0x61a3666d124bb204ull, 0x6096266533384a2bull, 0x5f8bccdb3d398841ull,
+    0x5e8451cfac061b5full, 0x5d7fad59099f22feull, 0x5c7dd7a3b17dcf75ull, 0x5b7ec8f19468bbc9ull,
+    0x5a827999fcef3242ull, 0x5988e20954889245ull, 0x5891fac0e95612c8ull, 0x579dbc56b48521baull,
+    0x56ac1f752150a563ull, 0x55bd1cdad49f699cull, 0x54d0ad5a753e077cull, 0x53e6c9da74b29ab5ull,
+    0x52ff6b54d8a89c75ull, 0x521a8ad704f3404full, 0x513821818624b40cull, 0x50582887dcb8a7e1ull,
+    0x4f7a993048d088d7ull, 0x4e9f6cd3967fdba8ull, 0x4dc69cdceaa72a9cull, 0x4cf022c9905bfd32ull,
+    0x4c1bf828c6dc54b8ull, 0x4b4a169b900c2d00ull, 0x4a7a77d47f7b84b1ull, 0x49ad159789f37496ull,
+    0x48e1e9b9d588e19bull, 0x4818ee218a3358eeull, 0x47521cc5a2e6a9e0ull, 0x468d6fadbf2dd4f3ull,
+    0x45cae0f1f545eb73ull, 0x450a6abaa4b77ecdull, 0x444c0740496d4294ull, 0x438fb0cb4f468808ull,
+    0x42d561b3e6243d8aull, 0x421d1461d66f2023ull, 0x4166c34c5615d0ecull, 0x40b268f9de0183baull};
+
+// exp(-c sqrt(S) 2^-q) for S = hi 2^64 + lo, c = Cm 2^(ec - 63) (Cm in [2^63, 2^64)), ezb = ec + 63 - q.
+__device__ __forceinline__ double entry(uint64_t hi, uint64_t lo, int ezb, uint64_t Cm, const uint64_t* tab) {
+  if ((hi | lo) == 0) return 1.0;
+  int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+  lz &= ~1;  // even shift: sqrt(S) = sqrt(F) 2^(63 - lz/2), F = H / 2^62 in [1, 4)
+  uint64_t H;
+  if (lz == 0) H = hi;
+  else if (lz < 64) H = (hi << lz) | (lo >> (64 - lz));
+  else H = lo << (lz - 64);
+  const unsigned top = (unsigned)(H >> 63);
+  const unsigned fb = ((127u + top) << 23) | (unsigned)((H >> (39 + top)) & 0x7fffffu);
+  const unsigned yb = __float_as_uint(rsqrtf(__uint_as_float(fb)));
+  const int ey = (int)((yb >> 23) & 0xffu) - 127;
+  const uint64_t Y0 = (uint64_t)((yb & 0x7fffffu) | 0x800000u) << (39 + ey);  // Q62
+  const uint64_t G0 = __umul64hi(H, Y0);                                      // F y0, Q60
+  const long long h = (long long)((1ull << 58) - __umul64hi(G0, Y0));         // 1 - F y0^2, Q58
+  const long long h2 = __mul64hi(h * 32, h * 32);                             // h^2, Q62
+  const long long corr = h * 8 + ((3 * h2) >> 3);                             // h/2 + 3h^2/8, Q62
+  const uint64_t G = G0 + (uint64_t)(__mul64hi((long long)G0, corr) * 4);     // sqrt(F), Q60
+  const uint64_t P = __umul64hi(G, Cm);                                       // z = P 2^(ez - 59)
+  const int ez = ezb - lz / 2;
+  if (ez >= 10) return 0.0;  // z >= 1024
+  const uint64_t phi = __umul64hi(P, KQ), plo = P * KQ;                       // z 64/ln2 = prod 2^(ez - 115)
+  const int sh = 115 - ez;
+  uint64_t n, frac;                                                           // frac: Q64 fraction of n
+  if (sh < 128) {
+    n = phi >> (sh - 64);
+    frac = (phi << (128 - sh)) | (plo >> (sh - 64));
+  } else {
+    n = 0;
+    frac = sh < 192 ? (phi >> (sh - 128)) : 0;
+  }
+  n += frac >> 63;  // nearest integer; frac becomes the signed remainder in [-1/2, 1/2)
+  if ((n >> 6) > 1020) return 0.0;
+  const long long sg = -__mul64hi((long long)frac, L69);                      // -rho, Q69
+  long long acc = F5 + (__mul64hi(sg, F6) >> 5);                             // Horner, Q62
+  acc = F4 + (__mul64hi(sg, acc) >> 5);
+  acc = F3 + (__mul64hi(sg, acc) >> 5);
+  acc = F2 + (__mul64hi(sg, acc) >> 5);
+  acc = F1 + (__mul64hi(sg, acc) >> 5);
+  const uint64_t E = (1ull << 62) + (uint64_t)(__mul64hi(sg, acc) >> 5);      // exp(-rho), Q62
+  const uint64_t V = __umul64hi(tab[n & 63], E);                              // Q61, in (0.49, 1.01)
+  const int lzv = __clzll((long long)V);
+  const uint64_t Vn = V << lzv;
+  const uint64_t M53 = (Vn >> 11) + ((Vn >> 10) & 1ull);                      // nearest, may carry to 2^53
+  const uint64_t bits = ((uint64_t)(1025 - lzv - (int)(n >> 6)) << 52) + (M53 - (1ull << 52));
+  return __longlong_as_double((long long)bits);
+}
+}  // namespace fx
+
+// round(x 2^q) as a 128-bit integer (|x| 2^q < 2^126), halves away from zero.
+__device__ __forceinline__ __int128 grid_round(double x, int q) {
+  const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((bx >> 52) & 0x7ff);
+  unsigned long long m = bx & ((1ull << 52) - 1);
+  int ex;
+  if (E == 0) {
+    ex = -1074;
+  } else {
+    m |= 1ull << 52;
+    ex = E - 1075;
+  }
+  const int sh = ex + q;
+  __int128 v;
+  if (m == 0) v = 0;
+  else if (sh >= 0) v = (__int128)m << sh;
+  else if (sh <= -64) v = 0;
+  else v = (__int128)(((m >> (-sh - 1)) + 1) >> 1);
+  return (bx >> 63) ? -v : v;
 }
 
-// With tmax, also records each tile's largest |entry| (as FP64 bits, atomically; zeroed by the caller).
-__global__ void k_gen_tiles(const double* __restrict__ pts, int64_t N, int d, double inv_ell,
-                            double nugget, int b, const int* __restrict__ ij, double* __restrict__ out,
-                            unsigned long long* __restrict__ tmax) {
-  __shared__ double tab[64];
-  if (threadIdx.x < 64) tab[threadIdx.x] = exp2((double)threadIdx.x / 64.0);
+// Grid scale and offsets of the points (one block): q and o_k = min_k x_k.  Comparisons on
+// order-preserving integer images of the FP64 bits.
+__device__ __forceinline__ unsigned long long ord_key(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | (1ull << 63));
+}
+__device__ __forceinline__ double ord_val(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & ~(1ull << 63)) : ~k));
+}
+__global__ void __launch_bounds__(256) k_grid_range(const double* __restrict__ pts, int64_t N, int d,
+                                                    GridInfo* __restrict__ gi) {
+  __shared__ unsigned long long smin[3][256], smax[3][256];
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0};
+  for (int64_t p = threadIdx.x; p < N; p += blockDim.x)
+    for (int k = 0; k < d; ++k) {
+      const unsigned long long key = ord_key(pts[p * d + k]);
+      mn[k] = key < mn[k] ? key : mn[k];
+      mx[k] = key > mx[k] ? key : mx[k];
+    }
+  for (int k = 0; k < 3; ++k) { smin[k][threadIdx.x] = mn[k]; smax[k][threadIdx.x] = mx[k]; }
   __syncthreads();
+  for (int w = 128; w; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int k = 0; k < 3; ++k) {
+        const unsigned long long a = smin[k][threadIdx.x + w], c = smax[k][threadIdx.x + w];
+        if (a < smin[k][threadIdx.x]) smin[k][threadIdx.x] = a;
+        if (c > smax[k][threadIdx.x]) smax[k][threadIdx.x] = c;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double R = 0.0, A = 0.0;
+    for (int k = 0; k < d; ++k) {
+      const double lo = ord_val(smin[0 + k][0]), hi = ord_val(smax[k][0]);
+      gi->o[k] = lo;
+      R = fmax(R, hi - lo);
+      A = fmax(A, fmax(fabs(lo), fabs(hi)));
+    }
+    int q = R > 0.0 ? 61 - ilogb(R) : 0;
+    if (A > 0.0) q = min(q, 125 - ilogb(A));
+    gi->q = q;
+  }
+}
+__global__ void k_grid_points(const double* __restrict__ pts, int64_t n, int d, const GridInfo* __restrict__ gi,
+                              long long* __restrict__ X) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int q = gi->q;
+  const int k = (int)(e % d);
+  X[e] = (long long)(grid_round(pts[e], q) - grid_round(gi->o[k], q));
+}
+
+void grid_points(tlr_ctx* ctx, const double* pts, int64_t N, int d, GridInfo* gi, long long* X) {
+  if (N <= 0) return;
+  TLR_SITE_PRE(ctx);
+  k_grid_range<<<1, 256, 0, ctx->stream>>>(pts, N, d, gi);
+  TLR_LAUNCH_CHECK(ctx);
+  TLR_SITE_PRE(ctx);
+  k_grid_points<<<cdiv(N * d, 256), 256, 0, ctx->stream>>>(pts, N * d, d, gi, X);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// One block per (column group of GT_COLS columns, tile); each thread owns rows tid, tid + 256, ... and
+// walks the group's columns, whose grid points sit in shared memory.  With tmax, also records each
+// tile's largest entry (as FP64 bits: the entries are >= 0, so the bit patterns order like the values;
+// zeroed by the caller).
+constexpr int GT_COLS = 16, GT_THREADS = 256;
+template <int D>
+__global__ void __launch_bounds__(GT_THREADS) k_gen_tiles(const long long* __restrict__ X,
+                                                          const GridInfo* __restrict__ gi, int64_t N, uint64_t Cm,
+                                                          int ec, double nugget, int b, const int* __restrict__ ij,
+                                                          double* __restrict__ out,
+                                                          unsigned long long* __restrict__ tmax) {
+  __shared__ uint64_t tab[64];
+  __shared__ long long xc[GT_COLS * D];
   const int t = blockIdx.y;
   const int i = ij[2 * t], j = ij[2 * t + 1];
-  double* T = out + (size_t)t * b * b;
-  double vmax = 0.0;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < b * b; e += gridDim.x * blockDim.x) {
-    const int r = e % b, c = e / b;
-    const int64_t gi = (int64_t)i * b + r, gj = (int64_t)j * b + c;
-    double v;
-    if (gi < N && gj < N) {
-      double s = 0.0;
-      for (int q = 0; q < d; ++q) {
-        const double df = pts[gi * d + q] - pts[gj * d + q];
-        s = fma(df, df, s);
+  const int c0 = blockIdx.x * GT_COLS, nc = min(GT_COLS, b - c0);
+  if (threadIdx.x < 64) tab[threadIdx.x] = fx::TAB[threadIdx.x];
+  if (threadIdx.x < nc * D) {
+    const int64_t gj = (int64_t)j * b + c0 + threadIdx.x / D;
+    xc[threadIdx.x] = gj < N ? X[gj * D + threadIdx.x % D] : 0;
+  }
+  __syncthreads();
+  const int ezb = ec + 63 - gi->q;
+  double* T = out + (size_t)t * b * b + (size_t)c0 * b;
+  unsigned long long vmax = 0;
+  for (int r = threadIdx.x; r < b; r += GT_THREADS) {
+    const int64_t g_i = (int64_t)i * b + r;
+    long long xr[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = g_i < N ? X[g_i * D + k] : 0;
+    for (int c = 0; c < nc; ++c) {
+      const int64_t g_j = (int64_t)j * b + c0 + c;
+      double v;
+      if (g_i < N && g_j < N) {
+        uint64_t hi = 0, lo = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const long long df = xr[k] - xc[c * D + k];
+          const uint64_t a = (uint64_t)(df < 0 ? -df : df);
+          const uint64_t l = a * a;
+          lo += l;
+          hi += __umul64hi(a, a) + (lo < l ? 1ull : 0ull);
+        }
+        v = fx::entry(hi, lo, ezb, Cm, tab);
+        if (g_i == g_j) v += nugget;
+      } else {
+        v = (g_i == g_j) ? 1.0 : 0.0;  // identity padding of a ragged last tile
       }
-      v = exp_nonpos(-sqrt(s) * inv_ell, tab);
-      if (gi == gj) v += nugget;
-    } else {
-      v = (gi == gj) ? 1.0 : 0.0;  // identity padding of a ragged last tile
+      T[r + (size_t)c * b] = v;
+      const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+      vmax = vb > vmax ? vb : vmax;
     }
-    T[e] = v;
-    vmax = fmax(vmax, fabs(v));
   }
   if (tmax) {
-    for (int o = 16; o; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(tmax + t, (unsigned long long)__double_as_longlong(vmax));
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, vmax, o);
+      vmax = w > vmax ? w : vmax;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(tmax + t, vmax);
   }
 }
 
-void gen_tiles(tlr_ctx* ctx, const double* pts, int64_t N, int d, double ell, double nugget, int b,
-               const int* tile_ij, int ntiles, double* out, unsigned long long* tmax) {
+void gen_tiles(tlr_ctx* ctx, const long long* X, const GridInfo* gi, int64_t N, int d, double ell, double nugget,
+               int b, const int* tile_ij, int ntiles, double* out, unsigned long long* tmax) {
   if (ntiles <= 0) return;
-  dim3 grid(std::min<unsigned>(cdiv((int64_t)b * b, 256), 64u), (unsigned)ntiles);
+  TLR_REQUIRE(d >= 1 && d <= 3, TLR_ERR_ARG, "points of dimension 1 to 3");
+  int ec = 0;
+  const double mc = frexp(1.0 / ell, &ec);  // 1/ell = mc 2^ec, mc in [1/2, 1)
+  const uint64_t Cm = (uint64_t)ldexp(mc, 64);
+  ec -= 1;
+  dim3 grid(cdiv(b, GT_COLS), (unsigned)ntiles);
   TLR_SITE_PRE(ctx);
-  k_gen_tiles<<<grid, 256, 0, ctx->stream>>>(pts, N, d, 1.0 / ell, nugget, b, tile_ij, out, tmax);
+  if (d == 1)
+    k_gen_tiles<1><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, nugget, b, tile_ij, out, tmax);
+  else if (d == 2)
+    k_gen_tiles<2><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, nugget, b, tile_ij, out, tmax);
+  else
+    k_gen_tiles<3><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, nugget, b, tile_ij, out, tmax);
   TLR_LAUNCH_CHECK(ctx);
 }
 

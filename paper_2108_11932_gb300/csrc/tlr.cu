@@ -689,11 +689,15 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
   M->dperm = static_cast<int64_t*>(dalloc(ctx, sizeof(int64_t) * N));
   TLR_CUDA(cudaMemcpyAsync(M->dperm, M->perm.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, ctx->stream));
   M->diag = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
+  Buf bGx(ctx), bGi(ctx);
+  long long* gx = bGx.need<long long>((size_t)N * d);
+  GridInfo* ginfo = reinterpret_cast<GridInfo*>(bGi.need<double>(sizeof(GridInfo) / sizeof(double) + 1));
+  grid_points(ctx, M->pts, N, d, ginfo, gx);
   {
     std::vector<int> ij;
     for (int k = 0; k < nb; ++k) { ij.push_back(k); ij.push_back(k); }
     const int* dij = static_cast<const int*>(upload(ctx, ij.data(), ij.size() * sizeof(int)));
-    gen_tiles(ctx, M->pts, N, d, kern->ell, kern->nugget, b, dij, nb, M->diag);
+    gen_tiles(ctx, gx, ginfo, N, d, kern->ell, kern->nugget, b, dij, nb, M->diag);
   }
   // Off-diagonal tiles, in batches of similar rank.  In KD order a tile's rank falls with its
   // distance from the diagonal, so the tiles are taken by diagonal offset i - j: a batch then
@@ -723,7 +727,7 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
     if (b % 8 == 0) {  // the tensor-core split products read 16-byte rows
       unsigned long long* tmax = bMax.need<unsigned long long>((size_t)nt);
       TLR_CUDA(cudaMemsetAsync(tmax, 0, sizeof(unsigned long long) * nt, ctx->stream));
-      gen_tiles(ctx, M->pts, N, d, kern->ell, kern->nugget, b, dij, nt, T, tmax);
+      gen_tiles(ctx, gx, ginfo, N, d, kern->ell, kern->nugget, b, dij, nt, T, tmax);
       OzTiles oz;
       oz.Sc = bSc.need<uint16_t>((size_t)nt * 8 * b * b);
       oz.Sr = bSr.need<uint16_t>((size_t)nt * 8 * b * b);
@@ -733,7 +737,7 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
       oz_split_tiles(ctx, nt, b, T, tmax, oz.Sc, oz.Sr, oz.e);
       ara_dense_run(ctx, nt, b, T, bs, eps, o->seed, STREAM_COMPRESS, 0, Q, B, q, as, &oz);
     } else {
-      gen_tiles(ctx, M->pts, N, d, kern->ell, kern->nugget, b, dij, nt, T);
+      gen_tiles(ctx, gx, ginfo, N, d, kern->ell, kern->nugget, b, dij, nt, T);
       ara_dense_run(ctx, nt, b, T, bs, eps, o->seed, STREAM_COMPRESS, 0, Q, B, q, as);
     }
     int64_t tot = 0;

@@ -156,6 +156,26 @@ def test_generated_tiles_match_oracle_entrywise(T, ctx, d, ell):
         assert np.all(np.abs(got - ref) / np.abs(ref) <= bound)
 
 
+@pytest.mark.parametrize("d,ell,shift,scale", [(1, 0.05, 0.0, 1.0), (2, 0.01, 0.0, 1.0), (3, 0.01, 0.0, 1.0),
+                                               (2, 0.3, 1000.0, 7.0), (3, 0.2, -3.5, 1e-3)])
+def test_generated_single_tile_all_distances(T, ctx, d, ell, shift, scale):
+    """One tile holding every pair of 512 points: arguments |x_i - x_j|/ell from 0 (duplicated points)
+    up to sqrt(d)/ell (173 at ell = 0.01 in 3D), and coordinates away from the unit box (shifted by
+    1000, or scaled by 1e-3), all within a few units of 2^-52 (1 + |log entry|) of the oracle."""
+    from oracle import kdtree
+    N = 512
+    x = inputs.points(N, d, 23) * scale + shift
+    x[5] = x[17]
+    x[300] = x[17]
+    A = ctx.compress(x, N, 1e-6, ell * scale, 1e-4, T.default_opts(bs=16, seed=3))
+    xo = x[kdtree.kd_order(x, N)]
+    got = A.tile(0, 0)[0]
+    ref = kernel.tile(xo, 0, 0, N, ell * scale, 1e-4)
+    assert ref.min() < 1e-30 or ell >= 0.05
+    bound = 4 * 2.0 ** -52 * (1.0 + np.abs(np.log(ref)))
+    assert np.all(np.abs(got - ref) / np.abs(ref) <= bound)
+
+
 def test_split_product_rejects_unaligned_size(T, ctx):
     Tn = np.eye(100)
     with pytest.raises(T.TLRError) as ei:
