@@ -60,6 +60,8 @@ struct GemmJob {
   int tiles_m, tiles_n, nsplit;
   int flags;     // GEMM_TRIL: write only C(m, n) with m >= n; skip tiles strictly above
                  // GEMM_ALOWER: op(A_0) is lower triangular (NN only): row m reads k <= m
+  int rule_n;    // columns the split-K rule assumes (0: N), so that a product formed for several
+                 // right-hand blocks at once sums every element as the one-block product does
   double alpha, beta;
 };
 enum { GEMM_TRIL = 1, GEMM_ALOWER = 2 };
@@ -312,6 +314,7 @@ struct OzJob {
   // last CTA of each output block (arrival counters).  nsplit = 0 lets oz_gemm choose from the
   // job's shape; the caller may fix it (1: no split).
   int nsplit = 0, tiles_n = 1;
+  int rule_n = 0;        // columns the split rule assumes (0: N), as for GemmJob
   double* ws = nullptr;
   int* ctr = nullptr;
 };

@@ -109,31 +109,45 @@ struct BatchSampler : Sampler {
   bool owns_omega() const override { return true; }
   bool mine(int op) const { return !member || (*member)[op]; }
 
-  void sample(const std::vector<int>& ops, int t, const double*, const std::vector<double*>& Ydst) override {
-    // matrices present in this call
-    std::vector<int> mp;
-    std::vector<int> slot_of_m(L->size(), -1);
-    for (int op : ops) {
-      const int m = (*op_m)[op];
-      if (slot_of_m[m] < 0) { slot_of_m[m] = (int)mp.size(); mp.push_back(m); }
-    }
-    // Omega_{m,k,t} per matrix (its own key) and the shared products X = Urow_k^T Omega, X0 = V0col_k^T Omega
-    std::vector<int64_t> omo(mp.size()), xo(mp.size()), x0o(mp.size());
-    int64_t omt = 0, xt = 0;
-    for (size_t u = 0; u < mp.size(); ++u) {
-      const Mat& M = *(*L)[mp[u]];
+  // X and X0 of one matrix for rounds [t0, t1): Kk x bs (t1 - t0) and R0k x bs (t1 - t0), round t's
+  // block at column bs (t - t0).  A column's tiles start their ARA at round 0 whenever they enter
+  // the batch, so the blocks serve every tile that reaches those rounds.
+  struct XRange {
+    int t0, t1;
+    T* X;
+    T* X0;
+    std::shared_ptr<Buf> buf;
+  };
+  std::vector<std::vector<XRange>> xr;  // per matrix of L
+
+  // Forms X = Urow_k^T [Omega_t0 .. Omega_t1-1] (and X0) for the matrices in `ms`, starting at round
+  // t: the first range covers the rounds the column's highest-rank tile is expected to need (its
+  // compressed rank / bs + 2), a later one half as many.  One Gaussian launch, one slicing and one
+  // product of width bs (t1 - t0) replace that many per-round launches; each product keeps the
+  // split-K of its one-round shape (rule_n = bs), so every element equals the one-round result.
+  void form_ranges(const std::vector<int>& ms, int t) {
+    std::vector<int> nr(ms.size());
+    std::vector<int64_t> omo(ms.size());
+    int64_t omt = 0;
+    for (size_t u = 0; u < ms.size(); ++u) {
+      const Mat& M = *(*L)[ms[u]];
+      int r0max = 0;
+      for (int i = M.k + 1; i < M.nb; ++i) r0max = std::max(r0max, M.A->rank[ix(M.A, i, M.k)]);
+      int n = (r0max + bs - 1) / bs + 2;
+      if (t > 0) n = std::max(2, n / 2);
+      const int64_t per = (int64_t)(std::max(M.Kk, 1) + std::max<int64_t>(M.R0k, 1)) * bs * (int64_t)sizeof(T);
+      n = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)n, 32, (int64_t)(32 << 20) / per}));
+      nr[u] = n;
       omo[u] = omt;
-      omt += (int64_t)M.b * bs;
-      xo[u] = xt;
-      xt += (int64_t)std::max(M.Kk, 1) * bs;
-      x0o[u] = xt;
-      xt += (int64_t)std::max<int64_t>(M.R0k, 1) * bs;
+      omt += (int64_t)M.b * bs * n;
     }
     double* Om = bom->need<double>((size_t)omt);
     std::vector<OmegaJob> oj;
-    for (size_t u = 0; u < mp.size(); ++u) {
-      const Mat& M = *(*L)[mp[u]];
-      oj.push_back(OmegaJob{Om + omo[u], M.o.seed, STREAM_FACTOR, (uint32_t)M.k, (uint32_t)t, M.b, bs});
+    for (size_t u = 0; u < ms.size(); ++u) {
+      const Mat& M = *(*L)[ms[u]];
+      for (int r = 0; r < nr[u]; ++r)
+        oj.push_back(OmegaJob{Om + omo[u] + (size_t)r * M.b * bs, M.o.seed, STREAM_FACTOR, (uint32_t)M.k,
+                              (uint32_t)(t + r), M.b, bs});
     }
     omega_batched(ctx, oj);
     const T* OmT = reinterpret_cast<const T*>(Om);
@@ -142,46 +156,84 @@ struct BatchSampler : Sampler {
       to_float(ctx, omt, Om, o32);
       OmT = reinterpret_cast<const T*>(o32);
     }
-    T* X = bx->need<T>((size_t)xt);
     std::vector<GemmJob<T>> jx;
     std::vector<OzColJob> ocj;
     std::vector<OzJob> oxj;
-    if (!F32) {  // slices of Omega for the matrices whose U panel products run split
-      int64_t ne = 0, nx = 0;
-      for (size_t u = 0; u < mp.size(); ++u) {
-        const Mat& M = *(*L)[mp[u]];
-        if (M.oz && (M.Kk > 0 || M.R0k > 0)) { ne += bs; nx += (int64_t)8 * M.b * bs; }
+    int64_t ne = 0, nx = 0;
+    if (!F32)
+      for (size_t u = 0; u < ms.size(); ++u) {
+        const Mat& M = *(*L)[ms[u]];
+        if (M.oz && (M.Kk > 0 || M.R0k > 0)) { ne += (int64_t)bs * nr[u]; nx += (int64_t)8 * M.b * bs * nr[u]; }
       }
-      uint16_t* os = bos->need<uint16_t>((size_t)std::max<int64_t>(nx, 1));
-      int* oe = boe->need<int>((size_t)std::max<int64_t>(ne, 1));
-      for (size_t u = 0; u < mp.size(); ++u) {
-        Mat& M = *(*L)[mp[u]];
-        if (!(M.oz && (M.Kk > 0 || M.R0k > 0))) continue;
-        ocj.push_back(OzColJob{Om + omo[u], os, oe, M.b, bs, 0, M.b});
+    uint16_t* os = bos->need<uint16_t>((size_t)std::max<int64_t>(nx, 1));
+    int* oe = boe->need<int>((size_t)std::max<int64_t>(ne, 1));
+    for (size_t u = 0; u < ms.size(); ++u) {
+      Mat& M = *(*L)[ms[u]];
+      const int n = nr[u], w = bs * n, kk = std::max(M.Kk, 1), r0k = (int)std::max<int64_t>(M.R0k, 1);
+      XRange rg;
+      rg.t0 = t;
+      rg.t1 = t + n;
+      rg.buf = std::make_shared<Buf>(ctx);
+      rg.X = rg.buf->template need<T>((size_t)(kk + r0k) * w);
+      rg.X0 = rg.X + (size_t)kk * w;
+      if (!F32 && M.oz && (M.Kk > 0 || M.R0k > 0)) {
+        ocj.push_back(OzColJob{Om + omo[u], os, oe, M.b, w, 0, M.b});
         // X = Urow_k^T Omega: rows of A^T are the panel's columns (k along the b rows)
-        if (M.Kk > 0)
-          oxj.push_back(OzJob{M.FUs[M.k], os, d_one, oe, reinterpret_cast<double*>(X + xo[u]),
-                              (size_t)M.b * M.fuscap[M.k], (size_t)M.b * bs, M.b, M.Kk, M.Kk, bs, M.b});
+        if (M.Kk > 0) {
+          oxj.push_back(OzJob{M.FUs[M.k], os, d_one, oe, reinterpret_cast<double*>(rg.X),
+                              (size_t)M.b * M.fuscap[M.k], (size_t)M.b * w, M.b, M.Kk, M.Kk, w, M.b});
+          oxj.back().rule_n = bs;
+        }
         // X0 = V0col_k^T Omega with the slices of the compressed input's V panel
-        if (M.R0k > 0)
-          oxj.push_back(OzJob{M.AVs[M.k], os, M.dAVe + M.k, oe, reinterpret_cast<double*>(X + x0o[u]),
-                              (size_t)M.b * M.R0k, (size_t)M.b * bs, M.b, (int)M.R0k, (int)M.R0k, bs, M.b});
-        os += (size_t)8 * M.b * bs;
-        oe += bs;
+        if (M.R0k > 0) {
+          oxj.push_back(OzJob{M.AVs[M.k], os, M.dAVe + M.k, oe, reinterpret_cast<double*>(rg.X0),
+                              (size_t)M.b * M.R0k, (size_t)M.b * w, M.b, (int)M.R0k, (int)M.R0k, w, M.b});
+          oxj.back().rule_n = bs;
+        }
+        os += (size_t)8 * M.b * w;
+        oe += w;
+      } else {
+        if (M.Kk > 0) {
+          jx.push_back(job<T>(TN, M.Kk, w, Panels<T>::U(M, M.k), M.b, OmT + omo[u], M.b, M.b, rg.X, M.Kk, 1.0, 0.0));
+          jx.back().rule_n = bs;
+        }
+        if (M.R0k > 0) {
+          jx.push_back(job<T>(TN, (int)M.R0k, w, Panels<T>::AV(M, M.k), M.b, OmT + omo[u], M.b, M.b, rg.X0,
+                              (int)M.R0k, 1.0, 0.0));
+          jx.back().rule_n = bs;
+        }
       }
-    }
-    for (size_t u = 0; u < mp.size(); ++u) {
-      Mat& M = *(*L)[mp[u]];
-      if (M.Kk > 0 && !(!F32 && M.oz))
-        jx.push_back(job<T>(TN, M.Kk, bs, Panels<T>::U(M, M.k), M.b, OmT + omo[u], M.b, M.b, X + xo[u], M.Kk, 1.0, 0.0));
-      if (M.R0k > 0 && !(!F32 && M.oz))
-        jx.push_back(job<T>(TN, (int)M.R0k, bs, Panels<T>::AV(M, M.k), M.b, OmT + omo[u], M.b, M.b, X + x0o[u],
-                            (int)M.R0k, 1.0, 0.0));
-      (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * bs * (M.Kk + M.R0k);
+      (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * w * (M.Kk + M.R0k);
+      xr[ms[u]].push_back(std::move(rg));
     }
     gemm<T>(ctx, TN, jx);
     oz_split_cols(ctx, ocj);
     oz_gemm(ctx, oxj);
+  }
+
+  void sample(const std::vector<int>& ops, int t, const double*, const std::vector<double*>& Ydst) override {
+    // matrices present in this call
+    std::vector<int> mp;
+    std::vector<int> slot_of_m(L->size(), -1);
+    for (int op : ops) {
+      const int m = (*op_m)[op];
+      if (slot_of_m[m] < 0) { slot_of_m[m] = (int)mp.size(); mp.push_back(m); }
+    }
+    // the shared products X = Urow_k^T Omega_t and X0 = V0col_k^T Omega_t of each matrix, formed for a
+    // range of rounds at once
+    if (xr.size() < L->size()) xr.resize(L->size());
+    std::vector<const XRange*> rng(mp.size(), nullptr);
+    std::vector<int> need;
+    for (size_t u = 0; u < mp.size(); ++u) {
+      for (const auto& r : xr[mp[u]])
+        if (t >= r.t0 && t < r.t1) rng[u] = &r;
+      if (!rng[u]) need.push_back(mp[u]);
+    }
+    if (!need.empty()) {
+      form_ranges(need, t);
+      for (size_t u = 0; u < mp.size(); ++u)
+        if (!rng[u]) rng[u] = &xr[mp[u]].back();
+    }
     // W blocks of every operand (block-diagonal Gram products), then Y = [U0 | Urow] W
     std::vector<SlotDescT<T>> sd(ops.size());
     int64_t wtot = 0, ytot = 0;
@@ -195,10 +247,10 @@ struct BatchSampler : Sampler {
       d.goff = M.dgoff;
       d.gld = M.dgld;
       d.G = Panels<T>::G(M);
-      d.X = X + xo[u];
-      d.X0 = X + x0o[u];
       d.ldx = std::max(M.Kk, 1);
       d.ldx0 = (int)std::max<int64_t>(M.R0k, 1);
+      d.X = rng[u]->X + (size_t)d.ldx * bs * (t - rng[u]->t0);
+      d.X0 = rng[u]->X0 + (size_t)d.ldx0 * bs * (t - rng[u]->t0);
       d.nb = M.nb;
       d.k = M.k;
       d.i = i;

@@ -281,11 +281,12 @@ void gemm(tlr_ctx* ctx, GemmMode mode, std::vector<GemmJob<T>>& jobs_in) {
     j.tiles_m = (j.M + TM - 1) / TM;
     j.tiles_n = (j.N + TN_ - 1) / TN_;
     // warps with work per tile row (columns per warp; FP64 tiles short in M: rows per warp)
+    const int Nr = j.rule_n > 0 ? j.rule_n : j.N;
     int64_t wpr;
     if (RM == 2 && j.M < TM) {
-      wpr = (int64_t)((j.M + 7) / 8) * j.tiles_n;
+      wpr = (int64_t)((j.M + 7) / 8) * ((Nr + TN_ - 1) / TN_);
     } else {
-      const int full = j.N / TN_, rem = j.N % TN_;
+      const int full = Nr / TN_, rem = Nr % TN_;
       wpr = (int64_t)full * 4 + (rem + 2 * RN - 1) / (2 * RN);
     }
     const int chunks = (j.K[0] + GEMM_TK - 1) / GEMM_TK + (j.K[1] > 0 ? (j.K[1] + GEMM_TK - 1) / GEMM_TK : 0);

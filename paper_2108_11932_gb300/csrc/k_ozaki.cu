@@ -416,7 +416,8 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
     const int tm = (j.M + OZ_TM - 1) / OZ_TM;
     j.tiles_n = (j.N + OZ_TN - 1) / OZ_TN;
     const int nch = (j.K + OZ_KC - 1) / OZ_KC;
-    const int64_t want = ((int64_t)std::max(ctx->sm_count, 1) + (int64_t)tm * j.tiles_n - 1) / ((int64_t)tm * j.tiles_n);
+    const int tnr = j.rule_n > 0 ? (j.rule_n + OZ_TN - 1) / OZ_TN : j.tiles_n;
+    const int64_t want = ((int64_t)std::max(ctx->sm_count, 1) + (int64_t)tm * tnr - 1) / ((int64_t)tm * tnr);
     if (j.nsplit <= 0) j.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, nch / 8, 64}));
     mx = std::max(mx, j.M);
     ny = std::max(ny, j.tiles_n * j.nsplit);
