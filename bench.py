@@ -418,8 +418,8 @@ def run_batch(args):
     def build(specs):
         mats, eps, opts = [], [], []
         for sp in specs:
-            b = autotune.choose(tuned["table"], sp["N"], sp["d"])
-            o = T.default_opts(bs=16, seed=sp["seed"])
+            b, bs, width = autotune.choose(tuned["table"], sp["N"], sp["d"])
+            o = T.default_opts(bs=bs, seed=sp["seed"], max_slots=width)
             mats.append(ctx.compress(inputs.points(sp["N"], sp["d"], sp["seed"]), b, sp["eps"], sp["ell"], 1e-4, o))
             eps.append(sp["eps"])
             opts.append(o)
@@ -442,14 +442,15 @@ def run_batch(args):
     secs = e0.elapsed_time(e1) / 1e3
     fl = sum(m.info()["flops_exec"] for m, s_ in zip(mats, st) if s_ == 0)
     bs_used = {}
-    for m in mats:
-        bs_used[m.info()["b"]] = bs_used.get(m.info()["b"], 0) + 1
+    for m, o in zip(mats, opts):
+        key = f"b{m.info()['b']}_bs{o.bs}_w{o.max_slots}"
+        bs_used[key] = bs_used.get(key, 0) + 1
     out = {"workload": f"batch{len(specs)}: {len(specs)} independent covariance matrices, N=256*U{{8..64}}, d in {{2,3}}, "
-                       "ell~U[0.05,0.3], nugget 1e-4, eps 1e-6, FP64; tile size from the autotuner",
+                       "ell~U[0.05,0.3], nugget 1e-4, eps 1e-6, FP64; (b, bs, batch width) from the autotuner",
            "matrices": len(specs), "ok": sum(1 for s_ in st if s_ == 0), "factor_s": secs,
            "matrices_per_s": len(specs) / secs, "tflops_exec": fl / secs / 1e12, "launches": ctx.launches() - l0,
-           "construction_s": t_build, "autotune_s": t_tune, "tile_sizes": bs_used,
-           "autotune_table": {f"d{k[0]}_N2^{k[1]}": v for k, v in tuned["table"].items()}}
+           "construction_s": t_build, "autotune_s": t_tune, "configs_used": bs_used,
+           "autotune_table": {f"d{k[0]}_N2^{k[1]}": list(v) for k, v in tuned["table"].items()}}
     print(json.dumps(out), flush=True)
 
 

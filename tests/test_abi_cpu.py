@@ -60,3 +60,13 @@ def test_null_arguments_are_rejected_without_gpu(lib):
 def test_kd_order_bit_exact_vs_oracle(lib, N, d, b, seed):
     x = inputs.points(N, d, seed)
     assert np.array_equal(lib.kd_order(x, b), kdtree.kd_order(x, b))
+
+
+def test_autotune_choose_takes_the_nearest_class_of_the_same_dimension():
+    from paper_2108_11932_gb300 import autotune
+    table = {(2, 11): (128, 16, 0), (2, 14): (256, 32, 16), (3, 12): (256, 16, 0)}
+    assert autotune.choose(table, 2048, 2) == (128, 16, 0)
+    assert autotune.choose(table, 3000, 2) == (128, 16, 0)     # bucket 12: 11 and 14 -> nearer 11
+    assert autotune.choose(table, 12000, 2) == (256, 32, 16)   # bucket 14
+    assert autotune.choose(table, 65536, 3) == (256, 16, 0)
+    assert autotune.choose(table, 4096, 1) == autotune.DEFAULT  # no class of that dimension

@@ -529,3 +529,17 @@ def test_session_join_mid_flight_is_bitwise_identical(T, ctx):
         a, g = alone[m].tile(nb - 1, 0), mats[m].tile(nb - 1, 0)
         assert np.array_equal(a[0], g[0]) and np.array_equal(a[1], g[1])
     S.close()
+
+
+def test_autotune_picks_a_measured_configuration(T, ctx):
+    """The tuner times every configuration it may pick and returns the fastest of its coordinate search."""
+    from paper_2108_11932_gb300 import autotune
+    res = autotune.tune(ctx, dims=(2,), sizes=(2048,), candidates=(128, 256), bs_candidates=(16, 32),
+                        width_candidates=(0, 8), repeats=1)
+    b, bs, width = res["table"][(2, 11)]
+    tm = res["timings"]
+    assert (2, 2048, b, bs, width) in tm
+    # each coordinate is the fastest measured along its line
+    assert tm[(2, 2048, b, 16, 0)] == min(tm[(2, 2048, v, 16, 0)] for v in (128, 256))
+    assert tm[(2, 2048, b, bs, 0)] == min(tm[(2, 2048, b, v, 0)] for v in (16, 32))
+    assert tm[(2, 2048, b, bs, width)] == min(tm[(2, 2048, b, bs, v)] for v in (0, 8))
