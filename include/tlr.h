@@ -162,7 +162,14 @@ tlr_status tlr_session_poll(tlr_session* s, int ticket, int* finished, tlr_statu
 
 /* Solve (L L^T) X = B or (L D L^T) X = B with the TLR triangular solve of
  * Algorithm 7 (forward) and its transpose (backward).  B: device, N x nrhs,
- * leading dimension ldb >= N, original point order; overwritten with X. */
+ * leading dimension ldb >= N, original point order; overwritten with X.
+ * The factor keeps a solve plan per group width (right-hand sides are taken in
+ * groups of at most 32; up to 4 widths are kept): two N x width work arrays and
+ * the job tables, allocated on the first solve of that width and freed with the
+ * factor.  The first solve of a width runs the plan's launches directly; the
+ * next captures them once as a CUDA graph, which later solves replay (same
+ * kernels, bitwise the same results).  Solves with one factor must not run
+ * concurrently (they share the plan's work arrays). */
 tlr_status tlr_solve(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* B, int64_t ldb);
 
 /* log|det| of the factored matrix: 2 sum log diag(L_kk) (Cholesky) or

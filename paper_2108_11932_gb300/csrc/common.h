@@ -71,6 +71,10 @@ constexpr int GEMM_TK = 16;
 
 }  // namespace tlr
 
+namespace tlr {
+struct SolvePlan;
+}
+
 // ----------------------------------------------------------------------------------------
 // Library-owned objects.
 struct tlr_ctx {
@@ -79,6 +83,7 @@ struct tlr_ctx {
   cudaStream_t main = nullptr;    // caller's stream
   cudaStream_t side = nullptr;    // library stream for work overlapped with the main stream
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaStream_t capture = nullptr;  // library stream on which solve graphs are captured
   tlr_alloc_fn alloc = nullptr;
   tlr_free_fn free_fn = nullptr;
   void* user = nullptr;
@@ -159,6 +164,8 @@ struct tlr_mat {
   double flops_exec = 0, flops_model = 0, ara_rounds = 0, seconds = 0;
   double tiles_fp32 = 0, tiles_fp64 = 0;  // tile-rounds sampled in each precision (mixed mode)
   double flops_fp32 = 0;                  // FP32 flops of the mixed-precision chains
+  // solve plans of a factor (buffers, job tables, captured graph), one per nrhs, most recent last
+  std::vector<tlr::SolvePlan*> plans;
 };
 
 namespace tlr {
@@ -372,6 +379,22 @@ struct CopyJob {
   int64_t n;
 };
 void batched_copy(tlr_ctx* ctx, std::vector<CopyJob>& jobs);
+// Skinny products of the triangular solves (k_solve.cu): C = alpha op(A) B + beta C with nrhs
+// columns, op(A) = A (tn = 0, A M x K) or A^T (tn = 1, A K x M), all column-major; lower: A is a
+// lower-triangular block (its zero half is skipped).  Job tables are device-resident.
+struct SkJob {
+  const double* A;
+  const double* B;
+  double* C;
+  int lda, ldb, ldc, M, K, lower;
+  double alpha, beta;
+};
+// work items of a launch: one CTA each (job, first row, log2 of the k-slots of an NN product)
+struct SkItem {
+  int job, m0, cfg;
+};
+void sk_items(int tn, const std::vector<SkJob>& jobs, int job0, std::vector<SkItem>& items);
+void sk_gemm(tlr_ctx* ctx, int tn, const SkJob* jobs, const SkItem* items, int nitems, int nrhs);
 struct ConvJob {
   const double* src;
   float* dst;

@@ -96,6 +96,7 @@ inline int64_t ix(const tlr_mat* M, int i, int j) { return (int64_t)i * M->nb + 
 inline double* Uptr(const tlr_mat* M, int i, int j) { return M->Urow[i] + (size_t)M->b * M->uoff[ix(M, i, j)]; }
 inline double* Vptr(const tlr_mat* M, int i, int j) { return M->Vcol[j] + (size_t)M->b * M->voff[ix(M, i, j)]; }
 void mat_free_storage(tlr_ctx* ctx, tlr_mat* M);
+void mat_drop_plans(tlr_ctx* ctx, tlr_mat* M);  // solve plans (and their graphs) of M
 void mat_destroy(tlr_ctx* ctx, tlr_mat* M);
 tlr_mat* mat_new(int64_t N, int d, int b);
 void ensure_ucap(tlr_ctx* ctx, tlr_mat* F, int i, int64_t extra);

@@ -620,6 +620,7 @@ void ara_dense_run(tlr_ctx* ctx, int nops, int n, const double* T, int bs, doubl
 namespace tlr {
 
 void mat_free_storage(tlr_ctx* ctx, tlr_mat* M) {
+  mat_drop_plans(ctx, M);  // the plans point into the storage
   for (double* p : M->Urow) dfree(ctx, p);
   for (double* p : M->Vcol) dfree(ctx, p);
   M->Urow.assign(M->nb, nullptr);
@@ -800,57 +801,184 @@ void ensure_ucap(tlr_ctx* ctx, tlr_mat* F, int i, int64_t extra) {
   F->ucap[i] = cap;
 }
 }  // namespace tlr
+namespace tlr {
 
-// ======================================================================== solve / products
-// Z = L^{-1} X (Algorithm 7): Z_k = L_kk^{-1} X_k, then X_i -= U_ik (V_ik^T Z_k) for i > k.
-// X (nb*b x nrhs, KD order, padded) is consumed.
-static void tri_forward(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* X, double* Z, int64_t ld, Buf& tmp) {
-  const int nb = F->nb, b = F->b;
-  for (int k = 0; k < nb; ++k) {
-    double* Zk = Z + (size_t)k * b;
-    std::vector<GemmJob<double>> j0{job<double>(NN, b, nrhs, F->dinv + (size_t)k * b * b, b, X + (size_t)k * b, (int)ld,
-                                                b, Zk, (int)ld, 1.0, 0.0)};
-    gemm<double>(ctx, NN, j0);
-    const int64_t Rk = F->vlen[k];
-    if (Rk == 0) continue;
-    double* T = tmp.need<double>((size_t)Rk * nrhs);
-    std::vector<GemmJob<double>> j1{job<double>(TN, (int)Rk, nrhs, F->Vcol[k], b, Zk, (int)ld, b, T, (int)Rk, 1.0, 0.0)};
-    gemm<double>(ctx, TN, j1);
-    std::vector<GemmJob<double>> j2;
-    for (int i = k + 1; i < nb; ++i) {
-      const int r = F->rank[ix(F, i, k)];
-      if (r == 0) continue;
-      j2.push_back(job<double>(NN, b, nrhs, Uptr(F, i, k), b, T + F->voff[ix(F, i, k)], (int)Rk, r,
-                               X + (size_t)i * b, (int)ld, -1.0, 1.0));
-    }
-    gemm<double>(ctx, NN, j2);
+// Solve plans.  For a factor and a number of right-hand sides the sequence of the two triangular
+// solves is fixed: per block column k (Algorithm 7) Z_k = L_kk^-1 X_k, T = Vcol_k^T Z_k,
+// X_i -= U_ik T_ik (i > k); then (LDL^T) Z = D^-1 Z; then, for k descending, S_ik = U_ik^T X_i,
+// Z_k -= Vcol_k S, X_k = L_kk^-T Z_k.  A plan holds the buffers and the device job tables of that
+// sequence (built once), runs it directly the first time, and on later solves with the same nrhs
+// replays it as a CUDA graph captured once (~6 nb launches become one graph launch).
+struct SolvePlan {
+  int nrhs = 0;
+  int64_t np = 0;
+  double *X = nullptr, *Z = nullptr, *T = nullptr;
+  SkJob* djobs = nullptr;
+  SkItem* ditems = nullptr;
+  struct Step { int kind, off, n; };  // kind 0 NN, 1 TN, 2 D^-1 scaling; items [off, off + n)
+  std::vector<Step> steps;
+  cudaGraphExec_t exec = nullptr;
+  int64_t graph_launches = 0;
+  int runs = 0;
+};
+
+static void plan_destroy(tlr_ctx* ctx, SolvePlan* P) {
+  if (!P) return;
+  if (P->exec) {
+    cudaStreamSynchronize(ctx->main);  // no replay of the graph still in flight
+    cudaGraphExecDestroy(P->exec);
   }
+  dfree(ctx, P->X);
+  dfree(ctx, P->Z);
+  dfree(ctx, P->T);
+  dfree(ctx, P->djobs);
+  dfree(ctx, P->ditems);
+  delete P;
 }
 
-// X = L^{-T} Z (transpose of Algorithm 7): Z_k -= sum_{i>k} V_ik (U_ik^T X_i); X_k = L_kk^{-T} Z_k.
-static void tri_backward(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* Z, double* X, int64_t ld, Buf& tmp) {
+void mat_drop_plans(tlr_ctx* ctx, tlr_mat* M) {
+  for (SolvePlan* P : M->plans) plan_destroy(ctx, P);
+  M->plans.clear();
+}
+
+static SolvePlan* plan_build(tlr_ctx* ctx, const tlr_mat* F, int nrhs) {
   const int nb = F->nb, b = F->b;
-  for (int k = nb - 1; k >= 0; --k) {
-    double* Zk = Z + (size_t)k * b;
-    const int64_t Rk = F->vlen[k];
-    if (Rk > 0) {
-      double* S = tmp.need<double>((size_t)Rk * nrhs);
-      std::vector<GemmJob<double>> j1;
+  auto* P = new SolvePlan();
+  P->nrhs = nrhs;
+  P->np = (int64_t)nb * b;
+  const int64_t np = P->np;
+  int64_t rmax = 1;
+  for (int k = 0; k < nb; ++k) rmax = std::max<int64_t>(rmax, F->vlen[k]);
+  try {
+    P->X = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)np * nrhs));
+    P->Z = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)np * nrhs));
+    P->T = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)rmax * nrhs));
+    std::vector<SkJob> jobs;
+    std::vector<SkItem> items;
+    auto step = [&](int kind, const std::vector<SkJob>& js) {
+      if (js.empty()) return;
+      const int i0 = (int)items.size();
+      sk_items(kind, js, (int)jobs.size(), items);
+      P->steps.push_back({kind, i0, (int)items.size() - i0});
+      jobs.insert(jobs.end(), js.begin(), js.end());
+    };
+    double *X = P->X, *Z = P->Z, *T = P->T;
+    const int ld = (int)np;
+    for (int k = 0; k < nb; ++k) {  // forward: L Z = X
+      double* Zk = Z + (size_t)k * b;
+      step(0, {SkJob{F->dinv + (size_t)k * b * b, X + (size_t)k * b, Zk, b, ld, ld, b, b, 1, 1.0, 0.0}});
+      const int Rk = (int)F->vlen[k];
+      if (Rk == 0) continue;
+      step(1, {SkJob{F->Vcol[k], Zk, T, b, ld, Rk, Rk, b, 0, 1.0, 0.0}});
+      std::vector<SkJob> upd;
       for (int i = k + 1; i < nb; ++i) {
         const int r = F->rank[ix(F, i, k)];
-        if (r == 0) continue;
-        j1.push_back(job<double>(TN, r, nrhs, Uptr(F, i, k), b, X + (size_t)i * b, (int)ld, b,
-                                 S + F->voff[ix(F, i, k)], (int)Rk, 1.0, 0.0));
+        if (r > 0) upd.push_back(SkJob{Uptr(F, i, k), T + F->voff[ix(F, i, k)], X + (size_t)i * b, b, Rk, ld, b, r, 0,
+                                       -1.0, 1.0});
       }
-      gemm<double>(ctx, TN, j1);
-      std::vector<GemmJob<double>> j2{job<double>(NN, b, nrhs, F->Vcol[k], b, S, (int)Rk, (int)Rk, Zk, (int)ld, -1.0, 1.0)};
-      gemm<double>(ctx, NN, j2);
+      step(0, upd);
     }
-    std::vector<GemmJob<double>> j3{job<double>(TN, b, nrhs, F->dinv + (size_t)k * b * b, b, Zk, (int)ld, b,
-                                                X + (size_t)k * b, (int)ld, 1.0, 0.0)};
-    gemm<double>(ctx, TN, j3);
+    if (F->state == 2) P->steps.push_back({2, 0, 0});
+    for (int k = nb - 1; k >= 0; --k) {  // backward: L^T X = Z
+      double* Zk = Z + (size_t)k * b;
+      const int Rk = (int)F->vlen[k];
+      if (Rk > 0) {
+        std::vector<SkJob> prj;
+        for (int i = k + 1; i < nb; ++i) {
+          const int r = F->rank[ix(F, i, k)];
+          if (r > 0) prj.push_back(SkJob{Uptr(F, i, k), X + (size_t)i * b, T + F->voff[ix(F, i, k)], b, ld, Rk, r, b, 0,
+                                         1.0, 0.0});
+        }
+        step(1, prj);
+        step(0, {SkJob{F->Vcol[k], T, Zk, b, Rk, ld, b, Rk, 0, -1.0, 1.0}});
+      }
+      step(1, {SkJob{F->dinv + (size_t)k * b * b, Zk, X + (size_t)k * b, b, ld, ld, b, b, 1, 1.0, 0.0}});
+    }
+    P->djobs = static_cast<SkJob*>(dalloc(ctx, sizeof(SkJob) * std::max<size_t>(jobs.size(), 1)));
+    P->ditems = static_cast<SkItem*>(dalloc(ctx, sizeof(SkItem) * std::max<size_t>(items.size(), 1)));
+    // through the pinned upload ring (no host synchronization), then into the plan's own arrays
+    auto put = [&](void* dst, const void* src, size_t bytes) {
+      const size_t chunk = (size_t)16 << 20;
+      for (size_t o = 0; o < bytes; o += chunk) {
+        const size_t n = std::min(chunk, bytes - o);
+        const void* d = upload(ctx, static_cast<const char*>(src) + o, n);
+        TLR_CUDA(cudaMemcpyAsync(static_cast<char*>(dst) + o, d, n, cudaMemcpyDeviceToDevice, ctx->stream));
+      }
+    };
+    put(P->djobs, jobs.data(), sizeof(SkJob) * jobs.size());
+    put(P->ditems, items.data(), sizeof(SkItem) * items.size());
+  } catch (...) {
+    plan_destroy(ctx, P);
+    throw;
+  }
+  return P;
+}
+
+static void plan_run(tlr_ctx* ctx, const tlr_mat* F, const SolvePlan* P) {
+  for (const auto& s : P->steps) {
+    if (s.kind == 2)
+      scale_rows(ctx, (int)P->np, P->nrhs, F->dvec, 1, P->Z, (int)P->np, P->Z, (int)P->np);
+    else
+      sk_gemm(ctx, s.kind, P->djobs, P->ditems + s.off, s.n, P->nrhs);
   }
 }
+
+// Runs the plan on ctx->stream: directly the first time, as a captured graph afterwards.
+static void plan_exec(tlr_ctx* ctx, const tlr_mat* F, SolvePlan* P) {
+  if (P->runs++ == 0) {
+    plan_run(ctx, F, P);
+    return;
+  }
+  if (!P->exec) {
+    if (!ctx->capture) TLR_CUDA(cudaStreamCreateWithFlags(&ctx->capture, cudaStreamNonBlocking));
+    cudaStream_t saved = ctx->stream;
+    const int prof = ctx->prof;
+    const int64_t l0 = ctx->launches;
+    ctx->stream = ctx->capture;
+    ctx->prof = 0;  // no profiling events inside the graph
+    cudaGraph_t g = nullptr;
+    TLR_CUDA(cudaStreamBeginCapture(ctx->capture, cudaStreamCaptureModeThreadLocal));
+    try {
+      plan_run(ctx, F, P);
+    } catch (...) {
+      cudaStreamEndCapture(ctx->capture, &g);
+      if (g) cudaGraphDestroy(g);
+      ctx->stream = saved;
+      ctx->prof = prof;
+      throw;
+    }
+    ctx->stream = saved;
+    ctx->prof = prof;
+    P->graph_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    TLR_CUDA(cudaStreamEndCapture(ctx->capture, &g));
+    const cudaError_t e = cudaGraphInstantiate(&P->exec, g, 0);
+    cudaGraphDestroy(g);
+    TLR_CUDA(e);
+  }
+  TLR_CUDA(cudaGraphLaunch(P->exec, ctx->stream));
+  ctx->launches += P->graph_launches;
+}
+
+static SolvePlan* plan_for(tlr_ctx* ctx, tlr_mat* F, int nrhs) {
+  for (size_t u = 0; u < F->plans.size(); ++u)
+    if (F->plans[u]->nrhs == nrhs) {
+      SolvePlan* P = F->plans[u];
+      F->plans.erase(F->plans.begin() + u);
+      F->plans.push_back(P);  // most recently used last
+      return P;
+    }
+  constexpr size_t MAX_PLANS = 4;
+  if (F->plans.size() >= MAX_PLANS) {
+    plan_destroy(ctx, F->plans.front());
+    F->plans.erase(F->plans.begin());
+  }
+  SolvePlan* P = plan_build(ctx, F, nrhs);
+  F->plans.push_back(P);
+  return P;
+}
+
+}  // namespace tlr
 
 // Y = L X or Y = L^T X (KD order, padded); Y must not alias X.
 static void tri_mul(tlr_ctx* ctx, const tlr_mat* F, int trans, int nrhs, const double* X, int64_t ldx, double* Y,
@@ -1026,6 +1154,7 @@ tlr_status tlr_destroy(tlr_ctx* ctx) {
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->hstatus) cudaFreeHost(ctx->hstatus);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->capture) cudaStreamDestroy(ctx->capture);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (auto e : ctx->ev) cudaEventDestroy(e);
@@ -1094,6 +1223,7 @@ tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* S, tlr_mat** D) {
   if (!ctx || !S || !D) return TLR_ERR_ARG;
   ABI_BEGIN
   tlr_mat* M = new tlr_mat(*S);
+  M->plans.clear();  // plans belong to the source
   const int nb = S->nb, b = S->b;
   auto dup = [&](const double* src, size_t n) -> double* {
     if (!src) return nullptr;
@@ -1169,16 +1299,16 @@ tlr_status tlr_solve(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* B, int64_
   if (F->state != 1 && F->state != 2) return TLR_ERR_STATE;
   if (nrhs == 0) return TLR_OK;
   ABI_BEGIN
-  const int64_t np = (int64_t)F->nb * F->b;
-  Buf bX(ctx), bZ(ctx), bT(ctx);
-  double* X = bX.need<double>((size_t)np * nrhs);
-  double* Z = bZ.need<double>((size_t)np * nrhs);
-  const int64_t* perm = F->dperm;
-  permute_rows(ctx, F->N, nrhs, perm, 1, B, ldb, X, np, np);
-  tri_forward(ctx, F, nrhs, X, Z, np, bT);
-  if (F->state == 2) scale_rows(ctx, (int)np, nrhs, F->dvec, 1, Z, (int)np, Z, (int)np);
-  tri_backward(ctx, F, nrhs, Z, X, np, bT);
-  permute_rows(ctx, F->N, nrhs, perm, 0, X, np, B, ldb, np);
+  // right-hand sides in groups of at most 32 (one plan each)
+  tlr_mat* Fm = const_cast<tlr_mat*>(F);  // the plan cache is not part of the factor's value
+  for (int c0 = 0; c0 < nrhs; c0 += 32) {
+    const int nc = std::min(32, nrhs - c0);
+    double* Bc = B + (size_t)c0 * ldb;
+    SolvePlan* P = plan_for(ctx, Fm, nc);
+    permute_rows(ctx, F->N, nc, F->dperm, 1, Bc, ldb, P->X, P->np, P->np);
+    plan_exec(ctx, F, P);
+    permute_rows(ctx, F->N, nc, F->dperm, 0, P->X, P->np, Bc, ldb, P->np);
+  }
   return TLR_OK;
   ABI_END
 }

@@ -269,6 +269,31 @@ def test_factor_matches_oracle_ara(case, ldl):
         assert rel(F.matvec(Zt, op).cpu().numpy(), tlr.matvec(Fo, Z, name)) < 1e-10
 
 
+@pytest.mark.parametrize("ldl", [False, True])
+def test_repeated_solves_replay_a_captured_graph(case, ldl):
+    """A factor's solves with one nrhs: the first runs the plan's launches directly, the second captures
+    them as a CUDA graph and replays it, later ones replay; every result matches the oracle's solve
+    and the direct and replayed runs agree bitwise.  nrhs = 40 runs as groups of 32 and 8."""
+    import paper_2108_11932_gb300 as TT
+    w = case["w"]
+    F = case["A"].copy()
+    (F.ldlt if ldl else F.potrf)(w["eps"], case["o"])
+    Fo = tlr.factor(case["Ao"], w["eps"], ldl=ldl, compressor="ara", bs=w["bs"], seed=7)
+    for nrhs in (1, 3, 40):
+        Y = inputs.rhs(w["N"], nrhs, 20 + nrhs)
+        ref = tlr.solve(Fo, Y)
+        outs = []
+        for rep in range(3):
+            Yt = _t(TT, Y)
+            l0 = F.ctx.launches()
+            F.solve(Yt)
+            assert F.ctx.launches() > l0  # replays count the graph's kernels
+            outs.append(Yt.cpu().numpy())
+            assert rel(outs[-1], ref) < 1e-9, (nrhs, rep)
+        assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
+    F.free()
+
+
 def test_tlr_product_of_A(case):
     import paper_2108_11932_gb300 as TT
     w = case["w"]
