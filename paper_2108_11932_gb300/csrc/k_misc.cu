@@ -236,7 +236,7 @@ constexpr int GT_COLS = 16, GT_THREADS = 256;
 template <int D>
 __global__ void __launch_bounds__(GT_THREADS) k_gen_tiles(const long long* __restrict__ X,
                                                           const GridInfo* __restrict__ gi, int64_t N, uint64_t Cm,
-                                                          int ec, double nugget, int b, const int* __restrict__ ij,
+                                                          int ec, double one_nug, int b, const int* __restrict__ ij,
                                                           double* __restrict__ out,
                                                           unsigned long long* __restrict__ tmax) {
   __shared__ uint64_t tab[64];
@@ -271,8 +271,7 @@ __global__ void __launch_bounds__(GT_THREADS) k_gen_tiles(const long long* __res
           lo += l;
           hi += __umul64hi(a, a) + (lo < l ? 1ull : 0ull);
         }
-        v = fx::entry(hi, lo, ezb, Cm, tab);
-        if (g_i == g_j) v += nugget;
+        v = g_i == g_j ? one_nug : fx::entry(hi, lo, ezb, Cm, tab);  // exp(0) + nugget on the diagonal
       } else {
         v = (g_i == g_j) ? 1.0 : 0.0;  // identity padding of a ragged last tile
       }
@@ -301,11 +300,11 @@ void gen_tiles(tlr_ctx* ctx, const long long* X, const GridInfo* gi, int64_t N, 
   dim3 grid(cdiv(b, GT_COLS), (unsigned)ntiles);
   TLR_SITE_PRE(ctx);
   if (d == 1)
-    k_gen_tiles<1><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, nugget, b, tile_ij, out, tmax);
+    k_gen_tiles<1><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, 1.0 + nugget, b, tile_ij, out, tmax);
   else if (d == 2)
-    k_gen_tiles<2><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, nugget, b, tile_ij, out, tmax);
+    k_gen_tiles<2><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, 1.0 + nugget, b, tile_ij, out, tmax);
   else
-    k_gen_tiles<3><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, nugget, b, tile_ij, out, tmax);
+    k_gen_tiles<3><<<grid, GT_THREADS, 0, ctx->stream>>>(X, gi, N, Cm, ec, 1.0 + nugget, b, tile_ij, out, tmax);
   TLR_LAUNCH_CHECK(ctx);
 }
 

@@ -26,7 +26,7 @@ __device__ __forceinline__ void sk_store(const SkJob& J, int m, int n, double v)
 // C = alpha A B + beta C, A column-major (M x K).  One CTA per work item (job, first row m0, 2^ks_log2
 // k-slots): 256 / KS rows x KS k-slots, thread (row, slot) sums k = slot, slot + KS, ...; the slot sums
 // of an output are added in slot order.  Items are made per job from its K (at most 8 steps per slot
-// up to 32 slots), so short and long products alike fill a launch.  lower: A(m, k) = 0 for k > m.
+// up to 64 slots), so short and long products alike fill a launch.  lower: A(m, k) = 0 for k > m.
 template <int NR>
 __global__ void __launch_bounds__(SK_THREADS) k_sk_nn(const SkJob* __restrict__ jobs, const SkItem* __restrict__ items,
                                                       int nrhs) {
@@ -139,9 +139,9 @@ __global__ void __launch_bounds__(SK_THREADS) k_sk_tn(const SkJob* __restrict__ 
 void sk_items(int tn, const std::vector<SkJob>& jobs, int job0, std::vector<SkItem>& items) {
   for (size_t q = 0; q < jobs.size(); ++q) {
     const SkJob& J = jobs[q];
-    int cfg = 0;  // log2 of the k-slots: at most 8 k steps per slot, at most 32 slots
+    int cfg = 0;  // log2 of the k-slots: at most 8 k steps per slot, at most 64 slots (4 rows)
     if (!tn)
-      while (cfg < 5 && ((J.K + (1 << cfg) - 1) >> cfg) > 8) ++cfg;
+      while (cfg < 6 && ((J.K + (1 << cfg) - 1) >> cfg) > 8) ++cfg;
     const int rows = tn ? SK_THREADS / 32 : SK_THREADS >> cfg;
     for (int m0 = 0; m0 < J.M; m0 += rows) items.push_back(SkItem{job0 + (int)q, m0, cfg});
   }
