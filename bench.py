@@ -421,7 +421,8 @@ def batch_specs(count, seed=3):
 
 
 def run_batch(args):
-    """Batched small factorizations: all matrices factored in one session (shared launches per column)."""
+    """Batched small factorizations: all matrices of one ARA block width factored in one session (shared
+    launches per column), one session per tuned block width."""
     import torch
     import paper_2108_11932_gb300 as T
     from paper_2108_11932_gb300 import autotune
@@ -441,8 +442,18 @@ def run_batch(args):
             eps.append(sp["eps"])
             opts.append(o)
         return mats, eps, opts
+    def factor_groups(mats, eps, opts):
+        """One tlr_factor_batch per ARA block width (a batch shares bs); statuses in input order."""
+        st = [None] * len(mats)
+        for bsv in sorted({o.bs for o in opts}):
+            idx = [i for i, o in enumerate(opts) if o.bs == bsv]
+            sg = ctx.factor_batch([mats[i] for i in idx], [eps[i] for i in idx], [opts[i] for i in idx])
+            for i, v in zip(idx, sg):
+                st[i] = v
+        return st
+
     warm = build(specs[: min(16, len(specs))])
-    ctx.factor_batch(*warm)
+    factor_groups(*warm)
     for m in warm[0]:
         m.free()
     torch.cuda.synchronize()
@@ -453,7 +464,7 @@ def run_batch(args):
     l0 = ctx.launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(ctx.stream)
-    st = ctx.factor_batch(mats, eps, opts)
+    st = factor_groups(mats, eps, opts)
     e1.record(ctx.stream)
     torch.cuda.synchronize()
     secs = e0.elapsed_time(e1) / 1e3

@@ -134,7 +134,9 @@ tlr_status tlr_ldlt(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts);
  * else LDL^T), each in place as with tlr_potrf / tlr_ldlt.  The matrices advance
  * column by column together and every step of every matrix shares the same
  * launches (one dynamic ARA batch per column step for all matrices; sizes,
- * thresholds and options may differ per matrix).  Each matrix draws its own
+ * thresholds and options may differ per matrix, except the ARA block width
+ * opts.bs, which all matrices of one call share: a call mixing block widths
+ * returns TLR_ERR_ARG without factoring any).  Each matrix draws its own
  * Gaussian blocks (its opts.seed), so its result does not depend on the batch.
  * eps[m] and opts[m] (opts may be NULL for defaults) per matrix; status[m]
  * (host) receives each matrix's outcome (TLR_ERR_NOT_SPD leaves it FAILED).

@@ -65,18 +65,19 @@ void omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, uint32_t t,
 //     ~2^-21), then one third-order Newton correction sqrt(F) = F y0 (1 + h/2 + 3h^2/8 + O(h^3)),
 //     h = 1 - F y0^2, in 64-bit fixed point (~2^-58 relative).
 //  4. z = c sqrt(S) 2^-q with c = 1/ell, then exp(-z) by the table-driven method of Tang (ACM TOMS
-//     15(2), 1989) in fixed point: z 64/ln2 = n + f (128-bit product, |f| <= 1/2), rho = f ln2/64,
-//     exp(-z) = 2^(-n/64) exp(-rho), exp(-rho) - 1 by its degree-6 Taylor polynomial (truncation
-//     below 2^-60 for |rho| <= ln2/128), 2^(-j/64) from a 64-entry Q63 table, then rounded to 53 bits.
+//     15(2), 1989) in fixed point: z 64/ln2 = n + f (128-bit product, n = floor, 0 <= f < 1),
+//     rho = f ln2/64, exp(-z) = 2^(-n/64) exp(-rho), exp(-rho) by its degree-6 Taylor polynomial in
+//     unsigned Horner form (truncation below 2^-58 for rho < ln2/64), 2^(-j/64) from a 64-entry Q63
+//     table, then rounded to 53 bits.
 //
 // Error: under 0.3 x 2^-52 (1 + z) relative (the (1 + z) is the conditioning of exp in its argument,
 // which the FP64 formula has as well).  Entries below 2^-1020 (z > 707) are returned as 0.
 namespace fx {
-// round(64/ln2 2^56), round(ln2/64 2^69), Fk = round(2^62 / k!), TAB[j] = round(2^(63 - j/64))
+// round(64/ln2 2^56), round(ln2/64 2^70), Fk = round(2^62 / k!), TAB[j] = round(2^(63 - j/64))
 constexpr uint64_t KQ = 0x5c551d94ae0bf85eull;
-constexpr long long L69 = 0x58b90bfbe8e7bcd6ll;
-constexpr long long F1 = 0x4000000000000000ll, F2 = 0x2000000000000000ll, F3 = 0x0aaaaaaaaaaaaaabll,
-                    F4 = 0x02aaaaaaaaaaaaabll, F5 = 0x0088888888888889ll, F6 = 0x0016c16c16c16c17ll;
+constexpr uint64_t L70 = 0xb17217f7d1cf79acull;
+constexpr uint64_t F1 = 0x4000000000000000ull, F2 = 0x2000000000000000ull, F3 = 0x0aaaaaaaaaaaaaabull,
+                   F4 = 0x02aaaaaaaaaaaaabull, F5 = 0x0088888888888889ull, F6 = 0x0016c16c16c16c17ull;
 __device__ const uint64_t TAB[64] = {
     0x8000000000000000ull, 0x7e9f06067a4360baull, 0x7d41d96db915019dull, 0x7be86fb985689ddcull,
     0x7a92be8a92436616ull, 0x7940bb9e2cffd89dull, 0x77f25ccdee6d7ae6ull, 0x76a7980f6cca15c2ull,
@@ -127,15 +128,15 @@ __device__ __forceinline__ double entry(uint64_t hi, uint64_t lo, int ezb, uint6
     n = 0;
     frac = sh < 192 ? (phi >> (sh - 128)) : 0;
   }
-  n += frac >> 63;  // nearest integer; frac becomes the signed remainder in [-1/2, 1/2)
-  if ((n >> 6) > 1020) return 0.0;
-  const long long sg = -__mul64hi((long long)frac, L69);                      // -rho, Q69
-  long long acc = F5 + (__mul64hi(sg, F6) >> 5);                             // Horner, Q62
-  acc = F4 + (__mul64hi(sg, acc) >> 5);
-  acc = F3 + (__mul64hi(sg, acc) >> 5);
-  acc = F2 + (__mul64hi(sg, acc) >> 5);
-  acc = F1 + (__mul64hi(sg, acc) >> 5);
-  const uint64_t E = (1ull << 62) + (uint64_t)(__mul64hi(sg, acc) >> 5);      // exp(-rho), Q62
+  if ((n >> 6) > 1020) return 0.0;  // n = floor(z 64/ln2), frac its remainder in [0, 1)
+  // exp(-rho) = 1 - rho (F1 - rho (F2 - rho (F3 - rho (F4 - rho (F5 - rho F6))))), all terms >= 0
+  const uint64_t rho = __umul64hi(frac, L70);                                 // Q70, in [0, ln2/64)
+  uint64_t acc = F5 - (__umul64hi(rho, F6) >> 6);                            // Horner, Q62
+  acc = F4 - (__umul64hi(rho, acc) >> 6);
+  acc = F3 - (__umul64hi(rho, acc) >> 6);
+  acc = F2 - (__umul64hi(rho, acc) >> 6);
+  acc = F1 - (__umul64hi(rho, acc) >> 6);
+  const uint64_t E = (1ull << 62) - (__umul64hi(rho, acc) >> 6);              // exp(-rho), Q62
   const uint64_t V = __umul64hi(tab[n & 63], E);                              // Q61, in (0.49, 1.01)
   const int lzv = __clzll((long long)V);
   const uint64_t Vn = V << lzv;
@@ -452,10 +453,10 @@ __global__ void __launch_bounds__(32) k_cholqr_reg(const double* __restrict__ Ga
       const double gjj = __shfl_sync(0xffffffffu, gdiag, j);
       const bool kept = (dj > fmax(thr2, tau * gjj)) && (dj > 0.0) && isfinite(dj);
       if (kept) {
-        // one reciprocal per pivot: every later use multiplies (a warp-wide FP64 divide costs
-        // as much as ten FMAs on this part, and the factor and its inverse need 3 BS of them)
-        const double rjj = sqrt(dj);
-        inv[j] = 1.0 / rjj;
+        // every later use multiplies (a warp-wide FP64 divide or square root costs as much as
+        // ten FMAs on this part, and the factor and its inverse need 3 BS of them)
+        inv[j] = rsqrt(dj);  // one reciprocal square root per pivot; R(j, j) = dj / sqrt(dj)
+        const double rjj = dj * inv[j];
         const double rj = (lane == j) ? rjj : ((lane > j && lane < n) ? g[j] * inv[j] : 0.0);
 #pragma unroll
         for (int a = j + 1; a < BS; ++a) {
