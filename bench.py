@@ -457,26 +457,33 @@ def run_batch(args):
     for m in warm[0]:
         m.free()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    mats, eps, opts = build(specs)
-    torch.cuda.synchronize()
-    t_build = time.perf_counter() - t0
-    l0 = ctx.launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(ctx.stream)
-    st = factor_groups(mats, eps, opts)
-    e1.record(ctx.stream)
-    torch.cuda.synchronize()
-    secs = e0.elapsed_time(e1) / 1e3
-    fl = sum(m.info()["flops_exec"] for m, s_ in zip(mats, st) if s_ == 0)
+    # chunks of matrices are built, factored (timed) and freed in turn: all 512 inputs and factors
+    # (up to ~250 MB each at N = 16384) do not fit in HBM at once
+    t_build, secs, fl, st, nl = 0.0, 0.0, 0.0, [], 0
     bs_used = {}
-    for m, o in zip(mats, opts):
-        key = f"b{m.info()['b']}_bs{o.bs}_w{o.max_slots}"
-        bs_used[key] = bs_used.get(key, 0) + 1
+    for c0 in range(0, len(specs), args.batch_chunk):
+        t0 = time.perf_counter()
+        mats, eps, opts = build(specs[c0:c0 + args.batch_chunk])
+        torch.cuda.synchronize()
+        t_build += time.perf_counter() - t0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ctx.launches()
+        e0.record(ctx.stream)
+        sc = factor_groups(mats, eps, opts)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        nl += ctx.launches() - l0
+        secs += e0.elapsed_time(e1) / 1e3
+        fl += sum(m.info()["flops_exec"] for m, s_ in zip(mats, sc) if s_ == 0)
+        st += sc
+        for m, o in zip(mats, opts):
+            key = f"b{m.info()['b']}_bs{o.bs}_w{o.max_slots}"
+            bs_used[key] = bs_used.get(key, 0) + 1
+            m.free()
     out = {"workload": f"batch{len(specs)}: {len(specs)} independent covariance matrices, N=256*U{{8..64}}, d in {{2,3}}, "
                        "ell~U[0.05,0.3], nugget 1e-4, eps 1e-6, FP64; (b, bs, batch width) from the autotuner",
-           "matrices": len(specs), "ok": sum(1 for s_ in st if s_ == 0), "factor_s": secs,
-           "matrices_per_s": len(specs) / secs, "tflops_exec": fl / secs / 1e12, "launches": ctx.launches() - l0,
+           "matrices": len(specs), "chunk": args.batch_chunk, "ok": sum(1 for s_ in st if s_ == 0), "factor_s": secs,
+           "matrices_per_s": len(specs) / secs, "tflops_exec": fl / secs / 1e12, "launches": nl,
            "construction_s": t_build, "autotune_s": t_tune, "configs_used": bs_used,
            "autotune_table": {f"d{k[0]}_N2^{k[1]}": list(v) for k, v in tuned["table"].items()}}
     print(json.dumps(out), flush=True)
@@ -588,6 +595,7 @@ def main():
                     help="phases mode: profile the compression as well as the factorization")
     ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve", "peaks", "phases"])
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-chunk", type=int, default=64, help="matrices built and factored together")
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--serve-nmax", type=int, default=65536)
