@@ -270,6 +270,34 @@ def test_factor_matches_oracle_ara(case, ldl):
 
 
 @pytest.mark.parametrize("ldl", [False, True])
+def test_schur_compensation_matches_oracle_ara(case, ldl):
+    """Section 5.1.1 compensation on both sides with one reading (Dbar_k from an ARA eps-basis of D_k
+    drawn from the Schur Gaussian stream): identical ranks, factor tiles and logdet as the oracle's."""
+    import paper_2108_11932_gb300 as TT
+    w = case["w"]
+    o = TT.default_opts(bs=w["bs"], seed=7, compensation=TT.COMP_SCHUR)
+    F = case["A"].copy()
+    (F.ldlt if ldl else F.potrf)(w["eps"], o)
+    Fo = tlr.factor(case["Ao"], w["eps"], ldl=ldl, compressor="ara", bs=w["bs"], seed=7, compensation="schur")
+    assert np.array_equal(F.ranks(), Fo.ranks())
+    b = w["b"]
+    for k in range(Fo.nb):
+        L, d = F.tile(k, k)
+        ref = Fo.diag[k]
+        assert rel(np.tril(L, -1) + (np.eye(b) if ldl else np.diag(np.diag(L))), ref) < 1e-10
+        if ldl:
+            assert rel(d, Fo.d[k]) < 1e-10
+    for (i, j) in Fo.U:
+        U, V = F.tile(i, j)
+        ref = Fo.U[(i, j)] @ Fo.V[(i, j)].T
+        if np.abs(ref).max() > 0:
+            assert rel(U @ V.T, ref) < 1e-9
+    ld, _ = F.logdet()
+    assert abs(ld - tlr.logdet(Fo)) <= 1e-10 * abs(tlr.logdet(Fo))
+    F.free()
+
+
+@pytest.mark.parametrize("ldl", [False, True])
 def test_repeated_solves_replay_a_captured_graph(case, ldl):
     """A factor's solves with one nrhs: the first runs the plan's launches directly, the second captures
     them as a CUDA graph and replays it, later ones replay; every result matches the oracle's solve

@@ -261,3 +261,26 @@ def test_backward_error_of_exact_factor_is_rounding_level():
     L = np.linalg.cholesky(A)
     be = measures.backward_error(lambda v: A @ v, lambda v: L @ (L.T @ v), np.ones(80))
     assert be < 1e-14
+
+
+def test_schur_compensation_pins():
+    """Section 5.1.1 compensation (A_kk - D_k + diag(rowsum|D_k - Dbar_k|)), pinned without its formula:
+    at eps = 1e-12 Dbar_k = D_k to rounding, so the factor is the uncompensated one; at eps = 1e-3 the
+    first compensated column (k = 1, whose D_1 both factorizations share) changes L_11 L_11^T by a
+    diagonal that is positive (the compensation is active) and, D-bar being an eps-truncation of the
+    symmetric D_1, at most sqrt(b) eps per row (||E_i||_1 <= sqrt(b) ||E||_2 <= sqrt(b) eps)."""
+    x = inputs.points(768, 2, 5)
+    b = 128
+    A = tlr.build(x, b, 1e-12, 0.1, 1e-4, compressor="svd")
+    P, C = tlr.factor(A, 1e-12), tlr.factor(A, 1e-12, compensation="schur")
+    for k in range(A.nb):
+        assert np.abs(P.diag[k] - C.diag[k]).max() <= 1e-10 * np.abs(P.diag[k]).max()
+    eps = 1e-3
+    A = tlr.build(x, b, eps, 0.1, 1e-4, compressor="svd")
+    P, C = tlr.factor(A, eps), tlr.factor(A, eps, compensation="schur")
+    assert np.allclose(P.diag[0], C.diag[0], rtol=0, atol=0)
+    D = C.diag[1] @ C.diag[1].T - P.diag[1] @ P.diag[1].T
+    scale = np.abs(A.diag[1]).max()
+    assert np.abs(D - np.diag(np.diag(D))).max() <= 1e-13 * scale
+    assert np.diag(D).min() > 0.0
+    assert np.diag(D).max() <= math.sqrt(b) * eps * (1 + 1e-12)
