@@ -20,6 +20,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -119,7 +120,10 @@ class Clocks:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # raw samples: a temporary file (the summary goes into the JSON line); TLR_CLOCKS_DIR keeps them
+        keep = os.environ.get("TLR_CLOCKS_DIR")
+        self.keep = bool(keep)
+        self.path = os.path.join(keep or tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -154,6 +158,11 @@ class Clocks:
             for n, v in zip(names, p[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(n)
+        if not self.keep:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
