@@ -1,8 +1,8 @@
 """Tile compressors (oracle; test infrastructure).
 
 svd_truncate: the reference compressor prescribed for the oracle: keep the
-  smallest rank r with sigma_{r+1} <= eps (absolute 2-norm threshold,
-  Section 6: "absolute compression threshold"), so ||T - Q B^T||_2 <= eps
+  smallest rank r with sigma_{r+1} <= eps (an absolute 2-norm threshold, as
+  Section 6 states), so ||T - Q B^T||_2 <= eps
   (Eckart-Young).  Q = U_r (orthonormal), B = V_r Sigma_r.
 
 ara: Adaptive Randomized Approximation, Algorithm 1 (Section 3.1), applied to

@@ -2,7 +2,7 @@
 //
 // The paper executes the products of its sampling chains (Equation 2 / 3),
 // projections (sampleLeftT), orthogonalization and dense updates as
-// non-uniform batched GEMMs (Section 4.1, "marshaling" + vbatched GEMM).  Here
+// non-uniform batched GEMMs (Section 4.1: pointer marshaling, then a vbatched GEMM).  Here
 // one launch takes an array of jobs of different shapes; each CTA computes one
 // output tile of one job over its whole K range or over one slice of it
 // (deterministic split-K: fixed slices, fixed-order reduction).
