@@ -116,6 +116,14 @@ def _diag_update(F: TLR, k: int) -> np.ndarray:
     return Dk
 
 
+def _schur_compensation(Dk: np.ndarray, comp) -> np.ndarray:
+    """Section 5.1.1: the term added to A(k,k) - D_k, diag(rowsum|D_k - Dbar_k|), with Dbar_k =
+    Q Q^T D_k Q Q^T and Q the compressor's eps-basis of the symmetric D_k."""
+    Q, _, _ = comp(Dk)
+    Dbar = Q @ (Q.T @ Dk @ Q) @ Q.T
+    return np.diag(np.sum(np.abs(Dk - Dbar), axis=1))
+
+
 def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: int = 16,
            seed: int = 0, compensation: str | None = None, shift: float = 0.0) -> TLR:
     """Left-looking TLR Cholesky (Algorithm 6) or LDL^T (Algorithm 10); returns the factor.
@@ -134,9 +142,7 @@ def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: i
         if compensation == "shift":
             Akk = Akk + shift * np.eye(b)
         elif compensation == "schur" and k > 0:
-            Q, _, _ = _compressor(compressor, eps, bs, seed, STREAM_SCHUR, k, b)(Dk)
-            Dbar = Q @ (Q.T @ Dk @ Q) @ Q.T
-            Akk = Akk + np.diag(np.sum(np.abs(Dk - Dbar), axis=1))
+            Akk = Akk + _schur_compensation(Dk, _compressor(compressor, eps, bs, seed, STREAM_SCHUR, k, b))
         try:
             if ldl:
                 Lkk, dk = Dn.ldlt(Akk)

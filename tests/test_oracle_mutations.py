@@ -112,3 +112,32 @@ def test_wrong_sign_in_left_looking_update_is_caught(monkeypatch):
         return lambda T: c(-T)
     monkeypatch.setattr(tlr, "_compressor", flip)
     assert not _ou_ok()
+
+
+def _schur_mutant(monkeypatch, term):
+    from test_oracle_pins import schur_pins_hold
+    orig = tlr._schur_compensation
+
+    def mutant(Dk, comp):
+        Q, _, _ = comp(Dk)
+        Dbar = Q @ (Q.T @ Dk @ Q) @ Q.T
+        return term(Dk, Dbar, orig(Dk, comp))
+
+    assert schur_pins_hold()
+    monkeypatch.setattr(tlr, "_schur_compensation", mutant)
+    return schur_pins_hold()
+
+
+def test_schur_compensation_by_D_instead_of_its_residual_is_caught(monkeypatch):
+    assert not _schur_mutant(monkeypatch, lambda D, Db, ok: np.diag(np.sum(np.abs(D), axis=1)))
+
+
+def test_schur_compensation_with_wrong_sign_is_caught(monkeypatch):
+    assert not _schur_mutant(monkeypatch, lambda D, Db, ok: -ok)
+
+
+def test_schur_compensation_off_the_diagonal_is_caught(monkeypatch):
+    def spread(D, Db, ok):
+        r = np.diag(ok)
+        return ok + 0.5 * (np.outer(np.sqrt(r), np.sqrt(r)) - np.diag(r))
+    assert not _schur_mutant(monkeypatch, spread)

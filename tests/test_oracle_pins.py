@@ -263,7 +263,7 @@ def test_backward_error_of_exact_factor_is_rounding_level():
     assert be < 1e-14
 
 
-def test_schur_compensation_pins():
+def schur_pins_hold() -> bool:
     """Section 5.1.1 compensation (A_kk - D_k + diag(rowsum|D_k - Dbar_k|)), pinned without its formula:
     at eps = 1e-12 Dbar_k = D_k to rounding, so the factor is the uncompensated one; at eps = 1e-3 the
     first compensated column (k = 1, whose D_1 both factorizations share) changes L_11 L_11^T by a
@@ -274,13 +274,21 @@ def test_schur_compensation_pins():
     A = tlr.build(x, b, 1e-12, 0.1, 1e-4, compressor="svd")
     P, C = tlr.factor(A, 1e-12), tlr.factor(A, 1e-12, compensation="schur")
     for k in range(A.nb):
-        assert np.abs(P.diag[k] - C.diag[k]).max() <= 1e-10 * np.abs(P.diag[k]).max()
+        if np.abs(P.diag[k] - C.diag[k]).max() > 1e-10 * np.abs(P.diag[k]).max():
+            return False
     eps = 1e-3
     A = tlr.build(x, b, eps, 0.1, 1e-4, compressor="svd")
-    P, C = tlr.factor(A, eps), tlr.factor(A, eps, compensation="schur")
-    assert np.allclose(P.diag[0], C.diag[0], rtol=0, atol=0)
+    try:
+        P, C = tlr.factor(A, eps), tlr.factor(A, eps, compensation="schur")
+    except dense.NotPositiveDefinite:
+        return False
+    if not np.array_equal(P.diag[0], C.diag[0]):
+        return False
     D = C.diag[1] @ C.diag[1].T - P.diag[1] @ P.diag[1].T
     scale = np.abs(A.diag[1]).max()
-    assert np.abs(D - np.diag(np.diag(D))).max() <= 1e-13 * scale
-    assert np.diag(D).min() > 0.0
-    assert np.diag(D).max() <= math.sqrt(b) * eps * (1 + 1e-12)
+    return (np.abs(D - np.diag(np.diag(D))).max() <= 1e-13 * scale and np.diag(D).min() > 0.0
+            and np.diag(D).max() <= math.sqrt(b) * eps * (1 + 1e-12))
+
+
+def test_schur_compensation_pins():
+    assert schur_pins_hold()
