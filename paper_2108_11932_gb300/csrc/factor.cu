@@ -100,7 +100,7 @@ struct BatchSampler : Sampler {
   const std::vector<char>* member = nullptr;
   const double* Q = nullptr;
   const std::vector<int64_t>* qoff = nullptr;
-  Buf *bom = nullptr, *bom32 = nullptr, *bx = nullptr, *bw = nullptr, *by32 = nullptr, *bp = nullptr, *bz = nullptr,
+  Buf *bom = nullptr, *bom32 = nullptr, *bw = nullptr, *by32 = nullptr, *bp = nullptr, *bz = nullptr,
       *bq32 = nullptr, *bb32 = nullptr;
   // tensor-core split products with F's U panels (FP64 arithmetic, matrices with M.oz)
   const int* d_one = nullptr;  // device int 1: the exponent of the U-panel slices
@@ -568,13 +568,13 @@ struct Session {
   tlr_ctx* ctx;
   int bs = -1;
   std::vector<std::unique_ptr<Mat>> mats;
-  Buf bnrm, bQ, bTab, bInfo, bTmp, bTmpMain, bOm, bOm32, bX, bW, bY32, bP, bZ, bQ32, bB32;
+  Buf bnrm, bQ, bTab, bInfo, bTmp, bTmpMain, bOm, bOm32, bW, bY32, bP, bZ, bQ32, bB32;
   Buf bOzMax, bOzS, bOzE, bOzX, bOzEx;  // split trsm products
   Buf bOzOs, bOzOe, bOzWs, bOzWe, bOne;  // split sampling / projection products
   int* d_one = nullptr;
   AraStats total;
   explicit Session(tlr_ctx* c)
-      : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bX(c), bW(c), bY32(c), bP(c), bZ(c),
+      : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bW(c), bY32(c), bP(c), bZ(c),
         bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c), bOzOs(c), bOzOe(c), bOzWs(c), bOzWe(c),
         bOne(c) {
     static const int one = 1;
@@ -1021,7 +1021,7 @@ struct Session {
       auto setup = [&](auto& S, const std::vector<char>* mem) {
         S.ctx = ctx; S.bs = bs; S.L = &L; S.op_m = &op_m; S.op_i = &op_i; S.member = mem;
         S.Q = Q; S.qoff = &qoff;
-        S.bom = &bOm; S.bom32 = &bOm32; S.bx = &bX; S.bw = &bW; S.by32 = &bY32; S.bp = &bP; S.bz = &bZ;
+        S.bom = &bOm; S.bom32 = &bOm32; S.bw = &bW; S.by32 = &bY32; S.bp = &bP; S.bz = &bZ;
         S.bq32 = &bQ32; S.bb32 = &bB32;
         S.d_one = d_one; S.bos = &bOzOs; S.boe = &bOzOe; S.bws = &bOzWs; S.bwe = &bOzWe;
       };
