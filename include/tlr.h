@@ -174,6 +174,23 @@ tlr_status tlr_session_poll(tlr_session* s, int ticket, int* finished, tlr_statu
  * concurrently (they share the plan's work arrays). */
 tlr_status tlr_solve(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* B, int64_t ldb);
 
+/* Preconditioned conjugate gradients (Section 6: a low-accuracy TLR factor of
+ * A + eps I as the CG preconditioner, run until ||A x - b|| / ||b|| <= tol).
+ * A: a compressed matrix (state "A", the operator, applied with tlr_matvec);
+ * F: a factor of the same N (the preconditioner, applied with tlr_solve, so its
+ * solves replay a captured graph after the first).  B: device, N x nrhs,
+ * leading dimension ldb >= N, original point order (read only); X: device,
+ * N x nrhs, ldx >= N, receives the solutions (started from 0).  Each column
+ * runs its own iteration (textbook PCG, Saad Algorithm 9.1) and stops when its
+ * updated residual is at most tol ||b|| or after maxit iterations; iters[c]
+ * (host) receives its iteration count and relres[c] (host) its true relative
+ * residual ||b - A x|| / ||b||.  A zero column gives x = 0 after 0 iterations.
+ * Errors: TLR_ERR_ARG (null pointers, nrhs < 0, tol <= 0, maxit < 0, N
+ * mismatch or above 2^31 - 1), TLR_ERR_STATE (A not in state "A" or F not
+ * factored). */
+tlr_status tlr_pcg(tlr_ctx* ctx, const tlr_mat* A, const tlr_mat* F, int nrhs, const double* B, int64_t ldb,
+                   double* X, int64_t ldx, double tol, int maxit, int* iters, double* relres);
+
 /* log|det| of the factored matrix: 2 sum log diag(L_kk) (Cholesky) or
  * sum log|D_ii| (LDL^T); *sign = sign of the determinant.  Host outputs. */
 tlr_status tlr_logdet(tlr_ctx* ctx, const tlr_mat* F, double* logdet, int* sign);

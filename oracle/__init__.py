@@ -23,4 +23,5 @@ Modules
   tlr       left-looking TLR Cholesky (Algorithm 6) and LDL^T (Algorithm 10),
             TLR triangular solve (Algorithm 7), log-determinant, matvec.
   measures  backward error by power iteration and solve residual (Section 6).
+  pcg       preconditioned CG with a TLR factor as the preconditioner (Section 6).
 """

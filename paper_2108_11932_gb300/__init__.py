@@ -89,6 +89,8 @@ def _load():
         "tlr_ldlt": (C.c_int, [P, P, C.c_double, C.POINTER(Opts)]),
         "tlr_solve": (C.c_int, [P, P, C.c_int, P, C.c_int64]),
         "tlr_logdet": (C.c_int, [P, P, D, C.POINTER(C.c_int)]),
+        "tlr_pcg": (C.c_int, [P, P, P, C.c_int, P, C.c_int64, P, C.c_int64, C.c_double, C.c_int,
+                              C.POINTER(C.c_int), D]),
         "tlr_matvec": (C.c_int, [P, P, C.c_int, C.c_int, P, C.c_int64, P, C.c_int64]),
         "tlr_kernel_matvec": (C.c_int, [P, P, C.c_int64, C.c_int, C.POINTER(Kernel), C.c_int, P, C.c_int64, P,
                                         C.c_int64]),
@@ -400,6 +402,19 @@ class Matrix:
         B2 = B if B.dim() == 2 else B[:, None]
         _check(_load().tlr_solve(self.ctx.h, self.h, B2.shape[1], _ptr(B2), _ld(B2)), "tlr_solve")
         return B
+
+    def pcg(self, F: "Matrix", B, tol: float = 1e-6, maxit: int = 300):
+        """PCG on this compressed matrix (the operator) with the factor F as preconditioner.
+
+        Returns (X, iterations per column, true relative residual per column); B is not modified."""
+        B2 = B if B.dim() == 2 else B[:, None]
+        X = fortran(self.ctx.torch.empty_like(B2))
+        k = B2.shape[1]
+        it = (C.c_int * max(k, 1))()
+        rr = (C.c_double * max(k, 1))()
+        _check(_load().tlr_pcg(self.ctx.h, self.h, F.h, k, _ptr(B2), _ld(B2), _ptr(X), _ld(X), float(tol), int(maxit),
+                               it, rr), "tlr_pcg")
+        return X, [it[c] for c in range(k)], [rr[c] for c in range(k)]
 
     def logdet(self) -> tuple[float, int]:
         v, s = C.c_double(0), C.c_int(0)

@@ -395,6 +395,14 @@ struct SkItem {
 };
 void sk_items(int tn, const std::vector<SkJob>& jobs, int job0, std::vector<SkItem>& items);
 void sk_gemm(tlr_ctx* ctx, int tn, const SkJob* jobs, const SkItem* items, int nitems, int nrhs);
+// Preconditioned CG vectors (k_solve.cu): per-column dot products (fixed-order sums) and the two
+// vector updates of an iteration, with per-column coefficients num/den read on the device.
+void coldot(tlr_ctx* ctx, int64_t n, int ncols, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+            double* out);
+void pcg_update_xr(tlr_ctx* ctx, int64_t n, int ncols, const double* num, const double* den, const int* active,
+                   double* x, int64_t ldx, const double* p, double* r, const double* q, int64_t ld);
+void pcg_update_p(tlr_ctx* ctx, int64_t n, int ncols, const double* num, const double* den, const int* active,
+                  const double* z, double* p, int64_t ld);
 struct ConvJob {
   const double* src;
   float* dst;

@@ -7,6 +7,8 @@
 // kernels run at the FP64 FMA rate (one FMA per 8 bytes for nrhs = 1 is ~0.85 TFMA/s of HBM
 // bandwidth against ~0.63 TFMA/s of DFMA) without padding.  Sums are reduced in a fixed order (no
 // atomics): results do not depend on timing.
+#include <algorithm>
+
 #include "common.h"
 
 namespace tlr {
@@ -165,6 +167,79 @@ void sk_gemm(tlr_ctx* ctx, int tn, const SkJob* jobs, const SkItem* items, int n
   else if (nrhs == 2) sk_launch<2>(ctx, tn, jobs, items, nitems, nrhs);
   else if (nrhs <= 4) sk_launch<4>(ctx, tn, jobs, items, nitems, nrhs);
   else sk_launch<8>(ctx, tn, jobs, items, nitems, nrhs);
+}
+
+// ------------------------------------------------------------------ preconditioned CG vectors
+// out[c] = sum_i X(i, c) Y(i, c): one CTA per column, strided partial sums, then a fixed-order tree.
+__global__ void __launch_bounds__(256) k_coldot(int64_t n, const double* __restrict__ X, int64_t ldx,
+                                                const double* __restrict__ Y, int64_t ldy, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int c = blockIdx.x;
+  const double* x = X + (size_t)c * ldx;
+  const double* y = Y + (size_t)c * ldy;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) s = fma(x[i], y[i], s);
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+void coldot(tlr_ctx* ctx, int64_t n, int ncols, const double* X, int64_t ldx, const double* Y, int64_t ldy,
+            double* out) {
+  if (ncols <= 0) return;
+  TLR_SITE_PRE(ctx);
+  k_coldot<<<(unsigned)ncols, 256, 0, ctx->stream>>>(n, X, ldx, Y, ldy, out);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+// Active columns c (active[c] != 0): x += a p, r -= a q with a = num[c] / den[c].
+__global__ void k_pcg_xr(int64_t n, const double* __restrict__ num, const double* __restrict__ den,
+                         const int* __restrict__ active, double* __restrict__ x, int64_t ldx,
+                         const double* __restrict__ p, double* __restrict__ r, const double* __restrict__ q,
+                         int64_t ld) {
+  const int c = blockIdx.y;
+  if (!active[c]) return;
+  const double a = num[c] / den[c];
+  const size_t o = (size_t)c * ld;
+  double* xc = x + (size_t)c * ldx;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    xc[i] = fma(a, p[o + i], xc[i]);
+    r[o + i] = fma(-a, q[o + i], r[o + i]);
+  }
+}
+
+// Active columns: p = z + b p with b = num[c] / den[c].
+__global__ void k_pcg_p(int64_t n, const double* __restrict__ num, const double* __restrict__ den,
+                        const int* __restrict__ active, const double* __restrict__ z, double* __restrict__ p,
+                        int64_t ld) {
+  const int c = blockIdx.y;
+  if (!active[c]) return;
+  const double bt = num[c] / den[c];
+  const size_t o = (size_t)c * ld;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[o + i] = fma(bt, p[o + i], z[o + i]);
+}
+
+void pcg_update_xr(tlr_ctx* ctx, int64_t n, int ncols, const double* num, const double* den, const int* active,
+                   double* x, int64_t ldx, const double* p, double* r, const double* q, int64_t ld) {
+  if (ncols <= 0 || n <= 0) return;
+  const unsigned gx = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+  TLR_SITE_PRE(ctx);
+  k_pcg_xr<<<dim3(gx, (unsigned)ncols), 256, 0, ctx->stream>>>(n, num, den, active, x, ldx, p, r, q, ld);
+  TLR_LAUNCH_CHECK(ctx);
+}
+
+void pcg_update_p(tlr_ctx* ctx, int64_t n, int ncols, const double* num, const double* den, const int* active,
+                  const double* z, double* p, int64_t ld) {
+  if (ncols <= 0 || n <= 0) return;
+  const unsigned gx = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+  TLR_SITE_PRE(ctx);
+  k_pcg_p<<<dim3(gx, (unsigned)ncols), 256, 0, ctx->stream>>>(n, num, den, active, z, p, ld);
+  TLR_LAUNCH_CHECK(ctx);
 }
 
 }  // namespace tlr

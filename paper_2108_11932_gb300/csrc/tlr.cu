@@ -1313,6 +1313,79 @@ tlr_status tlr_solve(tlr_ctx* ctx, const tlr_mat* F, int nrhs, double* B, int64_
   ABI_END
 }
 
+tlr_status tlr_pcg(tlr_ctx* ctx, const tlr_mat* A, const tlr_mat* F, int nrhs, const double* B, int64_t ldb,
+                   double* X, int64_t ldx, double tol, int maxit, int* iters, double* relres) {
+  if (!ctx || !A || !F || !B || !X || !iters || !relres || nrhs < 0 || !(tol > 0) || maxit < 0) return TLR_ERR_ARG;
+  if (A->N != F->N || ldb < A->N || ldx < A->N || A->N > INT32_MAX) return TLR_ERR_ARG;
+  if (A->state != 0 || (F->state != 1 && F->state != 2)) return TLR_ERR_STATE;
+  if (nrhs == 0) return TLR_OK;
+  ABI_BEGIN
+  const int64_t n = A->N;
+  auto check = [](tlr_status st, const char* what) {
+    if (st != TLR_OK) throw Error(st, what);
+  };
+  Buf bR(ctx), bP(ctx), bQ(ctx), bZ(ctx), bS(ctx);
+  double* R = bR.need<double>((size_t)n * nrhs);
+  double* P = bP.need<double>((size_t)n * nrhs);
+  double* Q = bQ.need<double>((size_t)n * nrhs);
+  double* Z = bZ.need<double>((size_t)n * nrhs);
+  double* sc = bS.need<double>((size_t)5 * nrhs);  // |b|^2, (r, z) twice, (p, A p), |r|^2 per column
+  double* bn2 = sc;
+  double* rz[2] = {sc + nrhs, sc + 2 * nrhs};
+  double* pq = sc + 3 * nrhs;
+  double* rr = sc + 4 * nrhs;
+  const size_t cb = sizeof(double) * (size_t)n;
+  TLR_CUDA(cudaMemset2DAsync(X, sizeof(double) * ldx, 0, cb, nrhs, ctx->stream));
+  TLR_CUDA(cudaMemcpy2DAsync(R, cb, B, sizeof(double) * ldb, cb, nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+  coldot(ctx, n, nrhs, B, ldb, B, ldb, bn2);
+  double* h = static_cast<double*>(host_status(ctx, sizeof(double) * nrhs));
+  d2h_sync(ctx, h, bn2, sizeof(double) * nrhs);
+  std::vector<double> hb(h, h + nrhs);
+  std::vector<int> act(nrhs);
+  int nact = 0;
+  for (int c = 0; c < nrhs; ++c) {
+    act[c] = hb[c] > 0.0;  // a zero right-hand side has x = 0 after 0 iterations
+    nact += act[c];
+    iters[c] = 0;
+  }
+  // z0 = M^-1 r0, p0 = z0
+  TLR_CUDA(cudaMemcpyAsync(Z, R, cb * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+  if (nact > 0) check(tlr_solve(ctx, F, nrhs, Z, n), "pcg: preconditioner solve");
+  TLR_CUDA(cudaMemcpyAsync(P, Z, cb * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+  coldot(ctx, n, nrhs, R, n, Z, n, rz[0]);
+  int cur = 0;
+  for (int it = 1; it <= maxit && nact > 0; ++it) {
+    check(tlr_matvec(ctx, A, TLR_OP_A, nrhs, P, n, Q, n), "pcg: operator product");
+    coldot(ctx, n, nrhs, P, n, Q, n, pq);
+    const int* da = static_cast<const int*>(upload(ctx, act.data(), sizeof(int) * nrhs));
+    pcg_update_xr(ctx, n, nrhs, rz[cur], pq, da, X, ldx, P, R, Q, n);
+    coldot(ctx, n, nrhs, R, n, R, n, rr);
+    d2h_sync(ctx, h, rr, sizeof(double) * nrhs);
+    for (int c = 0; c < nrhs; ++c)
+      if (act[c] && (std::sqrt(h[c]) <= tol * std::sqrt(hb[c]) || it == maxit)) {
+        act[c] = 0;
+        iters[c] = it;
+        --nact;
+      }
+    if (nact == 0) break;
+    TLR_CUDA(cudaMemcpyAsync(Z, R, cb * nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+    check(tlr_solve(ctx, F, nrhs, Z, n), "pcg: preconditioner solve");
+    coldot(ctx, n, nrhs, R, n, Z, n, rz[1 - cur]);
+    da = static_cast<const int*>(upload(ctx, act.data(), sizeof(int) * nrhs));
+    pcg_update_p(ctx, n, nrhs, rz[1 - cur], rz[cur], da, Z, P, n);
+    cur = 1 - cur;
+  }
+  // true residual |b - A x| / |b|
+  check(tlr_matvec(ctx, A, TLR_OP_A, nrhs, X, ldx, Q, n), "pcg: operator product");
+  TLR_CUDA(cudaMemcpy2DAsync(R, cb, B, sizeof(double) * ldb, cb, nrhs, cudaMemcpyDeviceToDevice, ctx->stream));
+  axpy_matrix(ctx, (int)n, nrhs, -1.0, Q, (int)n, R, (int)n);
+  coldot(ctx, n, nrhs, R, n, R, n, rr);
+  d2h_sync(ctx, h, rr, sizeof(double) * nrhs);
+  for (int c = 0; c < nrhs; ++c) relres[c] = hb[c] > 0.0 ? std::sqrt(h[c] / hb[c]) : 0.0;
+  return TLR_OK;
+  ABI_END
+}
+
 tlr_status tlr_logdet(tlr_ctx* ctx, const tlr_mat* F, double* logdet, int* sign) {
   if (!ctx || !F || !logdet) return TLR_ERR_ARG;
   if (F->state != 1 && F->state != 2) return TLR_ERR_STATE;

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import inputs
-from oracle import compress, dense, kernel, measures, philox, tlr
+from oracle import pcg as opcg, compress, dense, kernel, measures, philox, tlr
 
 pytestmark = pytest.mark.gpu
 
@@ -596,3 +596,33 @@ def test_autotune_picks_a_measured_configuration(T, ctx):
     assert tm[(2, 2048, b, 16, 0)] == min(tm[(2, 2048, v, 16, 0)] for v in (128, 256))
     assert tm[(2, 2048, b, bs, 0)] == min(tm[(2, 2048, b, v, 0)] for v in (16, 32))
     assert tm[(2, 2048, b, bs, width)] == min(tm[(2, 2048, b, bs, v)] for v in (0, 8))
+
+
+def test_pcg_matches_oracle(T, ctx):
+    """Section 6's use of a low-accuracy factor: PCG on the eps = 1e-8 compressed covariance matrix,
+    preconditioned by the factor of the eps = 1e-3 one with the shift eps I, against the oracle's PCG on
+    the oracle's matrices (same ARA streams): iteration counts within one of each other, true residuals
+    at the tolerance, a zero right-hand side solved by x = 0 in 0 iterations, and far fewer iterations
+    than unpreconditioned CG would need."""
+    N, d, ell, nug, b, bs, tol = 2048, 2, 0.1, 1e-4, 256, 16, 1e-8
+    x = inputs.points(N, d, 0)
+    o = T.default_opts(bs=bs, seed=7)
+    A = ctx.compress(x, b, 1e-8, ell, nug, o)
+    Fm = ctx.compress(x, b, 1e-3, ell, nug, o)
+    Fm.potrf(1e-3, T.default_opts(bs=bs, seed=7, compensation=T.COMP_SHIFT, shift=1e-3))
+    Ao = tlr.build(x, b, 1e-8, ell, nug, compressor="ara", bs=bs, seed=7)
+    Fo = tlr.factor(tlr.build(x, b, 1e-3, ell, nug, compressor="ara", bs=bs, seed=7), 1e-3, compressor="ara",
+                    bs=bs, seed=7, compensation="shift", shift=1e-3)
+    Y = inputs.rhs(N, 3, 31)
+    Y[:, 2] = 0.0
+    Xg, itg, rg = A.pcg(Fm, _t(T, Y), tol=tol, maxit=300)
+    Xo, ito, ro = opcg.pcg(lambda Z: tlr.matvec(Ao, Z, "A"), lambda R: tlr.solve(Fo, R), Y, tol, 300)
+    Xg = Xg.cpu().numpy()
+    assert itg[2] == 0 and ito[2] == 0 and not Xg[:, 2].any()
+    for c in range(2):
+        assert abs(itg[c] - int(ito[c])) <= 1, (itg, ito)
+        assert 0 < itg[c] < 60
+        assert rg[c] <= 2 * tol and ro[c] <= 2 * tol
+        assert rel(Xg[:, c], Xo[:, c]) < 1e-4
+    A.free()
+    Fm.free()

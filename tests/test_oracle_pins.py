@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import inputs
-from oracle import compress, dense, kdtree, kernel, measures, philox, tlr
+from oracle import compress, dense, kdtree, kernel, measures, pcg, philox, tlr
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -292,3 +292,42 @@ def schur_pins_hold() -> bool:
 
 def test_schur_compensation_pins():
     assert schur_pins_hold()
+
+
+def test_pcg_exact_preconditioner_converges_in_one_iteration():
+    """With M = A the preconditioned residual is the error: one step solves the system."""
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((60, 60))
+    A = G @ G.T + 60 * np.eye(60)
+    b = rng.standard_normal((60, 2))
+    x, it, res = pcg.pcg(lambda X: A @ X, lambda R: np.linalg.solve(A, R), b, 1e-12, 50)
+    assert list(it) == [1, 1]
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=0, atol=1e-12 * np.abs(np.linalg.solve(A, b)).max())
+    assert res.max() <= 1e-12
+
+
+def test_pcg_terminates_in_as_many_steps_as_distinct_eigenvalues():
+    """CG (M = I) on a matrix with 4 distinct eigenvalues: the Krylov space is exhausted after 4 steps."""
+    d = np.repeat([1.0, 3.0, 10.0, 40.0], 20)
+    A = np.diag(d)
+    b = np.random.default_rng(4).standard_normal((80, 1))
+    x, it, res = pcg.pcg(lambda X: A @ X, lambda R: R, b, 1e-10, 50)
+    assert it[0] <= 4 and res[0] <= 1e-10
+    assert np.allclose(x[:, 0], b[:, 0] / d, rtol=1e-9)
+
+
+def test_pcg_matches_scipy_cg_and_handles_a_zero_column():
+    """Against SciPy's CG with the same preconditioner, to the tolerance; a zero right-hand side takes 0 steps."""
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    rng = np.random.default_rng(5)
+    G = rng.standard_normal((70, 70))
+    A = G @ G.T + np.eye(70)
+    Md = np.diag(1.0 / np.diag(A))
+    b = np.zeros((70, 2))
+    b[:, 0] = rng.standard_normal(70)
+    x, it, res = pcg.pcg(lambda X: A @ X, lambda R: Md @ R, b, 1e-11, 500)
+    xs, info = spla.cg(A, b[:, 0], rtol=1e-13, maxiter=2000, M=Md)
+    assert info == 0 and res[0] <= 1e-11 * 10
+    cond = np.linalg.cond(A)
+    assert np.linalg.norm(x[:, 0] - xs) <= 1e-10 * cond * np.linalg.norm(xs)
+    assert it[1] == 0 and not x[:, 1].any()
