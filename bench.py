@@ -498,6 +498,46 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_pcg(args, w):
+    """Section 6's use of a low-accuracy factor: PCG on the eps = 1e-8 compressed matrix of the workload,
+    preconditioned by the factor of A + eps I at eps = 1e-2 and 1e-4, to ||Ax - b|| / ||b|| <= 1e-6."""
+    import torch
+    import paper_2108_11932_gb300 as T
+    T.build()
+    ctx = T.Context(0)
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    perm = T.kd_order(x, w["b"])
+    pts = torch.tensor(x[perm], device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    o = T.default_opts(bs=w["bs"], seed=w["seed"])
+    e0, e1 = ev(), ev()
+    e0.record(ctx.stream)
+    A = ctx.compress_ordered(pts, perm, w["b"], 1e-8, w["ell"], w["nugget"], o)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    out = {"workload": _workload_desc(w, 1e-8, "FP64") + "; operator compressed at eps=1e-8",
+           "operator_compress_s": e0.elapsed_time(e1) / 1e3, "operator_mean_rank": A.info()["mean_rank"],
+           "tol": 1e-6, "maxit": 300, "preconditioners": {}}
+    B = T.fortran(torch.tensor(inputs.rhs(w["N"], 1, 1), device="cuda"))
+    for pe in (1e-2, 1e-4):
+        e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+        e0.record(ctx.stream)
+        F = ctx.compress_ordered(pts, perm, w["b"], pe, w["ell"], w["nugget"], o)
+        e1.record(ctx.stream)
+        F.potrf(pe, T.default_opts(bs=w["bs"], seed=w["seed"], compensation=T.COMP_SHIFT, shift=pe))
+        e2.record(ctx.stream)
+        X, it, rr = A.pcg(F, B, tol=1e-6, maxit=300)
+        e3.record(ctx.stream)
+        torch.cuda.synchronize()
+        out["preconditioners"][f"eps{pe:g}"] = {
+            "compress_s": e0.elapsed_time(e1) / 1e3, "factor_s": e1.elapsed_time(e2) / 1e3,
+            "pcg_s": e2.elapsed_time(e3) / 1e3, "iterations": it[0], "true_relres": rr[0],
+            "factor_mean_rank": F.info()["mean_rank"]}
+        F.free()
+    A.free()
+    print(json.dumps(out), flush=True)
+
+
 def run_serve(args, ctx=None, n=None, quiet=False):
     """Serving: Poisson arrivals, continuous batching; latency arrival -> result."""
     import paper_2108_11932_gb300 as T
@@ -602,7 +642,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--profile-compress", action="store_true",
                     help="phases mode: profile the compression as well as the factorization")
-    ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve", "peaks", "phases"])
+    ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve", "peaks", "phases", "pcg"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-chunk", type=int, default=64, help="matrices built and factored together")
     ap.add_argument("--requests", type=int, default=200)
@@ -623,6 +663,8 @@ def main():
         run_peaks(args)
     elif args.mode == "phases":
         run_phases(args, w, args.eps)
+    elif args.mode == "pcg":
+        run_pcg(args, w)
     else:
         run_ours(args, w, args.eps)
 
