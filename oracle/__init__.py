@@ -20,8 +20,9 @@ Modules
             Section 5.3).
   compress  truncated-SVD compression and ARA (Algorithm 1) with BCGS2 +
             Cholesky-QR orthogonalization.
-  tlr       left-looking TLR Cholesky (Algorithm 6) and LDL^T (Algorithm 10),
-            TLR triangular solve (Algorithm 7), log-determinant, matvec.
+  tlr       left-looking TLR Cholesky (Algorithm 6), its tile-pivoted form
+            (Algorithm 9) and LDL^T (Algorithm 10), TLR triangular solve
+            (Algorithm 7), log-determinant, matvec.
   measures  backward error by power iteration and solve residual (Section 6).
   pcg       preconditioned CG with a TLR factor as the preconditioner (Section 6).
 """

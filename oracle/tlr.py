@@ -48,6 +48,7 @@ class TLR:
     d: list | None = None                      # LDL^T: D_k as vectors
     kind: str = "A"                            # "A", "chol" or "ldlt"
     rounds: dict = field(default_factory=dict)  # ARA rounds per tile (diagnostics)
+    tile_perm: list | None = None              # pivoted factor: original tile at each position
 
     def rank(self, i: int, j: int) -> int:
         return self.U[(i, j)].shape[1]
@@ -166,6 +167,83 @@ def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: i
                 Vik = Vik / F.d[k][:, None]                  # batchIDMult
             F.U[(i, k)], F.V[(i, k)] = Q, Vik.reshape(b, -1)
             F.rounds[(i, k)] = t
+    return F
+
+
+def _row_update(F: TLR, i: int, k: int) -> np.ndarray:
+    """D_i = sum_{j<k} L(i,j) L(i,j)^T for a row i >= k of a Cholesky factor in progress (Algorithm 9
+    keeps these sums for every remaining diagonal tile, denseUpdates)."""
+    b = F.b
+    Di = np.zeros((b, b))
+    for j in range(k):
+        U, V = F.U[(i, j)], F.V[(i, j)]
+        Di += U @ (V.T @ V) @ U.T
+    return Di
+
+
+def _select_pivot(Ad: list, D: dict, k: int) -> int:
+    """selectPivot (Algorithm 9, Section 5.2): the remaining diagonal tile whose updated value
+    A(i,i) - D_i has the largest Frobenius norm; the first such tile on ties."""
+    nrm = [np.linalg.norm(Ad[i] - D[i]) for i in range(k, len(Ad))]
+    return k + int(np.argmax(nrm))
+
+
+def _swap_tiles(F: TLR, Ad: list, At: dict, k: int, p: int) -> dict:
+    """pivotRowColumn (Algorithm 9): exchange tile rows and columns k and p (k < p) of the symmetric
+    trailing matrix and rows k and p of the factored columns.  At holds the trailing lower tiles
+    (i, j), i > j >= k, as (U, V) with A(i,j) = U V^T; a tile that crosses to the upper triangle is
+    stored transposed (U and V exchanged)."""
+    sig = lambda i: p if i == k else (k if i == p else i)
+    Ad[k], Ad[p] = Ad[p], Ad[k]
+    for j in range(k):
+        F.U[(k, j)], F.U[(p, j)] = F.U[(p, j)], F.U[(k, j)]
+        F.V[(k, j)], F.V[(p, j)] = F.V[(p, j)], F.V[(k, j)]
+    new = {}
+    for (i, j) in At:
+        a, c = sig(i), sig(j)
+        U, V = At[(a, c)] if a > c else At[(c, a)][::-1]
+        new[(i, j)] = (U, V)
+    return new
+
+
+def factor_pivoted(A: TLR, eps: float, compressor: str = "svd", bs: int = 16, seed: int = 0) -> TLR:
+    """Pivoted left-looking TLR Cholesky (Algorithm 9, Section 5.2): at step k every remaining diagonal
+    tile's update D_i is formed, the tile with the largest ||A(i,i) - D_i||_F becomes the pivot, tile
+    rows and columns k and pivot are exchanged, and the step continues as in Algorithm 6.  Returns the
+    factor of P A P^T; F.perm (point order) includes the tile exchanges and F.tile_perm[k] is the
+    original tile at position k, so solves and products in the original order apply A^{-1} and A.
+    Requires N to be a multiple of b (no padded tile to move)."""
+    b, nb = A.b, A.nb
+    assert A.N == nb * b, "pivoted factorization needs N divisible by b"
+    F = TLR(N=A.N, b=b, nb=nb, perm=A.perm.copy(), xo=A.xo, kind="chol")
+    Ad = [t.copy() for t in A.diag]
+    At = {(i, j): (A.U[(i, j)], A.V[(i, j)]) for (i, j) in A.U}
+    tp = list(range(nb))
+    for k in range(nb):
+        D = {i: _row_update(F, i, k) for i in range(k, nb)}
+        p = _select_pivot(Ad, D, k)
+        if p != k:
+            At = _swap_tiles(F, Ad, At, k, p)
+            D[k], D[p] = D[p], D[k]
+            tp[k], tp[p] = tp[p], tp[k]
+        try:
+            Lkk = Dn.cholesky(Ad[k] - D[k])
+        except Dn.NotPositiveDefinite as ex:
+            ex.tile = k
+            raise
+        F.diag.append(Lkk)
+        comp = _compressor(compressor, eps, bs, seed, STREAM_FACTOR, k, b)
+        for i in range(k + 1, nb):
+            U0, V0 = At[(i, k)]
+            T = U0 @ V0.T
+            for j in range(k):
+                T -= F.U[(i, j)] @ ((F.V[(i, j)].T @ F.V[(k, j)]) @ F.U[(k, j)].T)
+            Q, B, t = comp(T)
+            F.U[(i, k)], F.V[(i, k)] = Q, Dn.solve_lower(Lkk, B)
+            F.rounds[(i, k)] = t
+        At = {key: v for key, v in At.items() if key[1] > k}
+    F.tile_perm = tp
+    F.perm = np.concatenate([A.perm[t * b:(t + 1) * b] for t in tp])
     return F
 
 

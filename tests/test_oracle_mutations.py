@@ -141,3 +141,39 @@ def test_schur_compensation_off_the_diagonal_is_caught(monkeypatch):
         r = np.diag(ok)
         return ok + 0.5 * (np.outer(np.sqrt(r), np.sqrt(r)) - np.diag(r))
     assert not _schur_mutant(monkeypatch, spread)
+
+
+def _pivot_mutant(monkeypatch, name, fn):
+    from test_oracle_pins import pivoted_pins_hold
+    assert pivoted_pins_hold()
+    monkeypatch.setattr(tlr, name, fn)
+    return pivoted_pins_hold()
+
+
+def test_pivot_by_smallest_tile_is_caught(monkeypatch):
+    def smallest(Ad, D, k):
+        return k + int(np.argmin([np.linalg.norm(Ad[i] - D[i]) for i in range(k, len(Ad))]))
+    assert not _pivot_mutant(monkeypatch, "_select_pivot", smallest)
+
+
+def test_pivot_without_exchanging_factored_rows_is_caught(monkeypatch):
+    orig = tlr._swap_tiles
+
+    def keep_rows(F, Ad, At, k, p):
+        saved = {j: (F.U[(k, j)], F.V[(k, j)], F.U[(p, j)], F.V[(p, j)]) for j in range(k)}
+        out = orig(F, Ad, At, k, p)
+        for j, (uk, vk, up, vp) in saved.items():
+            F.U[(k, j)], F.V[(k, j)], F.U[(p, j)], F.V[(p, j)] = uk, vk, up, vp
+        return out
+    assert not _pivot_mutant(monkeypatch, "_swap_tiles", keep_rows)
+
+
+def test_pivot_without_transposing_crossing_tiles_is_caught(monkeypatch):
+    def no_transpose(F, Ad, At, k, p):
+        sig = lambda i: p if i == k else (k if i == p else i)
+        Ad[k], Ad[p] = Ad[p], Ad[k]
+        for j in range(k):
+            F.U[(k, j)], F.U[(p, j)] = F.U[(p, j)], F.U[(k, j)]
+            F.V[(k, j)], F.V[(p, j)] = F.V[(p, j)], F.V[(k, j)]
+        return {(i, j): (At[(sig(i), sig(j))] if sig(i) > sig(j) else At[(sig(j), sig(i))]) for (i, j) in At}
+    assert not _pivot_mutant(monkeypatch, "_swap_tiles", no_transpose)

@@ -331,3 +331,73 @@ def test_pcg_matches_scipy_cg_and_handles_a_zero_column():
     cond = np.linalg.cond(A)
     assert np.linalg.norm(x[:, 0] - xs) <= 1e-10 * cond * np.linalg.norm(xs)
     assert it[1] == 0 and not x[:, 1].any()
+
+
+def _dense_block_pivoted_order(Ad: np.ndarray, b: int) -> list:
+    """The definition of tile pivoting written densely: at each step the diagonal block of the current
+    Schur complement with the largest Frobenius norm is moved to the front, then eliminated."""
+    S = Ad.copy()
+    nb = S.shape[0] // b
+    order = list(range(nb))
+    blk = lambda i: slice(i * b, (i + 1) * b)
+    for k in range(nb):
+        nrm = [np.linalg.norm(S[blk(i), blk(i)]) for i in range(k, nb)]
+        p = k + int(np.argmax(nrm))
+        if p != k:
+            idx = np.arange(nb * b)
+            idx[blk(k)], idx[blk(p)] = np.arange(p * b, (p + 1) * b), np.arange(k * b, (k + 1) * b)
+            S = S[np.ix_(idx, idx)]
+            order[k], order[p] = order[p], order[k]
+        L = np.linalg.cholesky(S[blk(k), blk(k)])
+        R = np.linalg.solve(L, S[blk(k), (k + 1) * b:]).T        # rows below, times L^-T
+        S[(k + 1) * b:, (k + 1) * b:] -= R @ R.T
+    return order
+
+
+def pivoted_pins_hold() -> bool:
+    """Algorithm 9 pinned: at eps = 1e-13 the pivoted TLR factor reproduces P A P^T, its solve and logdet
+    those of the dense matrix, and its tile order is the dense block-pivoted Cholesky's."""
+    x = inputs.points(1024, 2, 3)
+    b = 128
+    A = tlr.build(x, b, 1e-13, 0.1, 1e-4)
+    try:
+        F = tlr.factor_pivoted(A, 1e-13)
+    except dense.NotPositiveDefinite:
+        return False
+    Ad = kernel.dense(x, 0.1, 1e-4)
+    L = F.to_dense()
+    P = F.perm
+    if np.linalg.norm(L @ L.T - Ad[np.ix_(P, P)]) > 1e-10 * np.linalg.norm(Ad):
+        return False
+    Y = inputs.rhs(1024, 2, 5)
+    Xd = np.linalg.solve(Ad, Y)
+    if np.linalg.norm(tlr.solve(F, Y) - Xd) > 1e-9 * np.linalg.norm(Xd):
+        return False
+    if abs(tlr.logdet(F) - np.linalg.slogdet(Ad)[1]) > 1e-9 * abs(np.linalg.slogdet(Ad)[1]):
+        return False
+    Ako = Ad[np.ix_(A.perm, A.perm)]
+    return list(F.tile_perm) == _dense_block_pivoted_order(Ako, b) and F.tile_perm != list(range(A.nb))
+
+
+def test_pivoted_tlr_cholesky_pins():
+    assert pivoted_pins_hold()
+
+
+def test_pivoting_is_idle_when_updated_diagonal_tiles_decrease():
+    """Tiles scaled by 4^-k: every updated diagonal tile is smaller than the one before, so no exchange
+    happens and the pivoted factor is Algorithm 6's."""
+    x = inputs.points(768, 2, 6)
+    b = 128
+    A = tlr.build(x, b, 1e-10, 0.1, 1e-4)
+    s = 4.0 ** -np.arange(A.nb)
+    A.diag = [A.diag[k] * s[k] ** 2 for k in range(A.nb)]
+    for (i, j) in list(A.U):
+        A.U[(i, j)] = A.U[(i, j)] * s[i]
+        A.V[(i, j)] = A.V[(i, j)] * s[j]
+    F = tlr.factor_pivoted(A, 1e-10)
+    G = tlr.factor(A, 1e-10)
+    assert F.tile_perm == list(range(A.nb))
+    for k in range(A.nb):
+        assert np.array_equal(F.diag[k], G.diag[k])
+    for key in G.U:
+        assert np.array_equal(F.U[key], G.U[key]) and np.array_equal(F.V[key], G.V[key])
