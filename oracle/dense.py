@@ -76,3 +76,39 @@ def solve_upper_t(L: np.ndarray, B: np.ndarray, unit: bool = False) -> np.ndarra
         if not unit:
             X[i] /= L[i, i]
     return X[:, 0] if vec else X
+
+
+def _modify_eigenvalues(w: np.ndarray, delta: float) -> np.ndarray:
+    """modifySPD (Algorithm 8) on one pivot block's eigenvalues: those below delta are raised to it."""
+    return np.maximum(w, delta)
+
+
+def modified_cholesky(A: np.ndarray, delta: float | None = None):
+    """ModChol (Algorithm 8, Section 5.1.2): the Cholesky factor of A if A is positive definite
+    (E = 0); otherwise the factor of A + E from a symmetric indefinite factorization
+    A = Lp D Lp^T (Bunch-Kaufman pivoting, SciPy's ldl as one step; Lp is a row-permuted unit lower
+    triangle) whose 1x1 and 2x2 diagonal blocks are modified as in Cheng and Higham (1998): each
+    block's eigenvalues are raised to at least delta (default sqrt(u) ||A||_inf, their choice),
+    giving D + F positive definite and A + E = Lp (D + F) Lp^T.  Returns (L, ||E||_2)."""
+    try:
+        return cholesky(A), 0.0
+    except NotPositiveDefinite:
+        pass
+    import scipy.linalg as sl
+    n = A.shape[0]
+    if delta is None:
+        delta = np.sqrt(np.finfo(np.float64).eps / 2) * np.abs(A).sum(axis=1).max()
+    Lp, D, _ = sl.ldl(A, lower=True)
+    DF = np.zeros_like(D)
+    i = 0
+    while i < n:
+        if i + 1 < n and D[i + 1, i] != 0.0:  # a 2 x 2 block
+            w, Q = np.linalg.eigh(D[i:i + 2, i:i + 2])
+            DF[i:i + 2, i:i + 2] = (Q * _modify_eigenvalues(w, delta)) @ Q.T
+            i += 2
+        else:
+            DF[i, i] = _modify_eigenvalues(np.array([D[i, i]]), delta)[0]
+            i += 1
+    At = Lp @ DF @ Lp.T
+    At = 0.5 * (At + At.T)
+    return cholesky(At), float(np.linalg.norm(At - A, 2))

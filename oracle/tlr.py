@@ -129,9 +129,11 @@ def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: i
            seed: int = 0, compensation: str | None = None, shift: float = 0.0) -> TLR:
     """Left-looking TLR Cholesky (Algorithm 6) or LDL^T (Algorithm 10); returns the factor.
 
-    compensation: None, "shift" (A + shift*I, Section 5.1) or "schur"
+    compensation: None, "shift" (A + shift*I, Section 5.1), "schur"
     (A(k,k) - D_k + diag(rowsum|D_k - Dbar_k|), Section 5.1.1, with Dbar_k the
-    compressor's eps-approximation Q Q^T D_k Q Q^T).
+    compressor's eps-approximation Q Q^T D_k Q Q^T) or "modchol" (Cholesky only:
+    a diagonal tile that is not positive definite is factored by the modified
+    Cholesky of Algorithm 8, Section 5.1.2).
     Raises dense.NotPositiveDefinite with attribute `.tile` on breakdown.
     """
     b, nb = A.b, A.nb
@@ -148,6 +150,8 @@ def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: i
             if ldl:
                 Lkk, dk = Dn.ldlt(Akk)
                 F.d[k] = dk
+            elif compensation == "modchol":
+                Lkk, _ = Dn.modified_cholesky(Akk)   # Algorithm 8 in place of the dense Cholesky
             else:
                 Lkk = Dn.cholesky(Akk)
         except Dn.NotPositiveDefinite as ex:

@@ -177,3 +177,12 @@ def test_pivot_without_transposing_crossing_tiles_is_caught(monkeypatch):
             F.V[(k, j)], F.V[(p, j)] = F.V[(p, j)], F.V[(k, j)]
         return {(i, j): (At[(sig(i), sig(j))] if sig(i) > sig(j) else At[(sig(j), sig(i))]) for (i, j) in At}
     assert not _pivot_mutant(monkeypatch, "_swap_tiles", no_transpose)
+
+
+def test_modified_cholesky_shifting_instead_of_clamping_is_caught(monkeypatch):
+    """A plausible variant adds delta to every block eigenvalue instead of raising only those below it."""
+    from test_oracle_pins import test_modified_cholesky_closed_forms
+    test_modified_cholesky_closed_forms()
+    monkeypatch.setattr(dense, "_modify_eigenvalues", lambda w, d: w + d)
+    with pytest.raises((AssertionError, dense.NotPositiveDefinite)):
+        test_modified_cholesky_closed_forms()

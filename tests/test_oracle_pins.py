@@ -401,3 +401,63 @@ def test_pivoting_is_idle_when_updated_diagonal_tiles_decrease():
         assert np.array_equal(F.diag[k], G.diag[k])
     for key in G.U:
         assert np.array_equal(F.U[key], G.U[key]) and np.array_equal(F.V[key], G.V[key])
+
+
+def test_modified_cholesky_closed_forms():
+    """Algorithm 8 with Cheng-Higham's modification: positive definite input -> plain Cholesky, E = 0;
+    a diagonal input -> entries raised to delta; a 2x2 pivot block [[1,2],[2,1]] (eigenvalues 3, -1)
+    -> the block with eigenvalues 3 and delta."""
+    rng = np.random.default_rng(1)
+    G = rng.standard_normal((20, 20))
+    S = G @ G.T + np.eye(20)
+    L, e = dense.modified_cholesky(S)
+    Lr = np.linalg.cholesky(S)
+    assert e == 0.0 and np.abs(L - Lr).max() <= 1e-13 * np.abs(Lr).max()
+    a = np.array([3.0, -1.0, 2.0, -1e-12, 5.0])
+    L, e = dense.modified_cholesky(np.diag(a), delta=1e-3)
+    assert np.allclose(L @ L.T, np.diag(np.maximum(a, 1e-3)), rtol=1e-14, atol=0)
+    assert abs(e - 1.001) <= 1e-12
+    A = np.array([[1.0, 2.0, 0.0], [2.0, 1.0, 0.0], [0.0, 0.0, -3.0]])
+    dl = 1e-2
+    L, e = dense.modified_cholesky(A, delta=dl)
+    ref = np.zeros((3, 3))
+    ref[:2, :2] = [[(3 + dl) / 2, (3 - dl) / 2], [(3 - dl) / 2, (3 + dl) / 2]]
+    ref[2, 2] = dl
+    assert np.allclose(L @ L.T, ref, rtol=0, atol=1e-14)
+
+
+def modchol_pins_hold() -> bool:
+    """In the TLR factorization (Algorithm 6 with Algorithm 8 for the diagonal tiles) the modification
+    stays inside the tile it repaired: A - s I, made indefinite by s just above lambda_min(A), fails the
+    plain factorization at tile t; with modified Cholesky L L^T equals A - s I everywhere except block
+    (t, t), where the difference is the E of the modified Cholesky of that tile's exact Schur
+    complement, and L L^T is positive definite."""
+    x = inputs.points(768, 2, 9)
+    b = 128
+    Ad = kernel.dense(x, 0.1, 1e-4)
+    sh = np.linalg.eigvalsh(Ad).min() + 1e-5
+    A = tlr.build(x, b, 1e-12, 0.1, 1e-4 - sh)
+    try:
+        tlr.factor(A, 1e-12)
+        return False
+    except dense.NotPositiveDefinite as ex:
+        t = ex.tile
+    try:
+        F = tlr.factor(A, 1e-12, compensation="modchol")
+    except dense.NotPositiveDefinite:
+        return False
+    L = F.to_dense()
+    As = (Ad - sh * np.eye(768))[np.ix_(F.perm, F.perm)]
+    Dif = L @ L.T - As
+    blk = slice(t * b, (t + 1) * b)
+    off = Dif.copy()
+    off[blk, blk] = 0.0
+    n0 = t * b
+    S = As[blk, blk] - As[blk, :n0] @ np.linalg.solve(As[:n0, :n0], As[:n0, blk]) if t else As[blk, blk]
+    _, e = dense.modified_cholesky(S)
+    return (np.abs(off).max() <= 1e-9 * np.abs(As).max() and e > 0
+            and abs(np.linalg.norm(Dif[blk, blk], 2) - e) <= 1e-6 * e and np.linalg.eigvalsh(L @ L.T).min() > 0)
+
+
+def test_modified_cholesky_in_tlr_factor_pins():
+    assert modchol_pins_hold()
