@@ -53,6 +53,10 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     assert so.tlr_compress(None, None, 0, 2, None, 0, 0.0, None, None) == lib.ERR_ARG
     assert so.tlr_potrf(None, None, 1e-6, None) == lib.ERR_ARG
     assert so.tlr_destroy(None) == lib.ERR_ARG
+    assert so.tlr_solve(None, None, 1, None, 1) == lib.ERR_ARG
+    it = (ctypes.c_int * 1)()
+    rr = (ctypes.c_double * 1)()
+    assert so.tlr_pcg(None, None, None, 1, None, 1, None, 1, 1e-6, 10, it, rr) == lib.ERR_ARG
 
 
 @pytest.mark.parametrize("N,d,b,seed", [(4096, 2, 256, 0), (5000, 3, 512, 1), (1000, 1, 64, 3), (777, 2, 100, 4),
