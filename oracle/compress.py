@@ -5,6 +5,9 @@ svd_truncate: the reference compressor prescribed for the oracle: keep the
   Section 6 states), so ||T - Q B^T||_2 <= eps
   (Eckart-Young).  Q = U_r (orthonormal), B = V_r Sigma_r.
 
+trim: ARA -> SVD rank trimming of a compressed tile (Q B^T -> its truncated
+  SVD, through the SVD of the short factor B).
+
 ara: Adaptive Randomized Approximation, Algorithm 1 (Section 3.1), applied to
   a dense operand T.  Steps in the paper's order: draw Omega (b x bs), sample
   Y = T Omega, orthog(Q, Y) = two iterations of block Gram-Schmidt against Q,
@@ -44,6 +47,17 @@ def svd_truncate(T: np.ndarray, eps: float) -> tuple[np.ndarray, np.ndarray]:
     U, s, Vt = np.linalg.svd(T, full_matrices=False)
     r = int(np.count_nonzero(s > eps))
     return U[:, :r].copy(), (Vt[:r].T * s[:r]).copy()
+
+
+def trim(Q: np.ndarray, B: np.ndarray, eps: float) -> tuple[np.ndarray, np.ndarray]:
+    """ARA -> SVD rank trimming of a tile Q B^T with orthonormal Q (b x r): the SVD of the short factor,
+    B = W S Z^T, gives Q B^T = (Q Z) S W^T, whose singular values are S; keep those above eps.
+    Returns (Q Z_r, W_r S_r): the rank the truncated SVD of the tile would keep, error <= eps."""
+    if B.shape[1] == 0:
+        return Q.copy(), B.copy()
+    W, sv, Zt = np.linalg.svd(B, full_matrices=False)
+    r = int(np.count_nonzero(sv > eps))
+    return Q @ Zt[:r].T, W[:, :r] * sv[:r]
 
 
 def chol_drop(G: np.ndarray, thr2: float, tau: float = TAU_DROP) -> tuple[np.ndarray, list[int]]:

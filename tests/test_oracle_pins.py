@@ -461,3 +461,21 @@ def modchol_pins_hold() -> bool:
 
 def test_modified_cholesky_in_tlr_factor_pins():
     assert modchol_pins_hold()
+
+
+def test_trim_gives_the_truncated_svd_rank_and_error():
+    """Trimming an ARA tile keeps exactly the ranks of the tile's own truncated SVD (Eckart-Young: the
+    error is the first dropped singular value), and never more than ARA found."""
+    x = inputs.points(512, 2, 7)
+    xo = x[kdtree.kd_order(x, 128)]
+    for (i, j) in [(1, 0), (3, 0), (2, 1)]:
+        T = kernel.tile(xo, i, j, 128, 0.1, 1e-4)
+        for eps in (1e-6, 1e-3):
+            Q, B, _ = compress.ara_dense(T, 16, eps, lambda t: philox.omega(3, 1, 0, t, 128, 16))
+            Qt, Bt = compress.trim(Q, B, eps)
+            sv = np.linalg.svd(T, compute_uv=False)
+            r_svd = int(np.count_nonzero(sv > eps))
+            assert Qt.shape[1] <= Q.shape[1]
+            assert abs(Qt.shape[1] - r_svd) <= 1          # the ARA basis captures T to ~eps / 10
+            assert np.linalg.norm(T - Qt @ Bt.T, 2) <= 1.01 * eps
+            assert np.allclose(Qt.T @ Qt, np.eye(Qt.shape[1]), atol=1e-12)
