@@ -636,7 +636,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--workload", default=WORKLOAD, choices=list(inputs.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--oracle-tiles", type=int, default=4)
+    ap.add_argument("--oracle-tiles", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
