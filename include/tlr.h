@@ -17,7 +17,7 @@
  *   - Point order: callers pass points, right-hand sides and vectors in their
  *     ORIGINAL order; the library keeps the KD-tree permutation internally.
  *   - A failed factorization leaves the matrix in state FAILED; every later
- *     call on it except tlr_info/tlr_free returns TLR_ERR_STATE.
+ *     call on it except tlr_get_info/tlr_free returns TLR_ERR_STATE.
  */
 #ifndef TLR_GB300_H
 #define TLR_GB300_H
@@ -102,7 +102,12 @@ tlr_status tlr_destroy(tlr_ctx* ctx);
  * matrix tile by tile on the device and compress every lower off-diagonal b x b
  * tile with batched ARA (Algorithm 1) to the absolute 2-norm threshold eps.
  * Diagonal tiles stay dense.  If b does not divide N the last tile is padded
- * with identity rows/columns.  *A receives a new matrix in state "A". */
+ * with identity rows/columns.  *A receives a new matrix in state "A".
+ * Entries are evaluated in 64-bit fixed point from the points on a per-matrix
+ * grid (no FP64 arithmetic), within 4 x 2^-52 (1 + |log a_ij|) relative of the
+ * FP64 formula; entries below 2^-1020 are 0.  Errors: TLR_ERR_ARG (null
+ * pointers, N <= 0, d outside 1..3, b < 1, eps <= 0, ell <= 0, nugget < 0,
+ * opts.bs > min(64, b)), TLR_ERR_NOMEM. */
 tlr_status tlr_compress(tlr_ctx* ctx, const double* points_host, int64_t N, int d,
                         const tlr_kernel* kernel, int b, double eps, const tlr_opts* opts,
                         tlr_mat** A);
