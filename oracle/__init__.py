@@ -24,5 +24,7 @@ Modules
             (Algorithm 9) and LDL^T (Algorithm 10), TLR triangular solve
             (Algorithm 7), log-determinant, matvec.
   measures  backward error by power iteration and solve residual (Section 6).
+  cmatvec   the exact kernel product in plain C with OpenMP (kernel_matvec.c), for the
+            power iterations at full size.
   pcg       preconditioned CG with a TLR factor as the preconditioner (Section 6).
 """

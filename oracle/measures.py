@@ -24,6 +24,29 @@ def power_norm(apply, x0: np.ndarray, iters: int = 30) -> float:
     return lam
 
 
+def power_norms(apply_block, X0: np.ndarray, iters: int = 30) -> np.ndarray:
+    """Independent power iterations, one per column of X0 (N x m): column c estimates ||M_c||_2 of
+    its own symmetric operator.  apply_block(V) returns [M_0 v_0 | ... | M_{m-1} v_{m-1}], so that
+    one pass over an expensive shared operand (the exact kernel matrix) serves every column.
+    Each column follows power_norm's steps: w = M v, lam = ||w||, v = w / lam (0 stays 0)."""
+    V = np.array(X0, dtype=np.float64, copy=True).reshape(X0.shape[0], -1)
+    V /= np.linalg.norm(V, axis=0)
+    m = V.shape[1]
+    lam = np.zeros(m)
+    live = np.ones(m, dtype=bool)
+    for _ in range(iters):
+        W = apply_block(V)
+        for c in range(m):
+            if not live[c]:
+                continue
+            lam[c] = float(np.linalg.norm(W[:, c]))
+            if lam[c] == 0.0:
+                live[c] = False
+            else:
+                V[:, c] = W[:, c] / lam[c]
+    return lam
+
+
 def backward_error(apply_A, apply_F, x0: np.ndarray, iters: int = 30) -> float:
     """||A - F||_2 / ||A||_2 with F the factored product (L L^T or L D L^T)."""
     nE = power_norm(lambda v: apply_A(v) - apply_F(v), x0, iters)

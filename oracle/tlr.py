@@ -88,33 +88,54 @@ def _compressor(name: str, eps: float, bs: int, seed: int, stream: int, k: int, 
 
 
 def build(points: np.ndarray, b: int, eps: float, ell: float, nugget: float,
-          compressor: str = "svd", bs: int = 16, seed: int = 0) -> TLR:
-    """KD-order the points and compress every lower off-diagonal tile to eps (Section 6)."""
+          compressor: str = "svd", bs: int = 16, seed: int = 0, mapper=map) -> TLR:
+    """KD-order the points and compress every lower off-diagonal tile to eps (Section 6).
+
+    mapper: how the independent tiles of one block column are visited (the builtin map, or the
+    map of a thread pool for large cases); every tile is computed the same way either way."""
     points = np.asarray(points, dtype=np.float64)
     N = points.shape[0]
     perm = kdtree.kd_order(points, b)
     xo = points[perm]
     nb = max(1, -(-N // b))
     A = TLR(N=N, b=b, nb=nb, perm=perm, xo=xo)
-    A.diag = [kernel.tile(xo, k, k, b, ell, nugget) for k in range(nb)]
+    A.diag = list(mapper(lambda k: kernel.tile(xo, k, k, b, ell, nugget), range(nb)))
     comp = _compressor(compressor, eps, bs, seed, STREAM_COMPRESS, 0, b)
     for j in range(nb):
-        for i in range(j + 1, nb):
-            Q, B, t = comp(kernel.tile(xo, i, j, b, ell, nugget))
+        rows = range(j + 1, nb)
+        for i, (Q, B, t) in zip(rows, mapper(lambda i: comp(kernel.tile(xo, i, j, b, ell, nugget)), rows)):
             A.U[(i, j)], A.V[(i, j)] = Q, B
             A.rounds[(i, j)] = t
     return A
 
 
+def _dv(F: TLR, j: int, V: np.ndarray) -> np.ndarray:
+    """[D_j] V: V itself for a Cholesky factor, D_j V for LDL^T (Equation 3)."""
+    return V if F.d is None else F.d[j][:, None] * V
+
+
+def _update_sum(F: TLR, i: int, l: int, k: int) -> np.ndarray:
+    """sum_{j<k} L(i,j) [D_j] L(l,j)^T = sum_j U_ij (V_ij^T [D_j] V_lj) U_lj^T, formed densely.
+
+    The sum over j is evaluated as one product of the concatenated factors,
+    [U_i0 M_0 | ... | U_i,k-1 M_k-1] [U_l0 | ... | U_l,k-1]^T with M_j = V_ij^T [D_j] V_lj:
+    the same sum written as a block inner product."""
+    b = F.b
+    if k == 0:
+        return np.zeros((b, b))
+    left = np.hstack([F.U[(i, j)] @ (F.V[(i, j)].T @ _dv(F, j, F.V[(l, j)])) for j in range(k)])
+    right = np.hstack([F.U[(l, j)] for j in range(k)])
+    return left @ right.T
+
+
 def _diag_update(F: TLR, k: int) -> np.ndarray:
     """D_k = sum_{j<k} L(k,j) [D_j] L(k,j)^T, formed densely (updateDense, Section 4.3)."""
-    b = F.b
-    Dk = np.zeros((b, b))
-    for j in range(k):
-        U, V = F.U[(k, j)], F.V[(k, j)]
-        mid = V.T @ (V if F.d is None else F.d[j][:, None] * V)
-        Dk += U @ mid @ U.T
-    return Dk
+    return _update_sum(F, k, k, k)
+
+
+def _update_tile(A: TLR, F: TLR, i: int, k: int) -> np.ndarray:
+    """Equation 1 / 3, formed densely: T = A(i,k) - sum_{j<k} U_ij V_ij^T [D_j] V_kj U_kj^T."""
+    return A.U[(i, k)] @ A.V[(i, k)].T - _update_sum(F, i, k, k)
 
 
 def _schur_compensation(Dk: np.ndarray, comp) -> np.ndarray:
@@ -126,7 +147,7 @@ def _schur_compensation(Dk: np.ndarray, comp) -> np.ndarray:
 
 
 def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: int = 16,
-           seed: int = 0, compensation: str | None = None, shift: float = 0.0) -> TLR:
+           seed: int = 0, compensation: str | None = None, shift: float = 0.0, mapper=map) -> TLR:
     """Left-looking TLR Cholesky (Algorithm 6) or LDL^T (Algorithm 10); returns the factor.
 
     compensation: None, "shift" (A + shift*I, Section 5.1), "schur"
@@ -134,6 +155,8 @@ def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: i
     compressor's eps-approximation Q Q^T D_k Q Q^T) or "modchol" (Cholesky only:
     a diagonal tile that is not positive definite is factored by the modified
     Cholesky of Algorithm 8, Section 5.1.2).
+    mapper: how the independent tiles below the diagonal of one column are visited (builtin map or
+    a thread pool's map); each tile's arithmetic is the same either way.
     Raises dense.NotPositiveDefinite with attribute `.tile` on breakdown.
     """
     b, nb = A.b, A.nb
@@ -159,17 +182,17 @@ def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: i
             raise
         F.diag.append(Lkk)
         comp = _compressor(compressor, eps, bs, seed, STREAM_FACTOR, k, b)
-        for i in range(k + 1, nb):
-            # Equation 1 / 3: T = A(i,k) - sum_j U_ij V_ij^T [D_j] V_kj U_kj^T
-            T = A.U[(i, k)] @ A.V[(i, k)].T
-            for j in range(k):
-                Vk = F.V[(k, j)] if F.d is None else F.d[j][:, None] * F.V[(k, j)]
-                T -= F.U[(i, j)] @ ((F.V[(i, j)].T @ Vk) @ F.U[(k, j)].T)
-            Q, B, t = comp(T)
-            Vik = Dn.solve_lower(Lkk, B, unit=ldl)          # batchTrsm
+
+        def column_tile(i):
+            Q, B, t = comp(_update_tile(A, F, i, k))          # Equation 1 / 3, compressed
+            Vik = Dn.solve_lower(Lkk, B, unit=ldl)           # batchTrsm
             if ldl:
                 Vik = Vik / F.d[k][:, None]                  # batchIDMult
-            F.U[(i, k)], F.V[(i, k)] = Q, Vik.reshape(b, -1)
+            return Q, Vik.reshape(b, -1), t
+
+        rows = range(k + 1, nb)
+        for i, (Q, Vik, t) in zip(rows, mapper(column_tile, rows)):
+            F.U[(i, k)], F.V[(i, k)] = Q, Vik
             F.rounds[(i, k)] = t
     return F
 
@@ -177,12 +200,7 @@ def factor(A: TLR, eps: float, ldl: bool = False, compressor: str = "svd", bs: i
 def _row_update(F: TLR, i: int, k: int) -> np.ndarray:
     """D_i = sum_{j<k} L(i,j) L(i,j)^T for a row i >= k of a Cholesky factor in progress (Algorithm 9
     keeps these sums for every remaining diagonal tile, denseUpdates)."""
-    b = F.b
-    Di = np.zeros((b, b))
-    for j in range(k):
-        U, V = F.U[(i, j)], F.V[(i, j)]
-        Di += U @ (V.T @ V) @ U.T
-    return Di
+    return _update_sum(F, i, i, k)
 
 
 def _select_pivot(Ad: list, D: dict, k: int) -> int:
@@ -239,10 +257,7 @@ def factor_pivoted(A: TLR, eps: float, compressor: str = "svd", bs: int = 16, se
         comp = _compressor(compressor, eps, bs, seed, STREAM_FACTOR, k, b)
         for i in range(k + 1, nb):
             U0, V0 = At[(i, k)]
-            T = U0 @ V0.T
-            for j in range(k):
-                T -= F.U[(i, j)] @ ((F.V[(i, j)].T @ F.V[(k, j)]) @ F.U[(k, j)].T)
-            Q, B, t = comp(T)
+            Q, B, t = comp(U0 @ V0.T - _update_sum(F, i, k, k))
             F.U[(i, k)], F.V[(i, k)] = Q, Dn.solve_lower(Lkk, B)
             F.rounds[(i, k)] = t
         At = {key: v for key, v in At.items() if key[1] > k}

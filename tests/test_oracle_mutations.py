@@ -186,3 +186,23 @@ def test_modified_cholesky_shifting_instead_of_clamping_is_caught(monkeypatch):
     monkeypatch.setattr(dense, "_modify_eigenvalues", lambda w, d: w + d)
     with pytest.raises((AssertionError, dense.NotPositiveDefinite)):
         test_modified_cholesky_closed_forms()
+
+
+def test_update_sum_pairing_the_wrong_columns_is_caught(monkeypatch):
+    """Equation 1's sum as one product of concatenated factors: the right-hand blocks must pair with
+    the left-hand blocks of the same column j.  Reversing their order pairs j with k-1-j.  (The 1D
+    closed form cannot see this: there every U_ij of a block row spans the same direction.)"""
+    def misaligned(F, i, l, k):
+        if k == 0:
+            return np.zeros((F.b, F.b))
+        left = np.hstack([F.U[(i, j)] @ (F.V[(i, j)].T @ tlr._dv(F, j, F.V[(l, j)])) for j in range(k)])
+        right = np.hstack([F.U[(l, j)] for j in reversed(range(k))])
+        return left @ right.T
+    monkeypatch.setattr(tlr, "_update_sum", misaligned)
+    assert not _dense_ok()
+
+
+def test_update_sum_stopping_one_column_early_is_caught(monkeypatch):
+    orig = tlr._update_sum
+    monkeypatch.setattr(tlr, "_update_sum", lambda F, i, l, k: orig(F, i, l, max(k - 1, 0)))
+    assert not _ou_ok() and not _ou_ok(ldl=True)

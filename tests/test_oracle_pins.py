@@ -479,3 +479,58 @@ def test_trim_gives_the_truncated_svd_rank_and_error():
             assert abs(Qt.shape[1] - r_svd) <= 1          # the ARA basis captures T to ~eps / 10
             assert np.linalg.norm(T - Qt @ Bt.T, 2) <= 1.01 * eps
             assert np.allclose(Qt.T @ Qt, np.eye(Qt.shape[1]), atol=1e-12)
+
+
+# Hand-computed kernel entries in 2D and 3D (Section 6: A_ij = exp(-||x_i - x_j||_2 / ell)): point
+# pairs whose Euclidean distance is exact (3-4-5 and 1-2-2 triangles).  A wrong norm (L1, squared,
+# max), a dropped coordinate or a swapped length scale gives a different value for at least one.
+_KERNEL_PAIRS = [
+    # (x_i, x_j, ell, exact distance)
+    ((0.1, 0.2), (0.4, 0.6), 0.1, 0.5),
+    ((0.75, 0.25), (0.75, 0.0), 0.1, 0.25),
+    ((0.0, 0.0, 0.0), (0.1, 0.2, 0.2), 0.2, 0.3),
+    ((0.5, 0.5, 0.5), (0.5, 0.8, 0.1), 0.2, 0.5),
+    ((0.25, 0.5, 0.75), (0.25, 0.5, 0.75), 0.2, 0.0),
+]
+
+
+def test_kernel_entries_2d_3d_hand_computed():
+    for xi, xj, ell, dist in _KERNEL_PAIRS:
+        a = kernel.kernel_block(np.array([xi]), np.array([xj]), ell)[0, 0]
+        assert a == pytest.approx(math.exp(-dist / ell), rel=4e-15, abs=0.0), (xi, xj)
+    # the tile assembly puts the nugget on the diagonal only, and identity on padded rows
+    x = np.array([[0.1, 0.2], [0.4, 0.6], [0.9, 0.9]])
+    T = kernel.tile(x, 0, 0, 4, 0.1, 1e-4)
+    assert T[0, 0] == 1.0 + 1e-4 and T[1, 1] == 1.0 + 1e-4 and T[3, 3] == 1.0
+    assert T[0, 1] == T[1, 0] == pytest.approx(math.exp(-5.0), rel=4e-15)
+    assert T[3, 0] == 0.0 and T[0, 3] == 0.0
+
+
+def test_c_kernel_product_hand_computed_and_dense():
+    """The plain-C exact product (used at full size) applied to unit vectors returns the hand-computed
+    entries, and equals the dense matrix times a block of vectors."""
+    from oracle import cmatvec
+    for xi, xj, ell, dist in _KERNEL_PAIRS:
+        x = np.array([xi, xj])
+        col = cmatvec.matvec(x, ell, 1e-4, np.array([0.0, 1.0]))
+        assert col[0] == pytest.approx(math.exp(-dist / ell), rel=4e-15)  # off the diagonal: no nugget
+        assert col[1] == 1.0 + 1e-4
+    x = inputs.points(300, 3, 11)
+    X = np.random.default_rng(0).standard_normal((300, 5))
+    Y = cmatvec.matvec(x, 0.2, 1e-4, X)
+    R = kernel.dense(x, 0.2, 1e-4) @ X
+    assert np.abs(Y - R).max() <= 1e-13 * np.abs(R).max()
+
+
+def test_block_power_iteration_equals_single_and_converges():
+    """measures.power_norms runs one independent power iteration per column: each column equals
+    power_norm on its own operator, and both reach ||M||_2 of a symmetric matrix with a gap."""
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    Ms = [(Q * np.linspace(-s, 0.5 * s, 40)) @ Q.T for s in (1.0, 3.0, 0.0)]
+    x0 = rng.standard_normal(40)
+    lam = measures.power_norms(lambda V: np.stack([Ms[c] @ V[:, c] for c in range(3)], axis=1),
+                               np.repeat(x0[:, None], 3, axis=1), iters=200)
+    for c in range(3):
+        assert lam[c] == pytest.approx(measures.power_norm(lambda v: Ms[c] @ v, x0, iters=200), rel=1e-14, abs=0.0)
+    assert lam[0] == pytest.approx(1.0, rel=1e-8) and lam[1] == pytest.approx(3.0, rel=1e-8) and lam[2] == 0.0
