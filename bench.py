@@ -355,6 +355,8 @@ def run_ours(args, w, eps):
     # end-to-end through host buffers (public API: host points, pinned RHS in, pinned solution out)
     run_e2e(args, ctx, T, torch, w, eps, o, x, rhs_host, dev, out)
     run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out)
+    if not args.no_acceptance:
+        out["acceptance"] = run_acceptance(ctx, T, torch, w, x, dev, prec)
     if rank == 0 and not args.no_serving:
         # the metric's serving part: a bounded run of the serving workload (p50/p99 latency)
         out["serving"] = run_serve(args, ctx=ctx, n=args.serve_default_requests, quiet=True)
@@ -415,6 +417,75 @@ def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
             variants[vname] = {"eps": veps, "error": str(ex)}
     if variants:
         out["variants"] = variants
+
+
+def run_acceptance(ctx, T, torch, w, x, dev, prec, iters=30, kinds=("chol", "ldlt")):
+    """Section 6's accuracy check of this run's factors against the stored truncated-SVD oracle values.
+
+    For every eps of tests/golden/acceptance_<workload>.json (written by the oracle-only script beside
+    it), the matrix is built and factored (Cholesky and LDL^T) with the bench's options, then
+    measured on the GPU: backward error ||A - F||_2 / ||A||_2 by `iters` power iterations from the
+    recorded start vector (the exact kernel matrix applied by tlr_kernel_matvec), the relative
+    residual of a solve with the recorded right-hand side, and log det; each is compared with the
+    acceptance rule (backward error <= max(2x oracle's, 10 eps), residual <= 2x oracle's, logdet
+    within 1e-3 relative at eps <= 1e-6).  Outside the timed region."""
+    path = os.path.join(ROOT, "tests", "golden", f"acceptance_{WORKLOAD}.json")
+    if not os.path.exists(path):
+        return {"error": f"no oracle record {os.path.relpath(path, ROOT)}"}
+    gold = json.load(open(path))
+    N = w["N"]
+    y = torch.tensor(inputs.rhs(N, 1, w["seed"])[:, 0], device=dev)
+    x0 = torch.tensor(inputs.start_vector(N, gold["power"]["seed"]), device=dev)
+    o = T.default_opts(bs=w["bs"], seed=w["seed"], precision=prec)
+    facs, res = [], {}
+    for key in gold["results"]:
+        eps = float(key)
+        A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], o)
+        for kind in kinds:
+            F = A.copy()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            (F.ldlt if kind == "ldlt" else F.potrf)(eps, o)
+            e1.record(ctx.stream)
+            Bt = T.fortran(y.clone()[:, None])
+            F.solve(Bt)
+            torch.cuda.synchronize()
+            ld, sign = F.logdet()
+            res[(key, kind)] = {"factor_s": e0.elapsed_time(e1) / 1e3, "logdet": ld, "sign": sign,
+                                "mean_rank": F.info()["mean_rank"]}
+            facs.append(((key, kind), F, Bt))
+        A.free()
+    m = 1 + len(facs)
+    AX = ctx.kernel_matvec(x, w["ell"], w["nugget"], T.fortran(torch.cat([f[2] for f in facs], dim=1)))
+    for c, (k, _, _) in enumerate(facs):
+        res[k]["residual"] = float(torch.linalg.norm(AX[:, c] - y) / torch.linalg.norm(y))
+    V = T.fortran(x0[:, None].repeat(1, m))
+    V /= torch.linalg.norm(V, dim=0)
+    lam = torch.zeros(m, dtype=torch.float64, device=dev)
+    for _ in range(iters):
+        W = ctx.kernel_matvec(x, w["ell"], w["nugget"], V)
+        for c, (_, F, _) in enumerate(facs, start=1):
+            W[:, c] -= F.matvec(V[:, c].contiguous())
+        lam = torch.linalg.norm(W, dim=0)
+        V = T.fortran(W / lam)
+    lam = lam.cpu().numpy()
+    out = {"oracle_record": os.path.relpath(path, ROOT), "power_iterations": iters, "normA": float(lam[0]),
+           "oracle_normA": gold["normA"], "results": {}}
+    ok = True
+    for c, (k, F, _) in enumerate(facs, start=1):
+        F.free()
+        g, orc = res[k], gold["results"][k[0]][k[1]]
+        g["backward_error"] = float(lam[c] / lam[0])
+        eps = float(k[0])
+        g["oracle"] = {"backward_error": orc["backward_error"], "residual": orc["residual"],
+                       "logdet": orc["logdet"], "mean_rank": orc["ranks"]["mean"]}
+        g["pass"] = bool(g["backward_error"] <= max(2 * orc["backward_error"], 10 * eps)
+                         and g["residual"] <= 2 * orc["residual"] and g["sign"] == 1
+                         and (eps > 1e-6 or abs(g["logdet"] - orc["logdet"]) <= 1e-3 * abs(orc["logdet"])))
+        ok = ok and g["pass"]
+        out["results"].setdefault(k[0], {})[k[1]] = g
+    out["all_pass"] = ok
+    return out
 
 
 # --------------------------------------------------------------------------- batched and serving workloads
@@ -640,6 +711,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-acceptance", action="store_true",
+                    help="skip the accuracy check against the stored oracle values (outside the timed region)")
     ap.add_argument("--profile-compress", action="store_true",
                     help="phases mode: profile the compression as well as the factorization")
     ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve", "peaks", "phases", "pcg"])

@@ -1,0 +1,130 @@
+"""Acceptance of the CUDA path at full workload size against the truncated-SVD oracle.
+
+The oracle's values (backward error ||A - L L^T||_2 / ||A||_2 by 30 power iterations, relative
+residual of a solve with one N(0,1) right-hand side, log det) are computed once on the host by
+tests/golden/make_acceptance.py, which calls only the oracle, and stored with their provenance in
+tests/golden/acceptance_<workload>.json.  Here the GPU factors the same matrix (same points, same
+eps, Cholesky and LDL^T), measures the same three quantities with the exact kernel matrix applied
+on the GPU (tlr_kernel_matvec) and the factor's product (tlr_matvec), and must meet Section 6's
+check as the acceptance rule states it:
+  backward error <= max(2 x oracle's, 10 eps); residual <= 2 x oracle's;
+  |logdet - logdet_oracle| <= 1e-3 |logdet_oracle| at eps <= 1e-6.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import inputs
+from oracle import measures
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def T():
+    import paper_2108_11932_gb300 as T
+    T.build()
+    return T
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return T.Context(0)
+
+
+def gpu_acceptance(T, ctx, workload, golden, kinds=("chol", "ldlt")):
+    """Factor the workload on the GPU at every eps of the golden record; return the measured values."""
+    import torch
+    w = inputs.WORKLOADS[workload]
+    N, d, ell, nug, b = w["N"], w["d"], w["ell"], w["nugget"], w["b"]
+    x = inputs.points(N, d, w["seed"])
+    y = inputs.rhs(N, 1, w["seed"])
+    x0 = inputs.start_vector(N, golden["power"]["seed"])
+    dev = "cuda:0"
+    o = T.default_opts(bs=w["bs"], seed=w["seed"])
+    facs, out = [], {}
+    for key in golden["results"]:
+        eps = float(key)
+        A = ctx.compress(x, b, eps, ell, nug, o)
+        for kind in kinds:
+            F = A.copy()
+            comp = None
+            try:
+                (F.ldlt if kind == "ldlt" else F.potrf)(eps, o)
+            except T.TLRError as ex:
+                if ex.status != T.ERR_NOT_SPD:
+                    raise
+                comp = "shift"
+                F.free()
+                F = A.copy()
+                os_ = T.default_opts(bs=w["bs"], seed=w["seed"], compensation=T.COMP_SHIFT, shift=eps)
+                (F.ldlt if kind == "ldlt" else F.potrf)(eps, os_)
+            Yt = T.fortran(torch.tensor(y, device=dev))
+            F.solve(Yt)
+            ld, sign = F.logdet()
+            out[(key, kind)] = dict(logdet=ld, sign=sign, compensation=comp, mean_rank=F.info()["mean_rank"])
+            facs.append(((key, kind), F, Yt))
+        A.free()
+    # residuals with the exact kernel matrix on the GPU
+    Xs = T.fortran(torch.cat([f[2] for f in facs], dim=1))
+    AX = ctx.kernel_matvec(x, ell, nug, Xs).cpu().numpy()
+    for c, (k, _, _) in enumerate(facs):
+        out[k]["residual"] = float(np.linalg.norm(AX[:, c] - y[:, 0]) / np.linalg.norm(y[:, 0]))
+
+    def apply_block(V):
+        Vt = T.fortran(torch.tensor(V, device=dev))
+        W = ctx.kernel_matvec(x, ell, nug, Vt)
+        for c, (_, F, _) in enumerate(facs, start=1):
+            W[:, c] -= F.matvec(Vt[:, c])
+        return W.cpu().numpy()
+
+    lam = measures.power_norms(apply_block, np.repeat(x0[:, None], 1 + len(facs), axis=1),
+                               golden["power"]["iters"])
+    for c, (k, F, _) in enumerate(facs, start=1):
+        out[k]["backward_error"] = float(lam[c] / lam[0])
+        F.free()
+    out["normA"] = float(lam[0])
+    return out
+
+
+def check(golden, got):
+    """The acceptance rule; returns a list of failures (empty when every result passes)."""
+    bad = []
+    for key, res in golden["results"].items():
+        eps = float(key)
+        for kind in ("chol", "ldlt"):
+            if (key, kind) not in got or kind not in res:
+                continue
+            g, o = got[(key, kind)], res[kind]
+            if not g["backward_error"] <= max(2 * o["backward_error"], 10 * eps):
+                bad.append((key, kind, "backward error", g["backward_error"], o["backward_error"]))
+            if not g["residual"] <= 2 * o["residual"]:
+                bad.append((key, kind, "residual", g["residual"], o["residual"]))
+            if eps <= 1e-6 and not abs(g["logdet"] - o["logdet"]) <= 1e-3 * abs(o["logdet"]):
+                bad.append((key, kind, "logdet", g["logdet"], o["logdet"]))
+            if g["sign"] != 1:
+                bad.append((key, kind, "sign", g["sign"], 1))
+    return bad
+
+
+@pytest.mark.parametrize("workload", ["cov2d_131k", "cov3d_32k"])
+def test_full_size_acceptance_against_svd_oracle(T, ctx, workload):
+    path = os.path.join(GOLDEN, f"acceptance_{workload}.json")
+    assert os.path.exists(path), f"missing oracle record {path} (tests/golden/make_acceptance.py)"
+    golden = json.load(open(path))
+    got = gpu_acceptance(T, ctx, workload, golden)
+    for (key, kind), g in sorted((k, v) for k, v in got.items() if isinstance(k, tuple)):
+        o = golden["results"][key][kind]
+        print(f"{workload} eps={key} {kind}: backward error {g['backward_error']:.3e} (oracle "
+              f"{o['backward_error']:.3e}), residual {g['residual']:.3e} (oracle {o['residual']:.3e}), logdet "
+              f"{g['logdet']:.10g} (oracle {o['logdet']:.10g}), mean rank {g['mean_rank']:.2f} (oracle "
+              f"{o['ranks']['mean']:.2f})")
+    assert abs(got["normA"] - golden["normA"]) <= 1e-6 * golden["normA"]
+    bad = check(golden, got)
+    assert not bad, bad
