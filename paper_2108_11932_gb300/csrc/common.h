@@ -287,50 +287,58 @@ struct SlotDescT {
   T* Z;
   int ldx, ldx0, nb, k, i, r0, x0off, Ki, Kk, q, bs;
 };
-// FP64 products on BF16 tensor cores by exact splitting (k_ozaki.cu)
-// columns to split: X (K x ncols, ld) -> slice q of column c at Xs + q * plane + c * ldo (rows
+// FP64 products on BF16 tensor cores by exact splitting (k_ozaki.cu).  Operands are stored as 8
+// planes of signed 7-bit chunks (int8, one byte per chunk); rows of a plane start on 16-byte
+// boundaries (the TMA rule), so leading dimensions along k are padded to oz_ld(K).
+inline __host__ __device__ int oz_ld(int K) { return (K + 15) / 16 * 16; }
+// columns to split: X (K x ncols, ld) -> plane q of column c at Xs + q * plane + c * ldo (rows
 // K .. ldo-1 zero), relative to 2^e[c] (e[c] computed), or to 2^efix for every column
 constexpr int OZ_EFIX_NONE = -100000;
 struct OzColJob {
   const double* X;
-  uint16_t* Xs;
+  int8_t* Xs;
   int* e;
   int ld, ncols, col0, K;
   size_t plane = 0;  // 0: ncols * ldo
-  int ldo = 0;       // 0: K
+  int ldo = 0;       // 0: oz_ld(K)
   int efix = OZ_EFIX_NONE;
   // with emax (device: the block's largest |x| as FP64 bits) every column uses that block bound,
   // written to e[0]
   const unsigned long long* emax = nullptr;
 };
 // C (M x N, ldc) = A B (or C += A B), A(m, k) = A_q[k + m * lda] (rows along k) or, with acol,
-// A_q[m + k * lda] (columns along m, M a multiple of 8); B(k, n) = B_q[k + n * ldb]
+// A_q[m + k * lda] (columns along m); B(k, n) = B_q[k + n * ldb].  lda, ldb, the plane strides and
+// the operand addresses are multiples of 16 bytes.
 struct OzJob {
-  const uint16_t* A;     // 8 slices, stride sA
-  const uint16_t* B;     // 8 slices, stride sB
+  const int8_t* A;       // 8 chunk planes, stride sA (bytes)
+  const int8_t* B;       // 8 chunk planes, stride sB
   const int* eA;         // block exponent of A (device)
   const int* eB;         // column exponents of B (device, N)
   double* C;
   size_t sA, sB;
   int lda, ldc, M, N, K;
-  int ldb = 0;           // 0: K
+  int ldb = 0;           // 0: oz_ld(K)
   int acol = 0;
   int accumulate = 0;
   int eB_stride = 1;     // 0: one exponent for all columns of B
-  // split K: slices of whole 32-deep chunks, FP64 partials in ws, summed in slice order by the
+  // split K: slices of whole 32-deep stages, FP64 partials in ws, summed in slice order by the
   // last CTA of each output block (arrival counters).  nsplit = 0 lets oz_gemm choose from the
   // job's shape; the caller may fix it (1: no split).
   int nsplit = 0, tiles_n = 1;
   int rule_n = 0;        // columns the split rule assumes (0: N), as for GemmJob
+  int S = 8;             // chunk planes used (8: FP64-exact; fewer: both operands truncated to 7S bits)
   double* ws = nullptr;
   int* ctr = nullptr;
 };
-// Sc may be null (only the transposed slices are written)
-void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, uint16_t* Sc,
-                    uint16_t* Sr, int* eT);
+// Sc may be null (only the transposed chunks are written)
+void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, int8_t* Sc,
+                    int8_t* Sr, int* eT);
 void oz_split_cols(tlr_ctx* ctx, std::vector<OzColJob>& jobs);
 void oz_absmax(tlr_ctx* ctx, int nblocks, int64_t n2, const double* T, unsigned long long* tmax);
 void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs);
+// Synchronizes the stream and returns (and clears) the flag a split product sets when one of its
+// bounded waits ran out.
+int oz_timeout_flag(tlr_ctx* ctx);
 
 // one 16 x 16 output tile of a block-diagonal Gram product: slot, block column j
 // (j = k: the tile's own factor part), row chunk, column chunk

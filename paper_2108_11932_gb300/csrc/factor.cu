@@ -52,17 +52,18 @@ struct Mat {
   Buf G, G32, E, DV, DV32, Bc;
   std::vector<float*> AU32, AV32, FU32, FV32;
   std::vector<int64_t> fu32cap;
-  // BF16 7-bit slices of F's U panels relative to 2 (their columns are orthonormal basis vectors,
-  // |u| <= 1): 8 planes of b x fuscap[i] each, for the tensor-core split products (b % 8 == 0)
+  // 7-bit chunk planes (int8) of F's U panels relative to 2 (their columns are orthonormal basis
+  // vectors, |u| <= 1): 8 planes of b x fuscap[i] each, for the tensor-core split products
+  // (b % 16 == 0)
   bool oz = false;
-  std::vector<uint16_t*> FUs;
+  std::vector<int8_t*> FUs;
   std::vector<int64_t> fuscap;
   // slices of F's V panels (written once, at column j) relative to each panel's bound
-  std::vector<uint16_t*> FVs;
+  std::vector<int8_t*> FVs;
   int* dFVe = nullptr;                 // per panel exponent (device, nb)
   unsigned long long* dFVmax = nullptr;  // per panel largest |v| (device, nb)
   // slices of the compressed input's V panels (static), relative to each panel's bound
-  std::vector<uint16_t*> AVs;
+  std::vector<int8_t*> AVs;
   int* dAVe = nullptr;
   unsigned long long* dAVmax = nullptr;
   std::vector<double> nA, nL;  // Frobenius norms of the tiles of A and of L (mixed precision rule)
@@ -165,7 +166,7 @@ struct BatchSampler : Sampler {
         const Mat& M = *(*L)[ms[u]];
         if (M.oz && (M.Kk > 0 || M.R0k > 0)) { ne += (int64_t)bs * nr[u]; nx += (int64_t)8 * M.b * bs * nr[u]; }
       }
-    uint16_t* os = bos->need<uint16_t>((size_t)std::max<int64_t>(nx, 1));
+    int8_t* os = bos->need<int8_t>((size_t)std::max<int64_t>(nx, 1));
     int* oe = boe->need<int>((size_t)std::max<int64_t>(ne, 1));
     for (size_t u = 0; u < ms.size(); ++u) {
       Mat& M = *(*L)[ms[u]];
@@ -291,9 +292,9 @@ struct BatchSampler : Sampler {
     if (!F32)
       for (size_t s = 0; s < ops.size(); ++s) {
         const Mat& M = *(*L)[(*op_m)[ops[s]]];
-        if (M.oz && sd[s].Ki > 0 && sd[s].Ki <= 16384) { wsl += (int64_t)8 * ((sd[s].Ki + 7) / 8 * 8) * bs; wex += bs; }
+        if (M.oz && sd[s].Ki > 0 && sd[s].Ki <= 16384) { wsl += (int64_t)8 * oz_ld(sd[s].Ki) * bs; wex += bs; }
       }
-    uint16_t* ws_ = wsl ? bws->need<uint16_t>((size_t)wsl) : nullptr;
+    int8_t* ws_ = wsl ? bws->need<int8_t>((size_t)wsl) : nullptr;
     int* we_ = wex ? bwe->need<int>((size_t)wex) : nullptr;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
@@ -304,7 +305,7 @@ struct BatchSampler : Sampler {
       GemmJob<T> g = job<T>(NN, M.b, bs, U0, M.b, sd[s].W, ldw, r0, Yo, M.b, 1.0, 0.0);
       const bool split = !F32 && M.oz && Ki > 0 && Ki <= 16384;  // exact integer totals need K <= 16384
       if (split) {  // Y = U0 W[0:r0] here, then + Urow_i W[r0:] on the tensor cores
-        const int ldo = (Ki + 7) / 8 * 8;
+        const int ldo = oz_ld(Ki);
         OzColJob c{reinterpret_cast<const double*>(sd[s].W + r0), ws_, we_, ldw, bs, 0, Ki};
         c.ldo = ldo;
         wcj.push_back(c);
@@ -404,7 +405,7 @@ struct BatchSampler : Sampler {
         const Mat& M = *(*L)[(*op_m)[ops[s]]];
         if (M.oz && sd[s].Ki > 0) { qsl += (int64_t)8 * M.b * q[ops[s]]; qex += q[ops[s]]; }
       }
-    uint16_t* qs_ = qsl ? bws->need<uint16_t>((size_t)qsl) : nullptr;
+    int8_t* qs_ = qsl ? bws->need<int8_t>((size_t)qsl) : nullptr;
     int* qe_ = qex ? bwe->need<int>((size_t)qex) : nullptr;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
@@ -449,9 +450,9 @@ struct BatchSampler : Sampler {
     if (!F32)
       for (size_t s = 0; s < ops.size(); ++s) {
         const Mat& M = *(*L)[(*op_m)[ops[s]]];
-        if (M.oz && M.Kk > 0 && M.Kk <= 16384) { zsl += (int64_t)8 * ((M.Kk + 7) / 8 * 8) * q[ops[s]]; zex += q[ops[s]]; }
+        if (M.oz && M.Kk > 0 && M.Kk <= 16384) { zsl += (int64_t)8 * oz_ld(M.Kk) * q[ops[s]]; zex += q[ops[s]]; }
       }
-    uint16_t* zs_ = zsl ? bws->need<uint16_t>((size_t)zsl) : nullptr;
+    int8_t* zs_ = zsl ? bws->need<int8_t>((size_t)zsl) : nullptr;
     int* ze_ = zex ? bwe->need<int>((size_t)zex) : nullptr;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
@@ -462,7 +463,7 @@ struct BatchSampler : Sampler {
       const T* V0 = r0 ? Panels<T>::AV(M, M.k) + (size_t)M.b * M.A->voff[ix(M.A, i, M.k)] : nullptr;
       GemmJob<T> g = job<T>(NN, M.b, q[op], V0, M.b, sd[s].Z, ldz, r0, Bo, M.b, 1.0, 0.0);
       if (!F32 && M.oz && M.Kk > 0 && M.Kk <= 16384) {  // B = V0 Z[0:r0] here, + Urow_k Z[r0:] split
-        const int ldo = (M.Kk + 7) / 8 * 8;
+        const int ldo = oz_ld(M.Kk);
         OzColJob c{reinterpret_cast<const double*>(sd[s].Z + r0), zs_, ze_, ldz, q[op], 0, M.Kk};
         c.ldo = ldo;
         zcj.push_back(c);
@@ -544,7 +545,7 @@ void free_f32(tlr_ctx* ctx, Mat& M) {
       p = nullptr;
     }
   for (auto* v : {&M.FUs, &M.FVs, &M.AVs})
-    for (uint16_t*& p : *v) {
+    for (int8_t*& p : *v) {
       dfree(ctx, p);
       p = nullptr;
     }
@@ -622,13 +623,13 @@ struct Session {
     if (ldl) F->dvec = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b));
     F->dinv = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
     for (int i = 0; i < nb; ++i) ensure_ucap(ctx, F, i, std::max<int64_t>(A->ulen[i], 16));
-    M.oz = b % 8 == 0;
+    M.oz = b % 16 == 0;
     if (M.oz) {
       M.FUs.assign(nb, nullptr);
       M.fuscap.assign(nb, 0);
       for (int i = 0; i < nb; ++i) {
         M.fuscap[i] = F->ucap[i];
-        M.FUs[i] = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * M.fuscap[i]));
+        M.FUs[i] = static_cast<int8_t*>(dalloc(ctx, 8 * (size_t)b * M.fuscap[i]));
       }
       M.FVs.assign(nb, nullptr);
       M.dFVe = static_cast<int*>(dalloc(ctx, sizeof(int) * nb));
@@ -639,7 +640,7 @@ struct Session {
       std::vector<OzColJob> vcj;
       for (int j = 0; j < nb; ++j) {
         if (A->vlen[j] == 0) continue;
-        M.AVs[j] = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * A->vlen[j]));
+        M.AVs[j] = static_cast<int8_t*>(dalloc(ctx, 8 * (size_t)b * A->vlen[j]));
         oz_absmax(ctx, 1, (int64_t)b * A->vlen[j], A->Vcol[j], M.dAVmax + j);
         OzColJob c{A->Vcol[j], M.AVs[j], M.dAVe + j, b, (int)A->vlen[j], 0, b};
         c.emax = M.dAVmax + j;
@@ -739,7 +740,7 @@ struct Session {
       std::vector<ConvJob> cdv;
       std::vector<OzJob> ogj;      // split Gram products
       std::vector<OzColJob> dvcj;  // LDL^T: slices of D_j V_kj
-      uint16_t* dvs_ = nullptr;
+      int8_t* dvs_ = nullptr;
       int* dve_ = nullptr;
       {
         int64_t el = 0, ex = 0;
@@ -751,7 +752,7 @@ struct Session {
               ex += r;
             }
         if (el) {
-          dvs_ = bOzOs.need<uint16_t>((size_t)el);
+          dvs_ = bOzOs.need<int8_t>((size_t)el);
           dve_ = bOzOe.need<int>((size_t)ex);
         }
       }
@@ -1124,7 +1125,7 @@ struct Session {
       F->Vcol[M.k] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(M.Rk, 1) * b));
       F->vlen[M.k] = M.Rk;
       if (M.Rk > 0) {
-        if (b % 8 == 0) {
+        if (b % 16 == 0) {
           split.push_back(Mp);
           scols += M.Rk;
         } else {
@@ -1144,11 +1145,11 @@ struct Session {
       int64_t tel = 0;
       for (Mat* Mp : split) tel += (int64_t)Mp->b * Mp->b;
       unsigned long long* tmax = bOzMax.need<unsigned long long>((size_t)ns);
-      uint16_t* Sr = bOzS.need<uint16_t>((size_t)8 * tel);
+      int8_t* Sr = bOzS.need<int8_t>((size_t)8 * tel);
       int* eT = bOzE.need<int>((size_t)ns);
       int64_t xel = 0;
       for (Mat* Mp : split) xel += (int64_t)8 * Mp->b * Mp->Rk;
-      uint16_t* Xs = bOzX.need<uint16_t>((size_t)std::max<int64_t>(xel, 1));
+      int8_t* Xs = bOzX.need<int8_t>((size_t)std::max<int64_t>(xel, 1));
       int* ex = bOzEx.need<int>((size_t)scols);
       std::vector<OzColJob> cj;
       std::vector<OzJob> oj;
@@ -1176,7 +1177,7 @@ struct Session {
         Mat& M = *Mp;
         if (!M.live || M.nops == 0 || !M.oz || M.Rk == 0) continue;
         const int b = M.b;
-        M.FVs[M.k] = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * M.Rk));
+        M.FVs[M.k] = static_cast<int8_t*>(dalloc(ctx, 8 * (size_t)b * M.Rk));
         oz_absmax(ctx, 1, (int64_t)b * M.Rk, M.F->Vcol[M.k], M.dFVmax + M.k);
         OzColJob c{M.F->Vcol[M.k], M.FVs[M.k], M.dFVe + M.k, b, (int)M.Rk, 0, b};
         c.emax = M.dFVmax + M.k;
@@ -1216,11 +1217,10 @@ struct Session {
         if (M.oz && r > 0) {
           if (F->ulen[i] + r > M.fuscap[i]) {  // grow the slices of block row i (8 planes)
             const int64_t cap = std::max<int64_t>(F->ucap[i], F->ulen[i] + r);
-            uint16_t* p = static_cast<uint16_t*>(dalloc(ctx, sizeof(uint16_t) * 8 * (size_t)b * cap));
+            int8_t* p = static_cast<int8_t*>(dalloc(ctx, 8 * (size_t)b * cap));
             if (F->ulen[i] > 0)
-              TLR_CUDA(cudaMemcpy2DAsync(p, sizeof(uint16_t) * (size_t)b * cap, M.FUs[i],
-                                         sizeof(uint16_t) * (size_t)b * M.fuscap[i],
-                                         sizeof(uint16_t) * (size_t)b * F->ulen[i], 8, cudaMemcpyDeviceToDevice,
+              TLR_CUDA(cudaMemcpy2DAsync(p, (size_t)b * cap, M.FUs[i], (size_t)b * M.fuscap[i],
+                                         (size_t)b * F->ulen[i], 8, cudaMemcpyDeviceToDevice,
                                          ctx->stream));
             dfree(ctx, M.FUs[i]);
             M.FUs[i] = p;
@@ -1256,6 +1256,7 @@ void factor_batch(tlr_ctx* ctx, const std::vector<tlr_mat*>& mats_in, const std:
   Session S(ctx);
   for (int m = 0; m < nm; ++m) S.add(mats_in[m], eps_in[m], opts[m], ldl);
   while (S.busy()) S.step();
+  TLR_REQUIRE(!oz_timeout_flag(ctx), TLR_ERR_TIMEOUT, "split product: a bounded device wait ran out");
   for (int m = 0; m < nm; ++m) status[m] = S.status(m);
 }
 
@@ -1316,6 +1317,7 @@ tlr_status tlr_session_step(tlr_session* s, int* unfinished) {
   if (!s) return TLR_ERR_ARG;
   SESSION_TRY
   s->S.step();
+  TLR_REQUIRE(!tlr::oz_timeout_flag(s->S.ctx), TLR_ERR_TIMEOUT, "split product: a bounded device wait ran out");
   if (unfinished) {
     int n = 0;
     for (auto& M : s->S.mats) n += (M->live && !M->done) ? 1 : 0;

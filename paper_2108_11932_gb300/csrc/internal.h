@@ -82,8 +82,8 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
 // Uniform dense ARA: nops operands T + op*n*n (n x n); Q (nops x n x (n+bs)), B (nops x n x n).
 // BF16 slices of a batch of dense tiles for the split products (k_ozaki.cu)
 struct OzTiles {
-  uint16_t* Sc;  // slices in the tiles' layout (columns of T contiguous)
-  uint16_t* Sr;  // transposed slices (rows of T contiguous)
+  int8_t* Sc;  // chunk planes in the tiles' layout (columns of T contiguous)
+  int8_t* Sr;  // transposed chunk planes (rows of T contiguous)
   int* e;        // per-tile exponent (device)
   Buf* bx;       // workspace for the right operand's slices
   Buf* be;       // workspace for its column exponents

@@ -1,41 +1,84 @@
-// FP64 products of the construction stage on BF16 tensor cores, exact to FP64 level.
+// FP64 products on the BF16 tensor cores (tcgen05), exact to FP64 level, operands fed by TMA.
 //
-// GB300 retires 2 FP64 FMAs per SM per clock but thousands of BF16 tensor-core FMAs, and
-// the construction's dominant products -- the ARA samples Y = T Omega and projections
-// B = T^T Q of every generated dense tile (Algorithm 1 applied to Section 6's kernel tiles)
-// -- are large dense contractions.  They are computed by error-free splitting (the Ozaki
-// scheme: Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012):
+// GB300 retires 2 FP64 FMAs per SM per clock but thousands of BF16 tensor-core FMAs, and the
+// method's large products -- the ARA samples Y = T Omega and projections B = T^T Q of the generated
+// tiles (Algorithm 1 on Section 6's kernel tiles), the sampling chains of Equation 2 with the
+// factor's U and V panels, batchTrsm -- are dense contractions.  They are computed by error-free
+// splitting (the Ozaki scheme: Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012):
 //
-//  * Every entry x of an operand is written as x = 2^e * sum_{i=1..8} x_i 2^(-7 i) with
-//    integers |x_i| <= 127, where 2^e bounds the operand block (the whole tile for T, each
-//    column for Omega and Q).  The x_i are the 7-bit chunks of the 56-bit truncation of
-//    |x| 2^(56-e), with the sign of x; they are found with integer operations on the FP64
-//    bit pattern.  Truncation error < 2^(e-56).
-//  * Each chunk is exact in BF16 (8 significant bits).  A product of chunks is an integer
-//    below 2^14, and the sum of the chunk products of one pair (i, j) over 128 consecutive k,
-//    even added over the (i+j-1) pairs with the same i+j, stays below 2^24: the FP32
-//    accumulation of mma.sync is exact.  Every 128 k the eight group sums (i+j = 2..9) move
-//    to 32-bit integer totals (exact for K <= 16384), which are combined in FP64 with weights
-//    2^(-7(i+j)) once at the end; pairs with i+j > 9 are below 2^-63 of the block bounds and
-//    are dropped.
+//  * Every entry x of an operand is written as x = 2^e * sum_{i=1..8} x_i 2^(-7 i) with integers
+//    |x_i| <= 127, where 2^e bounds the operand block (the whole tile for T, each column for Omega
+//    and Q).  The x_i are the 7-bit chunks of the 56-bit truncation of |x| 2^(56-e) with the sign of
+//    x, found with integer operations on the FP64 bit pattern and stored as int8: 8 bytes per
+//    entry, the bytes of the FP64 operand.  Truncation error < 2^(e-56).
+//  * The product keeps the chunk pairs (i, j) with i + j <= S + 1 (S = 8: every pair of weight
+//    >= 2^-63 of the block bounds; S < 8 truncates both operands to 7S bits, the precision knob of
+//    the mixed path).  Chunks are exact in BF16 (8 significant bits); a chunk product is below 2^14
+//    and the sum of one group g = i + j - 2 over 128 consecutive k, added over its g + 1 pairs, stays
+//    below 2^24: the FP32 accumulation of the tensor core is exact.  Every 128 k the group sums move
+//    from tensor memory to 32-bit integer totals (exact for K <= 16384), combined once at the end.
 //
-// The error of a result entry is below ~2^-55 sum_k 2^eA 2^eB (plus FP64 rounding of the
-// recombination), the same order as an FP64 dot product of the same length.
-#include <cuda_bf16.h>
+// Kernel structure (one CTA = 128 output rows x 16 output columns x one K slice, 320 threads):
+//  * warp 0: TMA producer.  3D boxes (k or m, row, slice) of the int8 chunk planes of A and B are
+//    copied by cp.async.bulk.tensor into a 3-stage ring (32 k per stage), mbarrier completion.
+//  * warps 2-5: converters.  Thread t owns row t of the A tile (and one stacked row of B): int8 chunks
+//    become BF16 in the canonical K-major layout of the tensor core (8-row x 16-byte core matrices;
+//    either orientation of A in HBM lands in the same layout).
+//  * warp 1: one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in tensor memory).
+//    For a 16-k step and A slice i, B is the stack [B_1 | ... | B_(S+1-i)] (N = 16 (S + 1 - i)) and
+//    the accumulator starts at the column block of group i - 1: every group sum accumulates in place.
+//    Two 128-column accumulator buffers alternate between 128-k windows.
+//  * warps 6-9: epilogue.  They drain each window's group sums (tcgen05.ld) into integer totals
+//    while the next window accumulates, then recombine in FP64 and store (or write split-K partials,
+//    summed in slice order by the last CTA of each output block).
+// Every wait is bounded: on a timeout the CTA sets a device flag, lets its copies land, frees its
+// tensor memory and returns; the host reports TLR_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
 
 #include "common.h"
 
 namespace tlr {
 
+__device__ int g_oz_timeout = 0;
+
 namespace {
 
-constexpr int OZ_S = 8;      // slices per operand
-constexpr int OZ_TM = 64;    // output rows per CTA (4 warps x 16)
-constexpr int OZ_TN = 16;    // output columns per CTA (2 n8 blocks)
-constexpr int OZ_KC = 32;    // k per shared-memory stage
-constexpr int OZ_KF = 128;   // k per exact FP32 group sum
-constexpr int OZ_LDS = 40;   // shared row stride in BF16 elements (32 + 8: conflict-free fragment loads)
-constexpr int OZ_LDSM = 72;  // shared row stride of a column-oriented A chunk (64 + 8)
+constexpr int OZ_S = 8;       // chunk planes per operand
+constexpr int OZ_TM = 128;    // output rows per CTA (tcgen05 M)
+constexpr int OZ_TN = 16;     // output columns per CTA
+constexpr int OZ_KS = 32;     // k per TMA stage
+constexpr int OZ_KC = 16;     // k per MMA
+constexpr int OZ_CW = 8;      // 16-k steps per exact window (128 k)
+constexpr int OZ_NST = 3;     // int8 stages in flight
+constexpr int OZ_THREADS = 320;
+constexpr int ST_A = OZ_S * OZ_TM * OZ_KS;        // int8 A per stage (32 KB)
+constexpr int ST_B = OZ_S * OZ_TN * OZ_KS;        // int8 B per stage (4 KB)
+constexpr int ST_BYTES = ST_A + ST_B;
+constexpr int BF_ASL = OZ_TM * OZ_KC * 2;         // one slice of the BF16 A chunk (4 KB)
+constexpr int BF_A = OZ_S * BF_ASL;
+constexpr int BF_B = OZ_S * OZ_TN * OZ_KC * 2;    // stacked BF16 B chunk, 128 rows (4 KB)
+constexpr int BF_BYTES = BF_A + BF_B;
+constexpr int CORE_K = OZ_TM * 16;                // A: byte stride between the two 8-k core columns
+constexpr int OZ_TMEM_COLS = 256;                 // two accumulator buffers of 8 x 16 columns
+constexpr int OZ_SMEM = 1024 + OZ_NST * ST_BYTES + 2 * BF_BYTES + 256;
+constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
+
+// Tensor maps live in the job table (global memory); CUtensorMap carries its own (>= 64-byte)
+// alignment, and the upload ring hands out 256-byte aligned regions.
+struct OzDev {
+  CUtensorMap ta, tb;
+  const int* eA;
+  const int* eB;
+  double* C;
+  double* ws;
+  int* ctr;
+  int M, N, K, ldc, acol, accumulate, eB_stride, nsplit, tiles_n, S;
+};
+static_assert(alignof(OzDev) >= 64 && sizeof(OzDev) % 64 == 0, "tensor maps need 64-byte alignment");
 
 inline int64_t oz_cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -45,8 +88,8 @@ __device__ __forceinline__ int oz_exponent(unsigned long long maxbits) {
   return ex == 0 ? 0 : ex - 1022;
 }
 
-// The eight signed 7-bit chunks of x relative to 2^e, as BF16 bit patterns.
-__device__ __forceinline__ void oz_split(double x, int e, uint16_t out[OZ_S]) {
+// The eight signed 7-bit chunks of x relative to 2^e.
+__device__ __forceinline__ void oz_split(double x, int e, int8_t out[OZ_S]) {
   const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((bits >> 52) & 0x7FF);
   unsigned long long F = 0;
@@ -60,66 +103,136 @@ __device__ __forceinline__ void oz_split(double x, int e, uint16_t out[OZ_S]) {
 #pragma unroll
   for (int i = 0; i < OZ_S; ++i) {
     const int c = (int)((F >> (49 - 7 * i)) & 127);
-    const float f = (float)(neg ? -c : c);
-    out[i] = (uint16_t)(__float_as_uint(f) >> 16);  // exact: at most 7 significant bits
+    out[i] = (int8_t)(neg ? -c : c);
   }
 }
 
-__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const uint16_t* p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
+// ---- PTX wrappers (tcgen05, TMA, mbarrier)
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const uint16_t* p) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p;}"
+               : "=r"(ok)
+               : "r"(bar), "r"(parity)
+               : "memory");
+  return ok != 0;
 }
-
-// 16-byte asynchronous global-to-shared copy; src_bytes = 0 writes zeros (the source is not read).
-__device__ __forceinline__ void cp16(uint16_t* dst, const uint16_t* src, int src_bytes) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+// Bounded wait on a barrier phase; a timeout (or another role's abort) returns false.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    if (gtimer() - t0 > OZ_WAIT_NS) {
+      *abort = 1;
+      atomicExch(&g_oz_timeout, 1);
+      return false;
+    }
+  }
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
+// Bounded wait that ignores aborts (for copies and MMAs that must land before the CTA exits).
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > OZ_WAIT_NS) {
+      atomicExch(&g_oz_timeout, 1);
+      return;
+    }
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
   asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+// Shared-memory matrix descriptor, K-major, no swizzle: lbo = byte stride between core matrices
+// along K, sbo = byte stride between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
+__device__ __forceinline__ uint32_t umma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, int acc) {
+  asm volatile("{.reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}" ::"r"(
+                   dtmem),
+               "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+               : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Two signed int8 chunks (bytes sel and sel + 1 of w) as packed BF16: 2^23 + (c + 128) is built in
+// the bits of an FP32 number, 2^23 + 128 is subtracted (exact), and the top half is the BF16 value.
+__device__ __forceinline__ float oz_c2f(uint32_t biased, uint32_t sel) {
+  return __int_as_float((int)__byte_perm(biased, 0x4B000000u, 0x7540u | sel)) - 8388736.0f;
+}
+__device__ __forceinline__ uint32_t oz_pack2(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+}
+// 16 int8 chunks (4 words) -> 16 BF16 (8 words)
+__device__ __forceinline__ void oz_cvt16(const uint32_t (&w)[4], uint32_t (&o)[8]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t b = w[q] ^ 0x80808080u;
+    o[2 * q] = oz_pack2(oz_c2f(b, 0), oz_c2f(b, 1));
+    o[2 * q + 1] = oz_pack2(oz_c2f(b, 2), oz_c2f(b, 3));
+  }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ splitting
-// Slices of a batch of dense tiles (n x n each, column-major) relative to each tile's bound,
-// written twice: Sc (same layout as T: row k of T^T is contiguous) and Sr (transposed: row m
-// of T contiguous), so that both T Omega and T^T Q read their left operand along k.
+// Chunks of a batch of dense tiles (n x n each, column-major) relative to each tile's bound,
+// written twice: Sc (same layout as T: row k of T^T is contiguous) and Sr (transposed: row m of T
+// contiguous), so that both T Omega and T^T Q read their left operand along k.
 // CTA = one 32 x 32 block of one tile; the transposed copy goes through shared memory.
 __global__ void __launch_bounds__(256) k_oz_split_tiles(const double* __restrict__ T, int n,
                                                         const unsigned long long* __restrict__ tmax,
-                                                        uint16_t* __restrict__ Sc, uint16_t* __restrict__ Sr,
+                                                        int8_t* __restrict__ Sc, int8_t* __restrict__ Sr,
                                                         int* __restrict__ eT) {
   const int t = blockIdx.z;
   const int e = oz_exponent(tmax[t]);
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) eT[t] = e;
   const size_t n2 = (size_t)n * n;
   const double* x = T + (size_t)t * n2;
-  uint16_t* oc = Sc ? Sc + (size_t)t * OZ_S * n2 : nullptr;
-  uint16_t* orow = Sr + (size_t)t * OZ_S * n2;
-  __shared__ uint16_t tr[OZ_S][32][33];
+  int8_t* oc = Sc ? Sc + (size_t)t * OZ_S * n2 : nullptr;
+  int8_t* orow = Sr + (size_t)t * OZ_S * n2;
+  __shared__ int8_t tr[OZ_S][32][33];
   const int m0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   for (int kk = ty; kk < 32; kk += 8) {
     const int m = m0 + tx, k = k0 + kk;
-    uint16_t sl[OZ_S];
+    int8_t sl[OZ_S];
     if (m < n && k < n) oz_split(x[m + (size_t)k * n], e, sl);
     else
 #pragma unroll
@@ -139,8 +252,8 @@ __global__ void __launch_bounds__(256) k_oz_split_tiles(const double* __restrict
   }
 }
 
-// Slices of column blocks X_j (K x ncols_j, leading dimension ld_j) relative to each
-// column's bound; slice q of column c of block j lands at Xs_j + (q * ncols_j + c) * K.
+// Chunks of column blocks X_j (K x ncols_j, leading dimension ld_j) relative to each column's
+// bound; plane q of column c of block j lands at Xs_j + q * plane + c * ldo (rows K .. ldo-1 zero).
 // One CTA per column.
 __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restrict__ jobs,
                                                        const int* __restrict__ col_job) {
@@ -149,202 +262,275 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restric
   const int K = J.K;
   const int c = g - J.col0;
   const double* x = J.X + (size_t)c * J.ld;
-  const int ldo = J.ldo > 0 ? J.ldo : K;
+  const int ldo = J.ldo > 0 ? J.ldo : oz_ld(K);
   const size_t plane = J.plane > 0 ? J.plane : (size_t)J.ncols * ldo;
-  uint16_t* xs = J.Xs + (size_t)c * ldo;
+  int8_t* xs = J.Xs + (size_t)c * ldo;
+  int e;
   if (J.efix != OZ_EFIX_NONE || J.emax) {
-    const int e = J.emax ? oz_exponent(*J.emax) : J.efix;
+    e = J.emax ? oz_exponent(*J.emax) : J.efix;
     if (J.emax && J.e && c == 0 && threadIdx.x == 0) J.e[0] = e;
-    for (int k = threadIdx.x; k < ldo; k += blockDim.x) {
-      uint16_t s[OZ_S];
-      if (k < K) oz_split(x[k], e, s);
-#pragma unroll
-      for (int q = 0; q < OZ_S; ++q) xs[(size_t)q * plane + k] = k < K ? s[q] : (uint16_t)0;
+  } else {
+    __shared__ unsigned long long red[8];
+    unsigned long long m = 0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x[k]));
+      m = b > m ? b : m;
     }
-    return;
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+      m = v > m ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+      red[0] = m;
+    }
+    __syncthreads();
+    e = oz_exponent(red[0]);
+    if (threadIdx.x == 0) J.e[c] = e;
   }
-  __shared__ unsigned long long red[8];
-  unsigned long long m = 0;
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(x[k]));
-    m = b > m ? b : m;
-  }
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
-    m = v > m ? v : m;
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
-    red[0] = m;
-  }
-  __syncthreads();
-  const int e = oz_exponent(red[0]);
-  if (threadIdx.x == 0) J.e[c] = e;
   for (int k = threadIdx.x; k < ldo; k += blockDim.x) {
-    uint16_t s[OZ_S];
+    int8_t s[OZ_S];
     if (k < K) oz_split(x[k], e, s);
 #pragma unroll
-    for (int q = 0; q < OZ_S; ++q) xs[(size_t)q * plane + k] = k < K ? s[q] : (uint16_t)0;
+    for (int q = 0; q < OZ_S; ++q) xs[(size_t)q * plane + k] = k < K ? s[q] : (int8_t)0;
   }
 }
 
 // ------------------------------------------------------------------ product
-// C(M x N) = 2^(eA + eB_c) * sum over slice pairs (i, j), i + j <= 9, of A_i B_j 2^(-7(i+j)):
-// A(m, k) = A_i[k + m * lda] (rows of A contiguous along k), B(k, n) = B_j[k + n * K].
-// K and lda are multiples of 8 (16-byte rows).  Grid (M / 64, N / 16, jobs); warp w owns
-// rows 16w .. 16w+15 of the CTA's 64 x 16 block.
-template <bool ACOL>
-__global__ void __launch_bounds__(128) k_oz_gemm(const OzJob* __restrict__ jobs) {
-  const OzJob J = jobs[blockIdx.z];
-  if ((int)blockIdx.y >= J.tiles_n * J.nsplit) return;
-  const int nt = blockIdx.y % J.tiles_n, split = blockIdx.y / J.tiles_n;
+// C(M x N) = 2^(eA + eB_n) * sum over chunk pairs (i, j), i + j <= S + 1, of A_i B_j 2^(-7(i+j)),
+// A(m, k) = A_i[k + m lda] (rows along k) or, with acol, A_i[m + k lda]; B(k, n) = B_j[k + n ldb].
+// Grid (ceil(M / 128), tiles_n * nsplit, jobs).
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restrict__ jobs) {
+  const OzDev* Jp = jobs + blockIdx.z;
+  const int tiles_n = Jp->tiles_n, nsplit = Jp->nsplit;
+  if ((int)blockIdx.y >= tiles_n * nsplit) return;
+  const int nt = blockIdx.y % tiles_n, split = blockIdx.y / tiles_n;
+  const int M = Jp->M, N = Jp->N, K = Jp->K, S = Jp->S, acol = Jp->acol;
   const int m0 = blockIdx.x * OZ_TM, n0 = nt * OZ_TN;
-  if (m0 >= J.M || n0 >= J.N) return;
-  extern __shared__ __align__(16) uint16_t oz_sm[];
-  constexpr int STAGE = OZ_S * (OZ_TM + OZ_TN) * OZ_LDS;  // elements per buffer
-  // two buffers, each [slice][row 64][k 32 (+8)] (A) then [slice][col 16][k 32 (+8)] (B)
+  if (m0 >= M || n0 >= N) return;
+  const int nst_all = (K + OZ_KS - 1) / OZ_KS;
+  const int sb = (int)((int64_t)nst_all * split / nsplit), se = (int)((int64_t)nst_all * (split + 1) / nsplit);
+  const int nst = se - sb;            // TMA stages of this K slice
+  const int nch = 2 * nst;            // 16-k MMA steps
+  const int nwin = (nch + OZ_CW - 1) / OZ_CW;
+
+  extern __shared__ uint8_t oz_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* ring = base;                           // OZ_NST stages of int8 A then B
+  uint8_t* bfb = ring + OZ_NST * ST_BYTES;        // 2 BF16 chunk buffers: A slices then stacked B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bfb + 2 * BF_BYTES);
+  // barriers: full8[3] empty8[3] fullbf[2] emptybf[2] accf[2] acce[2] fin
+  const uint32_t b_full8 = su32(bars), b_empty8 = su32(bars + 3), b_fullbf = su32(bars + 6),
+                 b_emptybf = su32(bars + 8), b_accf = su32(bars + 10), b_acce = su32(bars + 12),
+                 b_fin = su32(bars + 14);
+  volatile int* abort = reinterpret_cast<volatile int*>(bars + 15);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int gq = lane >> 2, tq = lane & 3;
-  const int M = J.M, N = J.N, K = J.K;
-  float acc[OZ_S][2][4];  // exact group sums of the current 128-k window (integers < 2^24)
-  int tot[OZ_S][2][4];    // exact group sums over all k so far (integers < 2^31 for K <= 16384)
-#pragma unroll
-  for (int g = 0; g < OZ_S; ++g)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        acc[g][j][r] = 0.f;
-        tot[g][j][r] = 0;
-      }
-  // ldmatrix row addresses: A matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15); B matrices
-  // (columns 0-7 | 8-15) x (k 0-7 | 8-15) of the CTA's 16 columns
-  const int mi = lane >> 3, ri = lane & 7;
-  // row-oriented A chunk [slice][row][k]: matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15);
-  // column-oriented [slice][k][row]: the same four matrices read transposed
-  const int a_off = ACOL ? ((mi >> 1) * 8 + ri) * OZ_LDSM + warp * 16 + (mi & 1) * 8
-                         : (warp * 16 + ri + (mi & 1) * 8) * OZ_LDS + (mi >> 1) * 8;
-  const int a_slice = ACOL ? OZ_KC * OZ_LDSM : OZ_TM * OZ_LDS;  // elements per slice of a chunk
-  const int a_ks = ACOL ? OZ_LDSM : 1;                          // step of k within a chunk
-  const int ldb = J.ldb > 0 ? J.ldb : K;
-  const int b_off = OZ_S * OZ_TM * OZ_LDS + (ri + (mi >> 1) * 8) * OZ_LDS + (mi & 1) * 8;
-  // copy chunk k0 (16-byte pieces of 8 consecutive k) into buffer `buf`, zero-filled outside
-  auto stage = [&](int k0, int buf) {
-    uint16_t* As = oz_sm + buf * STAGE;
-    uint16_t* Bs = As + OZ_S * OZ_TM * OZ_LDS;
-    if (ACOL) {  // pieces of 8 consecutive rows at one k
-      for (int e = tid; e < OZ_S * OZ_KC * 8; e += 128) {
-        const int p = e & 7, kk = (e >> 3) & (OZ_KC - 1), q = e / (8 * OZ_KC);
-        const int gm = m0 + 8 * p, gk = k0 + kk;
-        const bool in = gm < M && gk < K;
-        cp16(As + (q * OZ_KC + kk) * OZ_LDSM + 8 * p, in ? J.A + (size_t)q * J.sA + gm + (size_t)gk * J.lda : J.A,
-             in ? 16 : 0);
-      }
-    } else {  // pieces of 8 consecutive k in one row
-      for (int e = tid; e < OZ_S * OZ_TM * 4; e += 128) {
-        const int p = e & 3, r = (e >> 2) % OZ_TM, q = e / (4 * OZ_TM);
-        const int gm = m0 + r, gk = k0 + 8 * p;
-        const bool in = gm < M && gk < K;
-        cp16(As + (q * OZ_TM + r) * OZ_LDS + 8 * p, in ? J.A + (size_t)q * J.sA + gk + (size_t)gm * J.lda : J.A,
-             in ? 16 : 0);
-      }
+
+  if (tid == 0) {
+    for (int s = 0; s < OZ_NST; ++s) {
+      mbar_init(b_full8 + 8 * s, 1);
+      mbar_init(b_empty8 + 8 * s, 128);
     }
-    for (int e = tid; e < OZ_S * OZ_TN * 4; e += 128) {
-      const int p = e & 3, c = (e >> 2) % OZ_TN, q = e / (4 * OZ_TN);
-      const int gn = n0 + c, gk = k0 + 8 * p;
-      const bool in = gn < N && gk < K;
-      cp16(Bs + (q * OZ_TN + c) * OZ_LDS + 8 * p, in ? J.B + (size_t)q * J.sB + gk + (size_t)gn * ldb : J.B,
-           in ? 16 : 0);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(b_fullbf + 8 * s, 128);
+      mbar_init(b_emptybf + 8 * s, 1);
+      mbar_init(b_accf + 8 * s, 1);
+      mbar_init(b_acce + 8 * s, 128);
     }
-    cp_commit();
-  };
-  const int nch = (K + OZ_KC - 1) / OZ_KC;
-  const int kb = (int)((int64_t)nch * split / J.nsplit) * OZ_KC;
-  const int ke = min(K, (int)((int64_t)nch * (split + 1) / J.nsplit) * OZ_KC);
-  if (kb < ke) stage(kb, 0);
-  int buf = 0;
-  for (int k0 = kb; k0 < ke; k0 += OZ_KC, buf ^= 1) {
-    if (k0 + OZ_KC < ke) {
-      stage(k0 + OZ_KC, buf ^ 1);  // next chunk in flight while this one is multiplied
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
+    mbar_init(b_fin, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(OZ_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&Jp->ta) : "memory");
+      asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&Jp->tb) : "memory");
+      const uint32_t bytes = (uint32_t)(S * (OZ_TM * OZ_KS + OZ_TN * OZ_KS));
+      int issued = 0;
+      for (int s = 0; s < nst; ++s) {
+        const int slot = s % OZ_NST;
+        if (!mbar_wait(b_empty8 + 8 * slot, ((s / OZ_NST) & 1) ^ 1, abort)) break;
+        uint8_t* st = ring + slot * ST_BYTES;
+        const int k0 = (sb + s) * OZ_KS;
+        mbar_expect_tx(b_full8 + 8 * slot, bytes);
+        if (acol) tma_3d(su32(st), &Jp->ta, m0, k0, 0, b_full8 + 8 * slot);
+        else tma_3d(su32(st), &Jp->ta, k0, m0, 0, b_full8 + 8 * slot);
+        tma_3d(su32(st + ST_A), &Jp->tb, k0, n0, 0, b_full8 + 8 * slot);
+        issued = s + 1;
+      }
+      // every issued copy lands before the CTA can exit
+      for (int s = issued > OZ_NST ? issued - OZ_NST : 0; s < issued; ++s)
+        mbar_drain(b_full8 + 8 * (s % OZ_NST), (s / OZ_NST) & 1);
     }
-    __syncthreads();
-    const uint16_t* base = oz_sm + buf * STAGE;
-#pragma unroll
-    for (int ks = 0; ks < OZ_KC; ks += 16) {
-      uint32_t b[OZ_S][4];  // per slice j: b0, b1 of columns 0-7, then of columns 8-15
-#pragma unroll
-      for (int j = 0; j < OZ_S; ++j) ldsm_x4(b[j], base + b_off + j * OZ_TN * OZ_LDS + ks);
-#pragma unroll
-      for (int i = 0; i < OZ_S; ++i) {
-        uint32_t a[4];
-        if (ACOL) ldsm_x4_t(a, base + a_off + i * a_slice + ks * a_ks);
-        else ldsm_x4(a, base + a_off + i * a_slice + ks * a_ks);
-#pragma unroll
-        for (int j = 0; j + i < OZ_S; ++j) {
-          mma_bf16(acc[i + j][0], a[0], a[1], a[2], a[3], b[j][0], b[j][1]);
-          mma_bf16(acc[i + j][1], a[0], a[1], a[2], a[3], b[j][2], b[j][3]);
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t bf0 = su32(bfb);
+      for (int c = 0; c < nch; ++c) {
+        const int sbf = c & 1;
+        if (!mbar_wait(b_fullbf + 8 * sbf, (c >> 1) & 1, abort)) break;
+        const int w = c / OZ_CW, buf = w & 1;
+        const bool first = (c % OZ_CW) == 0;
+        if (first && !mbar_wait(b_acce + 8 * buf, ((w >> 1) & 1) ^ 1, abort)) break;
+        tc_fence_after();
+        const uint32_t abase = bf0 + sbf * BF_BYTES, bbase = abase + BF_A;
+        const uint64_t bd = umma_desc(bbase, OZ_S * OZ_TN * 16, 128);
+#pragma unroll 1
+        for (int i = 0; i < S; ++i)
+          umma_bf16(tmem + buf * 128 + OZ_TN * i, umma_desc(abase + i * BF_ASL, CORE_K, 128), bd,
+                    umma_idesc(OZ_TM, OZ_TN * (S - i)), (first && i == 0) ? 0 : 1);
+        umma_commit(b_emptybf + 8 * sbf);
+        if ((c % OZ_CW) == OZ_CW - 1 || c == nch - 1) umma_commit(b_accf + 8 * buf);
+      }
+      umma_commit(b_fin);  // arrives when every MMA of this thread has completed
+      mbar_drain(b_fin, 0);
+    }
+  } else if (warp < 6) {
+    // ---------------- converters: int8 chunks -> canonical BF16 layout
+    const int t = tid - 64;  // A row t; B stacked row t (slice t / 16, column t % 16) when t < 16 S
+    for (int s = 0; s < nst; ++s) {
+      const int slot = s % OZ_NST;
+      if (!mbar_wait(b_full8 + 8 * slot, (s / OZ_NST) & 1, abort)) break;
+      const uint8_t* a8 = ring + slot * ST_BYTES;
+      const uint8_t* b8 = a8 + ST_A;
+      bool ok = true;
+      for (int h = 0; h < 2; ++h) {
+        const int c = 2 * s + h, sbf = c & 1;
+        if (!mbar_wait(b_emptybf + 8 * sbf, ((c >> 1) & 1) ^ 1, abort)) {
+          ok = false;
+          break;
         }
+        uint8_t* abf = bfb + sbf * BF_BYTES;
+        uint8_t* bbf = abf + BF_A;
+        for (int q = 0; q < S; ++q) {
+          uint32_t w[4], o[8];
+          if (acol) {  // stage image [q][k 32][m 128]
+            const uint8_t* p = a8 + q * (OZ_TM * OZ_KS) + (16 * h) * OZ_TM + t;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              w[u] = (uint32_t)p[(4 * u) * OZ_TM] | ((uint32_t)p[(4 * u + 1) * OZ_TM] << 8) |
+                     ((uint32_t)p[(4 * u + 2) * OZ_TM] << 16) | ((uint32_t)p[(4 * u + 3) * OZ_TM] << 24);
+          } else {  // stage image [q][m 128][k 32]
+            const uint4 v = *reinterpret_cast<const uint4*>(a8 + q * (OZ_TM * OZ_KS) + t * OZ_KS + 16 * h);
+            w[0] = v.x;
+            w[1] = v.y;
+            w[2] = v.z;
+            w[3] = v.w;
+          }
+          oz_cvt16(w, o);
+          uint8_t* d = abf + q * BF_ASL + t * 16;
+          *reinterpret_cast<uint4*>(d) = make_uint4(o[0], o[1], o[2], o[3]);
+          *reinterpret_cast<uint4*>(d + CORE_K) = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+        if (t < OZ_TN * S) {  // B image [q][n 16][k 32] -> stacked row t
+          const uint4 v = *reinterpret_cast<const uint4*>(b8 + (t / OZ_TN) * (OZ_TN * OZ_KS) + (t % OZ_TN) * OZ_KS +
+                                                          16 * h);
+          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+          uint32_t o[8];
+          oz_cvt16(w, o);
+          uint8_t* d = bbf + t * 16;
+          *reinterpret_cast<uint4*>(d) = make_uint4(o[0], o[1], o[2], o[3]);
+          *reinterpret_cast<uint4*>(d + OZ_S * OZ_TN * 16) = make_uint4(o[4], o[5], o[6], o[7]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(b_fullbf + 8 * sbf);
       }
+      mbar_arrive(b_empty8 + 8 * slot);
+      if (!ok) break;
     }
-    __syncthreads();
-    if (((k0 + OZ_KC - kb) % OZ_KF) == 0 || k0 + OZ_KC >= ke) {  // move the exact window sums to integers
+  } else {
+    // ---------------- epilogue: window drains, FP64 recombination, store
+    const int lq = warp & 3, row = 32 * lq + lane, m = m0 + row;
+    int tot[OZ_S][OZ_TN];
+#pragma unroll
+    for (int g = 0; g < OZ_S; ++g)
+#pragma unroll
+      for (int c = 0; c < OZ_TN; ++c) tot[g][c] = 0;
+    for (int w = 0; w < nwin; ++w) {
+      const int buf = w & 1;
+      if (!mbar_wait(b_accf + 8 * buf, (w >> 1) & 1, abort)) break;
+      tc_fence_after();
+      const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + buf * 128;
 #pragma unroll
       for (int g = 0; g < OZ_S; ++g)
+        if (g < S) {
+          uint32_t r[16];
+          tmem_ld16(ta + OZ_TN * g, r);
 #pragma unroll
-        for (int nb = 0; nb < 2; ++nb)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            tot[g][nb][r] += __float2int_rn(acc[g][nb][r]);
-            acc[g][nb][r] = 0.f;
-          }
+          for (int c = 0; c < OZ_TN; ++c) tot[g][c] += __float2int_rn(__uint_as_float(r[c]));
+        }
+      tc_fence_before();
+      mbar_arrive(b_acce + 8 * buf);
     }
-  }
-  const int eA = *J.eA;
-  const size_t MN = (size_t)M * N;
+    // group g has weight 2^-7(g+2): hi = groups 0-3 (< 2^53), lo = groups 4-7 (< 2^53), both exact in
+    // 64-bit integers and in FP64; value = (hi 2^28 + lo) 2^-63 (one rounding)
+    const int eA = *Jp->eA;
+    double* Cp = Jp->C;
+    const int ldc = Jp->ldc;
+    const size_t MN = (size_t)M * N;
 #pragma unroll
-  for (int nb = 0; nb < 2; ++nb)
+    for (int c = 0; c < OZ_TN; ++c) {
+      const int n = n0 + c;
+      long long hi = 0, lo = 0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int gm = m0 + warp * 16 + gq + ((r & 2) ? 8 : 0);
-      const int gn = n0 + nb * 8 + 2 * tq + (r & 1);
-      if (gm < M && gn < N) {
-        double v = 0.0;  // smallest weights first
+      for (int g = 0; g < 4; ++g) hi += (long long)tot[g][c] << (7 * (3 - g));
 #pragma unroll
-        for (int g = OZ_S - 1; g >= 0; --g) v = fma((double)tot[g][nb][r], ldexp(1.0, -7 * (g + 2)), v);
-        v = ldexp(v, eA + J.eB[gn * J.eB_stride]);
-        if (J.nsplit > 1) {
-          J.ws[(size_t)split * MN + gm + (size_t)gn * M] = v;
+      for (int g = 4; g < OZ_S; ++g) lo += (long long)tot[g][c] << (7 * (7 - g));
+      if (m < M && n < N) {
+        double v = fma((double)hi, 268435456.0, (double)lo);
+        v = ldexp(v, eA + Jp->eB[n * Jp->eB_stride] - 63);
+        if (nsplit > 1) {
+          Jp->ws[(size_t)split * MN + m + (size_t)n * M] = v;
         } else {
-          double* c = J.C + gm + (size_t)gn * J.ldc;
-          *c = J.accumulate ? *c + v : v;
+          double* cp = Cp + m + (size_t)n * ldc;
+          *cp = Jp->accumulate ? *cp + v : v;
         }
       }
     }
-  if (J.nsplit == 1) return;
-  // the last slice to finish this output block sums the partials in slice order
-  __threadfence();
-  __syncthreads();
-  __shared__ int last;
-  int* ctr = J.ctr + (m0 / OZ_TM) * J.tiles_n + nt;
-  if (tid == 0) last = (atomicAdd(ctr, 1) == J.nsplit - 1);
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  for (int e = tid; e < OZ_TM * OZ_TN; e += 128) {
-    const int gm = m0 + e % OZ_TM, gn = n0 + e / OZ_TM;
-    if (gm >= M || gn >= N) continue;
-    const size_t o = gm + (size_t)gn * M;
-    double v = 0.0;
-    for (int sp = 0; sp < J.nsplit; ++sp) v += __ldcg(J.ws + (size_t)sp * MN + o);
-    double* c = J.C + gm + (size_t)gn * J.ldc;
-    *c = J.accumulate ? *c + v : v;
+    if (nsplit > 1) {
+      // the last slice to finish this output block sums the partials in slice order
+      __threadfence();
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      __shared__ int last;
+      int* ctr = Jp->ctr + (m0 / OZ_TM) * tiles_n + nt;
+      if (row == 0) last = (atomicAdd(ctr, 1) == nsplit - 1);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (last) {
+        __threadfence();
+        if (m < M)
+          for (int c = 0; c < OZ_TN; ++c) {
+            const int n = n0 + c;
+            if (n >= N) break;
+            const size_t o = m + (size_t)n * M;
+            double v = 0.0;
+            for (int sp = 0; sp < nsplit; ++sp) v += __ldcg(Jp->ws + (size_t)sp * MN + o);
+            double* cp = Cp + m + (size_t)n * ldc;
+            *cp = Jp->accumulate ? *cp + v : v;
+          }
+        if (row == 0) *ctr = 0;
+      }
+    }
   }
-  if (tid == 0) *ctr = 0;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS));
+  }
 }
 
 // Largest |entry| of each of a batch of n2-element blocks, as FP64 bits (atomic max; zeroed first).
@@ -366,10 +552,8 @@ void oz_absmax(tlr_ctx* ctx, int nblocks, int64_t n2, const double* T, unsigned 
   TLR_LAUNCH_CHECK(ctx);
 }
 
-static size_t oz_gemm_smem() { return 2 * sizeof(uint16_t) * OZ_S * (OZ_TM + OZ_TN) * OZ_LDS; }
-
-void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, uint16_t* Sc,
-                    uint16_t* Sr, int* eT) {
+void oz_split_tiles(tlr_ctx* ctx, int ntiles, int n, const double* T, const unsigned long long* tmax, int8_t* Sc,
+                    int8_t* Sr, int* eT) {
   if (ntiles <= 0) return;
   dim3 grid((unsigned)oz_cdiv(n, 32), (unsigned)oz_cdiv(n, 32), (unsigned)ntiles);
   TLR_SITE_PRE(ctx);
@@ -391,65 +575,118 @@ void oz_split_cols(tlr_ctx* ctx, std::vector<OzColJob>& jobs) {
   TLR_LAUNCH_CHECK(ctx);
 }
 
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  TLR_REQUIRE(fn != nullptr, TLR_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  return fn;
+}
+
+// 3D int8 map: dims (d0, d1, 8 planes), strides (s1, plane) bytes, box (b0, b1, S).
+void make_map(CUtensorMap* map, const int8_t* p, uint64_t d0, uint64_t d1, uint64_t s1, uint64_t plane, uint32_t b0,
+              uint32_t b1, uint32_t S) {
+  TLR_REQUIRE(reinterpret_cast<uintptr_t>(p) % 16 == 0 && s1 % 16 == 0 && plane % 16 == 0 && d0 > 0 && d1 > 0,
+              TLR_ERR_LIMIT, "split product: operand not on 16-byte boundaries");
+  const cuuint64_t dims[3] = {d0, d1, (cuuint64_t)OZ_S};
+  const cuuint64_t strides[2] = {s1, plane};
+  const cuuint32_t box[3] = {b0, b1, S};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<int8_t*>(p), dims, strides, box, es,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  TLR_REQUIRE(r == CUDA_SUCCESS, TLR_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+}
+}  // namespace
+
+int oz_timeout_flag(tlr_ctx* ctx) {
+  int v = 0;
+  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  TLR_CUDA(cudaMemcpyFromSymbol(&v, g_oz_timeout, sizeof(int)));
+  if (v) {
+    const int zero = 0;
+    TLR_CUDA(cudaMemcpyToSymbol(g_oz_timeout, &zero, sizeof(int)));
+  }
+  return v;
+}
+
 void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
   if (jobs.empty()) return;
   static bool attr = false;
   if (!attr) {
-    TLR_CUDA(cudaFuncSetAttribute(k_oz_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_gemm_smem()));
-    TLR_CUDA(cudaFuncSetAttribute(k_oz_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_gemm_smem()));
+    TLR_CUDA(cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
     attr = true;
   }
-  const bool acol = jobs[0].acol != 0;
-  for (auto& j : jobs) {
-    const int ldb = j.ldb > 0 ? j.ldb : j.K;
-    // 16-byte pieces: rows of A (or its columns), columns of B, all on 8-element boundaries
-    TLR_REQUIRE((j.acol != 0) == acol && j.lda % 8 == 0 && ldb % 8 == 0 && j.K <= 16384 &&
-                    (acol ? j.M % 8 == 0 : j.K % 8 == 0),
-                TLR_ERR_LIMIT, "split product: unsupported shape");
-  }
   // Split K per job (its shape only, so a product sums in the same order alone or in a batch):
-  // enough slices of at least eight 32-deep chunks for the job alone to give ~1 CTA per SM.
+  // enough slices of at least eight 32-deep stages for the job alone to give ~1 CTA per SM.
   int mx = 0, ny = 0;
-  double flops = 0;
+  double flops = 0, bytes = 0;
   size_t ws_elems = 0, nctr = 0;
   for (auto& j : jobs) {
-    const int tm = (j.M + OZ_TM - 1) / OZ_TM;
-    j.tiles_n = (j.N + OZ_TN - 1) / OZ_TN;
-    const int nch = (j.K + OZ_KC - 1) / OZ_KC;
-    const int tnr = j.rule_n > 0 ? (j.rule_n + OZ_TN - 1) / OZ_TN : j.tiles_n;
+    TLR_REQUIRE(j.K > 0 && j.K <= 16384 && j.M > 0 && j.N > 0 && j.S >= 1 && j.S <= OZ_S, TLR_ERR_LIMIT,
+                "split product: unsupported shape");
+    const int tm = (int)oz_cdiv(j.M, OZ_TM);
+    j.tiles_n = (int)oz_cdiv(j.N, OZ_TN);
+    const int nst = (int)oz_cdiv(j.K, OZ_KS);
+    const int tnr = j.rule_n > 0 ? (int)oz_cdiv(j.rule_n, OZ_TN) : j.tiles_n;
     const int64_t want = ((int64_t)std::max(ctx->sm_count, 1) + (int64_t)tm * tnr - 1) / ((int64_t)tm * tnr);
-    if (j.nsplit <= 0) j.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, nch / 8, 64}));
+    if (j.nsplit <= 0) j.nsplit = (int)std::max<int64_t>(1, std::min<int64_t>({want, nst / 8, 64}));
     mx = std::max(mx, j.M);
     ny = std::max(ny, j.tiles_n * j.nsplit);
     flops += 2.0 * j.M * j.N * (double)j.K;
+    // algorithmic: every chunk plane used read once, C written (and read when accumulating)
+    bytes += (double)j.S * ((double)j.M * j.K + (double)j.K * j.N) + 8.0 * j.M * j.N * (j.accumulate ? 2 : 1);
     if (j.nsplit > 1) {
       ws_elems += (size_t)j.nsplit * j.M * j.N;
       nctr += (size_t)tm * j.tiles_n;
     }
   }
-  if (ws_elems) {
-    double* ws = static_cast<double*>(scratch(ctx, ws_elems * sizeof(double)));
-    int* ctr = split_counters(ctx, nctr);
-    for (auto& j : jobs)
-      if (j.nsplit > 1) {
-        j.ws = ws;
-        j.ctr = ctr;
-        ws += (size_t)j.nsplit * j.M * j.N;
-        ctr += (size_t)((j.M + OZ_TM - 1) / OZ_TM) * j.tiles_n;
-      }
+  double* ws = ws_elems ? static_cast<double*>(scratch(ctx, ws_elems * sizeof(double))) : nullptr;
+  int* ctr = ws_elems ? split_counters(ctx, nctr) : nullptr;
+  std::vector<OzDev> dev(jobs.size());
+  for (size_t u = 0; u < jobs.size(); ++u) {
+    const OzJob& j = jobs[u];
+    OzDev& d = dev[u];
+    memset(&d, 0, sizeof(d));
+    const int ldb = j.ldb > 0 ? j.ldb : oz_ld(j.K);
+    if (j.acol) make_map(&d.ta, j.A, (uint64_t)j.M, (uint64_t)j.K, (uint64_t)j.lda, j.sA, OZ_TM, OZ_KS, j.S);
+    else make_map(&d.ta, j.A, (uint64_t)j.K, (uint64_t)j.M, (uint64_t)j.lda, j.sA, OZ_KS, OZ_TM, j.S);
+    make_map(&d.tb, j.B, (uint64_t)j.K, (uint64_t)j.N, (uint64_t)ldb, j.sB, OZ_KS, OZ_TN, j.S);
+    d.eA = j.eA;
+    d.eB = j.eB;
+    d.C = j.C;
+    d.M = j.M;
+    d.N = j.N;
+    d.K = j.K;
+    d.ldc = j.ldc;
+    d.acol = j.acol;
+    d.accumulate = j.accumulate;
+    d.eB_stride = j.eB_stride;
+    d.nsplit = j.nsplit;
+    d.tiles_n = j.tiles_n;
+    d.S = j.S;
+    if (j.nsplit > 1) {
+      d.ws = ws;
+      d.ctr = ctr;
+      ws += (size_t)j.nsplit * j.M * j.N;
+      ctr += (size_t)oz_cdiv(j.M, OZ_TM) * j.tiles_n;
+    }
   }
-  double bytes = 0;  // algorithmic: every slice read once, C written (and read when accumulating)
-  for (auto& j : jobs)
-    bytes += 16.0 * j.M * j.K + 16.0 * j.K * j.N + 8.0 * j.M * j.N * (j.accumulate ? 2 : 1);
-  for (size_t o = 0; o < jobs.size(); o += 65535) {
-    const int cnt = (int)std::min<size_t>(65535, jobs.size() - o);
-    const OzJob* dj = static_cast<const OzJob*>(upload(ctx, jobs.data() + o, cnt * sizeof(OzJob)));
+  for (size_t o = 0; o < dev.size(); o += 65535) {
+    const int cnt = (int)std::min<size_t>(65535, dev.size() - o);
+    const OzDev* dj = static_cast<const OzDev*>(upload(ctx, dev.data() + o, cnt * sizeof(OzDev)));
     if (ctx->kprof) kprof_begin(ctx);
     dim3 grid((unsigned)oz_cdiv(mx, OZ_TM), (unsigned)ny, (unsigned)cnt);
     ctx->site_next_flops = flops * cnt / jobs.size();
     TLR_SITE_PRE(ctx);
-    if (acol) k_oz_gemm<true><<<grid, 128, oz_gemm_smem(), ctx->stream>>>(dj);
-    else k_oz_gemm<false><<<grid, 128, oz_gemm_smem(), ctx->stream>>>(dj);
+    k_oz_mma<<<grid, OZ_THREADS, OZ_SMEM, ctx->stream>>>(dj);
     TLR_LAUNCH_CHECK(ctx);
     if (ctx->kprof) kprof_end(ctx, 6, flops * cnt / jobs.size(), bytes * cnt / jobs.size());
   }

@@ -549,7 +549,7 @@ struct DenseSampler : Sampler {
   void sample(const std::vector<int>& ops, int, const double* Om, const std::vector<double*>& Ydst) override {
     flops += 2.0 * n * n * bs * ops.size();
     if (oz) {
-      uint16_t* Xs = static_cast<uint16_t*>(oz->bx->need<uint16_t>((size_t)8 * n * bs));
+      int8_t* Xs = oz->bx->need<int8_t>((size_t)8 * n * bs);
       int* ex = oz->be->need<int>((size_t)bs);
       std::vector<OzColJob> cj{OzColJob{Om, Xs, ex, n, bs, 0, n}};
       oz_split_cols(ctx, cj);
@@ -573,14 +573,14 @@ struct DenseSampler : Sampler {
       int64_t cols = 0;
       for (int v : q) cols += v;
       if (cols == 0) return;
-      uint16_t* Xs = oz->bx->need<uint16_t>((size_t)8 * n * cols);
+      int8_t* Xs = oz->bx->need<int8_t>((size_t)8 * n * cols);
       int* ex = oz->be->need<int>((size_t)cols);
       std::vector<OzColJob> cj;
       std::vector<OzJob> jobs;
       int64_t c0 = 0;
       for (size_t op = 0; op < q.size(); ++op) {
         if (q[op] == 0) continue;
-        uint16_t* xo = Xs + (size_t)8 * n * c0;
+        int8_t* xo = Xs + (size_t)8 * n * c0;
         cj.push_back(OzColJob{Q + (*qoff)[op], xo, ex + c0, n, q[op], 0, n});
         jobs.push_back(OzJob{oz->Sc + op * (size_t)8 * n * n, xo, oz->e + op, ex + c0, B + op * (size_t)n * n,
                              (size_t)n * n, (size_t)n * q[op], n, n, n, q[op], n});
@@ -725,13 +725,13 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
     const int* dij = static_cast<const int*>(upload(ctx, ij.data(), ij.size() * sizeof(int)));
     std::vector<int> q;
     AraStats as;
-    if (b % 8 == 0) {  // the tensor-core split products read 16-byte rows
+    if (b % 16 == 0) {  // the tensor-core split products read 16-byte rows of int8 chunks
       unsigned long long* tmax = bMax.need<unsigned long long>((size_t)nt);
       TLR_CUDA(cudaMemsetAsync(tmax, 0, sizeof(unsigned long long) * nt, ctx->stream));
       gen_tiles(ctx, gx, ginfo, N, d, kern->ell, kern->nugget, b, dij, nt, T, tmax);
       OzTiles oz;
-      oz.Sc = bSc.need<uint16_t>((size_t)nt * 8 * b * b);
-      oz.Sr = bSr.need<uint16_t>((size_t)nt * 8 * b * b);
+      oz.Sc = bSc.need<int8_t>((size_t)nt * 8 * b * b);
+      oz.Sr = bSr.need<int8_t>((size_t)nt * 8 * b * b);
       oz.e = bEt.need<int>((size_t)nt);
       oz.bx = &bXs;
       oz.be = &bEx;
@@ -780,7 +780,7 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
     cj.push_back(CopyJob{st[t].V, Vptr(M, i, j), (int64_t)st[t].r * b});
   }
   batched_copy(ctx, cj);
-  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  TLR_REQUIRE(!oz_timeout_flag(ctx), TLR_ERR_TIMEOUT, "split product: a bounded device wait ran out");
   for (void* c : chunks) dfree(ctx, c);
   M->state = 0;
 }
@@ -1594,17 +1594,17 @@ tlr_status tlr_dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int uni
 tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const double* T, const double* X, int ldx,
                              double* C, int ldc) {
   if (!ctx || !T || !X || !C || n <= 0 || ncols < 0 || ldx < n || ldc < n || trans < 0 || trans > 2) return TLR_ERR_ARG;
-  if (n % 8 != 0) return TLR_ERR_LIMIT;
+  if (n % 16 != 0) return TLR_ERR_LIMIT;
   if (ncols == 0) return TLR_OK;
   ABI_BEGIN
   Buf bm(ctx), bS(ctx), be(ctx), bx(ctx), bex(ctx);
   unsigned long long* tmax = bm.need<unsigned long long>(1);
   oz_absmax(ctx, 1, (int64_t)n * n, T, tmax);
-  uint16_t* Sc = bS.need<uint16_t>((size_t)16 * n * n);
-  uint16_t* Sr = Sc + (size_t)8 * n * n;
+  int8_t* Sc = bS.need<int8_t>((size_t)16 * n * n);
+  int8_t* Sr = Sc + (size_t)8 * n * n;
   int* eT = be.need<int>(1);
   oz_split_tiles(ctx, 1, n, T, tmax, Sc, Sr, eT);
-  uint16_t* Xs = bx.need<uint16_t>((size_t)8 * n * ncols);
+  int8_t* Xs = bx.need<int8_t>((size_t)8 * n * ncols);
   int* ex = bex.need<int>((size_t)ncols);
   std::vector<OzColJob> cj{OzColJob{X, Xs, ex, ldx, ncols, 0, n}};
   oz_split_cols(ctx, cj);
@@ -1614,7 +1614,7 @@ tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const do
     jobs[0].acol = 1;
   }
   oz_gemm(ctx, jobs);
-  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (oz_timeout_flag(ctx)) return TLR_ERR_TIMEOUT;
   return TLR_OK;
   ABI_END
 }
