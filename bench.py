@@ -394,32 +394,59 @@ def run_e2e(args, ctx, T, torch, w, eps, o, x, rhs_host, dev, out):
 
 
 def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
-    # other precisions / thresholds of the metric, one untimed-by-contract step each (CUDA events)
+    """Other thresholds and precisions of the metric (FP64 vs mixed), outside the timed region: each
+    variant is built and factored `reps` times (CUDA events on the library stream; median reported),
+    with the split products' plane histogram of one factorization (mixed: planes chosen per block)."""
     variants = {}
-    for vname, veps, vprec in args.variant_list:
-        if (veps, vprec) == (eps, prec):
+    reps = 3
+    for vname, veps, vprec, vldl in args.variant_list:
+        if (veps, vprec, vldl) == (eps, prec, False):
             continue
         vo = T.default_opts(bs=w["bs"], seed=w["seed"], precision=vprec)
         try:
-            A = ctx.compress_ordered(pts, perm, w["b"], veps, w["ell"], w["nugget"], vo)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            A.potrf(veps, vo)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            fs = e0.elapsed_time(e1) / 1e3
-            inf = A.info()
-            variants[vname] = {"eps": veps, "factor_s": fs, "tflops_exec": inf["flops_exec"] / fs / 1e12,
-                               "tflops_model": inf["flops_model"] / fs / 1e12, "mean_rank": inf["mean_rank"],
-                               "logdet": A.logdet()[0]}
-            A.free()
+            cs, fs = [], []
+            for r in range(reps):
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                ctx.split_planes(reset=True)
+                e0.record(stream)
+                A = ctx.compress_ordered(pts, perm, w["b"], veps, w["ell"], w["nugget"], vo)
+                e1.record(stream)
+                c_planes, c_bytes = ctx.split_planes(reset=True)
+                (A.ldlt if vldl else A.potrf)(veps, vo)
+                e2.record(stream)
+                f_planes, f_bytes = ctx.split_planes(reset=True)
+                torch.cuda.synchronize()
+                cs.append(e0.elapsed_time(e1) / 1e3)
+                fs.append(e1.elapsed_time(e2) / 1e3)
+                inf = A.info()
+                ld = A.logdet()[0]
+                A.free()
+            f = statistics.median(fs)
+            variants[vname] = {"eps": veps, "precision": ["fp64", "fp32", "mixed"][vprec],
+                               "factorization": "ldlt" if vldl else "chol", "factor_s": f,
+                               "compress_s": statistics.median(cs), "reps": reps,
+                               "tflops_exec": inf["flops_exec"] / f / 1e12,
+                               "tflops_model": inf["flops_model"] / f / 1e12, "mean_rank": inf["mean_rank"],
+                               "logdet": ld,
+                               "split_planes": {"compress": {f"s{i}": c_planes[i] for i in range(1, 9) if c_planes[i]},
+                                                "factor": {f"s{i}": f_planes[i] for i in range(1, 9) if f_planes[i]},
+                                                "chunk_bytes_compress": c_bytes, "chunk_bytes_factor": f_bytes}}
         except Exception as ex:  # report, do not hide
             variants[vname] = {"eps": veps, "error": str(ex)}
+    # speedups of the mixed path over the FP64 path at the same threshold
+    for vname, v in list(variants.items()):
+        if v.get("precision") == "mixed" and v.get("factorization") == "chol":
+            ref = next((u for u in variants.values() if u.get("precision") == "fp64" and u.get("eps") == v["eps"]
+                        and u.get("factorization") == "chol" and "factor_s" in u), None)
+            if ref:
+                v["speedup_factor_vs_fp64"] = ref["factor_s"] / v["factor_s"]
+                v["speedup_compress_vs_fp64"] = ref["compress_s"] / v["compress_s"]
+                v["logdet_rel_diff_vs_fp64"] = abs(v["logdet"] - ref["logdet"]) / abs(ref["logdet"])
     if variants:
         out["variants"] = variants
 
 
-def run_acceptance(ctx, T, torch, w, x, dev, prec, iters=30, kinds=("chol", "ldlt")):
+def run_acceptance(ctx, T, torch, w, x, dev, prec, iters=30, kinds=("chol", "ldlt", "chol_mixed")):
     """Section 6's accuracy check of this run's factors against the stored truncated-SVD oracle values.
 
     For every eps of tests/golden/acceptance_<workload>.json (written by the oracle-only script beside
@@ -437,15 +464,19 @@ def run_acceptance(ctx, T, torch, w, x, dev, prec, iters=30, kinds=("chol", "ldl
     y = torch.tensor(inputs.rhs(N, 1, w["seed"])[:, 0], device=dev)
     x0 = torch.tensor(inputs.start_vector(N, gold["power"]["seed"]), device=dev)
     o = T.default_opts(bs=w["bs"], seed=w["seed"], precision=prec)
+    om = T.default_opts(bs=w["bs"], seed=w["seed"], precision=T.PREC_MIXED)
     facs, res = [], {}
     for key in gold["results"]:
         eps = float(key)
         A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], o)
+        Am = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], om) if "chol_mixed" in kinds and eps >= 1e-4 else None
         for kind in kinds:
-            F = A.copy()
+            if kind == "chol_mixed" and Am is None:
+                continue
+            F = (Am if kind == "chol_mixed" else A).copy()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(ctx.stream)
-            (F.ldlt if kind == "ldlt" else F.potrf)(eps, o)
+            (F.ldlt if kind == "ldlt" else F.potrf)(eps, om if kind == "chol_mixed" else o)
             e1.record(ctx.stream)
             Bt = T.fortran(y.clone()[:, None])
             F.solve(Bt)
@@ -455,6 +486,8 @@ def run_acceptance(ctx, T, torch, w, x, dev, prec, iters=30, kinds=("chol", "ldl
                                 "mean_rank": F.info()["mean_rank"]}
             facs.append(((key, kind), F, Bt))
         A.free()
+        if Am is not None:
+            Am.free()
     m = 1 + len(facs)
     AX = ctx.kernel_matvec(x, w["ell"], w["nugget"], T.fortran(torch.cat([f[2] for f in facs], dim=1)))
     for c, (k, _, _) in enumerate(facs):
@@ -474,7 +507,7 @@ def run_acceptance(ctx, T, torch, w, x, dev, prec, iters=30, kinds=("chol", "ldl
     ok = True
     for c, (k, F, _) in enumerate(facs, start=1):
         F.free()
-        g, orc = res[k], gold["results"][k[0]][k[1]]
+        g, orc = res[k], gold["results"][k[0]]["chol" if k[1] == "chol_mixed" else k[1]]
         g["backward_error"] = float(lam[c] / lam[0])
         eps = float(k[0])
         g["oracle"] = {"backward_error": orc["backward_error"], "residual": orc["residual"],
@@ -610,21 +643,24 @@ def run_pcg(args, w):
 
 
 def run_serve(args, ctx=None, n=None, quiet=False):
-    """Serving: Poisson arrivals, continuous batching; latency arrival -> result."""
+    """Serving: Poisson arrivals, continuous batching in the library's queue (tlr_submit / tlr_progress /
+    tlr_poll, admission by a 150 GB HBM budget); latency arrival -> result.  FP64 and mixed precision."""
     import paper_2108_11932_gb300 as T
     from paper_2108_11932_gb300 import serve
-    if ctx is None:
-        T.build()
-        ctx = T.Context(0)
+    T.build()
     n = n or args.requests
     res = {}
-    for name, prec in (("fp64", 0), ("mixed", 1)):
+    for name, prec in (("fp64", T.PREC_FP64), ("mixed", T.PREC_MIXED)):
+        sctx = T.Context(0, hbm_budget=int(150e9))  # a context of its own: the budget counts its bytes
         reqs = serve.make_requests(n, args.rate, seed=4, n_max=args.serve_nmax)
-        srv = serve.Server(ctx, budget_bytes=150e9, precision=prec)
-        res[name] = srv.run(reqs)
+        res[name] = serve.Server(sctx, precision=prec).run(reqs)
+        sctx.close()
+    full = n >= 2000
     out = {"workload": f"serve: {n} requests, Poisson arrivals at {args.rate}/s, N log-uniform in [4096, {args.serve_nmax}] "
                        "(multiple of 256), d in {2,3}, ell~U[0.05,0.3], eps in {1e-2,1e-4,1e-6}, nrhs~U{1..32}; "
                        "factor + solve + logdet per request; 150 GB admission budget; FP64 vs mixed",
+           "truncated": None if full else f"the first {n} requests of the 2000-request serving workload "
+                                          "(start-up latencies; the full run is bench.py --mode serve --requests 2000)",
            **res}
     if not quiet:
         print(json.dumps(out), flush=True)
@@ -725,7 +761,10 @@ def main():
     args = ap.parse_args()
     WORKLOAD = args.workload
     w = inputs.WORKLOADS[WORKLOAD]
-    args.variant_list = [] if args.no_variants else [("fp64_eps1e-2", 1e-2, 0), ("fp64_eps1e-6", 1e-6, 0)]
+    args.variant_list = [] if args.no_variants else [
+        ("fp64_eps1e-2", 1e-2, 0, False), ("mixed_eps1e-2", 1e-2, 2, False),
+        ("fp64_eps1e-4", 1e-4, 0, False), ("mixed_eps1e-4", 1e-4, 2, False),
+        ("fp64_eps1e-6", 1e-6, 0, False), ("fp64_ldlt_eps1e-6", 1e-6, 0, True)]
     if args.impl == "reference":
         run_reference(args, w, args.eps)
     elif args.mode == "batch":

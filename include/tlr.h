@@ -57,10 +57,19 @@ typedef struct {
  * diagonal-tile factorization and the triangular solves are FP64 always.     */
 enum {
   TLR_PREC_FP64 = 0, /* everything FP64 */
-  TLR_PREC_FP32 = 1  /* sampling/projection chains in FP32 with FP32 accumulation for every
+  TLR_PREC_FP32 = 1, /* sampling/projection chains in FP32 with FP32 accumulation for every
                         tile whose estimated FP32 rounding error u32 sqrt(K) (|A_ik|_F +
                         sum_j |L_ij|_F |L_kj|_F) is below 1/8 of the ARA threshold, FP64 for
                         the others; eps < 1e-4 uses FP64 throughout */
+  TLR_PREC_MIXED = 2 /* the products that form ARA samples and projections (construction:
+                        T Omega, T^T Q; factorization: Urow_i W_i of Equation 2's chain and
+                        Urow_k Z of its transpose) on the 16-bit tensor cores (FP16 inputs, FP32
+                        accumulation, power-of-two block scaling), truncated to the fewest 7-bit
+                        planes s
+                        (2 <= s <= 8) whose worst-case error K (s+1) 2^(eA+eB-7s) per entry keeps
+                        the sample's column norm (the projection's Frobenius norm) within 1/8 of
+                        the ARA threshold; chosen per 128 x 16 output block on the device from
+                        the blocks' exponents.  eps < 1e-4 keeps all 8 planes (FP64-exact) */
 };
 
 /* Definiteness safeguards (Section 5.1). */
@@ -91,9 +100,11 @@ void tlr_opts_default(tlr_opts* o);
 typedef void* (*tlr_alloc_fn)(size_t bytes, void* user);
 typedef void (*tlr_free_fn)(void* ptr, void* user);
 
-/* Create a context on `device`, enqueuing work on `cuda_stream`
- * (a cudaStream_t, or NULL for the legacy default stream). */
-tlr_status tlr_create(tlr_ctx** ctx, int device, void* cuda_stream, tlr_alloc_fn alloc,
+/* Create a context on `device`, enqueuing work on `cuda_stream` (a cudaStream_t, or NULL for the
+ * legacy default stream).  hbm_budget: device bytes the serving queue (tlr_submit) may let the
+ * context hold while it admits requests (0 = no limit); every device allocation of the library
+ * goes through the context and is counted. */
+tlr_status tlr_create(tlr_ctx** ctx, int device, size_t hbm_budget, void* cuda_stream, tlr_alloc_fn alloc,
                       tlr_free_fn free_fn, void* user);
 tlr_status tlr_destroy(tlr_ctx* ctx);
 
@@ -167,6 +178,55 @@ tlr_status tlr_session_step(tlr_session* s, int* unfinished);
 /* *finished = 1 once the ticket's factorization ended; *result its status. */
 tlr_status tlr_session_poll(tlr_session* s, int ticket, int* finished, tlr_status* result);
 
+/* Serving queue (no counterpart in the paper: the request loop of a deployment that evaluates
+ * many Gaussian-process likelihoods, the use Section 1 gives for the factorization).  A request
+ * is one covariance matrix to build, factor, solve with nrhs right-hand sides and take the log
+ * determinant of.  tlr_submit copies the request into the context's queue; tlr_progress does one
+ * scheduling step:
+ *   1. admission, in submission order: the next queued request is built (tlr_compress) and joins
+ *      the factorizations in flight when the context's device bytes plus the request's estimated
+ *      footprint fit in tlr_create's hbm_budget (always when nothing is in flight);
+ *   2. one column step of every factorization in flight, all of them in the same launches
+ *      (tlr_session: a request that joins mid-flight gets the result it would get alone);
+ *   3. each finished factorization: on TLR_ERR_NOT_SPD it is rebuilt and refactored once as
+ *      A + eps I (Section 5.1, diagonal shift); otherwise it is solved (its right-hand sides copied
+ *      in, the solution copied back to the queue's host memory), its logdet taken, and its device
+ *      memory released.
+ * tlr_poll reports a request; once it is done, the first tlr_poll that sees it copies the solution
+ * into x (if x is not NULL) and releases the request (its ticket is then unknown: TLR_ERR_ARG).
+ * All requests of a context share one ARA block width (the first request's opts.bs).
+ * tlr_progress and tlr_poll synchronize the context stream; they are not thread-safe. */
+typedef struct {
+  const double* points; /* host, N x d row-major, original point order; copied by tlr_submit */
+  int64_t N;
+  int d;
+  tlr_kernel kernel;
+  int b;                /* tile size */
+  double eps;           /* absolute tile threshold */
+  int ldl;              /* 0: L L^T (Algorithm 6), 1: L D L^T (Algorithm 10) */
+  int nrhs;             /* right-hand sides, 0..1024 */
+  const double* rhs;    /* host, N x nrhs column-major (leading dimension N), original point order;
+                           copied by tlr_submit (may be NULL when nrhs == 0) */
+  tlr_opts opts;        /* bs, precision, compensation, seed, max_slots of this request */
+} tlr_request;
+typedef struct {
+  int done;             /* 0: queued or in flight (the fields below are not set yet) */
+  tlr_status status;    /* TLR_OK, or the error that ended the request */
+  int retried;          /* 1: refactored as A + eps I after a loss of definiteness */
+  int sign;             /* sign of det (LDL^T of an indefinite matrix: -1 possible) */
+  double logdet;        /* log |det| of the factored matrix */
+  double wait_s;        /* host seconds from tlr_submit to admission */
+  double run_s;         /* host seconds from admission to the result */
+  int64_t bytes;        /* device bytes of the factor while it was resident */
+  double mean_rank;     /* mean rank of the factor's off-diagonal tiles */
+} tlr_result;
+tlr_status tlr_submit(tlr_ctx* ctx, const tlr_request* req, uint64_t* ticket);
+/* One scheduling step.  *queued / *in_flight (either may be NULL) receive the requests waiting for
+ * admission and those being factored after the step; both 0 means every request is done. */
+tlr_status tlr_progress(tlr_ctx* ctx, int* queued, int* in_flight);
+/* res->done = 0 while the request runs; x: host N x nrhs, leading dimension ldx >= N, or NULL. */
+tlr_status tlr_poll(tlr_ctx* ctx, uint64_t ticket, tlr_result* res, double* x, int64_t ldx);
+
 /* Solve (L L^T) X = B or (L D L^T) X = B with the TLR triangular solve of
  * Algorithm 7 (forward) and its transpose (backward).  B: device, N x nrhs,
  * leading dimension ldb >= N, original point order; overwritten with X.
@@ -211,9 +271,11 @@ tlr_status tlr_matvec(tlr_ctx* ctx, const tlr_mat* F, int op, int nrhs, const do
                       int64_t ldx, double* Y, int64_t ldy);
 
 /* Exact kernel-matrix product Y = A X, A generated on the fly from the points
- * (used to measure backward errors and residuals; Section 6 "all results were
- * verified ...").  Points host row-major N x d in ORIGINAL order; X, Y device
- * N x nrhs (ldx, ldy >= N). */
+ * (used to measure backward errors and residuals, the way Section 6 checks its
+ * factorizations).  Points host row-major N x d in ORIGINAL order; X, Y device
+ * N x nrhs (ldx, ldy >= N).  TLR_ERR_ARG for a NULL pointer, N <= 0, d outside
+ * 1..3, nrhs < 0, ldx or ldy < N, a kernel type other than TLR_KERNEL_EXP,
+ * ell <= 0 or nugget < 0 (the same rule as tlr_kernel_matvec_noalloc). */
 tlr_status tlr_kernel_matvec(tlr_ctx* ctx, const double* points_host, int64_t N, int d,
                              const tlr_kernel* kernel, int nrhs, const double* X, int64_t ldx,
                              double* Y, int64_t ldy);
@@ -230,6 +292,9 @@ tlr_status tlr_kernel_matvec(tlr_ctx* ctx, const double* points_host, int64_t N,
  *     stream); the call is enqueued on it and returns without synchronizing.
  *   points_host: host, row-major N x d, original order; copied during the call
  *     (if it is page-locked, leave it unchanged until the stream has run the call).
+ *     The copy is an asynchronous host-to-device copy on cuda_stream: if that stream is being
+ *     captured, the copy becomes a node of the graph and reads points_host again at every
+ *     replay, so points_host must then stay valid and unchanged for every replay.
  *   X, Y: device, N x nrhs, column-major, ldx, ldy >= N (caller-owned).
  * Limits and errors: N * d <= 393216 (131072 points in 3D), else TLR_ERR_LIMIT;
  * bad arguments TLR_ERR_ARG; a failing CUDA call TLR_ERR_CUDA.
@@ -310,12 +375,19 @@ tlr_status tlr_dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int uni
  * as the factorization reads its panels) or C = T^T X (trans = 1) for one dense n x n FP64 tile T (column-major,
  * leading dimension n) and X n x ncols (leading dimension ldx), C n x ncols (ldc): the
  * construction's ARA products (Algorithm 1 samples and projections of Section 6's tiles),
- * computed on BF16 tensor cores by exact splitting into 7-bit slices (Ozaki et al., 2012)
- * with an error of the order of an FP64 product.  n must be a positive multiple of 8
+ * computed on the 16-bit tensor cores (tcgen05) by exact splitting into 7-bit chunks (Ozaki et
+ * al., 2012) with an error of the order of an FP64 product.  n must be a positive multiple of 16
  * (TLR_ERR_LIMIT otherwise); all pointers are device memory owned by the caller; the call
  * returns after the product is complete. */
 tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const double* T, const double* X,
                              int ldx, double* C, int ldc);
+
+/* Measurement utility (not part of the method): what the split products used since the last
+ * reset.  counts[s] (s = 1..8; counts[0] unused) = output blocks (128 x 16 x one K slice)
+ * computed with s 7-bit planes (8: FP64-exact; fewer: TLR_PREC_MIXED truncation); *bytes = int8
+ * chunk bytes of the operands read, each operand block counted once.  Synchronizes the context
+ * stream; reset != 0 zeroes the counters.  counts (9 entries) or bytes may be NULL. */
+tlr_status tlr_split_planes(tlr_ctx* ctx, int64_t* counts, double* bytes, int reset);
 
 /* Measurement utility (not part of the method): FP64 DFMA throughput of this
  * GPU in TFLOP/s, from a register-resident FMA loop timed with CUDA events. */
@@ -326,7 +398,7 @@ int64_t tlr_launch_count(const tlr_ctx* ctx);
 
 /* Measurement utility (not part of the method): per-launch CUDA-event accounting of the
  * batched products, by family: 0-2 FP64 k_gemm NN / TN / NT, 3-5 FP32 k_gemm NN / TN / NT,
- * 6 the BF16 tensor-core split products (FP64-equivalent flops).  Copies the accumulated
+ * 6 the tensor-core split products (FP64-equivalent flops).  Copies the accumulated
  * milliseconds, algorithmic flops (2 M N K per job, half for a triangular operand), algorithmic
  * bytes (split products only: slices read once, C written) and launch counts since the last call
  * (any pointer may be NULL; arrays of TLR_GEMM_FAMILIES), resets them, and turns the

@@ -21,7 +21,7 @@ from .build import LIB, build  # noqa: F401
 __all__ = ["Context", "Matrix", "Opts", "TLRError", "build", "fortran", "kd_order", "library_path"]
 
 OK, ERR_ARG, ERR_NOMEM, ERR_NOT_SPD, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_LIMIT = 0, -1, -2, -3, -4, -5, -6, -7
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 COMP_NONE, COMP_SHIFT, COMP_SCHUR = 0, 1, 2
 OP_A, OP_L, OP_LT, OP_LLT = 0, 1, 2, 3
 STREAM_COMPRESS, STREAM_FACTOR, STREAM_SCHUR = 1, 2, 3
@@ -50,6 +50,17 @@ class Info(C.Structure):
                 ("tile_rounds_fp64", C.c_double)]
 
 
+class Request(C.Structure):
+    _fields_ = [("points", C.c_void_p), ("N", C.c_int64), ("d", C.c_int), ("kernel", Kernel), ("b", C.c_int),
+                ("eps", C.c_double), ("ldl", C.c_int), ("nrhs", C.c_int), ("rhs", C.c_void_p), ("opts", Opts)]
+
+
+class Result(C.Structure):
+    _fields_ = [("done", C.c_int), ("status", C.c_int), ("retried", C.c_int), ("sign", C.c_int),
+                ("logdet", C.c_double), ("wait_s", C.c_double), ("run_s", C.c_double), ("bytes", C.c_int64),
+                ("mean_rank", C.c_double)]
+
+
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 _lib = None
@@ -71,7 +82,7 @@ def _load():
     sig = {
         "tlr_opts_default": (None, [C.POINTER(Opts)]),
         "tlr_strerror": (C.c_char_p, [C.c_int]),
-        "tlr_create": (C.c_int, [C.POINTER(P), C.c_int, P, _ALLOC, _FREE, P]),
+        "tlr_create": (C.c_int, [C.POINTER(P), C.c_int, C.c_size_t, P, _ALLOC, _FREE, P]),
         "tlr_destroy": (C.c_int, [P]),
         "tlr_compress": (C.c_int, [P, P, C.c_int64, C.c_int, C.POINTER(Kernel), C.c_int, C.c_double,
                                    C.POINTER(Opts), C.POINTER(P)]),
@@ -108,6 +119,10 @@ def _load():
         "tlr_dense_trsm": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, C.c_int]),
         "tlr_split_product": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, C.c_int, P, C.c_int]),
         "tlr_fp64_peak": (C.c_int, [P, D]),
+        "tlr_submit": (C.c_int, [P, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        "tlr_progress": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "tlr_poll": (C.c_int, [P, C.c_uint64, C.POINTER(Result), P, C.c_int64]),
+        "tlr_split_planes": (C.c_int, [P, C.POINTER(C.c_int64), D, C.c_int]),
         "tlr_launch_count": (C.c_int64, [P]),
         "tlr_profile": (C.c_int, [P, C.c_int, D, C.POINTER(C.c_int64), C.c_int]),
     }
@@ -168,7 +183,7 @@ def kd_order(points: np.ndarray, b: int) -> np.ndarray:
 class Context:
     """A library context bound to one GPU and one CUDA stream (torch's current stream by default)."""
 
-    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = True):
+    def __init__(self, device: int = 0, stream=None, torch_allocator: bool = True, hbm_budget: int = 0):
         import torch
         L = _load()
         self.torch = torch
@@ -191,7 +206,8 @@ class Context:
             alloc, free = _ALLOC(_a), _FREE(_f)
             self._cbs = (alloc, free)
         h = P()
-        _check(L.tlr_create(C.byref(h), device, P(self.stream.cuda_stream), alloc, free, None), "tlr_create")
+        _check(L.tlr_create(C.byref(h), device, int(hbm_budget), P(self.stream.cuda_stream), alloc, free, None),
+               "tlr_create")
         self.h = h
 
     def close(self):
@@ -320,6 +336,43 @@ class Context:
         ln = (C.c_int64 * n)()
         _check(_load().tlr_profile(self.h, int(enable), ms, ln, n), "tlr_profile")
         return {p: (ms[i], ln[i]) for i, p in enumerate(self.PHASES)}
+
+    def split_planes(self, reset: bool = True) -> tuple[list, float]:
+        """Output blocks of the split products by 7-bit planes used (index 1..8) and chunk bytes read."""
+        c = (C.c_int64 * 9)()
+        by = C.c_double(0)
+        _check(_load().tlr_split_planes(self.h, c, C.byref(by), int(reset)), "tlr_split_planes")
+        return [c[i] for i in range(9)], by.value
+
+    # ---- serving queue (tlr_submit / tlr_progress / tlr_poll)
+    def submit(self, points: np.ndarray, b: int, eps: float, ell: float, nugget: float, rhs: np.ndarray | None = None,
+               opts: Opts | None = None, ldl: bool = False) -> int:
+        """Queue one factor + solve + logdet request; the library copies points and rhs."""
+        x = np.ascontiguousarray(points, dtype=np.float64)
+        N, d = x.shape
+        r = None if rhs is None else np.asfortranarray(np.asarray(rhs, dtype=np.float64).reshape(N, -1))
+        rq = Request(x.ctypes.data, N, d, Kernel(0, ell, nugget), b, eps, int(ldl), 0 if r is None else r.shape[1],
+                     None if r is None else r.ctypes.data, opts if opts is not None else default_opts())
+        t = C.c_uint64(0)
+        _check(_load().tlr_submit(self.h, C.byref(rq), C.byref(t)), "tlr_submit")
+        return t.value
+
+    def progress(self) -> tuple[int, int]:
+        """One scheduling step (admission, one column step, finished requests); (queued, in flight)."""
+        q, f = C.c_int(0), C.c_int(0)
+        _check(_load().tlr_progress(self.h, C.byref(q), C.byref(f)), "tlr_progress")
+        return q.value, f.value
+
+    def poll(self, ticket: int, N: int = 0, nrhs: int = 0):
+        """None while the request runs; else (result dict, solution N x nrhs or None).  A finished
+        request is released by the poll that returns it."""
+        res = Result()
+        X = np.zeros((N, nrhs), order="F") if N and nrhs else None
+        _check(_load().tlr_poll(self.h, ticket, C.byref(res), X.ctypes.data if X is not None else None, max(N, 1)),
+               "tlr_poll")
+        if not res.done:
+            return None
+        return {f: getattr(res, f) for f, _ in Result._fields_}, X
 
     def fp64_peak(self) -> float:
         v = C.c_double(0)

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <map>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/tlr.h"
@@ -73,12 +74,19 @@ constexpr int GEMM_TK = 16;
 
 namespace tlr {
 struct SolvePlan;
+struct Server;
 }
 
 // ----------------------------------------------------------------------------------------
 // Library-owned objects.
 struct tlr_ctx {
   int device = 0;
+  // device bytes this context holds (every allocation goes through dalloc / dfree) and the serving
+  // queue's admission budget (tlr_create's hbm_budget; 0 = no limit)
+  size_t hbm_budget = 0;
+  size_t live_bytes = 0, peak_bytes = 0;
+  std::unordered_map<void*, size_t> live;
+  tlr::Server* server = nullptr;  // request queue of tlr_submit / tlr_progress / tlr_poll (serve.cu)
   cudaStream_t stream = nullptr;  // stream the next launch goes to (main or side)
   cudaStream_t main = nullptr;    // caller's stream
   cudaStream_t side = nullptr;    // library stream for work overlapped with the main stream
@@ -198,6 +206,7 @@ void site_flush(tlr_ctx* ctx);
 void site_report(tlr_ctx* ctx);
 
 // memory
+void server_destroy(tlr_ctx* ctx);  // serve.cu: frees every request still held
 void* dalloc(tlr_ctx* ctx, size_t bytes);
 void dfree(tlr_ctx* ctx, void* p);
 void* scratch(tlr_ctx* ctx, size_t bytes);
@@ -287,7 +296,7 @@ struct SlotDescT {
   T* Z;
   int ldx, ldx0, nb, k, i, r0, x0off, Ki, Kk, q, bs;
 };
-// FP64 products on BF16 tensor cores by exact splitting (k_ozaki.cu).  Operands are stored as 8
+// FP64 products on the 16-bit tensor cores by exact splitting (k_ozaki.cu).  Operands are stored as 8
 // planes of signed 7-bit chunks (int8, one byte per chunk); rows of a plane start on 16-byte
 // boundaries (the TMA rule), so leading dimensions along k are padded to oz_ld(K).
 inline __host__ __device__ int oz_ld(int K) { return (K + 15) / 16 * 16; }
@@ -305,6 +314,8 @@ struct OzColJob {
   // with emax (device: the block's largest |x| as FP64 bits) every column uses that block bound,
   // written to e[0]
   const unsigned long long* emax = nullptr;
+  // tld > 0: transposed output, element k of column c at Xs + q * plane + k * tld + c (k < K only)
+  int tld = 0;
 };
 // C (M x N, ldc) = A B (or C += A B), A(m, k) = A_q[k + m * lda] (rows along k) or, with acol,
 // A_q[m + k * lda] (columns along m); B(k, n) = B_q[k + n * ldb].  lda, ldb, the plane strides and
@@ -327,6 +338,10 @@ struct OzJob {
   int nsplit = 0, tiles_n = 1;
   int rule_n = 0;        // columns the split rule assumes (0: N), as for GemmJob
   int S = 8;             // chunk planes used (8: FP64-exact; fewer: both operands truncated to 7S bits)
+  // mixed precision: with tol > 0 each CTA uses the fewest planes s >= smin (at most S) whose error
+  // bound per entry, K (s + 1) 2^(eA + eB - 7 s), stays below tol (an absolute error)
+  double tol = 0.0;
+  int smin = 2;
   double* ws = nullptr;
   int* ctr = nullptr;
 };
@@ -339,6 +354,9 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs);
 // Synchronizes the stream and returns (and clears) the flag a split product sets when one of its
 // bounded waits ran out.
 int oz_timeout_flag(tlr_ctx* ctx);
+// CTAs of the split products by planes used (out[1..8]) and chunk bytes read (out[9]), since the
+// last reset
+void oz_stats(tlr_ctx* ctx, unsigned long long out[10], int reset);
 
 // one 16 x 16 output tile of a block-diagonal Gram product: slot, block column j
 // (j = k: the tile's own factor part), row chunk, column chunk
@@ -423,6 +441,14 @@ void scale_cols(tlr_ctx* ctx, int m, int n, const double* dvec, const double* X,
 void tril_mask(tlr_ctx* ctx, int n, double* A, int lda, int unit);
 void set_diag(tlr_ctx* ctx, int n, double* A, int lda, const double* d);
 void axpy_matrix(tlr_ctx* ctx, int m, int n, double alpha, const double* X, int ldx, double* Y, int ldy);
+
+// Argument rule shared by tlr_kernel_matvec and tlr_kernel_matvec_noalloc (the same Y = A X): the
+// exponential kernel with ell > 0 and nugget >= 0, 1 <= d <= 3, N > 0, nrhs >= 0, ldx, ldy >= N.
+inline bool kernel_product_args_ok(const double* pts, const tlr_kernel* k, const double* X, const double* Y, int64_t N,
+                                   int d, int nrhs, int64_t ldx, int64_t ldy) {
+  return pts && k && X && Y && N > 0 && d >= 1 && d <= 3 && nrhs >= 0 && ldx >= N && ldy >= N && k->ell > 0 &&
+         k->type == TLR_KERNEL_EXP && k->nugget >= 0;
+}
 
 // kdtree.cpp
 void kd_order(const double* pts, int64_t N, int d, int b, int64_t* perm);

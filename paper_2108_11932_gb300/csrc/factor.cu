@@ -33,6 +33,7 @@ struct Mat {
   tlr_opts o{};
   int ldl = 0;
   bool mixed = false;
+  bool mixed16 = false;  // truncated split products for the samples and projections (TLR_PREC_MIXED)
   tlr_status st = TLR_OK;
   bool live = true;
   int nb = 0, b = 0;
@@ -58,6 +59,11 @@ struct Mat {
   bool oz = false;
   std::vector<int8_t*> FUs;
   std::vector<int64_t> fuscap;
+  // the same planes transposed (row m of Urow_i contiguous along the panel's columns, row stride
+  // futcap[i], a multiple of 16; columns past ulen[i] are zero), so that the products with Urow_i
+  // as the left operand (Y += Urow_i W_i, B += Urow_k Z) also read it along k
+  std::vector<int8_t*> FUt;
+  std::vector<int64_t> futcap;
   // slices of F's V panels (written once, at column j) relative to each panel's bound
   std::vector<int8_t*> FVs;
   int* dFVe = nullptr;                 // per panel exponent (device, nb)
@@ -309,11 +315,11 @@ struct BatchSampler : Sampler {
         OzColJob c{reinterpret_cast<const double*>(sd[s].W + r0), ws_, we_, ldw, bs, 0, Ki};
         c.ldo = ldo;
         wcj.push_back(c);
-        OzJob y{M.FUs[i], ws_, d_one, we_, reinterpret_cast<double*>(Yo), (size_t)M.b * M.fuscap[i],
-                (size_t)ldo * bs, M.b, M.b, M.b, bs, Ki};
+        OzJob y{M.FUt[i], ws_, d_one, we_, reinterpret_cast<double*>(Yo), (size_t)M.b * M.futcap[i],
+                (size_t)ldo * bs, (int)M.futcap[i], M.b, M.b, bs, Ki};
         y.ldb = ldo;
-        y.acol = 1;
         y.accumulate = 1;
+        if (M.mixed16) y.tol = M.thr / (8.0 * std::sqrt((double)M.b));  // column norm of Y within thr / 8
         wyj.push_back(y);
         ws_ += (size_t)8 * ldo * bs;
         we_ += bs;
@@ -467,11 +473,12 @@ struct BatchSampler : Sampler {
         OzColJob c{reinterpret_cast<const double*>(sd[s].Z + r0), zs_, ze_, ldz, q[op], 0, M.Kk};
         c.ldo = ldo;
         zcj.push_back(c);
-        OzJob bj{M.FUs[M.k], zs_, d_one, ze_, reinterpret_cast<double*>(Bo), (size_t)M.b * M.fuscap[M.k],
-                 (size_t)ldo * q[op], M.b, M.b, M.b, q[op], M.Kk};
+        OzJob bj{M.FUt[M.k], zs_, d_one, ze_, reinterpret_cast<double*>(Bo), (size_t)M.b * M.futcap[M.k],
+                 (size_t)ldo * q[op], (int)M.futcap[M.k], M.b, M.b, q[op], M.Kk};
         bj.ldb = ldo;
-        bj.acol = 1;
         bj.accumulate = 1;
+        // the projection B_i = A(i,k)^T Q_i within thr / 8 in Frobenius norm (it enters the tile as Q B^T)
+        if (M.mixed16) bj.tol = M.thr / (8.0 * std::sqrt((double)M.b * q[op]));
         zbj.push_back(bj);
         zs_ += (size_t)8 * ldo * q[op];
         ze_ += q[op];
@@ -539,12 +546,13 @@ void panel_tile_norms(tlr_ctx* ctx, const tlr_mat* M, int j, std::vector<double>
 }
 
 void free_f32(tlr_ctx* ctx, Mat& M) {
+  for (Buf* bf : {&M.G, &M.G32, &M.E, &M.DV, &M.DV32, &M.Bc}) bf->release();  // per-matrix work buffers
   for (auto* v : {&M.AU32, &M.AV32, &M.FU32, &M.FV32})
     for (float*& p : *v) {
       dfree(ctx, p);
       p = nullptr;
     }
-  for (auto* v : {&M.FUs, &M.FVs, &M.AVs})
+  for (auto* v : {&M.FUs, &M.FUt, &M.FVs, &M.AVs})
     for (int8_t*& p : *v) {
       dfree(ctx, p);
       p = nullptr;
@@ -612,6 +620,7 @@ struct Session {
     M.b = A->b;
     M.k = 0;
     M.mixed = o.precision == TLR_PREC_FP32 && eps >= 1e-4;
+    M.mixed16 = o.precision == TLR_PREC_MIXED && eps >= 1e-4;
     const int nb = M.nb, b = M.b;
     tlr_mat* F = mat_new(A->N, A->d, b);
     M.F = F;
@@ -627,9 +636,14 @@ struct Session {
     if (M.oz) {
       M.FUs.assign(nb, nullptr);
       M.fuscap.assign(nb, 0);
+      M.FUt.assign(nb, nullptr);
+      M.futcap.assign(nb, 0);
       for (int i = 0; i < nb; ++i) {
         M.fuscap[i] = F->ucap[i];
         M.FUs[i] = static_cast<int8_t*>(dalloc(ctx, 8 * (size_t)b * M.fuscap[i]));
+        M.futcap[i] = oz_ld((int)F->ucap[i]);
+        M.FUt[i] = static_cast<int8_t*>(dalloc(ctx, 8 * (size_t)b * M.futcap[i]));
+        TLR_CUDA(cudaMemsetAsync(M.FUt[i], 0, 8 * (size_t)b * M.futcap[i], ctx->stream));
       }
       M.FVs.assign(nb, nullptr);
       M.dFVe = static_cast<int*>(dalloc(ctx, sizeof(int) * nb));
@@ -1230,6 +1244,22 @@ struct Session {
           sjb.plane = (size_t)b * M.fuscap[i];
           sjb.efix = 1;
           usl.push_back(sjb);
+          if (F->ulen[i] + r > M.futcap[i]) {  // grow the transposed planes (rows keep their columns)
+            const int64_t cap = oz_ld((int)std::max<int64_t>(F->ucap[i], F->ulen[i] + r));
+            int8_t* p = static_cast<int8_t*>(dalloc(ctx, 8 * (size_t)b * cap));
+            TLR_CUDA(cudaMemsetAsync(p, 0, 8 * (size_t)b * cap, ctx->stream));
+            if (F->ulen[i] > 0)
+              TLR_CUDA(cudaMemcpy2DAsync(p, (size_t)cap, M.FUt[i], (size_t)M.futcap[i], (size_t)F->ulen[i],
+                                         (size_t)8 * b, cudaMemcpyDeviceToDevice, ctx->stream));
+            dfree(ctx, M.FUt[i]);
+            M.FUt[i] = p;
+            M.futcap[i] = cap;
+          }
+          OzColJob tjb{Q + qoff[op], M.FUt[i] + F->ulen[i], nullptr, b, r, 0, b};
+          tjb.plane = (size_t)b * M.futcap[i];
+          tjb.efix = 1;
+          tjb.tld = (int)M.futcap[i];
+          usl.push_back(tjb);
         }
         F->ulen[i] += r;
       }
@@ -1304,7 +1334,7 @@ tlr_status tlr_session_add(tlr_session* s, tlr_mat* A, double eps, const tlr_opt
   tlr_opts o;
   if (opts) o = *opts; else tlr_opts_default(&o);
   if (o.bs <= 0) o.bs = 16;
-  if (o.bs > 64 || o.bs > A->b || (o.precision != TLR_PREC_FP64 && o.precision != TLR_PREC_FP32) ||
+  if (o.bs > 64 || o.bs > A->b || o.precision < TLR_PREC_FP64 || o.precision > TLR_PREC_MIXED ||
       (s->S.bs >= 0 && o.bs != s->S.bs))
     return TLR_ERR_ARG;
   SESSION_TRY

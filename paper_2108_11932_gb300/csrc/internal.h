@@ -19,6 +19,11 @@ struct Buf {
   Buf(const Buf&) = delete;
   Buf& operator=(const Buf&) = delete;
   ~Buf() { dfree(ctx, p); }
+  void release() {  // back to empty (the next need() allocates again)
+    dfree(ctx, p);
+    p = nullptr;
+    cap = 0;
+  }
   template <typename T>
   T* need(size_t elems) {
     const size_t bytes = std::max<size_t>(elems * sizeof(T), 256);
@@ -87,6 +92,7 @@ struct OzTiles {
   int* e;        // per-tile exponent (device)
   Buf* bx;       // workspace for the right operand's slices
   Buf* be;       // workspace for its column exponents
+  double thr8 = 0.0;  // mixed precision: 1/8 of the ARA threshold (0: every product FP64-exact)
 };
 void ara_dense_run(tlr_ctx* ctx, int nops, int n, const double* T, int bs, double eps, uint64_t seed, uint32_t stream,
                    uint32_t k, double* Q, double* B, std::vector<int>& q, AraStats& st, const OzTiles* oz = nullptr);

@@ -871,7 +871,7 @@ void logdet_reduce(tlr_ctx* ctx, int n, const double* diag_tiles, int b, int nb,
 
 // Exact kernel product Y = A X, A_ij = exp(-|x_i - x_j| / ell) + nugget delta_ij,
 // one thread per row, points of the column block staged in shared memory.
-constexpr int KMV_T = 128, KMV_R = 4;
+constexpr int KMV_T = 128, KMV_R = 8;
 __global__ void __launch_bounds__(KMV_T) k_kernel_matvec(const double* __restrict__ pts, int64_t N, int d,
                                                         double inv_ell, double nugget, int nr,
                                                         const double* __restrict__ X, int64_t ldx,

@@ -46,9 +46,7 @@ cudaError_t points_address(int dev, double** out) {
 extern "C" tlr_status tlr_kernel_matvec_noalloc(void* cuda_stream, const double* points_host, int64_t N,
                                                 int d, const tlr_kernel* kern, int nrhs, const double* X,
                                                 int64_t ldx, double* Y, int64_t ldy) {
-  if (!points_host || !kern || !X || !Y || N <= 0 || d < 1 || d > 3 || nrhs < 0 || ldx < N || ldy < N ||
-      !(kern->ell > 0) || kern->type != TLR_KERNEL_EXP || kern->nugget < 0)
-    return TLR_ERR_ARG;
+  if (!tlr::kernel_product_args_ok(points_host, kern, X, Y, N, d, nrhs, ldx, ldy)) return TLR_ERR_ARG;
   if (N * d > kMaxPointDoubles) return TLR_ERR_LIMIT;
   if (nrhs == 0) return TLR_OK;
   int dev = 0;
@@ -74,6 +72,7 @@ extern "C" tlr_status tlr_kernel_matvec_noalloc(void* cuda_stream, const double*
   try {
     tlr::kernel_matvec(&launch_ctx, pts, N, d, kern->ell, kern->nugget, nrhs, X, ldx, Y, ldy);
   } catch (const tlr::Error& e) {
+    cudaGetLastError();  // a failed launch leaves its error pending: do not hand it to the caller's next call
     return e.status;
   }
   return TLR_OK;

@@ -1,6 +1,6 @@
-// FP64 products on the BF16 tensor cores (tcgen05), exact to FP64 level, operands fed by TMA.
+// FP64 products on the 16-bit tensor cores (tcgen05), exact to FP64 level, operands fed by TMA.
 //
-// GB300 retires 2 FP64 FMAs per SM per clock but thousands of BF16 tensor-core FMAs, and the
+// GB300 retires 2 FP64 FMAs per SM per clock but thousands of 16-bit tensor-core FMAs, and the
 // method's large products -- the ARA samples Y = T Omega and projections B = T^T Q of the generated
 // tiles (Algorithm 1 on Section 6's kernel tiles), the sampling chains of Equation 2 with the
 // factor's U and V panels, batchTrsm -- are dense contractions.  They are computed by error-free
@@ -13,24 +13,27 @@
 //    entry, the bytes of the FP64 operand.  Truncation error < 2^(e-56).
 //  * The product keeps the chunk pairs (i, j) with i + j <= S + 1 (S = 8: every pair of weight
 //    >= 2^-63 of the block bounds; S < 8 truncates both operands to 7S bits, the precision knob of
-//    the mixed path).  Chunks are exact in BF16 (8 significant bits); a chunk product is below 2^14
+//    the mixed path).  Chunks are exact in FP16 (and BF16); a chunk product is below 2^14
 //    and the sum of one group g = i + j - 2 over 128 consecutive k, added over its g + 1 pairs, stays
 //    below 2^24: the FP32 accumulation of the tensor core is exact.  Every 128 k the group sums move
 //    from tensor memory to 32-bit integer totals (exact for K <= 16384), combined once at the end.
 //
 // Kernel structure (one CTA = 128 output rows x 16 output columns x one K slice, 320 threads):
-//  * warp 0: TMA producer.  3D boxes (k or m, row, slice) of the int8 chunk planes of A and B are
-//    copied by cp.async.bulk.tensor into a 3-stage ring (32 k per stage), mbarrier completion.
-//  * warps 2-5: converters.  Thread t owns row t of the A tile (and one stacked row of B): int8 chunks
-//    become BF16 in the canonical K-major layout of the tensor core (8-row x 16-byte core matrices;
-//    either orientation of A in HBM lands in the same layout).
-//  * warp 1: one thread issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate in tensor memory).
+//  * warp 0: TMA producer.  Boxes of the int8 chunk planes of A and B (one per plane) are copied by
+//    cp.async.bulk.tensor into a 3-stage ring (32 k per stage), mbarrier completion.  Operands
+//    stored along k are read through a 4D view (16 k, rows, k / 16, plane), so a stage holds each
+//    16-k half as [row][16 bytes] and a warp's 16-byte reads of consecutive rows are contiguous.
+//  * warps 2-9: converters.  Thread t owns row t of the A tile for the planes of its parity (and one
+//    stacked row of B): int8 chunks become FP16 (two byte permutes and one f16x2 subtraction per
+//    pair) in the canonical K-major layout of the tensor core (8-row x 16-byte core matrices; either
+//    orientation of A in HBM lands in the same layout).
+//  * warp 1: one thread issues tcgen05.mma (kind::f16, FP16 in, FP32 accumulate in tensor memory).
 //    For a 16-k step and A slice i, B is the stack [B_1 | ... | B_(S+1-i)] (N = 16 (S + 1 - i)) and
 //    the accumulator starts at the column block of group i - 1: every group sum accumulates in place.
 //    Two 128-column accumulator buffers alternate between 128-k windows.
-//  * warps 6-9: epilogue.  They drain each window's group sums (tcgen05.ld) into integer totals
-//    while the next window accumulates, then recombine in FP64 and store (or write split-K partials,
-//    summed in slice order by the last CTA of each output block).
+//  * warps 6-9 also drain each window's group sums (tcgen05.ld) into integer totals while the next
+//    window accumulates, then recombine in FP64 and store (or write split-K partials, summed in slice
+//    order by the last CTA of each output block).
 // Every wait is bounded: on a timeout the CTA sets a device flag, lets its copies land, frees its
 // tensor memory and returns; the host reports TLR_ERR_TIMEOUT.
 #include <cuda.h>
@@ -44,6 +47,9 @@
 namespace tlr {
 
 __device__ int g_oz_timeout = 0;
+// statistics: CTAs by planes used ([s], s = 1..8) and chunk bytes of the operands read ([9]: each
+// A block counted once per output-column block 0, each B block once per row block 0)
+__device__ unsigned long long g_oz_stats[10];
 
 namespace {
 
@@ -58,9 +64,9 @@ constexpr int OZ_THREADS = 320;
 constexpr int ST_A = OZ_S * OZ_TM * OZ_KS;        // int8 A per stage (32 KB)
 constexpr int ST_B = OZ_S * OZ_TN * OZ_KS;        // int8 B per stage (4 KB)
 constexpr int ST_BYTES = ST_A + ST_B;
-constexpr int BF_ASL = OZ_TM * OZ_KC * 2;         // one slice of the BF16 A chunk (4 KB)
+constexpr int BF_ASL = OZ_TM * OZ_KC * 2;         // one plane of the FP16 A chunk (4 KB)
 constexpr int BF_A = OZ_S * BF_ASL;
-constexpr int BF_B = OZ_S * OZ_TN * OZ_KC * 2;    // stacked BF16 B chunk, 128 rows (4 KB)
+constexpr int BF_B = OZ_S * OZ_TN * OZ_KC * 2;    // stacked FP16 B chunk, 128 rows (4 KB)
 constexpr int BF_BYTES = BF_A + BF_B;
 constexpr int CORE_K = OZ_TM * 16;                // A: byte stride between the two 8-k core columns
 constexpr int OZ_TMEM_COLS = 256;                 // two accumulator buffers of 8 x 16 columns
@@ -76,7 +82,8 @@ struct OzDev {
   double* C;
   double* ws;
   int* ctr;
-  int M, N, K, ldc, acol, accumulate, eB_stride, nsplit, tiles_n, S;
+  double tol;  // > 0: truncate to the fewest planes whose error bound per entry stays below tol
+  int M, N, K, ldc, acol, accumulate, eB_stride, nsplit, tiles_n, S, smin;
 };
 static_assert(alignof(OzDev) >= 64 && sizeof(OzDev) % 64 == 0, "tensor maps need 64-byte alignment");
 
@@ -114,12 +121,15 @@ __device__ __forceinline__ unsigned long long gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps until the phase completes (or 20 us
+// pass) instead of taking issue slots from the converter warps.
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
-  asm volatile("{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p;}"
-               : "=r"(ok)
-               : "r"(bar), "r"(parity)
-               : "memory");
+  asm volatile(
+      "{.reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p;}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(20000)
+      : "memory");
   return ok != 0;
 }
 // Bounded wait on a barrier phase; a timeout (or another role's abort) returns false.
@@ -161,17 +171,25 @@ __device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, int
       "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, int w,
+                                       uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+      : "memory");
+}
 // Shared-memory matrix descriptor, K-major, no swizzle: lbo = byte stride between core matrices
 // along K, sbo = byte stride between 8-row groups.
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
-// Instruction descriptor of kind::f16: D FP32, A and B BF16, both K-major, M x N.
+// Instruction descriptor of kind::f16: D FP32, A and B FP16, both K-major, M x N.
 __device__ __forceinline__ uint32_t umma_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
-__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, int acc) {
+__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, int acc) {
   asm volatile("{.reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;}" ::"r"(
                    dtmem),
                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
@@ -191,22 +209,49 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Two signed int8 chunks (bytes sel and sel + 1 of w) as packed BF16: 2^23 + (c + 128) is built in
-// the bits of an FP32 number, 2^23 + 128 is subtracted (exact), and the top half is the BF16 value.
-__device__ __forceinline__ float oz_c2f(uint32_t biased, uint32_t sel) {
-  return __int_as_float((int)__byte_perm(biased, 0x4B000000u, 0x7540u | sel)) - 8388736.0f;
+// Four signed int8 chunks (one word) -> two packed FP16 pairs: with u = c + 128 (the byte XOR
+// 0x80), the FP16 bit pattern 0x6400 + u is 1024 + u, and subtracting 1152 leaves c exactly.
+__device__ __forceinline__ uint32_t oz_hsub(uint32_t h) {
+  uint32_t r;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(h), "r"(0x64806480u));
+  return r;
 }
-__device__ __forceinline__ uint32_t oz_pack2(float lo, float hi) {
-  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632u);
+__device__ __forceinline__ void oz_cvt4(uint32_t w, uint32_t& lo, uint32_t& hi) {
+  const uint32_t u = w ^ 0x80808080u;
+  lo = oz_hsub(__byte_perm(u, 0x64646464u, 0x5140u));
+  hi = oz_hsub(__byte_perm(u, 0x64646464u, 0x7362u));
 }
-// 16 int8 chunks (4 words) -> 16 BF16 (8 words)
+// 16 int8 chunks (4 words) -> 16 FP16 (8 words)
 __device__ __forceinline__ void oz_cvt16(const uint32_t (&w)[4], uint32_t (&o)[8]) {
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const uint32_t b = w[q] ^ 0x80808080u;
-    o[2 * q] = oz_pack2(oz_c2f(b, 0), oz_c2f(b, 1));
-    o[2 * q + 1] = oz_pack2(oz_c2f(b, 2), oz_c2f(b, 3));
-  }
+  for (int q = 0; q < 4; ++q) oz_cvt4(w[q], o[2 * q], o[2 * q + 1]);
+}
+
+// Drain accumulator window w (buffer w & 1) of this thread's TMEM lane and release the buffer to
+// the MMA issuer.  Group g (weight 2^-7(g+2)) of a window is an integer below 2^24; the totals keep
+// hi = sum_{g<4} acc_g 2^(7(3-g)) and lo = sum_{g>=4} acc_g 2^(7(7-g)) per column, each below 2^45
+// per window and 2^52 over K <= 16384: exact in 64-bit integers.
+__device__ __forceinline__ bool oz_drain(int w, int S, uint32_t b_accf, uint32_t b_acce, uint32_t tmem, int lq,
+                                         volatile int* abort, long long (&hi)[OZ_TN], long long (&lo)[OZ_TN]) {
+  const int buf = w & 1;
+  if (!mbar_wait(b_accf + 8 * buf, (w >> 1) & 1, abort)) return false;
+  tc_fence_after();
+  const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + buf * 128;
+#pragma unroll
+  for (int g = 0; g < OZ_S; ++g)
+    if (g < S) {
+      uint32_t r[16];
+      tmem_ld16(ta + OZ_TN * g, r);
+#pragma unroll
+      for (int c = 0; c < OZ_TN; ++c) {
+        const long long v = (long long)__float2int_rn(__uint_as_float(r[c]));
+        if (g < 4) hi[c] += v << (7 * (3 - g));
+        else lo[c] += v << (7 * (7 - g));
+      }
+    }
+  tc_fence_before();
+  mbar_arrive(b_acce + 8 * buf);
+  return true;
 }
 
 }  // namespace
@@ -262,9 +307,10 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restric
   const int K = J.K;
   const int c = g - J.col0;
   const double* x = J.X + (size_t)c * J.ld;
-  const int ldo = J.ldo > 0 ? J.ldo : oz_ld(K);
+  const int ldo = J.tld > 0 ? K : (J.ldo > 0 ? J.ldo : oz_ld(K));
   const size_t plane = J.plane > 0 ? J.plane : (size_t)J.ncols * ldo;
-  int8_t* xs = J.Xs + (size_t)c * ldo;
+  const size_t kst = J.tld > 0 ? (size_t)J.tld : 1;  // stride of k in the output
+  int8_t* xs = J.tld > 0 ? J.Xs + c : J.Xs + (size_t)c * ldo;
   int e;
   if (J.efix != OZ_EFIX_NONE || J.emax) {
     e = J.emax ? oz_exponent(*J.emax) : J.efix;
@@ -294,7 +340,7 @@ __global__ void __launch_bounds__(256) k_oz_split_cols(const OzColJob* __restric
     int8_t s[OZ_S];
     if (k < K) oz_split(x[k], e, s);
 #pragma unroll
-    for (int q = 0; q < OZ_S; ++q) xs[(size_t)q * plane + k] = k < K ? s[q] : (int8_t)0;
+    for (int q = 0; q < OZ_S; ++q) xs[(size_t)q * plane + k * kst] = k < K ? s[q] : (int8_t)0;
   }
 }
 
@@ -307,19 +353,42 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
   const int tiles_n = Jp->tiles_n, nsplit = Jp->nsplit;
   if ((int)blockIdx.y >= tiles_n * nsplit) return;
   const int nt = blockIdx.y % tiles_n, split = blockIdx.y / tiles_n;
-  const int M = Jp->M, N = Jp->N, K = Jp->K, S = Jp->S, acol = Jp->acol;
+  const int M = Jp->M, N = Jp->N, K = Jp->K, acol = Jp->acol;
   const int m0 = blockIdx.x * OZ_TM, n0 = nt * OZ_TN;
   if (m0 >= M || n0 >= N) return;
+  // Planes used: S, or with a tolerance the fewest s >= smin whose bound K (s + 1) 2^(eA + eB - 7 s)
+  // on every entry's error (truncation of both operands to 7s bits plus the dropped chunk pairs;
+  // eB = the largest column exponent of this CTA) is below tol.  Uniform over the CTA.
+  int S = Jp->S;
+  if (Jp->tol > 0.0) {
+    int eb = -100000;
+    for (int c = 0; c < OZ_TN; ++c)
+      if (n0 + c < N) eb = max(eb, Jp->eB[(n0 + c) * Jp->eB_stride]);
+    const int ea = *Jp->eA;
+    for (int s = Jp->smin; s < S; ++s)
+      if (ldexp((double)K * (s + 1), ea + eb - 7 * s) <= Jp->tol) {
+        S = s;
+        break;
+      }
+  }
   const int nst_all = (K + OZ_KS - 1) / OZ_KS;
   const int sb = (int)((int64_t)nst_all * split / nsplit), se = (int)((int64_t)nst_all * (split + 1) / nsplit);
   const int nst = se - sb;            // TMA stages of this K slice
+  if (threadIdx.x == 0) {
+    const int kl = min(se * OZ_KS, K) - sb * OZ_KS;
+    unsigned long long by = 0;
+    if (nt == 0) by += (unsigned long long)S * min(OZ_TM, M - m0) * kl;
+    if (blockIdx.x == 0) by += (unsigned long long)S * min(OZ_TN, N - n0) * kl;
+    atomicAdd(&g_oz_stats[S], 1ull);
+    atomicAdd(&g_oz_stats[9], by);
+  }
   const int nch = 2 * nst;            // 16-k MMA steps
   const int nwin = (nch + OZ_CW - 1) / OZ_CW;
 
   extern __shared__ uint8_t oz_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = base;                           // OZ_NST stages of int8 A then B
-  uint8_t* bfb = ring + OZ_NST * ST_BYTES;        // 2 BF16 chunk buffers: A slices then stacked B
+  uint8_t* bfb = ring + OZ_NST * ST_BYTES;        // 2 FP16 chunk buffers: A planes then stacked B
   uint64_t* bars = reinterpret_cast<uint64_t*>(bfb + 2 * BF_BYTES);
   // barriers: full8[3] empty8[3] fullbf[2] emptybf[2] accf[2] acce[2] fin
   const uint32_t b_full8 = su32(bars), b_empty8 = su32(bars + 3), b_fullbf = su32(bars + 6),
@@ -332,10 +401,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
   if (tid == 0) {
     for (int s = 0; s < OZ_NST; ++s) {
       mbar_init(b_full8 + 8 * s, 1);
-      mbar_init(b_empty8 + 8 * s, 128);
+      mbar_init(b_empty8 + 8 * s, 256);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(b_fullbf + 8 * s, 128);
+      mbar_init(b_fullbf + 8 * s, 256);
       mbar_init(b_emptybf + 8 * s, 1);
       mbar_init(b_accf + 8 * s, 1);
       mbar_init(b_acce + 8 * s, 128);
@@ -359,7 +428,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
     if (lane == 0) {
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&Jp->ta) : "memory");
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&Jp->tb) : "memory");
-      const uint32_t bytes = (uint32_t)(S * (OZ_TM * OZ_KS + OZ_TN * OZ_KS));
+      const uint32_t bytes = (uint32_t)(S * (OZ_TM * OZ_KS + OZ_TN * OZ_KS));  // one box per plane
       int issued = 0;
       for (int s = 0; s < nst; ++s) {
         const int slot = s % OZ_NST;
@@ -367,9 +436,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
         uint8_t* st = ring + slot * ST_BYTES;
         const int k0 = (sb + s) * OZ_KS;
         mbar_expect_tx(b_full8 + 8 * slot, bytes);
-        if (acol) tma_3d(su32(st), &Jp->ta, m0, k0, 0, b_full8 + 8 * slot);
-        else tma_3d(su32(st), &Jp->ta, k0, m0, 0, b_full8 + 8 * slot);
-        tma_3d(su32(st + ST_A), &Jp->tb, k0, n0, 0, b_full8 + 8 * slot);
+        for (int q = 0; q < S; ++q) {
+          if (acol) tma_3d(su32(st + q * (OZ_TM * OZ_KS)), &Jp->ta, m0, k0, q, b_full8 + 8 * slot);
+          else tma_4d(su32(st + q * (OZ_TM * OZ_KS)), &Jp->ta, 0, m0, k0 / 16, q, b_full8 + 8 * slot);
+          tma_4d(su32(st + ST_A + q * (OZ_TN * OZ_KS)), &Jp->tb, 0, n0, k0 / 16, q, b_full8 + 8 * slot);
+        }
         issued = s + 1;
       }
       // every issued copy lands before the CTA can exit
@@ -391,7 +462,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
         const uint64_t bd = umma_desc(bbase, OZ_S * OZ_TN * 16, 128);
 #pragma unroll 1
         for (int i = 0; i < S; ++i)
-          umma_bf16(tmem + buf * 128 + OZ_TN * i, umma_desc(abase + i * BF_ASL, CORE_K, 128), bd,
+          umma_f16(tmem + buf * 128 + OZ_TN * i, umma_desc(abase + i * BF_ASL, CORE_K, 128), bd,
                     umma_idesc(OZ_TM, OZ_TN * (S - i)), (first && i == 0) ? 0 : 1);
         umma_commit(b_emptybf + 8 * sbf);
         if ((c % OZ_CW) == OZ_CW - 1 || c == nch - 1) umma_commit(b_accf + 8 * buf);
@@ -399,15 +470,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
       umma_commit(b_fin);  // arrives when every MMA of this thread has completed
       mbar_drain(b_fin, 0);
     }
-  } else if (warp < 6) {
-    // ---------------- converters: int8 chunks -> canonical BF16 layout
-    const int t = tid - 64;  // A row t; B stacked row t (slice t / 16, column t % 16) when t < 16 S
-    for (int s = 0; s < nst; ++s) {
+  } else {
+    // ---------------- workers (warps 2-9): int8 chunks -> canonical FP16 layout.  Thread t owns A row
+    // t for the planes of its parity (warps 2-5 even planes and the stacked B rows, warps 6-9 odd
+    // planes).  Warps 6-9 also drain the accumulator windows -- window w while converting the
+    // fourth chunk of window w + 1, so that conversion never waits for it -- and write the result.
+    const int t = (tid - 64) & (OZ_TM - 1);
+    const int par = (tid - 64) >> 7;
+    const bool epi = par == 1;
+    const int lq = warp & 3, row = 32 * lq + lane, m = m0 + row;
+    long long hi[OZ_TN], lo[OZ_TN];
+#pragma unroll
+    for (int c = 0; c < OZ_TN; ++c) hi[c] = lo[c] = 0;
+    int drained = 0;
+    bool ok = true;
+    for (int s = 0; s < nst && ok; ++s) {
       const int slot = s % OZ_NST;
       if (!mbar_wait(b_full8 + 8 * slot, (s / OZ_NST) & 1, abort)) break;
       const uint8_t* a8 = ring + slot * ST_BYTES;
       const uint8_t* b8 = a8 + ST_A;
-      bool ok = true;
       for (int h = 0; h < 2; ++h) {
         const int c = 2 * s + h, sbf = c & 1;
         if (!mbar_wait(b_emptybf + 8 * sbf, ((c >> 1) & 1) ^ 1, abort)) {
@@ -416,68 +497,69 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
         }
         uint8_t* abf = bfb + sbf * BF_BYTES;
         uint8_t* bbf = abf + BF_A;
-        for (int q = 0; q < S; ++q) {
-          uint32_t w[4], o[8];
-          if (acol) {  // stage image [q][k 32][m 128]
-            const uint8_t* p = a8 + q * (OZ_TM * OZ_KS) + (16 * h) * OZ_TM + t;
+        uint32_t w[OZ_S / 2][4];
+        if (acol) {  // stage image [q][k 32][m 128]: 16 byte loads per plane
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              w[u] = (uint32_t)p[(4 * u) * OZ_TM] | ((uint32_t)p[(4 * u + 1) * OZ_TM] << 8) |
-                     ((uint32_t)p[(4 * u + 2) * OZ_TM] << 16) | ((uint32_t)p[(4 * u + 3) * OZ_TM] << 24);
-          } else {  // stage image [q][m 128][k 32]
-            const uint4 v = *reinterpret_cast<const uint4*>(a8 + q * (OZ_TM * OZ_KS) + t * OZ_KS + 16 * h);
-            w[0] = v.x;
-            w[1] = v.y;
-            w[2] = v.z;
-            w[3] = v.w;
+          for (int u2 = 0; u2 < OZ_S / 2; ++u2) {
+            const int q = par + 2 * u2;
+            if (q < S) {
+              const uint8_t* p = a8 + q * (OZ_TM * OZ_KS) + (16 * h) * OZ_TM + t;
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                w[u2][u] = __byte_perm(
+                    __byte_perm((uint32_t)p[(4 * u) * OZ_TM], (uint32_t)p[(4 * u + 1) * OZ_TM], 0x0040u),
+                    __byte_perm((uint32_t)p[(4 * u + 2) * OZ_TM], (uint32_t)p[(4 * u + 3) * OZ_TM], 0x0040u), 0x5410u);
+            }
           }
-          oz_cvt16(w, o);
-          uint8_t* d = abf + q * BF_ASL + t * 16;
-          *reinterpret_cast<uint4*>(d) = make_uint4(o[0], o[1], o[2], o[3]);
-          *reinterpret_cast<uint4*>(d + CORE_K) = make_uint4(o[4], o[5], o[6], o[7]);
+        } else {  // stage image [q][half 2][m 128][16 k]: one contiguous 16-byte load per plane
+#pragma unroll
+          for (int u2 = 0; u2 < OZ_S / 2; ++u2) {
+            const int q = par + 2 * u2;
+            if (q < S) {
+              const uint4 v = *reinterpret_cast<const uint4*>(a8 + q * (OZ_TM * OZ_KS) + h * (OZ_TM * 16) + t * 16);
+              w[u2][0] = v.x;
+              w[u2][1] = v.y;
+              w[u2][2] = v.z;
+              w[u2][3] = v.w;
+            }
+          }
         }
-        if (t < OZ_TN * S) {  // B image [q][n 16][k 32] -> stacked row t
-          const uint4 v = *reinterpret_cast<const uint4*>(b8 + (t / OZ_TN) * (OZ_TN * OZ_KS) + (t % OZ_TN) * OZ_KS +
-                                                          16 * h);
-          const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u2 = 0; u2 < OZ_S / 2; ++u2) {
+          const int q = par + 2 * u2;
+          if (q < S) {
+            uint32_t o[8];
+            oz_cvt16(w[u2], o);
+            uint8_t* d = abf + q * BF_ASL + t * 16;
+            *reinterpret_cast<uint4*>(d) = make_uint4(o[0], o[1], o[2], o[3]);
+            *reinterpret_cast<uint4*>(d + CORE_K) = make_uint4(o[4], o[5], o[6], o[7]);
+          }
+        }
+        if (!epi && t < OZ_TN * S) {  // B image [q][half 2][n 16][16 k] -> stacked row t
+          const uint4 v = *reinterpret_cast<const uint4*>(b8 + (t / OZ_TN) * (OZ_TN * OZ_KS) + h * (OZ_TN * 16) +
+                                                          (t % OZ_TN) * 16);
+          const uint32_t wb[4] = {v.x, v.y, v.z, v.w};
           uint32_t o[8];
-          oz_cvt16(w, o);
+          oz_cvt16(wb, o);
           uint8_t* d = bbf + t * 16;
           *reinterpret_cast<uint4*>(d) = make_uint4(o[0], o[1], o[2], o[3]);
           *reinterpret_cast<uint4*>(d + OZ_S * OZ_TN * 16) = make_uint4(o[4], o[5], o[6], o[7]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(b_fullbf + 8 * sbf);
+        if (epi && c % OZ_CW == 3 && drained == c / OZ_CW - 1) {  // the previous window is complete
+          if (!oz_drain(drained, S, b_accf, b_acce, tmem, lq, abort, hi, lo)) ok = false;
+          ++drained;
+        }
       }
       mbar_arrive(b_empty8 + 8 * slot);
-      if (!ok) break;
     }
-  } else {
-    // ---------------- epilogue: window drains, FP64 recombination, store
-    const int lq = warp & 3, row = 32 * lq + lane, m = m0 + row;
-    int tot[OZ_S][OZ_TN];
-#pragma unroll
-    for (int g = 0; g < OZ_S; ++g)
-#pragma unroll
-      for (int c = 0; c < OZ_TN; ++c) tot[g][c] = 0;
-    for (int w = 0; w < nwin; ++w) {
-      const int buf = w & 1;
-      if (!mbar_wait(b_accf + 8 * buf, (w >> 1) & 1, abort)) break;
-      tc_fence_after();
-      const uint32_t ta = tmem + ((uint32_t)(32 * lq) << 16) + buf * 128;
-#pragma unroll
-      for (int g = 0; g < OZ_S; ++g)
-        if (g < S) {
-          uint32_t r[16];
-          tmem_ld16(ta + OZ_TN * g, r);
-#pragma unroll
-          for (int c = 0; c < OZ_TN; ++c) tot[g][c] += __float2int_rn(__uint_as_float(r[c]));
-        }
-      tc_fence_before();
-      mbar_arrive(b_acce + 8 * buf);
+    if (!epi) goto done;
+    while (ok && drained < nwin) {
+      if (!oz_drain(drained, S, b_accf, b_acce, tmem, lq, abort, hi, lo)) ok = false;
+      ++drained;
     }
-    // group g has weight 2^-7(g+2): hi = groups 0-3 (< 2^53), lo = groups 4-7 (< 2^53), both exact in
-    // 64-bit integers and in FP64; value = (hi 2^28 + lo) 2^-63 (one rounding)
+    // hi and lo (< 2^53: exact in FP64) carry groups 0-3 and 4-7; value = (hi 2^28 + lo) 2^-63 (one rounding)
     const int eA = *Jp->eA;
     double* Cp = Jp->C;
     const int ldc = Jp->ldc;
@@ -485,13 +567,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
 #pragma unroll
     for (int c = 0; c < OZ_TN; ++c) {
       const int n = n0 + c;
-      long long hi = 0, lo = 0;
-#pragma unroll
-      for (int g = 0; g < 4; ++g) hi += (long long)tot[g][c] << (7 * (3 - g));
-#pragma unroll
-      for (int g = 4; g < OZ_S; ++g) lo += (long long)tot[g][c] << (7 * (7 - g));
       if (m < M && n < N) {
-        double v = fma((double)hi, 268435456.0, (double)lo);
+        double v = fma((double)hi[c], 268435456.0, (double)lo[c]);
         v = ldexp(v, eA + Jp->eB[n * Jp->eB_stride] - 63);
         if (nsplit > 1) {
           Jp->ws[(size_t)split * MN + m + (size_t)n * M] = v;
@@ -525,6 +602,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
       }
     }
   }
+done:
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -590,21 +668,48 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 3D int8 map: dims (d0, d1, 8 planes), strides (s1, plane) bytes, box (b0, b1, S).
-void make_map(CUtensorMap* map, const int8_t* p, uint64_t d0, uint64_t d1, uint64_t s1, uint64_t plane, uint32_t b0,
-              uint32_t b1, uint32_t S) {
-  TLR_REQUIRE(reinterpret_cast<uintptr_t>(p) % 16 == 0 && s1 % 16 == 0 && plane % 16 == 0 && d0 > 0 && d1 > 0,
-              TLR_ERR_LIMIT, "split product: operand not on 16-byte boundaries");
-  const cuuint64_t dims[3] = {d0, d1, (cuuint64_t)OZ_S};
-  const cuuint64_t strides[2] = {s1, plane};
-  const cuuint32_t box[3] = {b0, b1, S};
-  const cuuint32_t es[3] = {1, 1, 1};
-  const CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<int8_t*>(p), dims, strides, box, es,
-                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+void encode(CUtensorMap* map, const int8_t* p, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+            const cuuint32_t* box) {
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = encode_fn()(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, rank, const_cast<int8_t*>(p), dims, strides, box,
+                                 es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   TLR_REQUIRE(r == CUDA_SUCCESS, TLR_ERR_CUDA, "cuTensorMapEncodeTiled failed");
 }
+void check16(const int8_t* p, uint64_t s1, uint64_t plane) {
+  TLR_REQUIRE(reinterpret_cast<uintptr_t>(p) % 16 == 0 && s1 % 16 == 0 && plane % 16 == 0, TLR_ERR_LIMIT,
+              "split product: operand not on 16-byte boundaries");
+}
+// Operand stored along k (element (row, k) at row * ld + k): 4D view (16 k, rows, k / 16, plane),
+// box (16, box_rows, 2, 1).  Rows must be readable (and zero) up to the next multiple of 16 past K.
+void map_kmajor(CUtensorMap* map, const int8_t* p, uint64_t K, uint64_t rows, uint64_t ld, uint64_t plane,
+                uint32_t box_rows) {
+  check16(p, ld, plane);
+  TLR_REQUIRE(K > 0 && rows > 0 && ld >= (uint64_t)oz_ld((int)K), TLR_ERR_LIMIT, "split product: bad operand shape");
+  const cuuint64_t dims[4] = {16, rows, (K + 15) / 16, (cuuint64_t)OZ_S};
+  const cuuint64_t strides[3] = {ld, 16, plane};
+  const cuuint32_t box[4] = {16, box_rows, 2, 1};
+  encode(map, p, 4, dims, strides, box);
+}
+// A stored along m (element (m, k) at k * ld + m): 3D view (m, k, plane), box (128, 32, 1).
+void map_mmajor(CUtensorMap* map, const int8_t* p, uint64_t M, uint64_t K, uint64_t ld, uint64_t plane) {
+  check16(p, ld, plane);
+  TLR_REQUIRE(K > 0 && M > 0, TLR_ERR_LIMIT, "split product: bad operand shape");
+  const cuuint64_t dims[3] = {M, K, (cuuint64_t)OZ_S};
+  const cuuint64_t strides[2] = {ld, plane};
+  const cuuint32_t box[3] = {(cuuint32_t)OZ_TM, (cuuint32_t)OZ_KS, 1};
+  encode(map, p, 3, dims, strides, box);
+}
 }  // namespace
+
+void oz_stats(tlr_ctx* ctx, unsigned long long out[10], int reset) {
+  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  TLR_CUDA(cudaMemcpyFromSymbol(out, g_oz_stats, sizeof(unsigned long long) * 10));
+  if (reset) {
+    const unsigned long long z[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    TLR_CUDA(cudaMemcpyToSymbol(g_oz_stats, z, sizeof(z)));
+  }
+}
 
 int oz_timeout_flag(tlr_ctx* ctx) {
   int v = 0;
@@ -656,9 +761,9 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
     OzDev& d = dev[u];
     memset(&d, 0, sizeof(d));
     const int ldb = j.ldb > 0 ? j.ldb : oz_ld(j.K);
-    if (j.acol) make_map(&d.ta, j.A, (uint64_t)j.M, (uint64_t)j.K, (uint64_t)j.lda, j.sA, OZ_TM, OZ_KS, j.S);
-    else make_map(&d.ta, j.A, (uint64_t)j.K, (uint64_t)j.M, (uint64_t)j.lda, j.sA, OZ_KS, OZ_TM, j.S);
-    make_map(&d.tb, j.B, (uint64_t)j.K, (uint64_t)j.N, (uint64_t)ldb, j.sB, OZ_KS, OZ_TN, j.S);
+    if (j.acol) map_mmajor(&d.ta, j.A, (uint64_t)j.M, (uint64_t)j.K, (uint64_t)j.lda, j.sA);
+    else map_kmajor(&d.ta, j.A, (uint64_t)j.K, (uint64_t)j.M, (uint64_t)j.lda, j.sA, OZ_TM);
+    map_kmajor(&d.tb, j.B, (uint64_t)j.K, (uint64_t)j.N, (uint64_t)ldb, j.sB, OZ_TN);
     d.eA = j.eA;
     d.eB = j.eB;
     d.C = j.C;
@@ -672,6 +777,8 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
     d.nsplit = j.nsplit;
     d.tiles_n = j.tiles_n;
     d.S = j.S;
+    d.tol = j.tol;
+    d.smin = std::max(1, std::min(j.smin, j.S));
     if (j.nsplit > 1) {
       d.ws = ws;
       d.ctr = ctr;

@@ -31,11 +31,19 @@ void* dalloc(tlr_ctx* ctx, size_t bytes) {
       throw Error(TLR_ERR_NOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
     }
   }
+  ctx->live[p] = bytes;
+  ctx->live_bytes += bytes;
+  ctx->peak_bytes = std::max(ctx->peak_bytes, ctx->live_bytes);
   return p;
 }
 
 void dfree(tlr_ctx* ctx, void* p) {
   if (!p) return;
+  auto it = ctx->live.find(p);
+  if (it != ctx->live.end()) {
+    ctx->live_bytes -= it->second;
+    ctx->live.erase(it);
+  }
   if (ctx->free_fn) ctx->free_fn(p, ctx->user);
   else cudaFreeAsync(p, ctx->stream);
 }
@@ -535,7 +543,7 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
 }
 
 // ---------------------------------------------------------------- dense operands
-// With slices (construction tiles: `oz`), both products run on BF16 tensor cores by exact
+// With chunk planes (construction tiles: `oz`), both products run on the tensor cores by exact
 // splitting (k_ozaki.cu): T Omega reads the row-oriented slices, T^T Q the column-oriented ones.
 struct DenseSampler : Sampler {
   tlr_ctx* ctx;
@@ -558,6 +566,7 @@ struct DenseSampler : Sampler {
         jobs.push_back(OzJob{oz->Sr + (size_t)ops[s] * 8 * n * n, Xs, oz->e + ops[s], ex, Ydst[s], (size_t)n * n,
                              (size_t)n * bs, n, n, n, bs, n});
         jobs.back().nsplit = 1;  // a batch of tiles fills the GPU without splitting K
+        jobs.back().tol = oz->thr8 / std::sqrt((double)n);  // column norm of the sample within thr / 8
       }
       oz_gemm(ctx, jobs);
       return;
@@ -585,6 +594,7 @@ struct DenseSampler : Sampler {
         jobs.push_back(OzJob{oz->Sc + op * (size_t)8 * n * n, xo, oz->e + op, ex + c0, B + op * (size_t)n * n,
                              (size_t)n * n, (size_t)n * q[op], n, n, n, q[op], n});
         jobs.back().nsplit = 1;
+        jobs.back().tol = oz->thr8 / std::sqrt((double)n * q[op]);  // Frobenius norm of B within thr / 8
         c0 += q[op];
       }
       oz_split_cols(ctx, cj);
@@ -735,6 +745,7 @@ static void compress_ordered_impl(tlr_ctx* ctx, const double* pts_dev, const int
       oz.e = bEt.need<int>((size_t)nt);
       oz.bx = &bXs;
       oz.be = &bEx;
+      if (o->precision == TLR_PREC_MIXED && eps >= 1e-4) oz.thr8 = eps / HALKO / 8.0;
       oz_split_tiles(ctx, nt, b, T, tmax, oz.Sc, oz.Sr, oz.e);
       ara_dense_run(ctx, nt, b, T, bs, eps, o->seed, STREAM_COMPRESS, 0, Q, B, q, as, &oz);
     } else {
@@ -1100,12 +1111,14 @@ const char* tlr_strerror(tlr_status s) {
   return "unknown status";
 }
 
-tlr_status tlr_create(tlr_ctx** out, int device, void* stream, tlr_alloc_fn alloc, tlr_free_fn free_fn, void* user) {
+tlr_status tlr_create(tlr_ctx** out, int device, size_t hbm_budget, void* stream, tlr_alloc_fn alloc,
+                      tlr_free_fn free_fn, void* user) {
   if (!out || ((alloc == nullptr) != (free_fn == nullptr))) return TLR_ERR_ARG;
   tlr_ctx* ctx = nullptr;
   ABI_BEGIN
   ctx = new tlr_ctx();
   ctx->device = device;
+  ctx->hbm_budget = hbm_budget;
   TLR_CUDA(cudaSetDevice(device));
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->main = ctx->stream;
@@ -1137,6 +1150,7 @@ tlr_status tlr_create(tlr_ctx** out, int device, void* stream, tlr_alloc_fn allo
 tlr_status tlr_destroy(tlr_ctx* ctx) {
   if (!ctx) return TLR_ERR_ARG;
   ABI_BEGIN
+  server_destroy(ctx);
   cudaStreamSynchronize(ctx->stream);
   cudaStreamSynchronize(ctx->side);
   if (ctx->site_out) {
@@ -1248,7 +1262,7 @@ tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* S, tlr_mat** D) {
 static tlr_status check_factor_args(const tlr_mat* A, double eps, const tlr_opts& o) {
   if (!A || !(eps > 0)) return TLR_ERR_ARG;
   if (A->state != 0) return TLR_ERR_STATE;
-  if (o.bs > 64 || o.bs > A->b || (o.precision != TLR_PREC_FP64 && o.precision != TLR_PREC_FP32) ||
+  if (o.bs > 64 || o.bs > A->b || o.precision < TLR_PREC_FP64 || o.precision > TLR_PREC_MIXED ||
       o.compensation < TLR_COMP_NONE || o.compensation > TLR_COMP_SCHUR)
     return TLR_ERR_ARG;
   return TLR_OK;
@@ -1431,9 +1445,7 @@ tlr_status tlr_matvec(tlr_ctx* ctx, const tlr_mat* F, int op, int nrhs, const do
 
 tlr_status tlr_kernel_matvec(tlr_ctx* ctx, const double* pts, int64_t N, int d, const tlr_kernel* kern, int nrhs,
                              const double* X, int64_t ldx, double* Y, int64_t ldy) {
-  if (!ctx || !pts || !kern || !X || !Y || N <= 0 || d < 1 || d > 3 || ldx < N || ldy < N || nrhs < 0 ||
-      !(kern->ell > 0))
-    return TLR_ERR_ARG;
+  if (!ctx || !kernel_product_args_ok(pts, kern, X, Y, N, d, nrhs, ldx, ldy)) return TLR_ERR_ARG;
   ABI_BEGIN
   Buf bp(ctx);
   double* dp = bp.need<double>((size_t)N * d);
@@ -1615,6 +1627,18 @@ tlr_status tlr_split_product(tlr_ctx* ctx, int trans, int n, int ncols, const do
   }
   oz_gemm(ctx, jobs);
   if (oz_timeout_flag(ctx)) return TLR_ERR_TIMEOUT;
+  return TLR_OK;
+  ABI_END
+}
+
+tlr_status tlr_split_planes(tlr_ctx* ctx, int64_t* counts, double* bytes, int reset) {
+  if (!ctx) return TLR_ERR_ARG;
+  ABI_BEGIN
+  unsigned long long st[10];
+  oz_stats(ctx, st, reset);
+  if (counts)
+    for (int s = 0; s < 9; ++s) counts[s] = s == 0 ? 0 : (int64_t)st[s];
+  if (bytes) *bytes = (double)st[9];
   return TLR_OK;
   ABI_END
 }

@@ -4,15 +4,15 @@ Each request asks for the TLR Cholesky (or LDL^T) of a synthetic covariance
 matrix (N points in [0,1]^d, exponential kernel with length scale ell), a solve
 with nrhs right-hand sides and the log-determinant -- the unit of work of a
 Gaussian-process likelihood sweep (Section 1 motivates the factorization by
-such likelihoods).  Requests arrive over time; the server admits an arrived
-request when its estimated device footprint fits the memory budget, builds its
-TLR matrix, and adds it to the factorization session: it joins the in-flight
-batch at the next column step, so its work overlaps on the device with the
-requests already running (continuous batching).  When its factorization
-finishes the server solves and takes the logdet; the factor stays resident
-until then and is released afterwards.  Latency = arrival to result.
+such likelihoods).  Requests arrive over time and are submitted to the
+library's serving queue, which admits them by its device bytes against the
+context's HBM budget, builds their TLR matrices and adds them to one
+factorization session: a request joins the in-flight batch at the next column
+step, so its work overlaps on the device with the requests already running
+(continuous batching).  Latency = arrival to result.
 
-All GPU work runs in the library; this module only schedules.
+All GPU work and the admission, retry and request bookkeeping run in the
+library; this module only generates the workload and submits at arrival times.
 """
 from __future__ import annotations
 
@@ -69,91 +69,55 @@ def make_requests(n: int, rate: float, seed: int, n_min: int = 4096, n_max: int 
     return out
 
 
-def footprint(req: Request, mean_rank: float = 48.0) -> int:
-    """Device bytes of a request while in flight: dense diagonal tiles, their inverses and the
-    working copy (3 N b), low-rank factors of A and L (2 x 2 (N^2/b)/2 r) and the ARA workspace."""
-    nb = max(1, req.N // req.b)
-    lowrank = 2 * 2 * (nb * (nb - 1) / 2) * req.b * mean_rank
-    work = nb * req.b * (req.b + 32)
-    return int(8 * (3 * req.N * req.b + lowrank + work + req.N * (req.nrhs + req.d)))
-
-
 class Server:
-    def __init__(self, ctx, budget_bytes: float = 150e9, precision: int = 0, bs: int = 16, nugget: float = 1e-4):
+    """Drives the library's serving queue (tlr_submit / tlr_progress / tlr_poll) with requests that
+    arrive over time.  The library admits them by its device bytes against the context's HBM budget,
+    factors them in one continuous batch, retries a loss of definiteness with a diagonal shift, and
+    solves and takes the logdet; this loop only submits at arrival times and collects results."""
+
+    def __init__(self, ctx, precision: int = 0, bs: int = 16, nugget: float = 1e-4):
         self.ctx = ctx
-        self.budget = budget_bytes
         self.precision = precision
         self.bs = bs
         self.nugget = nugget
 
     def run(self, requests: list[Request], keep_results: bool = False) -> dict:
-        import torch
-
         import paper_2108_11932_gb300 as T
         ctx = self.ctx
-        S = T.Session(ctx)
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        active: dict[int, tuple[Request, object]] = {}
-        resident = 0
+        active: dict[int, Request] = {}
         steps = 0
-        busy_s = 0.0
         t0 = time.perf_counter()
         while pending or active:
             now = time.perf_counter() - t0
-            # admission: arrived requests, in arrival order, while the budget allows
             while pending and pending[0].arrival <= now:
-                r = pending[0]
-                r.est_bytes = footprint(r)
-                if active and resident + r.est_bytes > self.budget:
-                    break
-                pending.popleft()
-                r.admitted = time.perf_counter() - t0
-                x = inputs.points(r.N, r.d, r.seed)
+                r = pending.popleft()
                 o = T.default_opts(bs=self.bs, seed=r.seed, precision=self.precision)
-                A = ctx.compress(x, r.b, r.eps, r.ell, self.nugget, o)
-                ticket = S.add(A, r.eps, o)
-                active[ticket] = (r, A)
-                resident += r.est_bytes
+                x = inputs.points(r.N, r.d, r.seed)
+                active[ctx.submit(x, r.b, r.eps, r.ell, self.nugget, inputs.rhs(r.N, r.nrhs, r.seed), o)] = r
             if not active:
-                if pending:
-                    time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+                time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
                 continue
-            ts = time.perf_counter()
-            S.step()
+            ctx.progress()
             steps += 1
             for t in list(active):
-                fin, st = S.poll(t)
-                if not fin:
+                got = ctx.poll(t, active[t].N, active[t].nrhs)
+                if got is None:
                     continue
-                r, A = active.pop(t)
-                r.status = st
-                if st != 0 and not getattr(r, "retried", False):
-                    # loss of definiteness at a loose threshold: refactor A + eps I (Section 5.1,
-                    # diagonal shift s <= eps), noted on the request
-                    A.free()
-                    r.retried = True
-                    x = inputs.points(r.N, r.d, r.seed)
-                    o = T.default_opts(bs=self.bs, seed=r.seed, precision=self.precision,
-                                       compensation=T.COMP_SHIFT, shift=r.eps)
-                    A = ctx.compress(x, r.b, r.eps, r.ell, self.nugget, o)
-                    active[S.add(A, r.eps, o)] = (r, A)
-                    continue
-                if st == 0:
-                    B = T.fortran(torch.tensor(inputs.rhs(r.N, r.nrhs, r.seed), device=f"cuda:{ctx.device}"))
-                    A.solve(B)
-                    r.logdet = A.logdet()[0]
-                    if keep_results:
-                        r.result = B.cpu().numpy()
+                r = active.pop(t)
+                res, X = got
                 r.finished = time.perf_counter() - t0
-                resident -= r.est_bytes
-                A.free()
-            busy_s += time.perf_counter() - ts
+                r.admitted = r.finished - res["run_s"]
+                r.status, r.logdet, r.retried = res["status"], res["logdet"], bool(res["retried"])
+                r.est_bytes = res["bytes"]
+                if keep_results:
+                    r.result = X
         wall = time.perf_counter() - t0
-        S.close()
         lat = np.array([r.finished - r.arrival for r in requests])
+        wait = np.array([max(r.admitted - r.arrival, 0.0) for r in requests])
         ok = sum(1 for r in requests if r.status == 0)
         retried = sum(1 for r in requests if getattr(r, "retried", False))
         return {"requests": len(requests), "ok": ok, "shift_retries": retried, "wall_s": wall,
                 "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
                 "mean_s": float(lat.mean()), "throughput_req_s": len(requests) / wall,
-                "steps": steps, "step_busy_s": busy_s}
+                "queue_wait_p50_s": float(np.percentile(wait, 50)), "steps": steps}

@@ -74,3 +74,44 @@ def test_autotune_choose_takes_the_nearest_class_of_the_same_dimension():
     assert autotune.choose(table, 12000, 2) == (256, 32, 16)   # bucket 14
     assert autotune.choose(table, 65536, 3) == (256, 16, 0)
     assert autotune.choose(table, 4096, 1) == autotune.DEFAULT  # no class of that dimension
+
+
+def test_kernel_products_share_their_argument_rule(lib):
+    """tlr_kernel_matvec and tlr_kernel_matvec_noalloc compute the same Y = A X and reject the same
+    arguments before touching the GPU: an unknown kernel type and a negative nugget among them."""
+    so = lib._load()
+    so.tlr_kernel_matvec_noalloc.restype = ctypes.c_int
+    pts = np.zeros((4, 2))
+    X = (ctypes.c_double * 4)()
+    Y = (ctypes.c_double * 4)()
+    dummy_ctx = ctypes.create_string_buffer(4096)  # never dereferenced: the arguments are rejected first
+    for ktype, ell, nug in [(7, 0.1, 0.0), (0, 0.1, -1e-4), (0, 0.0, 0.0), (0, -0.1, 0.0)]:
+        k = lib.Kernel(ktype, ell, nug)
+        a = so.tlr_kernel_matvec(ctypes.cast(dummy_ctx, ctypes.c_void_p), pts.ctypes.data, 4, 2, ctypes.byref(k), 1,
+                                 ctypes.cast(X, ctypes.c_void_p), 4, ctypes.cast(Y, ctypes.c_void_p), 4)
+        b = so.tlr_kernel_matvec_noalloc(None, ctypes.c_void_p(pts.ctypes.data), ctypes.c_int64(4), 2, ctypes.byref(k),
+                                         1, ctypes.cast(X, ctypes.c_void_p), ctypes.c_int64(4),
+                                         ctypes.cast(Y, ctypes.c_void_p), ctypes.c_int64(4))
+        assert a == b == lib.ERR_ARG, (ktype, ell, nug, a, b)
+
+
+def test_submit_rejects_bad_requests_without_gpu(lib):
+    """tlr_submit validates a request before it touches the context or the GPU."""
+    so = lib._load()
+    pts = np.zeros((8, 2))
+    dummy_ctx = ctypes.create_string_buffer(8192)  # never dereferenced for a rejected request
+    t = ctypes.c_uint64(0)
+
+    def req(**kw):
+        r = lib.Request(pts.ctypes.data, 8, 2, lib.Kernel(0, 0.1, 1e-4), 4, 1e-6, 0, 0, None, lib.default_opts(bs=4))
+        for k, v in kw.items():
+            setattr(r, k, v)
+        return r
+    bad = [req(N=0), req(d=4), req(eps=0.0), req(b=0), req(nrhs=2), req(ldl=2), req(kernel=lib.Kernel(1, 0.1, 0.0)),
+           req(kernel=lib.Kernel(0, 0.1, -1.0)), req(opts=lib.default_opts(bs=8)), req(points=None)]
+    for r in bad:
+        assert so.tlr_submit(ctypes.cast(dummy_ctx, ctypes.c_void_p), ctypes.byref(r), ctypes.byref(t)) == lib.ERR_ARG
+    assert so.tlr_submit(None, ctypes.byref(req()), ctypes.byref(t)) == lib.ERR_ARG
+    assert so.tlr_progress(None, None, None) == lib.ERR_ARG
+    res = lib.Result()
+    assert so.tlr_poll(None, 1, ctypes.byref(res), None, 1) == lib.ERR_ARG

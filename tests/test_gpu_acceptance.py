@@ -38,7 +38,7 @@ def ctx(T):
     return T.Context(0)
 
 
-def gpu_acceptance(T, ctx, workload, golden, kinds=("chol", "ldlt")):
+def gpu_acceptance(T, ctx, workload, golden, kinds=("chol", "ldlt", "chol_mixed")):
     """Factor the workload on the GPU at every eps of the golden record; return the measured values."""
     import torch
     w = inputs.WORKLOADS[workload]
@@ -47,12 +47,18 @@ def gpu_acceptance(T, ctx, workload, golden, kinds=("chol", "ldlt")):
     y = inputs.rhs(N, 1, w["seed"])
     x0 = inputs.start_vector(N, golden["power"]["seed"])
     dev = "cuda:0"
-    o = T.default_opts(bs=w["bs"], seed=w["seed"])
     facs, out = [], {}
     for key in golden["results"]:
         eps = float(key)
-        A = ctx.compress(x, b, eps, ell, nug, o)
+        mats = {}
         for kind in kinds:
+            prec = T.PREC_MIXED if kind == "chol_mixed" else T.PREC_FP64
+            if kind == "chol_mixed" and eps < 1e-4:  # the mixed path is FP64 below 1e-4
+                continue
+            o = T.default_opts(bs=w["bs"], seed=w["seed"], precision=prec)
+            if prec not in mats:
+                mats[prec] = ctx.compress(x, b, eps, ell, nug, o)
+            A = mats[prec]
             F = A.copy()
             comp = None
             try:
@@ -63,14 +69,15 @@ def gpu_acceptance(T, ctx, workload, golden, kinds=("chol", "ldlt")):
                 comp = "shift"
                 F.free()
                 F = A.copy()
-                os_ = T.default_opts(bs=w["bs"], seed=w["seed"], compensation=T.COMP_SHIFT, shift=eps)
+                os_ = T.default_opts(bs=w["bs"], seed=w["seed"], precision=prec, compensation=T.COMP_SHIFT, shift=eps)
                 (F.ldlt if kind == "ldlt" else F.potrf)(eps, os_)
             Yt = T.fortran(torch.tensor(y, device=dev))
             F.solve(Yt)
             ld, sign = F.logdet()
             out[(key, kind)] = dict(logdet=ld, sign=sign, compensation=comp, mean_rank=F.info()["mean_rank"])
             facs.append(((key, kind), F, Yt))
-        A.free()
+        for A in mats.values():
+            A.free()
     # residuals with the exact kernel matrix on the GPU
     Xs = T.fortran(torch.cat([f[2] for f in facs], dim=1))
     AX = ctx.kernel_matvec(x, ell, nug, Xs).cpu().numpy()
@@ -98,10 +105,11 @@ def check(golden, got):
     bad = []
     for key, res in golden["results"].items():
         eps = float(key)
-        for kind in ("chol", "ldlt"):
-            if (key, kind) not in got or kind not in res:
+        for kind in ("chol", "ldlt", "chol_mixed"):
+            ref = "chol" if kind == "chol_mixed" else kind  # the mixed path meets the FP64 path's rule
+            if (key, kind) not in got or ref not in res:
                 continue
-            g, o = got[(key, kind)], res[kind]
+            g, o = got[(key, kind)], res[ref]
             if not g["backward_error"] <= max(2 * o["backward_error"], 10 * eps):
                 bad.append((key, kind, "backward error", g["backward_error"], o["backward_error"]))
             if not g["residual"] <= 2 * o["residual"]:
@@ -120,7 +128,7 @@ def test_full_size_acceptance_against_svd_oracle(T, ctx, workload):
     golden = json.load(open(path))
     got = gpu_acceptance(T, ctx, workload, golden)
     for (key, kind), g in sorted((k, v) for k, v in got.items() if isinstance(k, tuple)):
-        o = golden["results"][key][kind]
+        o = golden["results"][key]["chol" if kind == "chol_mixed" else kind]
         print(f"{workload} eps={key} {kind}: backward error {g['backward_error']:.3e} (oracle "
               f"{o['backward_error']:.3e}), residual {g['residual']:.3e} (oracle {o['residual']:.3e}), logdet "
               f"{g['logdet']:.10g} (oracle {o['logdet']:.10g}), mean rank {g['mean_rank']:.2f} (oracle "

@@ -479,14 +479,17 @@ def test_acceptance_cov2d_4k_against_svd_oracle(T, ctx, ldl):
 
 
 # ------------------------------------------------------------------ mixed precision (FP32 sampling chains)
-@pytest.mark.parametrize("eps,ldl", [(1e-2, False), (1e-4, False), (1e-4, True)])
-def test_mixed_precision_meets_acceptance(T, ctx, eps, ldl):
-    """FP32 sampling/projection (FP64 orthogonalization, potrf, trsm) meets the same acceptance rule."""
+@pytest.mark.parametrize("eps,ldl,prec", [(1e-2, False, 1), (1e-4, False, 1), (1e-4, True, 1),
+                                          (1e-2, False, 2), (1e-4, False, 2), (1e-4, True, 2), (1e-2, True, 2)])
+def test_mixed_precision_meets_acceptance(T, ctx, eps, ldl, prec):
+    """Mixed sampling/projection products (FP64 orthogonalization, potrf, trsm) meet the same acceptance
+    rule as the FP64 path: FP32 chains (prec 1) or products truncated to fewer 7-bit planes on the
+    16-bit tensor cores (prec 2; the construction truncates too)."""
     w = inputs.WORKLOADS["cov2d_4k"]
     x = inputs.points(w["N"], w["d"], w["seed"])
-    A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=0))
+    A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=0, precision=prec))
     F32 = A.copy()
-    (F32.ldlt if ldl else F32.potrf)(eps, T.default_opts(bs=w["bs"], seed=0, precision=T.PREC_FP32))
+    (F32.ldlt if ldl else F32.potrf)(eps, T.default_opts(bs=w["bs"], seed=0, precision=prec))
     F64 = A.copy()
     (F64.ldlt if ldl else F64.potrf)(eps, T.default_opts(bs=w["bs"], seed=0))
     Ao = tlr.build(x, w["b"], eps, w["ell"], w["nugget"])
@@ -507,14 +510,42 @@ def test_mixed_precision_meets_acceptance(T, ctx, eps, ldl):
     assert abs(ld32 - ld64) <= 1e-3 * abs(ld64)
 
 
-def test_mixed_precision_falls_back_to_fp64_below_1e4(T, ctx):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_precision_falls_back_to_fp64_below_1e4(T, ctx, prec):
     w = CASES["cov2d_2k"]
     x = inputs.points(w["N"], w["d"], w["seed"])
     A = ctx.compress(x, w["b"], w["eps"], w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=7))
-    F32 = A.copy().potrf(w["eps"], T.default_opts(bs=w["bs"], seed=7, precision=T.PREC_FP32))
+    Am = ctx.compress(x, w["b"], w["eps"], w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=7, precision=prec))
+    assert np.array_equal(A.ranks(), Am.ranks())
+    F32 = Am.copy().potrf(w["eps"], T.default_opts(bs=w["bs"], seed=7, precision=prec))
     F64 = A.copy().potrf(w["eps"], T.default_opts(bs=w["bs"], seed=7))
     assert np.array_equal(F32.ranks(), F64.ranks())
     assert F32.logdet()[0] == F64.logdet()[0]
+
+
+def test_truncated_planes_are_chosen_per_block_within_the_bound(T, ctx):
+    """The mixed path's products use fewer 7-bit planes at eps = 1e-2 than at 1e-4, never fewer than 2,
+    and every block of an FP64 run uses all 8 (tlr_split_planes); the mixed construction's tiles
+    stay within eps of the FP64 construction's in 2-norm."""
+    w = inputs.WORKLOADS["cov2d_4k"]
+    x = inputs.points(w["N"], w["d"], w["seed"])
+    used = {}
+    for eps, prec in [(1e-2, 2), (1e-4, 2), (1e-2, 0)]:
+        ctx.split_planes(reset=True)
+        A = ctx.compress(x, w["b"], eps, w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=0, precision=prec))
+        A.copy().potrf(eps, T.default_opts(bs=w["bs"], seed=0, precision=prec))
+        c, _ = ctx.split_planes(reset=True)
+        used[(eps, prec)] = c
+        if prec == 2 and eps == 1e-2:
+            Am = A
+    assert sum(used[(1e-2, 0)][1:8]) == 0 and used[(1e-2, 0)][8] > 0
+    mean = lambda c: sum(i * c[i] for i in range(9)) / max(sum(c), 1)
+    assert used[(1e-2, 2)][1] == 0 and mean(used[(1e-2, 2)]) < mean(used[(1e-4, 2)]) < 8
+    A64 = ctx.compress(x, w["b"], 1e-2, w["ell"], w["nugget"], T.default_opts(bs=w["bs"], seed=0))
+    for (i, j) in [(1, 0), (5, 2), (15, 0)]:
+        U, V = Am.tile(i, j)
+        U6, V6 = A64.tile(i, j)
+        assert np.linalg.norm(U @ V.T - U6 @ V6.T, 2) <= 2e-2
 
 
 # ------------------------------------------------------------------ batched factorization of many matrices
