@@ -208,7 +208,7 @@ def run_ours(args, w, eps):
     T.build()
     ctx = T.Context(local)
     dev = f"cuda:{local}"
-    prec = T.PREC_FP64 if args.precision == "fp64" else T.PREC_FP32
+    prec = {"fp64": T.PREC_FP64, "fp32": T.PREC_FP32, "mixed": T.PREC_MIXED}[args.precision]
     x = inputs.points(w["N"], w["d"], w["seed"])
     perm = T.kd_order(x, w["b"])
     pts = torch.tensor(x[perm], device=dev)
@@ -331,7 +331,7 @@ def run_ours(args, w, eps):
     roofline_other = roof_split() if g64["ms"] >= gsp["ms"] else roof_gemm()
     out = {"metric": METRIC, "value": ms_per_step / 1e3, "unit": "s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if prec == T.PREC_FP64 else "f32+f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": {T.PREC_FP64: "f64", T.PREC_FP32: "f32+f64", T.PREC_MIXED: "f16-planes+f64"}[prec], "data": "synthetic",
            "config": {"workload": _workload_desc(w, eps, args.precision.upper()),
                       "step": "compress + potrf + solve(1 rhs) + logdet",
                       "l2": "no flush: matrix data (1 GB dense diagonal tiles + factors) is larger than the 129 MB L2",
@@ -705,7 +705,7 @@ def run_phases(args, w, eps):
     T.build()
     ctx = T.Context(0)
     x = inputs.points(w["N"], w["d"], w["seed"])
-    prec = T.PREC_FP64 if args.precision == "fp64" else T.PREC_FP32
+    prec = {"fp64": T.PREC_FP64, "fp32": T.PREC_FP32, "mixed": T.PREC_MIXED}[args.precision]
     o = T.default_opts(bs=w["bs"], seed=w["seed"], precision=prec)
     if args.profile_compress:
         ctx.profile(True)
@@ -740,7 +740,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--eps", type=float, default=1e-6)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--workload", default=WORKLOAD, choices=list(inputs.WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--oracle-tiles", type=int, default=6)

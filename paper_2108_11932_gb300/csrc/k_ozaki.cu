@@ -20,20 +20,20 @@
 //
 // Kernel structure (one CTA = 128 output rows x 16 output columns x one K slice, 320 threads):
 //  * warp 0: TMA producer.  Boxes of the int8 chunk planes of A and B (one per plane) are copied by
-//    cp.async.bulk.tensor into a 3-stage ring (32 k per stage), mbarrier completion.  Operands
+//    cp.async.bulk.tensor into a 2-stage ring (32 k per stage), mbarrier completion.  Operands
 //    stored along k are read through a 4D view (16 k, rows, k / 16, plane), so a stage holds each
 //    16-k half as [row][16 bytes] and a warp's 16-byte reads of consecutive rows are contiguous.
-//  * warps 2-9: converters.  Thread t owns row t of the A tile for the planes of its parity (and one
-//    stacked row of B): int8 chunks become FP16 (two byte permutes and one f16x2 subtraction per
-//    pair) in the canonical K-major layout of the tensor core (8-row x 16-byte core matrices; either
-//    orientation of A in HBM lands in the same layout).
+//  * warps 2-5: converters.  Thread t owns row t of the A tile (and one stacked row of B): int8 chunks
+//    become FP16 (two byte permutes and one f16x2 subtraction per pair) in the canonical K-major
+//    layout of the tensor core (8-row x 16-byte core matrices; either orientation of A in HBM lands
+//    in the same layout), into one of four chunk buffers, so conversion runs ahead of the MMAs.
 //  * warp 1: one thread issues tcgen05.mma (kind::f16, FP16 in, FP32 accumulate in tensor memory).
 //    For a 16-k step and A slice i, B is the stack [B_1 | ... | B_(S+1-i)] (N = 16 (S + 1 - i)) and
 //    the accumulator starts at the column block of group i - 1: every group sum accumulates in place.
 //    Two 128-column accumulator buffers alternate between 128-k windows.
-//  * warps 6-9 also drain each window's group sums (tcgen05.ld) into integer totals while the next
-//    window accumulates, then recombine in FP64 and store (or write split-K partials, summed in slice
-//    order by the last CTA of each output block).
+//  * warps 6-9: epilogue.  They drain each window's group sums (tcgen05.ld) into integer totals
+//    while the next window accumulates, then recombine in FP64 and store (or write split-K partials,
+//    summed in slice order by the last CTA of each output block).
 // Every wait is bounded: on a timeout the CTA sets a device flag, lets its copies land, frees its
 // tensor memory and returns; the host reports TLR_ERR_TIMEOUT.
 #include <cuda.h>
@@ -59,18 +59,21 @@ constexpr int OZ_TN = 16;     // output columns per CTA
 constexpr int OZ_KS = 32;     // k per TMA stage
 constexpr int OZ_KC = 16;     // k per MMA
 constexpr int OZ_CW = 8;      // 16-k steps per exact window (128 k)
-constexpr int OZ_NST = 3;     // int8 stages in flight
+constexpr int OZ_NST = 4;     // int8 stages in flight
+constexpr int OZ_NBF = 4;     // FP16 chunk buffers between the converters and the MMA issuer
 constexpr int OZ_THREADS = 320;
 constexpr int ST_A = OZ_S * OZ_TM * OZ_KS;        // int8 A per stage (32 KB)
 constexpr int ST_B = OZ_S * OZ_TN * OZ_KS;        // int8 B per stage (4 KB)
 constexpr int ST_BYTES = ST_A + ST_B;
-constexpr int BF_ASL = OZ_TM * OZ_KC * 2;         // one plane of the FP16 A chunk (4 KB)
-constexpr int BF_A = OZ_S * BF_ASL;
-constexpr int BF_B = OZ_S * OZ_TN * OZ_KC * 2;    // stacked FP16 B chunk, 128 rows (4 KB)
-constexpr int BF_BYTES = BF_A + BF_B;
-constexpr int CORE_K = OZ_TM * 16;                // A: byte stride between the two 8-k core columns
-constexpr int OZ_TMEM_COLS = 256;                 // two accumulator buffers of 8 x 16 columns
-constexpr int OZ_SMEM = 1024 + OZ_NST * ST_BYTES + 2 * BF_BYTES + 256;
+constexpr int BF_B = OZ_S * OZ_TN * OZ_KC * 2;    // stacked FP16 B chunk in shared memory, 128 rows (4 KB)
+constexpr int BF_BYTES = BF_B;
+// Tensor memory: two accumulator buffers of 8 groups x 16 columns (columns 0-255), then OZ_NBF FP16
+// A chunks (128 lanes = rows; 8 planes x 8 columns, each column two k values)
+constexpr int OZ_TMEM_COLS = 512;
+constexpr int OZ_TMEM_A = 256;
+constexpr int OZ_A_COLS = OZ_S * OZ_KC / 2;       // 64 columns per A chunk
+constexpr int OZ_SMEM = 1024 + OZ_NST * ST_BYTES + OZ_NBF * BF_BYTES + 256;
+static_assert(OZ_TMEM_A + OZ_NBF * OZ_A_COLS <= OZ_TMEM_COLS, "tensor memory budget");
 constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
 
 // Tensor maps live in the job table (global memory); CUtensorMap carries its own (>= 64-byte)
@@ -195,6 +198,18 @@ __device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t ad, uint64_t b
                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                : "memory");
 }
+// The same with the A operand in tensor memory (lane = row, each 32-bit column two consecutive k).
+__device__ __forceinline__ void umma_f16_ts(uint32_t dtmem, uint32_t atmem, uint64_t bd, uint32_t idesc, int acc) {
+  asm volatile("{.reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;}" ::"r"(
+                   dtmem),
+               "r"(atmem), "l"(bd), "r"(idesc), "r"(acc)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -227,12 +242,11 @@ __device__ __forceinline__ void oz_cvt16(const uint32_t (&w)[4], uint32_t (&o)[8
   for (int q = 0; q < 4; ++q) oz_cvt4(w[q], o[2 * q], o[2 * q + 1]);
 }
 
-// Drain accumulator window w (buffer w & 1) of this thread's TMEM lane and release the buffer to
-// the MMA issuer.  Group g (weight 2^-7(g+2)) of a window is an integer below 2^24; the totals keep
-// hi = sum_{g<4} acc_g 2^(7(3-g)) and lo = sum_{g>=4} acc_g 2^(7(7-g)) per column, each below 2^45
-// per window and 2^52 over K <= 16384: exact in 64-bit integers.
+// Drain accumulator window w (buffer w & 1) of this thread's TMEM lane into the integer totals (each
+// group of a window is an integer below 2^24; over K <= 16384 a total stays below 2^31) and release
+// the buffer to the MMA issuer.
 __device__ __forceinline__ bool oz_drain(int w, int S, uint32_t b_accf, uint32_t b_acce, uint32_t tmem, int lq,
-                                         volatile int* abort, long long (&hi)[OZ_TN], long long (&lo)[OZ_TN]) {
+                                         volatile int* abort, int (&tot)[OZ_S][OZ_TN]) {
   const int buf = w & 1;
   if (!mbar_wait(b_accf + 8 * buf, (w >> 1) & 1, abort)) return false;
   tc_fence_after();
@@ -243,11 +257,7 @@ __device__ __forceinline__ bool oz_drain(int w, int S, uint32_t b_accf, uint32_t
       uint32_t r[16];
       tmem_ld16(ta + OZ_TN * g, r);
 #pragma unroll
-      for (int c = 0; c < OZ_TN; ++c) {
-        const long long v = (long long)__float2int_rn(__uint_as_float(r[c]));
-        if (g < 4) hi[c] += v << (7 * (3 - g));
-        else lo[c] += v << (7 * (7 - g));
-      }
+      for (int c = 0; c < OZ_TN; ++c) tot[g][c] += __float2int_rn(__uint_as_float(r[c]));
     }
   tc_fence_before();
   mbar_arrive(b_acce + 8 * buf);
@@ -388,24 +398,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
   extern __shared__ uint8_t oz_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ring = base;                           // OZ_NST stages of int8 A then B
-  uint8_t* bfb = ring + OZ_NST * ST_BYTES;        // 2 FP16 chunk buffers: A planes then stacked B
-  uint64_t* bars = reinterpret_cast<uint64_t*>(bfb + 2 * BF_BYTES);
-  // barriers: full8[3] empty8[3] fullbf[2] emptybf[2] accf[2] acce[2] fin
-  const uint32_t b_full8 = su32(bars), b_empty8 = su32(bars + 3), b_fullbf = su32(bars + 6),
-                 b_emptybf = su32(bars + 8), b_accf = su32(bars + 10), b_acce = su32(bars + 12),
-                 b_fin = su32(bars + 14);
-  volatile int* abort = reinterpret_cast<volatile int*>(bars + 15);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 16);
+  uint8_t* bfb = ring + OZ_NST * ST_BYTES;        // OZ_NBF FP16 chunk buffers: A planes then stacked B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bfb + OZ_NBF * BF_BYTES);
+  // barriers: full8[OZ_NST] empty8[OZ_NST] fullbf[OZ_NBF] emptybf[OZ_NBF] accf[2] acce[2] fin
+  const uint32_t b_full8 = su32(bars), b_empty8 = su32(bars + OZ_NST), b_fullbf = su32(bars + 2 * OZ_NST),
+                 b_emptybf = su32(bars + 2 * OZ_NST + OZ_NBF), b_accf = su32(bars + 2 * OZ_NST + 2 * OZ_NBF),
+                 b_acce = b_accf + 16, b_fin = b_accf + 32;
+  volatile int* abort = reinterpret_cast<volatile int*>(bars + 2 * OZ_NST + 2 * OZ_NBF + 5);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * OZ_NST + 2 * OZ_NBF + 6);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
     for (int s = 0; s < OZ_NST; ++s) {
       mbar_init(b_full8 + 8 * s, 1);
-      mbar_init(b_empty8 + 8 * s, 256);
+      mbar_init(b_empty8 + 8 * s, 128);
+    }
+    for (int s = 0; s < OZ_NBF; ++s) {
+      mbar_init(b_fullbf + 8 * s, 128);
+      mbar_init(b_emptybf + 8 * s, 1);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(b_fullbf + 8 * s, 256);
-      mbar_init(b_emptybf + 8 * s, 1);
       mbar_init(b_accf + 8 * s, 1);
       mbar_init(b_acce + 8 * s, 128);
     }
@@ -452,37 +464,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
     if (lane == 0) {
       const uint32_t bf0 = su32(bfb);
       for (int c = 0; c < nch; ++c) {
-        const int sbf = c & 1;
-        if (!mbar_wait(b_fullbf + 8 * sbf, (c >> 1) & 1, abort)) break;
+        const int sbf = c % OZ_NBF;
+        if (!mbar_wait(b_fullbf + 8 * sbf, (c / OZ_NBF) & 1, abort)) break;
         const int w = c / OZ_CW, buf = w & 1;
         const bool first = (c % OZ_CW) == 0;
         if (first && !mbar_wait(b_acce + 8 * buf, ((w >> 1) & 1) ^ 1, abort)) break;
         tc_fence_after();
-        const uint32_t abase = bf0 + sbf * BF_BYTES, bbase = abase + BF_A;
-        const uint64_t bd = umma_desc(bbase, OZ_S * OZ_TN * 16, 128);
+        const uint64_t bd = umma_desc(bf0 + sbf * BF_BYTES, OZ_S * OZ_TN * 16, 128);
+        const uint32_t at = tmem + OZ_TMEM_A + sbf * OZ_A_COLS;
 #pragma unroll 1
         for (int i = 0; i < S; ++i)
-          umma_f16(tmem + buf * 128 + OZ_TN * i, umma_desc(abase + i * BF_ASL, CORE_K, 128), bd,
-                    umma_idesc(OZ_TM, OZ_TN * (S - i)), (first && i == 0) ? 0 : 1);
+          umma_f16_ts(tmem + buf * 128 + OZ_TN * i, at + i * (OZ_KC / 2), bd, umma_idesc(OZ_TM, OZ_TN * (S - i)),
+                      (first && i == 0) ? 0 : 1);
         umma_commit(b_emptybf + 8 * sbf);
         if ((c % OZ_CW) == OZ_CW - 1 || c == nch - 1) umma_commit(b_accf + 8 * buf);
       }
       umma_commit(b_fin);  // arrives when every MMA of this thread has completed
       mbar_drain(b_fin, 0);
     }
-  } else {
-    // ---------------- workers (warps 2-9): int8 chunks -> canonical FP16 layout.  Thread t owns A row
-    // t for the planes of its parity (warps 2-5 even planes and the stacked B rows, warps 6-9 odd
-    // planes).  Warps 6-9 also drain the accumulator windows -- window w while converting the
-    // fourth chunk of window w + 1, so that conversion never waits for it -- and write the result.
-    const int t = (tid - 64) & (OZ_TM - 1);
-    const int par = (tid - 64) >> 7;
-    const bool epi = par == 1;
-    const int lq = warp & 3, row = 32 * lq + lane, m = m0 + row;
-    long long hi[OZ_TN], lo[OZ_TN];
-#pragma unroll
-    for (int c = 0; c < OZ_TN; ++c) hi[c] = lo[c] = 0;
-    int drained = 0;
+  } else if (warp < 6) {
+    // ---------------- converters (warps 2-5): int8 chunks -> FP16.  A warp may reach only its quarter
+    // of the tensor-memory lanes, so thread (warp, lane) owns A row 32 (warp % 4) + lane, written to
+    // the chunk's A buffer in tensor memory (one 8-column store per plane); thread t = tid - 64 owns
+    // stacked B row t when t < 16 S, written to shared memory in the canonical K-major layout.
+    const int t = tid - 64;
+    const int row = 32 * (warp & 3) + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + OZ_TMEM_A;
     bool ok = true;
     for (int s = 0; s < nst && ok; ++s) {
       const int slot = s % OZ_NST;
@@ -490,52 +497,45 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
       const uint8_t* a8 = ring + slot * ST_BYTES;
       const uint8_t* b8 = a8 + ST_A;
       for (int h = 0; h < 2; ++h) {
-        const int c = 2 * s + h, sbf = c & 1;
-        if (!mbar_wait(b_emptybf + 8 * sbf, ((c >> 1) & 1) ^ 1, abort)) {
+        const int c = 2 * s + h, sbf = c % OZ_NBF;
+        if (!mbar_wait(b_emptybf + 8 * sbf, ((c / OZ_NBF) & 1) ^ 1, abort)) {
           ok = false;
           break;
         }
-        uint8_t* abf = bfb + sbf * BF_BYTES;
-        uint8_t* bbf = abf + BF_A;
-        uint32_t w[OZ_S / 2][4];
+        tc_fence_after();
+        uint8_t* bbf = bfb + sbf * BF_BYTES;
+        uint32_t w[OZ_S][4];
         if (acol) {  // stage image [q][k 32][m 128]: 16 byte loads per plane
 #pragma unroll
-          for (int u2 = 0; u2 < OZ_S / 2; ++u2) {
-            const int q = par + 2 * u2;
+          for (int q = 0; q < OZ_S; ++q)
             if (q < S) {
-              const uint8_t* p = a8 + q * (OZ_TM * OZ_KS) + (16 * h) * OZ_TM + t;
+              const uint8_t* p = a8 + q * (OZ_TM * OZ_KS) + (16 * h) * OZ_TM + row;
 #pragma unroll
               for (int u = 0; u < 4; ++u)
-                w[u2][u] = __byte_perm(
+                w[q][u] = __byte_perm(
                     __byte_perm((uint32_t)p[(4 * u) * OZ_TM], (uint32_t)p[(4 * u + 1) * OZ_TM], 0x0040u),
                     __byte_perm((uint32_t)p[(4 * u + 2) * OZ_TM], (uint32_t)p[(4 * u + 3) * OZ_TM], 0x0040u), 0x5410u);
             }
-          }
         } else {  // stage image [q][half 2][m 128][16 k]: one contiguous 16-byte load per plane
 #pragma unroll
-          for (int u2 = 0; u2 < OZ_S / 2; ++u2) {
-            const int q = par + 2 * u2;
+          for (int q = 0; q < OZ_S; ++q)
             if (q < S) {
-              const uint4 v = *reinterpret_cast<const uint4*>(a8 + q * (OZ_TM * OZ_KS) + h * (OZ_TM * 16) + t * 16);
-              w[u2][0] = v.x;
-              w[u2][1] = v.y;
-              w[u2][2] = v.z;
-              w[u2][3] = v.w;
+              const uint4 v = *reinterpret_cast<const uint4*>(a8 + q * (OZ_TM * OZ_KS) + h * (OZ_TM * 16) + row * 16);
+              w[q][0] = v.x;
+              w[q][1] = v.y;
+              w[q][2] = v.z;
+              w[q][3] = v.w;
             }
-          }
         }
+        const uint32_t ta = trow + sbf * OZ_A_COLS;
 #pragma unroll
-        for (int u2 = 0; u2 < OZ_S / 2; ++u2) {
-          const int q = par + 2 * u2;
+        for (int q = 0; q < OZ_S; ++q)
           if (q < S) {
             uint32_t o[8];
-            oz_cvt16(w[u2], o);
-            uint8_t* d = abf + q * BF_ASL + t * 16;
-            *reinterpret_cast<uint4*>(d) = make_uint4(o[0], o[1], o[2], o[3]);
-            *reinterpret_cast<uint4*>(d + CORE_K) = make_uint4(o[4], o[5], o[6], o[7]);
+            oz_cvt16(w[q], o);
+            tmem_st8(ta + q * (OZ_KC / 2), o);
           }
-        }
-        if (!epi && t < OZ_TN * S) {  // B image [q][half 2][n 16][16 k] -> stacked row t
+        if (t < OZ_TN * S) {  // B image [q][half 2][n 16][16 k] -> stacked row t
           const uint4 v = *reinterpret_cast<const uint4*>(b8 + (t / OZ_TN) * (OZ_TN * OZ_KS) + h * (OZ_TN * 16) +
                                                           (t % OZ_TN) * 16);
           const uint32_t wb[4] = {v.x, v.y, v.z, v.w};
@@ -545,21 +545,31 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
           *reinterpret_cast<uint4*>(d) = make_uint4(o[0], o[1], o[2], o[3]);
           *reinterpret_cast<uint4*>(d + OZ_S * OZ_TN * 16) = make_uint4(o[4], o[5], o[6], o[7]);
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
         mbar_arrive(b_fullbf + 8 * sbf);
-        if (epi && c % OZ_CW == 3 && drained == c / OZ_CW - 1) {  // the previous window is complete
-          if (!oz_drain(drained, S, b_accf, b_acce, tmem, lq, abort, hi, lo)) ok = false;
-          ++drained;
-        }
       }
       mbar_arrive(b_empty8 + 8 * slot);
     }
-    if (!epi) goto done;
-    while (ok && drained < nwin) {
-      if (!oz_drain(drained, S, b_accf, b_acce, tmem, lq, abort, hi, lo)) ok = false;
-      ++drained;
+  } else {
+    // ---------------- epilogue (warps 6-9): window drains, FP64 recombination, store
+    const int lq = warp & 3, row = 32 * lq + lane, m = m0 + row;
+    int tot[OZ_S][OZ_TN];
+#pragma unroll
+    for (int g = 0; g < OZ_S; ++g)
+#pragma unroll
+      for (int c = 0; c < OZ_TN; ++c) tot[g][c] = 0;
+    bool ok = true;
+    for (int w = 0; w < nwin && ok; ++w) ok = oz_drain(w, S, b_accf, b_acce, tmem, lq, abort, tot);
+    // group g has weight 2^-7(g+2): hi = groups 0-3 and lo = groups 4-7, both below 2^53 (exact in
+    // 64-bit integers and in FP64); value = (hi 2^28 + lo) 2^-63 (one rounding)
+    long long hi[OZ_TN], lo[OZ_TN];
+#pragma unroll
+    for (int c = 0; c < OZ_TN; ++c) {
+      hi[c] = ((long long)tot[0][c] << 21) + ((long long)tot[1][c] << 14) + ((long long)tot[2][c] << 7) + tot[3][c];
+      lo[c] = ((long long)tot[4][c] << 21) + ((long long)tot[5][c] << 14) + ((long long)tot[6][c] << 7) + tot[7][c];
     }
-    // hi and lo (< 2^53: exact in FP64) carry groups 0-3 and 4-7; value = (hi 2^28 + lo) 2^-63 (one rounding)
     const int eA = *Jp->eA;
     double* Cp = Jp->C;
     const int ldc = Jp->ldc;
@@ -602,7 +612,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
       }
     }
   }
-done:
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -681,7 +690,8 @@ void check16(const int8_t* p, uint64_t s1, uint64_t plane) {
               "split product: operand not on 16-byte boundaries");
 }
 // Operand stored along k (element (row, k) at row * ld + k): 4D view (16 k, rows, k / 16, plane),
-// box (16, box_rows, 2, 1).  Rows must be readable (and zero) up to the next multiple of 16 past K.
+// box (16, box_rows, 2, 1), so that a stage holds each 16-k half as [row][16 bytes].  Rows must be
+// readable (and zero) up to the next multiple of 16 past K.
 void map_kmajor(CUtensorMap* map, const int8_t* p, uint64_t K, uint64_t rows, uint64_t ld, uint64_t plane,
                 uint32_t box_rows) {
   check16(p, ld, plane);
