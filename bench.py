@@ -305,7 +305,7 @@ def run_ours(args, w, eps):
     info = infos[-1][1]
     factor_s = med["factor"]
     # Roofline of the dominant kernel: the FP64 batched GEMM k_gemm (all modes; DFMA-bound) or the
-    # tensor-core split product k_oz_gemm (HBM-bound), whichever takes more time in the step.
+    # tensor-core split product k_oz_mma (HBM-bound by design), whichever takes more time in the step.
     peak64 = ctx.fp64_peak()
     hbm_peak = _measured_hbm_gbs()
     g64 = {"ms": sum(gst[f]["ms"] for f in ("fp64_NN", "fp64_TN", "fp64_NT")),
@@ -331,12 +331,12 @@ def run_ours(args, w, eps):
         by = gsp["bytes"] / max(gsp["launches"], 1)
         sec = gsp["ms"] / 1e3 / max(gsp["launches"], 1)
         ach = by / sec / 1e9 if sec > 0 else 0.0
-        tpb = _profile_value("split_product_bf16.md", "traffic_per_algorithmic_byte")
-        return {"bound": "hbm", "kernel": "k_oz_gemm (FP64 products on BF16 tensor cores, exact splitting)",
+        tpb = _profile_value("split_product_tcgen05_cov2d_16k.md", "traffic_per_algorithmic_byte")
+        return {"bound": "hbm", "kernel": "k_oz_mma (FP64-exact split products on tcgen05 tensor cores, int8 chunk planes)",
                 "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak if hbm_peak else None,
                 "traffic": tpb * by if tpb is not None else None,
-                "traffic_source": "profiles/split_product_bf16.md: ncu DRAM bytes per algorithmic byte x live "
-                                  "algorithmic bytes per launch",
+                "traffic_source": "profiles/split_product_tcgen05_cov2d_16k.md: ncu DRAM bytes per algorithmic byte "
+                                  "x live algorithmic bytes per launch",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "fp64_equivalent_tflops": gsp["flops"] / gsp["ms"] / 1e9 if gsp["ms"] else 0.0,
                 "share_of_step": gsp["ms"] / ms_per_step, "launches": gsp["launches"], "bytes_per_launch": by,

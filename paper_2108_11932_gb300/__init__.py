@@ -317,8 +317,8 @@ class Context:
                "tlr_dense_trsm")
 
     def split_product(self, T, X, trans=False, out=None):
-        """C = T X (trans False/0, or 2: read T by columns) or T^T X (True/1) on BF16 tensor cores by exact
-        splitting."""
+        """C = T X (trans False/0, or 2: A read by columns) or T^T X (True/1) on the tcgen05 tensor cores by exact
+        splitting into 7-bit chunk planes."""
         n, ncols = T.shape[0], X.shape[1]
         C_ = out if out is not None else fortran(self.torch.empty((n, ncols), dtype=self.torch.float64,
                                                                    device=T.device))

@@ -110,6 +110,8 @@ struct tlr_ctx {
   // own), one array per stream
   int* split_ctr[2] = {nullptr, nullptr};
   size_t split_ctr_cap[2] = {0, 0};
+  // grid-barrier words of the fused orthogonalization kernel: {arrivals, generation} per stream
+  unsigned* orth_bar = nullptr;
   // Small host-pinned status buffer for per-round device->host reads.
   void* hstatus = nullptr;
   size_t hstatus_cap = 0;
@@ -185,7 +187,7 @@ void prof_mark(tlr_ctx* ctx, int phase);
 void prof_flush(tlr_ctx* ctx);
 // kernel families of the GEMM accounting: fp64 NN/TN/NT, fp32 NN/TN/NT
 void kprof_begin(tlr_ctx* ctx);
-// families: 0-2 FP64 k_gemm NN/TN/NT, 3-5 FP32 k_gemm, 6 split products (k_oz_gemm)
+// families: 0-2 FP64 k_gemm NN/TN/NT, 3-5 FP32 k_gemm, 6 split products (k_oz_mma)
 void kprof_end(tlr_ctx* ctx, int family, double flops, double bytes = 0);
 void kprof_flush(tlr_ctx* ctx);
 void site_tick(tlr_ctx* ctx, const char* file, int line);

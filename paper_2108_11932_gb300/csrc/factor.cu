@@ -580,12 +580,13 @@ struct Session {
   Buf bnrm, bQ, bTab, bInfo, bTmp, bTmpMain, bOm, bOm32, bW, bY32, bP, bZ, bQ32, bB32;
   Buf bOzMax, bOzS, bOzE, bOzX, bOzEx;  // split trsm products
   Buf bOzOs, bOzOe, bOzWs, bOzWe, bOne;  // split sampling / projection products
+  Buf bOzDs, bOzDe, bOzDm;               // split updateDense products (side stream)
   int* d_one = nullptr;
   AraStats total;
   explicit Session(tlr_ctx* c)
       : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bW(c), bY32(c), bP(c), bZ(c),
         bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c), bOzOs(c), bOzOe(c), bOzWs(c), bOzWe(c),
-        bOne(c) {
+        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c) {
     static const int one = 1;
     d_one = bOne.need<int>(1);
     TLR_CUDA(cudaMemcpyAsync(d_one, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -845,12 +846,30 @@ struct Session {
     // with its own workspaces and stays on the main stream.)
     const int nm = (int)mats.size();
     int* info = bInfo.need<int>((size_t)nm);
+    // updateDense on the tensor cores (side stream): D_k += E Urow_k^T with E = -[U_kj G_kj]_j split into
+    // chunk planes per column and the transposed U-panel planes as the right operand; exact integer totals
+    // need K <= 16384
+    auto dense_split = [&](const Mat& M) { return M.o.compensation != TLR_COMP_SCHUR && M.oz && M.Kk > 0 && M.Kk <= 16384; };
+    int8_t* dsp = nullptr;
+    int* dse = nullptr;
+    unsigned long long* dsm = nullptr;
     {  // the side stream must not reallocate its workspace: size it here
       std::vector<DenseTile> probe[2];
-      for (Mat* Mp : L)
+      int64_t del = 0, dn = 0;
+      for (Mat* Mp : L) {
         if (Mp->o.compensation != TLR_COMP_SCHUR)
           probe[Mp->ldl].push_back(DenseTile{nullptr, nullptr, nullptr, Mp->F->dinv, Mp->b, Mp->b});
+        if (dense_split(*Mp)) {
+          del += (int64_t)8 * Mp->b * Mp->Kk;
+          ++dn;
+        }
+      }
       bTmp.need<double>(std::max(dense_tmp_doubles(probe[0], 0), dense_tmp_doubles(probe[1], 1)));
+      if (dn) {
+        dsp = bOzDs.need<int8_t>((size_t)del);
+        dse = bOzDe.need<int>((size_t)dn);
+        dsm = bOzDm.need<unsigned long long>((size_t)dn);
+      }
     }
     TLR_CUDA(cudaMemsetAsync(info, 0xff, sizeof(int) * nm, ctx->main));
     TLR_CUDA(cudaEventRecord(ctx->ev_fork, ctx->main));
@@ -863,6 +882,9 @@ struct Session {
       if (S.empty()) continue;
       ctx->stream = pass == 0 ? ctx->side : ctx->main;
       std::vector<GemmJob<double>> je, jd;
+      std::vector<OzColJob> ecj;  // split updateDense: slices of E
+      std::vector<OzJob> edj;
+      std::vector<std::pair<const double*, int64_t>> emx;  // E blocks whose bound is taken
       std::vector<DiagJob> shifts;
       std::vector<DenseTile> tiles[2];  // by factorization kind (Cholesky, LDL^T)
       for (Mat* Mp : S) {
@@ -873,22 +895,41 @@ struct Session {
         const double* G = static_cast<const double*>(M.G.p);
         if (M.Kk > 0) {
           double* E = M.E.need<double>((size_t)b * M.Kk);
+          const bool sp = pass == 0 && dense_split(M);
           for (int j = 0; j < M.k; ++j) {
             const int rkj = F->rank[ix(F, M.k, j)];
             if (rkj == 0) continue;
             je.push_back(job<double>(NN, b, rkj, Uptr(F, M.k, j), b, G + M.goff[j], M.gld[j], rkj,
-                                     E + (size_t)b * F->uoff[ix(F, M.k, j)], b, 1.0, 0.0));
+                                     E + (size_t)b * F->uoff[ix(F, M.k, j)], b, sp ? -1.0 : 1.0, 0.0));
             M.fl_exec += 2.0 * b * rkj * rkj;
           }
-          GemmJob<double> g = job<double>(NT, b, b, E, b, F->Urow[M.k], b, M.Kk, Akk, b, -1.0, 1.0);
-          if (pass == 0) g.flags = GEMM_TRIL;
-          M.fl_exec += (pass == 0 ? 1.0 : 2.0) * b * b * M.Kk;
-          if (pass == 1) {  // full D_k into a scratch tile for the compensation
-            g.C = static_cast<double*>(M.DV.need<double>((size_t)b * b));  // reuse: D_k
-            g.alpha = 1.0;
-            g.beta = 0.0;
+          if (sp) {  // D_k += E Urow_k^T, E(m, k) read along m (its own column-major layout)
+            emx.push_back({E, (int64_t)b * M.Kk});
+            OzColJob c{E, dsp, dse, b, (int)M.Kk, 0, b};
+            c.emax = dsm;
+            ecj.push_back(c);
+            OzJob d{dsp, M.FUt[M.k], dse, d_one, Akk, (size_t)b * M.Kk, (size_t)b * M.futcap[M.k], b, b, b, b,
+                    (int)M.Kk};
+            d.acol = 1;
+            d.ldb = (int)M.futcap[M.k];
+            d.eB_stride = 0;
+            d.accumulate = 1;
+            edj.push_back(d);
+            dsp += (size_t)8 * b * M.Kk;
+            ++dse;
+            ++dsm;
+            M.fl_exec += 2.0 * b * b * M.Kk;  // the whole tile (the factorization reads its lower triangle)
+          } else {
+            GemmJob<double> g = job<double>(NT, b, b, E, b, F->Urow[M.k], b, M.Kk, Akk, b, -1.0, 1.0);
+            if (pass == 0) g.flags = GEMM_TRIL;
+            M.fl_exec += (pass == 0 ? 1.0 : 2.0) * b * b * M.Kk;
+            if (pass == 1) {  // full D_k into a scratch tile for the compensation
+              g.C = static_cast<double*>(M.DV.need<double>((size_t)b * b));  // reuse: D_k
+              g.alpha = 1.0;
+              g.beta = 0.0;
+            }
+            jd.push_back(g);
           }
-          jd.push_back(g);
         }
         if (M.o.compensation == TLR_COMP_SHIFT && M.o.shift != 0.0) shifts.push_back(DiagJob{Akk, b, b, M.o.shift});
         int mi = 0;
@@ -905,6 +946,12 @@ struct Session {
       }
       gemm<double>(ctx, NN, je);
       gemm<double>(ctx, NT, jd);
+      if (!edj.empty()) {
+        unsigned long long* m0 = static_cast<unsigned long long*>(bOzDm.p);
+        for (size_t u = 0; u < emx.size(); ++u) oz_absmax(ctx, 1, emx[u].second, emx[u].first, m0 + u);
+        oz_split_cols(ctx, ecj);
+        oz_gemm(ctx, edj);
+      }
       if (pass == 1) {
         // Section 5.1.1: A_kk - D_k + diag(rowsum |D_k - Dbar_k|), Dbar_k = Q Q^T D_k Q Q^T,
         // Q the eps-basis of D_k from ARA.

@@ -78,6 +78,21 @@ struct AraStats {
 };
 extern const double HALKO;
 extern const double TAU_DROP;
+
+// Fused orthogonalization round (k_orth.cu, block width 16 or 32): for every slot, BCGS2 of its sample block Y against its
+// basis Q (n x q, room for q + bs columns) and Cholesky-QR with dropping, in one launch; writes the
+// slot's {converged, kept} pair to status[2 s], its new basis columns at Q + q n, uses W as workspace.
+struct OrthSlot {
+  double* Q;
+  double* Y;
+  double* W;
+  int n, q;
+  double thr;
+};
+bool orth_fused_ok(int bs);
+void orth_round(tlr_ctx* ctx, int bs, const std::vector<OrthSlot>& slots, int* status, double* enorm, double tau, Buf& work);
+// 1 if a bounded wait of the orthogonalization kernel ran out since the last call (then cleared)
+int orth_timeout_flag(tlr_ctx* ctx);
 // nrow[op] = rows of operand op; thr[op] = its convergence threshold (eps / HALKO);
 // Q_op at Q + qoff[op] with room for nrow[op] x (nrow[op] + bs).
 void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::vector<double>& thr,

@@ -2,6 +2,7 @@
 #include <math.h>
 
 #include "common.h"
+#include "cholqr.cuh"
 
 namespace tlr {
 
@@ -398,107 +399,16 @@ __global__ void __launch_bounds__(32) k_cholqr_small(int bs, const double* __res
 #undef Ri
 }
 
-// Register-resident Cholesky-QR step for bs <= 32 (one warp per slot, lane c holds
-// column c of the Gram matrix).  Same decisions as k_cholqr_small, computed
-// right-looking: when column j is kept, every later column c is reduced by the
-// rank-one term R(j, :)^T R(j, c); a dropped column leaves the others unchanged.
-// The kept factor is embedded in an upper-triangular Rt whose dropped rows and
-// columns are the identity, so Rt^{-1} restricted to the kept indices is the
-// inverse of the kept factor, and every register index is a compile-time constant.
+// Register-resident Cholesky-QR step for bs <= 32 (one warp per slot, lane c holds column c of the
+// Gram matrix): the same decisions as k_cholqr_small, computed right-looking (cholqr.cuh).
 template <int BS>
 __global__ void __launch_bounds__(32) k_cholqr_reg(const double* __restrict__ Gall, double* __restrict__ Mall,
                                                    int* __restrict__ status, double* __restrict__ enorm,
                                                    const double* __restrict__ thrv, double tau, int first_pass,
                                                    const int* __restrict__ nk_in) {
-  const int s = blockIdx.x, lane = threadIdx.x;
-  const double* G = Gall + (size_t)s * BS * BS;
-  double* M = Mall + (size_t)s * BS * BS;
-  double g[BS];  // column `lane` of G, reduced in place
-#pragma unroll
-  for (int r = 0; r < BS; ++r) g[r] = (lane < BS) ? G[r + (size_t)lane * BS] : 0.0;
-  double gdiag = 0.0;
-#pragma unroll
-  for (int r = 0; r < BS; ++r)
-    if (r == lane) gdiag = g[r];
-  int n = BS;
-  const double thr = thrv[s];
-  double thr2 = thr * thr;
-  if (first_pass) {
-    double gmax = gdiag;
-    for (int o = 16; o; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-    const double e = sqrt(fmax(gmax, 0.0));
-    if (lane == 0) enorm[s] = e;
-    if (!(e > thr)) {
-      if (lane < BS) {
-#pragma unroll
-        for (int r = 0; r < BS; ++r) M[r + (size_t)lane * BS] = 0.0;
-      }
-      if (lane == 0) { status[2 * s] = 1; status[2 * s + 1] = 0; }
-      return;
-    }
-    if (lane == 0) status[2 * s] = 0;
-  } else {
-    n = nk_in[2 * s + 1];
-    thr2 = 0.0;
-  }
-  double rt[BS];      // rt[j] = Rt(j, lane)
-  double inv[BS];     // 1 / Rt(j, j), the same in every lane
-  unsigned mask = 0;  // kept columns
-#pragma unroll
-  for (int j = 0; j < BS; ++j) {
-    rt[j] = (lane == j) ? 1.0 : 0.0;
-    inv[j] = 1.0;
-    if (j < n) {
-      const double dj = __shfl_sync(0xffffffffu, g[j], j);  // pivot of column j
-      const double gjj = __shfl_sync(0xffffffffu, gdiag, j);
-      const bool kept = (dj > fmax(thr2, tau * gjj)) && (dj > 0.0) && isfinite(dj);
-      if (kept) {
-        // every later use multiplies (a warp-wide FP64 divide or square root costs as much as
-        // ten FMAs on this part, and the factor and its inverse need 3 BS of them)
-        inv[j] = rsqrt(dj);  // one reciprocal square root per pivot; R(j, j) = dj / sqrt(dj)
-        const double rjj = dj * inv[j];
-        const double rj = (lane == j) ? rjj : ((lane > j && lane < n) ? g[j] * inv[j] : 0.0);
-#pragma unroll
-        for (int a = j + 1; a < BS; ++a) {
-          const double rja = __shfl_sync(0xffffffffu, rj, a);
-          if (lane > j && lane < n) g[a] = fma(-rja, rj, g[a]);
-        }
-        rt[j] = rj;
-        mask |= 1u << j;
-      }
-    }
-  }
-  // decouple dropped columns: Rt(j, c) = 0 for kept j and dropped c != j
-  const bool mine = (lane < BS) && ((mask >> lane) & 1u);
-#pragma unroll
-  for (int j = 0; j < BS; ++j)
-    if (!mine && lane != j) rt[j] = 0.0;
-  // column `lane` of Rt^{-1} by back substitution: x[p] = -(sum_{q>p} Rt(p,q) x[q]) / Rt(p,p)
-  double x[BS];
-#pragma unroll
-  for (int p = BS - 1; p >= 0; --p) {
-    double acc = 0.0;
-#pragma unroll
-    for (int q = p + 1; q < BS; ++q) {
-      const double rpq = __shfl_sync(0xffffffffu, rt[p], q);
-      if (q <= lane) acc = fma(rpq, x[q], acc);
-    }
-    x[p] = (p == lane) ? inv[p] : ((p < lane) ? -acc * inv[p] : 0.0);
-  }
-  // M column pos(lane) = kept part of column `lane` of Rt^{-1}; zero elsewhere
-  const int nk = __popc(mask);
-  if (lane < BS) {
-#pragma unroll
-    for (int r = 0; r < BS; ++r) M[r + (size_t)lane * BS] = 0.0;
-  }
-  __syncwarp();
-  if (mine) {
-    const int pos = __popc(mask & ((1u << lane) - 1u));
-#pragma unroll
-    for (int p = 0; p < BS; ++p)
-      if (p <= lane && ((mask >> p) & 1u)) M[p + (size_t)pos * BS] = x[p];
-  }
-  if (lane == 0) status[2 * s + 1] = nk;
+  const int s = blockIdx.x;
+  cholqr_warp<BS>(Gall + (size_t)s * BS * BS, Mall + (size_t)s * BS * BS, status + 2 * s, enorm + s, thrv[s], tau,
+                  first_pass, first_pass ? 0 : nk_in[2 * s + 1]);
 }
 
 void cholqr_small(tlr_ctx* ctx, int nslots, int bs, const double* G, double* Mout, int* status,

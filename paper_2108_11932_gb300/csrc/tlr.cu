@@ -422,7 +422,7 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
   int nmax = 0;
   for (int v : nrow) nmax = std::max(nmax, v);
   const int slots = std::max(1, std::min(cf.max_slots > 0 ? cf.max_slots : nops, nops));
-  Buf bOm(ctx), bY(ctx), bW(ctx), bS(ctx), bG(ctx), bM(ctx), bSt(ctx), bE(ctx), bT(ctx);
+  Buf bOm(ctx), bY(ctx), bW(ctx), bS(ctx), bG(ctx), bM(ctx), bSt(ctx), bE(ctx), bT(ctx), bOr(ctx);
   double* Om = S.owns_omega() ? nullptr : bOm.need<double>((size_t)nmax * bs);
   double* Y = bY.need<double>((size_t)slots * nmax * bs);
   double* W = bW.need<double>((size_t)slots * nmax * bs);
@@ -460,11 +460,20 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
       if (Om) omega(ctx, cf.seed, cf.stream, cf.k, (uint32_t)t, nrow[ops_t[0]], bs, Om);
       S.sample(ops_t, t, Om, ydst);
     }
+    prof_mark(ctx, PH_ORTH);
+    if (orth_fused_ok(bs)) {  // both iterations below in one launch (k_orth.cu)
+      std::vector<OrthSlot> os(ns);
+      for (int s = 0; s < ns; ++s) {
+        const int op = active[s], n = nrow[op];
+        os[s] = OrthSlot{Q + qoff[op], Y + (size_t)s * nmax * bs, W + (size_t)s * nmax * bs, n, q[op], thr[op]};
+        st.flops += 8.0 * n * q[op] * bs + 6.0 * n * bs * bs;
+      }
+      orth_round(ctx, bs, os, status, en, TAU_DROP, bOr);
+    } else {
     for (int s = 0; s < ns; ++s) thr_h[s] = thr[active[s]];
     TLR_CUDA(cudaMemcpyAsync(thr_d, upload(ctx, thr_h.data(), sizeof(double) * ns), sizeof(double) * ns,
                              cudaMemcpyDeviceToDevice, ctx->stream));
     // ---- orthog, iteration 1: Y <- Y - Q (Q^T Y); G = Y^T Y
-    prof_mark(ctx, PH_ORTH);
     {
       std::vector<GemmJob<double>> j1, j2, j3;
       for (int s = 0; s < ns; ++s) {
@@ -517,6 +526,7 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
       }
       gemm<double>(ctx, NN, j4);
     }
+    }
     prof_mark(ctx, PH_SYNC);
     int* hs = static_cast<int*>(host_status(ctx, sizeof(int) * 2 * slots));
     d2h_sync(ctx, hs, status, sizeof(int) * 2 * ns);
@@ -538,6 +548,8 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
     active.swap(still);
     refill();
   }
+  if (orth_fused_ok(bs))
+    TLR_REQUIRE(!orth_timeout_flag(ctx), TLR_ERR_TIMEOUT, "orthogonalization: a bounded device wait ran out");
   prof_mark(ctx, PH_PROJECT);
   S.project(q);
 }
@@ -1122,7 +1134,12 @@ tlr_status tlr_create(tlr_ctx** out, int device, size_t hbm_budget, void* stream
   TLR_CUDA(cudaSetDevice(device));
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->main = ctx->stream;
-  TLR_CUDA(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  {  // the side stream carries the diagonal tile's dependent chain (the column's trsm waits for it): its
+     // CTAs are scheduled ahead of the main stream's when SMs free up
+    int lo = 0, hi = 0;
+    TLR_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    TLR_CUDA(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi));
+  }
   TLR_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
   TLR_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
   ctx->alloc = alloc;
@@ -1164,6 +1181,7 @@ tlr_status tlr_destroy(tlr_ctx* ctx) {
   dfree(ctx, ctx->scratch_side);
   dfree(ctx, ctx->split_ctr[0]);
   dfree(ctx, ctx->split_ctr[1]);
+  dfree(ctx, ctx->orth_bar);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   if (ctx->hstatus) cudaFreeHost(ctx->hstatus);

@@ -120,7 +120,7 @@ def _lowrank(n, r, seed, decay):
 @pytest.mark.parametrize("n,ncols,trans,off", [(256, 16, 0, 1), (256, 37, 1, 3), (1024, 16, 0, 1),
                                                (512, 70, 1, 2), (64, 1, 0, 0), (256, 37, 2, 3), (1024, 16, 2, 1)])
 def test_split_product_matches_fp64(T, ctx, n, ncols, trans, off):
-    """T X and T^T X on BF16 tensor cores by exact 7-bit splitting: error of an FP64 product.
+    """T X and T^T X on the tcgen05 tensor cores by exact 7-bit splitting: error of an FP64 product.
 
     T is an exponential-kernel tile between two point clusters (entries over several orders of
     magnitude, off = 0: the diagonal tile with its nugget); X is Gaussian with one scaled column.
@@ -186,9 +186,10 @@ def test_split_product_rejects_unaligned_size(T, ctx):
     assert ei.value.status == T.ERR_LIMIT
 
 
-def test_ara_dense_matches_oracle(T, ctx):
+@pytest.mark.parametrize("n", [256, 200])  # 200: row blocks and basis column blocks with ragged ends
+def test_ara_dense_matches_oracle(T, ctx, n):
     import torch
-    n, bs, eps = 256, 16, 1e-6
+    bs, eps = 16, 1e-6
     xo = inputs.points(2048, 2, 0)
     xo = xo[np.argsort(xo[:, 0])]
     ops = [kernel.tile(xo, 1, 0, n, 0.1, 1e-4), kernel.tile(xo, 5, 0, n, 0.1, 1e-4), np.zeros((n, n)),
