@@ -1107,6 +1107,7 @@ struct Session {
       int max_slots = 0;
       for (Mat* Mp : L) max_slots += Mp->o.max_slots > 0 ? Mp->o.max_slots : Mp->nb;
       AraConfig cf{bs, 0, STREAM_FACTOR, 0, max_slots};
+      cf.fused_all = true;  // slot results independent of the batch
       AraStats as;
       ara_run(ctx, dsmp, nrow, thr, cf, order, Q, qoff, q, as);
       total.rounds += as.rounds;

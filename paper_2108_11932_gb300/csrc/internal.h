@@ -70,7 +70,14 @@ struct AraConfig {
   uint64_t seed;      // Gaussian blocks drawn by the engine (when the sampler does not own them)
   uint32_t stream, k;
   int max_slots;
+  // every round's orthogonalization in the fused kernel (k_orth.cu).  Otherwise a round whose FP64
+  // work exceeds ORTH_FUSED_MAX_FMA runs as batched GEMMs and Cholesky-QR launches, which keep the FP64
+  // unit busier on large rounds; the choice depends on the round alone, so it is deterministic for a
+  // given input, but a slot's rounding then depends on the slots it shares a round with, which the
+  // factorization (whose batches span matrices and sessions) must not allow.
+  bool fused_all = false;
 };
+constexpr double ORTH_FUSED_MAX_FMA = 1.3e8;
 struct AraStats {
   int64_t rounds = 0;   // sum over operands of their rounds
   int64_t batches = 0;  // number of batched rounds

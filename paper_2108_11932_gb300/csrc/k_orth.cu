@@ -182,7 +182,7 @@ __device__ __forceinline__ bool ticket(int* cnt, int add, int target) {
 // whatever the step holds.
 template <int BS>
 __device__ void phase_qtx(const OrthHdr& H, const OrthDev* J, const int* pa, int pass, double* sm) {
-  constexpr int QG = 64 / BS;            // units per step
+  constexpr int QG = 128 / BS;           // units per step
   constexpr int NQ = QG * OR_CB;         // basis columns per step
   constexpr int PT = NQ * BS / OR_T;     // outputs per thread
   static_assert(NQ * BS % OR_T == 0, "step shape");

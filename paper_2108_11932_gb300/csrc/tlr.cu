@@ -436,6 +436,7 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
 
   std::vector<int> active;
   std::vector<int> round(nops, 0);
+  bool any_fused = false;
   size_t next = 0;
   auto refill = [&]() {
     while ((int)active.size() < slots && next < order.size()) active.push_back(order[next++]);
@@ -461,7 +462,14 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
       S.sample(ops_t, t, Om, ydst);
     }
     prof_mark(ctx, PH_ORTH);
-    if (orth_fused_ok(bs)) {  // both iterations below in one launch (k_orth.cu)
+    bool fused = orth_fused_ok(bs);
+    if (fused && !cf.fused_all) {
+      double fma = 0;
+      for (int s = 0; s < ns; ++s) fma += 4.0 * nrow[active[s]] * (double)bs * (q[active[s]] + bs);
+      fused = fma <= ORTH_FUSED_MAX_FMA;
+    }
+    any_fused |= fused;
+    if (fused) {  // both iterations below in one launch (k_orth.cu)
       std::vector<OrthSlot> os(ns);
       for (int s = 0; s < ns; ++s) {
         const int op = active[s], n = nrow[op];
@@ -548,7 +556,7 @@ void ara_run(tlr_ctx* ctx, Sampler& S, const std::vector<int>& nrow, const std::
     active.swap(still);
     refill();
   }
-  if (orth_fused_ok(bs))
+  if (any_fused)
     TLR_REQUIRE(!orth_timeout_flag(ctx), TLR_ERR_TIMEOUT, "orthogonalization: a bounded device wait ran out");
   prof_mark(ctx, PH_PROJECT);
   S.project(q);
