@@ -398,12 +398,13 @@ int64_t tlr_launch_count(const tlr_ctx* ctx);
 
 /* Measurement utility (not part of the method): per-launch CUDA-event accounting of the
  * batched products, by family: 0-2 FP64 k_gemm NN / TN / NT, 3-5 FP32 k_gemm NN / TN / NT,
- * 6 the tensor-core split products (FP64-equivalent flops).  Copies the accumulated
+ * 6 the tensor-core split products (FP64-equivalent flops), 7 the fused orthogonalization rounds
+ * (k_orth_round: 8 n q bs + 6 n bs^2 flops per slot).  Copies the accumulated
  * milliseconds, algorithmic flops (2 M N K per job, half for a triangular operand), algorithmic
  * bytes (split products only: slices read once, C written) and launch counts since the last call
  * (any pointer may be NULL; arrays of TLR_GEMM_FAMILIES), resets them, and turns the
  * accounting on (enable != 0) or off. */
-#define TLR_GEMM_FAMILIES 7
+#define TLR_GEMM_FAMILIES 8
 tlr_status tlr_gemm_stats(tlr_ctx* ctx, int enable, double* ms, double* flops, double* bytes, int64_t* launches);
 
 /* Measurement utility (not part of the method): phase profiler in the spirit

@@ -264,7 +264,7 @@ class Context:
         _check(_load().tlr_factor_batch(self.h, n, hs, ev, op, int(ldl), st), "tlr_factor_batch")
         return [st[i] for i in range(n)]
 
-    GEMM_FAMILIES = ["fp64_NN", "fp64_TN", "fp64_NT", "fp32_NN", "fp32_TN", "fp32_NT", "split_bf16"]
+    GEMM_FAMILIES = ["fp64_NN", "fp64_TN", "fp64_NT", "fp32_NN", "fp32_TN", "fp32_NT", "split_planes", "orth_fp64"]
 
     def gemm_stats(self, enable: bool = True) -> dict:
         """Return (and reset) per-family GEMM launch accounting; switch it on/off."""

@@ -187,7 +187,7 @@ void prof_mark(tlr_ctx* ctx, int phase);
 void prof_flush(tlr_ctx* ctx);
 // kernel families of the GEMM accounting: fp64 NN/TN/NT, fp32 NN/TN/NT
 void kprof_begin(tlr_ctx* ctx);
-// families: 0-2 FP64 k_gemm NN/TN/NT, 3-5 FP32 k_gemm, 6 split products (k_oz_mma)
+// families: 0-2 FP64 k_gemm NN/TN/NT, 3-5 FP32 k_gemm, 6 split products (k_oz_mma), 7 k_orth_round
 void kprof_end(tlr_ctx* ctx, int family, double flops, double bytes = 0);
 void kprof_flush(tlr_ctx* ctx);
 void site_tick(tlr_ctx* ctx, const char* file, int line);

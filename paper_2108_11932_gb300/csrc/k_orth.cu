@@ -73,7 +73,7 @@ __host__ __device__ constexpr int or_scap() { return BS == 16 ? 256 : 128; }
 // shared doubles of the largest phase (X - Q S with its Gram partials and Cholesky-QR)
 template <int BS>
 __host__ __device__ constexpr int or_smem() {
-  return BS * OR_LD + OR_QCAP + or_scap<BS>() * (BS + 1) + BS * BS + BS * BS;
+  return BS * OR_LD + 2 * OR_QCAP + or_scap<BS>() * (BS + 1) + BS * BS + BS * BS;
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -162,233 +162,350 @@ __device__ __forceinline__ double xm_entry(const double* Xs, int ldx, int r, con
   return acc;
 }
 
-// arrival ticket: true in the CTA whose `add` arrivals bring the count to `target` (that CTA resets it)
+// Arrival ticket: true in the CTA whose `add` arrivals bring the count to `target` (that CTA resets
+// it).  The CTA barrier orders its threads' writes before thread 0's device-scope fence and atomic (the
+// fence is cumulative), and thread 0's fence after a completing count orders the partials written by
+// the other CTAs before this CTA's reads of them.
 __device__ __forceinline__ bool ticket(int* cnt, int add, int target) {
   __shared__ int last;
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     last = atomicAdd(cnt, add) + add == target;
-    if (last) *cnt = 0;
+    if (last) {
+      *cnt = 0;
+      __threadfence();
+    }
   }
   __syncthreads();
-  if (last) __threadfence();
   return last != 0;
 }
 
 // S = Q^T X (X = Y in pass 0, W in pass 1) for the slots with a basis.  Units (row chunk rc, column
 // block cb), rc-major; a CTA takes up to QG consecutive units of one slot and chunk in one step (the rows
-// of X staged once).  Each output of a unit is the sum of two chains, rows 0-31 and 32-63 of the chunk,
-// whatever the step holds.
+// of X staged once), and loads the next step's basis tile into registers while it computes.  Each output
+// of a unit is the sum of two chains, rows 0-31 and 32-63 of the chunk, whatever the step holds.
 template <int BS>
 __device__ void phase_qtx(const OrthHdr& H, const OrthDev* J, const int* pa, int pass, double* sm) {
-  constexpr int QG = 128 / BS;           // units per step
+  constexpr int QG = 64 / BS;            // units per step
   constexpr int NQ = QG * OR_CB;         // basis columns per step
   constexpr int PT = NQ * BS / OR_T;     // outputs per thread
-  static_assert(NQ * BS % OR_T == 0, "step shape");
+  constexpr int QPF = NQ * OR_RC / OR_T; // basis entries per thread of a step's tile
+  static_assert(NQ * BS % OR_T == 0 && NQ * OR_RC % OR_T == 0, "step shape");
   double* Qs = sm;                 // NQ x OR_LD
   double* Xs = Qs + NQ * OR_LD;    // BS x OR_LD
   __shared__ int fin[QG];
   const int t = threadIdx.x;
   const Range R = unit_range(pa, H.ns, H.total[0]);
-  int s = R.s, xs_slot = -1, xs_rc = -1;
-  for (int u = R.u0; u < R.u1;) {
-    s = next_slot(pa, H.ns, s, u);
-    const OrthDev& D = J[s];
-    const int li = u - pa[s];
-    const int rc = li / D.ncb, cb0 = li % D.ncb;
-    const int k = min(min(R.u1 - u, QG), D.ncb - cb0);
-    u += k;
-    if (pass && converged(D)) continue;
-    const int c0 = cb0 * OR_CB, r0 = rc * OR_RC, q = D.q;
-    const int nc = min(k * OR_CB, q - c0), nr = min(OR_RC, D.n - r0);
-    __syncthreads();  // the previous step's readers of the staged blocks are done
-    for (int e = t; e < NQ * OR_RC; e += OR_T) {
-      const int r = e % OR_RC, cc = e / OR_RC;
-      Qs[cc * OR_LD + r] = (r < nr && cc < nc) ? D.Q[(size_t)(r0 + r) + (size_t)(c0 + cc) * D.n] : 0.0;
-    }
-    if (s != xs_slot || rc != xs_rc) {
-      const double* X = pass ? D.W : D.Y;
-      for (int e = t; e < BS * OR_RC; e += OR_T) {
-        const int r = e % OR_RC, jj = e / OR_RC;
-        Xs[jj * OR_LD + r] = r < nr ? __ldcg(X + (size_t)(r0 + r) + (size_t)jj * D.n) : 0.0;
-      }
-      xs_slot = s;
-      xs_rc = rc;
-    }
-    __syncthreads();
+  if (R.u0 >= R.u1) return;
+  struct Step {
+    int s, rc, cb0, k;
+    bool skip;
+  };
+  auto step_at = [&](int u, int s_from) {
+    Step st;
+    st.s = next_slot(pa, H.ns, s_from, u);
+    const OrthDev& D = J[st.s];
+    const int li = u - pa[st.s];
+    st.rc = li / D.ncb;
+    st.cb0 = li % D.ncb;
+    st.k = min(min(R.u1 - u, QG), D.ncb - st.cb0);
+    st.skip = pass && converged(D);
+    return st;
+  };
+  double pf[QPF];
+  auto load_tile = [&](const Step& st) {
+    const OrthDev& D = J[st.s];
+    const int c0 = st.cb0 * OR_CB, r0 = st.rc * OR_RC;
+    const int nc = min(st.k * OR_CB, D.q - c0), nr = min(OR_RC, D.n - r0);
 #pragma unroll
-    for (int v = 0; v < PT; ++v) {
-      const int o = t + v * OR_T, c = o / BS, j = o % BS;
-      if (c < nc) {
-        double a0 = 0.0, a1 = 0.0;
-#pragma unroll 8
-        for (int r = 0; r < OR_RC / 2; ++r) {
-          a0 = fma(Qs[c * OR_LD + r], Xs[j * OR_LD + r], a0);
-          a1 = fma(Qs[c * OR_LD + r + OR_RC / 2], Xs[j * OR_LD + r + OR_RC / 2], a1);
+    for (int v = 0; v < QPF; ++v) {
+      const int e = t + v * OR_T, r = e % OR_RC, cc = e / OR_RC;
+      pf[v] = (r < nr && cc < nc) ? D.Q[(size_t)(r0 + r) + (size_t)(c0 + cc) * D.n] : 0.0;
+    }
+  };
+  int u = R.u0, xs_slot = -1, xs_rc = -1;
+  Step cur = step_at(u, R.s);
+  if (!cur.skip) load_tile(cur);
+  while (true) {
+    const int un = u + cur.k;
+    const bool more = un < R.u1;
+    Step nxt = cur;
+    if (more) nxt = step_at(un, cur.s);
+    if (cur.skip) {
+      if (more && !nxt.skip) load_tile(nxt);
+    } else {
+      const OrthDev& D = J[cur.s];
+      const int rc = cur.rc, k = cur.k, c0 = cur.cb0 * OR_CB, r0 = rc * OR_RC, q = D.q;
+      const int nc = min(k * OR_CB, q - c0), nr = min(OR_RC, D.n - r0);
+      __syncthreads();  // the previous step's readers of the staged blocks are done
+#pragma unroll
+      for (int v = 0; v < QPF; ++v) {
+        const int e = t + v * OR_T;
+        Qs[(e / OR_RC) * OR_LD + e % OR_RC] = pf[v];
+      }
+      if (cur.s != xs_slot || rc != xs_rc) {
+        const double* X = pass ? D.W : D.Y;
+        for (int e = t; e < BS * OR_RC; e += OR_T) {
+          const int r = e % OR_RC, jj = e / OR_RC;
+          Xs[jj * OR_LD + r] = r < nr ? __ldcg(X + (size_t)(r0 + r) + (size_t)jj * D.n) : 0.0;
         }
-        D.Sp[(size_t)rc * q * BS + (c0 + c) + (size_t)j * q] = a0 + a1;
+        xs_slot = cur.s;
+        xs_rc = rc;
       }
-    }
-    __threadfence();
-    __syncthreads();
-    if (t < k) {  // arrival tickets of the step's column blocks
-      const int cb = cb0 + t;
-      const bool l = atomicAdd(D.cnt + cb, 1) + 1 == D.nrc;
-      if (l) D.cnt[cb] = 0;
-      fin[t] = l;
-    }
-    __syncthreads();
-    bool any = false;
-    for (int i = 0; i < k; ++i) any |= fin[i] != 0;
-    if (!any) continue;
-    __threadfence();
+      if (more && !nxt.skip) load_tile(nxt);  // in flight during this step's products
+      __syncthreads();
 #pragma unroll
-    for (int v = 0; v < PT; ++v) {  // completed column blocks: the sums in row-chunk order
-      const int o = t + v * OR_T, c = o / BS, j = o % BS;
-      if (c < nc && fin[c / OR_CB]) {
-        double w = 0.0;
-        for (int kk = 0; kk < D.nrc; ++kk) w += __ldcg(D.Sp + (size_t)kk * q * BS + (c0 + c) + (size_t)j * q);
-        D.Sf[(c0 + c) + (size_t)j * q] = w;
+      for (int v = 0; v < PT; ++v) {
+        const int o = t + v * OR_T, c = o / BS, j = o % BS;
+        if (c < nc) {
+          double a0 = 0.0, a1 = 0.0;
+#pragma unroll 8
+          for (int r = 0; r < OR_RC / 2; ++r) {
+            a0 = fma(Qs[c * OR_LD + r], Xs[j * OR_LD + r], a0);
+            a1 = fma(Qs[c * OR_LD + r + OR_RC / 2], Xs[j * OR_LD + r + OR_RC / 2], a1);
+          }
+          D.Sp[(size_t)rc * q * BS + (c0 + c) + (size_t)j * q] = a0 + a1;
+        }
+      }
+      __syncthreads();
+      if (t < k) {  // arrival tickets of the step's column blocks (see ticket())
+        const int cb = cur.cb0 + t;
+        __threadfence();
+        const bool l = atomicAdd(D.cnt + cb, 1) + 1 == D.nrc;
+        if (l) {
+          D.cnt[cb] = 0;
+          __threadfence();
+        }
+        fin[t] = l;
+      }
+      __syncthreads();
+      bool any = false;
+      for (int i = 0; i < k; ++i) any |= fin[i] != 0;
+      if (any) {
+#pragma unroll
+        for (int v = 0; v < PT; ++v) {  // completed column blocks: the sums in row-chunk order
+          const int o = t + v * OR_T, c = o / BS, j = o % BS;
+          if (c < nc && fin[c / OR_CB]) {
+            double w = 0.0;
+            for (int kk = 0; kk < D.nrc; ++kk) w += __ldcg(D.Sp + (size_t)kk * q * BS + (c0 + c) + (size_t)j * q);
+            D.Sf[(c0 + c) + (size_t)j * q] = w;
+          }
+        }
       }
     }
+    if (!more) break;
+    u = un;
+    cur = nxt;
   }
 }
 
+// 8-byte asynchronous copy global -> shared (zero-filled when !valid); the basis it is used for is not
+// written by the kernel, so the L1-allocating form is safe
+__device__ __forceinline__ void cp_async8(double* dst, const double* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // X <- X - Q S on rb-row units and their Gram partials; the CTA completing a chunk adds the chunk's
 // partials, the CTA completing the slot adds the chunks' and runs the Cholesky-QR.  A CTA takes up to a
-// chunk of consecutive units of one slot in one step.  In the second pass a slot without a basis forms
-// its rows of W = Y M1 here (the first pass's X M phase skips it: no Q^T W needs the whole of W).
+// chunk of consecutive units of one slot in one step; the next step's first basis chunk is copied
+// asynchronously into the other of two buffers while the step computes, and S stays staged across the
+// steps of a slot when it fits one chunk.  In the second pass a slot without a basis forms its rows of
+// W = Y M1 here (the first pass's X M phase skips it: no Q^T W needs the whole of W).
 template <int BS>
 __device__ void phase_project(const OrthHdr& H, const OrthDev* J, const int* pb, int pass, double* sm) {
   constexpr int SLD = BS + 1;                 // padded leading dimension of staged rows of S
   constexpr int MAXO = OR_RC * BS / OR_T;     // outputs per thread for a full chunk
   constexpr int GE = (BS * BS + OR_T - 1) / OR_T;  // Gram entries per thread per unit
   double* Xn = sm;                   // BS x OR_LD: the step's rows, column-major
-  double* Qs = Xn + BS * OR_LD;      // kc x rows (second pass without a basis: the Y rows, ld OR_LD)
-  double* Ss = Qs + OR_QCAP;         // kc x SLD
+  double* Qb[2] = {Xn + BS * OR_LD, Xn + BS * OR_LD + OR_QCAP};  // kc x rows (Y rows, ld OR_LD, without a basis)
+  double* Ss = Qb[1] + OR_QCAP;      // kc x SLD
   double* Ms = Ss + or_scap<BS>() * SLD;  // BS x BS
   double* Gs = Ms + BS * BS;         // BS x BS
   static_assert(BS * OR_LD <= OR_QCAP, "Y rows fit the staging area");
   const int t = threadIdx.x;
   const Range R = unit_range(pb, H.ns, H.total[1]);
-  int s = R.s;
-  for (int u = R.u0; u < R.u1;) {
-    s = next_slot(pb, H.ns, s, u);
-    const OrthDev& D = J[s];
-    const int RB = D.rb, bpc = OR_RC / RB, q = D.q;
-    const int blk0 = u - pb[s], rc = blk0 / bpc;
-    // this step: units blk0 .. blk0 + k - 1 of chunk rc, within the CTA's range
-    const int k = min(min(R.u1 - u, bpc - blk0 % bpc), D.nrb - blk0);
-    u += k;
-    if (pass && converged(D)) continue;
-    const int r0 = blk0 * RB, nr = min(k * RB, D.n - r0);  // rows of the step
-    double* X = pass ? D.W : D.Y;
-    __syncthreads();
-    if (pass && q == 0) {
-      for (int e = t; e < BS * BS; e += OR_T) Ms[e] = __ldcg(D.M + e);
-      for (int e = t; e < BS * OR_RC; e += OR_T) {
-        const int r = e % OR_RC, kk = e / OR_RC;
-        Qs[kk * OR_LD + r] = r < nr ? __ldcg(D.Y + (size_t)(r0 + r) + (size_t)kk * D.n) : 0.0;
-      }
-      __syncthreads();
-      for (int e = t; e < BS * OR_RC; e += OR_T) {
-        const int r = e % OR_RC, jj = e / OR_RC;
-        Xn[jj * OR_LD + r] = r < nr ? xm_entry<BS>(Qs, OR_LD, r, Ms, jj) : 0.0;
-      }
-    } else {
-      for (int e = t; e < BS * OR_RC; e += OR_T) {
-        const int r = e % OR_RC, jj = e / OR_RC;
-        Xn[jj * OR_LD + r] = r < nr ? __ldcg(X + (size_t)(r0 + r) + (size_t)jj * D.n) : 0.0;
-      }
+  if (R.u0 >= R.u1) return;
+  struct Step {
+    int s, blk0, k;
+    bool skip;
+  };
+  auto step_at = [&](int u, int s_from) {
+    Step st;
+    st.s = next_slot(pb, H.ns, s_from, u);
+    const OrthDev& D = J[st.s];
+    const int bpc = OR_RC / D.rb;
+    st.blk0 = u - pb[st.s];
+    // units blk0 .. blk0 + k - 1 of one chunk, within the CTA's range
+    st.k = min(min(R.u1 - u, bpc - st.blk0 % bpc), D.nrb - st.blk0);
+    st.skip = pass && converged(D);
+    return st;
+  };
+  auto kc_of = [](int q, int nr) { return max(2, min(min(or_scap<BS>(), OR_QCAP / nr), (q + 1) & ~1) & ~1); };
+  // the first basis chunk of a step (Qs[cc * nr + r], zero past q) into buffer dst
+  auto copy_chunk0 = [&](const Step& st, double* dst) {
+    const OrthDev& D = J[st.s];
+    const int q = D.q, r0 = st.blk0 * D.rb, nr = min(st.k * D.rb, D.n - r0);
+    const int kq = min(kc_of(q, nr), q), ke = (kq + 1) & ~1;
+    for (int e = t; e < ke * nr; e += OR_T) {
+      const int r = e % nr, cc = e / nr;
+      const bool ok = cc < kq;
+      cp_async8(dst + e, D.Q + (ok ? (size_t)(r0 + r) + (size_t)cc * D.n : 0), ok);
     }
-    if (q > 0) {
-      // each output: two chains (even and odd basis columns) added at the end, so the arithmetic is
-      // the same however many rows and basis columns a step stages (zero columns pad a step to even)
-      const int nout = nr * BS;
-      const int kc = max(2, min(min(or_scap<BS>(), OR_QCAP / nr), (q + 1) & ~1) & ~1);
-      double ae[MAXO], ao[MAXO];
-#pragma unroll
-      for (int v = 0; v < MAXO; ++v) ae[v] = ao[v] = 0.0;
-      for (int k0 = 0; k0 < q; k0 += kc) {
-        const int kq = min(kc, q - k0), ke = (kq + 1) & ~1;
-        __syncthreads();
-        for (int e = t; e < ke * nr; e += OR_T) {
-          const int r = e % nr, cc = e / nr;
-          Qs[cc * nr + r] = cc < kq ? D.Q[(size_t)(r0 + r) + (size_t)(k0 + cc) * D.n] : 0.0;
+  };
+  int u = R.u0, ss_slot = -1, qbuf = 0;  // ss_slot: the slot whose whole S is staged in Ss
+  bool ready = false;                    // the current step's first chunk is in flight to Qb[qbuf]
+  Step cur = step_at(u, R.s);
+  while (true) {
+    const int un = u + cur.k;
+    const bool more = un < R.u1;
+    Step nxt = cur;
+    if (more) nxt = step_at(un, cur.s);
+    if (!cur.skip) {
+      const OrthDev& D = J[cur.s];
+      const int RB = D.rb, bpc = OR_RC / RB, q = D.q, blk0 = cur.blk0, k = cur.k, rc = blk0 / bpc;
+      const int r0 = blk0 * RB, nr = min(k * RB, D.n - r0);  // rows of the step
+      double* X = pass ? D.W : D.Y;
+      double* Qs = Qb[qbuf];
+      const int kc = q > 0 ? kc_of(q, nr) : 2;
+      const int kq0 = min(kc, q), ke0 = (kq0 + 1) & ~1;
+      __syncthreads();  // the previous steps' readers of both buffers are done
+      if (pass && q == 0) {
+        for (int e = t; e < BS * BS; e += OR_T) Ms[e] = __ldcg(D.M + e);
+        for (int e = t; e < BS * OR_RC; e += OR_T) {
+          const int r = e % OR_RC, kk = e / OR_RC;
+          Qs[kk * OR_LD + r] = r < nr ? __ldcg(D.Y + (size_t)(r0 + r) + (size_t)kk * D.n) : 0.0;
         }
-        for (int e = t; e < ke * BS; e += OR_T) {
-          const int cc = e % ke, jj = e / ke;
-          Ss[cc * SLD + jj] = cc < kq ? __ldcg(D.Sf + (size_t)(k0 + cc) + (size_t)jj * q) : 0.0;
+      } else {
+        for (int e = t; e < BS * OR_RC; e += OR_T) {
+          const int r = e % OR_RC, jj = e / OR_RC;
+          Xn[jj * OR_LD + r] = r < nr ? __ldcg(X + (size_t)(r0 + r) + (size_t)jj * D.n) : 0.0;
         }
-        __syncthreads();
+      }
+      if (q > 0) {
+        if (!ready) copy_chunk0(cur, Qs);
+        if (cur.s != ss_slot) {
+          for (int e = t; e < ke0 * BS; e += OR_T) {
+            const int cc = e % ke0, jj = e / ke0;
+            Ss[cc * SLD + jj] = cc < kq0 ? __ldcg(D.Sf + (size_t)cc + (size_t)jj * q) : 0.0;
+          }
+        }
+        ss_slot = ke0 >= q ? cur.s : -1;
+      }
+      cp_async_commit();  // this step's chunk (when not prefetched)
+      const bool pre = more && !nxt.skip && J[nxt.s].q > 0;
+      if (pre) copy_chunk0(nxt, Qb[qbuf ^ 1]);  // in flight during this step's products
+      cp_async_commit();
+      cp_async_wait1();   // everything but the group just committed
+      __syncthreads();
+      ready = pre;
+      if (pass && q == 0) {
+        for (int e = t; e < BS * OR_RC; e += OR_T) {
+          const int r = e % OR_RC, jj = e / OR_RC;
+          Xn[jj * OR_LD + r] = r < nr ? xm_entry<BS>(Qs, OR_LD, r, Ms, jj) : 0.0;
+        }
+      }
+      if (q > 0) {
+        // each output: two chains (even and odd basis columns) added at the end, so the arithmetic is
+        // the same however many rows and basis columns a step stages (zero columns pad a step to even)
+        const int nout = nr * BS;
+        double ae[MAXO], ao[MAXO];
 #pragma unroll
-        for (int v = 0; v < MAXO; ++v) {
-          const int o = t + v * OR_T;
-          if (o < nout) {
-            const int r = o % nr, jj = o / nr;
+        for (int v = 0; v < MAXO; ++v) ae[v] = ao[v] = 0.0;
+        for (int k0 = 0; k0 < q; k0 += kc) {
+          const int kq = min(kc, q - k0), ke = (kq + 1) & ~1;
+          if (k0 > 0) {
+            __syncthreads();
+            for (int e = t; e < ke * nr; e += OR_T) {
+              const int r = e % nr, cc = e / nr;
+              Qs[cc * nr + r] = cc < kq ? D.Q[(size_t)(r0 + r) + (size_t)(k0 + cc) * D.n] : 0.0;
+            }
+            for (int e = t; e < ke * BS; e += OR_T) {
+              const int cc = e % ke, jj = e / ke;
+              Ss[cc * SLD + jj] = cc < kq ? __ldcg(D.Sf + (size_t)(k0 + cc) + (size_t)jj * q) : 0.0;
+            }
+            __syncthreads();
+          }
+#pragma unroll
+          for (int v = 0; v < MAXO; ++v) {
+            const int o = t + v * OR_T;
+            if (o < nout) {
+              const int r = o % nr, jj = o / nr;
 #pragma unroll 4
-            for (int cc = 0; cc < ke; cc += 2) {
-              ae[v] = fma(Qs[cc * nr + r], Ss[cc * SLD + jj], ae[v]);
-              ao[v] = fma(Qs[(cc + 1) * nr + r], Ss[(cc + 1) * SLD + jj], ao[v]);
+              for (int cc = 0; cc < ke; cc += 2) {
+                ae[v] = fma(Qs[cc * nr + r], Ss[cc * SLD + jj], ae[v]);
+                ao[v] = fma(Qs[(cc + 1) * nr + r], Ss[(cc + 1) * SLD + jj], ao[v]);
+              }
             }
           }
         }
-      }
 #pragma unroll
-      for (int v = 0; v < MAXO; ++v) {
-        const int o = t + v * OR_T;
-        if (o < nout) Xn[(o / nr) * OR_LD + (o % nr)] -= ae[v] + ao[v];
-      }
-    }
-    __syncthreads();
-    if (q > 0 || pass) {  // projected rows (or the rows of W formed here) back in place
-      for (int e = t; e < BS * nr; e += OR_T) {
-        const int r = e % nr, jj = e / nr;
-        X[(size_t)(r0 + r) + (size_t)jj * D.n] = Xn[jj * OR_LD + r];
-      }
-    }
-    for (int b = 0; b < k; ++b) {  // Gram partial of each unit
-      const int rb0 = b * RB, rn = min(RB, nr - rb0);
-#pragma unroll
-      for (int v = 0; v < GE; ++v) {
-        const int e = t + v * OR_T;
-        if (e < BS * BS) {
-          const int a = e % BS, c = e / BS;
-          double g = 0.0;
-          for (int r = rb0; r < rb0 + rn; ++r) g = fma(Xn[a * OR_LD + r], Xn[c * OR_LD + r], g);
-          D.Gp[(size_t)(blk0 + b) * BS * BS + e] = g;
+        for (int v = 0; v < MAXO; ++v) {
+          const int o = t + v * OR_T;
+          if (o < nout) Xn[(o / nr) * OR_LD + (o % nr)] -= ae[v] + ao[v];
         }
       }
-    }
-    const int units_in_chunk = min(bpc, D.nrb - rc * bpc);
-    if (!ticket(D.cnt + D.ncb + rc, k, units_in_chunk)) continue;
-#pragma unroll
-    for (int v = 0; v < GE; ++v) {  // the chunk's partial: its units' in order
-      const int e = t + v * OR_T;
-      if (e < BS * BS) {
-        double g = 0.0;
-        for (int b = 0; b < units_in_chunk; ++b) g += __ldcg(D.Gp + (size_t)(rc * bpc + b) * BS * BS + e);
-        D.Gc[(size_t)rc * BS * BS + e] = g;
+      __syncthreads();
+      if (q > 0 || pass) {  // projected rows (or the rows of W formed here) back in place
+        for (int e = t; e < BS * nr; e += OR_T) {
+          const int r = e % nr, jj = e / nr;
+          X[(size_t)(r0 + r) + (size_t)jj * D.n] = Xn[jj * OR_LD + r];
+        }
       }
-    }
-    if (!ticket(D.cnt + D.ncb + D.nrc, 1, D.nrc)) continue;
+      for (int b = 0; b < k; ++b) {  // Gram partial of each unit
+        const int rb0 = b * RB, rn = min(RB, nr - rb0);
 #pragma unroll
-    for (int v = 0; v < GE; ++v) {  // G: the chunks' partials in order
-      const int e = t + v * OR_T;
-      if (e < BS * BS) {
-        double g = 0.0;
+        for (int v = 0; v < GE; ++v) {
+          const int e = t + v * OR_T;
+          if (e < BS * BS) {
+            const int a = e % BS, c = e / BS;
+            double g = 0.0;
+            for (int r = rb0; r < rb0 + rn; ++r) g = fma(Xn[a * OR_LD + r], Xn[c * OR_LD + r], g);
+            D.Gp[(size_t)(blk0 + b) * BS * BS + e] = g;
+          }
+        }
+      }
+      const int units_in_chunk = min(bpc, D.nrb - rc * bpc);
+      if (ticket(D.cnt + D.ncb + rc, k, units_in_chunk)) {
+#pragma unroll
+        for (int v = 0; v < GE; ++v) {  // the chunk's partial: its units' in order
+          const int e = t + v * OR_T;
+          if (e < BS * BS) {
+            double g = 0.0;
+            for (int b = 0; b < units_in_chunk; ++b) g += __ldcg(D.Gp + (size_t)(rc * bpc + b) * BS * BS + e);
+            D.Gc[(size_t)rc * BS * BS + e] = g;
+          }
+        }
+        if (ticket(D.cnt + D.ncb + D.nrc, 1, D.nrc)) {
+#pragma unroll
+          for (int v = 0; v < GE; ++v) {  // G: the chunks' partials in order
+            const int e = t + v * OR_T;
+            if (e < BS * BS) {
+              double g = 0.0;
 #pragma unroll 4
-        for (int c = 0; c < D.nrc; ++c) g += __ldcg(D.Gc + (size_t)c * BS * BS + e);
-        Gs[e] = g;
+              for (int c = 0; c < D.nrc; ++c) g += __ldcg(D.Gc + (size_t)c * BS * BS + e);
+              Gs[e] = g;
+            }
+          }
+          __syncthreads();
+          if (t < 32) {
+            const int nk1 = pass ? __ldcg(D.st + 1) : 0;
+            cholqr_slot<BS>(Gs, D.M, D.st, D.en, D.thr, H.tau, pass == 0, nk1);
+          }
+        }
       }
+      qbuf ^= 1;
+    } else {
+      ready = false;
     }
-    __syncthreads();
-    if (t < 32) {
-      const int nk1 = pass ? __ldcg(D.st + 1) : 0;
-      cholqr_slot<BS>(Gs, D.M, D.st, D.en, D.thr, H.tau, pass == 0, nk1);
-    }
+    if (!more) break;
+    u = un;
+    cur = nxt;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // out = X M, row-local: pass 0 W = Y M1 (slots with a basis), pass 1 Q[:, q:q+BS] = W M2.  Units of
@@ -577,8 +694,12 @@ void orth_round(tlr_ctx* ctx, int bs, const std::vector<OrthSlot>& sl, int* stat
   memcpy(hp + 2 * (ns + 1), pd1.data(), sizeof(int) * (ns + 1));
   memcpy(hp + 3 * (ns + 1), pd2.data(), sizeof(int) * (ns + 1));
   const char* dtab = static_cast<const char*>(upload(ctx, tab.data(), tab.size()));
+  double flops = 0;
+  for (const OrthSlot& x : sl) flops += 8.0 * x.n * x.q * bs + 6.0 * x.n * bs * bs;
+  if (ctx->kprof) kprof_begin(ctx);
   if (bs == 16) launch_orth<16>(ctx, dtab, bar);
   else launch_orth<32>(ctx, dtab, bar);
+  if (ctx->kprof) kprof_end(ctx, 7, flops);
 }
 
 }  // namespace tlr
