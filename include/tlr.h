@@ -49,7 +49,8 @@ enum { TLR_KERNEL_EXP = 0 };
 typedef struct {
   int type;      /* TLR_KERNEL_EXP */
   double ell;    /* length scale > 0 */
-  double nugget; /* >= 0, added to the diagonal */
+  double nugget; /* added to the diagonal, > -1 (a negative nugget shifts the covariance down, which
+                    makes it indefinite: the case of the safeguards of Section 5.1) */
 } tlr_kernel;
 
 /* Arithmetic of the ARA sampling / projection products (the chains of
@@ -76,7 +77,9 @@ enum {
 enum {
   TLR_COMP_NONE = 0,
   TLR_COMP_SHIFT = 1, /* factor A + shift*I (Section 5.1, "diagonal shifting") */
-  TLR_COMP_SCHUR = 2  /* A(k,k) - D_k + diag(rowsum|D_k - Dbar_k|) (Section 5.1.1) */
+  TLR_COMP_SCHUR = 2, /* A(k,k) - D_k + diag(rowsum|D_k - Dbar_k|) (Section 5.1.1) */
+  TLR_COMP_MODCHOL = 3 /* Cholesky only: a diagonal tile that is not positive definite is factored by
+                          the modified Cholesky of Algorithm 8 (Section 5.1.2, tlr_dense_modchol) */
 };
 
 typedef struct {
@@ -117,7 +120,7 @@ tlr_status tlr_destroy(tlr_ctx* ctx);
  * Entries are evaluated in 64-bit fixed point from the points on a per-matrix
  * grid (no FP64 arithmetic), within 4 x 2^-52 (1 + |log a_ij|) relative of the
  * FP64 formula; entries below 2^-1020 are 0.  Errors: TLR_ERR_ARG (null
- * pointers, N <= 0, d outside 1..3, b < 1, eps <= 0, ell <= 0, nugget < 0,
+ * pointers, N <= 0, d outside 1..3, b < 1, eps <= 0, ell <= 0, nugget <= -1,
  * opts.bs > min(64, b)), TLR_ERR_NOMEM. */
 tlr_status tlr_compress(tlr_ctx* ctx, const double* points_host, int64_t N, int d,
                         const tlr_kernel* kernel, int b, double eps, const tlr_opts* opts,
@@ -275,7 +278,7 @@ tlr_status tlr_matvec(tlr_ctx* ctx, const tlr_mat* F, int op, int nrhs, const do
  * factorizations).  Points host row-major N x d in ORIGINAL order; X, Y device
  * N x nrhs (ldx, ldy >= N).  TLR_ERR_ARG for a NULL pointer, N <= 0, d outside
  * 1..3, nrhs < 0, ldx or ldy < N, a kernel type other than TLR_KERNEL_EXP,
- * ell <= 0 or nugget < 0 (the same rule as tlr_kernel_matvec_noalloc). */
+ * ell <= 0 or nugget <= -1 (the same rule as tlr_kernel_matvec_noalloc). */
 tlr_status tlr_kernel_matvec(tlr_ctx* ctx, const double* points_host, int64_t N, int d,
                              const tlr_kernel* kernel, int nrhs, const double* X, int64_t ldx,
                              double* Y, int64_t ldy);
@@ -365,6 +368,14 @@ tlr_status tlr_ara_dense(tlr_ctx* ctx, int nops, int n, const double* T, int bs,
 /* Dense FP64 Cholesky (lower, in place) of an n x n device matrix (lda >= n);
  * *info (host) = -1 on success, else the first failing column. */
 tlr_status tlr_dense_potrf(tlr_ctx* ctx, int n, double* A, int lda, int* info);
+/* Modified Cholesky (Algorithm 8, Section 5.1.2) of a symmetric n x n device matrix (lower triangle
+ * read, lda >= n, n <= 2048): if A is positive definite, its Cholesky factor (*modified = 0);
+ * otherwise (*modified = 1) the Cholesky factor of A + E = P L (D + F) L^T P^T, where P^T A P = L D L^T
+ * is the symmetric factorization with the 1x1 / 2x2 pivoting of Bunch and Kaufman (1977) and F raises
+ * each pivot block's eigenvalues to at least sqrt(u / 2) ||A||_inf (Cheng and Higham, 1998).  In
+ * place: L in the lower triangle; after a modification the strict upper triangle holds A + E.
+ * *info (host) = -1, or the failing column should A + E itself not factor. */
+tlr_status tlr_dense_modchol(tlr_ctx* ctx, int n, double* A, int lda, int* modified, int* info);
 /* Dense unpivoted LDL^T (in place: unit L below the diagonal, D on it). */
 tlr_status tlr_dense_ldlt(tlr_ctx* ctx, int n, double* A, int lda, int* info);
 /* X = L^{-1} B in place (L lower n x n, unit diagonal if unit != 0), B n x nrhs. */

@@ -22,7 +22,7 @@ __all__ = ["Context", "Matrix", "Opts", "TLRError", "build", "fortran", "kd_orde
 
 OK, ERR_ARG, ERR_NOMEM, ERR_NOT_SPD, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_LIMIT = 0, -1, -2, -3, -4, -5, -6, -7
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
-COMP_NONE, COMP_SHIFT, COMP_SCHUR = 0, 1, 2
+COMP_NONE, COMP_SHIFT, COMP_SCHUR, COMP_MODCHOL = 0, 1, 2, 3
 OP_A, OP_L, OP_LT, OP_LLT = 0, 1, 2, 3
 STREAM_COMPRESS, STREAM_FACTOR, STREAM_SCHUR = 1, 2, 3
 
@@ -115,6 +115,7 @@ def _load():
         "tlr_ara_dense": (C.c_int, [P, C.c_int, C.c_int, P, C.c_int, C.c_double, C.c_uint64, C.c_uint32,
                                     C.c_uint32, P, P, P]),
         "tlr_dense_potrf": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int)]),
+        "tlr_dense_modchol": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "tlr_dense_ldlt": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int)]),
         "tlr_dense_trsm": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, C.c_int]),
         "tlr_split_product": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, C.c_int, P, C.c_int]),
@@ -305,6 +306,13 @@ class Context:
         _check(_load().tlr_ara_dense(self.h, nops, n, _ptr(Tc), bs, eps, seed, stream, k, _ptr(Q), _ptr(B), _ptr(r)),
                "tlr_ara_dense")
         return Q, B, r
+
+    def dense_modchol(self, A):
+        """Modified Cholesky (Algorithm 8) in place; returns (modified, info)."""
+        mod, info = C.c_int(0), C.c_int(0)
+        _check(_load().tlr_dense_modchol(self.h, A.shape[0], _ptr(A), _ld(A), C.byref(mod), C.byref(info)),
+               "tlr_dense_modchol")
+        return mod.value, info.value
 
     def dense_potrf(self, A, ldl: bool = False):
         info = C.c_int(0)

@@ -449,7 +449,7 @@ void axpy_matrix(tlr_ctx* ctx, int m, int n, double alpha, const double* X, int 
 inline bool kernel_product_args_ok(const double* pts, const tlr_kernel* k, const double* X, const double* Y, int64_t N,
                                    int d, int nrhs, int64_t ldx, int64_t ldy) {
   return pts && k && X && Y && N > 0 && d >= 1 && d <= 3 && nrhs >= 0 && ldx >= N && ldy >= N && k->ell > 0 &&
-         k->type == TLR_KERNEL_EXP && k->nugget >= 0;
+         k->type == TLR_KERNEL_EXP && k->nugget > -1.0;
 }
 
 // kdtree.cpp

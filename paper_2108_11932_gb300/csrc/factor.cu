@@ -26,7 +26,7 @@ namespace {
 constexpr double U32 = 5.96e-8;  // FP32 unit roundoff, 2^-24
 
 struct Mat {
-  explicit Mat(tlr_ctx* c) : G(c), G32(c), E(c), DV(c), DV32(c), Bc(c) {}
+  explicit Mat(tlr_ctx* c) : G(c), G32(c), E(c), DV(c), DV32(c), Bc(c), Asave(c) {}
   tlr_mat* A = nullptr;  // input, then (on success) the factor
   tlr_mat* F = nullptr;  // factor under construction
   double eps = 0, thr = 0;
@@ -51,6 +51,8 @@ struct Mat {
   int op0 = 0, nops = 0;
   std::vector<int64_t> boff;
   Buf G, G32, E, DV, DV32, Bc;
+  Buf Asave;  // TLR_COMP_MODCHOL: the column's updated diagonal tile, kept for Algorithm 8
+  int modified = 0;  // diagonal tiles factored by the modified Cholesky
   std::vector<float*> AU32, AV32, FU32, FV32;
   std::vector<int64_t> fu32cap;
   // 7-bit chunk planes (int8) of F's U panels relative to 2 (their columns are orthonormal basis
@@ -581,12 +583,13 @@ struct Session {
   Buf bOzMax, bOzS, bOzE, bOzX, bOzEx;  // split trsm products
   Buf bOzOs, bOzOe, bOzWs, bOzWe, bOne;  // split sampling / projection products
   Buf bOzDs, bOzDe, bOzDm;               // split updateDense products (side stream)
+  Buf bMcW, bMcT;                        // modified Cholesky workspaces (main stream)
   int* d_one = nullptr;
   AraStats total;
   explicit Session(tlr_ctx* c)
       : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bW(c), bY32(c), bP(c), bZ(c),
         bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c), bOzOs(c), bOzOe(c), bOzWs(c), bOzWe(c),
-        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c) {
+        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c), bMcW(c), bMcT(c) {
     static const int one = 1;
     d_one = bOne.need<int>(1);
     TLR_CUDA(cudaMemcpyAsync(d_one, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -741,6 +744,39 @@ struct Session {
     prof_flush(ctx);
   }
 
+  // After the diagonal tiles' join: a tile that is not positive definite fails its matrix, or, with
+  // TLR_COMP_MODCHOL, is factored again by Algorithm 8 from its saved copy (main stream).
+  void diagonal_failures(int* info) {
+    const int nm = (int)mats.size();
+    std::vector<int> hinfo(nm);
+    TLR_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->main));
+    TLR_CUDA(cudaStreamSynchronize(ctx->main));
+    bool redo = false;
+    for (int mi = 0; mi < nm; ++mi) {
+      Mat& M = *mats[mi];
+      if (!M.live || M.done || hinfo[mi] < 0 || M.o.compensation != TLR_COMP_MODCHOL) continue;
+      const int b = M.b;
+      double* T = static_cast<double*>(M.Asave.p);
+      modified_cholesky_tile(ctx, b, T, b, M.F->dinv + (size_t)M.k * b * b, info + mi, bMcW, bMcT);
+      copy_matrix(ctx, b, b, T, b, M.F->diag + (size_t)M.k * b * b, b);
+      ++M.modified;
+      redo = true;
+    }
+    if (redo) {
+      TLR_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->main));
+      TLR_CUDA(cudaStreamSynchronize(ctx->main));
+    }
+    for (int mi = 0; mi < nm; ++mi) {
+      Mat& M = *mats[mi];
+      if (M.live && !M.done && hinfo[mi] >= 0) {
+        M.live = false;
+        M.st = TLR_ERR_NOT_SPD;
+        M.A->state = 3;
+        M.A->k_fail = M.k;
+      }
+    }
+  }
+
   void step_columns() {
     std::vector<Mat*> L;
     for (auto& M : mats)
@@ -863,6 +899,7 @@ struct Session {
           del += (int64_t)8 * Mp->b * Mp->Kk;
           ++dn;
         }
+        if (Mp->o.compensation == TLR_COMP_MODCHOL) Mp->Asave.need<double>((size_t)Mp->b * Mp->b);
       }
       bTmp.need<double>(std::max(dense_tmp_doubles(probe[0], 0), dense_tmp_doubles(probe[1], 1)));
       if (dn) {
@@ -983,6 +1020,10 @@ struct Session {
         }
       }
       batched_add_diag(ctx, shifts);
+      for (Mat* Mp : S)  // Algorithm 8 needs the tile as it was before the factorization attempt
+        if (Mp->o.compensation == TLR_COMP_MODCHOL)
+          copy_matrix(ctx, Mp->b, Mp->b, Mp->F->diag + (size_t)Mp->k * Mp->b * Mp->b, Mp->b,
+                      static_cast<double*>(Mp->Asave.p), Mp->b);
       // pass 1 runs on the main stream while pass 0 may still be running: own workspace
       Buf& tmp = pass == 0 ? bTmp : bTmpMain;
       for (int l = 0; l < 2; ++l) {
@@ -1118,18 +1159,7 @@ struct Session {
       // ---------------------------------------------------------------- join, failures
       prof_mark(ctx, PH_POTRF);  // waiting for the diagonal tiles
       TLR_CUDA(cudaStreamWaitEvent(ctx->main, ctx->ev_join, 0));
-      std::vector<int> hinfo(nm);
-      TLR_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->main));
-      TLR_CUDA(cudaStreamSynchronize(ctx->main));
-      for (int mi = 0; mi < nm; ++mi) {
-        Mat& M = *mats[mi];
-        if (M.live && !M.done && hinfo[mi] >= 0) {
-          M.live = false;
-          M.st = TLR_ERR_NOT_SPD;
-          M.A->state = 3;
-          M.A->k_fail = M.k;
-        }
-      }
+      diagonal_failures(info);
       // ---------------------------------------------------------------- projection (sampleLeftT)
       prof_mark(ctx, PH_PROJECT);
       for (Mat* Mp : L) {
@@ -1157,18 +1187,7 @@ struct Session {
     } else {
       prof_mark(ctx, PH_POTRF);
       TLR_CUDA(cudaStreamWaitEvent(ctx->main, ctx->ev_join, 0));
-      std::vector<int> hinfo(nm);
-      TLR_CUDA(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nm, cudaMemcpyDeviceToHost, ctx->main));
-      TLR_CUDA(cudaStreamSynchronize(ctx->main));
-      for (int mi = 0; mi < nm; ++mi) {
-        Mat& M = *mats[mi];
-        if (M.live && !M.done && hinfo[mi] >= 0) {
-          M.live = false;
-          M.st = TLR_ERR_NOT_SPD;
-          M.A->state = 3;
-          M.A->k_fail = M.k;
-        }
-      }
+      diagonal_failures(info);
     }
     // ---------------------------------------------------------------- batchTrsm, updateTiles
     prof_mark(ctx, PH_TRSM);
@@ -1383,7 +1402,8 @@ tlr_status tlr_session_add(tlr_session* s, tlr_mat* A, double eps, const tlr_opt
   if (opts) o = *opts; else tlr_opts_default(&o);
   if (o.bs <= 0) o.bs = 16;
   if (o.bs > 64 || o.bs > A->b || o.precision < TLR_PREC_FP64 || o.precision > TLR_PREC_MIXED ||
-      (s->S.bs >= 0 && o.bs != s->S.bs))
+      o.compensation < TLR_COMP_NONE || o.compensation > TLR_COMP_MODCHOL ||
+      (o.compensation == TLR_COMP_MODCHOL && (ldl || A->b > 2048)) || (s->S.bs >= 0 && o.bs != s->S.bs))
     return TLR_ERR_ARG;
   SESSION_TRY
   *ticket = s->S.add(A, eps, o, ldl);

@@ -54,6 +54,10 @@ size_t dense_tmp_doubles(const std::vector<DenseTile>& tiles, int ldl);
 void dense_factor_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int ldl, Buf& tmp);
 void dense_trinv_batch(tlr_ctx* ctx, std::vector<DenseTile>& tiles, int unit, Buf& tmp);
 void dense_trsm(tlr_ctx* ctx, int n, const double* L, int lda, int unit, int nrhs, double* X, int ldx, int trans);
+// Algorithm 8 on a tile that is not positive definite (k_modchol.cu): A (lower triangle read) is replaced
+// by the Cholesky factor of A + E (lower; the strict upper triangle holds A + E), Linv (n x n, or null) by
+// its inverse, *info (device) by -1 or the failing column of A + E
+void modified_cholesky_tile(tlr_ctx* ctx, int n, double* A, int lda, double* Linv, int* info, Buf& work, Buf& tmp);
 
 // ARA engine (Algorithm 1 batched, dynamic batching of Algorithm 5)
 struct Sampler {

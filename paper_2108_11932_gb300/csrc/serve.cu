@@ -163,11 +163,12 @@ extern "C" {
 tlr_status tlr_submit(tlr_ctx* ctx, const tlr_request* r, uint64_t* ticket) {
   if (!ctx || !r || !ticket || !r->points || r->N <= 0 || r->d < 1 || r->d > 3 || r->b < 1 || !(r->eps > 0) ||
       r->nrhs < 0 || r->nrhs > 1024 || (r->nrhs > 0 && !r->rhs) || r->ldl < 0 || r->ldl > 1 ||
-      r->kernel.type != TLR_KERNEL_EXP || !(r->kernel.ell > 0) || r->kernel.nugget < 0)
+      r->kernel.type != TLR_KERNEL_EXP || !(r->kernel.ell > 0) || !(r->kernel.nugget > -1.0))
     return TLR_ERR_ARG;
   const int bs = r->opts.bs > 0 ? r->opts.bs : 16;
   if (bs > 64 || bs > r->b || r->opts.precision < TLR_PREC_FP64 || r->opts.precision > TLR_PREC_MIXED ||
-      r->opts.compensation < TLR_COMP_NONE || r->opts.compensation > TLR_COMP_SCHUR)
+      r->opts.compensation < TLR_COMP_NONE || r->opts.compensation > TLR_COMP_MODCHOL ||
+      (r->opts.compensation == TLR_COMP_MODCHOL && r->ldl))
     return TLR_ERR_ARG;
   try {
     if (!ctx->server) ctx->server = new Server(ctx);

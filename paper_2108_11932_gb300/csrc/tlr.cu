@@ -1214,7 +1214,7 @@ static tlr_opts opts_or_default(const tlr_opts* o) {
 tlr_status tlr_compress(tlr_ctx* ctx, const double* pts, int64_t N, int d, const tlr_kernel* kern, int b,
                         double eps, const tlr_opts* opts, tlr_mat** A) {
   if (!ctx || !pts || !kern || !A || N <= 0 || d < 1 || d > 3 || b < 1 || !(eps > 0) || !(kern->ell > 0) ||
-      kern->type != TLR_KERNEL_EXP || kern->nugget < 0)
+      kern->type != TLR_KERNEL_EXP || !(kern->nugget > -1.0))
     return TLR_ERR_ARG;
   tlr_opts o = opts_or_default(opts);
   if (o.bs > 64 || o.bs > b) return TLR_ERR_ARG;
@@ -1238,7 +1238,7 @@ tlr_status tlr_compress(tlr_ctx* ctx, const double* pts, int64_t N, int d, const
 tlr_status tlr_compress_ordered(tlr_ctx* ctx, const double* pts_dev, const int64_t* perm_host, int64_t N, int d,
                                 const tlr_kernel* kern, int b, double eps, const tlr_opts* opts, tlr_mat** A) {
   if (!ctx || !pts_dev || !kern || !A || N <= 0 || d < 1 || d > 3 || b < 1 || !(eps > 0) || !(kern->ell > 0) ||
-      kern->type != TLR_KERNEL_EXP || kern->nugget < 0)
+      kern->type != TLR_KERNEL_EXP || !(kern->nugget > -1.0))
     return TLR_ERR_ARG;
   tlr_opts o = opts_or_default(opts);
   if (o.bs > 64 || o.bs > b) return TLR_ERR_ARG;
@@ -1285,11 +1285,12 @@ tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* S, tlr_mat** D) {
   ABI_END
 }
 
-static tlr_status check_factor_args(const tlr_mat* A, double eps, const tlr_opts& o) {
+static tlr_status check_factor_args(const tlr_mat* A, double eps, const tlr_opts& o, int ldl) {
   if (!A || !(eps > 0)) return TLR_ERR_ARG;
   if (A->state != 0) return TLR_ERR_STATE;
   if (o.bs > 64 || o.bs > A->b || o.precision < TLR_PREC_FP64 || o.precision > TLR_PREC_MIXED ||
-      o.compensation < TLR_COMP_NONE || o.compensation > TLR_COMP_SCHUR)
+      o.compensation < TLR_COMP_NONE || o.compensation > TLR_COMP_MODCHOL ||
+      (o.compensation == TLR_COMP_MODCHOL && (ldl || A->b > 2048)))
     return TLR_ERR_ARG;
   return TLR_OK;
 }
@@ -1297,7 +1298,7 @@ static tlr_status check_factor_args(const tlr_mat* A, double eps, const tlr_opts
 static tlr_status factor_abi(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts, int ldl) {
   if (!ctx) return TLR_ERR_ARG;
   tlr_opts o = opts_or_default(opts);
-  const tlr_status c = check_factor_args(A, eps, o);
+  const tlr_status c = check_factor_args(A, eps, o, ldl);
   if (c != TLR_OK) return c;
   ABI_BEGIN
   std::vector<tlr_status> st;
@@ -1315,7 +1316,7 @@ tlr_status tlr_factor_batch(tlr_ctx* ctx, int count, tlr_mat** A, const double* 
   std::vector<int> idx;
   for (int m = 0; m < count; ++m) {
     tlr_opts o = opts_or_default(opts ? &opts[m] : nullptr);
-    status[m] = check_factor_args(A[m], eps[m], o);
+    status[m] = check_factor_args(A[m], eps[m], o, ldl);
     if (status[m] != TLR_OK) continue;
     mats.push_back(A[m]);
     ev.push_back(eps[m]);
@@ -1600,6 +1601,28 @@ tlr_status tlr_dense_potrf(tlr_ctx* ctx, int n, double* A, int lda, int* info) {
   std::vector<DenseTile> t{DenseTile{A, nullptr, di, nullptr, n, lda}};
   dense_factor_batch(ctx, t, 0, tmp);
   d2h_sync(ctx, info, di, sizeof(int));
+  return TLR_OK;
+  ABI_END
+}
+
+tlr_status tlr_dense_modchol(tlr_ctx* ctx, int n, double* A, int lda, int* modified, int* info) {
+  if (!ctx || !A || n < 0 || n > 2048 || lda < n || !info || !modified) return TLR_ERR_ARG;
+  ABI_BEGIN
+  Buf bi(ctx), tmp(ctx), cp(ctx), work(ctx);
+  int* di = bi.need<int>(1);
+  double* A0 = cp.need<double>(std::max<size_t>((size_t)n * n, 1));
+  copy_matrix(ctx, n, n, A, lda, A0, n);
+  TLR_CUDA(cudaMemsetAsync(di, 0xff, sizeof(int), ctx->stream));
+  std::vector<DenseTile> t{DenseTile{A, nullptr, di, nullptr, n, lda}};
+  dense_factor_batch(ctx, t, 0, tmp);
+  d2h_sync(ctx, info, di, sizeof(int));
+  *modified = 0;
+  if (*info >= 0) {  // not positive definite: Algorithm 8 on the input
+    *modified = 1;
+    copy_matrix(ctx, n, n, A0, n, A, lda);
+    modified_cholesky_tile(ctx, n, A, lda, nullptr, di, work, tmp);
+    d2h_sync(ctx, info, di, sizeof(int));
+  }
   return TLR_OK;
   ABI_END
 }

@@ -78,14 +78,14 @@ def test_autotune_choose_takes_the_nearest_class_of_the_same_dimension():
 
 def test_kernel_products_share_their_argument_rule(lib):
     """tlr_kernel_matvec and tlr_kernel_matvec_noalloc compute the same Y = A X and reject the same
-    arguments before touching the GPU: an unknown kernel type and a negative nugget among them."""
+    arguments before touching the GPU: an unknown kernel type and a nugget of -1 (a zero diagonal) among them."""
     so = lib._load()
     so.tlr_kernel_matvec_noalloc.restype = ctypes.c_int
     pts = np.zeros((4, 2))
     X = (ctypes.c_double * 4)()
     Y = (ctypes.c_double * 4)()
     dummy_ctx = ctypes.create_string_buffer(4096)  # never dereferenced: the arguments are rejected first
-    for ktype, ell, nug in [(7, 0.1, 0.0), (0, 0.1, -1e-4), (0, 0.0, 0.0), (0, -0.1, 0.0)]:
+    for ktype, ell, nug in [(7, 0.1, 0.0), (0, 0.1, -1.0), (0, 0.1, -2.5), (0, 0.0, 0.0), (0, -0.1, 0.0)]:
         k = lib.Kernel(ktype, ell, nug)
         a = so.tlr_kernel_matvec(ctypes.cast(dummy_ctx, ctypes.c_void_p), pts.ctypes.data, 4, 2, ctypes.byref(k), 1,
                                  ctypes.cast(X, ctypes.c_void_p), 4, ctypes.cast(Y, ctypes.c_void_p), 4)
