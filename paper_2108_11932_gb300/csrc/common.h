@@ -297,6 +297,8 @@ struct SlotDescT {
   T* P;              // project: P block ((r0 + Ki) x q) and output Z ((r0 + Kk) x q)
   T* Z;
   int ldx, ldx0, nb, k, i, r0, x0off, Ki, Kk, q, bs;
+  int r0w;           // sample: rows of W holding X0 (r0, or r0 rounded up to 32 and zero-padded when the
+                     // product runs as one split product over [U0 | Urow])
 };
 // FP64 products on the 16-bit tensor cores by exact splitting (k_ozaki.cu).  Operands are stored as 8
 // planes of signed 7-bit chunks (int8, one byte per chunk); rows of a plane start on 16-byte
@@ -344,6 +346,12 @@ struct OzJob {
   // bound per entry, K (s + 1) 2^(eA + eB - 7 s), stays below tol (an absolute error)
   double tol = 0.0;
   int smin = 2;
+  // optional first K segment (rows along k, not acol): A(m, k) for k < K0 from A0 (8 planes, stride
+  // sA0, leading dimension lda0), A(m, k) = A_q[(k - K0) + m * lda] for k >= K0; K0 a multiple of 32,
+  // the segment zero past its data; both segments relative to the block exponent eA
+  const int8_t* A0 = nullptr;
+  size_t sA0 = 0;
+  int lda0 = 0, K0 = 0;
   double* ws = nullptr;
   int* ctr = nullptr;
 };

@@ -114,6 +114,12 @@ struct BatchSampler : Sampler {
   // tensor-core split products with F's U panels (FP64 arithmetic, matrices with M.oz)
   const int* d_one = nullptr;  // device int 1: the exponent of the U-panel slices
   Buf *bos = nullptr, *boe = nullptr, *bws = nullptr, *bwe = nullptr;  // Omega / W (or Q) slices
+  // the compressed input's U0 block of each operand's tile (i, k), sliced once per column step
+  // (transposed: rows along its r0 columns, zero-padded to r0w = r0 rounded up to 32), so that
+  // Y = [U0 | Urow_i] W is one split product; u0off[op] < 0 where that product stays in FP64
+  Buf* bu0 = nullptr;
+  std::vector<int64_t> u0off;
+  bool u0_ready = false;
   static constexpr bool F32 = sizeof(T) == 4;
   bool owns_omega() const override { return true; }
   bool mine(int op) const { return !member || (*member)[op]; }
@@ -220,7 +226,41 @@ struct BatchSampler : Sampler {
     oz_gemm(ctx, oxj);
   }
 
+  static int round32(int r) { return (r + 31) / 32 * 32; }
+  void prepare_u0() {
+    u0_ready = true;
+    const int nops = (int)op_m->size();
+    u0off.assign(nops, -1);
+    if (F32 || !bu0) return;
+    int64_t tot = 0;
+    for (int op = 0; op < nops; ++op) {
+      if (!mine(op)) continue;
+      const Mat& M = *(*L)[(*op_m)[op]];
+      const int i = (*op_i)[op], r0 = M.A->rank[ix(M.A, i, M.k)];
+      if (!M.oz || r0 == 0 || round32(r0) + M.F->ulen[i] > 16384) continue;
+      u0off[op] = tot;
+      tot += (int64_t)8 * M.b * round32(r0);
+    }
+    if (tot == 0) return;
+    int8_t* base = bu0->need<int8_t>((size_t)tot);
+    TLR_CUDA(cudaMemsetAsync(base, 0, (size_t)tot, ctx->stream));
+    std::vector<OzColJob> cj;
+    for (int op = 0; op < nops; ++op) {
+      if (u0off[op] < 0) continue;
+      const Mat& M = *(*L)[(*op_m)[op]];
+      const int i = (*op_i)[op], r0 = M.A->rank[ix(M.A, i, M.k)], r0w = round32(r0);
+      OzColJob c{reinterpret_cast<const double*>(Panels<T>::AU(M, i)) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)],
+                 base + u0off[op], nullptr, M.b, r0, 0, M.b};
+      c.plane = (size_t)M.b * r0w;
+      c.efix = 1;
+      c.tld = r0w;
+      cj.push_back(c);
+    }
+    oz_split_cols(ctx, cj);
+  }
+
   void sample(const std::vector<int>& ops, int t, const double*, const std::vector<double*>& Ydst) override {
+    if (!u0_ready) prepare_u0();
     // matrices present in this call
     std::vector<int> mp;
     std::vector<int> slot_of_m(L->size(), -1);
@@ -269,10 +309,11 @@ struct BatchSampler : Sampler {
       d.Kk = M.Kk;
       d.q = bs;
       d.bs = bs;
+      d.r0w = u0off[op] >= 0 ? round32(d.r0) : d.r0;
       d.W = reinterpret_cast<T*>(wtot);  // offset, fixed below
       d.P = nullptr;
       d.Z = nullptr;
-      wtot += (int64_t)(d.r0 + d.Ki) * bs;
+      wtot += (int64_t)(d.r0w + d.Ki) * bs;
       ytot += (int64_t)M.b * bs;
     }
     T* W = bw->need<T>((size_t)std::max<int64_t>(wtot, 1));
@@ -283,7 +324,7 @@ struct BatchSampler : Sampler {
       const Mat& M = *(*L)[(*op_m)[ops[s]]];
       const int i = sd[s].i;
       for (int j = 0; j <= M.k; ++j) {
-        const int R = j < M.k ? M.F->rank[ix(M.F, i, j)] : sd[s].r0;
+        const int R = j < M.k ? M.F->rank[ix(M.F, i, j)] : sd[s].r0w;
         for (int rc = 0; 16 * rc < R; ++rc)
           for (int cc = 0; 16 * cc < bs; ++cc)
             items.push_back(BlkItem{(uint32_t)s, (uint16_t)j, (uint8_t)rc, (uint8_t)cc});
@@ -296,31 +337,56 @@ struct BatchSampler : Sampler {
     std::vector<OzColJob> wcj;
     std::vector<OzJob> wyj;
     int64_t yo = 0;
-    int64_t wsl = 0, wex = 0;  // slices of the W_i rows that multiply Urow_i (split path)
-    if (!F32)
-      for (size_t s = 0; s < ops.size(); ++s) {
-        const Mat& M = *(*L)[(*op_m)[ops[s]]];
-        if (M.oz && sd[s].Ki > 0 && sd[s].Ki <= 16384) { wsl += (int64_t)8 * oz_ld(sd[s].Ki) * bs; wex += bs; }
-      }
+    // split path: Y = [U0 | Urow_i] W as one product when U0 has slices (K = r0w + Ki), or Urow_i W_i
+    // after the FP64 product with U0 when it has none
+    auto folded = [&](size_t s) { return u0off[ops[s]] >= 0; };
+    auto split_k = [&](size_t s) -> int {
+      const Mat& M = *(*L)[(*op_m)[ops[s]]];
+      if (F32 || !M.oz) return 0;
+      if (folded(s)) return sd[s].r0w + sd[s].Ki;
+      return (sd[s].Ki > 0 && sd[s].Ki <= 16384) ? sd[s].Ki : 0;
+    };
+    int64_t wsl = 0, wex = 0;  // slices of the W_i rows of the split products
+    for (size_t s = 0; s < ops.size(); ++s) {
+      const int ks = split_k(s);
+      if (ks > 0) { wsl += (int64_t)8 * oz_ld(ks) * bs; wex += bs; }
+    }
     int8_t* ws_ = wsl ? bws->need<int8_t>((size_t)wsl) : nullptr;
     int* we_ = wex ? bwe->need<int>((size_t)wex) : nullptr;
     for (size_t s = 0; s < ops.size(); ++s) {
       const int op = ops[s], i = (*op_i)[op];
       Mat& M = *(*L)[(*op_m)[op]];
-      const int r0 = sd[s].r0, Ki = sd[s].Ki, ldw = std::max(r0 + Ki, 1);
+      const int r0 = sd[s].r0, r0w = sd[s].r0w, Ki = sd[s].Ki, ldw = std::max(r0w + Ki, 1);
       T* Yo = F32 ? Y32 + yo : reinterpret_cast<T*>(Ydst[s]);
       const T* U0 = r0 ? Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)] : nullptr;
       GemmJob<T> g = job<T>(NN, M.b, bs, U0, M.b, sd[s].W, ldw, r0, Yo, M.b, 1.0, 0.0);
-      const bool split = !F32 && M.oz && Ki > 0 && Ki <= 16384;  // exact integer totals need K <= 16384
-      if (split) {  // Y = U0 W[0:r0] here, then + Urow_i W[r0:] on the tensor cores
-        const int ldo = oz_ld(Ki);
-        OzColJob c{reinterpret_cast<const double*>(sd[s].W + r0), ws_, we_, ldw, bs, 0, Ki};
+      const int ks = split_k(s);  // exact integer totals need K <= 16384
+      if (ks > 0) {
+        const int ldo = oz_ld(ks);
+        const int w0 = folded(s) ? 0 : r0;  // first W row of the product
+        OzColJob c{reinterpret_cast<const double*>(sd[s].W + w0), ws_, we_, ldw, bs, 0, ks};
         c.ldo = ldo;
         wcj.push_back(c);
         OzJob y{M.FUt[i], ws_, d_one, we_, reinterpret_cast<double*>(Yo), (size_t)M.b * M.futcap[i],
-                (size_t)ldo * bs, (int)M.futcap[i], M.b, M.b, bs, Ki};
+                (size_t)ldo * bs, (int)M.futcap[i], M.b, M.b, bs, ks};
         y.ldb = ldo;
-        y.accumulate = 1;
+        if (folded(s)) {  // Y = [U0 | Urow_i] W on the tensor cores alone
+          const int8_t* u0 = static_cast<const int8_t*>(bu0->p) + u0off[ops[s]];
+          if (Ki > 0) {
+            y.A0 = u0;
+            y.sA0 = (size_t)M.b * r0w;
+            y.lda0 = r0w;
+            y.K0 = r0w;
+          } else {
+            y.A = u0;
+            y.sA = (size_t)M.b * r0w;
+            y.lda = r0w;
+          }
+          y.accumulate = 0;
+        } else {  // Y = U0 W[0:r0] in FP64 first, then + Urow_i W[r0:]
+          y.accumulate = 1;
+          jy.push_back(g);
+        }
         if (M.mixed16) y.tol = M.thr / (8.0 * std::sqrt((double)M.b));  // column norm of Y within thr / 8
         wyj.push_back(y);
         ws_ += (size_t)8 * ldo * bs;
@@ -331,8 +397,8 @@ struct BatchSampler : Sampler {
         g.B[1] = sd[s].W + r0;
         g.ldb[1] = ldw;
         g.K[1] = Ki;
+        jy.push_back(g);
       }
-      jy.push_back(g);
       if (F32) cb.push_back(ConvBackJob{reinterpret_cast<const float*>(Yo), Ydst[s], (int64_t)M.b * bs});
       yo += (int64_t)M.b * bs;
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * bs * (r0 + Ki);
@@ -584,12 +650,13 @@ struct Session {
   Buf bOzOs, bOzOe, bOzWs, bOzWe, bOne;  // split sampling / projection products
   Buf bOzDs, bOzDe, bOzDm;               // split updateDense products (side stream)
   Buf bMcW, bMcT;                        // modified Cholesky workspaces (main stream)
+  Buf bOzU0;                             // slices of the column's U0 blocks (split sampling products)
   int* d_one = nullptr;
   AraStats total;
   explicit Session(tlr_ctx* c)
       : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bW(c), bY32(c), bP(c), bZ(c),
         bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c), bOzOs(c), bOzOe(c), bOzWs(c), bOzWe(c),
-        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c), bMcW(c), bMcT(c) {
+        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c), bMcW(c), bMcT(c), bOzU0(c) {
     static const int one = 1;
     d_one = bOne.need<int>(1);
     TLR_CUDA(cudaMemcpyAsync(d_one, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -1126,7 +1193,7 @@ struct Session {
         S.Q = Q; S.qoff = &qoff;
         S.bom = &bOm; S.bom32 = &bOm32; S.bw = &bW; S.by32 = &bY32; S.bp = &bP; S.bz = &bZ;
         S.bq32 = &bQ32; S.bb32 = &bB32;
-        S.d_one = d_one; S.bos = &bOzOs; S.boe = &bOzOe; S.bws = &bOzWs; S.bwe = &bOzWe;
+        S.d_one = d_one; S.bos = &bOzOs; S.boe = &bOzOe; S.bws = &bOzWs; S.bwe = &bOzWe; S.bu0 = &bOzU0;
       };
       setup(s64, any32 ? &is64 : nullptr);
       setup(s32, &is32);

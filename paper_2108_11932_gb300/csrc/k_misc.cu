@@ -921,14 +921,15 @@ __global__ void __launch_bounds__(128) k_blkdiag(const SlotDescT<T>* __restrict_
   const int tid = threadIdx.x;
   const int C = PROJ ? sd.q : sd.bs;
   const int ldin = PROJ ? sd.r0 + sd.Ki : sd.ldx;          // P (project) or X (sample)
-  const int ldout = PROJ ? sd.r0 + sd.Kk : sd.r0 + sd.Ki;  // Z (project) or W (sample)
+  const int ldout = PROJ ? sd.r0 + sd.Kk : sd.r0w + sd.Ki;  // Z (project) or W (sample)
   T* const outbase = PROJ ? sd.Z : sd.W;
   if (j == k) {  // leading block: the tile's own factor part
     const T* src = PROJ ? sd.P : sd.X0 + sd.x0off;
     const int lds = PROJ ? ldin : sd.ldx0;
+    const int rows = PROJ ? sd.r0 : sd.r0w;  // rows past r0 (sample, padded layout) are zero
     for (int e = tid; e < 256; e += blockDim.x) {
       const int a = a0 + (e & 15), c = c0 + (e >> 4);
-      if (a < sd.r0 && c < C) outbase[a + (size_t)c * ldout] = src[a + (size_t)c * lds];
+      if (a < rows && c < C) outbase[a + (size_t)c * ldout] = a < sd.r0 ? src[a + (size_t)c * lds] : T(0);
     }
     return;
   }
@@ -938,7 +939,7 @@ __global__ void __launch_bounds__(128) k_blkdiag(const SlotDescT<T>* __restrict_
   const int ldg = sd.gld[j];
   // sample: In = X_j (the r_kj rows of X at U_kj's offset); project: In = P_j (r_ij rows)
   const T* In = PROJ ? sd.P + sd.r0 + sd.uoff[i * nb + j] : sd.X + sd.uoff[k * nb + j];
-  T* out = outbase + sd.r0 + (PROJ ? sd.uoff[k * nb + j] : sd.uoff[i * nb + j]);
+  T* out = outbase + (PROJ ? sd.r0 + sd.uoff[k * nb + j] : sd.r0w + sd.uoff[i * nb + j]);
   __shared__ T As[16][17];  // op(G) chunk [row][kk]
   __shared__ T Bs[16][17];  // In chunk [kk][col]
   // Thread (row, column pair): warp w owns rows 4w .. 4w+3, so warps whose rows lie beyond R

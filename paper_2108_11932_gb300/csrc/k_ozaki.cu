@@ -79,14 +79,14 @@ constexpr unsigned long long OZ_WAIT_NS = 2000000000ull;
 // Tensor maps live in the job table (global memory); CUtensorMap carries its own (>= 64-byte)
 // alignment, and the upload ring hands out 256-byte aligned regions.
 struct OzDev {
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, ta0;  // ta0: the first K segment of A (K0 > 0)
   const int* eA;
   const int* eB;
   double* C;
   double* ws;
   int* ctr;
   double tol;  // > 0: truncate to the fewest planes whose error bound per entry stays below tol
-  int M, N, K, ldc, acol, accumulate, eB_stride, nsplit, tiles_n, S, smin;
+  int M, N, K, ldc, acol, accumulate, eB_stride, nsplit, tiles_n, S, smin, K0;
 };
 static_assert(alignof(OzDev) >= 64 && sizeof(OzDev) % 64 == 0, "tensor maps need 64-byte alignment");
 
@@ -440,6 +440,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
     if (lane == 0) {
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&Jp->ta) : "memory");
       asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&Jp->tb) : "memory");
+      const int K0 = Jp->K0;
+      if (K0 > 0) asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&Jp->ta0) : "memory");
       const uint32_t bytes = (uint32_t)(S * (OZ_TM * OZ_KS + OZ_TN * OZ_KS));  // one box per plane
       int issued = 0;
       for (int s = 0; s < nst; ++s) {
@@ -450,7 +452,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_mma(const OzDev* __restric
         mbar_expect_tx(b_full8 + 8 * slot, bytes);
         for (int q = 0; q < S; ++q) {
           if (acol) tma_3d(su32(st + q * (OZ_TM * OZ_KS)), &Jp->ta, m0, k0, q, b_full8 + 8 * slot);
-          else tma_4d(su32(st + q * (OZ_TM * OZ_KS)), &Jp->ta, 0, m0, k0 / 16, q, b_full8 + 8 * slot);
+          else if (k0 < K0) tma_4d(su32(st + q * (OZ_TM * OZ_KS)), &Jp->ta0, 0, m0, k0 / 16, q, b_full8 + 8 * slot);
+          else tma_4d(su32(st + q * (OZ_TM * OZ_KS)), &Jp->ta, 0, m0, (k0 - K0) / 16, q, b_full8 + 8 * slot);
           tma_4d(su32(st + ST_A + q * (OZ_TN * OZ_KS)), &Jp->tb, 0, n0, k0 / 16, q, b_full8 + 8 * slot);
         }
         issued = s + 1;
@@ -771,8 +774,17 @@ void oz_gemm(tlr_ctx* ctx, std::vector<OzJob>& jobs) {
     OzDev& d = dev[u];
     memset(&d, 0, sizeof(d));
     const int ldb = j.ldb > 0 ? j.ldb : oz_ld(j.K);
-    if (j.acol) map_mmajor(&d.ta, j.A, (uint64_t)j.M, (uint64_t)j.K, (uint64_t)j.lda, j.sA);
-    else map_kmajor(&d.ta, j.A, (uint64_t)j.K, (uint64_t)j.M, (uint64_t)j.lda, j.sA, OZ_TM);
+    if (j.K0 > 0) {  // two K segments: [0, K0) from A0, [K0, K) from A
+      TLR_REQUIRE(!j.acol && j.K0 % OZ_KS == 0 && j.K0 < j.K && j.A0, TLR_ERR_LIMIT,
+                  "split product: bad first K segment");
+      map_kmajor(&d.ta0, j.A0, (uint64_t)j.K0, (uint64_t)j.M, (uint64_t)j.lda0, j.sA0, OZ_TM);
+      map_kmajor(&d.ta, j.A, (uint64_t)(j.K - j.K0), (uint64_t)j.M, (uint64_t)j.lda, j.sA, OZ_TM);
+    } else if (j.acol) {
+      map_mmajor(&d.ta, j.A, (uint64_t)j.M, (uint64_t)j.K, (uint64_t)j.lda, j.sA);
+    } else {
+      map_kmajor(&d.ta, j.A, (uint64_t)j.K, (uint64_t)j.M, (uint64_t)j.lda, j.sA, OZ_TM);
+    }
+    d.K0 = j.K0;
     map_kmajor(&d.tb, j.B, (uint64_t)j.K, (uint64_t)j.N, (uint64_t)ldb, j.sB, OZ_TN);
     d.eA = j.eA;
     d.eB = j.eB;
