@@ -119,6 +119,10 @@ struct BatchSampler : Sampler {
   // Y = [U0 | Urow_i] W is one split product; u0off[op] < 0 where that product stays in FP64
   Buf* bu0 = nullptr;
   std::vector<int64_t> u0off;
+  // the same blocks sliced along their columns (rows along b, like Urow_i's), for P0 = U0^T Q in the
+  // projection; u0poff[op] < 0 where that product stays in FP64
+  Buf* bu0p = nullptr;
+  std::vector<int64_t> u0poff;
   bool u0_ready = false;
   static constexpr bool F32 = sizeof(T) == 4;
   bool owns_omega() const override { return true; }
@@ -231,7 +235,33 @@ struct BatchSampler : Sampler {
     u0_ready = true;
     const int nops = (int)op_m->size();
     u0off.assign(nops, -1);
-    if (F32 || !bu0) return;
+    u0poff.assign(nops, -1);
+    if (F32 || !bu0 || !bu0p) return;
+    {  // column-oriented slices for the projection
+      int64_t tot = 0;
+      for (int op = 0; op < nops; ++op) {
+        if (!mine(op)) continue;
+        const Mat& M = *(*L)[(*op_m)[op]];
+        const int i = (*op_i)[op], r0 = M.A->rank[ix(M.A, i, M.k)];
+        if (!M.oz || r0 == 0) continue;
+        u0poff[op] = tot;
+        tot += (int64_t)8 * M.b * r0;
+      }
+      if (tot > 0) {
+        int8_t* base = bu0p->need<int8_t>((size_t)tot);
+        std::vector<OzColJob> cj;
+        for (int op = 0; op < nops; ++op) {
+          if (u0poff[op] < 0) continue;
+          const Mat& M = *(*L)[(*op_m)[op]];
+          const int i = (*op_i)[op], r0 = M.A->rank[ix(M.A, i, M.k)];
+          OzColJob c{reinterpret_cast<const double*>(Panels<T>::AU(M, i)) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)],
+                     base + u0poff[op], nullptr, M.b, r0, 0, M.b};
+          c.efix = 1;
+          cj.push_back(c);
+        }
+        oz_split_cols(ctx, cj);
+      }
+    }
     int64_t tot = 0;
     for (int op = 0; op < nops; ++op) {
       if (!mine(op)) continue;
@@ -473,11 +503,13 @@ struct BatchSampler : Sampler {
     std::vector<GemmJob<T>> jp;
     std::vector<OzColJob> qcj;
     std::vector<OzJob> pqj;
-    int64_t qsl = 0, qex = 0;  // slices of Q_i for the split products with Urow_i
+    if (!u0_ready) prepare_u0();
+    auto p0_split = [&](size_t s) { return !F32 && u0poff[ops[s]] >= 0; };
+    int64_t qsl = 0, qex = 0;  // slices of Q_i for the split products with Urow_i and U0
     if (!F32)
       for (size_t s = 0; s < ops.size(); ++s) {
         const Mat& M = *(*L)[(*op_m)[ops[s]]];
-        if (M.oz && sd[s].Ki > 0) { qsl += (int64_t)8 * M.b * q[ops[s]]; qex += q[ops[s]]; }
+        if (M.oz && (sd[s].Ki > 0 || p0_split(s))) { qsl += (int64_t)8 * M.b * q[ops[s]]; qex += q[ops[s]]; }
       }
     int8_t* qs_ = qsl ? bws->need<int8_t>((size_t)qsl) : nullptr;
     int* qe_ = qex ? bwe->need<int>((size_t)qex) : nullptr;
@@ -485,19 +517,29 @@ struct BatchSampler : Sampler {
       const int op = ops[s], i = (*op_i)[op];
       Mat& M = *(*L)[(*op_m)[op]];
       const int r0 = sd[s].r0, Ki = sd[s].Ki, ldp = r0 + Ki;
-      if (r0 > 0)
-        jp.push_back(job<T>(TN, r0, q[op], Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)], M.b, Qop(s),
-                            M.b, M.b, sd[s].P, ldp, 1.0, 0.0));
+      const bool qsplit = !F32 && M.oz && (Ki > 0 || p0_split(s));
+      if (qsplit) qcj.push_back(OzColJob{reinterpret_cast<const double*>(Qop(s)), qs_, qe_, M.b, q[op], 0, M.b});
+      if (r0 > 0) {
+        if (p0_split(s)) {  // P[0:r0] = U0^T Q_i on the tensor cores
+          pqj.push_back(OzJob{static_cast<const int8_t*>(bu0p->p) + u0poff[op], qs_, d_one, qe_,
+                              reinterpret_cast<double*>(sd[s].P), (size_t)M.b * r0, (size_t)M.b * q[op], M.b, ldp,
+                              r0, q[op], M.b});
+        } else {
+          jp.push_back(job<T>(TN, r0, q[op], Panels<T>::AU(M, i) + (size_t)M.b * M.A->uoff[ix(M.A, i, M.k)], M.b,
+                              Qop(s), M.b, M.b, sd[s].P, ldp, 1.0, 0.0));
+        }
+      }
       if (Ki > 0) {
         if (!F32 && M.oz) {  // P[r0:] = Urow_i^T Q_i on the tensor cores
-          qcj.push_back(OzColJob{reinterpret_cast<const double*>(Qop(s)), qs_, qe_, M.b, q[op], 0, M.b});
           pqj.push_back(OzJob{M.FUs[i], qs_, d_one, qe_, reinterpret_cast<double*>(sd[s].P + r0),
                               (size_t)M.b * M.fuscap[i], (size_t)M.b * q[op], M.b, ldp, Ki, q[op], M.b});
-          qs_ += (size_t)8 * M.b * q[op];
-          qe_ += q[op];
         } else {
           jp.push_back(job<T>(TN, Ki, q[op], Panels<T>::U(M, i), M.b, Qop(s), M.b, M.b, sd[s].P + r0, ldp, 1.0, 0.0));
         }
+      }
+      if (qsplit) {
+        qs_ += (size_t)8 * M.b * q[op];
+        qe_ += q[op];
       }
       (F32 ? M.fl32 : M.fl_exec) += 2.0 * M.b * q[op] * (r0 + Ki);
     }
@@ -650,13 +692,13 @@ struct Session {
   Buf bOzOs, bOzOe, bOzWs, bOzWe, bOne;  // split sampling / projection products
   Buf bOzDs, bOzDe, bOzDm;               // split updateDense products (side stream)
   Buf bMcW, bMcT;                        // modified Cholesky workspaces (main stream)
-  Buf bOzU0;                             // slices of the column's U0 blocks (split sampling products)
+  Buf bOzU0, bOzU0p;                     // slices of the column's U0 blocks (split sampling / projection)
   int* d_one = nullptr;
   AraStats total;
   explicit Session(tlr_ctx* c)
       : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bW(c), bY32(c), bP(c), bZ(c),
         bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c), bOzOs(c), bOzOe(c), bOzWs(c), bOzWe(c),
-        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c), bMcW(c), bMcT(c), bOzU0(c) {
+        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c), bMcW(c), bMcT(c), bOzU0(c), bOzU0p(c) {
     static const int one = 1;
     d_one = bOne.need<int>(1);
     TLR_CUDA(cudaMemcpyAsync(d_one, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -1194,6 +1236,7 @@ struct Session {
         S.bom = &bOm; S.bom32 = &bOm32; S.bw = &bW; S.by32 = &bY32; S.bp = &bP; S.bz = &bZ;
         S.bq32 = &bQ32; S.bb32 = &bB32;
         S.d_one = d_one; S.bos = &bOzOs; S.boe = &bOzOe; S.bws = &bOzWs; S.bwe = &bOzWe; S.bu0 = &bOzU0;
+        S.bu0p = &bOzU0p;
       };
       setup(s64, any32 ? &is64 : nullptr);
       setup(s32, &is32);
