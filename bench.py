@@ -432,10 +432,12 @@ def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
     with the split products' plane histogram of one factorization (mixed: planes chosen per block)."""
     variants = {}
     reps = 3
-    for vname, veps, vprec, vldl in args.variant_list:
-        if (veps, vprec, vldl) == (eps, prec, False):
+    for vname, veps, vprec, vldl, *vrest in args.variant_list:
+        vpiv = bool(vrest and vrest[0])
+        if (veps, vprec, vldl, vpiv) == (eps, prec, False, False):
             continue
-        vo = T.default_opts(bs=w["bs"], seed=w["seed"], precision=vprec)
+        vo = T.default_opts(bs=w["bs"], seed=w["seed"], precision=vprec,
+                            pivot=T.PIVOT_FROBENIUS if vpiv else T.PIVOT_NONE)
         try:
             cs, fs = [], []
             for r in range(reps):
@@ -453,14 +455,17 @@ def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
                 fs.append(e1.elapsed_time(e2) / 1e3)
                 inf = A.info()
                 ld = A.logdet()[0]
+                # tile exchanges of Algorithm 9: positions whose tile is not the construction's
+                moved = int(np.sum(A.perm()[:: w["b"]] != np.asarray(perm)[:: w["b"]])) if vpiv else 0
                 A.free()
             f = statistics.median(fs)
             variants[vname] = {"eps": veps, "precision": ["fp64", "fp32", "mixed"][vprec],
-                               "factorization": "ldlt" if vldl else "chol", "factor_s": f,
+                               "factorization": "ldlt" if vldl else ("chol_pivoted" if vpiv else "chol"),
+                               "factor_s": f,
                                "compress_s": statistics.median(cs), "reps": reps,
                                "tflops_exec": inf["flops_exec"] / f / 1e12,
                                "tflops_model": inf["flops_model"] / f / 1e12, "mean_rank": inf["mean_rank"],
-                               "logdet": ld,
+                               "logdet": ld, **({"tiles_moved": moved} if vpiv else {}),
                                "split_planes": {"compress": {f"s{i}": c_planes[i] for i in range(1, 9) if c_planes[i]},
                                                 "factor": {f"s{i}": f_planes[i] for i in range(1, 9) if f_planes[i]},
                                                 "chunk_bytes_compress": c_bytes, "chunk_bytes_factor": f_bytes}}
@@ -825,6 +830,8 @@ def main():
     if WORKLOAD != "cov3d_32k":
         vl += [("fp64_eps1e-4", 1e-4, 0, False), ("mixed_eps1e-4", 1e-4, 2, False)]
     vl += [(f"fp64_eps{hi:g}", hi, 0, False), (f"fp64_ldlt_eps{hi:g}", hi, 0, True)]
+    # tile-pivoted Cholesky (Algorithm 9) at both thresholds
+    vl += [(f"fp64_pivot_eps{lo:g}", lo, 0, False, True), (f"fp64_pivot_eps{hi:g}", hi, 0, False, True)]
     args.variant_list = [] if args.no_variants else vl
     if args.impl == "reference":
         run_reference(args, w, args.eps)

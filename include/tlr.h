@@ -82,6 +82,19 @@ enum {
                           the modified Cholesky of Algorithm 8 (Section 5.1.2, tlr_dense_modchol) */
 };
 
+/* Tile pivoting (Algorithm 9, Section 5.2). */
+enum {
+  TLR_PIVOT_NONE = 0,
+  TLR_PIVOT_FROBENIUS = 1 /* Cholesky only, FP64 precision, compensation NONE or SHIFT, N a multiple of b:
+                             at step k every remaining diagonal tile holds A(i,i) - D_i (the terms of the
+                             finished columns are added as each column ends); the one with the largest
+                             Frobenius norm (the first on ties) is exchanged with tile k, rows and columns,
+                             before the step proceeds as in Algorithm 6.  The factor is that of P A P^T;
+                             tlr_get_perm returns the point order with the exchanges, and the solve,
+                             logdet and products take and return vectors in the original order.  With
+                             SHIFT the shift is added to every diagonal tile before the first step. */
+};
+
 typedef struct {
   int bs;           /* ARA sampling block width (Algorithm 1), 1..64; 0 = 16 */
   int max_slots;    /* dynamic-batch width: tiles sampled concurrently (Algorithm 5
@@ -91,7 +104,8 @@ typedef struct {
   double shift;     /* diagonal shift for TLR_COMP_SHIFT (Section 5.1: s <= eps) */
   uint64_t seed;    /* Philox key of the Gaussian blocks */
   int ldl;          /* internal: set by tlr_ldlt */
-  int reserved[7];
+  int pivot;        /* TLR_PIVOT_* */
+  int reserved[6];
 } tlr_opts;
 
 /* Fill `o` with defaults: bs 16, all tiles in the batch, FP64, no compensation, seed 0. */
@@ -139,14 +153,20 @@ tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* src, tlr_mat** dst);
 
 /* Left-looking TLR Cholesky, Algorithm 6 (updateDense, chol, cholARAUpdate
  * with dynamic batching per Algorithm 5, batchTrsm, updateTiles).  In place:
- * A := L with A ~= L L^T.  Every updated tile is recompressed to eps.
- * TLR_ERR_NOT_SPD if a diagonal tile is not positive definite (k_fail in tlr_info). */
+ * A := L with A ~= L L^T.  Every updated tile is recompressed to eps.  With
+ * opts.pivot = TLR_PIVOT_FROBENIUS, Algorithm 9 (tile pivoting): A := L with
+ * P A P^T ~= L L^T, P recorded in the factor's point order.
+ * TLR_ERR_NOT_SPD if a diagonal tile is not positive definite (k_fail in tlr_info).
+ * TLR_ERR_ARG for options outside their rules (bs > min(64, b); MODCHOL with
+ * b > 2048; pivoting with precision other than FP64, compensation other than
+ * NONE or SHIFT, or N not a multiple of b). */
 tlr_status tlr_potrf(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts);
 
 /* Pivot-free left-looking TLR LDL^T, Algorithm 10 (five-product sampling
  * chain of Equation 3, dense unpivoted LDL^T of the diagonal tiles, batchTrsm
  * followed by batchIDMult).  In place: A := (L, D), L unit lower on the diagonal
- * tiles.  TLR_ERR_NOT_SPD if a pivot of D is exactly zero or not finite. */
+ * tiles.  TLR_ERR_NOT_SPD if a pivot of D is exactly zero or not finite.
+ * TLR_ERR_ARG also for TLR_COMP_MODCHOL and for tile pivoting (Cholesky only). */
 tlr_status tlr_ldlt(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts);
 
 /* Batched factorization of `count` independent matrices (Cholesky if ldl == 0,

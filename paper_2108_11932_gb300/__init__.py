@@ -23,6 +23,7 @@ __all__ = ["Context", "Matrix", "Opts", "TLRError", "build", "fortran", "kd_orde
 OK, ERR_ARG, ERR_NOMEM, ERR_NOT_SPD, ERR_CUDA, ERR_TIMEOUT, ERR_STATE, ERR_LIMIT = 0, -1, -2, -3, -4, -5, -6, -7
 PREC_FP64, PREC_FP32, PREC_MIXED = 0, 1, 2
 COMP_NONE, COMP_SHIFT, COMP_SCHUR, COMP_MODCHOL = 0, 1, 2, 3
+PIVOT_NONE, PIVOT_FROBENIUS = 0, 1
 OP_A, OP_L, OP_LT, OP_LLT = 0, 1, 2, 3
 STREAM_COMPRESS, STREAM_FACTOR, STREAM_SCHUR = 1, 2, 3
 
@@ -35,7 +36,8 @@ class TLRError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("bs", C.c_int), ("max_slots", C.c_int), ("precision", C.c_int), ("compensation", C.c_int),
-                ("shift", C.c_double), ("seed", C.c_uint64), ("ldl", C.c_int), ("reserved", C.c_int * 7)]
+                ("shift", C.c_double), ("seed", C.c_uint64), ("ldl", C.c_int), ("pivot", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class Kernel(C.Structure):

@@ -53,6 +53,11 @@ struct Mat {
   Buf G, G32, E, DV, DV32, Bc;
   Buf Asave;  // TLR_COMP_MODCHOL: the column's updated diagonal tile, kept for Algorithm 8
   int modified = 0;  // diagonal tiles factored by the modified Cholesky
+  // TLR_PIVOT_FROBENIUS (Algorithm 9): the diagonal tiles of F hold A(i,i) - D_i for every i >= k (the
+  // finished columns' terms are added as each column ends, not by updateDense), and tile rows and
+  // columns are exchanged before a step; the compressed input A is rewritten to the exchanged order
+  bool piv = false;
+  int swaps = 0;
   std::vector<float*> AU32, AV32, FU32, FV32;
   std::vector<int64_t> fu32cap;
   // 7-bit chunk planes (int8) of F's U panels relative to 2 (their columns are orthonormal basis
@@ -116,7 +121,9 @@ struct BatchSampler : Sampler {
   Buf *bos = nullptr, *boe = nullptr, *bws = nullptr, *bwe = nullptr;  // Omega / W (or Q) slices
   // the compressed input's U0 block of each operand's tile (i, k), sliced once per column step
   // (transposed: rows along its r0 columns, zero-padded to r0w = r0 rounded up to 32), so that
-  // Y = [U0 | Urow_i] W is one split product; u0off[op] < 0 where that product stays in FP64
+  // Y = [U0 | Urow_i] W is one split product; u0off[op] < 0 where that product stays in FP64 (as for
+  // tile-pivoted matrices: a tile moved across the diagonal has the old V0 as its U0, whose entries
+  // the slices' fixed bound 2 does not cover)
   Buf* bu0 = nullptr;
   std::vector<int64_t> u0off;
   // the same blocks sliced along their columns (rows along b, like Urow_i's), for P0 = U0^T Q in the
@@ -243,7 +250,7 @@ struct BatchSampler : Sampler {
         if (!mine(op)) continue;
         const Mat& M = *(*L)[(*op_m)[op]];
         const int i = (*op_i)[op], r0 = M.A->rank[ix(M.A, i, M.k)];
-        if (!M.oz || r0 == 0) continue;
+        if (!M.oz || r0 == 0 || M.piv) continue;
         u0poff[op] = tot;
         tot += (int64_t)8 * M.b * r0;
       }
@@ -267,7 +274,7 @@ struct BatchSampler : Sampler {
       if (!mine(op)) continue;
       const Mat& M = *(*L)[(*op_m)[op]];
       const int i = (*op_i)[op], r0 = M.A->rank[ix(M.A, i, M.k)];
-      if (!M.oz || r0 == 0 || round32(r0) + M.F->ulen[i] > 16384) continue;
+      if (!M.oz || r0 == 0 || M.piv || round32(r0) + M.F->ulen[i] > 16384) continue;
       u0off[op] = tot;
       tot += (int64_t)8 * M.b * round32(r0);
     }
@@ -693,12 +700,14 @@ struct Session {
   Buf bOzDs, bOzDe, bOzDm;               // split updateDense products (side stream)
   Buf bMcW, bMcT;                        // modified Cholesky workspaces (main stream)
   Buf bOzU0, bOzU0p;                     // slices of the column's U0 blocks (split sampling / projection)
+  Buf bPiv, bPivG, bPivE, bSwap, bSwapV;  // tile pivoting: norms, dense-update products, exchange staging
   int* d_one = nullptr;
   AraStats total;
   explicit Session(tlr_ctx* c)
       : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bW(c), bY32(c), bP(c), bZ(c),
         bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c), bOzOs(c), bOzOe(c), bOzWs(c), bOzWe(c),
-        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c), bMcW(c), bMcT(c), bOzU0(c), bOzU0p(c) {
+        bOne(c), bOzDs(c), bOzDe(c), bOzDm(c), bMcW(c), bMcT(c), bOzU0(c), bOzU0p(c), bPiv(c), bPivG(c), bPivE(c),
+        bSwap(c), bSwapV(c) {
     static const int one = 1;
     d_one = bOne.need<int>(1);
     TLR_CUDA(cudaMemcpyAsync(d_one, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -744,6 +753,12 @@ struct Session {
                              ctx->stream));
     if (ldl) F->dvec = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b));
     F->dinv = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)nb * b * b));
+    M.piv = o.pivot == TLR_PIVOT_FROBENIUS;
+    if (M.piv && o.compensation == TLR_COMP_SHIFT && o.shift != 0.0) {  // A + shift I, before any selection
+      std::vector<DiagJob> dj;
+      for (int i = 0; i < nb; ++i) dj.push_back(DiagJob{F->diag + (size_t)i * b * b, b, b, o.shift});
+      batched_add_diag(ctx, dj);
+    }
     for (int i = 0; i < nb; ++i) ensure_ucap(ctx, F, i, std::max<int64_t>(A->ulen[i], 16));
     M.oz = b % 16 == 0;
     if (M.oz) {
@@ -886,11 +901,244 @@ struct Session {
     }
   }
 
+  // selectPivot (Algorithm 9): for every pivoting matrix not at its last column, the remaining
+  // diagonal tile whose updated value A(i,i) - D_i has the largest Frobenius norm (the first on
+  // ties); tile rows and columns k and p are exchanged when p != k.
+  void select_pivots(const std::vector<Mat*>& L) {
+    std::vector<Mat*> P;
+    int64_t tot = 0;
+    for (Mat* Mp : L)
+      if (Mp->piv && Mp->k < Mp->nb - 1) {
+        P.push_back(Mp);
+        tot += (int64_t)(Mp->nb - Mp->k) * Mp->b;
+      }
+    if (P.empty()) return;
+    double* d = bPiv.need<double>((size_t)tot);
+    int64_t o = 0;
+    for (Mat* Mp : P) {  // squared norms of the tiles' columns (the tiles are contiguous b x b blocks)
+      const int64_t n = (int64_t)(Mp->nb - Mp->k) * Mp->b;
+      col_sqnorms(ctx, Mp->F->diag + (size_t)Mp->k * Mp->b * Mp->b, Mp->b, n, d + o);
+      o += n;
+    }
+    std::vector<double> h((size_t)tot);
+    TLR_CUDA(cudaMemcpyAsync(h.data(), d, sizeof(double) * tot, cudaMemcpyDeviceToHost, ctx->stream));
+    TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+    o = 0;
+    for (Mat* Mp : P) {
+      Mat& M = *Mp;
+      int p = M.k;
+      double best = -1.0;
+      for (int i = M.k; i < M.nb; ++i) {
+        double sq = 0.0;
+        for (int c = 0; c < M.b; ++c) sq += h[(size_t)o + (size_t)(i - M.k) * M.b + c];
+        const double nrm = std::sqrt(sq);
+        if (nrm > best) {
+          best = nrm;
+          p = i;
+        }
+      }
+      o += (int64_t)(M.nb - M.k) * M.b;
+      if (p != M.k) exchange_tiles(M, M.k, p);
+    }
+  }
+
+  // pivotRowColumn (Algorithm 9): exchange tile rows and columns k < p.  The updated diagonal tiles,
+  // the points and the permutation swap blocks; F's finished rows k and p (columns j < k) swap their
+  // U panels and the positions of their V blocks in each V panel; the compressed input's trailing
+  // tiles (i, j), k <= j < i, are rewritten as new(i, j) = old(s(i), s(j)), with s exchanging k and p,
+  // or the transpose of old(s(j), s(i)) (U and V exchanged) where the pair crosses the diagonal.  The
+  // input's finished columns j < k are no longer read and are released.
+  void exchange_tiles(Mat& M, int k, int p) {
+    tlr_mat* A = M.A;
+    tlr_mat* F = M.F;
+    const int nb = M.nb, b = M.b;
+    auto sg = [&](int i) { return i == k ? p : (i == p ? k : i); };
+    ++M.swaps;
+    {  // diagonal tiles, ordered points, device permutation: swap block k and block p
+      const size_t bb = (size_t)b * b, pb = (size_t)b * A->d;
+      double* t = bSwap.need<double>(std::max(bb, pb + (size_t)b));
+      auto swap_dev = [&](void* x, void* y, size_t bytes) {
+        TLR_CUDA(cudaMemcpyAsync(t, x, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        TLR_CUDA(cudaMemcpyAsync(x, y, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        TLR_CUDA(cudaMemcpyAsync(y, t, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      };
+      swap_dev(F->diag + k * bb, F->diag + p * bb, bb * sizeof(double));
+      if (A->pts) swap_dev(A->pts + k * pb, A->pts + p * pb, pb * sizeof(double));
+      if (A->dperm) swap_dev(A->dperm + (size_t)k * b, A->dperm + (size_t)p * b, (size_t)b * sizeof(int64_t));
+      std::swap_ranges(A->perm.begin() + (size_t)k * b, A->perm.begin() + (size_t)(k + 1) * b,
+                       A->perm.begin() + (size_t)p * b);
+    }
+    // ---------------------------------------------------------------- F: rows k and p of columns j < k
+    if (k > 0) {
+      const std::vector<int> fr = F->rank;
+      const std::vector<int64_t> fv = F->voff;
+      std::swap(F->Urow[k], F->Urow[p]);
+      std::swap(F->ucap[k], F->ucap[p]);
+      std::swap(F->ulen[k], F->ulen[p]);
+      if (M.oz) {
+        std::swap(M.FUs[k], M.FUs[p]);
+        std::swap(M.fuscap[k], M.fuscap[p]);
+        std::swap(M.FUt[k], M.FUt[p]);
+        std::swap(M.futcap[k], M.futcap[p]);
+      }
+      int64_t seg = 0;
+      for (int j = 0; j < k; ++j) {
+        std::swap(F->rank[ix(F, k, j)], F->rank[ix(F, p, j)]);
+        std::swap(F->uoff[ix(F, k, j)], F->uoff[ix(F, p, j)]);
+        seg += F->vlen[j] - fv[ix(F, k, j)];
+      }
+      // each V panel's rows >= k, staged, then written back block by block in the new row order
+      double* t = bSwapV.need<double>((size_t)std::max<int64_t>(seg, 1) * b);
+      std::vector<CopyJob> stage, back;
+      std::vector<OzColJob> vcj;
+      int64_t to = 0;
+      for (int j = 0; j < k; ++j) {
+        const int64_t s0 = fv[ix(F, k, j)], n = F->vlen[j] - s0;
+        if (n <= 0) continue;
+        stage.push_back(CopyJob{F->Vcol[j] + (size_t)b * s0, t + (size_t)b * to, n * b});
+        int64_t c = s0;
+        for (int i = k; i < nb; ++i) {
+          const int a = sg(i), r = fr[ix(F, a, j)];
+          F->voff[ix(F, i, j)] = c;
+          if (r > 0) back.push_back(CopyJob{t + (size_t)b * (to + fv[ix(F, a, j)] - s0), F->Vcol[j] + (size_t)b * c,
+                                           (int64_t)r * b});
+          c += r;
+        }
+        to += n;
+        if (M.oz && M.FVs[j]) {  // the panel's chunk planes, against its unchanged bound
+          OzColJob cj{F->Vcol[j], M.FVs[j], M.dFVe + j, b, (int)F->vlen[j], 0, b};
+          cj.emax = M.dFVmax + j;
+          vcj.push_back(cj);
+        }
+      }
+      batched_copy(ctx, stage);
+      batched_copy(ctx, back);
+      oz_split_cols(ctx, vcj);
+    }
+    // ---------------------------------------------------------------- the compressed input's trailing tiles
+    const std::vector<int> ar = A->rank;
+    const std::vector<int64_t> au = A->uoff, av = A->voff;
+    const std::vector<double*> AU = A->Urow, AV = A->Vcol;
+    struct Src {
+      const double* U;
+      const double* V;
+      int r;
+    };
+    auto src = [&](int i, int j) -> Src {  // the tile at (i, j), i > j >= k, after the exchange
+      const int a = sg(i), c = sg(j);
+      if (a > c) return Src{AU[a] + (size_t)b * au[ix(A, a, c)], AV[c] + (size_t)b * av[ix(A, a, c)], ar[ix(A, a, c)]};
+      return Src{AV[a] + (size_t)b * av[ix(A, c, a)], AU[c] + (size_t)b * au[ix(A, c, a)], ar[ix(A, c, a)]};
+    };
+    std::vector<CopyJob> cp;
+    std::vector<double*> release;
+    for (int i = 0; i < nb; ++i) {  // row panels: only the tiles of columns >= k remain
+      for (int j = 0; j < std::min(i, k); ++j) {
+        A->rank[ix(A, i, j)] = 0;
+        A->uoff[ix(A, i, j)] = 0;
+        A->voff[ix(A, i, j)] = 0;
+      }
+      release.push_back(AU[i]);
+      A->Urow[i] = nullptr;
+      A->ulen[i] = 0;
+      A->ucap[i] = 0;
+      if (i <= k) continue;
+      int64_t len = 0;
+      for (int j = k; j < i; ++j) len += src(i, j).r;
+      A->Urow[i] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(len, 1) * b));
+      A->ulen[i] = len;
+      A->ucap[i] = std::max<int64_t>(len, 1);
+      int64_t c = 0;
+      for (int j = k; j < i; ++j) {
+        const Src e = src(i, j);
+        A->rank[ix(A, i, j)] = e.r;
+        A->uoff[ix(A, i, j)] = c;
+        if (e.r > 0) cp.push_back(CopyJob{e.U, A->Urow[i] + (size_t)b * c, (int64_t)e.r * b});
+        c += e.r;
+      }
+    }
+    std::vector<OzColJob> acj;
+    std::vector<int> acol;
+    for (int j = 0; j <= p; ++j) {  // column panels: those of columns k..p change, those before k go
+      if (j >= k && j == nb - 1) continue;
+      release.push_back(AV[j]);
+      A->Vcol[j] = nullptr;
+      A->vlen[j] = 0;
+      if (M.oz) {
+        dfree(ctx, M.AVs[j]);
+        M.AVs[j] = nullptr;
+      }
+      if (j < k) continue;
+      int64_t len = 0;
+      for (int i = j + 1; i < nb; ++i) len += src(i, j).r;
+      A->Vcol[j] = static_cast<double*>(dalloc(ctx, sizeof(double) * (size_t)std::max<int64_t>(len, 1) * b));
+      A->vlen[j] = len;
+      int64_t c = 0;
+      for (int i = j + 1; i < nb; ++i) {
+        const Src e = src(i, j);
+        A->voff[ix(A, i, j)] = c;
+        if (e.r > 0) cp.push_back(CopyJob{e.V, A->Vcol[j] + (size_t)b * c, (int64_t)e.r * b});
+        c += e.r;
+      }
+      if (M.oz && len > 0) {
+        M.AVs[j] = static_cast<int8_t*>(dalloc(ctx, 8 * (size_t)b * len));
+        OzColJob cj{A->Vcol[j], M.AVs[j], M.dAVe + j, b, (int)len, 0, b};
+        cj.emax = M.dAVmax + j;
+        acj.push_back(cj);
+        acol.push_back(j);
+      }
+    }
+    batched_copy(ctx, cp);
+    for (double* q : release) dfree(ctx, q);
+    for (int j : acol) oz_absmax(ctx, 1, (int64_t)b * A->vlen[j], A->Vcol[j], M.dAVmax + j);
+    oz_split_cols(ctx, acj);
+  }
+
+  // denseUpdates (Algorithm 9): once column k is final, every later diagonal tile of a pivoting matrix
+  // takes its term, A(i,i) -= U_ik (V_ik^T V_ik) U_ik^T, so that at the next step the tiles hold
+  // A(i,i) - D_i for the pivot selection (whole tiles: the norm is that of the symmetric tile).
+  void pivot_dense_updates(const std::vector<Mat*>& L) {
+    int64_t gt = 0, et = 0;
+    for (Mat* Mp : L)
+      if (Mp->piv && Mp->live && Mp->nops > 0)
+        for (int i = Mp->k + 1; i < Mp->nb; ++i) {
+          const int r = Mp->F->rank[ix(Mp->F, i, Mp->k)];
+          gt += (int64_t)r * r;
+          et += (int64_t)Mp->b * r;
+        }
+    if (et == 0) return;
+    double* G = bPivG.need<double>((size_t)gt);
+    double* E = bPivE.need<double>((size_t)et);
+    std::vector<GemmJob<double>> jg, je, jd;
+    int64_t go = 0, eo = 0;
+    for (Mat* Mp : L) {
+      Mat& M = *Mp;
+      if (!M.piv || !M.live || M.nops == 0) continue;
+      tlr_mat* F = M.F;
+      const int b = M.b;
+      for (int i = M.k + 1; i < M.nb; ++i) {
+        const int r = F->rank[ix(F, i, M.k)];
+        if (r == 0) continue;
+        const double* U = Uptr(F, i, M.k);
+        const double* V = Vptr(F, i, M.k);
+        jg.push_back(job<double>(TN, r, r, V, b, V, b, b, G + go, r, 1.0, 0.0));
+        je.push_back(job<double>(NN, b, r, U, b, G + go, r, r, E + eo, b, 1.0, 0.0));
+        jd.push_back(job<double>(NT, b, b, E + eo, b, U, b, r, F->diag + (size_t)i * b * b, b, -1.0, 1.0));
+        M.fl_exec += 2.0 * b * r * r * 2.0 + 2.0 * b * b * r;
+        go += (int64_t)r * r;
+        eo += (int64_t)b * r;
+      }
+    }
+    gemm<double>(ctx, TN, jg);
+    gemm<double>(ctx, NN, je);
+    gemm<double>(ctx, NT, jd);
+  }
+
   void step_columns() {
     std::vector<Mat*> L;
     for (auto& M : mats)
       if (M->live && !M->done) L.push_back(M.get());
     if (L.empty()) return;
+    select_pivots(L);
     // ---------------------------------------------------------------- Gram factors
     prof_mark(ctx, PH_GRAM);
     {
@@ -994,7 +1242,9 @@ struct Session {
     // updateDense on the tensor cores (side stream): D_k += E Urow_k^T with E = -[U_kj G_kj]_j split into
     // chunk planes per column and the transposed U-panel planes as the right operand; exact integer totals
     // need K <= 16384
-    auto dense_split = [&](const Mat& M) { return M.o.compensation != TLR_COMP_SCHUR && M.oz && M.Kk > 0 && M.Kk <= 16384; };
+    auto dense_split = [&](const Mat& M) {
+      return M.o.compensation != TLR_COMP_SCHUR && M.oz && !M.piv && M.Kk > 0 && M.Kk <= 16384;
+    };
     int8_t* dsp = nullptr;
     int* dse = nullptr;
     unsigned long long* dsm = nullptr;
@@ -1039,7 +1289,7 @@ struct Session {
         const int b = M.b;
         double* Akk = F->diag + (size_t)M.k * b * b;
         const double* G = static_cast<const double*>(M.G.p);
-        if (M.Kk > 0) {
+        if (M.Kk > 0 && !M.piv) {  // with tile pivoting D_k is already in the tile
           double* E = M.E.need<double>((size_t)b * M.Kk);
           const bool sp = pass == 0 && dense_split(M);
           for (int j = 0; j < M.k; ++j) {
@@ -1077,7 +1327,8 @@ struct Session {
             jd.push_back(g);
           }
         }
-        if (M.o.compensation == TLR_COMP_SHIFT && M.o.shift != 0.0) shifts.push_back(DiagJob{Akk, b, b, M.o.shift});
+        if (M.o.compensation == TLR_COMP_SHIFT && M.o.shift != 0.0 && !M.piv)
+          shifts.push_back(DiagJob{Akk, b, b, M.o.shift});
         int mi = 0;
         for (; mi < nm; ++mi)
           if (mats[mi].get() == Mp) break;
@@ -1450,7 +1701,7 @@ struct Session {
     oz_split_cols(ctx, usl);
     for (Mat* Mp : L)
       if (Mp->live && Mp->mixed && Mp->nops > 0) panel_tile_norms(ctx, Mp->F, Mp->k, Mp->nL, bnrm);
-  
+    pivot_dense_updates(L);
     for (Mat* Mp : L) Mp->stepped = true;
   }
 };
@@ -1511,10 +1762,7 @@ tlr_status tlr_session_add(tlr_session* s, tlr_mat* A, double eps, const tlr_opt
   tlr_opts o;
   if (opts) o = *opts; else tlr_opts_default(&o);
   if (o.bs <= 0) o.bs = 16;
-  if (o.bs > 64 || o.bs > A->b || o.precision < TLR_PREC_FP64 || o.precision > TLR_PREC_MIXED ||
-      o.compensation < TLR_COMP_NONE || o.compensation > TLR_COMP_MODCHOL ||
-      (o.compensation == TLR_COMP_MODCHOL && (ldl || A->b > 2048)) || (s->S.bs >= 0 && o.bs != s->S.bs))
-    return TLR_ERR_ARG;
+  if (!tlr::factor_opts_ok(o, ldl, A->N, A->b) || (s->S.bs >= 0 && o.bs != s->S.bs)) return TLR_ERR_ARG;
   SESSION_TRY
   *ticket = s->S.add(A, eps, o, ldl);
   return TLR_OK;

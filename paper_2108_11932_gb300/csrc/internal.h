@@ -132,6 +132,9 @@ void mat_drop_plans(tlr_ctx* ctx, tlr_mat* M);  // solve plans (and their graphs
 void mat_destroy(tlr_ctx* ctx, tlr_mat* M);
 tlr_mat* mat_new(int64_t N, int d, int b);
 void ensure_ucap(tlr_ctx* ctx, tlr_mat* F, int i, int64_t extra);
+// The rules of the factorization options (bs already defaulted), shared by tlr_potrf / tlr_ldlt /
+// tlr_factor_batch, tlr_session_add and tlr_submit.
+bool factor_opts_ok(const tlr_opts& o, int ldl, int64_t N, int b);
 
 // Batched left-looking TLR Cholesky / LDL^T over several matrices (factor.cu).
 // On return status[m] is TLR_OK (mats[m] now holds its factor) or an error

@@ -165,11 +165,10 @@ tlr_status tlr_submit(tlr_ctx* ctx, const tlr_request* r, uint64_t* ticket) {
       r->nrhs < 0 || r->nrhs > 1024 || (r->nrhs > 0 && !r->rhs) || r->ldl < 0 || r->ldl > 1 ||
       r->kernel.type != TLR_KERNEL_EXP || !(r->kernel.ell > 0) || !(r->kernel.nugget > -1.0))
     return TLR_ERR_ARG;
-  const int bs = r->opts.bs > 0 ? r->opts.bs : 16;
-  if (bs > 64 || bs > r->b || r->opts.precision < TLR_PREC_FP64 || r->opts.precision > TLR_PREC_MIXED ||
-      r->opts.compensation < TLR_COMP_NONE || r->opts.compensation > TLR_COMP_MODCHOL ||
-      (r->opts.compensation == TLR_COMP_MODCHOL && r->ldl))
-    return TLR_ERR_ARG;
+  tlr_opts ro = r->opts;
+  if (ro.bs <= 0) ro.bs = 16;
+  const int bs = ro.bs;
+  if (!tlr::factor_opts_ok(ro, r->ldl, r->N, r->b)) return TLR_ERR_ARG;
   try {
     if (!ctx->server) ctx->server = new Server(ctx);
     Server& sv = *ctx->server;

@@ -1107,6 +1107,21 @@ static void sym_mul(tlr_ctx* ctx, const tlr_mat* M, int nrhs, const double* X, i
     return TLR_ERR_CUDA;                            \
   }
 
+namespace tlr {
+bool factor_opts_ok(const tlr_opts& o, int ldl, int64_t N, int b) {
+  if (o.bs < 1 || o.bs > 64 || o.bs > b) return false;
+  if (o.precision < TLR_PREC_FP64 || o.precision > TLR_PREC_MIXED) return false;
+  if (o.compensation < TLR_COMP_NONE || o.compensation > TLR_COMP_MODCHOL) return false;
+  if (o.compensation == TLR_COMP_MODCHOL && (ldl || b > 2048)) return false;  // Algorithm 8: Cholesky
+  if (o.pivot < TLR_PIVOT_NONE || o.pivot > TLR_PIVOT_FROBENIUS) return false;
+  if (o.pivot != TLR_PIVOT_NONE &&  // Algorithm 9: Cholesky, FP64, no padded tile to move
+      (ldl || o.precision != TLR_PREC_FP64 || N % b != 0 ||
+       (o.compensation != TLR_COMP_NONE && o.compensation != TLR_COMP_SHIFT)))
+    return false;
+  return true;
+}
+}  // namespace tlr
+
 extern "C" {
 
 void tlr_opts_default(tlr_opts* o) {
@@ -1285,14 +1300,11 @@ tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* S, tlr_mat** D) {
   ABI_END
 }
 
+
 static tlr_status check_factor_args(const tlr_mat* A, double eps, const tlr_opts& o, int ldl) {
   if (!A || !(eps > 0)) return TLR_ERR_ARG;
   if (A->state != 0) return TLR_ERR_STATE;
-  if (o.bs > 64 || o.bs > A->b || o.precision < TLR_PREC_FP64 || o.precision > TLR_PREC_MIXED ||
-      o.compensation < TLR_COMP_NONE || o.compensation > TLR_COMP_MODCHOL ||
-      (o.compensation == TLR_COMP_MODCHOL && (ldl || A->b > 2048)))
-    return TLR_ERR_ARG;
-  return TLR_OK;
+  return tlr::factor_opts_ok(o, ldl, A->N, A->b) ? TLR_OK : TLR_ERR_ARG;
 }
 
 static tlr_status factor_abi(tlr_ctx* ctx, tlr_mat* A, double eps, const tlr_opts* opts, int ldl) {

@@ -108,7 +108,13 @@ def test_submit_rejects_bad_requests_without_gpu(lib):
             setattr(r, k, v)
         return r
     bad = [req(N=0), req(d=4), req(eps=0.0), req(b=0), req(nrhs=2), req(ldl=2), req(kernel=lib.Kernel(1, 0.1, 0.0)),
-           req(kernel=lib.Kernel(0, 0.1, -1.0)), req(opts=lib.default_opts(bs=8)), req(points=None)]
+           req(kernel=lib.Kernel(0, 0.1, -1.0)), req(opts=lib.default_opts(bs=8)), req(points=None),
+           # tile pivoting (Algorithm 9): Cholesky only, FP64, no padded tile (N a multiple of b)
+           req(opts=lib.default_opts(bs=4, pivot=lib.PIVOT_FROBENIUS), ldl=1),
+           req(opts=lib.default_opts(bs=4, pivot=lib.PIVOT_FROBENIUS), N=7),
+           req(opts=lib.default_opts(bs=4, pivot=lib.PIVOT_FROBENIUS, precision=lib.PREC_MIXED)),
+           req(opts=lib.default_opts(bs=4, pivot=lib.PIVOT_FROBENIUS, compensation=lib.COMP_SCHUR)),
+           req(opts=lib.default_opts(bs=4, pivot=2))]
     for r in bad:
         assert so.tlr_submit(ctypes.cast(dummy_ctx, ctypes.c_void_p), ctypes.byref(r), ctypes.byref(t)) == lib.ERR_ARG
     assert so.tlr_submit(None, ctypes.byref(req()), ctypes.byref(t)) == lib.ERR_ARG
