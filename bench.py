@@ -434,24 +434,31 @@ def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
     reps = 3
     for vname, veps, vprec, vldl, *vrest in args.variant_list:
         vpiv = bool(vrest and vrest[0])
-        if (veps, vprec, vldl, vpiv) == (eps, prec, False, False):
+        vtrim = bool(len(vrest) > 1 and vrest[1])
+        if (veps, vprec, vldl, vpiv, vtrim) == (eps, prec, False, False, False):
             continue
         vo = T.default_opts(bs=w["bs"], seed=w["seed"], precision=vprec,
                             pivot=T.PIVOT_FROBENIUS if vpiv else T.PIVOT_NONE)
         try:
-            cs, fs = [], []
+            cs, fs, ts = [], [], []
             for r in range(reps):
-                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0, e1, e2, et = (torch.cuda.Event(enable_timing=True) for _ in range(4))
                 ctx.split_planes(reset=True)
                 e0.record(stream)
                 A = ctx.compress_ordered(pts, perm, w["b"], veps, w["ell"], w["nugget"], vo)
+                et.record(stream)
+                if vtrim:  # ARA -> SVD rank trimming of the compressed matrix before the factorization
+                    r_ara, b_ara = A.info()["mean_rank"], A.info()["bytes"]
+                    A.trim(veps)
+                    r_trim, b_trim = A.info()["mean_rank"], A.info()["bytes"]
                 e1.record(stream)
                 c_planes, c_bytes = ctx.split_planes(reset=True)
                 (A.ldlt if vldl else A.potrf)(veps, vo)
                 e2.record(stream)
                 f_planes, f_bytes = ctx.split_planes(reset=True)
                 torch.cuda.synchronize()
-                cs.append(e0.elapsed_time(e1) / 1e3)
+                cs.append(e0.elapsed_time(et) / 1e3)
+                ts.append(et.elapsed_time(e1) / 1e3)
                 fs.append(e1.elapsed_time(e2) / 1e3)
                 inf = A.info()
                 ld = A.logdet()[0]
@@ -461,11 +468,15 @@ def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
             f = statistics.median(fs)
             variants[vname] = {"eps": veps, "precision": ["fp64", "fp32", "mixed"][vprec],
                                "factorization": "ldlt" if vldl else ("chol_pivoted" if vpiv else "chol"),
+                               "trimmed_input": vtrim,
                                "factor_s": f,
                                "compress_s": statistics.median(cs), "reps": reps,
                                "tflops_exec": inf["flops_exec"] / f / 1e12,
                                "tflops_model": inf["flops_model"] / f / 1e12, "mean_rank": inf["mean_rank"],
                                "logdet": ld, **({"tiles_moved": moved} if vpiv else {}),
+                               **({"trim_s": statistics.median(ts), "input_mean_rank_ara": r_ara,
+                                   "input_mean_rank_trimmed": r_trim, "input_bytes_ara": b_ara,
+                                   "input_bytes_trimmed": b_trim} if vtrim else {}),
                                "split_planes": {"compress": {f"s{i}": c_planes[i] for i in range(1, 9) if c_planes[i]},
                                                 "factor": {f"s{i}": f_planes[i] for i in range(1, 9) if f_planes[i]},
                                                 "chunk_bytes_compress": c_bytes, "chunk_bytes_factor": f_bytes}}
@@ -832,6 +843,8 @@ def main():
     vl += [(f"fp64_eps{hi:g}", hi, 0, False), (f"fp64_ldlt_eps{hi:g}", hi, 0, True)]
     # tile-pivoted Cholesky (Algorithm 9) at both thresholds
     vl += [(f"fp64_pivot_eps{lo:g}", lo, 0, False, True), (f"fp64_pivot_eps{hi:g}", hi, 0, False, True)]
+    # ARA -> SVD rank trimming of the compressed matrix (Section 6), then the factorization
+    vl += [(f"fp64_trim_eps{hi:g}", hi, 0, False, False, True)]
     args.variant_list = [] if args.no_variants else vl
     if args.impl == "reference":
         run_reference(args, w, args.eps)

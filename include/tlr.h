@@ -148,6 +148,12 @@ tlr_status tlr_compress_ordered(tlr_ctx* ctx, const double* pts, const int64_t* 
                                 int d, const tlr_kernel* kernel, int b, double eps,
                                 const tlr_opts* opts, tlr_mat** A);
 
+/* Rank trimming of every off-diagonal tile U_ij V_ij^T of A, a compressed matrix (state A) or a factor,
+ * as tlr_trim_tiles does for one tile: ranks never grow and each tile's error is its first dropped
+ * singular value (<= eps); U_ij keeps orthonormal columns.  In place (new panels).  Errors: TLR_ERR_ARG,
+ * TLR_ERR_STATE (a failed factorization), TLR_ERR_LIMIT (as tlr_trim_tiles). */
+tlr_status tlr_trim(tlr_ctx* ctx, tlr_mat* A, double eps);
+
 /* Deep copy (device-to-device) of a TLR matrix or factor. */
 tlr_status tlr_copy(tlr_ctx* ctx, const tlr_mat* src, tlr_mat** dst);
 
@@ -384,6 +390,17 @@ tlr_status tlr_omega(tlr_ctx* ctx, uint64_t seed, uint32_t stream, uint32_t k, u
 tlr_status tlr_ara_dense(tlr_ctx* ctx, int nops, int n, const double* T, int bs, double eps,
                          uint64_t seed, uint32_t stream, uint32_t k, double* Q, double* B,
                          int* rank);
+
+/* ARA -> SVD rank trimming (Section 6: the post-processing step that applies the SVD to each low-rank
+ * tile to bring its rank down to the minimum) of `ntiles` tiles Q_t B_t^T of one shape: Q and B device,
+ * ntiles blocks of b x r column-major (leading dimension b, block t at t * b * r), Q_t with orthonormal
+ * columns.  B_t = W S Z^T (Householder QR of B_t, then one-sided Jacobi SVD of its triangular factor);
+ * the r'_t singular values above eps are kept, in descending order: Qout_t = Q_t Z_r, Bout_t = B_t Z_r
+ * (= W_r S_r), columns r'_t .. r - 1 zero; rank (host, ntiles) receives r'_t.  The tile's error is its
+ * first dropped singular value (<= eps).  Errors: TLR_ERR_ARG (null pointers, b < 1, r outside 0..b,
+ * eps <= 0), TLR_ERR_LIMIT (b above ~11000: the CTA's shared memory). */
+tlr_status tlr_trim_tiles(tlr_ctx* ctx, int ntiles, int b, int r, const double* Q, const double* B, double eps,
+                          double* Qout, double* Bout, int* rank);
 
 /* Dense FP64 Cholesky (lower, in place) of an n x n device matrix (lda >= n);
  * *info (host) = -1 on success, else the first failing column. */

@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
 
 This module holds no arithmetic of the factorization method: it only draws
-points, right-hand sides and power-iteration start vectors from fixed seeds.
+points, right-hand sides, power-iteration start vectors and synthetic low-rank
+tiles of a prescribed spectrum from fixed seeds.
 Random numbers the method itself draws (the ARA Gaussian blocks) are NOT
 generated here; each side implements its own counter-based generator.
 
@@ -65,6 +66,27 @@ def rhs(N: int, nrhs: int, seed: int) -> np.ndarray:
 def start_vector(N: int, seed: int = 12345) -> np.ndarray:
     """Gaussian start vector for power iterations (stream 2)."""
     return gaussian(seed, 2, N)
+
+
+def lowrank_tiles(ntiles: int, b: int, r: int, seed: int, smax: float = 10.0, smin: float = 1e-10):
+    """Synthetic low-rank tiles Q_t B_t^T with a prescribed spectrum (rank-trimming inputs): Q_t and W_t
+    (b x r) and Z_t (r x r) with orthonormal columns (orthonormalized Gaussians), s_t log-spaced from smax
+    down to smin with a seeded jitter of up to a tenth of a step, and B_t = W_t diag(s_t) Z_t^T, so that the
+    singular values of Q_t B_t^T are s_t exactly.  Returns Q, B (ntiles, b, r) and s (ntiles, r), stream 3."""
+    g = gaussian(seed, 3, ntiles * (2 * b * r + r * r + r))
+    Q = np.empty((ntiles, b, r))
+    B = np.empty((ntiles, b, r))
+    s = np.empty((ntiles, r))
+    step = (np.log10(smax) - np.log10(smin)) / max(r - 1, 1)
+    o = 0
+    for t in range(ntiles):
+        Qt = np.linalg.qr(g[o:o + b * r].reshape(b, r))[0]; o += b * r
+        Wt = np.linalg.qr(g[o:o + b * r].reshape(b, r))[0]; o += b * r
+        Zt = np.linalg.qr(g[o:o + r * r].reshape(r, r))[0]; o += r * r
+        jit = 0.1 * step * np.tanh(g[o:o + r]); o += r
+        st = 10.0 ** (np.log10(smax) - step * np.arange(r) + jit)
+        Q[t], B[t], s[t] = Qt, (Wt * st) @ Zt.T, st
+    return Q, B, s
 
 
 # Workload recipes (paper Section 6 and the covariance configurations used by

@@ -117,6 +117,8 @@ def _load():
         "tlr_ara_dense": (C.c_int, [P, C.c_int, C.c_int, P, C.c_int, C.c_double, C.c_uint64, C.c_uint32,
                                     C.c_uint32, P, P, P]),
         "tlr_dense_potrf": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int)]),
+        "tlr_trim_tiles": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, C.c_double, P, P, P]),
+        "tlr_trim": (C.c_int, [P, P, C.c_double]),
         "tlr_dense_modchol": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "tlr_dense_ldlt": (C.c_int, [P, C.c_int, P, C.c_int, C.POINTER(C.c_int)]),
         "tlr_dense_trsm": (C.c_int, [P, C.c_int, P, C.c_int, C.c_int, C.c_int, P, C.c_int]),
@@ -309,6 +311,18 @@ class Context:
                "tlr_ara_dense")
         return Q, B, r
 
+    def trim_tiles(self, Q, B, eps: float):
+        """ARA -> SVD rank trimming of tiles Q[t] B[t]^T: Q, B (ntiles, r, b) tensors whose [t] slices are
+        column-major b x r blocks.  Returns (Q', B', ranks) with the first ranks[t] columns kept."""
+        torch = self.torch
+        nt, r, b = Q.shape
+        Qc, Bc = Q.contiguous(), B.contiguous()
+        Qo, Bo = torch.empty_like(Qc), torch.empty_like(Bc)
+        rk = np.zeros(nt, dtype=np.int32)
+        _check(_load().tlr_trim_tiles(self.h, nt, b, r, _ptr(Qc), _ptr(Bc), eps, _ptr(Qo), _ptr(Bo),
+                                      rk.ctypes.data), "tlr_trim_tiles")
+        return Qo, Bo, rk
+
     def dense_modchol(self, A):
         """Modified Cholesky (Algorithm 8) in place; returns (modified, info)."""
         mod, info = C.c_int(0), C.c_int(0)
@@ -454,6 +468,11 @@ class Matrix:
 
     def potrf(self, eps: float, opts: Opts | None = None):
         _check(_load().tlr_potrf(self.ctx.h, self.h, eps, C.byref(opts) if opts else None), "tlr_potrf")
+        return self
+
+    def trim(self, eps: float):
+        """ARA -> SVD rank trimming of every off-diagonal tile (in place; ranks never grow)."""
+        _check(_load().tlr_trim(self.ctx.h, self.h, eps), "tlr_trim")
         return self
 
     def ldlt(self, eps: float, opts: Opts | None = None):

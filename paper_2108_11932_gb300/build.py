@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtlr_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["k_gemm.cu", "k_misc.cu", "tlr.cu", "factor.cu", "kdtree.cpp", "k_noalloc.cu", "k_ozaki.cu", "k_solve.cu",
-           "serve.cu", "k_orth.cu", "k_modchol.cu"]
+           "serve.cu", "k_orth.cu", "k_modchol.cu", "k_trim.cu"]
 
 
 def _nvcc() -> str:

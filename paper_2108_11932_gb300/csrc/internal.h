@@ -132,6 +132,16 @@ void mat_drop_plans(tlr_ctx* ctx, tlr_mat* M);  // solve plans (and their graphs
 void mat_destroy(tlr_ctx* ctx, tlr_mat* M);
 tlr_mat* mat_new(int64_t N, int d, int b);
 void ensure_ucap(tlr_ctx* ctx, tlr_mat* F, int i, int64_t extra);
+// ARA -> SVD rank trimming (k_trim.cu): tile B (b x r, leading dimension b) of a tile Q B^T
+struct TrimTile {
+  const double* B;
+  int r;
+};
+bool trim_fits(int b);
+// ranks r' (host) and, per tile, Z_r (device, r x r', leading dimension r, inside `work`)
+void trim_tiles(tlr_ctx* ctx, int b, const std::vector<TrimTile>& tiles, double eps, std::vector<int>& rank,
+                std::vector<double*>& Zs, Buf& work);
+void trim_matrix(tlr_ctx* ctx, tlr_mat* M, double eps);
 // The rules of the factorization options (bs already defaulted), shared by tlr_potrf / tlr_ldlt /
 // tlr_factor_batch, tlr_session_add and tlr_submit.
 bool factor_opts_ok(const tlr_opts& o, int ldl, int64_t N, int b);

@@ -1639,6 +1639,49 @@ tlr_status tlr_dense_modchol(tlr_ctx* ctx, int n, double* A, int lda, int* modif
   ABI_END
 }
 
+tlr_status tlr_trim_tiles(tlr_ctx* ctx, int ntiles, int b, int r, const double* Q, const double* B, double eps,
+                          double* Qout, double* Bout, int* rank) {
+  if (!ctx || ntiles < 0 || b < 1 || r < 0 || r > b || !(eps > 0) || (ntiles > 0 && !rank) ||
+      (ntiles > 0 && r > 0 && (!Q || !B || !Qout || !Bout)))
+    return TLR_ERR_ARG;
+  if (!trim_fits(b)) return TLR_ERR_LIMIT;
+  ABI_BEGIN
+  std::vector<int> rk(ntiles, 0);
+  if (r > 0 && ntiles > 0) {
+    std::vector<TrimTile> tl(ntiles);
+    for (int t = 0; t < ntiles; ++t) tl[t] = TrimTile{B + (size_t)t * b * r, r};
+    Buf work(ctx);
+    std::vector<double*> Zs;
+    trim_tiles(ctx, b, tl, eps, rk, Zs, work);
+    const size_t bytes = sizeof(double) * (size_t)ntiles * b * r;
+    TLR_CUDA(cudaMemsetAsync(Qout, 0, bytes, ctx->stream));
+    TLR_CUDA(cudaMemsetAsync(Bout, 0, bytes, ctx->stream));
+    std::vector<GemmJob<double>> jobs;
+    for (int t = 0; t < ntiles; ++t) {
+      if (rk[t] == 0) continue;
+      const size_t o = (size_t)t * b * r;
+      jobs.push_back(job<double>(NN, b, rk[t], Q + o, b, Zs[t], r, r, Qout + o, b, 1.0, 0.0));
+      jobs.push_back(job<double>(NN, b, rk[t], B + o, b, Zs[t], r, r, Bout + o, b, 1.0, 0.0));
+    }
+    gemm<double>(ctx, NN, jobs);
+    TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  for (int t = 0; t < ntiles; ++t) rank[t] = rk[t];
+  return TLR_OK;
+  ABI_END
+}
+
+tlr_status tlr_trim(tlr_ctx* ctx, tlr_mat* A, double eps) {
+  if (!ctx || !A || !(eps > 0)) return TLR_ERR_ARG;
+  if (A->state != 0 && A->state != 1 && A->state != 2) return TLR_ERR_STATE;
+  if (!trim_fits(A->b)) return TLR_ERR_LIMIT;
+  ABI_BEGIN
+  trim_matrix(ctx, A, eps);
+  TLR_CUDA(cudaStreamSynchronize(ctx->stream));
+  return TLR_OK;
+  ABI_END
+}
+
 tlr_status tlr_dense_ldlt(tlr_ctx* ctx, int n, double* A, int lda, int* info) {
   if (!ctx || !A || n < 0 || lda < n || !info) return TLR_ERR_ARG;
   ABI_BEGIN

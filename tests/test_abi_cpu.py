@@ -57,6 +57,8 @@ def test_null_arguments_are_rejected_without_gpu(lib):
     it = (ctypes.c_int * 1)()
     rr = (ctypes.c_double * 1)()
     assert so.tlr_pcg(None, None, None, 1, None, 1, None, 1, 1e-6, 10, it, rr) == lib.ERR_ARG
+    assert so.tlr_trim(None, None, 1e-6) == lib.ERR_ARG
+    assert so.tlr_trim_tiles(None, 1, 16, 4, None, None, 1e-6, None, None, None) == lib.ERR_ARG
 
 
 @pytest.mark.parametrize("N,d,b,seed", [(4096, 2, 256, 0), (5000, 3, 512, 1), (1000, 1, 64, 3), (777, 2, 100, 4),
