@@ -462,6 +462,13 @@ def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
                 fs.append(e1.elapsed_time(e2) / 1e3)
                 inf = A.info()
                 ld = A.logdet()[0]
+                if vtrim:  # and of the factor
+                    e3, e4 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                    e3.record(stream)
+                    A.trim(veps)
+                    e4.record(stream)
+                    torch.cuda.synchronize()
+                    ftrim = (e3.elapsed_time(e4) / 1e3, A.info()["mean_rank"], A.info()["bytes"])
                 # tile exchanges of Algorithm 9: positions whose tile is not the construction's
                 moved = int(np.sum(A.perm()[:: w["b"]] != np.asarray(perm)[:: w["b"]])) if vpiv else 0
                 A.free()
@@ -476,7 +483,9 @@ def run_variants(args, ctx, T, torch, w, o, pts, perm, stream, eps, prec, out):
                                "logdet": ld, **({"tiles_moved": moved} if vpiv else {}),
                                **({"trim_s": statistics.median(ts), "input_mean_rank_ara": r_ara,
                                    "input_mean_rank_trimmed": r_trim, "input_bytes_ara": b_ara,
-                                   "input_bytes_trimmed": b_trim} if vtrim else {}),
+                                   "input_bytes_trimmed": b_trim, "factor_trim_s": ftrim[0],
+                                   "factor_mean_rank_trimmed": ftrim[1], "factor_bytes": inf["bytes"],
+                                   "factor_bytes_trimmed": ftrim[2]} if vtrim else {}),
                                "split_planes": {"compress": {f"s{i}": c_planes[i] for i in range(1, 9) if c_planes[i]},
                                                 "factor": {f"s{i}": f_planes[i] for i in range(1, 9) if f_planes[i]},
                                                 "chunk_bytes_compress": c_bytes, "chunk_bytes_factor": f_bytes}}

@@ -2,7 +2,8 @@
 // to each low-rank tile to bring its rank down to the minimum).
 //
 // A tile Q B^T with orthonormal Q (b x r) has the singular values of B.  One CTA per tile: a Householder
-// QR of B (B = H R, the reflectors applied to the trailing columns in place, in a global working copy),
+// QR of B (B = H R, the reflectors applied to the trailing columns in place, in a working copy in global
+// memory: the QR runs at GB300's FP64 rate, and a small shared footprint lets several tiles share an SM),
 // then one-sided Jacobi (Hestenes) on X = R^T: plane rotations of column pairs in the parallel
 // round-robin order (r/2 disjoint pairs per round, r - 1 rounds per sweep) until no pair is rotated,
 // giving X J = Y with orthogonal columns whose norms are the singular values sigma of R (and of B), and
@@ -11,6 +12,8 @@
 // form Z_r (r x r'); Q' = Q Z_r and B' = B Z_r = W_r S_r are two batched GEMMs.  Every reduction has a
 // fixed order, so the result depends on the tile only.
 #include <math.h>
+
+#include <map>
 
 #include "internal.h"
 
@@ -46,8 +49,9 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// XS: X = R^T in shared memory (r * r doubles after the reflector vector)
-template <bool XS>
+// MODE 0: X = R^T in global memory; 1: X in shared memory (after the reflector vector, the singular
+// values and their order)
+template <int MODE>
 __global__ void __launch_bounds__(TR_T) k_trim(const TrimDev* __restrict__ jobs, int b, double eps) {
   const TrimDev J = jobs[blockIdx.x];
   const int r = J.r, tid = threadIdx.x, w = tid >> 5, l = tid & 31;
@@ -56,13 +60,15 @@ __global__ void __launch_bounds__(TR_T) k_trim(const TrimDev* __restrict__ jobs,
   double* red = v + b;                             // TR_W
   double* sig = red + TR_W;                        // r
   int* pos = reinterpret_cast<int*>(sig + r);      // r
-  double* X = XS ? reinterpret_cast<double*>(pos + r + (r & 1)) : J.X;
+  double* nxt = reinterpret_cast<double*>(pos + r + (r & 1));
+  const int rp = r | 1;  // X's leading dimension, odd: the pair threads below read distinct banks
+  double* X = MODE == 1 ? nxt : J.X;
+  double* W = J.W;
   __shared__ int rot, keep;
   if (r == 0) {
     if (tid == 0) *J.rank = 0;
     return;
   }
-  double* W = J.W;
   for (int64_t e = tid; e < (int64_t)b * r; e += TR_T) W[e] = J.B[e];
   __syncthreads();
   // ---- Householder QR: R in the upper triangle of W's first r rows
@@ -83,8 +89,10 @@ __global__ void __launch_bounds__(TR_T) k_trim(const TrimDev* __restrict__ jobs,
       for (int c = j + 1 + w; c < r; c += TR_W) {  // H = I - tau v v^T on the trailing columns
         double* col = W + (size_t)c * b;
         double d = 0.0;
+#pragma unroll 4
         for (int m = j + l; m < b; m += 32) d += v[m] * col[m];
         const double f = tau * warp_sum(d);
+#pragma unroll 4
         for (int m = j + l; m < b; m += 32) col[m] -= f * v[m];
       }
     }
@@ -93,17 +101,18 @@ __global__ void __launch_bounds__(TR_T) k_trim(const TrimDev* __restrict__ jobs,
   // ---- X = R^T (lower triangular)
   for (int64_t e = tid; e < (int64_t)r * r; e += TR_T) {
     const int m = (int)(e % r), c = (int)(e / r);
-    X[e] = c <= m ? W[c + (size_t)m * b] : 0.0;
+    X[m + (size_t)c * rp] = c <= m ? W[c + (size_t)m * b] : 0.0;
   }
   __syncthreads();
-  // ---- one-sided Jacobi on X, round-robin pairs (position 0 fixed, 1 .. n-1 rotating)
+  // ---- one-sided Jacobi on X, round-robin pairs (position 0 fixed, 1 .. n-1 rotating), one thread per
+  // pair: GB300's FP64 unit is the bound, and a thread's serial dot products waste no lanes on reductions
   const int n = r + (r & 1);
   const double tol = (double)r * 0x1p-53;
   for (int sweep = 0; sweep < TR_SWEEPS; ++sweep) {
     if (tid == 0) rot = 0;
     __syncthreads();
     for (int t = 0; t < n - 1; ++t) {
-      for (int k = w; k < n / 2; k += TR_W) {
+      for (int k = tid; k < n / 2; k += TR_T) {
         int p = k == 0 ? 0 : (k - 1 + t) % (n - 1) + 1;
         int q = (n - 2 - k + t) % (n - 1) + 1;  // the position n - 1 - k >= 1
         if (p > q) {
@@ -112,28 +121,25 @@ __global__ void __launch_bounds__(TR_T) k_trim(const TrimDev* __restrict__ jobs,
           q = x;
         }
         if (q >= r) continue;  // the padding index of an odd r
-        double* xp = X + (size_t)p * r;
-        double* xq = X + (size_t)q * r;
+        double* xp = X + (size_t)p * rp;
+        double* xq = X + (size_t)q * rp;
         double a = 0.0, bb = 0.0, g = 0.0;
-        for (int m = l; m < r; m += 32) {
+        for (int m = 0; m < r; ++m) {
           const double x = xp[m], y = xq[m];
-          a += x * x;
-          bb += y * y;
-          g += x * y;
+          a = fma(x, x, a);
+          bb = fma(y, y, bb);
+          g = fma(x, y, g);
         }
-        a = warp_sum(a);
-        bb = warp_sum(bb);
-        g = warp_sum(g);
         if (g != 0.0 && fabs(g) > tol * sqrt(a * bb)) {
           const double z = (bb - a) / (2.0 * g);
           const double tt = fabs(z) < 1e150 ? (z >= 0.0 ? 1.0 : -1.0) / (fabs(z) + sqrt(1.0 + z * z)) : 0.5 / z;
           const double c = 1.0 / sqrt(1.0 + tt * tt), sn = c * tt;
-          for (int m = l; m < r; m += 32) {
+          for (int m = 0; m < r; ++m) {
             const double x = xp[m], y = xq[m];
             xp[m] = c * x - sn * y;
             xq[m] = sn * x + c * y;
           }
-          if (l == 0) rot = 1;
+          rot = 1;
         }
       }
       __syncthreads();
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(TR_T) k_trim(const TrimDev* __restrict__ jobs,
   }
   // ---- singular values, their descending order, the kept columns
   for (int c = w; c < r; c += TR_W) {
-    const double* xc = X + (size_t)c * r;
+    const double* xc = X + (size_t)c * rp;
     double s2 = 0.0;
     for (int m = l; m < r; m += 32) s2 += xc[m] * xc[m];
     s2 = warp_sum(s2);
@@ -166,23 +172,23 @@ __global__ void __launch_bounds__(TR_T) k_trim(const TrimDev* __restrict__ jobs,
     const int ps = pos[c];
     if (ps >= keep) continue;
     const double inv = 1.0 / sig[c];
-    const double* xc = X + (size_t)c * r;
+    const double* xc = X + (size_t)c * rp;
     double* zc = J.Zs + (size_t)ps * r;
     for (int m = l; m < r; m += 32) zc[m] = xc[m] * inv;
   }
   if (tid == 0) *J.rank = keep;
 }
 
-size_t trim_smem(int b, int r, bool xs) {
+size_t trim_smem(int b, int r, int mode) {
   return sizeof(double) * ((size_t)b + TR_W + r) + sizeof(int) * ((size_t)r + (r & 1)) +
-         (xs ? sizeof(double) * (size_t)r * r : 0);
+         (mode == 1 ? sizeof(double) * (size_t)r * (r | 1) : 0);
 }
 
 constexpr size_t TRIM_SMEM_MAX = 220 * 1024;
 
 }  // namespace
 
-bool trim_fits(int b) { return trim_smem(b, b, false) <= TRIM_SMEM_MAX; }
+bool trim_fits(int b) { return trim_smem(b, b, 0) <= TRIM_SMEM_MAX; }
 
 void trim_tiles(tlr_ctx* ctx, int b, const std::vector<TrimTile>& tiles, double eps, std::vector<int>& rank,
                 std::vector<double*>& Zs, Buf& work) {
@@ -196,29 +202,36 @@ void trim_tiles(tlr_ctx* ctx, int b, const std::vector<TrimTile>& tiles, double 
   std::vector<int64_t> off(nt);
   for (int t = 0; t < nt; ++t) {
     off[t] = tot;
-    tot += (int64_t)tiles[t].r * (b + 2 * (int64_t)tiles[t].r);
+    tot += (int64_t)tiles[t].r * (b + (tiles[t].r | 1) + (int64_t)tiles[t].r);
   }
   double* ws = work.need<double>((size_t)std::max<int64_t>(tot, 1) + (size_t)(nt + 1) / 2 + 1);
   int* dr = reinterpret_cast<int*>(ws + std::max<int64_t>(tot, 1));
-  std::vector<TrimDev> js[2];
+  // launch groups: the most on-chip mode the tile's rank allows, then rank classes (so that a group's
+  // shared memory, sized by its largest rank, does not hold many small tiles to one CTA per SM)
+  static const int cls[] = {8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024, 1 << 30};
+  std::map<std::pair<int, int>, std::vector<TrimDev>> groups;
   for (int t = 0; t < nt; ++t) {
     const int r = tiles[t].r;
     double* W = ws + off[t];
     double* X = W + (size_t)b * r;
-    TrimDev d{tiles[t].B, W, X, X + (size_t)r * r, dr + t, r};
+    TrimDev d{tiles[t].B, W, X, X + (size_t)r * (r | 1), dr + t, r};
     Zs[t] = d.Zs;
-    js[trim_smem(b, r, true) <= TRIM_SMEM_MAX ? 1 : 0].push_back(d);
+    const int mode = trim_smem(b, r, 1) <= TRIM_SMEM_MAX ? 1 : 0;
+    int c = 0;
+    while (cls[c] < r) ++c;
+    groups[{mode, c}].push_back(d);
   }
-  for (int xs = 0; xs < 2; ++xs) {
-    if (js[xs].empty()) continue;
+  for (auto& g : groups) {
+    const int mode = g.first.first;
+    std::vector<TrimDev>& js = g.second;
     int rmax = 0;
-    for (const TrimDev& d : js[xs]) rmax = std::max(rmax, d.r);
-    const size_t sm = trim_smem(b, rmax, xs == 1);
-    auto kern = xs ? k_trim<true> : k_trim<false>;
+    for (const TrimDev& d : js) rmax = std::max(rmax, d.r);
+    const size_t sm = trim_smem(b, rmax, mode);
+    auto kern = mode == 1 ? k_trim<1> : k_trim<0>;
     if (sm > 48 * 1024) TLR_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    for (size_t o = 0; o < js[xs].size(); o += 65535) {
-      const int cnt = (int)std::min<size_t>(65535, js[xs].size() - o);
-      const TrimDev* dj = static_cast<const TrimDev*>(upload(ctx, js[xs].data() + o, sizeof(TrimDev) * cnt));
+    for (size_t o = 0; o < js.size(); o += 65535) {
+      const int cnt = (int)std::min<size_t>(65535, js.size() - o);
+      const TrimDev* dj = static_cast<const TrimDev*>(upload(ctx, js.data() + o, sizeof(TrimDev) * cnt));
       TLR_SITE_PRE(ctx);
       kern<<<cnt, TR_T, sm, ctx->stream>>>(dj, b, eps);
       TLR_LAUNCH_CHECK(ctx);
