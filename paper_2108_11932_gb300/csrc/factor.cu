@@ -701,13 +701,14 @@ struct Session {
   Buf bMcW, bMcT;                        // modified Cholesky workspaces (main stream)
   Buf bOzU0, bOzU0p;                     // slices of the column's U0 blocks (split sampling / projection)
   Buf bPiv, bPivG, bPivE, bSwap, bSwapV;  // tile pivoting: norms, dense-update products, exchange staging
+  Buf bPivS, bPivX;                       // tile pivoting: chunk planes and bounds of the dense updates
   int* d_one = nullptr;
   AraStats total;
   explicit Session(tlr_ctx* c)
       : ctx(c), bnrm(c), bQ(c), bTab(c), bInfo(c), bTmp(c), bTmpMain(c), bOm(c), bOm32(c), bW(c), bY32(c), bP(c), bZ(c),
         bQ32(c), bB32(c), bOzMax(c), bOzS(c), bOzE(c), bOzX(c), bOzEx(c), bOzOs(c), bOzOe(c), bOzWs(c), bOzWe(c),
         bOne(c), bOzDs(c), bOzDe(c), bOzDm(c), bMcW(c), bMcT(c), bOzU0(c), bOzU0p(c), bPiv(c), bPivG(c), bPivE(c),
-        bSwap(c), bSwapV(c) {
+        bSwap(c), bSwapV(c), bPivS(c), bPivX(c) {
     static const int one = 1;
     d_one = bOne.need<int>(1);
     TLR_CUDA(cudaMemcpyAsync(d_one, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
@@ -1094,43 +1095,121 @@ struct Session {
   }
 
   // denseUpdates (Algorithm 9): once column k is final, every later diagonal tile of a pivoting matrix
-  // takes its term, A(i,i) -= U_ik (V_ik^T V_ik) U_ik^T, so that at the next step the tiles hold
-  // A(i,i) - D_i for the pivot selection (whole tiles: the norm is that of the symmetric tile).
+  // takes its term, A(i,i) -= U_ik (V_ikᵀ V_ik) U_ikᵀ, so that at the next step the tiles hold
+  // A(i,i) - D_i for the pivot selection (whole tiles: the norm is that of the symmetric tile).  The
+  // Gram factor and E = U_ik G are FP64 GEMMs.  The b x b update A(i,i) -= E U_ik^T is an FP64 GEMM
+  // for ranks below 32 and a product on the tensor cores by exact splitting otherwise (tiles of a
+  // multiple of 16): with K = r that small, the split product's per-block cost (a 128 x 16 FP64 output
+  // block read and written per CTA) exceeds the 2 b^2 r FP64 flops (C3 at eps 1e-2: 1.01 s against
+  // 1.21 s all split; C2 at eps 1e-8, ranks ~100: 1.54 s all FP64 against 1.49 s).  For the split
+  // products E = -U_ik G is split per tile against its own bound (a matrix's blocks padded to its
+  // largest split rank of the step, so that one launch takes every bound) and U_ik, whose columns are
+  // orthonormal, transposed against the fixed bound 2.
   void pivot_dense_updates(const std::vector<Mat*>& L) {
-    int64_t gt = 0, et = 0;
-    for (Mat* Mp : L)
-      if (Mp->piv && Mp->live && Mp->nops > 0)
-        for (int i = Mp->k + 1; i < Mp->nb; ++i) {
-          const int r = Mp->F->rank[ix(Mp->F, i, Mp->k)];
-          gt += (int64_t)r * r;
-          et += (int64_t)Mp->b * r;
-        }
-    if (et == 0) return;
+    struct Up {
+      Mat* M;
+      int i, r;
+      int64_t go, eo;
+      bool sp;  // the update on the tensor cores
+    };
+    auto split = [](const Mat& M, int r) { return M.oz && r >= 32; };
+    std::vector<Up> ups;
+    std::vector<int64_t> rmax(L.size(), 0), ebase(L.size(), 0);
+    int64_t gt = 0, et = 0, nsp = 0;
+    for (size_t u = 0; u < L.size(); ++u) {
+      Mat& M = *L[u];
+      if (!M.piv || !M.live || M.nops == 0) continue;
+      for (int i = M.k + 1; i < M.nb; ++i) {
+        const int r = M.F->rank[ix(M.F, i, M.k)];
+        if (split(M, r)) rmax[u] = std::max<int64_t>(rmax[u], r);
+      }
+      ebase[u] = et;
+      for (int i = M.k + 1; i < M.nb; ++i) {  // the split blocks first: contiguous for their bounds
+        const int r = M.F->rank[ix(M.F, i, M.k)];
+        if (r == 0 || !split(M, r)) continue;
+        ups.push_back(Up{&M, i, r, gt, et, true});
+        gt += (int64_t)r * r;
+        et += (int64_t)M.b * rmax[u];
+        ++nsp;
+      }
+      for (int i = M.k + 1; i < M.nb; ++i) {
+        const int r = M.F->rank[ix(M.F, i, M.k)];
+        if (r == 0 || split(M, r)) continue;
+        ups.push_back(Up{&M, i, r, gt, et, false});
+        gt += (int64_t)r * r;
+        et += (int64_t)M.b * r;
+      }
+    }
+    if (ups.empty()) return;
     double* G = bPivG.need<double>((size_t)gt);
     double* E = bPivE.need<double>((size_t)et);
+    if (nsp) TLR_CUDA(cudaMemsetAsync(E, 0, sizeof(double) * (size_t)et, ctx->stream));  // zero padding
     std::vector<GemmJob<double>> jg, je, jd;
-    int64_t go = 0, eo = 0;
-    for (Mat* Mp : L) {
-      Mat& M = *Mp;
-      if (!M.piv || !M.live || M.nops == 0) continue;
+    for (const Up& w : ups) {
+      Mat& M = *w.M;
       tlr_mat* F = M.F;
-      const int b = M.b;
-      for (int i = M.k + 1; i < M.nb; ++i) {
-        const int r = F->rank[ix(F, i, M.k)];
-        if (r == 0) continue;
-        const double* U = Uptr(F, i, M.k);
-        const double* V = Vptr(F, i, M.k);
-        jg.push_back(job<double>(TN, r, r, V, b, V, b, b, G + go, r, 1.0, 0.0));
-        je.push_back(job<double>(NN, b, r, U, b, G + go, r, r, E + eo, b, 1.0, 0.0));
-        jd.push_back(job<double>(NT, b, b, E + eo, b, U, b, r, F->diag + (size_t)i * b * b, b, -1.0, 1.0));
-        M.fl_exec += 2.0 * b * r * r * 2.0 + 2.0 * b * b * r;
-        go += (int64_t)r * r;
-        eo += (int64_t)b * r;
-      }
+      const int b = M.b, r = w.r;
+      const double* U = Uptr(F, w.i, M.k);
+      const double* V = Vptr(F, w.i, M.k);
+      jg.push_back(job<double>(TN, r, r, V, b, V, b, b, G + w.go, r, 1.0, 0.0));
+      je.push_back(job<double>(NN, b, r, U, b, G + w.go, r, r, E + w.eo, b, w.sp ? -1.0 : 1.0, 0.0));
+      if (!w.sp)
+        jd.push_back(job<double>(NT, b, b, E + w.eo, b, U, b, r, F->diag + (size_t)w.i * b * b, b, -1.0, 1.0));
+      M.fl_exec += 2.0 * b * r * r * 2.0 + 2.0 * b * b * r;
     }
     gemm<double>(ctx, TN, jg);
     gemm<double>(ctx, NN, je);
     gemm<double>(ctx, NT, jd);
+    if (nsp == 0) return;
+    // chunk planes: E (columns along b, acol) and U_ik^T (rows along its r columns, padded to 16)
+    int64_t pe = 0, pu = 0;
+    for (const Up& w : ups)
+      if (w.sp) {
+        pe += (int64_t)8 * w.M->b * w.r;
+        pu += (int64_t)8 * w.M->b * oz_ld(w.r);
+      }
+    int8_t* Es = bPivS.need<int8_t>((size_t)(pe + pu));
+    int8_t* Us = Es + pe;
+    unsigned long long* em = bPivX.need<unsigned long long>((size_t)nsp * 2);
+    int* ee = reinterpret_cast<int*>(em + nsp);
+    TLR_CUDA(cudaMemsetAsync(Us, 0, (size_t)pu, ctx->stream));
+    std::vector<OzColJob> cj;
+    std::vector<OzJob> dj;
+    int64_t oe = 0, ou = 0, t = 0;
+    for (size_t u = 0; u < L.size(); ++u) {  // one bound per E block, one launch per matrix
+      Mat& M = *L[u];
+      if (!M.piv || !M.live || M.nops == 0 || !M.oz) continue;
+      int64_t nblk = 0;
+      for (const Up& w : ups) nblk += (w.M == &M && w.sp) ? 1 : 0;
+      if (nblk) oz_absmax(ctx, (int)nblk, (int64_t)M.b * rmax[u], E + ebase[u], em + t);
+      t += nblk;
+    }
+    t = 0;
+    for (const Up& w : ups) {
+      Mat& M = *w.M;
+      if (!w.sp) continue;
+      const int b = M.b, r = w.r, tl = oz_ld(r);
+      OzColJob ce{E + w.eo, Es + oe, ee + t, b, r, 0, b};
+      ce.emax = em + t;
+      cj.push_back(ce);
+      OzColJob cu{Uptr(M.F, w.i, M.k), Us + ou, nullptr, b, r, 0, b};
+      cu.plane = (size_t)b * tl;
+      cu.efix = 1;
+      cu.tld = tl;
+      cj.push_back(cu);
+      OzJob d{Es + oe, Us + ou, ee + t, d_one, M.F->diag + (size_t)w.i * b * b, (size_t)b * r, (size_t)b * tl, b, b, b,
+              b, r};
+      d.acol = 1;
+      d.ldb = tl;
+      d.eB_stride = 0;
+      d.accumulate = 1;
+      dj.push_back(d);
+      oe += (int64_t)8 * b * r;
+      ou += (int64_t)8 * b * tl;
+      ++t;
+    }
+    oz_split_cols(ctx, cj);
+    oz_gemm(ctx, dj);
   }
 
   void step_columns() {
