@@ -749,6 +749,34 @@ def run_orth(args):
     ctx.close()
 
 
+def run_trim(args):
+    """ARA -> SVD rank trimming of synthetic tiles (the target of the committed k_trim profile): batches of
+    graded-spectrum tiles at the tile shapes of C3 (b = 1024, r = 16) and C2 (b = 512, r = 100), eps between
+    two prescribed singular values; three calls each, the last timed with CUDA events.  The FP64 work per
+    tile is b r^2 FMAs for the QR and ~3.5 r^3 per Jacobi sweep."""
+    import torch
+    import paper_2108_11932_gb300 as T
+    T.build()
+    ctx = T.Context(0)
+    out = {"mode": "trim", "cases": []}
+    for (n, b, r) in [(2000, 1024, 16), (300, 512, 100)]:
+        Q, B, s = inputs.lowrank_tiles(n, b, r, seed=1)
+        q = torch.tensor(np.ascontiguousarray(np.transpose(Q, (0, 2, 1))), device="cuda:0")
+        bt = torch.tensor(np.ascontiguousarray(np.transpose(B, (0, 2, 1))), device="cuda:0")
+        eps = float(np.sqrt(s[0][r // 2] * s[0][r // 2 + 1]))
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, _, rk = ctx.trim_tiles(q, bt, eps)
+            e1.record()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["cases"].append({"tiles": n, "b": b, "r": r, "kept": int(rk[0]), "ms": ms, "us_per_tile": ms * 1e3 / n,
+                             "qr_gflop": 2.0 * n * b * r * r / 1e9})
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def run_peaks(args):
     """Peak rates of this GPU: FP64 DFMA loop (library), and torch.matmul GEMMs (8192^3) per dtype."""
     import torch
@@ -833,7 +861,7 @@ def main():
                     help="skip the accuracy check against the stored oracle values (outside the timed region)")
     ap.add_argument("--profile-compress", action="store_true",
                     help="phases mode: profile the compression as well as the factorization")
-    ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve", "peaks", "phases", "pcg", "orth"])
+    ap.add_argument("--mode", default="factor", choices=["factor", "batch", "serve", "peaks", "phases", "pcg", "orth", "trim"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-chunk", type=int, default=64, help="matrices built and factored together")
     ap.add_argument("--requests", type=int, default=200)
@@ -867,6 +895,8 @@ def main():
         run_phases(args, w, args.eps)
     elif args.mode == "pcg":
         run_pcg(args, w)
+    elif args.mode == "trim":
+        run_trim(args)
     elif args.mode == "orth":
         run_orth(args)
     else:
