@@ -34,7 +34,7 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-# nb = 8, 12, 16 and a 3D case; every case exchanges tiles at most steps.  The smallest relative gap
+# nb = 8-16, 2D and 3D; every case exchanges tiles at most steps.  The smallest relative gap
 # between the two largest updated-tile norms at any step (from the oracle) is 5.6e-4 or more, far above
 # the difference rounding and eps-level compression can make, so the pivot order is unique.
 CASES = {
@@ -42,6 +42,9 @@ CASES = {
     "cov2d_1536_b128": dict(N=1536, d=2, ell=0.1, nugget=1e-4, b=128, bs=16, seed=5, eps=1e-8),
     "cov3d_2k_b256": dict(N=2048, d=3, ell=0.2, nugget=1e-4, b=256, bs=32, seed=4, eps=1e-6),
     "cov2d_4k_b256": dict(N=4096, d=2, ell=0.1, nugget=1e-4, b=256, bs=16, seed=6, eps=1e-6),
+    # tiles that are not a multiple of 16: FP64 products throughout (no chunk planes to exchange)
+    "cov2d_1k_b100": dict(N=1000, d=2, ell=0.1, nugget=1e-4, b=100, bs=8, seed=7, eps=1e-6),
+    "cov3d_1200_b120": dict(N=1200, d=3, ell=0.2, nugget=1e-4, b=120, bs=8, seed=2, eps=1e-6),
 }
 
 
