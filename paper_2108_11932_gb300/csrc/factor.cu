@@ -57,7 +57,6 @@ struct Mat {
   // finished columns' terms are added as each column ends, not by updateDense), and tile rows and
   // columns are exchanged before a step; the compressed input A is rewritten to the exchanged order
   bool piv = false;
-  int swaps = 0;
   std::vector<float*> AU32, AV32, FU32, FV32;
   std::vector<int64_t> fu32cap;
   // 7-bit chunk planes (int8) of F's U panels relative to 2 (their columns are orthonormal basis
@@ -954,7 +953,6 @@ struct Session {
     tlr_mat* F = M.F;
     const int nb = M.nb, b = M.b;
     auto sg = [&](int i) { return i == k ? p : (i == p ? k : i); };
-    ++M.swaps;
     {  // diagonal tiles, ordered points, device permutation: swap block k and block p
       const size_t bb = (size_t)b * b, pb = (size_t)b * A->d;
       double* t = bSwap.need<double>(std::max(bb, pb + (size_t)b));
