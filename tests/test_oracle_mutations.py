@@ -206,3 +206,30 @@ def test_update_sum_stopping_one_column_early_is_caught(monkeypatch):
     orig = tlr._update_sum
     monkeypatch.setattr(tlr, "_update_sum", lambda F, i, l, k: orig(F, i, l, max(k - 1, 0)))
     assert not _ou_ok() and not _ou_ok(ldl=True)
+
+
+# ---------------------------------------------------------------- rank trimming (Section 6)
+def _trim_variant(keep, scale=True, transpose=True):
+    def trim(Q, B, eps):
+        W, sv, Zt = np.linalg.svd(B, full_matrices=False)
+        r = keep(sv, eps)
+        Z = Zt[:r].T if transpose else Zt[:, :r]
+        return Q @ Z, (W[:, :r] * sv[:r]) if scale else W[:, :r]
+    return trim
+
+
+def test_unmutated_trim_variant_passes():
+    from test_oracle_pins import trim_pins_hold
+    assert trim_pins_hold(_trim_variant(lambda sv, eps: int(np.count_nonzero(sv > eps))))
+
+
+@pytest.mark.parametrize("name,variant", [
+    ("keeps the values below eps", _trim_variant(lambda sv, eps: int(np.count_nonzero(sv < eps)))),
+    ("drops one value too many", _trim_variant(lambda sv, eps: int(np.count_nonzero(sv > eps)) - 1)),
+    ("keeps one value too many", _trim_variant(lambda sv, eps: int(np.count_nonzero(sv > eps)) + 1)),
+    ("forgets the singular values", _trim_variant(lambda sv, eps: int(np.count_nonzero(sv > eps)), scale=False)),
+    ("takes Z's rows for its columns", _trim_variant(lambda sv, eps: int(np.count_nonzero(sv > eps)), transpose=False)),
+])
+def test_trim_mistakes_are_caught(name, variant):
+    from test_oracle_pins import trim_pins_hold
+    assert not trim_pins_hold(variant), name

@@ -481,6 +481,34 @@ def test_trim_gives_the_truncated_svd_rank_and_error():
             assert np.allclose(Qt.T @ Qt, np.eye(Qt.shape[1]), atol=1e-12)
 
 
+def trim_pins_hold(trim=None) -> bool:
+    """Rank trimming pinned by a closed form: tiles with a prescribed spectrum (inputs.lowrank_tiles),
+    eps halfway between two prescribed singular values.  The trimmed rank is exactly the number of
+    values above eps, the kept singular values are the prescribed ones, the error is the first dropped
+    value (Eckart-Young), and the new U has orthonormal columns."""
+    trim = trim or compress.trim
+    Q, B, s = inputs.lowrank_tiles(3, 96, 20, seed=11)
+    step = 11.0 / 19
+    for k in (4, 12):
+        eps = 10.0 ** (1.0 - step * (k + 0.5))
+        for t in range(3):
+            Qt, Bt = trim(Q[t], B[t], eps)
+            q = Qt.shape[1]
+            if q != k + 1 or Bt.shape[1] != q:
+                return False
+            if not np.allclose(Qt.T @ Qt, np.eye(q), atol=1e-12):
+                return False
+            if not np.allclose(np.linalg.svd(Qt @ Bt.T, compute_uv=False)[:q], s[t][:q], rtol=1e-10, atol=0):
+                return False
+            if abs(np.linalg.norm(Q[t] @ B[t].T - Qt @ Bt.T, 2) - s[t][q]) > 1e-10 * s[t][q] + 1e-14:
+                return False
+    return True
+
+
+def test_trim_matches_the_prescribed_spectrum():
+    assert trim_pins_hold()
+
+
 # Hand-computed kernel entries in 2D and 3D (Section 6: A_ij = exp(-||x_i - x_j||_2 / ell)): point
 # pairs whose Euclidean distance is exact (3-4-5 and 1-2-2 triangles).  A wrong norm (L1, squared,
 # max), a dropped coordinate or a swapped length scale gives a different value for at least one.
