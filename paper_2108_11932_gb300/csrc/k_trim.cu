@@ -197,7 +197,7 @@ void trim_tiles(tlr_ctx* ctx, int b, const std::vector<TrimTile>& tiles, double 
   Zs.assign(nt, nullptr);
   if (nt == 0) return;
   TLR_REQUIRE(trim_fits(b), TLR_ERR_LIMIT, "rank trimming: tile size above the shared-memory limit");
-  // workspace per tile: W (b r), X (r^2, used when it does not fit in shared memory), Zs (r^2); ranks
+  // workspace per tile: W (b r), X (r (r | 1), used when it does not fit in shared memory), Zs (r^2); ranks
   int64_t tot = 0;
   std::vector<int64_t> off(nt);
   for (int t = 0; t < nt; ++t) {
